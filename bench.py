@@ -1,0 +1,275 @@
+"""Benchmark of the OCI time step on GB300 (one JSON line on rank 0).
+
+Workload: 2^18-cell slab, S16, one group, 3 repeating regions of 1024 cells with
+optical thickness 0.01 / 0.1 / 1, scattering ratio c = 0.9, mean free time
+tau = 0.1, unit source, vacuum, tol 1e-10, FP64 (the 2^18-cell config).  A
+"step" is one time step: per-step constant, OCI sweeps to convergence on the
+device, carry / scalar flux / balance.  Metric: cell-unknown updates per second
+= J * 4NG * sweeps / time.
+
+--impl reference times the CPU FP64 oracle on a bounded sample of the same
+workload (the host cores of this machine).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2503_00264_gb300 import workloads as W  # noqa: E402
+
+METRIC = "OCI cell-unknown updates/s"
+UNIT = "updates/s"
+SAMPLE_J = 3072
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--c", type=float, default=0.9)
+    ap.add_argument("--tau", type=float, default=0.1)
+    ap.add_argument("--J", type=int, default=2 ** 18)
+    ap.add_argument("--solver", default="structured", choices=["structured", "dense"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload(args, J=None):
+    return W.slab_3region(c=args.c, tau=args.tau, J=J or args.J)
+
+
+def config(args, p):
+    return {"workload": p.name, "J": p.J, "N": p.N, "G": p.G, "c": args.c, "tau": args.tau,
+            "regions": "3 x 1024 cells, delta 0.01/0.1/1", "tol": p.tol, "solver": args.solver,
+            "l2": "inputs larger than L2: Psi ping-pong + per-step constant = "
+                  f"{3 * p.unknowns * 8 / 1e6:.0f} MB per sweep vs 129 MB L2",
+            "parallelism": "replicas (independent slabs per rank)"}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Clocks:
+    """nvidia-smi sampler for the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", delete=False, suffix=".csv")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-lms", "100", "-i", str(index)], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = max(mx, float(r[2]))
+                for k, nm in enumerate(names):
+                    if r[5 + k].strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(args, budget_s=12.0, steps=None):
+    """The oracle as it stands on the host cores, on the first SAMPLE_J cells of
+    the workload (3 regions of 1024 cells)."""
+    import oracle
+    p = workload(args, SAMPLE_J)
+    o = oracle.Oracle(p)
+    done_steps, upd, t_tot = 0, 0, 0.0
+    while True:
+        t0 = time.perf_counter()
+        r = o.step()
+        t_tot += time.perf_counter() - t0
+        upd += p.unknowns * r["iters"]
+        done_steps += 1
+        if (steps is not None and done_steps >= steps) or (steps is None and t_tot >= budget_s):
+            break
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": upd / t_tot, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{SAMPLE_J} cells (3 regions of 1024) of the same slab, {done_steps} time steps, "
+                      f"{t_tot:.1f} s of convergence loops"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    p = workload(args, SAMPLE_J)
+    o = oracle.Oracle(p)
+    for _ in range(args.warmup):
+        o.step()
+    upd, t_tot = 0, 0.0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        r = o.step()
+        t_tot += time.perf_counter() - t0
+        upd += p.unknowns * r["iters"]
+    v = upd / t_tot
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_tot / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config(args, workload(args)),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{SAMPLE_J} cells of the same slab per step"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2503_00264_gb300 import oci
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group(backend="nccl", device_id=torch.device("cuda", local))
+    stream = torch.cuda.Stream()
+    p = workload(args)
+    solver = oci.SOLVER_DENSE_LU if args.solver == "dense" else oci.SOLVER_STRUCTURED
+    peak_fp64 = oci.fp64_peak()
+    s = oci.Solver(p, solver=solver, stream=stream.cuda_stream)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    for _ in range(args.warmup):
+        s.step()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clk = Clocks(local)
+    barrier()
+    e0.record(stream)
+    sweeps, launches = 0, 0
+    stats = []
+    for _ in range(args.steps):
+        st = s.step()
+        stats.append(st)
+        sweeps += st["iters"]
+        launches += 1 + 2 * st["iters"] + 2
+    e1.record(stream)
+    barrier()
+    clocks = clk.stop()
+    ms = max_over_ranks(e0.elapsed_time(e1))
+    total_sweeps = sweeps * world  # replicas: every rank does the same work
+    value = p.unknowns * total_sweeps / (ms * 1e-3)
+
+    # dominant kernel: the fused sweep; its launch time from a run of n sweeps
+    n_sw = 50
+    psi_keep = s.psi()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    f0.record(stream)
+    s.iterate(n_sw)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    sweep_ms = f0.elapsed_time(f1) / n_sw
+    s.set_psi(psi_keep)
+    NG = p.N * p.G
+    flops_cell = 68 * NG + 32 * p.G * p.G
+    bytes_cell = 96 * NG + 4
+    flops = flops_cell * p.J
+    achieved_tf = flops / (sweep_ms * 1e-3) / 1e12
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"hbm_gbs": 6800.0}
+    hbm_gbs = bytes_cell * p.J / (sweep_ms * 1e-3) / 1e9
+
+    # end to end: host psi_prev in, host phi out, every step
+    pp_host = torch.zeros((p.J, p.G, p.N, 2), dtype=torch.float64).pin_memory()
+    phi_host = torch.zeros((p.J, p.G, 4), dtype=torch.float64).pin_memory()
+    pp0, t0 = s.state()
+    pp_host.copy_(torch.from_numpy(pp0))
+    barrier()
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    e2e_sweeps = 0
+    for _ in range(args.steps):
+        s.set_state(pp_host, t0)
+        st = s.step()
+        s.phi(phi_host)
+        e2e_sweeps += st["iters"]
+    g1.record(stream)
+    barrier()
+    e2e_ms = max_over_ranks(g0.elapsed_time(g1))
+    e2e_value = p.unknowns * e2e_sweeps * world / (e2e_ms * 1e-3)
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config(args, p),
+            "sweeps_per_step": sweeps / args.steps,
+            "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": peak_fp64 / 1e12, "unit": "TFLOP/s",
+                         "frac": achieved_tf * 1e12 / peak_fp64, "traffic": None,
+                         "kernel": "k_oci_sweep (FP64 structured cell solve)",
+                         "peak_source": "measured live: register-only DFMA loop (oci_probe_fp64_peak)",
+                         "hbm_achieved_gbs": hbm_gbs, "hbm_peak_gbs": peaks.get("hbm_gbs"),
+                         "hbm_frac": hbm_gbs / peaks.get("hbm_gbs", 6800.0),
+                         "sweep_us": sweep_ms * 1e3, "flops_per_cell": flops_cell, "bytes_per_cell": bytes_cell},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": p.J * p.G * p.N * 2 * 8,
+                    "d2h_bytes_per_step": p.J * p.G * 4 * 8},
+            "gpu_launches": launches,
+            "clocks": clocks}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    s.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

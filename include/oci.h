@@ -1,0 +1,196 @@
+/*
+ * oci.h -- C ABI of liboci: one-cell inversion (OCI) and source iteration (SI)
+ * for the simple-corner-balance (SCB) x multiple-balance (MB) discretisation of
+ * time-dependent multigroup slab S_N transport, on NVIDIA GB300 (sm_103a).
+ *
+ * Method: arXiv 2503.00264 (Morgan, Variansyah, Palmer, Niemeyer).
+ *   problem statement ............. Sec. 2.1, Eq. sn_nte
+ *   space-time discretisation ..... Eqs. scb-mb-a..d and the two closures
+ *   per-cell OCI system ........... Eqs. oci, Aja, Aj, rhs_sg, scatter, x_vec
+ *   multigroup system ............. Sec. 2.4, Eqs. scatter_mg, fullOCIlhs/rhs
+ *   stop rule ..................... Sec. 2.1 (||Psi^{l+1}-Psi^l||_2 < eps(1-rho_e))
+ *   OCI loop ...................... Algorithm 2
+ *   SI loop ....................... Algorithm 1, App. A
+ *
+ * Conventions shared by every entry point
+ *   - Every function returns int status: OCI_OK (0) or a negative OCI_E_* code;
+ *     oci_last_error() then gives a message (thread-local).  No C++ exception
+ *     crosses the ABI.
+ *   - Arrays are dense, row-major (C order), FP64 unless stated otherwise.
+ *   - Array arguments marked "host or device" may be host memory (pageable or
+ *     pinned) or CUDA device memory of the handle's device; the library copies
+ *     with cudaMemcpyAsync(..., cudaMemcpyDefault) on the handle's stream and
+ *     synchronises that stream before returning.
+ *   - Ownership: the caller owns every array it passes; oci_setup copies what it
+ *     needs, so inputs may be freed once it returns.  The library owns the
+ *     handle and all device memory behind it; oci_destroy releases them.
+ *   - A handle is not thread-safe; distinct handles are independent.
+ *   - Invalid arguments return OCI_E_INVAL before any device work.
+ *   - Angles are Gauss-Legendre ordinates in ascending mu (the first N/2 are
+ *     negative), with weights summing to 2.
+ *   - Unknowns of one cell are ordered idx(g,m,p) = (g*N + m)*4 + p with
+ *     p = 0 kL, 1 kR, 2 hL, 3 hR (k: time average over the step, h: time edge
+ *     t_{k+1/2}; L/R: left/right corner) -- Eq. x_vec extended to groups.
+ */
+#ifndef OCI_H
+#define OCI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+enum {
+  OCI_OK = 0,
+  OCI_E_INVAL = -1,     /* bad argument (detected before any device work)      */
+  OCI_E_NOMEM = -2,     /* device or host allocation failed                     */
+  OCI_E_CUDA = -3,      /* a CUDA call failed; see oci_last_error()             */
+  OCI_E_NOCONV = -4,    /* max_iter sweeps without meeting the stop rule; the
+                           step is NOT committed (t and psi_{k-1/2} unchanged,
+                           the last iterate stays readable)                     */
+  OCI_E_SINGULAR = -5,  /* a local block could not be factored                  */
+  OCI_E_NONFINITE = -6, /* the convergence norm became NaN or Inf               */
+  OCI_E_TIMEOUT = -7,   /* a bounded device-side wait gave up                   */
+  OCI_E_STATE = -8      /* call not valid in the handle's current state         */
+};
+
+/* arithmetic of the OCI cell solve (oci_problem.precision) */
+enum {
+  OCI_FP64 = 0,       /* everything in IEEE FP64                                   */
+  OCI_TF32_IR = 1,    /* block apply on tensor cores in TF32 (FP32 accumulation),
+                         FP64 residual, norm, balance and carry (defect correction) */
+  OCI_BF16X3_IR = 2   /* block apply as three BF16 products (hi*hi + hi*lo + lo*hi),
+                         FP32 accumulation, FP64 residual/norm/balance/carry        */
+};
+
+/* initial iterate of every time step (oci_problem.guess) */
+enum {
+  OCI_GUESS_PREV = 0, /* the handle's current Psi: the previous step's converged
+                         Psi, zero before the first step, or what oci_set_psi set */
+  OCI_GUESS_ZERO = 1  /* zero                                                      */
+};
+
+/* local solver of the FP64 form (oci_problem.solver) */
+enum {
+  OCI_SOLVER_AUTO = 0,       /* structured solve                                  */
+  OCI_SOLVER_STRUCTURED = 1, /* exact solve of A_j through its angle blocks and a
+                                4G x 4G scalar-flux system per cell type; cells
+                                that share (material, dx) share the tables        */
+  OCI_SOLVER_DENSE_LU = 2    /* (4NG <= 1024) dense A_j of every cell factored once on the GPU
+                                (warp-cooperative LU, partial pivoting), then one
+                                forward/back substitution per cell per sweep:
+                                the paper's gesv/getrs scheme (Algorithm 2)       */
+};
+
+/* Problem description -- the arguments of Eq. sn_nte plus the iteration
+ * controls of Sec. 2.1.  Sizes: J cells, N ordinates, G groups. */
+typedef struct {
+  int32_t J, N, G, n_mat;   /* J >= 1; N even, 2 <= N <= 128; 1 <= G <= 16;
+                               4*N*G <= 2048; n_mat >= 1                              */
+  const double *dx;         /* [J] cell widths, finite and > 0                        */
+  const int32_t *mat;       /* [J] material of each cell, in [0, n_mat)               */
+  const double *sigma_t;    /* [n_mat][G] total cross section, >= 0                   */
+  const double *sigma_s;    /* [n_mat][G][G]; sigma_s[m][gp][g] = Sigma_s,gp->g >= 0  */
+  const double *v;          /* [G] speeds, > 0                                        */
+  const double *Q;          /* [J][G][4] isotropic total emission per corner and time
+                               level (kL,kR,hL,hR); the angular source is Q/2.
+                               NULL = no source                                       */
+  double dt;                /* time step, finite and > 0                              */
+  const double *psi_init;   /* [J][G][N][2] psi at t = 0 at corners (L,R); NULL = 0   */
+  const double *inc_left;   /* [G][N][2] incident flux at x = 0 for mu > 0: index 0 the
+                               time average over the step, 1 the value at t_{k+1/2};
+                               entries of mu < 0 are ignored.  NULL = vacuum          */
+  const double *inc_right;  /* [G][N][2] same at x = X for mu < 0.  NULL = vacuum     */
+  double tol;               /* eps of the stop rule, >= 0 (absolute 2-norm)           */
+  int32_t max_iter;         /* >= 1 sweeps per step                                   */
+  int32_t precision;        /* OCI_FP64 | OCI_TF32_IR | OCI_BF16X3_IR                 */
+  int32_t guess;            /* OCI_GUESS_PREV | OCI_GUESS_ZERO                        */
+  int32_t solver;           /* OCI_SOLVER_*                                           */
+  void *stream;             /* cudaStream_t for all work of the handle; NULL = the
+                               legacy default stream                                 */
+} oci_problem;
+
+/* Per-step statistics. */
+typedef struct {
+  int32_t iters;            /* sweeps taken in this step                              */
+  int32_t status;           /* OCI_OK or OCI_E_NOCONV / OCI_E_NONFINITE               */
+  double e_last;            /* ||Psi^{l+1} - Psi^l||_2 of the last sweep (FP64)       */
+  double rho_e_last;        /* e_l / e_{l-1} of the last sweep (0 if l = 0)           */
+  double balance_rel[2];    /* max over groups of |balance residual| / sum of |terms|:
+                               [0] time-average balance (Eqs. scb-mb-a + b summed),
+                               [1] time-edge balance (Eqs. scb-mb-c + d summed)       */
+  double t;                 /* simulated time after the step                          */
+  double seconds;           /* wall time of the convergence loop (CUDA events)        */
+} oci_stats;
+
+typedef struct oci_handle oci_handle;
+
+/* Validate and copy the problem, build the quadrature and the per-cell-type
+ * tables (or the per-cell dense LU factors), move everything to the device.
+ * Setup is excluded from the convergence-loop timing, as in the paper
+ * (Sec. 3.2).  *out receives a new handle on success. */
+int oci_setup(const oci_problem *p, oci_handle **out);
+
+/* One time step (Algorithm 2 and the carry of Sec. 2.1): set the initial
+ * iterate per p->guess, sweep until the stop rule holds, then commit: scalar
+ * flux, balance tallies, psi_{k+1/2} -> psi_{k-1/2}, t += dt.  The whole
+ * convergence loop runs on the device (CUDA graph with a conditional WHILE
+ * node); the host reads a small stats record once per step.  st may be NULL.
+ * Returns OCI_E_NOCONV without committing when max_iter is reached. */
+int oci_step(oci_handle *h, oci_stats *st);
+
+/* n_steps calls of oci_step.  phi_out: [n_steps][J][G][4] (host or device) or
+ * NULL; st: [n_steps] or NULL.  Stops at the first failing step and returns its
+ * status. */
+int oci_solve_transient(oci_handle *h, int32_t n_steps, double *phi_out, oci_stats *st);
+
+/* The same time step by source iteration (Algorithm 1, App. A): per (g,m)
+ * sweep the cells in the direction of flight with the 4x4 L_{c,j,g,m}, the
+ * current sweep's upstream edge and the scattering source of all groups lagged
+ * from phi^(l) (Jacobi over groups); stop rule on ||phi^{l+1} - phi^l||_2.
+ * Commits like oci_step.  Comparison path; FP64 only. */
+int si_sweep(oci_handle *h, oci_stats *st);
+
+/* Exactly n OCI (or SI) sweeps from the current iterate, no stop test, no
+ * commit; e_hist: [n] (host or device) receives e of each sweep, or NULL.
+ * For timing and for parity at a fixed sweep count. */
+int oci_iterate(oci_handle *h, int32_t n, double *e_hist);
+int si_iterate(oci_handle *h, int32_t n, double *e_hist);
+
+/* State access.  psi: [J][G][N][4]; phi: [J][G][4]; psi_prev: [J][G][N][2];
+ * bal: [G][2][5] = per group, per balance (0 time average, 1 time edge), the
+ * tallies {time, leak, collision, scatter_in, source} of the last committed
+ * step (residual = time + leak + collision - scatter_in - source).
+ * All buffers host or device. */
+int oci_get_psi(const oci_handle *h, double *psi);
+int oci_set_psi(oci_handle *h, const double *psi);
+int oci_get_phi(const oci_handle *h, double *phi);
+int oci_get_state(const oci_handle *h, double *psi_prev, double *t);
+int oci_set_state(oci_handle *h, const double *psi_prev, double t);
+int oci_get_balance(const oci_handle *h, double *bal);
+
+/* Replace the incident fluxes ([G][N][2] each, host or device, NULL = vacuum)
+ * for the following steps. */
+int oci_set_boundary(oci_handle *h, const double *inc_left, const double *inc_right);
+
+/* e of every sweep of the last oci_step / si_sweep: e_hist [max_iter] (host or
+ * device); *n receives the number of valid entries. */
+int oci_get_e_hist(const oci_handle *h, double *e_hist, int32_t *n);
+
+/* Release the handle and its device memory.  NULL is accepted. */
+void oci_destroy(oci_handle *h);
+
+/* Message of the last failure on the calling thread ("" if none). */
+const char *oci_last_error(void);
+
+/* Measured FP64 fused-multiply-add throughput of the current device in
+ * FLOP/s (a register-only DFMA loop, CUDA-event timed): the arithmetic
+ * roofline of the FP64 path.  Returns a negative status on failure. */
+int oci_probe_fp64_peak(double *flops_per_s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OCI_H */

@@ -1,0 +1,748 @@
+// oci_api.cu -- the C ABI of liboci (include/oci.h): validation, setup of the
+// per-cell-type tables, device state, the convergence loops as CUDA graphs with a
+// conditional WHILE node, and state access.
+#include <math.h>
+#include <string.h>
+
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "oci_internal.h"
+
+struct oci_handle : public oci::Handle {};
+
+namespace oci {
+
+static thread_local std::string g_err;
+void set_error(const std::string &msg) { g_err = msg; }
+int cuda_fail(cudaError_t e, const char *what) {
+  g_err = std::string(what) + ": " + cudaGetErrorString(e);
+  return OCI_E_CUDA;
+}
+
+int si_partials(const Handle &h);
+int dense_partials(const Handle &h);
+void launch_si_phi_from_psi(Handle &h, double *);
+
+#define CK(call)                                          \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);   \
+  } while (0)
+
+// ---------------------------------------------------------------- quadrature
+// Gauss-Legendre nodes/weights on [-1,1] (the paper uses Gauss-Legendre S_N
+// throughout, Sec. 1): Newton iteration on P_N from Tricomi's initial guess;
+// P_N and P_N' from the three-term recurrence.  Ascending nodes.
+static void gauss_legendre(int N, std::vector<double> &x, std::vector<double> &wt) {
+  x.assign(N, 0.0);
+  wt.assign(N, 0.0);
+  const double pi = 3.141592653589793238462643;
+  for (int k = 1; k <= (N + 1) / 2; k++) {
+    double z = (1.0 - 1.0 / (8.0 * N * N) + 1.0 / (8.0 * N * N * N)) * cos(pi * (4.0 * k - 1.0) / (4.0 * N + 2.0));
+    double dP = 1.0;
+    for (int it = 0; it < 100; it++) {
+      double pm1 = 1.0, p = z;
+      for (int n = 1; n < N; n++) {
+        const double pn = ((2.0 * n + 1.0) * z * p - n * pm1) / (n + 1.0);
+        pm1 = p;
+        p = pn;
+      }
+      dP = N * (pm1 - z * p) / (1.0 - z * z);
+      const double dz = p / dP;
+      z -= dz;
+      if (fabs(dz) <= 1e-17) break;
+    }
+    {
+      double pm1 = 1.0, p = z;
+      for (int n = 1; n < N; n++) {
+        const double pn = ((2.0 * n + 1.0) * z * p - n * pm1) / (n + 1.0);
+        pm1 = p;
+        p = pn;
+      }
+      dP = N * (pm1 - z * p) / (1.0 - z * z);
+    }
+    const double wk = 2.0 / ((1.0 - z * z) * dP * dP);
+    x[N - k] = z;       // k-th largest node
+    x[k - 1] = -z;
+    wt[N - k] = wk;
+    wt[k - 1] = wk;
+  }
+}
+
+// Dense inverse by Gauss-Jordan elimination with partial pivoting (host, FP64).
+static bool invert(int n, std::vector<double> A, std::vector<double> &inv) {
+  inv.assign((size_t)n * n, 0.0);
+  for (int i = 0; i < n; i++) inv[(size_t)i * n + i] = 1.0;
+  for (int k = 0; k < n; k++) {
+    int pr = k;
+    double best = fabs(A[(size_t)k * n + k]);
+    for (int r = k + 1; r < n; r++)
+      if (fabs(A[(size_t)r * n + k]) > best) {
+        best = fabs(A[(size_t)r * n + k]);
+        pr = r;
+      }
+    if (best == 0.0 || !std::isfinite(best)) return false;
+    if (pr != k)
+      for (int c = 0; c < n; c++) {
+        std::swap(A[(size_t)k * n + c], A[(size_t)pr * n + c]);
+        std::swap(inv[(size_t)k * n + c], inv[(size_t)pr * n + c]);
+      }
+    const double d = A[(size_t)k * n + k];
+    for (int c = 0; c < n; c++) {
+      A[(size_t)k * n + c] /= d;
+      inv[(size_t)k * n + c] /= d;
+    }
+    for (int r = 0; r < n; r++) {
+      if (r == k) continue;
+      const double f = A[(size_t)r * n + k];
+      if (f == 0.0) continue;
+      for (int c = 0; c < n; c++) {
+        A[(size_t)r * n + c] -= f * A[(size_t)k * n + c];
+        inv[(size_t)r * n + c] -= f * inv[(size_t)k * n + c];
+      }
+    }
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------- validation
+static bool finite_ge(const double *a, size_t n, double lo, bool strict) {
+  for (size_t i = 0; i < n; i++) {
+    if (!std::isfinite(a[i])) return false;
+    if (strict ? !(a[i] > lo) : !(a[i] >= lo)) return false;
+  }
+  return true;
+}
+static bool all_finite(const double *a, size_t n) {
+  for (size_t i = 0; i < n; i++)
+    if (!std::isfinite(a[i])) return false;
+  return true;
+}
+
+static int validate(const oci_problem *p) {
+  if (!p) return set_error("problem is NULL"), OCI_E_INVAL;
+  if (p->J < 1) return set_error("J must be >= 1"), OCI_E_INVAL;
+  if (p->N < 2 || p->N > kMaxN || (p->N & 1)) return set_error("N must be even, 2 <= N <= 128"), OCI_E_INVAL;
+  if (p->G < 1 || p->G > kMaxG) return set_error("G must be in [1, 16]"), OCI_E_INVAL;
+  if (4 * p->N * p->G > kMaxUnknowns) return set_error("4*N*G must be <= 2048"), OCI_E_INVAL;
+  if (p->n_mat < 1) return set_error("n_mat must be >= 1"), OCI_E_INVAL;
+  if (!p->dx || !p->mat || !p->sigma_t || !p->sigma_s || !p->v)
+    return set_error("dx, mat, sigma_t, sigma_s and v are required"), OCI_E_INVAL;
+  const size_t J = p->J, G = p->G, N = p->N, M = p->n_mat;
+  if (!finite_ge(p->dx, J, 0.0, true)) return set_error("dx must be finite and > 0"), OCI_E_INVAL;
+  for (size_t j = 0; j < J; j++)
+    if (p->mat[j] < 0 || p->mat[j] >= p->n_mat) return set_error("mat out of range"), OCI_E_INVAL;
+  if (!finite_ge(p->sigma_t, M * G, 0.0, false)) return set_error("sigma_t must be finite and >= 0"), OCI_E_INVAL;
+  if (!finite_ge(p->sigma_s, M * G * G, 0.0, false)) return set_error("sigma_s must be finite and >= 0"), OCI_E_INVAL;
+  if (!finite_ge(p->v, G, 0.0, true)) return set_error("v must be finite and > 0"), OCI_E_INVAL;
+  if (!(std::isfinite(p->dt) && p->dt > 0)) return set_error("dt must be finite and > 0"), OCI_E_INVAL;
+  if (p->Q && !all_finite(p->Q, J * G * 4)) return set_error("Q must be finite"), OCI_E_INVAL;
+  if (p->psi_init && !all_finite(p->psi_init, J * G * N * 2)) return set_error("psi_init must be finite"), OCI_E_INVAL;
+  if (p->inc_left && !all_finite(p->inc_left, G * N * 2)) return set_error("inc_left must be finite"), OCI_E_INVAL;
+  if (p->inc_right && !all_finite(p->inc_right, G * N * 2)) return set_error("inc_right must be finite"), OCI_E_INVAL;
+  if (!(std::isfinite(p->tol) && p->tol >= 0)) return set_error("tol must be finite and >= 0"), OCI_E_INVAL;
+  if (p->max_iter < 1) return set_error("max_iter must be >= 1"), OCI_E_INVAL;
+  if (p->precision < OCI_FP64 || p->precision > OCI_BF16X3_IR) return set_error("bad precision"), OCI_E_INVAL;
+  if (p->guess < OCI_GUESS_PREV || p->guess > OCI_GUESS_ZERO) return set_error("bad guess policy"), OCI_E_INVAL;
+  if (p->solver < OCI_SOLVER_AUTO || p->solver > OCI_SOLVER_DENSE_LU) return set_error("bad solver"), OCI_E_INVAL;
+  if (p->precision != OCI_FP64 && p->solver == OCI_SOLVER_DENSE_LU)
+    return set_error("the dense per-cell solver is FP64 only"), OCI_E_INVAL;
+  if (p->solver == OCI_SOLVER_DENSE_LU && 4 * p->N * p->G > 1024)
+    return set_error("the dense per-cell solver needs 4*N*G <= 1024"), OCI_E_INVAL;
+  if (p->precision != OCI_FP64)
+    return set_error("this precision form is not built"), OCI_E_INVAL;
+  return OCI_OK;
+}
+
+// ---------------------------------------------------------------- tables
+// Per unique (material, dx) cell type: L_{g,m}^{-1} (Eq. Aj), the inflow columns,
+// Mp = (I - K H)^{-1} K and K.
+static int build_tables(Handle &h, std::vector<double> &Linv, std::vector<double> &Cin, std::vector<double> &Mp,
+                        std::vector<double> &Kap, std::vector<double> &tdx, std::vector<double> &tsig) {
+  const int N = h.N, G = h.G, J = h.J;
+  std::map<std::pair<int, uint64_t>, int> ids;
+  h.h_type.assign(J, 0);
+  std::vector<std::pair<int, double>> types;
+  for (int j = 0; j < J; j++) {
+    uint64_t bits;
+    std::memcpy(&bits, &h.h_dx[j], 8);
+    auto key = std::make_pair((int)h.h_mat[j], bits);
+    auto it = ids.find(key);
+    if (it == ids.end()) {
+      const int id = (int)types.size();
+      ids.emplace(key, id);
+      types.emplace_back(h.h_mat[j], h.h_dx[j]);
+      h.h_type[j] = id;
+    } else {
+      h.h_type[j] = it->second;
+    }
+  }
+  const int T = (int)types.size();
+  h.tt.n_types = T;
+  const int G4 = 4 * G;
+  Linv.assign((size_t)T * G * N * 16, 0.0);
+  Cin.assign((size_t)T * G * N * 8, 0.0);
+  Mp.assign((size_t)T * G4 * G4, 0.0);
+  Kap.assign((size_t)T * G * G, 0.0);
+  tdx.assign(T, 0.0);
+  tsig.assign((size_t)T * G, 0.0);
+  std::vector<double> L(16), Li, KH((size_t)G4 * G4), IKH((size_t)G4 * G4), IKHinv;
+  for (int t = 0; t < T; t++) {
+    const int mt = types[t].first;
+    const double dx = types[t].second;
+    tdx[t] = dx;
+    std::vector<double> H((size_t)G * 16, 0.0);
+    for (int g = 0; g < G; g++) {
+      const double sig = h.h_sigma_t[(size_t)mt * G + g];
+      tsig[(size_t)t * G + g] = sig;
+      const double al = dx / (h.h_v[g] * h.dt);
+      for (int gp = 0; gp < G; gp++)
+        Kap[((size_t)t * G + gp) * G + g] = dx / 4.0 * h.h_sigma_s[((size_t)mt * G + gp) * G + g];
+      for (int m = 0; m < N; m++) {
+        const double mu = h.h_mu[m];
+        const double a = (fabs(mu) + dx * sig) / 2.0;
+        const double Lm[16] = {a,   mu / 2.0, al / 2.0, 0.0,      -mu / 2.0, a,   0.0,       al / 2.0,
+                               -al, 0.0,      al + a,   mu / 2.0, 0.0,       -al, -mu / 2.0, al + a};
+        L.assign(Lm, Lm + 16);
+        if (!invert(4, L, Li)) {
+          set_error("a 4x4 angle block L_c is singular (zero width, cross section and speed term)");
+          return OCI_E_SINGULAR;
+        }
+        const size_t o = ((size_t)t * G * N + (size_t)g * N + m);
+        for (int k = 0; k < 16; k++) Linv[o * 16 + k] = Li[k];
+        // inflow enters rows 0,2 (mu > 0) or 1,3 (mu < 0) with factor |mu|
+        const int ca = mu > 0 ? 0 : 1, cb = mu > 0 ? 2 : 3;
+        for (int p = 0; p < 4; p++) {
+          Cin[o * 8 + p * 2 + 0] = fabs(mu) * Li[p * 4 + ca];
+          Cin[o * 8 + p * 2 + 1] = fabs(mu) * Li[p * 4 + cb];
+        }
+        for (int k = 0; k < 16; k++) H[(size_t)g * 16 + k] += h.h_w[m] * Li[k];
+      }
+    }
+    // KH: block (g, gp) = Kap[gp->g] * H_gp ; IKH = I - KH ; Mp = IKH^{-1} K
+    for (int g = 0; g < G; g++)
+      for (int gp = 0; gp < G; gp++) {
+        const double k = Kap[((size_t)t * G + gp) * G + g];
+        for (int r = 0; r < 4; r++)
+          for (int c = 0; c < 4; c++) KH[(size_t)(g * 4 + r) * G4 + gp * 4 + c] = k * H[(size_t)gp * 16 + r * 4 + c];
+      }
+    for (int r = 0; r < G4; r++)
+      for (int c = 0; c < G4; c++) IKH[(size_t)r * G4 + c] = (r == c ? 1.0 : 0.0) - KH[(size_t)r * G4 + c];
+    if (!invert(G4, IKH, IKHinv)) {
+      set_error("the within-cell scalar-flux system (I - K H) is singular");
+      return OCI_E_SINGULAR;
+    }
+    for (int r = 0; r < G4; r++)
+      for (int gp = 0; gp < G; gp++)
+        for (int c = 0; c < 4; c++) {
+          // (IKHinv K)[r][(gp,c)] = sum_g IKHinv[r][(g,c)] * Kap[gp->g]
+          double s = 0.0;
+          for (int g = 0; g < G; g++) s += IKHinv[(size_t)r * G4 + g * 4 + c] * Kap[((size_t)t * G + gp) * G + g];
+          Mp[(size_t)t * G4 * G4 + (size_t)r * G4 + gp * 4 + c] = s;
+        }
+  }
+  return OCI_OK;
+}
+
+template <class T>
+static int dev_upload(T **dst, const T *src, size_t n, cudaStream_t s) {
+  CK(cudaMalloc(dst, n * sizeof(T) + 16));
+  if (src) CK(cudaMemcpyAsync(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice, s));
+  return OCI_OK;
+}
+
+static int build_graph(Handle &h, bool si, cudaGraphExec_t *out);
+
+static void free_handle(Handle *h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  void *ptrs[] = {h->Psi[0], h->Psi[1], h->tc,        h->psi_prev,  h->phi,          h->phi_si[0], h->phi_si[1],
+                  h->Q,      h->inc,    h->type,      h->mu,        h->w,            h->v,         h->tt.Linv,
+                  h->tt.Cin, h->tt.Mp,  h->tt.Kap,    h->tt.dx,     h->tt.sig,       h->si_z,      h->si_uin,
+                  h->LU,     h->piv,    h->partials,  h->bal_partials, h->bal,       h->e_hist,    h->ds,
+                  h->stage};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  if (h->h_ds) cudaFreeHost(h->h_ds);
+  if (h->h_bal) cudaFreeHost(h->h_bal);
+  if (h->g_oci) cudaGraphExecDestroy(h->g_oci);
+  if (h->g_si) cudaGraphExecDestroy(h->g_si);
+  if (h->ev0) cudaEventDestroy(h->ev0);
+  if (h->ev1) cudaEventDestroy(h->ev1);
+  delete static_cast<oci_handle *>(h);
+}
+
+static int setup_impl(const oci_problem *p, oci_handle *h) {
+  h->J = p->J;
+  h->N = p->N;
+  h->G = p->G;
+  h->n_mat = p->n_mat;
+  h->Jp = (p->J + 31) / 32 * 32;
+  h->dt = p->dt;
+  h->tol = p->tol;
+  h->max_iter = p->max_iter;
+  h->precision = p->precision;
+  h->guess = p->guess;
+  h->solver = p->solver == OCI_SOLVER_AUTO ? OCI_SOLVER_STRUCTURED : p->solver;
+  h->stream = (cudaStream_t)p->stream;
+  CK(cudaGetDevice(&h->device));
+  const size_t J = h->J, N = h->N, G = h->G, Jp = h->Jp;
+  h->h_dx.assign(p->dx, p->dx + J);
+  h->h_mat.assign(p->mat, p->mat + J);
+  h->h_sigma_t.assign(p->sigma_t, p->sigma_t + (size_t)p->n_mat * G);
+  h->h_sigma_s.assign(p->sigma_s, p->sigma_s + (size_t)p->n_mat * G * G);
+  h->h_v.assign(p->v, p->v + G);
+  gauss_legendre(h->N, h->h_mu, h->h_w);
+
+  std::vector<double> Linv, Cin, Mp, Kap, tdx, tsig;
+  int rc = build_tables(*h, Linv, Cin, Mp, Kap, tdx, tsig);
+  if (rc) return rc;
+  cudaStream_t s = h->stream;
+  const size_t nPsi = G * N * 4 * Jp;
+  CK(cudaMalloc(&h->Psi[0], nPsi * 8));
+  CK(cudaMalloc(&h->Psi[1], nPsi * 8));
+  CK(cudaMalloc(&h->tc, nPsi * 8));
+  CK(cudaMalloc(&h->psi_prev, G * N * 2 * Jp * 8));
+  CK(cudaMalloc(&h->phi, G * 4 * Jp * 8));
+  CK(cudaMalloc(&h->stage, nPsi * 8));
+  CK(cudaMemsetAsync(h->Psi[0], 0, nPsi * 8, s));
+  CK(cudaMemsetAsync(h->Psi[1], 0, nPsi * 8, s));
+  CK(cudaMemsetAsync(h->tc, 0, nPsi * 8, s));
+  CK(cudaMemsetAsync(h->psi_prev, 0, G * N * 2 * Jp * 8, s));
+  CK(cudaMemsetAsync(h->phi, 0, G * 4 * Jp * 8, s));
+  std::vector<int32_t> typ(Jp, 0);
+  for (size_t j = 0; j < J; j++) typ[j] = h->h_type[j];
+  if ((rc = dev_upload(&h->type, typ.data(), Jp, s))) return rc;
+  if ((rc = dev_upload(&h->mu, h->h_mu.data(), N, s))) return rc;
+  if ((rc = dev_upload(&h->w, h->h_w.data(), N, s))) return rc;
+  if ((rc = dev_upload(&h->v, h->h_v.data(), G, s))) return rc;
+  if ((rc = dev_upload(&h->tt.Linv, Linv.data(), Linv.size(), s))) return rc;
+  if ((rc = dev_upload(&h->tt.Cin, Cin.data(), Cin.size(), s))) return rc;
+  if ((rc = dev_upload(&h->tt.Mp, Mp.data(), Mp.size(), s))) return rc;
+  if ((rc = dev_upload(&h->tt.Kap, Kap.data(), Kap.size(), s))) return rc;
+  if ((rc = dev_upload(&h->tt.dx, tdx.data(), tdx.size(), s))) return rc;
+  if ((rc = dev_upload(&h->tt.sig, tsig.data(), tsig.size(), s))) return rc;
+  std::vector<double> inc(2 * G * N * 2, 0.0);
+  if (p->inc_left) std::memcpy(inc.data(), p->inc_left, G * N * 2 * 8);
+  if (p->inc_right) std::memcpy(inc.data() + G * N * 2, p->inc_right, G * N * 2 * 8);
+  if ((rc = dev_upload(&h->inc, inc.data(), inc.size(), s))) return rc;
+  if (p->Q) {
+    if ((rc = dev_upload(&h->Q, (const double *)nullptr, G * 4 * Jp, s))) return rc;
+    CK(cudaMemcpyAsync(h->stage, p->Q, J * G * 4 * 8, cudaMemcpyHostToDevice, s));
+    launch_transpose_in(*h, h->stage, h->Q, (int)(G * 4));
+  }
+  if (p->psi_init) {
+    CK(cudaMemcpyAsync(h->stage, p->psi_init, J * G * N * 2 * 8, cudaMemcpyHostToDevice, s));
+    launch_transpose_in(*h, h->stage, h->psi_prev, (int)(G * N * 2));
+  }
+  // reduction scratch
+  SweepCfg sc = sweep_config(*h);
+  int np = sc.grid;
+  np = std::max(np, si_partials(*h));
+  np = std::max(np, dense_partials(*h));
+  h->n_partials = np;
+  CK(cudaMalloc(&h->partials, (size_t)np * 8));
+  const int nblk_carry = (h->J + 31) / 32;
+  CK(cudaMalloc(&h->bal_partials, (size_t)nblk_carry * G * 8 * 8));
+  CK(cudaMalloc(&h->bal, G * 10 * 8));
+  CK(cudaMemsetAsync(h->bal, 0, G * 10 * 8, s));
+  h->e_hist_cap = h->max_iter;
+  CK(cudaMalloc(&h->e_hist, (size_t)h->e_hist_cap * 8));
+  CK(cudaMalloc(&h->ds, sizeof(DevState)));
+  CK(cudaMallocHost(&h->h_ds, sizeof(DevState)));
+  CK(cudaMallocHost(&h->h_bal, G * 10 * 8));
+  std::memset(h->h_ds, 0, sizeof(DevState));
+  h->h_ds->done = 1;
+  CK(cudaMemcpyAsync(h->ds, h->h_ds, sizeof(DevState), cudaMemcpyHostToDevice, s));
+  CK(cudaEventCreate(&h->ev0));
+  CK(cudaEventCreate(&h->ev1));
+  if (h->solver == OCI_SOLVER_DENSE_LU) {
+    if ((rc = dense_setup(*h))) return rc;
+  }
+  CK(cudaFuncSetAttribute(k_oci_sweep_ptr(), cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  if ((rc = build_graph(*h, false, &h->g_oci))) return rc;
+  CK(cudaStreamSynchronize(s));
+  CK(cudaGetLastError());
+  return OCI_OK;
+}
+
+// Body of one iteration of the convergence loop (sweep + finalize).
+static void launch_body(Handle &h, bool si, cudaGraphConditionalHandle cond, int use_cond) {
+  if (si) {
+    launch_si_sweep(h);
+    launch_finalize(h, h.partials, si_partials(h), cond, use_cond);
+  } else if (h.solver == OCI_SOLVER_DENSE_LU) {
+    launch_dense_sweep(h);
+    launch_finalize(h, h.partials, dense_partials(h), cond, use_cond);
+  } else {
+    launch_oci_sweep(h);
+    launch_finalize(h, h.partials, sweep_config(h).grid, cond, use_cond);
+  }
+}
+
+static int build_graph(Handle &h, bool si, cudaGraphExec_t *out) {
+  cudaGraph_t graph;
+  CK(cudaGraphCreate(&graph, 0));
+  cudaGraphConditionalHandle cond;
+  CK(cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams np = {};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = cond;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  CK(cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np));
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  cudaStream_t cs;
+  CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaStream_t saved = h.stream;
+  h.stream = cs;
+  cudaError_t e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    launch_body(h, si, cond, 1);
+    e = cudaStreamEndCapture(cs, &body);
+  }
+  h.stream = saved;
+  cudaStreamDestroy(cs);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    return cuda_fail(e, "capturing the convergence loop");
+  }
+  e = cudaGraphInstantiate(out, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+  return OCI_OK;
+}
+
+// ---------------------------------------------------------------- stepping
+static int begin_iteration(Handle &h, int fixed, int cap) {
+  DevState &d = *h.h_ds;
+  d.l = 0;
+  d.status = OCI_OK;
+  d.done = 0;
+  d.max_iter = cap;
+  d.fixed = fixed;
+  d.tol = h.tol;
+  d.e = d.e_prev = d.rho = 0.0;
+  CK(cudaMemcpyAsync(h.ds, h.h_ds, sizeof(DevState), cudaMemcpyHostToDevice, h.stream));
+  return OCI_OK;
+}
+
+static int run_step(Handle &h, bool si, oci_stats *st) {
+  const size_t nPsi = (size_t)h.G * h.N * 4 * h.Jp;
+  cudaStream_t s = h.stream;
+  if (h.guess == OCI_GUESS_ZERO) CK(cudaMemsetAsync(h.Psi[h.h_ds->cur], 0, nPsi * 8, s));
+  int rc = begin_iteration(h, 0, h.max_iter);
+  if (rc) return rc;
+  if (si) {
+    launch_si_phi_from_psi(h, nullptr);
+  } else if (h.solver == OCI_SOLVER_DENSE_LU) {
+    launch_dense_step_const(h);
+  } else {
+    launch_step_const(h);
+  }
+  cudaGraphExec_t g = si ? h.g_si : h.g_oci;
+  CK(cudaEventRecord(h.ev0, s));
+  CK(cudaGraphLaunch(g, s));
+  CK(cudaEventRecord(h.ev1, s));
+  launch_carry(h);  // device-guarded: commits only a converged step
+  CK(cudaMemcpyAsync(h.h_ds, h.ds, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(h.h_bal, h.bal, (size_t)h.G * 10 * 8, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  CK(cudaGetLastError());
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, h.ev0, h.ev1);
+  const DevState &d = *h.h_ds;
+  h.last_iters = d.l;
+  if (d.status == OCI_OK) h.t += h.dt;
+  if (st) {
+    st->iters = d.l;
+    st->status = d.status;
+    st->e_last = d.e;
+    st->rho_e_last = d.rho;
+    st->t = h.t;
+    st->seconds = ms * 1e-3;
+    st->balance_rel[0] = st->balance_rel[1] = 0.0;
+    if (d.status == OCI_OK) {
+      for (int g = 0; g < h.G; g++)
+        for (int b = 0; b < 2; b++) {
+          const double *x = h.h_bal + g * 10 + b * 5;
+          const double r = x[0] + x[1] + x[2] - x[3] - x[4];
+          const double sc = fabs(x[0]) + fabs(x[1]) + fabs(x[2]) + fabs(x[3]) + fabs(x[4]);
+          const double rel = sc > 0 ? fabs(r) / sc : 0.0;
+          if (rel > st->balance_rel[b]) st->balance_rel[b] = rel;
+        }
+    }
+  }
+  if (d.status == OCI_E_NOCONV) {
+    char buf[160];
+    snprintf(buf, sizeof buf, "no convergence after %d sweeps (e = %.3e)", d.l, d.e);
+    set_error(buf);
+  } else if (d.status == OCI_E_NONFINITE) {
+    set_error("the convergence norm is not finite");
+  }
+  return d.status;
+}
+
+static int run_fixed(Handle &h, bool si, int n, double *e_hist) {
+  if (n < 0) return set_error("n must be >= 0"), OCI_E_INVAL;
+  if (n > h.e_hist_cap) {
+    cudaFree(h.e_hist);
+    h.e_hist_cap = n;
+    CK(cudaMalloc(&h.e_hist, (size_t)n * 8));
+  }
+  int rc = begin_iteration(h, 1, h.e_hist_cap);
+  if (rc) return rc;
+  if (si) {
+    launch_si_phi_from_psi(h, nullptr);
+  } else if (h.solver == OCI_SOLVER_DENSE_LU) {
+    launch_dense_step_const(h);
+  } else {
+    launch_step_const(h);
+  }
+  cudaGraphConditionalHandle none{};
+  for (int i = 0; i < n; i++) launch_body(h, si, none, 0);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(h.h_ds, h.ds, sizeof(DevState), cudaMemcpyDeviceToHost, h.stream));
+  if (e_hist && n > 0) CK(cudaMemcpyAsync(e_hist, h.e_hist, (size_t)n * 8, cudaMemcpyDefault, h.stream));
+  CK(cudaStreamSynchronize(h.stream));
+  h.last_iters = n;
+  h.h_ds->done = 1;
+  CK(cudaMemcpyAsync(h.ds, h.h_ds, sizeof(DevState), cudaMemcpyHostToDevice, h.stream));
+  CK(cudaStreamSynchronize(h.stream));
+  return OCI_OK;
+}
+
+static bool is_device_ptr(const void *p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// copy a [J][K] ABI array (host or device) into the device SoA array [K][Jp]
+static int put_soa(Handle &h, const double *src, double *dst, int K) {
+  const size_t bytes = (size_t)h.J * K * 8;
+  const double *s = src;
+  if (!is_device_ptr(src)) {
+    CK(cudaMemcpyAsync(h.stage, src, bytes, cudaMemcpyHostToDevice, h.stream));
+    s = h.stage;
+  }
+  launch_transpose_in(h, s, dst, K);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(h.stream));
+  return OCI_OK;
+}
+
+static int get_soa(const Handle &hc, const double *src, double *dst, int K) {
+  Handle &h = const_cast<Handle &>(hc);
+  const size_t bytes = (size_t)h.J * K * 8;
+  if (is_device_ptr(dst)) {
+    launch_transpose_out(h, src, dst, K);
+  } else {
+    launch_transpose_out(h, src, h.stage, K);
+    CK(cudaMemcpyAsync(dst, h.stage, bytes, cudaMemcpyDeviceToHost, h.stream));
+  }
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(h.stream));
+  return OCI_OK;
+}
+
+__global__ void k_fp64_peak(double *out, int iters) {
+  double a0 = threadIdx.x * 1e-3, a1 = a0 + 1, a2 = a0 + 2, a3 = a0 + 3, a4 = a0 + 4, a5 = a0 + 5, a6 = a0 + 6,
+         a7 = a0 + 7;
+  const double m = 0.999999, c = 1.0;
+  for (int i = 0; i < iters; i++) {
+    a0 = fma(a0, m, c); a1 = fma(a1, m, c); a2 = fma(a2, m, c); a3 = fma(a3, m, c);
+    a4 = fma(a4, m, c); a5 = fma(a5, m, c); a6 = fma(a6, m, c); a7 = fma(a7, m, c);
+  }
+  out[blockIdx.x * blockDim.x + threadIdx.x] = a0 + a1 + a2 + a3 + a4 + a5 + a6 + a7;
+}
+
+}  // namespace oci
+
+using namespace oci;
+
+#define GUARD(h)                                         \
+  do {                                                   \
+    if (!(h)) return set_error("handle is NULL"), OCI_E_INVAL; \
+  } while (0)
+
+extern "C" {
+
+int oci_setup(const oci_problem *p, oci_handle **out) {
+  if (!out) return set_error("out is NULL"), OCI_E_INVAL;
+  *out = nullptr;
+  int rc = validate(p);
+  if (rc) return rc;
+  oci_handle *h = new (std::nothrow) oci_handle();
+  if (!h) return set_error("host allocation failed"), OCI_E_NOMEM;
+  rc = setup_impl(p, h);
+  if (rc) {
+    free_handle(h);
+    return rc;
+  }
+  *out = h;
+  set_error("");
+  return OCI_OK;
+}
+
+int oci_step(oci_handle *h, oci_stats *st) {
+  GUARD(h);
+  return run_step(*h, false, st);
+}
+
+int oci_solve_transient(oci_handle *h, int32_t n_steps, double *phi_out, oci_stats *st) {
+  GUARD(h);
+  if (n_steps < 0) return set_error("n_steps must be >= 0"), OCI_E_INVAL;
+  const size_t per = (size_t)h->J * h->G * 4;
+  for (int k = 0; k < n_steps; k++) {
+    int rc = run_step(*h, false, st ? st + k : nullptr);
+    if (rc) return rc;
+    if (phi_out) {
+      rc = get_soa(*h, h->phi, phi_out + per * k, h->G * 4);
+      if (rc) return rc;
+    }
+  }
+  return OCI_OK;
+}
+
+static int ensure_si(Handle &h) {
+  if (h.g_si) return OCI_OK;
+  const size_t G = h.G, N = h.N, Jp = h.Jp;
+  CK(cudaMalloc(&h.si_z, G * N * 4 * Jp * 8));
+  CK(cudaMalloc(&h.si_uin, G * N * 2 * Jp * 8));
+  CK(cudaMalloc(&h.phi_si[0], G * 4 * Jp * 8));
+  CK(cudaMalloc(&h.phi_si[1], G * 4 * Jp * 8));
+  return build_graph(h, true, &h.g_si);
+}
+
+int si_sweep(oci_handle *h, oci_stats *st) {
+  GUARD(h);
+  int rc = ensure_si(*h);
+  if (rc) return rc;
+  return run_step(*h, true, st);
+}
+
+int oci_iterate(oci_handle *h, int32_t n, double *e_hist) {
+  GUARD(h);
+  return run_fixed(*h, false, n, e_hist);
+}
+
+int si_iterate(oci_handle *h, int32_t n, double *e_hist) {
+  GUARD(h);
+  int rc = ensure_si(*h);
+  if (rc) return rc;
+  return run_fixed(*h, true, n, e_hist);
+}
+
+int oci_get_psi(const oci_handle *h, double *psi) {
+  GUARD(h);
+  if (!psi) return set_error("psi is NULL"), OCI_E_INVAL;
+  return get_soa(*h, h->Psi[h->h_ds->cur], psi, h->G * h->N * 4);
+}
+
+int oci_set_psi(oci_handle *h, const double *psi) {
+  GUARD(h);
+  if (!psi) return set_error("psi is NULL"), OCI_E_INVAL;
+  return put_soa(*h, psi, h->Psi[h->h_ds->cur], h->G * h->N * 4);
+}
+
+int oci_get_phi(const oci_handle *h, double *phi) {
+  GUARD(h);
+  if (!phi) return set_error("phi is NULL"), OCI_E_INVAL;
+  return get_soa(*h, h->phi, phi, h->G * 4);
+}
+
+int oci_get_state(const oci_handle *h, double *psi_prev, double *t) {
+  GUARD(h);
+  if (t) *t = h->t;
+  if (!psi_prev) return OCI_OK;
+  return get_soa(*h, h->psi_prev, psi_prev, h->G * h->N * 2);
+}
+
+int oci_set_state(oci_handle *h, const double *psi_prev, double t) {
+  GUARD(h);
+  if (!std::isfinite(t)) return set_error("t must be finite"), OCI_E_INVAL;
+  if (psi_prev) {
+    int rc = put_soa(*h, psi_prev, h->psi_prev, h->G * h->N * 2);
+    if (rc) return rc;
+  }
+  h->t = t;
+  return OCI_OK;
+}
+
+int oci_get_balance(const oci_handle *h, double *bal) {
+  GUARD(h);
+  if (!bal) return set_error("bal is NULL"), OCI_E_INVAL;
+  CK(cudaMemcpyAsync(bal, h->bal, (size_t)h->G * 10 * 8, cudaMemcpyDefault, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return OCI_OK;
+}
+
+int oci_set_boundary(oci_handle *h, const double *inc_left, const double *inc_right) {
+  GUARD(h);
+  const size_t n = (size_t)h->G * h->N * 2;
+  std::vector<double> tmp(2 * n, 0.0);
+  if (inc_left) CK(cudaMemcpy(tmp.data(), inc_left, n * 8, cudaMemcpyDefault));
+  if (inc_right) CK(cudaMemcpy(tmp.data() + n, inc_right, n * 8, cudaMemcpyDefault));
+  if (!all_finite(tmp.data(), 2 * n)) return set_error("incident fluxes must be finite"), OCI_E_INVAL;
+  CK(cudaMemcpyAsync(h->inc, tmp.data(), 2 * n * 8, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return OCI_OK;
+}
+
+int oci_get_e_hist(const oci_handle *h, double *e_hist, int32_t *n) {
+  GUARD(h);
+  const int cnt = std::min(h->last_iters, h->e_hist_cap);
+  if (n) *n = cnt;
+  if (e_hist && cnt > 0) {
+    CK(cudaMemcpyAsync(e_hist, h->e_hist, (size_t)cnt * 8, cudaMemcpyDefault, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+  }
+  return OCI_OK;
+}
+
+void oci_destroy(oci_handle *h) { free_handle(h); }
+
+const char *oci_last_error(void) { return g_err.c_str(); }
+
+int oci_probe_fp64_peak(double *flops_per_s) {
+  if (!flops_per_s) return set_error("NULL argument"), OCI_E_INVAL;
+  int dev = 0, sms = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int blocks = sms * 8, threads = 256, iters = 4096;
+  double *out = nullptr;
+  CK(cudaMalloc(&out, (size_t)blocks * threads * 8));
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  k_fp64_peak<<<blocks, threads>>>(out, 64);
+  float best = 1e30f;
+  for (int r = 0; r < 3; r++) {
+    cudaEventRecord(a);
+    k_fp64_peak<<<blocks, threads>>>(out, iters);
+    cudaEventRecord(b);
+    cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    if (ms < best) best = ms;
+  }
+  cudaError_t e = cudaGetLastError();
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  cudaFree(out);
+  if (e != cudaSuccess) return cuda_fail(e, "fp64 peak probe");
+  *flops_per_s = 2.0 * 8.0 * iters * (double)blocks * threads / (best * 1e-3);
+  return OCI_OK;
+}
+
+}  // extern "C"

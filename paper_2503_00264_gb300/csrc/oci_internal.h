@@ -1,0 +1,127 @@
+// oci_internal.h -- shared declarations of liboci (not part of the ABI).
+//
+// Device layout (structure of arrays, cells fastest so that consecutive threads
+// touch consecutive addresses):
+//   Psi, tc      [G][N][4][Jp]   element (g,m,p,j) at ((g*N+m)*4+p)*Jp + j
+//   psi_prev     [G][N][2][Jp]
+//   phi, Q       [G][4][Jp]
+// Jp = J rounded up to a multiple of 32.  The ABI's [J][G][N][*] order is
+// converted by transpose kernels in oci_api.cu.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/oci.h"
+
+namespace oci {
+
+constexpr int kMaxN = 128;
+constexpr int kMaxG = 16;
+constexpr int kMaxUnknowns = 2048;      // 4*N*G per cell
+constexpr int kFinalizeThreads = 512;
+
+// Device-resident iteration state of one handle.
+struct DevState {
+  int cur;        // index (0/1) of the Psi buffer holding the current iterate
+  int l;          // sweeps done in this step
+  int status;     // OCI_OK while iterating / converged, OCI_E_NOCONV, OCI_E_NONFINITE
+  int done;       // 1 once the stop rule (or a failure) ended the loop
+  int max_iter;
+  int fixed;      // 1: no stop test (oci_iterate)
+  double tol;
+  double e, e_prev, rho;
+};
+
+// Per-cell-type tables of the structured solve (all FP64, device).
+struct TypeTables {
+  int n_types = 0;
+  double *Linv = nullptr;   // [T][G][N][16]  inverse of the 4x4 L_{c,g,m} (Eq. Aj), row-major
+  double *Cin = nullptr;    // [T][G][N][8]   |mu| * the two columns of Linv that the inflow feeds
+  double *Mp = nullptr;     // [T][4G][4G]    s = Mp y: within-cell scattering source from y
+  double *Kap = nullptr;    // [T][G][G]      dx/4 * Sigma_s,gp->g  (index [gp][g])
+  double *dx = nullptr;     // [T]
+  double *sig = nullptr;    // [T][G]         Sigma_t,g
+};
+
+struct Handle {
+  int J = 0, N = 0, G = 0, n_mat = 0, Jp = 0;
+  double dt = 0, tol = 0, t = 0;
+  int max_iter = 0, precision = 0, guess = 0, solver = 0;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+
+  // host copies of the problem (for re-setup and validation)
+  std::vector<double> h_dx, h_sigma_t, h_sigma_s, h_v;
+  std::vector<int32_t> h_mat;
+  std::vector<double> h_mu, h_w;
+  std::vector<int32_t> h_type;   // cell -> type
+
+  // device state
+  double *Psi[2] = {nullptr, nullptr};
+  double *tc = nullptr;          // per-step constant Linv * c (structured) or c (dense)
+  double *psi_prev = nullptr;
+  double *phi = nullptr;
+  double *phi_si[2] = {nullptr, nullptr};
+  double *Q = nullptr;
+  double *inc = nullptr;         // [2][G][N][2] left, right
+  int32_t *type = nullptr;       // [Jp]
+  double *mu = nullptr, *w = nullptr, *v = nullptr;
+  TypeTables tt;
+  // SI scratch
+  double *si_z = nullptr;        // [G][N][4][Jp]   Linv * d0
+  double *si_uin = nullptr;      // [G][N][2][Jp]   incoming edge of every cell
+  // dense path
+  double *LU = nullptr;          // [J][n][n] column-major per cell
+  int32_t *piv = nullptr;        // [J][n]
+  // reductions
+  double *partials = nullptr;    // [max blocks]
+  int n_partials = 0;
+  double *bal_partials = nullptr;  // [max blocks][G][8]
+  double *bal = nullptr;           // [G][2][5]
+  double *e_hist = nullptr;        // [e_hist_cap]
+  int e_hist_cap = 0;
+  double *stage = nullptr;         // device staging buffer, size of one Psi
+  DevState *ds = nullptr;
+  // pinned host mirrors
+  DevState *h_ds = nullptr;
+  double *h_bal = nullptr;
+  // graphs
+  cudaGraphExec_t g_oci = nullptr, g_si = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  int last_iters = 0;
+  bool committed_once = false;
+};
+
+// ---------------------------------------------------------------- launches
+struct SweepCfg {
+  int cells_per_block;
+  int grid;
+  size_t smem;
+};
+SweepCfg sweep_config(const Handle &h);
+
+void launch_step_const(Handle &h);
+void launch_oci_sweep(Handle &h);
+const void *k_oci_sweep_ptr();
+void launch_finalize(Handle &h, const double *partials, int n, cudaGraphConditionalHandle cond,
+                     int use_cond);
+void launch_carry(Handle &h);
+void launch_transpose_in(Handle &h, const double *src_abi, double *dst_soa, int P);
+void launch_transpose_out(Handle &h, const double *src_soa, double *dst_abi, int P);
+void launch_phi_out(Handle &h, double *dst_abi);
+// SI
+void launch_si_sweep(Handle &h);
+void launch_si_phi_from_psi(Handle &h, double *phi_dst);
+// dense path
+int dense_setup(Handle &h);
+void launch_dense_step_const(Handle &h);
+void launch_dense_sweep(Handle &h);
+
+// errors
+void set_error(const std::string &msg);
+int cuda_fail(cudaError_t e, const char *what);
+
+}  // namespace oci

@@ -1,0 +1,192 @@
+// oci_si.cu -- source iteration (SI) comparison path, FP64 (Algorithm 1, App. A).
+//
+// One SI sweep solves, for every (g,m) and cell j in the direction of flight,
+//   L_{c,j,g,m} psi_j = d_j,   d_j = d0_j + |mu| (u_k e_a + u_h e_b)      (Eq. app:si_sys)
+// with d0 = dx/4 (sum_gp Sigma_s,gp->g phi^(l)_gp + Q) + dx/(2 v dt) (psi_prev_L, psi_prev_R, 0, 0)
+// (Eq. app:si_rhs; all groups' scattering lagged = Jacobi over groups) and the
+// upstream edge (u_k, u_h) of the CURRENT sweep (rows a,b = 0,2 for mu > 0 and
+// 1,3 for mu < 0).  Writing z_j = L^{-1} d0_j, the solution is
+//   psi_j = z_j + Cin_j u_j
+// so the serial dependency of the sweep is only the two outgoing edge values,
+//   u_{next} = z_j[out] + Cin_j[out,:] u_j       (2 dependent FMA levels per cell).
+// The sweep is split into a parallel pre-pass (z), a serial chain per (g,m)
+// (one thread each), and a parallel post-pass (psi, phi, ||phi^{l+1}-phi^l||^2).
+#include <math.h>
+
+#include "oci_internal.h"
+
+namespace oci {
+
+// Scattering + fixed source of every (j,g): src_p = dx/4 (sum_gp Ss,gp->g phi_gp,p + Q_g,p),
+// folded with the time term into d0 and pre-multiplied by L^{-1}: z = L^{-1} d0.
+__global__ void k_si_pre(int J, int Jp, int N, int G, const int32_t *__restrict__ type,
+                         const double *__restrict__ tdx, const double *__restrict__ Kap,
+                         const double *__restrict__ v, double dt, const double *__restrict__ Q,
+                         const double *__restrict__ psi_prev, const double *__restrict__ Linv,
+                         const double *phi0, const double *phi1, const DevState *__restrict__ ds,
+                         double *__restrict__ z) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int g = blockIdx.y;
+  if (j >= J || ds->done) return;
+  const double *__restrict__ phl = ds->cur ? phi1 : phi0;
+  const int tau = type[j];
+  const double dx = tdx[tau];
+  double s[4];
+#pragma unroll
+  for (int p = 0; p < 4; p++) s[p] = Q ? dx / 4.0 * Q[(size_t)(g * 4 + p) * Jp + j] : 0.0;
+  for (int gp = 0; gp < G; gp++) {
+    const double k = Kap[((size_t)tau * G + gp) * G + g];
+#pragma unroll
+    for (int p = 0; p < 4; p++) s[p] = fma(k, phl[(size_t)(gp * 4 + p) * Jp + j], s[p]);
+  }
+  const double ah = dx / (2.0 * v[g] * dt);
+  for (int m = 0; m < N; m++) {
+    const int gm = g * N + m;
+    const double d0 = s[0] + ah * psi_prev[(size_t)(gm * 2 + 0) * Jp + j];
+    const double d1 = s[1] + ah * psi_prev[(size_t)(gm * 2 + 1) * Jp + j];
+    const double *L = Linv + ((size_t)tau * G * N + gm) * 16;
+#pragma unroll
+    for (int p = 0; p < 4; p++)
+      z[(size_t)(gm * 4 + p) * Jp + j] = L[p * 4 + 0] * d0 + L[p * 4 + 1] * d1 + L[p * 4 + 2] * s[2] + L[p * 4 + 3] * s[3];
+  }
+}
+
+// Serial chain of one (g,m): store the incoming edge of every cell.
+constexpr int kChainUnroll = 8;
+__global__ void k_si_chain(int J, int Jp, int N, int G, const int32_t *__restrict__ type,
+                           const double *__restrict__ Cin, const double *__restrict__ inc,
+                           const double *__restrict__ z, const DevState *__restrict__ ds,
+                           double *__restrict__ uin) {
+  const int gm = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gm >= G * N || ds->done) return;
+  const int m = gm % N;
+  const bool fwd = m >= N / 2;       // mu > 0: sweep j = 0 .. J-1
+  const int oa = fwd ? 1 : 0;         // outgoing rows: R corners (mu > 0) or L corners (mu < 0)
+  const int ob = fwd ? 3 : 2;
+  const double *incp = inc + (fwd ? 0 : (size_t)G * N * 2) + gm * 2;
+  double uk = incp[0], uh = incp[1];
+  const double *za = z + (size_t)(gm * 4 + oa) * Jp;
+  const double *zb = z + (size_t)(gm * 4 + ob) * Jp;
+  double *uk_out = uin + (size_t)(gm * 2 + 0) * Jp;
+  double *uh_out = uin + (size_t)(gm * 2 + 1) * Jp;
+  for (int s0 = 0; s0 < J; s0 += kChainUnroll) {
+    double a[kChainUnroll], b[kChainUnroll], c[kChainUnroll][4];
+#pragma unroll
+    for (int k = 0; k < kChainUnroll; k++) {
+      const int s = s0 + k;
+      if (s < J) {
+        const int j = fwd ? s : J - 1 - s;
+        a[k] = za[j];
+        b[k] = zb[j];
+        const double *C = Cin + ((size_t)type[j] * G * N + gm) * 8;
+        c[k][0] = C[oa * 2 + 0];
+        c[k][1] = C[oa * 2 + 1];
+        c[k][2] = C[ob * 2 + 0];
+        c[k][3] = C[ob * 2 + 1];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kChainUnroll; k++) {
+      const int s = s0 + k;
+      if (s < J) {
+        const int j = fwd ? s : J - 1 - s;
+        uk_out[j] = uk;
+        uh_out[j] = uh;
+        const double nk = fma(c[k][1], uh, fma(c[k][0], uk, a[k]));
+        const double nh = fma(c[k][3], uh, fma(c[k][2], uk, b[k]));
+        uk = nk;
+        uh = nh;
+      }
+    }
+  }
+}
+
+// psi_j = z_j + Cin_j u_j for all (g,m); phi^{l+1}; block sum of (phi^{l+1} - phi^l)^2.
+__global__ void __launch_bounds__(256) k_si_post(int J, int Jp, int N, int G, const int32_t *__restrict__ type,
+                                                 const double *__restrict__ Cin, const double *__restrict__ w,
+                                                 const double *__restrict__ z, const double *__restrict__ uin,
+                                                 double *Psi0, double *Psi1, double *phi0, double *phi1,
+                                                 const DevState *__restrict__ ds, double *__restrict__ partials) {
+  __shared__ double red[32];
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int g = blockIdx.y;
+  if (ds->done) return;
+  const int cur = ds->cur;
+  double *__restrict__ Pout = cur ? Psi0 : Psi1;
+  const double *__restrict__ phl = cur ? phi1 : phi0;
+  double *__restrict__ phn = cur ? phi0 : phi1;
+  double e2 = 0.0;
+  if (j < J) {
+    const int tau = type[j];
+    double ph[4] = {0, 0, 0, 0};
+    for (int m = 0; m < N; m++) {
+      const int gm = g * N + m;
+      const double uk = uin[(size_t)(gm * 2 + 0) * Jp + j];
+      const double uh = uin[(size_t)(gm * 2 + 1) * Jp + j];
+      const double *C = Cin + ((size_t)tau * G * N + gm) * 8;
+      const double wm = w[m];
+#pragma unroll
+      for (int p = 0; p < 4; p++) {
+        const size_t ix = (size_t)(gm * 4 + p) * Jp + j;
+        const double o = fma(C[p * 2 + 1], uh, fma(C[p * 2 + 0], uk, z[ix]));
+        Pout[ix] = o;
+        ph[p] = fma(wm, o, ph[p]);
+      }
+    }
+#pragma unroll
+    for (int p = 0; p < 4; p++) {
+      const size_t ix = (size_t)(g * 4 + p) * Jp + j;
+      const double d = ph[p] - phl[ix];
+      e2 = fma(d, d, e2);
+      phn[ix] = ph[p];
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) e2 += __shfl_down_sync(0xffffffffu, e2, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = e2;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < (int)(blockDim.x + 31) / 32; i++) s += red[i];
+    partials[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+// phi[cur] = sum_m w_m Psi[cur] (initial SI iterate from the handle's Psi).
+__global__ void k_si_phi_init(int J, int Jp, int N, int G, const double *__restrict__ w, const double *Psi0,
+                              const double *Psi1, double *phi0, double *phi1, const DevState *__restrict__ ds) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int g = blockIdx.y;
+  if (j >= J) return;
+  const int cur = ds->cur;
+  const double *P = cur ? Psi1 : Psi0;
+  double *ph = cur ? phi1 : phi0;
+  double s[4] = {0, 0, 0, 0};
+  for (int m = 0; m < N; m++) {
+#pragma unroll
+    for (int p = 0; p < 4; p++) s[p] = fma(w[m], P[(size_t)((g * N + m) * 4 + p) * Jp + j], s[p]);
+  }
+#pragma unroll
+  for (int p = 0; p < 4; p++) ph[(size_t)(g * 4 + p) * Jp + j] = s[p];
+}
+
+void launch_si_sweep(Handle &h) {
+  dim3 g1((h.J + 255) / 256, h.G);
+  k_si_pre<<<g1, 256, 0, h.stream>>>(h.J, h.Jp, h.N, h.G, h.type, h.tt.dx, h.tt.Kap, h.v, h.dt, h.Q, h.psi_prev,
+                                     h.tt.Linv, h.phi_si[0], h.phi_si[1], h.ds, h.si_z);
+  const int chains = h.G * h.N;
+  k_si_chain<<<(chains + 31) / 32, 32, 0, h.stream>>>(h.J, h.Jp, h.N, h.G, h.type, h.tt.Cin, h.inc, h.si_z, h.ds,
+                                                      h.si_uin);
+  k_si_post<<<g1, 256, 0, h.stream>>>(h.J, h.Jp, h.N, h.G, h.type, h.tt.Cin, h.w, h.si_z, h.si_uin, h.Psi[0],
+                                      h.Psi[1], h.phi_si[0], h.phi_si[1], h.ds, h.partials);
+}
+
+int si_partials(const Handle &h) { return ((h.J + 255) / 256) * h.G; }
+
+void launch_si_phi_from_psi(Handle &h, double *) {
+  dim3 g1((h.J + 255) / 256, h.G);
+  k_si_phi_init<<<g1, 256, 0, h.stream>>>(h.J, h.Jp, h.N, h.G, h.w, h.Psi[0], h.Psi[1], h.phi_si[0], h.phi_si[1],
+                                          h.ds);
+}
+
+}  // namespace oci

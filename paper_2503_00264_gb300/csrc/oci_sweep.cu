@@ -1,0 +1,432 @@
+// oci_sweep.cu -- FP64 kernels of the OCI time step (structured cell solve).
+//
+// Cell solve.  For cell j the OCI system (Eq. oci; multigroup Eq. fullOCIlhs)
+//   (L_c - S) Psi = b,   L_c = blockdiag_{g,m} L_{c,g,m} (Eq. Aj),
+//   (S Psi)_{g,m,p} = sum_{gp} dx/4 Sigma_s,gp->g phi_{gp,p},  phi_{g,p} = sum_n w_n Psi_{g,n,p}
+// (Eq. scatter read with the column angle's weight) is solved exactly through
+// its structure instead of a dense LU:
+//   t_{g,m} = L_{g,m}^{-1} b_{g,m}
+//   y_g     = sum_m w_m t_{g,m}
+//   s       = Mp y,       Mp = (I - K H)^{-1} K,  H = blockdiag_g sum_m w_m L_{g,m}^{-1},
+//                          K[g][gp] = dx/4 Sigma_s,gp->g I_4
+//   Psi_{g,m} = t_{g,m} + L_{g,m}^{-1} s_g
+// which is A_j^{-1} b_j up to rounding.  b = c + (lagged inflow) with the
+// per-step constant c of Eq. rhs_sg, so t = tc + Cin u with tc = L^{-1} c
+// computed once per step (k_step_const) and u the two upstream edge values.
+#include <math.h>
+
+#include "oci_internal.h"
+
+namespace oci {
+
+// ------------------------------------------------------------------ a1
+// tc_{g,m} = L_{g,m}^{-1} c_{g,m},
+// c = [dx/4 Q_kL + dx/(2 v dt) psi_prev_L, dx/4 Q_kR + dx/(2 v dt) psi_prev_R, dx/4 Q_hL, dx/4 Q_hR]
+__global__ void k_step_const(int J, int Jp, int N, int G, const int32_t *__restrict__ type,
+                             const double *__restrict__ tdx, const double *__restrict__ v, double dt,
+                             const double *__restrict__ Q, const double *__restrict__ psi_prev,
+                             const double *__restrict__ Linv, double *__restrict__ tc) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int gm = blockIdx.y;
+  if (j >= J) return;
+  const int g = gm / N;
+  const int tau = type[j];
+  const double dx = tdx[tau];
+  const double ah = dx / (2.0 * v[g] * dt);
+  double q[4] = {0.0, 0.0, 0.0, 0.0};
+  if (Q) {
+#pragma unroll
+    for (int p = 0; p < 4; p++) q[p] = dx / 4.0 * Q[(size_t)(g * 4 + p) * Jp + j];
+  }
+  const double c0 = q[0] + ah * psi_prev[(size_t)(gm * 2 + 0) * Jp + j];
+  const double c1 = q[1] + ah * psi_prev[(size_t)(gm * 2 + 1) * Jp + j];
+  const double *L = Linv + ((size_t)tau * G * N + gm) * 16;
+#pragma unroll
+  for (int p = 0; p < 4; p++)
+    tc[(size_t)(gm * 4 + p) * Jp + j] = L[p * 4 + 0] * c0 + L[p * 4 + 1] * c1 + L[p * 4 + 2] * q[2] + L[p * 4 + 3] * q[3];
+}
+
+// Deterministic block sum of one double; result valid in thread 0.
+__device__ __forceinline__ double block_sum(double v, double *red) {
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int nthr = blockDim.x * blockDim.y;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((tid & 31) == 0) red[tid >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (tid == 0)
+    for (int i = 0; i < (nthr + 31) / 32; i++) s += red[i];
+  return s;
+}
+
+// ------------------------------------------------------------------ a2..a4
+// One OCI sweep.  Thread (cell j, group g); block = CB cells x G groups.
+// Reads Psi[cur], writes Psi[cur^1], writes this block's sum of (Psi_new - Psi_old)^2.
+// Shared memory: t [G*N*4][CB], y [G*4][CB], reduction scratch.
+__global__ void __launch_bounds__(256) k_oci_sweep(
+    int J, int Jp, int N, int G, const int32_t *__restrict__ type, const double *__restrict__ Linv,
+    const double *__restrict__ Cin, const double *__restrict__ Mp, const double *__restrict__ w,
+    const double *__restrict__ inc, const double *__restrict__ tc, double *Psi0, double *Psi1,
+    const DevState *__restrict__ ds, double *__restrict__ partials) {
+  extern __shared__ double sm[];
+  const int CB = blockDim.x;
+  const int cl = threadIdx.x, g = threadIdx.y;
+  const int j = blockIdx.x * CB + cl;
+  if (ds->done) return;  // uniform across the grid
+  const int cur = ds->cur;
+  const double *__restrict__ Pin = cur ? Psi1 : Psi0;
+  double *__restrict__ Pout = cur ? Psi0 : Psi1;
+  double *t_s = sm;
+  double *y_s = sm + (size_t)G * N * 4 * CB;
+  double *red = y_s + (size_t)G * 4 * CB;
+  const bool active = j < J;
+  const int tau = active ? type[j] : 0;
+  const int N2 = N / 2;
+  const size_t tb = (size_t)tau * G * N;
+
+  double y0 = 0.0, y1 = 0.0, y2 = 0.0, y3 = 0.0;
+  if (active) {
+#pragma unroll 2
+    for (int m = 0; m < N; m++) {
+      const int gm = g * N + m;
+      const size_t base = (size_t)gm * 4 * Jp + j;
+      double uk, uh;
+      if (m >= N2) {  // mu > 0: upstream edge is the R corner of cell j-1
+        if (j > 0) {
+          uk = Pin[base + 1 * (size_t)Jp - 1];
+          uh = Pin[base + 3 * (size_t)Jp - 1];
+        } else {
+          uk = inc[gm * 2 + 0];
+          uh = inc[gm * 2 + 1];
+        }
+      } else {  // mu < 0: upstream edge is the L corner of cell j+1
+        if (j < J - 1) {
+          uk = Pin[base + 0 * (size_t)Jp + 1];
+          uh = Pin[base + 2 * (size_t)Jp + 1];
+        } else {
+          uk = inc[(G * N + gm) * 2 + 0];
+          uh = inc[(G * N + gm) * 2 + 1];
+        }
+      }
+      const double *C = Cin + (tb + gm) * 8;
+      const double t0 = fma(C[1], uh, fma(C[0], uk, tc[base]));
+      const double t1 = fma(C[3], uh, fma(C[2], uk, tc[base + (size_t)Jp]));
+      const double t2 = fma(C[5], uh, fma(C[4], uk, tc[base + 2 * (size_t)Jp]));
+      const double t3 = fma(C[7], uh, fma(C[6], uk, tc[base + 3 * (size_t)Jp]));
+      double *ts = t_s + (size_t)(gm * 4) * CB + cl;
+      ts[0] = t0;
+      ts[CB] = t1;
+      ts[2 * CB] = t2;
+      ts[3 * CB] = t3;
+      const double wm = w[m];
+      y0 = fma(wm, t0, y0);
+      y1 = fma(wm, t1, y1);
+      y2 = fma(wm, t2, y2);
+      y3 = fma(wm, t3, y3);
+    }
+    double *ys = y_s + (size_t)(g * 4) * CB + cl;
+    ys[0] = y0;
+    ys[CB] = y1;
+    ys[2 * CB] = y2;
+    ys[3 * CB] = y3;
+  }
+  __syncthreads();
+  double e2 = 0.0;
+  if (active) {
+    // s_g = sum_{gp} Mp[g][gp] y_gp
+    const int G4 = 4 * G;
+    const double *M = Mp + (size_t)tau * G4 * G4 + (size_t)(g * 4) * G4;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    for (int k = 0; k < G4; k++) {
+      const double yk = y_s[(size_t)k * CB + cl];
+      s0 = fma(M[k], yk, s0);
+      s1 = fma(M[G4 + k], yk, s1);
+      s2 = fma(M[2 * G4 + k], yk, s2);
+      s3 = fma(M[3 * G4 + k], yk, s3);
+    }
+#pragma unroll 2
+    for (int m = 0; m < N; m++) {
+      const int gm = g * N + m;
+      const size_t base = (size_t)gm * 4 * Jp + j;
+      const double *L = Linv + (tb + gm) * 16;
+      const double *ts = t_s + (size_t)(gm * 4) * CB + cl;
+      double o[4];
+#pragma unroll
+      for (int p = 0; p < 4; p++)
+        o[p] = fma(L[p * 4 + 3], s3, fma(L[p * 4 + 2], s2, fma(L[p * 4 + 1], s1, fma(L[p * 4 + 0], s0, ts[p * CB]))));
+#pragma unroll
+      for (int p = 0; p < 4; p++) {
+        const double d = o[p] - Pin[base + (size_t)p * Jp];
+        e2 = fma(d, d, e2);
+        Pout[base + (size_t)p * Jp] = o[p];
+      }
+    }
+  }
+  const double bs = block_sum(e2, red);
+  if (threadIdx.x == 0 && threadIdx.y == 0) partials[blockIdx.x] = bs;
+}
+
+const void *k_oci_sweep_ptr() { return (const void *)k_oci_sweep; }
+
+SweepCfg sweep_config(const Handle &h) {
+  SweepCfg c;
+  const size_t per_cell = (size_t)h.G * h.N * 4 * 8 + (size_t)h.G * 4 * 8;
+  int cb = 128;
+  while (cb > 1 && ((size_t)cb * h.G > 256 || (size_t)cb * per_cell > 96 * 1024)) cb /= 2;
+  c.cells_per_block = cb;
+  c.grid = (h.J + cb - 1) / cb;
+  c.smem = (size_t)cb * per_cell + 64 * sizeof(double);
+  return c;
+}
+
+void launch_step_const(Handle &h) {
+  dim3 grid((h.J + 255) / 256, h.G * h.N);
+  k_step_const<<<grid, 256, 0, h.stream>>>(h.J, h.Jp, h.N, h.G, h.type, h.tt.dx, h.v, h.dt, h.Q, h.psi_prev,
+                                           h.tt.Linv, h.tc);
+}
+
+void launch_oci_sweep(Handle &h) {
+  SweepCfg c = sweep_config(h);
+  dim3 block(c.cells_per_block, h.G);
+  k_oci_sweep<<<c.grid, block, c.smem, h.stream>>>(h.J, h.Jp, h.N, h.G, h.type, h.tt.Linv, h.tt.Cin, h.tt.Mp, h.w,
+                                                   h.inc, h.tc, h.Psi[0], h.Psi[1], h.ds, h.partials);
+}
+
+// ------------------------------------------------------------------ a4, a5
+// Sum the block partials in a fixed order, take e = sqrt(sum), apply the stop
+// rule of Sec. 2.1 (Algorithm 2), flip the ping-pong index and, inside a
+// conditional WHILE graph, end the loop when the step is done.
+__global__ void __launch_bounds__(kFinalizeThreads) k_finalize(const double *__restrict__ partials, int n,
+                                                                 DevState *ds, double *e_hist,
+                                                                 cudaGraphConditionalHandle cond, int use_cond) {
+  __shared__ double sh[kFinalizeThreads];
+  if (ds->done) {
+    if (threadIdx.x == 0 && use_cond) cudaGraphSetConditional(cond, 0);
+    return;
+  }
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += kFinalizeThreads) s += partials[i];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = kFinalizeThreads / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double e = sqrt(sh[0]);
+    const int l = ds->l;
+    if (e_hist && l < ds->max_iter) e_hist[l] = e;
+    double rho = 0.0;
+    int conv = 0;
+    if (!isfinite(e)) {
+      ds->status = OCI_E_NONFINITE;
+      ds->done = 1;
+    } else {
+      if (l >= 1 && ds->e_prev > 0.0) rho = e / ds->e_prev;
+      if (!ds->fixed) {
+        if (e == 0.0) conv = 1;
+        else if (l >= 1) conv = e < ds->tol * (1.0 - rho);
+      }
+    }
+    ds->e = e;
+    ds->rho = rho;
+    ds->e_prev = e;
+    ds->l = l + 1;
+    ds->cur ^= 1;
+    if (!ds->fixed && !ds->done) {
+      if (conv) {
+        ds->status = OCI_OK;
+        ds->done = 1;
+      } else if (l + 1 >= ds->max_iter) {
+        ds->status = OCI_E_NOCONV;
+        ds->done = 1;
+      }
+    }
+    if (use_cond && ds->done) cudaGraphSetConditional(cond, 0);
+  }
+}
+
+void launch_finalize(Handle &h, const double *partials, int n, cudaGraphConditionalHandle cond, int use_cond) {
+  k_finalize<<<1, kFinalizeThreads, 0, h.stream>>>(partials, n, h.ds, h.e_hist, cond, use_cond);
+}
+
+// ------------------------------------------------------------------ a6
+// Commit of a converged step: phi = sum_m w_m Psi (Eq. app:si_sf form),
+// psi_{k-1/2} <- (Psi_hL, Psi_hR), and per-block particle-balance tallies:
+//   time average (Eqs. scb-mb-a + b summed over corners, angles):
+//     dx/(2 v dt) sum_{L,R}(phi_h - phi_prev) + leak + dx/2 St (phi_kL + phi_kR)
+//       - dx/2 sum_gp Ss,gp->g (phi_gp,kL + phi_gp,kR) - dx/2 (Q_kL + Q_kR) = 0
+//   time edge (Eqs. scb-mb-c + d):
+//     dx/(v dt) sum_{L,R}(phi_h - phi_k) + leak + dx/2 St (phi_hL + phi_hR) - ... = 0
+// partial layout [block][g][8] = {timeA, timeE, collA, collE, scatA, scatE, srcA, srcE}.
+__global__ void __launch_bounds__(256) k_carry(int J, int Jp, int N, int G, const int32_t *__restrict__ type,
+                                               const double *__restrict__ tdx, const double *__restrict__ tsig,
+                                               const double *__restrict__ Kap, const double *__restrict__ v,
+                                               double dt, const double *__restrict__ w,
+                                               const double *__restrict__ Q, const double *Psi0,
+                                               const double *Psi1, const DevState *__restrict__ ds,
+                                               double *__restrict__ psi_prev, double *__restrict__ phi,
+                                               double *__restrict__ bal_partials) {
+  __shared__ double ph_s[kMaxG * 4][32];
+  const int cl = threadIdx.x, g = threadIdx.y;
+  const int j = blockIdx.x * 32 + cl;
+  if (ds->status != OCI_OK) return;  // commit only a converged step (uniform)
+  const bool active = j < J;
+  const double *__restrict__ P = ds->cur ? Psi1 : Psi0;
+  double ph[4] = {0, 0, 0, 0}, pp[2] = {0, 0};
+  int tau = 0;
+  if (active) {
+    tau = type[j];
+    for (int m = 0; m < N; m++) {
+      const int gm = g * N + m;
+      const double wm = w[m];
+      const size_t base = (size_t)gm * 4 * Jp + j;
+      double o[4];
+#pragma unroll
+      for (int p = 0; p < 4; p++) {
+        o[p] = P[base + (size_t)p * Jp];
+        ph[p] = fma(wm, o[p], ph[p]);
+      }
+      const size_t pb = (size_t)gm * 2 * Jp + j;
+      pp[0] = fma(wm, psi_prev[pb], pp[0]);
+      pp[1] = fma(wm, psi_prev[pb + Jp], pp[1]);
+      psi_prev[pb] = o[2];
+      psi_prev[pb + Jp] = o[3];
+    }
+#pragma unroll
+    for (int p = 0; p < 4; p++) {
+      phi[(size_t)(g * 4 + p) * Jp + j] = ph[p];
+      ph_s[g * 4 + p][cl] = ph[p];
+    }
+  }
+  __syncthreads();
+  double tally[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  if (active) {
+    const double dx = tdx[tau];
+    const double sig = tsig[(size_t)tau * G + g];
+    const double rate = dx / (v[g] * dt);
+    tally[0] = rate / 2.0 * ((ph[2] - pp[0]) + (ph[3] - pp[1]));
+    tally[1] = rate * ((ph[2] - ph[0]) + (ph[3] - ph[1]));
+    tally[2] = dx / 2.0 * sig * (ph[0] + ph[1]);
+    tally[3] = dx / 2.0 * sig * (ph[2] + ph[3]);
+    for (int gp = 0; gp < G; gp++) {
+      const double k2 = 2.0 * Kap[((size_t)tau * G + gp) * G + g];  // dx/2 Sigma_s,gp->g
+      tally[4] += k2 * (ph_s[gp * 4 + 0][cl] + ph_s[gp * 4 + 1][cl]);
+      tally[5] += k2 * (ph_s[gp * 4 + 2][cl] + ph_s[gp * 4 + 3][cl]);
+    }
+    if (Q) {
+      const double *q = Q + j;
+      tally[6] = dx / 2.0 * (q[(size_t)(g * 4 + 0) * Jp] + q[(size_t)(g * 4 + 1) * Jp]);
+      tally[7] = dx / 2.0 * (q[(size_t)(g * 4 + 2) * Jp] + q[(size_t)(g * 4 + 3) * Jp]);
+    }
+  }
+  // reduce each tally over the 32 cells of this group's warp (one warp per group)
+#pragma unroll
+  for (int k = 0; k < 8; k++) {
+    double x = tally[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (cl == 0) bal_partials[((size_t)blockIdx.x * G + g) * 8 + k] = x;
+  }
+}
+
+// Sum the balance partials in a fixed order and add the leakage
+// sum_m w_m mu_m (psi at x = X - psi at x = 0) with the upstream edge values.
+__global__ void k_balance_final(int J, int Jp, int N, int G, int nblk, const double *__restrict__ bal_partials,
+                                const double *__restrict__ mu, const double *__restrict__ w,
+                                const double *__restrict__ inc, const double *Psi0, const double *Psi1,
+                                const DevState *__restrict__ ds, double *__restrict__ bal) {
+  const int g = blockIdx.x;
+  __shared__ double acc[8][64];
+  if (ds->status != OCI_OK) return;
+  const int t = threadIdx.x;  // 64 threads
+  double s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int b = t; b < nblk; b += 64)
+    for (int k = 0; k < 8; k++) s[k] += bal_partials[((size_t)b * G + g) * 8 + k];
+  for (int k = 0; k < 8; k++) acc[k][t] = s[k];
+  __syncthreads();
+  if (t == 0) {
+    double tot[8];
+    for (int k = 0; k < 8; k++) {
+      double x = 0.0;
+      for (int i = 0; i < 64; i++) x += acc[k][i];
+      tot[k] = x;
+    }
+    const double *P = ds->cur ? Psi1 : Psi0;
+    double lA = 0.0, lE = 0.0;
+    for (int m = 0; m < N; m++) {
+      const int gm = g * N + m;
+      double rk, rh, lk, lh;
+      if (mu[m] > 0) {
+        rk = P[(size_t)(gm * 4 + 1) * Jp + (J - 1)];
+        rh = P[(size_t)(gm * 4 + 3) * Jp + (J - 1)];
+        lk = inc[gm * 2 + 0];
+        lh = inc[gm * 2 + 1];
+      } else {
+        lk = P[(size_t)(gm * 4 + 0) * Jp];
+        lh = P[(size_t)(gm * 4 + 2) * Jp];
+        rk = inc[(G * N + gm) * 2 + 0];
+        rh = inc[(G * N + gm) * 2 + 1];
+      }
+      lA += w[m] * mu[m] * (rk - lk);
+      lE += w[m] * mu[m] * (rh - lh);
+    }
+    double *bg = bal + (size_t)g * 10;
+    bg[0] = tot[0]; bg[1] = lA; bg[2] = tot[2]; bg[3] = tot[4]; bg[4] = tot[6];
+    bg[5] = tot[1]; bg[6] = lE; bg[7] = tot[3]; bg[8] = tot[5]; bg[9] = tot[7];
+  }
+}
+
+void launch_carry(Handle &h) {
+  const int nblk = (h.J + 31) / 32;
+  dim3 block(32, h.G);
+  k_carry<<<nblk, block, 0, h.stream>>>(h.J, h.Jp, h.N, h.G, h.type, h.tt.dx, h.tt.sig, h.tt.Kap, h.v, h.dt, h.w,
+                                        h.Q, h.Psi[0], h.Psi[1], h.ds, h.psi_prev, h.phi, h.bal_partials);
+  k_balance_final<<<h.G, 64, 0, h.stream>>>(h.J, h.Jp, h.N, h.G, nblk, h.bal_partials, h.mu, h.w, h.inc, h.Psi[0],
+                                            h.Psi[1], h.ds, h.bal);
+}
+
+// ------------------------------------------------------------------ layout
+// ABI [J][K] (K = G*N*P or G*4) <-> device [K][Jp], 32x32 tiles through shared memory.
+__global__ void k_transpose_in(int J, int Jp, int K, const double *__restrict__ src, double *__restrict__ dst) {
+  __shared__ double tile[32][33];
+  const int k0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int j = j0 + r, k = k0 + threadIdx.x;
+    tile[r][threadIdx.x] = (j < J && k < K) ? src[(size_t)j * K + k] : 0.0;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int k = k0 + r, j = j0 + threadIdx.x;
+    if (k < K && j < Jp) dst[(size_t)k * Jp + j] = tile[threadIdx.x][r];
+  }
+}
+
+__global__ void k_transpose_out(int J, int Jp, int K, const double *__restrict__ src, double *__restrict__ dst) {
+  __shared__ double tile[32][33];
+  const int k0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int k = k0 + r, j = j0 + threadIdx.x;
+    tile[r][threadIdx.x] = (k < K && j < J) ? src[(size_t)k * Jp + j] : 0.0;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int j = j0 + r, k = k0 + threadIdx.x;
+    if (j < J && k < K) dst[(size_t)j * K + k] = tile[threadIdx.x][r];
+  }
+}
+
+void launch_transpose_in(Handle &h, const double *src_abi, double *dst_soa, int K) {
+  dim3 grid((K + 31) / 32, (h.Jp + 31) / 32);
+  k_transpose_in<<<grid, dim3(32, 8), 0, h.stream>>>(h.J, h.Jp, K, src_abi, dst_soa);
+}
+
+void launch_transpose_out(Handle &h, const double *src_soa, double *dst_abi, int K) {
+  dim3 grid((K + 31) / 32, (h.J + 31) / 32);
+  k_transpose_out<<<grid, dim3(32, 8), 0, h.stream>>>(h.J, h.Jp, K, src_soa, dst_abi);
+}
+
+void launch_phi_out(Handle &h, double *dst_abi) { launch_transpose_out(h, h.phi, dst_abi, h.G * 4); }
+
+}  // namespace oci

@@ -1,0 +1,188 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Bar: scalar flux within 1e-12 relative (max |diff| / max |oracle|), angular
+flux within 1e-11, identical sweep counts per step, balance tallies within
+1e-11 of their magnitude.  Sizes span several thread blocks and ragged tails;
+full-size configurations are checked on sampled cells after one sweep from a
+seeded random iterate."""
+import numpy as np
+import pytest
+
+from oracle import OCI, SI, Oracle
+from paper_2503_00264_gb300 import oci
+from paper_2503_00264_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def compare_steps(p, steps, solver=oci.SOLVER_AUTO, method="oci", guess=None):
+    o = Oracle(p, factor=(method == "oci"))
+    with oci.Solver(p, solver=solver, guess=guess) as s:
+        for k in range(steps):
+            r = o.step(OCI if method == "oci" else SI, guess=guess)
+            st = s.step() if method == "oci" else s.si_step()
+            assert st["status"] == 0
+            assert st["iters"] == r["iters"], (k, st["iters"], r["iters"])
+            assert rel(s.phi(), r["phi"]) < 1e-12, k
+            assert rel(s.psi(), r["Psi"]) < 1e-11, k
+            bal = s.balance()
+            scale = np.abs(r["bal"]).max()
+            assert np.abs(bal - r["bal"]).max() <= 1e-11 * max(scale, 1e-300), k
+            pp, t = s.state()
+            assert rel(pp, o.psi_prev) < 1e-11 and abs(t - o.t) < 1e-12
+    return o
+
+
+SMALL = [(1, 1, 2, 1), (2, 5, 4, 1), (3, 33, 8, 1), (4, 129, 8, 1), (5, 40, 4, 2), (6, 17, 8, 3),
+         (7, 70, 16, 1), (8, 9, 8, 5)]
+
+
+@pytest.mark.parametrize("seed,J,N,G", SMALL)
+def test_oci_structured_matches_oracle(seed, J, N, G):
+    compare_steps(W.random_slab(seed, J, N, G).replace(tol=1e-11), 3)
+
+
+@pytest.mark.parametrize("seed,J,N,G", SMALL[:6])
+def test_oci_dense_lu_matches_oracle(seed, J, N, G):
+    compare_steps(W.random_slab(seed, J, N, G).replace(tol=1e-11), 2, solver=oci.SOLVER_DENSE_LU)
+
+
+@pytest.mark.parametrize("seed,J,N,G", SMALL[:6])
+def test_si_matches_oracle(seed, J, N, G):
+    compare_steps(W.random_slab(seed, J, N, G).replace(tol=1e-11), 2, method="si")
+
+
+def test_slab64_ten_steps():
+    """64 uniform cells, S8, c = 0.5, dt = 0.1, left inflow 1, tol 1e-8, 10 steps."""
+    compare_steps(W.slab_64_cells(), 10)
+
+
+def test_guess_zero_policy():
+    compare_steps(W.random_slab(12, 50, 8, 2).replace(tol=1e-11), 2, guess=oci.GUESS_ZERO)
+
+
+def test_max_sizes():
+    """Largest angular order (N = 128) and many groups (G = 16)."""
+    compare_steps(W.random_slab(13, 4, 128, 1).replace(tol=1e-10), 1)
+    compare_steps(W.random_slab(14, 6, 8, 16).replace(tol=1e-10), 1)
+
+
+def test_fixed_sweeps_and_history():
+    p = W.random_slab(15, 300, 16, 2)
+    o = Oracle(p)
+    o.Psi[...] = W.random_guess(p, 5)
+    with oci.Solver(p) as s:
+        s.set_psi(W.random_guess(p, 5))
+        e_gpu = s.iterate(25)
+        e_orc = o.iterate(25)
+        keep = e_orc > 1e-8 * np.abs(o.Psi).max()
+        assert np.all(np.abs(e_gpu - e_orc)[keep] <= 1e-9 * e_orc[keep])
+        assert rel(s.psi(), o.Psi) < 1e-11
+
+
+def test_noconv_is_not_committed():
+    p = W.random_slab(16, 60, 8, 1, c_max=0.99).replace(tol=1e-14, max_iter=3)
+    with oci.Solver(p) as s:
+        pp0, t0 = s.state()
+        st = s.step(allow_noconv=True)
+        assert st["status"] == oci.E_NOCONV and st["iters"] == 3
+        pp1, t1 = s.state()
+        assert t1 == t0 and np.array_equal(pp0, pp1)
+
+
+def test_mb_closed_form_with_boundary_updates():
+    """Spatially uniform transient (multiple-balance pair per step) through
+    oci_set_boundary, as in the oracle pin."""
+    J, N = 40, 8
+    st_, ss_, v, dt, Qv = 1.3, 0.6, 2.0, 0.25, 0.8
+    sa = st_ - ss_
+    M = np.array([[sa, 1 / (v * dt)], [-2 / (v * dt), 2 / (v * dt) + sa]])
+    p = W.Problem(J=J, N=N, G=1, n_mat=1, dx=np.full(J, 0.2), mat=np.zeros(J, np.int32), sigma_t=[[st_]],
+                  sigma_s=[[[ss_]]], v=[v], dt=dt, Q=np.full((J, 1, 4), Qv), psi_init=np.full((J, 1, N, 2), 0.3),
+                  tol=1e-13)
+    prev = 0.3
+    with oci.Solver(p) as s:
+        for k in range(5):
+            pk, ph = np.linalg.solve(M, [Qv / 2 + prev / (v * dt), Qv / 2])
+            inc = np.zeros((1, N, 2))
+            inc[..., 0], inc[..., 1] = pk, ph
+            s.set_boundary(inc, inc)
+            s.step()
+            psi = s.psi()
+            assert np.abs(psi[..., 0:2] - pk).max() < 1e-12
+            assert np.abs(psi[..., 2:4] - ph).max() < 1e-12
+            prev = ph
+
+
+def test_checkpoint_resume_bitwise_and_deterministic():
+    p = W.random_slab(17, 200, 8, 2).replace(tol=1e-10)
+    with oci.Solver(p) as a:
+        for _ in range(5):
+            a.step()
+        pp, t = a.state()
+        psi = a.psi()
+        for _ in range(3):
+            a.step()
+        ref = a.psi()
+    with oci.Solver(p) as b:
+        b.set_state(pp, t)
+        b.set_psi(psi)
+        for _ in range(3):
+            b.step()
+        assert np.array_equal(b.psi(), ref)
+
+
+def _sampled_one_sweep(p, cells):
+    guess = W.random_guess(p, 11)
+    with oci.Solver(p) as s:
+        s.set_psi(guess)
+        s.iterate(1)
+        got = s.psi()[cells]
+    o = Oracle(p, factor=False)
+    ref = o.cells(cells, guess)
+    return got, ref
+
+
+def test_full_size_slab3_sampled():
+    """2^18 cells, S16, 3 regions: one sweep from a random iterate, sampled cells
+    (boundaries, region borders, random) against the oracle's per-cell solve."""
+    p = W.slab_3region(c=0.99, tau=0.1)
+    rng = np.random.default_rng(0)
+    cells = np.unique(np.concatenate([[0, 1, 1023, 1024, 2047, 2048, p.J - 2, p.J - 1],
+                                      rng.integers(0, p.J, 56)])).astype(np.int32)
+    got, ref = _sampled_one_sweep(p, cells)
+    assert rel(got, ref) < 1e-12
+
+
+def test_full_size_multigroup_sampled():
+    """2^16 cells, S16, G = 8, 4 materials: one sweep, sampled cells."""
+    p = W.slab_multigroup()
+    cells = np.array([0, 1, 1023, 1024, 30000, 65534, 65535], np.int32)
+    got, ref = _sampled_one_sweep(p, cells)
+    assert rel(got, ref) < 1e-12
+
+
+def test_full_size_ragged_dense_sampled():
+    """2^16 cells of distinct widths through the dense per-cell LU path."""
+    p = W.slab_3region(c=0.9, tau=1.0, J=2 ** 16, ragged=True)
+    guess = W.random_guess(p, 12)
+    cells = np.array([0, 5, 1024, 40000, p.J - 1], np.int32)
+    with oci.Solver(p, solver=oci.SOLVER_DENSE_LU) as s:
+        s.set_psi(guess)
+        s.iterate(1)
+        got = s.psi()[cells]
+    ref = Oracle(p, factor=False).cells(cells, guess)
+    assert rel(got, ref) < 1e-12
+
+
+def test_full_size_step_balance():
+    """A converged step at full size satisfies both particle balances to O(e)."""
+    p = W.slab_3region(c=0.5, tau=0.01)
+    with oci.Solver(p) as s:
+        st = s.step()
+        assert st["status"] == 0
+        assert max(st["balance_rel"]) < 1e-9
