@@ -260,7 +260,7 @@ void launch_finalize(Handle &h, const double *partials, int n, cudaGraphConditio
 //   time edge (Eqs. scb-mb-c + d):
 //     dx/(v dt) sum_{L,R}(phi_h - phi_k) + leak + dx/2 St (phi_hL + phi_hR) - ... = 0
 // partial layout [block][g][8] = {timeA, timeE, collA, collE, scatA, scatE, srcA, srcE}.
-__global__ void __launch_bounds__(256) k_carry(int J, int Jp, int N, int G, const int32_t *__restrict__ type,
+__global__ void __launch_bounds__(32 * kMaxG) k_carry(int J, int Jp, int N, int G, const int32_t *__restrict__ type,
                                                const double *__restrict__ tdx, const double *__restrict__ tsig,
                                                const double *__restrict__ Kap, const double *__restrict__ v,
                                                double dt, const double *__restrict__ w,

@@ -1,0 +1,58 @@
+"""Small driver for profiling one kernel of liboci under a profiler.
+
+    python -m paper_2503_00264_gb300.profile_case --case slab3 --sweeps 3
+    python -m paper_2503_00264_gb300.profile_case --case multigroup --sweeps 3
+    python -m paper_2503_00264_gb300.profile_case --case slab3 --si --sweeps 2
+
+Sets up the workload, loads a seeded random iterate and runs exactly --sweeps
+sweeps through the C ABI (oci_iterate / si_iterate), then exits.  Prints one
+line with the device time of the sweeps (CUDA events).
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2503_00264_gb300 import oci  # noqa: E402
+from paper_2503_00264_gb300 import workloads as W  # noqa: E402
+
+
+def make(case: str, J: int | None):
+    if case == "slab3":
+        return W.slab_3region(c=0.9, tau=0.1, J=J or 2 ** 18)
+    if case == "slab3_ragged":
+        return W.slab_3region(c=0.9, tau=0.1, J=J or 2 ** 16, ragged=True)
+    if case == "multigroup":
+        return W.slab_multigroup(J=J or 2 ** 16)
+    raise SystemExit(f"unknown case {case}")
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--case", default="slab3")
+    ap.add_argument("--J", type=int, default=None)
+    ap.add_argument("--sweeps", type=int, default=3)
+    ap.add_argument("--solver", default="structured", choices=["structured", "dense"])
+    ap.add_argument("--si", action="store_true")
+    a = ap.parse_args()
+    import torch
+    p = make(a.case, a.J)
+    solver = oci.SOLVER_DENSE_LU if a.solver == "dense" else oci.SOLVER_STRUCTURED
+    stream = torch.cuda.Stream()
+    with oci.Solver(p, solver=solver, stream=stream.cuda_stream) as s:
+        s.set_psi(W.random_guess(p, 1))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        (s.si_iterate if a.si else s.iterate)(a.sweeps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        print(f"{p.name}: {a.sweeps} {'SI' if a.si else 'OCI'} sweeps, {e0.elapsed_time(e1) / a.sweeps * 1e3:.1f} us/sweep")
+
+
+if __name__ == "__main__":
+    main()
