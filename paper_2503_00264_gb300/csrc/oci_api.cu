@@ -2,7 +2,10 @@
 // per-cell-type tables, device state, the convergence loops as CUDA graphs with a
 // conditional WHILE node, and state access.
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
+
+#include <algorithm>
 
 #include <cstdio>
 #include <cstring>
@@ -290,6 +293,10 @@ static int setup_impl(const oci_problem *p, oci_handle *h) {
   h->guess = p->guess;
   h->solver = p->solver == OCI_SOLVER_AUTO ? OCI_SOLVER_STRUCTURED : p->solver;
   h->stream = (cudaStream_t)p->stream;
+  {
+    const char *ng = getenv("OCI_NO_GRAPH");
+    h->no_graph = ng && ng[0] == '1';
+  }
   CK(cudaGetDevice(&h->device));
   const size_t J = h->J, N = h->N, G = h->G, Jp = h->Jp;
   h->h_dx.assign(p->dx, p->dx + J);
@@ -448,7 +455,22 @@ static int run_step(Handle &h, bool si, oci_stats *st) {
   }
   cudaGraphExec_t g = si ? h.g_si : h.g_oci;
   CK(cudaEventRecord(h.ev0, s));
-  CK(cudaGraphLaunch(g, s));
+  if (h.no_graph) {
+    // host-driven loop over the same kernels (for profilers that do not
+    // descend into conditional graph bodies): batches of sweeps, each kernel
+    // returns at once when the device state says the step is done
+    cudaGraphConditionalHandle none{};
+    for (int done_sweeps = 0; done_sweeps < h.max_iter;) {
+      const int batch = std::min(16, h.max_iter - done_sweeps);
+      for (int i = 0; i < batch; i++) launch_body(h, si, none, 0);
+      done_sweeps += batch;
+      CK(cudaMemcpyAsync(h.h_ds, h.ds, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      if (h.h_ds->done) break;
+    }
+  } else {
+    CK(cudaGraphLaunch(g, s));
+  }
   CK(cudaEventRecord(h.ev1, s));
   launch_carry(h);  // device-guarded: commits only a converged step
   CK(cudaMemcpyAsync(h.h_ds, h.ds, sizeof(DevState), cudaMemcpyDeviceToHost, s));

@@ -92,7 +92,7 @@ struct Handle {
   cudaGraphExec_t g_oci = nullptr, g_si = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   int last_iters = 0;
-  bool committed_once = false;
+  bool no_graph = false;           // OCI_NO_GRAPH=1: host-driven loop instead of the WHILE graph
 };
 
 // ---------------------------------------------------------------- launches
