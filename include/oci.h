@@ -61,9 +61,16 @@ enum {
   OCI_FP64 = 0,       /* everything in IEEE FP64                                   */
   OCI_TF32_IR = 1,    /* block apply on tensor cores in TF32 (FP32 accumulation),
                          FP64 residual, norm, balance and carry (defect correction) */
-  OCI_BF16X3_IR = 2   /* block apply as three BF16 products (hi*hi + hi*lo + lo*hi),
+  OCI_BF16X3_IR = 2,  /* block apply as three BF16 products (hi*hi + hi*lo + lo*hi),
                          FP32 accumulation, FP64 residual/norm/balance/carry        */
+  OCI_FP32_IR = 3     /* structured block apply in FP32 on the CUDA cores, FP64
+                         residual/norm/balance/carry                               */
 };
+/* The three *_IR forms run the OCI sweeps on an FP32 correction delta of an FP64
+ * iterate Psi (delta^{i+1} = A~^{-1}(r + B delta^i), r = c + B Psi - A Psi in
+ * FP64) and fold delta into Psi with a fresh FP64 residual every few sweeps
+ * (defect correction).  In exact arithmetic the iterates, and so the norm and
+ * the stop rule, are those of the FP64 form; the fixed point is the FP64 one. */
 
 /* initial iterate of every time step (oci_problem.guess) */
 enum {

@@ -30,6 +30,8 @@ int cuda_fail(cudaError_t e, const char *what) {
 int si_partials(const Handle &h);
 int dense_partials(const Handle &h);
 void launch_si_phi_from_psi(Handle &h, double *);
+void launch_mx_settle(Handle &h, int kind);
+const void *k_mx_inner_ptr();
 
 #define CK(call)                                          \
   do {                                                    \
@@ -150,14 +152,14 @@ static int validate(const oci_problem *p) {
   if (p->inc_right && !all_finite(p->inc_right, G * N * 2)) return set_error("inc_right must be finite"), OCI_E_INVAL;
   if (!(std::isfinite(p->tol) && p->tol >= 0)) return set_error("tol must be finite and >= 0"), OCI_E_INVAL;
   if (p->max_iter < 1) return set_error("max_iter must be >= 1"), OCI_E_INVAL;
-  if (p->precision < OCI_FP64 || p->precision > OCI_BF16X3_IR) return set_error("bad precision"), OCI_E_INVAL;
+  if (p->precision < OCI_FP64 || p->precision > OCI_FP32_IR) return set_error("bad precision"), OCI_E_INVAL;
   if (p->guess < OCI_GUESS_PREV || p->guess > OCI_GUESS_ZERO) return set_error("bad guess policy"), OCI_E_INVAL;
   if (p->solver < OCI_SOLVER_AUTO || p->solver > OCI_SOLVER_DENSE_LU) return set_error("bad solver"), OCI_E_INVAL;
   if (p->precision != OCI_FP64 && p->solver == OCI_SOLVER_DENSE_LU)
     return set_error("the dense per-cell solver is FP64 only"), OCI_E_INVAL;
   if (p->solver == OCI_SOLVER_DENSE_LU && 4 * p->N * p->G > 1024)
     return set_error("the dense per-cell solver needs 4*N*G <= 1024"), OCI_E_INVAL;
-  if (p->precision != OCI_FP64)
+  if (p->precision == OCI_TF32_IR || p->precision == OCI_BF16X3_IR)
     return set_error("this precision form is not built"), OCI_E_INVAL;
   return OCI_OK;
 }
@@ -166,7 +168,8 @@ static int validate(const oci_problem *p) {
 // Per unique (material, dx) cell type: L_{g,m}^{-1} (Eq. Aj), the inflow columns,
 // Mp = (I - K H)^{-1} K and K.
 static int build_tables(Handle &h, std::vector<double> &Linv, std::vector<double> &Cin, std::vector<double> &Mp,
-                        std::vector<double> &Kap, std::vector<double> &tdx, std::vector<double> &tsig) {
+                        std::vector<double> &Kap, std::vector<double> &tdx, std::vector<double> &tsig,
+                        std::vector<double> &Lco) {
   const int N = h.N, G = h.G, J = h.J;
   std::map<std::pair<int, uint64_t>, int> ids;
   h.h_type.assign(J, 0);
@@ -194,6 +197,7 @@ static int build_tables(Handle &h, std::vector<double> &Linv, std::vector<double
   Kap.assign((size_t)T * G * G, 0.0);
   tdx.assign(T, 0.0);
   tsig.assign((size_t)T * G, 0.0);
+  Lco.assign((size_t)T * G * N * 5, 0.0);
   std::vector<double> L(16), Li, KH((size_t)G4 * G4), IKH((size_t)G4 * G4), IKHinv;
   for (int t = 0; t < T; t++) {
     const int mt = types[t].first;
@@ -218,6 +222,11 @@ static int build_tables(Handle &h, std::vector<double> &Linv, std::vector<double
         }
         const size_t o = ((size_t)t * G * N + (size_t)g * N + m);
         for (int k = 0; k < 16; k++) Linv[o * 16 + k] = Li[k];
+        Lco[o * 5 + 0] = a;
+        Lco[o * 5 + 1] = mu / 2.0;
+        Lco[o * 5 + 2] = al / 2.0;
+        Lco[o * 5 + 3] = al;
+        Lco[o * 5 + 4] = al + a;
         // inflow enters rows 0,2 (mu > 0) or 1,3 (mu < 0) with factor |mu|
         const int ca = mu > 0 ? 0 : 1, cb = mu > 0 ? 2 : 3;
         for (int p = 0; p < 4; p++) {
@@ -268,7 +277,8 @@ static void free_handle(Handle *h) {
                   h->Q,      h->inc,    h->type,      h->mu,        h->w,            h->v,         h->tt.Linv,
                   h->tt.Cin, h->tt.Mp,  h->tt.Kap,    h->tt.dx,     h->tt.sig,       h->si_z,      h->si_uin,
                   h->LU,     h->piv,    h->partials,  h->bal_partials, h->bal,       h->e_hist,    h->ds,
-                  h->stage};
+                  h->stage,  h->delta[0], h->delta[1], h->z32, h->w32, h->tt.Lco, h->tt.Linv32, h->tt.Cin32,
+                  h->tt.Mp32};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (h->h_ds) cudaFreeHost(h->h_ds);
@@ -306,8 +316,8 @@ static int setup_impl(const oci_problem *p, oci_handle *h) {
   h->h_v.assign(p->v, p->v + G);
   gauss_legendre(h->N, h->h_mu, h->h_w);
 
-  std::vector<double> Linv, Cin, Mp, Kap, tdx, tsig;
-  int rc = build_tables(*h, Linv, Cin, Mp, Kap, tdx, tsig);
+  std::vector<double> Linv, Cin, Mp, Kap, tdx, tsig, Lco;
+  int rc = build_tables(*h, Linv, Cin, Mp, Kap, tdx, tsig, Lco);
   if (rc) return rc;
   cudaStream_t s = h->stream;
   const size_t nPsi = G * N * 4 * Jp;
@@ -352,6 +362,7 @@ static int setup_impl(const oci_problem *p, oci_handle *h) {
   int np = sc.grid;
   np = std::max(np, si_partials(*h));
   np = std::max(np, dense_partials(*h));
+  np = std::max(np, mx_partials(*h));
   h->n_partials = np;
   CK(cudaMalloc(&h->partials, (size_t)np * 8));
   const int nblk_carry = (h->J + 31) / 32;
@@ -372,6 +383,30 @@ static int setup_impl(const oci_problem *p, oci_handle *h) {
     if ((rc = dense_setup(*h))) return rc;
   }
   CK(cudaFuncSetAttribute(k_oci_sweep_ptr(), cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  if (h->precision != OCI_FP64) {
+    auto to32 = [](const std::vector<double> &a) {
+      std::vector<float> f(a.size());
+      for (size_t i = 0; i < a.size(); i++) f[i] = (float)a[i];
+      return f;
+    };
+    std::vector<float> L32 = to32(Linv), C32 = to32(Cin), M32 = to32(Mp), W32 = to32(h->h_w);
+    if ((rc = dev_upload(&h->tt.Lco, Lco.data(), Lco.size(), s))) return rc;
+    if ((rc = dev_upload(&h->tt.Linv32, L32.data(), L32.size(), s))) return rc;
+    if ((rc = dev_upload(&h->tt.Cin32, C32.data(), C32.size(), s))) return rc;
+    if ((rc = dev_upload(&h->tt.Mp32, M32.data(), M32.size(), s))) return rc;
+    if ((rc = dev_upload(&h->w32, W32.data(), W32.size(), s))) return rc;
+    CK(cudaMalloc(&h->delta[0], nPsi * 4));
+    CK(cudaMalloc(&h->delta[1], nPsi * 4));
+    CK(cudaMalloc(&h->z32, nPsi * 4));
+    CK(cudaMemsetAsync(h->delta[0], 0, nPsi * 4, s));
+    CK(cudaMemsetAsync(h->delta[1], 0, nPsi * 4, s));
+    CK(cudaMemsetAsync(h->z32, 0, nPsi * 4, s));
+    CK(cudaFuncSetAttribute(k_mx_inner_ptr(), cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    const char *km = getenv("OCI_MX_KMAX");
+    if (km) h->mx_kmax = std::max(1, atoi(km));
+    const char *th = getenv("OCI_MX_THETA");
+    if (th) h->mx_theta = atof(th);
+  }
   if ((rc = build_graph(*h, false, &h->g_oci))) return rc;
   CK(cudaStreamSynchronize(s));
   CK(cudaGetLastError());
@@ -383,6 +418,10 @@ static void launch_body(Handle &h, bool si, cudaGraphConditionalHandle cond, int
   if (si) {
     launch_si_sweep(h);
     launch_finalize(h, h.partials, si_partials(h), cond, use_cond);
+  } else if (h.precision != OCI_FP64) {
+    launch_mx_inner(h);
+    launch_mx_finalize(h, cond, use_cond);
+    launch_mx_outer(h, 1);
   } else if (h.solver == OCI_SOLVER_DENSE_LU) {
     launch_dense_sweep(h);
     launch_finalize(h, h.partials, dense_partials(h), cond, use_cond);
@@ -436,6 +475,14 @@ static int begin_iteration(Handle &h, int fixed, int cap) {
   d.fixed = fixed;
   d.tol = h.tol;
   d.e = d.e_prev = d.rho = 0.0;
+  d.dcur = 0;
+  d.blk_i = 0;
+  d.refine = 0;
+  d.applied = 0;
+  d.k_max = h.mx_kmax;
+  d.n_refine = 0;
+  d.theta = h.mx_theta;
+  d.e_blk0 = 0.0;
   CK(cudaMemcpyAsync(h.ds, h.h_ds, sizeof(DevState), cudaMemcpyHostToDevice, h.stream));
   return OCI_OK;
 }
@@ -448,6 +495,9 @@ static int run_step(Handle &h, bool si, oci_stats *st) {
   if (rc) return rc;
   if (si) {
     launch_si_phi_from_psi(h, nullptr);
+  } else if (h.precision != OCI_FP64) {
+    launch_dense_step_const(h);  // c (not pre-multiplied)
+    launch_mx_outer(h, 0);       // FP64 residual of the initial iterate
   } else if (h.solver == OCI_SOLVER_DENSE_LU) {
     launch_dense_step_const(h);
   } else {
@@ -472,6 +522,7 @@ static int run_step(Handle &h, bool si, oci_stats *st) {
     CK(cudaGraphLaunch(g, s));
   }
   CK(cudaEventRecord(h.ev1, s));
+  if (!si && h.precision != OCI_FP64) launch_mx_settle(h, 0);
   launch_carry(h);  // device-guarded: commits only a converged step
   CK(cudaMemcpyAsync(h.h_ds, h.ds, sizeof(DevState), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(h.h_bal, h.bal, (size_t)h.G * 10 * 8, cudaMemcpyDeviceToHost, s));
@@ -520,8 +571,12 @@ static int run_fixed(Handle &h, bool si, int n, double *e_hist) {
   }
   int rc = begin_iteration(h, 1, h.e_hist_cap);
   if (rc) return rc;
+  const bool mx = !si && h.precision != OCI_FP64;
   if (si) {
     launch_si_phi_from_psi(h, nullptr);
+  } else if (mx) {
+    launch_dense_step_const(h);
+    launch_mx_outer(h, 0);
   } else if (h.solver == OCI_SOLVER_DENSE_LU) {
     launch_dense_step_const(h);
   } else {
@@ -529,6 +584,11 @@ static int run_fixed(Handle &h, bool si, int n, double *e_hist) {
   }
   cudaGraphConditionalHandle none{};
   for (int i = 0; i < n; i++) launch_body(h, si, none, 0);
+  if (mx) {
+    launch_mx_settle(h, 0);
+    launch_mx_outer(h, 2);
+    launch_mx_settle(h, 1);
+  }
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(h.h_ds, h.ds, sizeof(DevState), cudaMemcpyDeviceToHost, h.stream));
   if (e_hist && n > 0) CK(cudaMemcpyAsync(e_hist, h.e_hist, (size_t)n * 8, cudaMemcpyDefault, h.stream));

@@ -33,6 +33,15 @@ struct DevState {
   int fixed;      // 1: no stop test (oci_iterate)
   double tol;
   double e, e_prev, rho;
+  // mixed-precision form (inner sweeps on an FP32 correction, FP64 refinement)
+  int dcur;       // index (0/1) of the delta buffer holding the current correction
+  int blk_i;      // inner sweeps since the last refinement (0: correction is zero)
+  int refine;     // 1: the next outer kernel applies delta and refreshes the residual
+  int applied;    // 1: the correction has been folded into Psi after convergence
+  int k_max;      // inner sweeps per refinement at most
+  int n_refine;   // refinements in this step
+  double theta;   // refine once e < theta * (first e of the block)
+  double e_blk0;
 };
 
 // Per-cell-type tables of the structured solve (all FP64, device).
@@ -44,6 +53,10 @@ struct TypeTables {
   double *Kap = nullptr;    // [T][G][G]      dx/4 * Sigma_s,gp->g  (index [gp][g])
   double *dx = nullptr;     // [T]
   double *sig = nullptr;    // [T][G]         Sigma_t,g
+  double *Lco = nullptr;    // [T][G][N][5]   {a, mu/2, alpha/2, alpha, alpha+a} of L_{c,g,m} (Eq. Aj)
+  float *Linv32 = nullptr;  // FP32 copies for the low-precision inner solve
+  float *Cin32 = nullptr;
+  float *Mp32 = nullptr;
 };
 
 struct Handle {
@@ -70,6 +83,12 @@ struct Handle {
   int32_t *type = nullptr;       // [Jp]
   double *mu = nullptr, *w = nullptr, *v = nullptr;
   TypeTables tt;
+  // mixed-precision form
+  float *delta[2] = {nullptr, nullptr};  // [G][N][4][Jp] correction ping-pong
+  float *z32 = nullptr;                  // [G][N][4][Jp] L~^{-1} r of the last refinement
+  float *w32 = nullptr;
+  int mx_kmax = 64;
+  double mx_theta = 1e-3;
   // SI scratch
   double *si_z = nullptr;        // [G][N][4][Jp]   Linv * d0
   double *si_uin = nullptr;      // [G][N][2][Jp]   incoming edge of every cell
@@ -115,6 +134,11 @@ void launch_phi_out(Handle &h, double *dst_abi);
 // SI
 void launch_si_sweep(Handle &h);
 void launch_si_phi_from_psi(Handle &h, double *phi_dst);
+// mixed-precision form
+void launch_mx_inner(Handle &h);
+void launch_mx_outer(Handle &h, int mode);
+void launch_mx_finalize(Handle &h, cudaGraphConditionalHandle cond, int use_cond);
+int mx_partials(const Handle &h);
 // dense path
 int dense_setup(Handle &h);
 void launch_dense_step_const(Handle &h);

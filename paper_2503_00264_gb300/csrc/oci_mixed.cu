@@ -1,0 +1,362 @@
+// oci_mixed.cu -- mixed-precision form of the OCI step: inner sweeps on an FP32
+// correction, FP64 refinement.
+//
+// With A = L_c - S block diagonal and B the lagged-inflow coupling (Eq. oci),
+// plain OCI is Psi^{l+1} = A^{-1}(c + B Psi^l).  From an outer iterate Psi with
+// FP64 residual r = c + B Psi - A Psi, the iterates of plain OCI are
+// Psi^{l+i} = Psi + delta^i with
+//     delta^0 = 0,   delta^{i+1} = A^{-1}(r + B delta^i),
+// and the per-sweep change e_i = ||delta^{i+1} - delta^i||_2 equals plain OCI's
+// ||Psi^{l+i+1} - Psi^{l+i}||_2.  The inner recursion runs in FP32 (structured
+// cell solve with FP32 tables); every few sweeps the correction is folded into
+// the FP64 iterate and the residual is recomputed in FP64, which removes the
+// FP32 error accumulated so far (defect correction).  The stop rule of Sec. 2.1
+// is applied to every inner sweep, so sweep counts track the FP64 form.
+//
+// A refinement happens after k_max inner sweeps, or once e < theta * (first e
+// of the block) -- by then the FP32 correction has gained about -log10(theta)
+// digits and more inner sweeps would only resolve FP32 rounding -- and at
+// convergence.  FP64 is kept for Psi, the residual, the norm accumulation, the
+// balance tallies and the carry.
+#include <math.h>
+
+#include "oci_internal.h"
+
+namespace oci {
+
+// ---------------------------------------------------------------- inner sweep
+// delta_out = A~^{-1}(r + B delta_in) through the structured solve in FP32:
+// t = z + Cin u, y = sum_m w t, s = Mp y, delta = t + Linv s, where z = A~-block
+// solve of r precomputed by the outer kernel (z = Linv r).  The correction has
+// zero incident flux at the slab ends (the boundary values live in r).
+__global__ void __launch_bounds__(256) k_mx_inner(int J, int Jp, int N, int G, const int32_t *__restrict__ type,
+                                                  const float *__restrict__ Linv, const float *__restrict__ Cin,
+                                                  const float *__restrict__ Mp, const float *__restrict__ w,
+                                                  const float *__restrict__ z, float *D0, float *D1,
+                                                  const DevState *__restrict__ ds, double *__restrict__ partials) {
+  extern __shared__ float smf[];
+  __shared__ double red[32];
+  const int CB = blockDim.x;
+  const int cl = threadIdx.x, g = threadIdx.y;
+  const int j = blockIdx.x * CB + cl;
+  if (ds->done) return;
+  const bool zero = ds->refine || ds->blk_i == 0;
+  const int dcur = ds->dcur;
+  const float *__restrict__ Din = dcur ? D1 : D0;
+  float *__restrict__ Dout = dcur ? D0 : D1;
+  float *t_s = smf;
+  float *y_s = smf + (size_t)G * N * 4 * CB;
+  const bool active = j < J;
+  const int tau = active ? type[j] : 0;
+  const int N2 = N / 2;
+  const size_t tb = (size_t)tau * G * N;
+  float y0 = 0.f, y1 = 0.f, y2 = 0.f, y3 = 0.f;
+  if (active) {
+#pragma unroll 4
+    for (int m = 0; m < N; m++) {
+      const int gm = g * N + m;
+      const size_t base = (size_t)gm * 4 * Jp + j;
+      float uk = 0.f, uh = 0.f;
+      if (!zero) {
+        if (m >= N2) {
+          if (j > 0) {
+            uk = Din[base + (size_t)Jp - 1];
+            uh = Din[base + 3 * (size_t)Jp - 1];
+          }
+        } else if (j < J - 1) {
+          uk = Din[base + 1];
+          uh = Din[base + 2 * (size_t)Jp + 1];
+        }
+      }
+      const float *C = Cin + (tb + gm) * 8;
+      const float t0 = fmaf(C[1], uh, fmaf(C[0], uk, z[base]));
+      const float t1 = fmaf(C[3], uh, fmaf(C[2], uk, z[base + (size_t)Jp]));
+      const float t2 = fmaf(C[5], uh, fmaf(C[4], uk, z[base + 2 * (size_t)Jp]));
+      const float t3 = fmaf(C[7], uh, fmaf(C[6], uk, z[base + 3 * (size_t)Jp]));
+      float *ts = t_s + (size_t)(gm * 4) * CB + cl;
+      ts[0] = t0;
+      ts[CB] = t1;
+      ts[2 * CB] = t2;
+      ts[3 * CB] = t3;
+      const float wm = w[m];
+      y0 = fmaf(wm, t0, y0);
+      y1 = fmaf(wm, t1, y1);
+      y2 = fmaf(wm, t2, y2);
+      y3 = fmaf(wm, t3, y3);
+    }
+    float *ys = y_s + (size_t)(g * 4) * CB + cl;
+    ys[0] = y0;
+    ys[CB] = y1;
+    ys[2 * CB] = y2;
+    ys[3 * CB] = y3;
+  }
+  __syncthreads();
+  float e2 = 0.f;
+  if (active) {
+    const int G4 = 4 * G;
+    const float *M = Mp + (size_t)tau * G4 * G4 + (size_t)(g * 4) * G4;
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+    for (int k = 0; k < G4; k++) {
+      const float yk = y_s[(size_t)k * CB + cl];
+      s0 = fmaf(M[k], yk, s0);
+      s1 = fmaf(M[G4 + k], yk, s1);
+      s2 = fmaf(M[2 * G4 + k], yk, s2);
+      s3 = fmaf(M[3 * G4 + k], yk, s3);
+    }
+#pragma unroll 4
+    for (int m = 0; m < N; m++) {
+      const int gm = g * N + m;
+      const size_t base = (size_t)gm * 4 * Jp + j;
+      const float *L = Linv + (tb + gm) * 16;
+      const float *ts = t_s + (size_t)(gm * 4) * CB + cl;
+#pragma unroll
+      for (int p = 0; p < 4; p++) {
+        const float o = fmaf(L[p * 4 + 3], s3, fmaf(L[p * 4 + 2], s2, fmaf(L[p * 4 + 1], s1, fmaf(L[p * 4 + 0], s0, ts[p * CB]))));
+        const float d = zero ? o : o - Din[base + (size_t)p * Jp];
+        e2 = fmaf(d, d, e2);
+        Dout[base + (size_t)p * Jp] = o;
+      }
+    }
+  }
+  // FP64 accumulation of the per-thread FP32 partial sums
+  double v = (double)e2;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((tid & 31) == 0) red[tid >> 5] = v;
+  __syncthreads();
+  if (tid == 0) {
+    double s = 0.0;
+    for (int i = 0; i < (CB * G + 31) / 32; i++) s += red[i];
+    partials[blockIdx.x] = s;
+  }
+}
+
+// ---------------------------------------------------------------- outer (FP64)
+// mode 0: residual of Psi[cur] (start of a step, correction zero)
+// mode 1: if ds->refine: Psi[cur^1] = Psi[cur] + delta[dcur]; unless the step is
+//         done, residual of Psi[cur^1]
+// mode 2: if ds->blk_i > 0: Psi[cur^1] = Psi[cur] + delta[dcur] (apply only)
+// The residual r = c + s + inflow - L_c Psi (Eqs. oci, Aj, rhs_sg, scatter) is
+// formed in FP64 and z = Linv r (FP32) is stored for the inner sweeps.
+__global__ void __launch_bounds__(256) k_mx_outer(int J, int Jp, int N, int G, const int32_t *__restrict__ type,
+                                                  const double *__restrict__ Lco, const double *__restrict__ Kap,
+                                                  const float *__restrict__ Linv32, const double *__restrict__ w,
+                                                  const double *__restrict__ mu, const double *__restrict__ inc,
+                                                  const double *__restrict__ cvec, double *Psi0, double *Psi1,
+                                                  const float *D0, const float *D1, const DevState *__restrict__ ds,
+                                                  int mode, float *__restrict__ z32) {
+  extern __shared__ double smd[];
+  const int CB = blockDim.x;
+  const int cl = threadIdx.x, g = threadIdx.y;
+  const int j = blockIdx.x * CB + cl;
+  if (mode == 1 && !ds->refine) return;
+  if (mode == 2 && ds->blk_i == 0) return;
+  const bool apply = mode != 0;
+  const bool resid = mode == 0 || (mode == 1 && !ds->done);
+  const int cur = ds->cur;
+  const double *__restrict__ Pin = cur ? Psi1 : Psi0;
+  double *__restrict__ Pout = cur ? Psi0 : Psi1;
+  const float *__restrict__ Dl = ds->dcur ? D1 : D0;
+  const bool active = j < J;
+  const int tau = active ? type[j] : 0;
+  double ph[4] = {0.0, 0.0, 0.0, 0.0};
+  if (active) {
+    for (int m = 0; m < N; m++) {
+      const int gm = g * N + m;
+      const size_t base = (size_t)gm * 4 * Jp + j;
+      const double wm = w[m];
+#pragma unroll
+      for (int p = 0; p < 4; p++) {
+        double v = Pin[base + (size_t)p * Jp];
+        if (apply) {
+          v += (double)Dl[base + (size_t)p * Jp];
+          Pout[base + (size_t)p * Jp] = v;
+        }
+        ph[p] = fma(wm, v, ph[p]);
+      }
+    }
+  }
+  if (!resid) return;  // uniform
+  double *ph_s = smd;  // [G*4][CB]
+#pragma unroll
+  for (int p = 0; p < 4; p++) ph_s[(size_t)(g * 4 + p) * CB + cl] = ph[p];
+  __syncthreads();
+  if (!active) return;
+  double s[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int gp = 0; gp < G; gp++) {
+    const double k = Kap[((size_t)tau * G + gp) * G + g];
+#pragma unroll
+    for (int p = 0; p < 4; p++) s[p] = fma(k, ph_s[(size_t)(gp * 4 + p) * CB + cl], s[p]);
+  }
+  const double *__restrict__ P = apply ? Pout : Pin;
+  const int N2 = N / 2;
+  for (int m = 0; m < N; m++) {
+    const int gm = g * N + m;
+    const size_t base = (size_t)gm * 4 * Jp + j;
+    const double v0 = P[base], v1 = P[base + (size_t)Jp], v2 = P[base + 2 * (size_t)Jp], v3 = P[base + 3 * (size_t)Jp];
+    const double *L = Lco + ((size_t)tau * G * N + gm) * 5;  // a, mu/2, alpha/2, alpha, alpha+a
+    const double a = L[0], hm = L[1], ha = L[2], al = L[3], aa = L[4];
+    double r0 = cvec[base] + s[0];
+    double r1 = cvec[base + (size_t)Jp] + s[1];
+    double r2 = cvec[base + 2 * (size_t)Jp] + s[2];
+    double r3 = cvec[base + 3 * (size_t)Jp] + s[3];
+    if (m >= N2) {  // mu > 0: upstream R corner of cell j-1 into rows 0, 2
+      double uk, uh;
+      if (j > 0) {
+        const size_t nb = base - 1;
+        uk = Pin[nb + (size_t)Jp];
+        uh = Pin[nb + 3 * (size_t)Jp];
+        if (apply) {
+          uk += (double)Dl[nb + (size_t)Jp];
+          uh += (double)Dl[nb + 3 * (size_t)Jp];
+        }
+      } else {
+        uk = inc[gm * 2 + 0];
+        uh = inc[gm * 2 + 1];
+      }
+      r0 = fma(mu[m], uk, r0);
+      r2 = fma(mu[m], uh, r2);
+    } else {  // mu < 0: upstream L corner of cell j+1 into rows 1, 3
+      double uk, uh;
+      if (j < J - 1) {
+        const size_t nb = base + 1;
+        uk = Pin[nb];
+        uh = Pin[nb + 2 * (size_t)Jp];
+        if (apply) {
+          uk += (double)Dl[nb];
+          uh += (double)Dl[nb + 2 * (size_t)Jp];
+        }
+      } else {
+        uk = inc[(G * N + gm) * 2 + 0];
+        uh = inc[(G * N + gm) * 2 + 1];
+      }
+      r1 = fma(-mu[m], uk, r1);
+      r3 = fma(-mu[m], uh, r3);
+    }
+    // r -= L_c Psi  (rows of Eq. Aj)
+    r0 = fma(-a, v0, fma(-hm, v1, fma(-ha, v2, r0)));
+    r1 = fma(hm, v0, fma(-a, v1, fma(-ha, v3, r1)));
+    r2 = fma(al, v0, fma(-aa, v2, fma(-hm, v3, r2)));
+    r3 = fma(al, v1, fma(hm, v2, fma(-aa, v3, r3)));
+    const float f0 = (float)r0, f1 = (float)r1, f2 = (float)r2, f3 = (float)r3;
+    const float *Li = Linv32 + ((size_t)tau * G * N + gm) * 16;
+#pragma unroll
+    for (int p = 0; p < 4; p++)
+      z32[base + (size_t)p * Jp] = fmaf(Li[p * 4 + 3], f3, fmaf(Li[p * 4 + 2], f2, fmaf(Li[p * 4 + 1], f1, Li[p * 4 + 0] * f0)));
+  }
+}
+
+// ---------------------------------------------------------------- control
+__global__ void __launch_bounds__(kFinalizeThreads) k_mx_finalize(const double *__restrict__ partials, int n,
+                                                                    DevState *ds, double *e_hist,
+                                                                    cudaGraphConditionalHandle cond, int use_cond) {
+  __shared__ double sh[kFinalizeThreads];
+  if (ds->done) {
+    if (threadIdx.x == 0 && use_cond) cudaGraphSetConditional(cond, 0);
+    return;
+  }
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += kFinalizeThreads) s += partials[i];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = kFinalizeThreads / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x != 0) return;
+  // settle the refinement made by the previous body's outer kernel
+  if (ds->refine) {
+    ds->cur ^= 1;
+    ds->refine = 0;
+    ds->blk_i = 0;
+  }
+  const double e = sqrt(sh[0]);
+  const int l = ds->l;
+  if (e_hist && l < ds->max_iter) e_hist[l] = e;
+  double rho = 0.0;
+  int conv = 0;
+  if (!isfinite(e)) {
+    ds->status = OCI_E_NONFINITE;
+    ds->done = 1;
+  } else {
+    if (l >= 1 && ds->e_prev > 0.0) rho = e / ds->e_prev;
+    if (!ds->fixed) {
+      if (e == 0.0) conv = 1;
+      else if (l >= 1) conv = e < ds->tol * (1.0 - rho);
+    }
+  }
+  ds->e = e;
+  ds->rho = rho;
+  ds->e_prev = e;
+  ds->l = l + 1;
+  ds->dcur ^= 1;
+  ds->blk_i += 1;
+  if (ds->blk_i == 1) ds->e_blk0 = e;
+  if (!ds->fixed && !ds->done) {
+    if (conv) {
+      ds->status = OCI_OK;
+      ds->done = 1;
+    } else if (l + 1 >= ds->max_iter) {
+      ds->status = OCI_E_NOCONV;
+      ds->done = 1;
+    }
+  }
+  const int refine = ds->done || ds->blk_i >= ds->k_max || e < ds->theta * ds->e_blk0;
+  ds->refine = refine;
+  if (refine) ds->n_refine += 1;
+  if (use_cond && ds->done) cudaGraphSetConditional(cond, 0);
+}
+
+// kind 0: settle a pending refinement (flip Psi, zero correction)
+// kind 1: after an apply-only outer kernel (mode 2), flip Psi
+__global__ void k_mx_settle(DevState *ds, int kind) {
+  if (kind == 0) {
+    if (ds->refine) {
+      ds->cur ^= 1;
+      ds->refine = 0;
+      ds->blk_i = 0;
+    }
+  } else if (ds->blk_i > 0) {
+    ds->cur ^= 1;
+    ds->blk_i = 0;
+  }
+}
+
+static size_t mx_inner_smem(const Handle &h, int cb) { return (size_t)cb * h.G * (h.N * 4 + 4) * sizeof(float); }
+
+static int mx_cb(const Handle &h) {
+  int cb = 128;
+  while (cb > 1 && ((size_t)cb * h.G > 256 || mx_inner_smem(h, cb) > 96 * 1024)) cb /= 2;
+  return cb;
+}
+
+int mx_partials(const Handle &h) { return (h.J + mx_cb(h) - 1) / mx_cb(h); }
+
+void launch_mx_inner(Handle &h) {
+  const int cb = mx_cb(h);
+  dim3 block(cb, h.G);
+  k_mx_inner<<<(h.J + cb - 1) / cb, block, mx_inner_smem(h, cb), h.stream>>>(
+      h.J, h.Jp, h.N, h.G, h.type, h.tt.Linv32, h.tt.Cin32, h.tt.Mp32, h.w32, h.z32, h.delta[0], h.delta[1], h.ds,
+      h.partials);
+}
+
+void launch_mx_outer(Handle &h, int mode) {
+  int cb = 128;
+  while (cb > 1 && cb * h.G > 256) cb /= 2;
+  dim3 block(cb, h.G);
+  const size_t smem = (size_t)cb * h.G * 4 * sizeof(double);
+  k_mx_outer<<<(h.J + cb - 1) / cb, block, smem, h.stream>>>(h.J, h.Jp, h.N, h.G, h.type, h.tt.Lco, h.tt.Kap,
+                                                             h.tt.Linv32, h.w, h.mu, h.inc, h.tc, h.Psi[0], h.Psi[1],
+                                                             h.delta[0], h.delta[1], h.ds, mode, h.z32);
+}
+
+void launch_mx_finalize(Handle &h, cudaGraphConditionalHandle cond, int use_cond) {
+  k_mx_finalize<<<1, kFinalizeThreads, 0, h.stream>>>(h.partials, mx_partials(h), h.ds, h.e_hist, cond, use_cond);
+}
+
+void launch_mx_settle(Handle &h, int kind) { k_mx_settle<<<1, 1, 0, h.stream>>>(h.ds, kind); }
+
+const void *k_mx_inner_ptr() { return (const void *)k_mx_inner; }
+
+}  // namespace oci

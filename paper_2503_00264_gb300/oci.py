@@ -19,7 +19,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "liboci.so")
 
 OK, E_INVAL, E_NOMEM, E_CUDA, E_NOCONV, E_SINGULAR, E_NONFINITE, E_TIMEOUT, E_STATE = 0, -1, -2, -3, -4, -5, -6, -7, -8
-FP64, TF32_IR, BF16X3_IR = 0, 1, 2
+FP64, TF32_IR, BF16X3_IR, FP32_IR = 0, 1, 2, 3
 GUESS_PREV, GUESS_ZERO = 0, 1
 SOLVER_AUTO, SOLVER_STRUCTURED, SOLVER_DENSE_LU = 0, 1, 2
 

@@ -1,0 +1,72 @@
+"""Mixed-precision form (FP32 inner sweeps on the correction, FP64 refinement)
+against the FP64 oracle: scalar and angular flux within 1e-10 relative, balance
+tallies within 1e-10 of their magnitude, sweep counts within 2 of the FP64 ones."""
+import numpy as np
+import pytest
+
+from oracle import OCI, Oracle
+from paper_2503_00264_gb300 import oci
+from paper_2503_00264_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+CASES = [(21, 1, 4, 1), (22, 40, 8, 1), (23, 129, 16, 1), (24, 50, 8, 2), (25, 33, 4, 3)]
+
+
+@pytest.mark.parametrize("seed,J,N,G", CASES)
+def test_fp32_ir_matches_fp64_oracle(seed, J, N, G):
+    p = W.random_slab(seed, J, N, G).replace(tol=1e-11)
+    o = Oracle(p)
+    with oci.Solver(p, precision=oci.FP32_IR) as s:
+        for k in range(3):
+            r = o.step(OCI)
+            st = s.step()
+            assert st["status"] == 0
+            assert abs(st["iters"] - r["iters"]) <= 2, (k, st["iters"], r["iters"])
+            assert rel(s.phi(), r["phi"]) < 1e-10
+            assert rel(s.psi(), r["Psi"]) < 1e-10
+            assert np.abs(s.balance() - r["bal"]).max() <= 1e-10 * np.abs(r["bal"]).max()
+
+
+def test_fp32_ir_sweeps_track_fp64_history():
+    """Per-sweep e of the mixed form follows plain OCI's (Sec. 2.1 norm)."""
+    p = W.random_slab(26, 200, 16, 1)
+    guess = W.random_guess(p, 2)
+    o = Oracle(p)
+    o.Psi[...] = guess
+    e_orc = o.iterate(60)
+    with oci.Solver(p, precision=oci.FP32_IR) as s:
+        s.set_psi(guess)
+        e_mx = s.iterate(60)
+        assert rel(s.psi(), o.Psi) < 1e-9
+    keep = e_orc > 1e-6 * e_orc[0]
+    assert np.all(np.abs(e_mx - e_orc)[keep] <= 1e-5 * e_orc[keep])
+
+
+def test_fp32_ir_full_size_matches_fp64_path():
+    """2^18-cell slab, S16 (c = 0.9, tau = 0.1), two steps: mixed vs FP64 path."""
+    p = W.slab_3region(c=0.9, tau=0.1)
+    with oci.Solver(p) as a, oci.Solver(p, precision=oci.FP32_IR) as b:
+        for _ in range(2):
+            sa, sb = a.step(), b.step()
+            assert abs(sa["iters"] - sb["iters"]) <= 2
+            assert max(sb["balance_rel"]) < 1e-9
+        assert rel(b.phi(), a.phi()) < 1e-10
+        assert rel(b.psi(), a.psi()) < 1e-10
+
+
+def test_fp32_ir_noconv_keeps_last_iterate():
+    p = W.random_slab(27, 60, 8, 1, c_max=0.99).replace(tol=1e-14, max_iter=5)
+    o = Oracle(p)
+    o.iterate(5)
+    with oci.Solver(p, precision=oci.FP32_IR) as s:
+        st = s.step(allow_noconv=True)
+        assert st["status"] == oci.E_NOCONV
+        assert rel(s.psi(), o.Psi) < 1e-6
+        pp, t = s.state()
+        assert t == 0.0
