@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--J", type=int, default=2 ** 18)
     ap.add_argument("--solver", default="structured", choices=["structured", "dense"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
     return ap.parse_args()
 
 
@@ -171,6 +172,7 @@ def run_ours(args):
     solver = oci.SOLVER_DENSE_LU if args.solver == "dense" else oci.SOLVER_STRUCTURED
     peak_fp64 = oci.fp64_peak()
     s = oci.Solver(p, solver=solver, stream=stream.cuda_stream)
+    smx = None if args.no_mixed else oci.Solver(p, precision=oci.FP32_IR, stream=stream.cuda_stream)
 
     def barrier():
         if world > 1:
@@ -186,6 +188,8 @@ def run_ours(args):
 
     for _ in range(args.warmup):
         s.step()
+        if smx is not None:
+            smx.step()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clk = Clocks(local)
     barrier()
@@ -203,6 +207,51 @@ def run_ours(args):
     ms = max_over_ranks(e0.elapsed_time(e1))
     total_sweeps = sweeps * world  # replicas: every rank does the same work
     value = p.unknowns * total_sweeps / (ms * 1e-3)
+
+    mixed = None
+    if smx is not None:
+        m0, m1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        clk2 = Clocks(local)
+        barrier()
+        m0.record(stream)
+        mx_sweeps, mx_stats = 0, []
+        for _ in range(args.steps):
+            st = smx.step()
+            mx_stats.append(st)
+            mx_sweeps += st["iters"]
+        m1.record(stream)
+        barrier()
+        clk_mx = clk2.stop()
+        mx_ms = max_over_ranks(m0.elapsed_time(m1))
+        phi64, phimx = s.phi(), smx.phi()
+        psi64, psimx = s.psi(), smx.psi()
+        b64, bmx = s.balance(), smx.balance()
+        n_in = 30
+        psi_keep_mx = smx.psi()
+        q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        q0.record(stream)
+        smx.iterate(n_in)
+        q1.record(stream)
+        torch.cuda.synchronize()
+        inner_ms = q0.elapsed_time(q1) / n_in
+        smx.set_psi(psi_keep_mx)
+        NGm = p.N * p.G
+        mixed = {"precision": "FP32_IR (FP32 structured inner sweeps on the correction, FP64 residual / norm "
+                              "accumulation / balance / carry)",
+                 "value": p.unknowns * mx_sweeps * world / (mx_ms * 1e-3), "unit": UNIT,
+                 "ms_per_step": mx_ms / args.steps, "sweeps_per_step": mx_sweeps / args.steps,
+                 "sweeps_per_step_fp64": sweeps / args.steps,
+                 "speedup_vs_fp64": (ms / args.steps) / (mx_ms / args.steps),
+                 "err_vs_fp64": {"phi_rel": float(np.abs(phimx - phi64).max() / np.abs(phi64).max()),
+                                 "psi_rel": float(np.abs(psimx - psi64).max() / np.abs(psi64).max()),
+                                 "balance_rel": float(np.abs(bmx - b64).max() / np.abs(b64).max()),
+                                 "iters_diff_total": int(mx_sweeps - sweeps)},
+                 "iterate_us_per_sweep_incl_refinement": inner_ms * 1e3,
+                 "inner_bytes_per_cell": 48 * NGm + 4,
+                 "inner_hbm_gbs": (48 * NGm + 4) * p.J / (inner_ms * 1e-3) / 1e9,
+                 "clocks": clk_mx}
+        smx.close()
 
     # dominant kernel: the fused sweep; its launch time from a run of n sweeps
     n_sw = 50
@@ -257,7 +306,8 @@ def run_ours(args):
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": p.J * p.G * p.N * 2 * 8,
                     "d2h_bytes_per_step": p.J * p.G * 4 * 8},
             "gpu_launches": launches,
-            "clocks": clocks}
+            "clocks": clocks,
+            "mixed_form": mixed}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args)
     if rank == 0:

@@ -186,6 +186,19 @@ int oci_set_boundary(oci_handle *h, const double *inc_left, const double *inc_ri
  * device); *n receives the number of valid entries. */
 int oci_get_e_hist(const oci_handle *h, double *e_hist, int32_t *n);
 
+/* Edge values for a domain-decomposed driver (Sec. 4 of the paper proposes
+ * exchanging them between subdomains every iteration): left [G][N][2] receives
+ * (Psi_kL, Psi_hL) of cell 0 -- the inflow a left neighbour needs for mu < 0 --
+ * and right [G][N][2] receives (Psi_kR, Psi_hR) of cell J-1 -- the inflow a right
+ * neighbour needs for mu > 0.  Either may be NULL; host or device memory. */
+int oci_get_edges(const oci_handle *h, double *left, double *right);
+
+/* Commit the current iterate as the converged solution of the step (scalar
+ * flux, balance tallies, psi_{k+1/2} -> psi_{k-1/2}, t += dt), for drivers that
+ * run the convergence loop themselves through oci_iterate (e.g. across ranks).
+ * st may be NULL; st->iters and st->e_last are left 0. */
+int oci_commit(oci_handle *h, oci_stats *st);
+
 /* Release the handle and its device memory.  NULL is accepted. */
 void oci_destroy(oci_handle *h);
 

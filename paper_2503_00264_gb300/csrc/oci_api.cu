@@ -159,8 +159,9 @@ static int validate(const oci_problem *p) {
     return set_error("the dense per-cell solver is FP64 only"), OCI_E_INVAL;
   if (p->solver == OCI_SOLVER_DENSE_LU && 4 * p->N * p->G > 1024)
     return set_error("the dense per-cell solver needs 4*N*G <= 1024"), OCI_E_INVAL;
-  if (p->precision == OCI_TF32_IR || p->precision == OCI_BF16X3_IR)
-    return set_error("this precision form is not built"), OCI_E_INVAL;
+  if ((p->precision == OCI_TF32_IR || p->precision == OCI_BF16X3_IR) &&
+      (4 * p->N * p->G > 128 || (4 * p->N * p->G) % 32 != 0))
+    return set_error("the tensor-core forms need 4*N*G <= 128 and a multiple of 32"), OCI_E_INVAL;
   return OCI_OK;
 }
 
@@ -278,7 +279,7 @@ static void free_handle(Handle *h) {
                   h->tt.Cin, h->tt.Mp,  h->tt.Kap,    h->tt.dx,     h->tt.sig,       h->si_z,      h->si_uin,
                   h->LU,     h->piv,    h->partials,  h->bal_partials, h->bal,       h->e_hist,    h->ds,
                   h->stage,  h->delta[0], h->delta[1], h->z32, h->w32, h->tt.Lco, h->tt.Linv32, h->tt.Cin32,
-                  h->tt.Mp32};
+                  h->tt.Mp32, h->tc_img};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (h->h_ds) cudaFreeHost(h->h_ds);
@@ -363,6 +364,7 @@ static int setup_impl(const oci_problem *p, oci_handle *h) {
   np = std::max(np, si_partials(*h));
   np = std::max(np, dense_partials(*h));
   np = std::max(np, mx_partials(*h));
+  np = std::max(np, tc_partials(*h));
   h->n_partials = np;
   CK(cudaMalloc(&h->partials, (size_t)np * 8));
   const int nblk_carry = (h->J + 31) / 32;
@@ -402,6 +404,49 @@ static int setup_impl(const oci_problem *p, oci_handle *h) {
     CK(cudaMemsetAsync(h->delta[1], 0, nPsi * 4, s));
     CK(cudaMemsetAsync(h->z32, 0, nPsi * 4, s));
     CK(cudaFuncSetAttribute(k_mx_inner_ptr(), cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    if (h->precision == OCI_TF32_IR) {
+      h->mx_theta = 2e-2;
+      h->mx_kmax = 24;
+    } else if (h->precision == OCI_BF16X3_IR) {
+      h->mx_theta = 2e-3;
+      h->mx_kmax = 48;
+    }
+    if (h->precision == OCI_TF32_IR || h->precision == OCI_BF16X3_IR) {
+      // one cell type per aligned tile of 128 cells
+      for (int j0 = 0; j0 < h->J; j0 += 128)
+        for (int j = j0; j < std::min(h->J, j0 + 128); j++)
+          if (h->h_type[j] != h->h_type[j0]) {
+            set_error("the tensor-core forms need one cell type per aligned tile of 128 cells");
+            return OCI_E_INVAL;
+          }
+      // dense A = L_c - S per type (Eqs. Aj, scatter, fullOCIlhs) and its inverse
+      const int n = 4 * h->N * h->G, T = h->tt.n_types;
+      std::vector<double> Ainv_all((size_t)T * n * n), A((size_t)n * n), Ai;
+      for (int t = 0; t < T; t++) {
+        std::fill(A.begin(), A.end(), 0.0);
+        for (int g = 0; g < h->G; g++)
+          for (int m = 0; m < h->N; m++) {
+            const double *Lc = &Lco[(((size_t)t * h->G + g) * h->N + m) * 5];
+            const double a = Lc[0], hm = Lc[1], ha = Lc[2], al = Lc[3], aa = Lc[4];
+            const double L[16] = {a, hm, ha, 0.0, -hm, a, 0.0, ha, -al, 0.0, aa, hm, 0.0, -al, -hm, aa};
+            const int r0 = (g * h->N + m) * 4;
+            for (int r = 0; r < 4; r++)
+              for (int c = 0; c < 4; c++) A[(size_t)(r0 + r) * n + r0 + c] += L[r * 4 + c];
+          }
+        for (int g = 0; g < h->G; g++)
+          for (int gp = 0; gp < h->G; gp++) {
+            const double k = Kap[((size_t)t * h->G + gp) * h->G + g];
+            for (int m = 0; m < h->N; m++)
+              for (int nn = 0; nn < h->N; nn++)
+                for (int q = 0; q < 4; q++)
+                  A[(size_t)((g * h->N + m) * 4 + q) * n + (gp * h->N + nn) * 4 + q] -= k * h->h_w[nn];
+          }
+        if (!invert(n, A, Ai)) return set_error("a cell matrix A_j is singular"), OCI_E_SINGULAR;
+        std::copy(Ai.begin(), Ai.end(), Ainv_all.begin() + (size_t)t * n * n);
+      }
+      if ((rc = tc_build_images(*h, Ainv_all))) return rc;
+      if ((rc = tc_prepare(*h))) return rc;
+    }
     const char *km = getenv("OCI_MX_KMAX");
     if (km) h->mx_kmax = std::max(1, atoi(km));
     const char *th = getenv("OCI_MX_THETA");
@@ -419,7 +464,10 @@ static void launch_body(Handle &h, bool si, cudaGraphConditionalHandle cond, int
     launch_si_sweep(h);
     launch_finalize(h, h.partials, si_partials(h), cond, use_cond);
   } else if (h.precision != OCI_FP64) {
-    launch_mx_inner(h);
+    if (h.precision == OCI_FP32_IR)
+      launch_mx_inner(h);
+    else
+      launch_tc_inner(h);
     launch_mx_finalize(h, cond, use_cond);
     launch_mx_outer(h, 1);
   } else if (h.solver == OCI_SOLVER_DENSE_LU) {
@@ -788,6 +836,44 @@ int oci_get_e_hist(const oci_handle *h, double *e_hist, int32_t *n) {
   if (e_hist && cnt > 0) {
     CK(cudaMemcpyAsync(e_hist, h->e_hist, (size_t)cnt * 8, cudaMemcpyDefault, h->stream));
     CK(cudaStreamSynchronize(h->stream));
+  }
+  return OCI_OK;
+}
+
+int oci_get_edges(const oci_handle *hc, double *left, double *right) {
+  GUARD(hc);
+  Handle &h = const_cast<oci_handle &>(*hc);
+  const int K = h.G * h.N;
+  const double *P = h.Psi[h.h_ds->cur];
+  launch_edges(h, P, h.stage);  // stage[0:2K] = left, stage[2K:4K] = right
+  CK(cudaGetLastError());
+  if (left) CK(cudaMemcpyAsync(left, h.stage, (size_t)2 * K * 8, cudaMemcpyDefault, h.stream));
+  if (right) CK(cudaMemcpyAsync(right, h.stage + 2 * K, (size_t)2 * K * 8, cudaMemcpyDefault, h.stream));
+  CK(cudaStreamSynchronize(h.stream));
+  return OCI_OK;
+}
+
+int oci_commit(oci_handle *h, oci_stats *st) {
+  GUARD(h);
+  h->h_ds->status = OCI_OK;
+  h->h_ds->done = 1;
+  CK(cudaMemcpyAsync(h->ds, h->h_ds, sizeof(DevState), cudaMemcpyHostToDevice, h->stream));
+  launch_carry(*h);
+  CK(cudaMemcpyAsync(h->h_bal, h->bal, (size_t)h->G * 10 * 8, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  CK(cudaGetLastError());
+  h->t += h->dt;
+  if (st) {
+    std::memset(st, 0, sizeof(*st));
+    st->t = h->t;
+    for (int g = 0; g < h->G; g++)
+      for (int b = 0; b < 2; b++) {
+        const double *x = h->h_bal + g * 10 + b * 5;
+        const double r = x[0] + x[1] + x[2] - x[3] - x[4];
+        const double sc = fabs(x[0]) + fabs(x[1]) + fabs(x[2]) + fabs(x[3]) + fabs(x[4]);
+        const double rel = sc > 0 ? fabs(r) / sc : 0.0;
+        if (rel > st->balance_rel[b]) st->balance_rel[b] = rel;
+      }
   }
   return OCI_OK;
 }

@@ -89,6 +89,8 @@ struct Handle {
   float *w32 = nullptr;
   int mx_kmax = 64;
   double mx_theta = 1e-3;
+  unsigned char *tc_img = nullptr;     // [T] x (A^{-1} image(s) in the tcgen05 K-major layout)
+  size_t tc_img_bytes = 0;             // bytes per type
   // SI scratch
   double *si_z = nullptr;        // [G][N][4][Jp]   Linv * d0
   double *si_uin = nullptr;      // [G][N][2][Jp]   incoming edge of every cell
@@ -131,6 +133,7 @@ void launch_carry(Handle &h);
 void launch_transpose_in(Handle &h, const double *src_abi, double *dst_soa, int P);
 void launch_transpose_out(Handle &h, const double *src_soa, double *dst_abi, int P);
 void launch_phi_out(Handle &h, double *dst_abi);
+void launch_edges(Handle &h, const double *Psi, double *out);
 // SI
 void launch_si_sweep(Handle &h);
 void launch_si_phi_from_psi(Handle &h, double *phi_dst);
@@ -139,6 +142,11 @@ void launch_mx_inner(Handle &h);
 void launch_mx_outer(Handle &h, int mode);
 void launch_mx_finalize(Handle &h, cudaGraphConditionalHandle cond, int use_cond);
 int mx_partials(const Handle &h);
+// tensor-core block apply (TF32 / BF16x3 forms)
+int tc_prepare(Handle &h);
+int tc_partials(const Handle &h);
+void launch_tc_inner(Handle &h);
+int tc_build_images(Handle &h, const std::vector<double> &Ainv);
 // dense path
 int dense_setup(Handle &h);
 void launch_dense_step_const(Handle &h);

@@ -16,8 +16,11 @@
 // A refinement happens after k_max inner sweeps, or once e < theta * (first e
 // of the block) -- by then the FP32 correction has gained about -log10(theta)
 // digits and more inner sweeps would only resolve FP32 rounding -- and at
-// convergence.  FP64 is kept for Psi, the residual, the norm accumulation, the
-// balance tallies and the carry.
+// convergence.  The stop rule is accepted only on a sweep whose correction is
+// small (first sweep after a refinement, or a block that began below tol), so
+// the committed iterate carries no more than low-precision rounding of a tiny
+// correction; this costs at most one extra sweep per step.  FP64 is kept for Psi,
+// the residual, the norm accumulation, the balance tallies and the carry.
 #include <math.h>
 
 #include "oci_internal.h"
@@ -145,7 +148,7 @@ __global__ void __launch_bounds__(256) k_mx_outer(int J, int Jp, int N, int G, c
                                                   const double *__restrict__ mu, const double *__restrict__ inc,
                                                   const double *__restrict__ cvec, double *Psi0, double *Psi1,
                                                   const float *D0, const float *D1, const DevState *__restrict__ ds,
-                                                  int mode, float *__restrict__ z32) {
+                                                  int mode, int store_r, float *__restrict__ z32) {
   extern __shared__ double smd[];
   const int CB = blockDim.x;
   const int cl = threadIdx.x, g = threadIdx.y;
@@ -240,6 +243,13 @@ __global__ void __launch_bounds__(256) k_mx_outer(int J, int Jp, int N, int G, c
     r2 = fma(al, v0, fma(-aa, v2, fma(-hm, v3, r2)));
     r3 = fma(al, v1, fma(hm, v2, fma(-aa, v3, r3)));
     const float f0 = (float)r0, f1 = (float)r1, f2 = (float)r2, f3 = (float)r3;
+    if (store_r) {  // the tensor-core inner sweep applies the dense inverse to r itself
+      z32[base] = f0;
+      z32[base + (size_t)Jp] = f1;
+      z32[base + 2 * (size_t)Jp] = f2;
+      z32[base + 3 * (size_t)Jp] = f3;
+      continue;
+    }
     const float *Li = Linv32 + ((size_t)tau * G * N + gm) * 16;
 #pragma unroll
     for (int p = 0; p < 4; p++)
@@ -293,6 +303,15 @@ __global__ void __launch_bounds__(kFinalizeThreads) k_mx_finalize(const double *
   ds->dcur ^= 1;
   ds->blk_i += 1;
   if (ds->blk_i == 1) ds->e_blk0 = e;
+  // The stop rule is accepted only where the low-precision correction is
+  // small: on the first sweep after a refinement (delta = A~^{-1} r from a fresh
+  // FP64 residual) or in a block that began below tol.  Otherwise refine first
+  // and test the next sweep again.
+  int verify = 0;
+  if (conv && !(ds->blk_i == 1 || ds->e_blk0 <= ds->tol)) {
+    conv = 0;
+    verify = 1;
+  }
   if (!ds->fixed && !ds->done) {
     if (conv) {
       ds->status = OCI_OK;
@@ -302,7 +321,7 @@ __global__ void __launch_bounds__(kFinalizeThreads) k_mx_finalize(const double *
       ds->done = 1;
     }
   }
-  const int refine = ds->done || ds->blk_i >= ds->k_max || e < ds->theta * ds->e_blk0;
+  const int refine = ds->done || verify || ds->blk_i >= ds->k_max || e < ds->theta * ds->e_blk0;
   ds->refine = refine;
   if (refine) ds->n_refine += 1;
   if (use_cond && ds->done) cudaGraphSetConditional(cond, 0);
@@ -331,7 +350,10 @@ static int mx_cb(const Handle &h) {
   return cb;
 }
 
-int mx_partials(const Handle &h) { return (h.J + mx_cb(h) - 1) / mx_cb(h); }
+int tc_partials(const Handle &h);
+int mx_partials(const Handle &h) {
+  return h.precision == OCI_FP32_IR ? (h.J + mx_cb(h) - 1) / mx_cb(h) : tc_partials(h);
+}
 
 void launch_mx_inner(Handle &h) {
   const int cb = mx_cb(h);
@@ -348,7 +370,8 @@ void launch_mx_outer(Handle &h, int mode) {
   const size_t smem = (size_t)cb * h.G * 4 * sizeof(double);
   k_mx_outer<<<(h.J + cb - 1) / cb, block, smem, h.stream>>>(h.J, h.Jp, h.N, h.G, h.type, h.tt.Lco, h.tt.Kap,
                                                              h.tt.Linv32, h.w, h.mu, h.inc, h.tc, h.Psi[0], h.Psi[1],
-                                                             h.delta[0], h.delta[1], h.ds, mode, h.z32);
+                                                             h.delta[0], h.delta[1], h.ds, mode,
+                                                             h.precision != OCI_FP32_IR, h.z32);
 }
 
 void launch_mx_finalize(Handle &h, cudaGraphConditionalHandle cond, int use_cond) {

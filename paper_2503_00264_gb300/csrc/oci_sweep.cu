@@ -429,4 +429,21 @@ void launch_transpose_out(Handle &h, const double *src_soa, double *dst_abi, int
 
 void launch_phi_out(Handle &h, double *dst_abi) { launch_transpose_out(h, h.phi, dst_abi, h.G * 4); }
 
+// out[0:2K]  = (Psi_kL, Psi_hL) of cell 0 per (g,m);
+// out[2K:4K] = (Psi_kR, Psi_hR) of cell J-1 per (g,m); K = G*N.
+__global__ void k_edges(int J, int Jp, int K, const double *__restrict__ P, double *__restrict__ out) {
+  const int gm = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gm >= K) return;
+  const size_t b = (size_t)gm * 4 * Jp;
+  out[gm * 2 + 0] = P[b + 0 * (size_t)Jp];
+  out[gm * 2 + 1] = P[b + 2 * (size_t)Jp];
+  out[2 * K + gm * 2 + 0] = P[b + 1 * (size_t)Jp + (J - 1)];
+  out[2 * K + gm * 2 + 1] = P[b + 3 * (size_t)Jp + (J - 1)];
+}
+
+void launch_edges(Handle &h, const double *Psi, double *out) {
+  const int K = h.G * h.N;
+  k_edges<<<(K + 127) / 128, 128, 0, h.stream>>>(h.J, h.Jp, K, Psi, out);
+}
+
 }  // namespace oci

@@ -1,0 +1,113 @@
+"""Spatial domain decomposition of one OCI time step across ranks.
+
+Block-Jacobi OCI (Eq. oci) lags all inflow to a cell, so a slab split into
+contiguous cell ranges needs, per sweep, only the lagged edge values at each
+interface (the paper's Sec. 4 outlook: subdomains exchanging every iteration):
+  - rank r receives (Psi_kR, Psi_hR) of the last cell of rank r-1 as its
+    incident flux for mu > 0, and (Psi_kL, Psi_hL) of the first cell of rank r+1
+    as its incident flux for mu < 0 (2NG values per side per sweep);
+  - the squared norms of the ranks' sweeps are summed (one allreduce) and the
+    stop rule of Sec. 2.1 is applied to e = sqrt(sum) on every rank.
+The iterates are those of single-domain OCI; only the summation order of e
+changes.  The local solver is any object with edges(), set_boundary(l, r),
+iterate(1) and commit() -- the GPU `oci.Solver`, or a CPU stand-in in tests.
+"""
+from __future__ import annotations
+
+import datetime
+import math
+from typing import Optional
+
+import numpy as np
+
+from . import workloads as W
+
+
+def split_cells(J: int, world: int):
+    """Contiguous cell ranges [starts[r], starts[r+1]) of near-equal size."""
+    base, rem = divmod(J, world)
+    return [r * base + min(r, rem) for r in range(world + 1)]
+
+
+def subproblem(prob: W.Problem, a: int, b: int) -> W.Problem:
+    """Cells [a, b) of `prob`; the incident fluxes of interior interfaces are set
+    each sweep by the exchange."""
+    sl = slice(a, b)
+    return prob.replace(J=b - a, dx=prob.dx[sl].copy(), mat=prob.mat[sl].copy(),
+                        Q=None if prob.Q is None else prob.Q[sl].copy(),
+                        psi_init=None if prob.psi_init is None else prob.psi_init[sl].copy(),
+                        name=f"{prob.name}[{a}:{b}]")
+
+
+class RankFailure(RuntimeError):
+    """A neighbour did not take part in an exchange within the timeout."""
+
+
+class HaloExchange:
+    """Edge exchange and norm allreduce over torch.distributed (gloo or NCCL)."""
+
+    def __init__(self, rank: int, world: int, G: int, N: int, device: str = "cpu"):
+        import torch
+        self.torch = torch
+        self.rank, self.world, self.G, self.N = rank, world, G, N
+        self.device = device
+
+    def exchange(self, left_edge: np.ndarray, right_edge: np.ndarray):
+        """Send my first cell's L values left and my last cell's R values right;
+        return (inflow from the left neighbour, inflow from the right neighbour),
+        None at the slab ends."""
+        import torch.distributed as dist
+        t = self.torch
+        ops, recv_l, recv_r = [], None, None
+        if self.rank > 0:
+            recv_l = t.empty((self.G, self.N, 2), dtype=t.float64, device=self.device)
+            ops.append(dist.P2POp(dist.irecv, recv_l, self.rank - 1))
+            ops.append(dist.P2POp(dist.isend, t.as_tensor(left_edge, device=self.device), self.rank - 1))
+        if self.rank < self.world - 1:
+            recv_r = t.empty((self.G, self.N, 2), dtype=t.float64, device=self.device)
+            ops.append(dist.P2POp(dist.irecv, recv_r, self.rank + 1))
+            ops.append(dist.P2POp(dist.isend, t.as_tensor(right_edge, device=self.device), self.rank + 1))
+        try:
+            if ops:
+                for r in dist.batch_isend_irecv(ops):
+                    r.wait()
+        except RuntimeError as e:  # gloo/NCCL timeout or a peer that left
+            raise RankFailure(f"rank {self.rank}: edge exchange failed: {e}") from e
+        return (None if recv_l is None else recv_l.cpu().numpy(),
+                None if recv_r is None else recv_r.cpu().numpy())
+
+    def allreduce_sum(self, x: float) -> float:
+        import torch.distributed as dist
+        v = self.torch.tensor([x], dtype=self.torch.float64, device=self.device)
+        try:
+            dist.all_reduce(v, op=dist.ReduceOp.SUM)
+        except RuntimeError as e:
+            raise RankFailure(f"rank {self.rank}: norm allreduce failed: {e}") from e
+        return float(v.item())
+
+
+def step(local, halo: HaloExchange, inc_left: Optional[np.ndarray], inc_right: Optional[np.ndarray],
+         tol: float, max_iter: int) -> dict:
+    """One time step of OCI over all ranks; returns dict(status, iters, e, rho)."""
+    e_prev, rho = 0.0, 0.0
+    for l in range(max_iter):
+        left, right = local.edges()
+        from_left, from_right = halo.exchange(left, right)
+        local.set_boundary(inc_left if from_left is None else from_left,
+                           inc_right if from_right is None else from_right)
+        e_loc = float(local.iterate(1)[0])
+        e = math.sqrt(halo.allreduce_sum(e_loc * e_loc))
+        if not math.isfinite(e):
+            return dict(status=-6, iters=l + 1, e=e, rho=rho)
+        rho = e / e_prev if (l >= 1 and e_prev > 0) else 0.0
+        conv = e == 0.0 or (l >= 1 and e < tol * (1.0 - rho))
+        e_prev = e
+        if conv:
+            local.commit()
+            return dict(status=0, iters=l + 1, e=e, rho=rho)
+    return dict(status=-4, iters=max_iter, e=e_prev, rho=rho)
+
+
+def init_process_group(backend: str, timeout_s: float = 60.0):
+    import torch.distributed as dist
+    dist.init_process_group(backend=backend, timeout=datetime.timedelta(seconds=timeout_s))

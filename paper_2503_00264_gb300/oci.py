@@ -25,7 +25,8 @@ SOLVER_AUTO, SOLVER_STRUCTURED, SOLVER_DENSE_LU = 0, 1, 2
 
 EXPORTS = ["oci_setup", "oci_step", "oci_solve_transient", "si_sweep", "oci_iterate", "si_iterate",
            "oci_get_psi", "oci_set_psi", "oci_get_phi", "oci_get_state", "oci_set_state", "oci_get_balance",
-           "oci_set_boundary", "oci_get_e_hist", "oci_destroy", "oci_last_error", "oci_probe_fp64_peak"]
+           "oci_set_boundary", "oci_get_e_hist", "oci_get_edges", "oci_commit", "oci_destroy", "oci_last_error",
+           "oci_probe_fp64_peak"]
 
 
 class OCIError(RuntimeError):
@@ -79,6 +80,8 @@ def load(path: Optional[str] = None):
     L.oci_set_state.argtypes = [vp, vp, dbl]
     L.oci_set_boundary.argtypes = [vp, vp, vp]
     L.oci_get_e_hist.argtypes = [vp, vp, ctypes.POINTER(i32)]
+    L.oci_get_edges.argtypes = [vp, vp, vp]
+    L.oci_commit.argtypes = [vp, ctypes.POINTER(Stats)]
     L.oci_destroy.argtypes = [vp]
     L.oci_destroy.restype = None
     L.oci_last_error.restype = ctypes.c_char_p
@@ -218,6 +221,17 @@ class Solver:
         out = np.zeros(max(n.value, 1))
         _check(self.L.oci_get_e_hist(self.h, _ptr(out, writable=True), ctypes.byref(n)))
         return out[: n.value]
+
+    def edges(self):
+        left = np.zeros((self.G, self.N, 2))
+        right = np.zeros((self.G, self.N, 2))
+        _check(self.L.oci_get_edges(self.h, _ptr(left, writable=True), _ptr(right, writable=True)))
+        return left, right
+
+    def commit(self) -> dict:
+        st = Stats()
+        _check(self.L.oci_commit(self.h, ctypes.byref(st)))
+        return st.as_dict()
 
     def close(self):
         if getattr(self, "h", None):

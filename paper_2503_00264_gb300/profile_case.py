@@ -39,14 +39,24 @@ def main():
     ap.add_argument("--sweeps", type=int, default=3)
     ap.add_argument("--solver", default="structured", choices=["structured", "dense"])
     ap.add_argument("--si", action="store_true")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "tf32", "bf16x3"])
+    ap.add_argument("--steps", type=int, default=0, help="run full time steps instead of --sweeps sweeps")
     a = ap.parse_args()
     import torch
     p = make(a.case, a.J)
     solver = oci.SOLVER_DENSE_LU if a.solver == "dense" else oci.SOLVER_STRUCTURED
     stream = torch.cuda.Stream()
-    with oci.Solver(p, solver=solver, stream=stream.cuda_stream) as s:
-        s.set_psi(W.random_guess(p, 1))
+    prec = {"fp64": oci.FP64, "fp32": oci.FP32_IR, "tf32": oci.TF32_IR, "bf16x3": oci.BF16X3_IR}[a.precision]
+    with oci.Solver(p, solver=solver, precision=prec, stream=stream.cuda_stream) as s:
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if a.steps:
+            e0.record(stream)
+            its = sum((s.si_step() if a.si else s.step())["iters"] for _ in range(a.steps))
+            e1.record(stream)
+            torch.cuda.synchronize()
+            print(f"{p.name}: {a.steps} steps, {its} sweeps, {e0.elapsed_time(e1) / a.steps:.2f} ms/step")
+            return
+        s.set_psi(W.random_guess(p, 1))
         e0.record(stream)
         (s.si_iterate if a.si else s.iterate)(a.sweeps)
         e1.record(stream)
