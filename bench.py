@@ -31,6 +31,9 @@ from paper_2503_00264_gb300 import workloads as W  # noqa: E402
 METRIC = "OCI cell-unknown updates/s"
 UNIT = "updates/s"
 SAMPLE_J = 3072
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_oci_sweep launch on this workload
+# (2^18 cells, S16, G = 1), from the ncu --set full capture summarised in profiles/.
+SWEEP_DRAM_BYTES_NCU = 273.335552e6 + 100.828416e6
 
 
 def parse():
@@ -45,6 +48,7 @@ def parse():
     ap.add_argument("--solver", default="structured", choices=["structured", "dense"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-si", action="store_true")
     return ap.parse_args()
 
 
@@ -253,6 +257,29 @@ def run_ours(args):
                  "clocks": clk_mx}
         smx.close()
 
+    # seconds per converged time step: OCI (FP64 and mixed) against GPU SI
+    si_cmp = None
+    if not args.no_si:
+        si_cmp = []
+        for tau in (0.01, 0.1):
+            q = W.slab_3region(c=args.c, tau=tau, J=args.J)
+            row = {"tau": tau}
+            for name, kw, si in (("oci_fp64", {}, False), ("oci_fp32ir", {"precision": oci.FP32_IR}, False),
+                                 ("si_fp64", {}, True)):
+                with oci.Solver(q, stream=stream.cuda_stream, **kw) as sv:
+                    (sv.si_step if si else sv.step)()  # warm step (builds graphs, touches memory)
+                    t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    nst, its = 2, 0
+                    t0e.record(stream)
+                    for _ in range(nst):
+                        its += (sv.si_step if si else sv.step)()["iters"]
+                    t1e.record(stream)
+                    torch.cuda.synchronize()
+                    row[name] = {"s_per_step": t0e.elapsed_time(t1e) / nst / 1e3, "sweeps_per_step": its / nst}
+            row["oci_fp64_speedup_vs_si"] = row["si_fp64"]["s_per_step"] / row["oci_fp64"]["s_per_step"]
+            row["oci_fp32ir_speedup_vs_si"] = row["si_fp64"]["s_per_step"] / row["oci_fp32ir"]["s_per_step"]
+            si_cmp.append(row)
+
     # dominant kernel: the fused sweep; its launch time from a run of n sweeps
     n_sw = 50
     psi_keep = s.psi()
@@ -297,7 +324,10 @@ def run_ours(args):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config(args, p),
             "sweeps_per_step": sweeps / args.steps,
             "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": peak_fp64 / 1e12, "unit": "TFLOP/s",
-                         "frac": achieved_tf * 1e12 / peak_fp64, "traffic": None,
+                         "frac": achieved_tf * 1e12 / peak_fp64,
+                         "traffic": SWEEP_DRAM_BYTES_NCU if (p.J == 2 ** 18 and p.N == 16 and p.G == 1) else None,
+                         "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
+                         "algorithmic_bytes": bytes_cell * p.J,
                          "kernel": "k_oci_sweep (FP64 structured cell solve)",
                          "peak_source": "measured live: register-only DFMA loop (oci_probe_fp64_peak)",
                          "hbm_achieved_gbs": hbm_gbs, "hbm_peak_gbs": peaks.get("hbm_gbs"),
@@ -307,7 +337,8 @@ def run_ours(args):
                     "d2h_bytes_per_step": p.J * p.G * 4 * 8},
             "gpu_launches": launches,
             "clocks": clocks,
-            "mixed_form": mixed}
+            "mixed_form": mixed,
+            "si_comparison": si_cmp}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args)
     if rank == 0:
