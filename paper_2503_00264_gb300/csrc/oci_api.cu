@@ -271,6 +271,84 @@ static int dev_upload(T **dst, const T *src, size_t n, cudaStream_t s) {
 
 static int build_graph(Handle &h, bool si, cudaGraphExec_t *out);
 
+// ---------------------------------------------------------------- autotuner
+// Launch shape of the sweep kernel (cells per block CB, angle chunks P per cell
+// and group): every legal shape -- CB*G*P threads in [32, 256], P | N, shared
+// memory <= 100 KB -- is timed over a few sweeps of this problem (CUDA events),
+// and the fastest is kept for the graphs.  State is zeroed afterwards.
+// OCI_AUTOTUNE=0 keeps the default shape.
+static int autotune(Handle &h) {
+  const char *at = getenv("OCI_AUTOTUNE");
+  if (at && at[0] == '0') return OCI_OK;
+  const bool mx = h.precision == OCI_FP32_IR;
+  if (h.solver == OCI_SOLVER_DENSE_LU || (h.precision != OCI_FP64 && !mx)) return OCI_OK;
+  const size_t es = mx ? 4 : 8;
+  std::vector<std::pair<int, int>> cands;
+  for (int cb : {32, 64, 128, 256})
+    for (int P : {1, 2, 4, 8}) {
+      if (h.N % P) continue;
+      const int thr = cb * h.G * P;
+      if (thr < 32 || thr > 256) continue;
+      if (sweep_smem(h.N, h.G, cb, P, es) > 100 * 1024) continue;
+      cands.emplace_back(cb, P);
+    }
+  if (cands.size() < 2) return OCI_OK;
+  DevState &d = *h.h_ds;
+  d.done = 0;
+  d.fixed = 1;
+  d.refine = 0;
+  d.blk_i = 1;
+  d.cur = 0;
+  d.dcur = 0;
+  CK(cudaMemcpyAsync(h.ds, h.h_ds, sizeof(DevState), cudaMemcpyHostToDevice, h.stream));
+  float best = 1e30f;
+  int bcb = 0, bP = 0;
+  const int reps = 3;
+  for (auto &c : cands) {
+    if (mx) {
+      h.mx_cb = c.first;
+      h.mx_P = c.second;
+      launch_mx_inner(h);
+    } else {
+      h.tune_cb = c.first;
+      h.tune_P = c.second;
+      launch_oci_sweep(h);
+    }
+    CK(cudaEventRecord(h.ev0, h.stream));
+    for (int r = 0; r < reps; r++) mx ? launch_mx_inner(h) : launch_oci_sweep(h);
+    CK(cudaEventRecord(h.ev1, h.stream));
+    CK(cudaEventSynchronize(h.ev1));
+    CK(cudaGetLastError());
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, h.ev0, h.ev1);
+    if (ms < best) {
+      best = ms;
+      bcb = c.first;
+      bP = c.second;
+    }
+  }
+  if (mx) {
+    h.mx_cb = bcb;
+    h.mx_P = bP;
+  } else {
+    h.tune_cb = bcb;
+    h.tune_P = bP;
+  }
+  h.tune_us = 1e3 * best / reps;
+  const size_t nPsi = (size_t)h.G * h.N * 4 * h.Jp;
+  CK(cudaMemsetAsync(h.Psi[0], 0, nPsi * 8, h.stream));
+  CK(cudaMemsetAsync(h.Psi[1], 0, nPsi * 8, h.stream));
+  if (mx) {
+    CK(cudaMemsetAsync(h.delta[0], 0, nPsi * 4, h.stream));
+    CK(cudaMemsetAsync(h.delta[1], 0, nPsi * 4, h.stream));
+  }
+  std::memset(h.h_ds, 0, sizeof(DevState));
+  h.h_ds->done = 1;
+  CK(cudaMemcpyAsync(h.ds, h.h_ds, sizeof(DevState), cudaMemcpyHostToDevice, h.stream));
+  CK(cudaStreamSynchronize(h.stream));
+  return OCI_OK;
+}
+
 static void free_handle(Handle *h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
@@ -365,6 +443,7 @@ static int setup_impl(const oci_problem *p, oci_handle *h) {
   np = std::max(np, dense_partials(*h));
   np = std::max(np, mx_partials(*h));
   np = std::max(np, tc_partials(*h));
+  np = std::max(np, h->J + 64);  // any sweep shape down to one cell per block
   h->n_partials = np;
   CK(cudaMalloc(&h->partials, (size_t)np * 8));
   const int nblk_carry = (h->J + 31) / 32;
@@ -452,6 +531,7 @@ static int setup_impl(const oci_problem *p, oci_handle *h) {
     const char *th = getenv("OCI_MX_THETA");
     if (th) h->mx_theta = atof(th);
   }
+  if ((rc = autotune(*h))) return rc;
   if ((rc = build_graph(*h, false, &h->g_oci))) return rc;
   CK(cudaStreamSynchronize(s));
   CK(cudaGetLastError());

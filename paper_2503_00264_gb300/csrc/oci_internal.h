@@ -114,15 +114,20 @@ struct Handle {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   int last_iters = 0;
   bool no_graph = false;           // OCI_NO_GRAPH=1: host-driven loop instead of the WHILE graph
+  int tune_cb = 0, tune_P = 0;     // sweep launch shape picked by the autotuner (0: default)
+  int mx_cb = 0, mx_P = 0;         // same for the FP32 inner sweep of the mixed form
+  double tune_us = 0.0;            // measured sweep time of the chosen shape
 };
 
 // ---------------------------------------------------------------- launches
 struct SweepCfg {
   int cells_per_block;
+  int chunks;  // angle chunks per (cell, group): threads per cell and group
   int grid;
   size_t smem;
 };
 SweepCfg sweep_config(const Handle &h);
+size_t sweep_smem(int N, int G, int cb, int P, size_t es);
 
 void launch_step_const(Handle &h);
 void launch_oci_sweep(Handle &h);

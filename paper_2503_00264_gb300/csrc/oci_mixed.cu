@@ -32,15 +32,18 @@ namespace oci {
 // t = z + Cin u, y = sum_m w t, s = Mp y, delta = t + Linv s, where z = A~-block
 // solve of r precomputed by the outer kernel (z = Linv r).  The correction has
 // zero incident flux at the slab ends (the boundary values live in r).
-__global__ void __launch_bounds__(256) k_mx_inner(int J, int Jp, int N, int G, const int32_t *__restrict__ type,
-                                                  const float *__restrict__ Linv, const float *__restrict__ Cin,
-                                                  const float *__restrict__ Mp, const float *__restrict__ w,
-                                                  const float *__restrict__ z, float *D0, float *D1,
-                                                  const DevState *__restrict__ ds, double *__restrict__ partials) {
+__global__ void __launch_bounds__(256) k_mx_inner(int J, int Jp, int N, int G, int P,
+                                                  const int32_t *__restrict__ type, const float *__restrict__ Linv,
+                                                  const float *__restrict__ Cin, const float *__restrict__ Mp,
+                                                  const float *__restrict__ w, const float *__restrict__ z, float *D0,
+                                                  float *D1, const DevState *__restrict__ ds,
+                                                  double *__restrict__ partials) {
   extern __shared__ float smf[];
   __shared__ double red[32];
   const int CB = blockDim.x;
-  const int cl = threadIdx.x, g = threadIdx.y;
+  const int cl = threadIdx.x, gy = threadIdx.y;
+  const int g = gy / P, ch = gy % P;
+  const int NP = N / P, m0 = ch * NP;
   const int j = blockIdx.x * CB + cl;
   if (ds->done) return;
   const bool zero = ds->refine || ds->blk_i == 0;
@@ -56,7 +59,7 @@ __global__ void __launch_bounds__(256) k_mx_inner(int J, int Jp, int N, int G, c
   float y0 = 0.f, y1 = 0.f, y2 = 0.f, y3 = 0.f;
   if (active) {
 #pragma unroll 4
-    for (int m = 0; m < N; m++) {
+    for (int m = m0; m < m0 + NP; m++) {
       const int gm = g * N + m;
       const size_t base = (size_t)gm * 4 * Jp + j;
       float uk = 0.f, uh = 0.f;
@@ -87,7 +90,7 @@ __global__ void __launch_bounds__(256) k_mx_inner(int J, int Jp, int N, int G, c
       y2 = fmaf(wm, t2, y2);
       y3 = fmaf(wm, t3, y3);
     }
-    float *ys = y_s + (size_t)(g * 4) * CB + cl;
+    float *ys = y_s + (size_t)(gy * 4) * CB + cl;
     ys[0] = y0;
     ys[CB] = y1;
     ys[2 * CB] = y2;
@@ -100,14 +103,16 @@ __global__ void __launch_bounds__(256) k_mx_inner(int J, int Jp, int N, int G, c
     const float *M = Mp + (size_t)tau * G4 * G4 + (size_t)(g * 4) * G4;
     float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
     for (int k = 0; k < G4; k++) {
-      const float yk = y_s[(size_t)k * CB + cl];
+      const int gp = k >> 2, q = k & 3;
+      float yk = y_s[(size_t)((gp * P) * 4 + q) * CB + cl];
+      for (int c = 1; c < P; c++) yk += y_s[(size_t)((gp * P + c) * 4 + q) * CB + cl];
       s0 = fmaf(M[k], yk, s0);
       s1 = fmaf(M[G4 + k], yk, s1);
       s2 = fmaf(M[2 * G4 + k], yk, s2);
       s3 = fmaf(M[3 * G4 + k], yk, s3);
     }
 #pragma unroll 4
-    for (int m = 0; m < N; m++) {
+    for (int m = m0; m < m0 + NP; m++) {
       const int gm = g * N + m;
       const size_t base = (size_t)gm * 4 * Jp + j;
       const float *L = Linv + (tb + gm) * 16;
@@ -124,13 +129,14 @@ __global__ void __launch_bounds__(256) k_mx_inner(int J, int Jp, int N, int G, c
   // FP64 accumulation of the per-thread FP32 partial sums
   double v = (double)e2;
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int nthr = blockDim.x * blockDim.y;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   if ((tid & 31) == 0) red[tid >> 5] = v;
   __syncthreads();
   if (tid == 0) {
     double s = 0.0;
-    for (int i = 0; i < (CB * G + 31) / 32; i++) s += red[i];
+    for (int i = 0; i < (nthr + 31) / 32; i++) s += red[i];
     partials[blockIdx.x] = s;
   }
 }
@@ -152,8 +158,7 @@ __global__ void __launch_bounds__(256) k_mx_outer(int J, int Jp, int N, int G, c
   extern __shared__ double smd[];
   const int CB = blockDim.x;
   const int cl = threadIdx.x, g = threadIdx.y;
-  const int j = blockIdx.x * CB + cl;
-  if (mode == 1 && !ds->refine) return;
+  if (mode == 1 && !ds->refine) return;  // the common case: a small grid exits at once
   if (mode == 2 && ds->blk_i == 0) return;
   const bool apply = mode != 0;
   const bool resid = mode == 0 || (mode == 1 && !ds->done);
@@ -161,99 +166,105 @@ __global__ void __launch_bounds__(256) k_mx_outer(int J, int Jp, int N, int G, c
   const double *__restrict__ Pin = cur ? Psi1 : Psi0;
   double *__restrict__ Pout = cur ? Psi0 : Psi1;
   const float *__restrict__ Dl = ds->dcur ? D1 : D0;
-  const bool active = j < J;
-  const int tau = active ? type[j] : 0;
-  double ph[4] = {0.0, 0.0, 0.0, 0.0};
-  if (active) {
+  const int N2 = N / 2;
+  const int ntiles = (J + CB - 1) / CB;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int j = tile * CB + cl;
+    const bool active = j < J;
+    const int tau = active ? type[j] : 0;
+    double ph[4] = {0.0, 0.0, 0.0, 0.0};
+    if (active) {
+      for (int m = 0; m < N; m++) {
+        const int gm = g * N + m;
+        const size_t base = (size_t)gm * 4 * Jp + j;
+        const double wm = w[m];
+#pragma unroll
+        for (int p = 0; p < 4; p++) {
+          double v = Pin[base + (size_t)p * Jp];
+          if (apply) {
+            v += (double)Dl[base + (size_t)p * Jp];
+            Pout[base + (size_t)p * Jp] = v;
+          }
+          ph[p] = fma(wm, v, ph[p]);
+        }
+      }
+    }
+    if (!resid) continue;  // uniform
+    double *ph_s = smd;    // [G*4][CB]
+    __syncthreads();       // previous tile's readers are done
+#pragma unroll
+    for (int p = 0; p < 4; p++) ph_s[(size_t)(g * 4 + p) * CB + cl] = ph[p];
+    __syncthreads();
+    if (!active) continue;
+    double s[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int gp = 0; gp < G; gp++) {
+      const double k = Kap[((size_t)tau * G + gp) * G + g];
+#pragma unroll
+      for (int p = 0; p < 4; p++) s[p] = fma(k, ph_s[(size_t)(gp * 4 + p) * CB + cl], s[p]);
+    }
+    const double *__restrict__ P = apply ? Pout : Pin;
     for (int m = 0; m < N; m++) {
       const int gm = g * N + m;
       const size_t base = (size_t)gm * 4 * Jp + j;
-      const double wm = w[m];
-#pragma unroll
-      for (int p = 0; p < 4; p++) {
-        double v = Pin[base + (size_t)p * Jp];
-        if (apply) {
-          v += (double)Dl[base + (size_t)p * Jp];
-          Pout[base + (size_t)p * Jp] = v;
+      const double v0 = P[base], v1 = P[base + (size_t)Jp], v2 = P[base + 2 * (size_t)Jp],
+                   v3 = P[base + 3 * (size_t)Jp];
+      const double *L = Lco + ((size_t)tau * G * N + gm) * 5;  // a, mu/2, alpha/2, alpha, alpha+a
+      const double a = L[0], hm = L[1], ha = L[2], al = L[3], aa = L[4];
+      double r0 = cvec[base] + s[0];
+      double r1 = cvec[base + (size_t)Jp] + s[1];
+      double r2 = cvec[base + 2 * (size_t)Jp] + s[2];
+      double r3 = cvec[base + 3 * (size_t)Jp] + s[3];
+      if (m >= N2) {  // mu > 0: upstream R corner of cell j-1 into rows 0, 2
+        double uk, uh;
+        if (j > 0) {
+          const size_t nb = base - 1;
+          uk = Pin[nb + (size_t)Jp];
+          uh = Pin[nb + 3 * (size_t)Jp];
+          if (apply) {
+            uk += (double)Dl[nb + (size_t)Jp];
+            uh += (double)Dl[nb + 3 * (size_t)Jp];
+          }
+        } else {
+          uk = inc[gm * 2 + 0];
+          uh = inc[gm * 2 + 1];
         }
-        ph[p] = fma(wm, v, ph[p]);
-      }
-    }
-  }
-  if (!resid) return;  // uniform
-  double *ph_s = smd;  // [G*4][CB]
-#pragma unroll
-  for (int p = 0; p < 4; p++) ph_s[(size_t)(g * 4 + p) * CB + cl] = ph[p];
-  __syncthreads();
-  if (!active) return;
-  double s[4] = {0.0, 0.0, 0.0, 0.0};
-  for (int gp = 0; gp < G; gp++) {
-    const double k = Kap[((size_t)tau * G + gp) * G + g];
-#pragma unroll
-    for (int p = 0; p < 4; p++) s[p] = fma(k, ph_s[(size_t)(gp * 4 + p) * CB + cl], s[p]);
-  }
-  const double *__restrict__ P = apply ? Pout : Pin;
-  const int N2 = N / 2;
-  for (int m = 0; m < N; m++) {
-    const int gm = g * N + m;
-    const size_t base = (size_t)gm * 4 * Jp + j;
-    const double v0 = P[base], v1 = P[base + (size_t)Jp], v2 = P[base + 2 * (size_t)Jp], v3 = P[base + 3 * (size_t)Jp];
-    const double *L = Lco + ((size_t)tau * G * N + gm) * 5;  // a, mu/2, alpha/2, alpha, alpha+a
-    const double a = L[0], hm = L[1], ha = L[2], al = L[3], aa = L[4];
-    double r0 = cvec[base] + s[0];
-    double r1 = cvec[base + (size_t)Jp] + s[1];
-    double r2 = cvec[base + 2 * (size_t)Jp] + s[2];
-    double r3 = cvec[base + 3 * (size_t)Jp] + s[3];
-    if (m >= N2) {  // mu > 0: upstream R corner of cell j-1 into rows 0, 2
-      double uk, uh;
-      if (j > 0) {
-        const size_t nb = base - 1;
-        uk = Pin[nb + (size_t)Jp];
-        uh = Pin[nb + 3 * (size_t)Jp];
-        if (apply) {
-          uk += (double)Dl[nb + (size_t)Jp];
-          uh += (double)Dl[nb + 3 * (size_t)Jp];
+        r0 = fma(mu[m], uk, r0);
+        r2 = fma(mu[m], uh, r2);
+      } else {  // mu < 0: upstream L corner of cell j+1 into rows 1, 3
+        double uk, uh;
+        if (j < J - 1) {
+          const size_t nb = base + 1;
+          uk = Pin[nb];
+          uh = Pin[nb + 2 * (size_t)Jp];
+          if (apply) {
+            uk += (double)Dl[nb];
+            uh += (double)Dl[nb + 2 * (size_t)Jp];
+          }
+        } else {
+          uk = inc[(G * N + gm) * 2 + 0];
+          uh = inc[(G * N + gm) * 2 + 1];
         }
-      } else {
-        uk = inc[gm * 2 + 0];
-        uh = inc[gm * 2 + 1];
+        r1 = fma(-mu[m], uk, r1);
+        r3 = fma(-mu[m], uh, r3);
       }
-      r0 = fma(mu[m], uk, r0);
-      r2 = fma(mu[m], uh, r2);
-    } else {  // mu < 0: upstream L corner of cell j+1 into rows 1, 3
-      double uk, uh;
-      if (j < J - 1) {
-        const size_t nb = base + 1;
-        uk = Pin[nb];
-        uh = Pin[nb + 2 * (size_t)Jp];
-        if (apply) {
-          uk += (double)Dl[nb];
-          uh += (double)Dl[nb + 2 * (size_t)Jp];
-        }
-      } else {
-        uk = inc[(G * N + gm) * 2 + 0];
-        uh = inc[(G * N + gm) * 2 + 1];
+      // r -= L_c Psi  (rows of Eq. Aj)
+      r0 = fma(-a, v0, fma(-hm, v1, fma(-ha, v2, r0)));
+      r1 = fma(hm, v0, fma(-a, v1, fma(-ha, v3, r1)));
+      r2 = fma(al, v0, fma(-aa, v2, fma(-hm, v3, r2)));
+      r3 = fma(al, v1, fma(hm, v2, fma(-aa, v3, r3)));
+      const float f0 = (float)r0, f1 = (float)r1, f2 = (float)r2, f3 = (float)r3;
+      if (store_r) {  // the tensor-core inner sweep applies the dense inverse to r itself
+        z32[base] = f0;
+        z32[base + (size_t)Jp] = f1;
+        z32[base + 2 * (size_t)Jp] = f2;
+        z32[base + 3 * (size_t)Jp] = f3;
+        continue;
       }
-      r1 = fma(-mu[m], uk, r1);
-      r3 = fma(-mu[m], uh, r3);
-    }
-    // r -= L_c Psi  (rows of Eq. Aj)
-    r0 = fma(-a, v0, fma(-hm, v1, fma(-ha, v2, r0)));
-    r1 = fma(hm, v0, fma(-a, v1, fma(-ha, v3, r1)));
-    r2 = fma(al, v0, fma(-aa, v2, fma(-hm, v3, r2)));
-    r3 = fma(al, v1, fma(hm, v2, fma(-aa, v3, r3)));
-    const float f0 = (float)r0, f1 = (float)r1, f2 = (float)r2, f3 = (float)r3;
-    if (store_r) {  // the tensor-core inner sweep applies the dense inverse to r itself
-      z32[base] = f0;
-      z32[base + (size_t)Jp] = f1;
-      z32[base + 2 * (size_t)Jp] = f2;
-      z32[base + 3 * (size_t)Jp] = f3;
-      continue;
-    }
-    const float *Li = Linv32 + ((size_t)tau * G * N + gm) * 16;
+      const float *Li = Linv32 + ((size_t)tau * G * N + gm) * 16;
 #pragma unroll
-    for (int p = 0; p < 4; p++)
-      z32[base + (size_t)p * Jp] = fmaf(Li[p * 4 + 3], f3, fmaf(Li[p * 4 + 2], f2, fmaf(Li[p * 4 + 1], f1, Li[p * 4 + 0] * f0)));
+      for (int p = 0; p < 4; p++)
+        z32[base + (size_t)p * Jp] = fmaf(Li[p * 4 + 3], f3, fmaf(Li[p * 4 + 2], f2, fmaf(Li[p * 4 + 1], f1, Li[p * 4 + 0] * f0)));
+    }
   }
 }
 
@@ -275,56 +286,58 @@ __global__ void __launch_bounds__(kFinalizeThreads) k_mx_finalize(const double *
     __syncthreads();
   }
   if (threadIdx.x != 0) return;
+  DevState d = *ds;  // one load of the state, one store below
   // settle the refinement made by the previous body's outer kernel
-  if (ds->refine) {
-    ds->cur ^= 1;
-    ds->refine = 0;
-    ds->blk_i = 0;
+  if (d.refine) {
+    d.cur ^= 1;
+    d.refine = 0;
+    d.blk_i = 0;
   }
   const double e = sqrt(sh[0]);
-  const int l = ds->l;
-  if (e_hist && l < ds->max_iter) e_hist[l] = e;
+  const int l = d.l;
+  if (e_hist && l < d.max_iter) e_hist[l] = e;
   double rho = 0.0;
   int conv = 0;
   if (!isfinite(e)) {
-    ds->status = OCI_E_NONFINITE;
-    ds->done = 1;
+    d.status = OCI_E_NONFINITE;
+    d.done = 1;
   } else {
-    if (l >= 1 && ds->e_prev > 0.0) rho = e / ds->e_prev;
-    if (!ds->fixed) {
+    if (l >= 1 && d.e_prev > 0.0) rho = e / d.e_prev;
+    if (!d.fixed) {
       if (e == 0.0) conv = 1;
-      else if (l >= 1) conv = e < ds->tol * (1.0 - rho);
+      else if (l >= 1) conv = e < d.tol * (1.0 - rho);
     }
   }
-  ds->e = e;
-  ds->rho = rho;
-  ds->e_prev = e;
-  ds->l = l + 1;
-  ds->dcur ^= 1;
-  ds->blk_i += 1;
-  if (ds->blk_i == 1) ds->e_blk0 = e;
+  d.e = e;
+  d.rho = rho;
+  d.e_prev = e;
+  d.l = l + 1;
+  d.dcur ^= 1;
+  d.blk_i += 1;
+  if (d.blk_i == 1) d.e_blk0 = e;
   // The stop rule is accepted only where the low-precision correction is
   // small: on the first sweep after a refinement (delta = A~^{-1} r from a fresh
   // FP64 residual) or in a block that began below tol.  Otherwise refine first
   // and test the next sweep again.
   int verify = 0;
-  if (conv && !(ds->blk_i == 1 || ds->e_blk0 <= ds->tol)) {
+  if (conv && !(d.blk_i == 1 || d.e_blk0 <= d.tol)) {
     conv = 0;
     verify = 1;
   }
-  if (!ds->fixed && !ds->done) {
+  if (!d.fixed && !d.done) {
     if (conv) {
-      ds->status = OCI_OK;
-      ds->done = 1;
-    } else if (l + 1 >= ds->max_iter) {
-      ds->status = OCI_E_NOCONV;
-      ds->done = 1;
+      d.status = OCI_OK;
+      d.done = 1;
+    } else if (l + 1 >= d.max_iter) {
+      d.status = OCI_E_NOCONV;
+      d.done = 1;
     }
   }
-  const int refine = ds->done || verify || ds->blk_i >= ds->k_max || e < ds->theta * ds->e_blk0;
-  ds->refine = refine;
-  if (refine) ds->n_refine += 1;
-  if (use_cond && ds->done) cudaGraphSetConditional(cond, 0);
+  const int refine = d.done || verify || d.blk_i >= d.k_max || e < d.theta * d.e_blk0;
+  d.refine = refine;
+  if (refine) d.n_refine += 1;
+  *ds = d;
+  if (use_cond && d.done) cudaGraphSetConditional(cond, 0);
 }
 
 // kind 0: settle a pending refinement (flip Psi, zero correction)
@@ -342,24 +355,29 @@ __global__ void k_mx_settle(DevState *ds, int kind) {
   }
 }
 
-static size_t mx_inner_smem(const Handle &h, int cb) { return (size_t)cb * h.G * (h.N * 4 + 4) * sizeof(float); }
-
-static int mx_cb(const Handle &h) {
-  int cb = 128;
-  while (cb > 1 && ((size_t)cb * h.G > 256 || mx_inner_smem(h, cb) > 96 * 1024)) cb /= 2;
-  return cb;
+static void mx_shape(const Handle &h, int &cb, int &P) {
+  cb = h.mx_cb;
+  P = h.mx_P;
+  if (cb > 0) return;
+  P = 1;
+  cb = 128;
+  while (cb > 1 && ((size_t)cb * h.G > 256 || sweep_smem(h.N, h.G, cb, 1, 4) > 96 * 1024)) cb /= 2;
 }
 
 int tc_partials(const Handle &h);
 int mx_partials(const Handle &h) {
-  return h.precision == OCI_FP32_IR ? (h.J + mx_cb(h) - 1) / mx_cb(h) : tc_partials(h);
+  if (h.precision != OCI_FP32_IR) return tc_partials(h);
+  int cb, P;
+  mx_shape(h, cb, P);
+  return (h.J + cb - 1) / cb;
 }
 
 void launch_mx_inner(Handle &h) {
-  const int cb = mx_cb(h);
-  dim3 block(cb, h.G);
-  k_mx_inner<<<(h.J + cb - 1) / cb, block, mx_inner_smem(h, cb), h.stream>>>(
-      h.J, h.Jp, h.N, h.G, h.type, h.tt.Linv32, h.tt.Cin32, h.tt.Mp32, h.w32, h.z32, h.delta[0], h.delta[1], h.ds,
+  int cb, P;
+  mx_shape(h, cb, P);
+  dim3 block(cb, h.G * P);
+  k_mx_inner<<<(h.J + cb - 1) / cb, block, sweep_smem(h.N, h.G, cb, P, 4), h.stream>>>(
+      h.J, h.Jp, h.N, h.G, P, h.type, h.tt.Linv32, h.tt.Cin32, h.tt.Mp32, h.w32, h.z32, h.delta[0], h.delta[1], h.ds,
       h.partials);
 }
 
@@ -368,7 +386,12 @@ void launch_mx_outer(Handle &h, int mode) {
   while (cb > 1 && cb * h.G > 256) cb /= 2;
   dim3 block(cb, h.G);
   const size_t smem = (size_t)cb * h.G * 4 * sizeof(double);
-  k_mx_outer<<<(h.J + cb - 1) / cb, block, smem, h.stream>>>(h.J, h.Jp, h.N, h.G, h.type, h.tt.Lco, h.tt.Kap,
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int ntiles = (h.J + cb - 1) / cb;
+  const int grid = ntiles < 4 * sms ? ntiles : 4 * sms;  // grid-stride over tiles
+  k_mx_outer<<<grid, block, smem, h.stream>>>(h.J, h.Jp, h.N, h.G, h.type, h.tt.Lco, h.tt.Kap,
                                                              h.tt.Linv32, h.w, h.mu, h.inc, h.tc, h.Psi[0], h.Psi[1],
                                                              h.delta[0], h.delta[1], h.ds, mode,
                                                              h.precision != OCI_FP32_IR, h.z32);

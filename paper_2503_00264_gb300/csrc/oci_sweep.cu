@@ -61,17 +61,20 @@ __device__ __forceinline__ double block_sum(double v, double *red) {
 }
 
 // ------------------------------------------------------------------ a2..a4
-// One OCI sweep.  Thread (cell j, group g); block = CB cells x G groups.
-// Reads Psi[cur], writes Psi[cur^1], writes this block's sum of (Psi_new - Psi_old)^2.
-// Shared memory: t [G*N*4][CB], y [G*4][CB], reduction scratch.
+// One OCI sweep.  Block = CB cells x (G groups x P angle chunks); thread
+// (cell, g, c) handles the angles m in [c N/P, (c+1) N/P) of group g.
+// Reads Psi[cur], writes Psi[cur^1] and this block's sum of (Psi_new - Psi_old)^2.
+// Shared memory: t [G*N*4][CB], partial y [G*P*4][CB], reduction scratch.
 __global__ void __launch_bounds__(256) k_oci_sweep(
-    int J, int Jp, int N, int G, const int32_t *__restrict__ type, const double *__restrict__ Linv,
+    int J, int Jp, int N, int G, int P, const int32_t *__restrict__ type, const double *__restrict__ Linv,
     const double *__restrict__ Cin, const double *__restrict__ Mp, const double *__restrict__ w,
     const double *__restrict__ inc, const double *__restrict__ tc, double *Psi0, double *Psi1,
     const DevState *__restrict__ ds, double *__restrict__ partials) {
   extern __shared__ double sm[];
   const int CB = blockDim.x;
-  const int cl = threadIdx.x, g = threadIdx.y;
+  const int cl = threadIdx.x, gy = threadIdx.y;
+  const int g = gy / P, ch = gy % P;
+  const int NP = N / P, m0 = ch * NP;
   const int j = blockIdx.x * CB + cl;
   if (ds->done) return;  // uniform across the grid
   const int cur = ds->cur;
@@ -79,7 +82,7 @@ __global__ void __launch_bounds__(256) k_oci_sweep(
   double *__restrict__ Pout = cur ? Psi0 : Psi1;
   double *t_s = sm;
   double *y_s = sm + (size_t)G * N * 4 * CB;
-  double *red = y_s + (size_t)G * 4 * CB;
+  double *red = y_s + (size_t)G * P * 4 * CB;
   const bool active = j < J;
   const int tau = active ? type[j] : 0;
   const int N2 = N / 2;
@@ -88,7 +91,7 @@ __global__ void __launch_bounds__(256) k_oci_sweep(
   double y0 = 0.0, y1 = 0.0, y2 = 0.0, y3 = 0.0;
   if (active) {
 #pragma unroll 2
-    for (int m = 0; m < N; m++) {
+    for (int m = m0; m < m0 + NP; m++) {
       const int gm = g * N + m;
       const size_t base = (size_t)gm * 4 * Jp + j;
       double uk, uh;
@@ -125,7 +128,7 @@ __global__ void __launch_bounds__(256) k_oci_sweep(
       y2 = fma(wm, t2, y2);
       y3 = fma(wm, t3, y3);
     }
-    double *ys = y_s + (size_t)(g * 4) * CB + cl;
+    double *ys = y_s + (size_t)(gy * 4) * CB + cl;
     ys[0] = y0;
     ys[CB] = y1;
     ys[2 * CB] = y2;
@@ -134,19 +137,21 @@ __global__ void __launch_bounds__(256) k_oci_sweep(
   __syncthreads();
   double e2 = 0.0;
   if (active) {
-    // s_g = sum_{gp} Mp[g][gp] y_gp
+    // s_g = sum_{gp} Mp[g][gp] y_gp,  y_gp = sum over the gp chunks (fixed order)
     const int G4 = 4 * G;
     const double *M = Mp + (size_t)tau * G4 * G4 + (size_t)(g * 4) * G4;
     double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
     for (int k = 0; k < G4; k++) {
-      const double yk = y_s[(size_t)k * CB + cl];
+      const int gp = k >> 2, q = k & 3;
+      double yk = y_s[(size_t)((gp * P) * 4 + q) * CB + cl];
+      for (int c = 1; c < P; c++) yk += y_s[(size_t)((gp * P + c) * 4 + q) * CB + cl];
       s0 = fma(M[k], yk, s0);
       s1 = fma(M[G4 + k], yk, s1);
       s2 = fma(M[2 * G4 + k], yk, s2);
       s3 = fma(M[3 * G4 + k], yk, s3);
     }
 #pragma unroll 2
-    for (int m = 0; m < N; m++) {
+    for (int m = m0; m < m0 + NP; m++) {
       const int gm = g * N + m;
       const size_t base = (size_t)gm * 4 * Jp + j;
       const double *L = Linv + (tb + gm) * 16;
@@ -169,14 +174,24 @@ __global__ void __launch_bounds__(256) k_oci_sweep(
 
 const void *k_oci_sweep_ptr() { return (const void *)k_oci_sweep; }
 
+size_t sweep_smem(int N, int G, int cb, int P, size_t es) {
+  return (size_t)cb * ((size_t)G * N * 4 + (size_t)G * P * 4) * es + 64 * sizeof(double);
+}
+
+// Default launch shape (used when the autotuner is off): the largest block of
+// cells that keeps <= 256 threads and <= 96 KB of shared memory, one chunk.
 SweepCfg sweep_config(const Handle &h) {
   SweepCfg c;
-  const size_t per_cell = (size_t)h.G * h.N * 4 * 8 + (size_t)h.G * 4 * 8;
-  int cb = 128;
-  while (cb > 1 && ((size_t)cb * h.G > 256 || (size_t)cb * per_cell > 96 * 1024)) cb /= 2;
+  int cb = h.tune_cb, P = h.tune_P;
+  if (cb <= 0) {
+    P = 1;
+    cb = 128;
+    while (cb > 1 && ((size_t)cb * h.G > 256 || sweep_smem(h.N, h.G, cb, 1, 8) > 96 * 1024)) cb /= 2;
+  }
   c.cells_per_block = cb;
+  c.chunks = P;
   c.grid = (h.J + cb - 1) / cb;
-  c.smem = (size_t)cb * per_cell + 64 * sizeof(double);
+  c.smem = sweep_smem(h.N, h.G, cb, P, 8);
   return c;
 }
 
@@ -188,9 +203,9 @@ void launch_step_const(Handle &h) {
 
 void launch_oci_sweep(Handle &h) {
   SweepCfg c = sweep_config(h);
-  dim3 block(c.cells_per_block, h.G);
-  k_oci_sweep<<<c.grid, block, c.smem, h.stream>>>(h.J, h.Jp, h.N, h.G, h.type, h.tt.Linv, h.tt.Cin, h.tt.Mp, h.w,
-                                                   h.inc, h.tc, h.Psi[0], h.Psi[1], h.ds, h.partials);
+  dim3 block(c.cells_per_block, h.G * c.chunks);
+  k_oci_sweep<<<c.grid, block, c.smem, h.stream>>>(h.J, h.Jp, h.N, h.G, c.chunks, h.type, h.tt.Linv, h.tt.Cin, h.tt.Mp,
+                                                   h.w, h.inc, h.tc, h.Psi[0], h.Psi[1], h.ds, h.partials);
 }
 
 // ------------------------------------------------------------------ a4, a5
@@ -214,36 +229,38 @@ __global__ void __launch_bounds__(kFinalizeThreads) k_finalize(const double *__r
     __syncthreads();
   }
   if (threadIdx.x == 0) {
+    DevState d = *ds;  // one load of the state, one store below
     const double e = sqrt(sh[0]);
-    const int l = ds->l;
-    if (e_hist && l < ds->max_iter) e_hist[l] = e;
+    const int l = d.l;
+    if (e_hist && l < d.max_iter) e_hist[l] = e;
     double rho = 0.0;
     int conv = 0;
     if (!isfinite(e)) {
-      ds->status = OCI_E_NONFINITE;
-      ds->done = 1;
+      d.status = OCI_E_NONFINITE;
+      d.done = 1;
     } else {
-      if (l >= 1 && ds->e_prev > 0.0) rho = e / ds->e_prev;
-      if (!ds->fixed) {
+      if (l >= 1 && d.e_prev > 0.0) rho = e / d.e_prev;
+      if (!d.fixed) {
         if (e == 0.0) conv = 1;
-        else if (l >= 1) conv = e < ds->tol * (1.0 - rho);
+        else if (l >= 1) conv = e < d.tol * (1.0 - rho);
       }
     }
-    ds->e = e;
-    ds->rho = rho;
-    ds->e_prev = e;
-    ds->l = l + 1;
-    ds->cur ^= 1;
-    if (!ds->fixed && !ds->done) {
+    d.e = e;
+    d.rho = rho;
+    d.e_prev = e;
+    d.l = l + 1;
+    d.cur ^= 1;
+    if (!d.fixed && !d.done) {
       if (conv) {
-        ds->status = OCI_OK;
-        ds->done = 1;
-      } else if (l + 1 >= ds->max_iter) {
-        ds->status = OCI_E_NOCONV;
-        ds->done = 1;
+        d.status = OCI_OK;
+        d.done = 1;
+      } else if (l + 1 >= d.max_iter) {
+        d.status = OCI_E_NOCONV;
+        d.done = 1;
       }
     }
-    if (use_cond && ds->done) cudaGraphSetConditional(cond, 0);
+    *ds = d;
+    if (use_cond && d.done) cudaGraphSetConditional(cond, 0);
   }
 }
 

@@ -70,3 +70,53 @@ def test_fp32_ir_noconv_keeps_last_iterate():
         assert rel(s.psi(), o.Psi) < 1e-6
         pp, t = s.state()
         assert t == 0.0
+
+
+def _uniform_tiles(seed, J, N, G, region=128):
+    """Random slab whose material and width are constant over aligned blocks of
+    `region` cells (one cell type per 128-cell tile, as the tensor-core forms need)."""
+    p = W.random_slab(seed, J, N, G)
+    blk = np.arange(J) // region
+    return p.replace(mat=(blk % p.n_mat).astype(np.int32), dx=p.dx[(blk * region) % J].copy(), tol=1e-11)
+
+
+TC_CASES = [(31, 64, 8, 1), (32, 300, 16, 1), (33, 257, 8, 2), (34, 200, 16, 2), (35, 130, 4, 2)]
+
+
+@pytest.mark.parametrize("prec", [oci.TF32_IR, oci.BF16X3_IR])
+@pytest.mark.parametrize("seed,J,N,G", TC_CASES)
+def test_tensor_core_forms_match_fp64_oracle(prec, seed, J, N, G):
+    """Block apply on tcgen05 tensor cores (TF32, or BF16 hi/lo x3) with FP64
+    refinement: flux within 1e-10 of the FP64 oracle."""
+    p = _uniform_tiles(seed, J, N, G)
+    o = Oracle(p)
+    with oci.Solver(p, precision=prec) as s:
+        for k in range(3):
+            r = o.step(OCI)
+            st = s.step()
+            assert st["status"] == 0
+            assert st["iters"] <= r["iters"] + 12, (st["iters"], r["iters"])
+            assert rel(s.phi(), r["phi"]) < 1e-10
+            assert rel(s.psi(), r["Psi"]) < 1e-10
+            assert np.abs(s.balance() - r["bal"]).max() <= 1e-10 * np.abs(r["bal"]).max()
+
+
+def test_tensor_core_forms_reject_mixed_tiles():
+    p = W.random_slab(36, 200, 8, 1)  # a different cell type in almost every cell
+    with pytest.raises(oci.OCIError) as ei:
+        oci.Solver(p, precision=oci.TF32_IR)
+    assert ei.value.code == oci.E_INVAL
+
+
+@pytest.mark.parametrize("prec", [oci.TF32_IR, oci.BF16X3_IR])
+def test_tensor_core_full_size_matches_fp64_path(prec):
+    """Precision form of the 2^18-cell S16 slab: two steps against the FP64 path."""
+    p = W.slab_3region(c=0.9, tau=0.1)
+    with oci.Solver(p) as a, oci.Solver(p, precision=prec) as b:
+        for _ in range(2):
+            sa, sb = a.step(), b.step()
+            assert sb["status"] == 0
+            assert sb["iters"] <= sa["iters"] + 12
+            assert max(sb["balance_rel"]) < 1e-9
+        assert rel(b.phi(), a.phi()) < 1e-10
+        assert rel(b.psi(), a.psi()) < 1e-10
