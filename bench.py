@@ -214,48 +214,41 @@ def run_ours(args):
 
     mixed = None
     if smx is not None:
-        m0, m1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        clk2 = Clocks(local)
-        barrier()
-        m0.record(stream)
-        mx_sweeps, mx_stats = 0, []
-        for _ in range(args.steps):
-            st = smx.step()
-            mx_stats.append(st)
-            mx_sweeps += st["iters"]
-        m1.record(stream)
-        barrier()
-        clk_mx = clk2.stop()
-        mx_ms = max_over_ranks(m0.elapsed_time(m1))
-        phi64, phimx = s.phi(), smx.phi()
-        psi64, psimx = s.psi(), smx.psi()
-        b64, bmx = s.balance(), smx.balance()
-        n_in = 30
-        psi_keep_mx = smx.psi()
-        q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        barrier()
-        q0.record(stream)
-        smx.iterate(n_in)
-        q1.record(stream)
-        torch.cuda.synchronize()
-        inner_ms = q0.elapsed_time(q1) / n_in
-        smx.set_psi(psi_keep_mx)
-        NGm = p.N * p.G
-        mixed = {"precision": "FP32_IR (FP32 structured inner sweeps on the correction, FP64 residual / norm "
-                              "accumulation / balance / carry)",
-                 "value": p.unknowns * mx_sweeps * world / (mx_ms * 1e-3), "unit": UNIT,
-                 "ms_per_step": mx_ms / args.steps, "sweeps_per_step": mx_sweeps / args.steps,
-                 "sweeps_per_step_fp64": sweeps / args.steps,
-                 "speedup_vs_fp64": (ms / args.steps) / (mx_ms / args.steps),
-                 "err_vs_fp64": {"phi_rel": float(np.abs(phimx - phi64).max() / np.abs(phi64).max()),
-                                 "psi_rel": float(np.abs(psimx - psi64).max() / np.abs(psi64).max()),
-                                 "balance_rel": float(np.abs(bmx - b64).max() / np.abs(b64).max()),
-                                 "iters_diff_total": int(mx_sweeps - sweeps)},
-                 "iterate_us_per_sweep_incl_refinement": inner_ms * 1e3,
-                 "inner_bytes_per_cell": 48 * NGm + 4,
-                 "inner_hbm_gbs": (48 * NGm + 4) * p.J / (inner_ms * 1e-3) / 1e9,
-                 "clocks": clk_mx}
         smx.close()
+        mixed = []
+        phi64, psi64, b64 = s.phi(), s.psi(), s.balance()
+        forms = (("FP32_IR", oci.FP32_IR, "FP32 structured block apply on CUDA cores"),
+                 ("TF32_IR", oci.TF32_IR, "TF32 dense block apply on tcgen05 tensor cores"),
+                 ("BF16X3_IR", oci.BF16X3_IR, "BF16 hi/lo x3 dense block apply on tcgen05 tensor cores"))
+        for name, prec, what in forms:
+            sv = oci.Solver(p, precision=prec, stream=stream.cuda_stream)
+            for _ in range(args.warmup):
+                sv.step()
+            m0, m1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            clk2 = Clocks(local)
+            barrier()
+            m0.record(stream)
+            mx_sweeps = 0
+            for _ in range(args.steps):
+                mx_sweeps += sv.step()["iters"]
+            m1.record(stream)
+            barrier()
+            clk_mx = clk2.stop()
+            mx_ms = max_over_ranks(m0.elapsed_time(m1))
+            phimx, psimx, bmx = sv.phi(), sv.psi(), sv.balance()
+            sv.close()
+            mixed.append({
+                "form": name, "block_apply": what,
+                "fp64_kept_for": "iterate, residual, norm accumulation, balance tallies, carry",
+                "value": p.unknowns * mx_sweeps * world / (mx_ms * 1e-3), "unit": UNIT,
+                "ms_per_step": mx_ms / args.steps, "sweeps_per_step": mx_sweeps / args.steps,
+                "sweeps_per_step_fp64": sweeps / args.steps,
+                "speedup_vs_fp64": (ms / args.steps) / (mx_ms / args.steps),
+                "err_vs_fp64": {"phi_rel": float(np.abs(phimx - phi64).max() / np.abs(phi64).max()),
+                                "psi_rel": float(np.abs(psimx - psi64).max() / np.abs(psi64).max()),
+                                "balance_rel": float(np.abs(bmx - b64).max() / np.abs(b64).max()),
+                                "sweeps_diff_total": int(mx_sweeps - sweeps)},
+                "clocks": clk_mx})
 
     # seconds per converged time step: OCI (FP64 and mixed) against GPU SI
     si_cmp = None
@@ -337,7 +330,7 @@ def run_ours(args):
                     "d2h_bytes_per_step": p.J * p.G * 4 * 8},
             "gpu_launches": launches,
             "clocks": clocks,
-            "mixed_form": mixed,
+            "precision_forms": mixed,
             "si_comparison": si_cmp}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args)
