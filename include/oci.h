@@ -199,6 +199,31 @@ int oci_get_edges(const oci_handle *h, double *left, double *right);
  * st may be NULL; st->iters and st->e_last are left 0. */
 int oci_commit(oci_handle *h, oci_stats *st);
 
+/* Batched form: n independent slabs (each its own oci_problem: sizes, angle
+ * order, groups, materials, dt, tolerances) advanced together.  Slabs that
+ * share (N, G) are packed into one cell range; every time step is one CUDA
+ * graph launch whose persistent sweep kernels skip slabs that have converged,
+ * each slab with its own stop rule (Sec. 2.1).  FP64, structured solver and
+ * OCI_GUESS_PREV only; all problems must name the same stream.  The returned
+ * handle accepts only the oci_batch_* calls and oci_destroy (others return
+ * OCI_E_STATE). */
+int oci_batch_setup(const oci_problem *probs, int32_t n, oci_handle **out);
+
+/* One time step of every slab; st: [n] (or NULL) per-slab statistics.
+ * Returns OCI_OK, or the status of a slab that did not converge (that slab is
+ * not committed; the others are). */
+int oci_batch_step(oci_handle *h, oci_stats *st);
+
+/* Number of slabs of a batched handle. */
+int oci_batch_size(const oci_handle *h, int32_t *n);
+
+/* Per-slab state of a batched handle, slab index s in [0, n): psi
+ * [J_s][G_s][N_s][4], phi [J_s][G_s][4], bal [G_s][2][5] (as oci_get_balance);
+ * host or device memory. */
+int oci_batch_get_psi(const oci_handle *h, int32_t s, double *psi);
+int oci_batch_get_phi(const oci_handle *h, int32_t s, double *phi);
+int oci_batch_get_balance(const oci_handle *h, int32_t s, double *bal);
+
 /* Release the handle and its device memory.  NULL is accepted. */
 void oci_destroy(oci_handle *h);
 

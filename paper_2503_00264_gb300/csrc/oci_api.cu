@@ -16,7 +16,6 @@
 
 #include "oci_internal.h"
 
-struct oci_handle : public oci::Handle {};
 
 namespace oci {
 
@@ -43,7 +42,7 @@ const void *k_mx_inner_ptr();
 // Gauss-Legendre nodes/weights on [-1,1] (the paper uses Gauss-Legendre S_N
 // throughout, Sec. 1): Newton iteration on P_N from Tricomi's initial guess;
 // P_N and P_N' from the three-term recurrence.  Ascending nodes.
-static void gauss_legendre(int N, std::vector<double> &x, std::vector<double> &wt) {
+void gauss_legendre(int N, std::vector<double> &x, std::vector<double> &wt) {
   x.assign(N, 0.0);
   wt.assign(N, 0.0);
   const double pi = 3.141592653589793238462643;
@@ -129,7 +128,7 @@ static bool all_finite(const double *a, size_t n) {
   return true;
 }
 
-static int validate(const oci_problem *p) {
+int validate(const oci_problem *p) {
   if (!p) return set_error("problem is NULL"), OCI_E_INVAL;
   if (p->J < 1) return set_error("J must be >= 1"), OCI_E_INVAL;
   if (p->N < 2 || p->N > kMaxN || (p->N & 1)) return set_error("N must be even, 2 <= N <= 128"), OCI_E_INVAL;
@@ -168,9 +167,9 @@ static int validate(const oci_problem *p) {
 // ---------------------------------------------------------------- tables
 // Per unique (material, dx) cell type: L_{g,m}^{-1} (Eq. Aj), the inflow columns,
 // Mp = (I - K H)^{-1} K and K.
-static int build_tables(Handle &h, std::vector<double> &Linv, std::vector<double> &Cin, std::vector<double> &Mp,
-                        std::vector<double> &Kap, std::vector<double> &tdx, std::vector<double> &tsig,
-                        std::vector<double> &Lco) {
+int build_tables(Handle &h, std::vector<double> &Linv, std::vector<double> &Cin, std::vector<double> &Mp,
+                 std::vector<double> &Kap, std::vector<double> &tdx, std::vector<double> &tsig,
+                 std::vector<double> &Lco) {
   const int N = h.N, G = h.G, J = h.J;
   std::map<std::pair<int, uint64_t>, int> ids;
   h.h_type.assign(J, 0);
@@ -349,8 +348,14 @@ static int autotune(Handle &h) {
   return OCI_OK;
 }
 
+void free_batch(Batch *b);
+
 static void free_handle(Handle *h) {
   if (!h) return;
+  if (h->batch) {
+    free_batch(h->batch);
+    h->batch = nullptr;
+  }
   if (h->stream) cudaStreamSynchronize(h->stream);
   void *ptrs[] = {h->Psi[0], h->Psi[1], h->tc,        h->psi_prev,  h->phi,          h->phi_si[0], h->phi_si[1],
                   h->Q,      h->inc,    h->type,      h->mu,        h->w,            h->v,         h->tt.Linv,
@@ -780,9 +785,10 @@ __global__ void k_fp64_peak(double *out, int iters) {
 
 using namespace oci;
 
-#define GUARD(h)                                         \
-  do {                                                   \
-    if (!(h)) return set_error("handle is NULL"), OCI_E_INVAL; \
+#define GUARD(h)                                                                          \
+  do {                                                                                    \
+    if (!(h)) return set_error("handle is NULL"), OCI_E_INVAL;                            \
+    if ((h)->batch) return set_error("not valid on a batched handle"), OCI_E_STATE;      \
   } while (0)
 
 extern "C" {

@@ -1,0 +1,347 @@
+// oci_batch.cu -- batched form: many independent slabs of uneven size, angle
+// order and group count advanced by one graph launch per time step.
+//
+// Slabs are grouped by (N, G) into classes.  Within a class the slabs are
+// concatenated into one structure-of-arrays cell range ([G][N][4][Jc], cells
+// fastest), each slab padded to a multiple of 128 cells so that no tile of the
+// sweep and no 32-cell block of the carry straddles two slabs.  Per cell: the
+// class-wide cell-type id (the type tables carry each slab's dt and speeds) and
+// the slab index (-1 for padding).  Per slab: first cell, length, first and last
+// tile, its own convergence state (DevState) and incident fluxes.
+//
+// The sweep kernel is persistent: a grid sized to the resident capacity loops
+// over the class's tiles, skipping tiles of slabs that have converged.  The
+// per-slab finalize (one warp per slab) applies the stop rule of Sec. 2.1 to
+// that slab's norm; a device counter of unconverged slabs ends the conditional
+// WHILE graph when it reaches zero.  The cell solve is the FP64 structured solve
+// of oci_sweep.cu; the slab boundaries replace the inflow of the neighbouring
+// cell by the slab's incident flux.
+#include <math.h>
+
+#include "oci_batch.h"
+
+namespace oci {
+
+__global__ void k_b_step_const(int Jc, int N, int G, const int32_t *__restrict__ type,
+                               const int32_t *__restrict__ seg, const double *__restrict__ tdx,
+                               const double *__restrict__ tah, const double *__restrict__ Q,
+                               const double *__restrict__ psi_prev, const double *__restrict__ Linv,
+                               double *__restrict__ tc) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int gm = blockIdx.y;
+  if (j >= Jc || seg[j] < 0) return;
+  const int g = gm / N;
+  const int tau = type[j];
+  const double dx = tdx[tau];
+  const double ah = tah[(size_t)tau * G + g];
+  double q[4] = {0.0, 0.0, 0.0, 0.0};
+  if (Q) {
+#pragma unroll
+    for (int p = 0; p < 4; p++) q[p] = dx / 4.0 * Q[(size_t)(g * 4 + p) * Jc + j];
+  }
+  const double c0 = q[0] + ah * psi_prev[(size_t)(gm * 2 + 0) * Jc + j];
+  const double c1 = q[1] + ah * psi_prev[(size_t)(gm * 2 + 1) * Jc + j];
+  const double *L = Linv + ((size_t)tau * G * N + gm) * 16;
+#pragma unroll
+  for (int p = 0; p < 4; p++)
+    tc[(size_t)(gm * 4 + p) * Jc + j] = L[p * 4 + 0] * c0 + L[p * 4 + 1] * c1 + L[p * 4 + 2] * q[2] + L[p * 4 + 3] * q[3];
+}
+
+// Persistent batched sweep.  Block = CB cells x G groups; tiles of CB cells.
+__global__ void __launch_bounds__(256) k_b_sweep(BatchClassDev c, DevState *__restrict__ ds) {
+  extern __shared__ double sm[];
+  const int CB = blockDim.x, N = c.N, G = c.G, Jc = c.Jc;
+  const int cl = threadIdx.x, g = threadIdx.y;
+  double *t_s = sm;
+  double *y_s = sm + (size_t)G * N * 4 * CB;
+  __shared__ double red[8];
+  const int N2 = N / 2;
+  for (int tile = blockIdx.x; tile < c.n_tiles; tile += gridDim.x) {
+    const int s = c.tile_slab[tile];
+    if (ds[s].done) continue;  // uniform over the block
+    const int cur = ds[s].cur;
+    const double *__restrict__ Pin = cur ? c.Psi1 : c.Psi0;
+    double *__restrict__ Pout = cur ? c.Psi0 : c.Psi1;
+    const int j = c.tile_first_cell[tile] + cl;
+    const int jl = j - c.slab_start[s];
+    const int Js = c.slab_J[s];
+    const bool active = jl < Js;
+    const int tau = active ? c.type[j] : 0;
+    const size_t tb = (size_t)tau * G * N;
+    const double *inc = c.inc + (size_t)s * 2 * G * N * 2;
+    double y0 = 0.0, y1 = 0.0, y2 = 0.0, y3 = 0.0;
+    if (active) {
+#pragma unroll 2
+      for (int m = 0; m < N; m++) {
+        const int gm = g * N + m;
+        const size_t base = (size_t)gm * 4 * Jc + j;
+        double uk, uh;
+        if (m >= N2) {
+          if (jl > 0) {
+            uk = Pin[base + (size_t)Jc - 1];
+            uh = Pin[base + 3 * (size_t)Jc - 1];
+          } else {
+            uk = inc[gm * 2 + 0];
+            uh = inc[gm * 2 + 1];
+          }
+        } else {
+          if (jl < Js - 1) {
+            uk = Pin[base + 1];
+            uh = Pin[base + 2 * (size_t)Jc + 1];
+          } else {
+            uk = inc[(G * N + gm) * 2 + 0];
+            uh = inc[(G * N + gm) * 2 + 1];
+          }
+        }
+        const double *C = c.Cin + (tb + gm) * 8;
+        const double t0 = fma(C[1], uh, fma(C[0], uk, c.tc[base]));
+        const double t1 = fma(C[3], uh, fma(C[2], uk, c.tc[base + (size_t)Jc]));
+        const double t2 = fma(C[5], uh, fma(C[4], uk, c.tc[base + 2 * (size_t)Jc]));
+        const double t3 = fma(C[7], uh, fma(C[6], uk, c.tc[base + 3 * (size_t)Jc]));
+        double *ts = t_s + (size_t)(gm * 4) * CB + cl;
+        ts[0] = t0;
+        ts[CB] = t1;
+        ts[2 * CB] = t2;
+        ts[3 * CB] = t3;
+        const double wm = c.w[m];
+        y0 = fma(wm, t0, y0);
+        y1 = fma(wm, t1, y1);
+        y2 = fma(wm, t2, y2);
+        y3 = fma(wm, t3, y3);
+      }
+      double *ys = y_s + (size_t)(g * 4) * CB + cl;
+      ys[0] = y0;
+      ys[CB] = y1;
+      ys[2 * CB] = y2;
+      ys[3 * CB] = y3;
+    }
+    __syncthreads();
+    double e2 = 0.0;
+    if (active) {
+      const int G4 = 4 * G;
+      const double *M = c.Mp + (size_t)tau * G4 * G4 + (size_t)(g * 4) * G4;
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+      for (int k = 0; k < G4; k++) {
+        const double yk = y_s[(size_t)k * CB + cl];
+        s0 = fma(M[k], yk, s0);
+        s1 = fma(M[G4 + k], yk, s1);
+        s2 = fma(M[2 * G4 + k], yk, s2);
+        s3 = fma(M[3 * G4 + k], yk, s3);
+      }
+#pragma unroll 2
+      for (int m = 0; m < N; m++) {
+        const int gm = g * N + m;
+        const size_t base = (size_t)gm * 4 * Jc + j;
+        const double *L = c.Linv + (tb + gm) * 16;
+        const double *ts = t_s + (size_t)(gm * 4) * CB + cl;
+        double o[4];
+#pragma unroll
+        for (int p = 0; p < 4; p++)
+          o[p] = fma(L[p * 4 + 3], s3, fma(L[p * 4 + 2], s2, fma(L[p * 4 + 1], s1, fma(L[p * 4 + 0], s0, ts[p * CB]))));
+#pragma unroll
+        for (int p = 0; p < 4; p++) {
+          const double d = o[p] - Pin[base + (size_t)p * Jc];
+          e2 = fma(d, d, e2);
+          Pout[base + (size_t)p * Jc] = o[p];
+        }
+      }
+    }
+    // fixed-order block sum
+    const int tid = threadIdx.y * CB + threadIdx.x;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) e2 += __shfl_down_sync(0xffffffffu, e2, o);
+    if ((tid & 31) == 0) red[tid >> 5] = e2;
+    __syncthreads();
+    if (tid == 0) {
+      double v = 0.0;
+      for (int i = 0; i < (CB * G + 31) / 32; i++) v += red[i];
+      c.partials[tile] = v;
+    }
+    __syncthreads();  // t_s / y_s / red reused by the next tile
+  }
+}
+
+// One warp per slab: fixed-order sum of the slab's tile partials, stop rule,
+// ping-pong flip; the last slab to finish ends the WHILE loop.
+__global__ void k_b_finalize(BatchClassDev c, DevState *__restrict__ ds, int *active, int use_cond,
+                             cudaGraphConditionalHandle cond) {
+  const int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (s >= c.n_slabs) return;
+  DevState &d = ds[s];
+  if (d.done) return;
+  double v = 0.0;
+  for (int t = c.slab_tile0[s] + lane; t < c.slab_tile1[s]; t += 32) v += c.partials[t];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if (lane != 0) return;
+  const double e = sqrt(v);
+  const int l = d.l;
+  double rho = 0.0;
+  int conv = 0;
+  if (!isfinite(e)) {
+    d.status = OCI_E_NONFINITE;
+    d.done = 1;
+  } else {
+    if (l >= 1 && d.e_prev > 0.0) rho = e / d.e_prev;
+    if (e == 0.0) conv = 1;
+    else if (l >= 1) conv = e < d.tol * (1.0 - rho);
+  }
+  d.e = e;
+  d.rho = rho;
+  d.e_prev = e;
+  d.l = l + 1;
+  d.cur ^= 1;
+  if (!d.done) {
+    if (conv) {
+      d.status = OCI_OK;
+      d.done = 1;
+    } else if (l + 1 >= d.max_iter) {
+      d.status = OCI_E_NOCONV;
+      d.done = 1;
+    }
+  }
+  if (d.done) {
+    const int before = atomicSub(active, 1);
+    if (before == 1 && use_cond) cudaGraphSetConditional(cond, 0);
+  }
+}
+
+// Commit of converged slabs: phi, carry and per-block balance tallies (as k_carry).
+__global__ void __launch_bounds__(32 * kMaxG) k_b_carry(BatchClassDev c, const DevState *__restrict__ ds) {
+  __shared__ double ph_s[kMaxG * 4][32];
+  const int N = c.N, G = c.G, Jc = c.Jc;
+  const int cl = threadIdx.x, g = threadIdx.y;
+  const int j = blockIdx.x * 32 + cl;
+  const int s = c.seg[blockIdx.x * 32];  // blocks never straddle slabs
+  if (s < 0 || ds[s].status != OCI_OK) return;  // uniform
+  const double *__restrict__ P = ds[s].cur ? c.Psi1 : c.Psi0;
+  const bool active = c.seg[j] >= 0;
+  double ph[4] = {0, 0, 0, 0}, pp[2] = {0, 0};
+  int tau = 0;
+  if (active) {
+    tau = c.type[j];
+    for (int m = 0; m < N; m++) {
+      const int gm = g * N + m;
+      const double wm = c.w[m];
+      const size_t base = (size_t)gm * 4 * Jc + j;
+      double o[4];
+#pragma unroll
+      for (int p = 0; p < 4; p++) {
+        o[p] = P[base + (size_t)p * Jc];
+        ph[p] = fma(wm, o[p], ph[p]);
+      }
+      const size_t pb = (size_t)gm * 2 * Jc + j;
+      pp[0] = fma(wm, c.psi_prev[pb], pp[0]);
+      pp[1] = fma(wm, c.psi_prev[pb + Jc], pp[1]);
+      c.psi_prev[pb] = o[2];
+      c.psi_prev[pb + Jc] = o[3];
+    }
+#pragma unroll
+    for (int p = 0; p < 4; p++) {
+      c.phi[(size_t)(g * 4 + p) * Jc + j] = ph[p];
+      ph_s[g * 4 + p][cl] = ph[p];
+    }
+  }
+  __syncthreads();
+  double tally[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  if (active) {
+    const double dx = c.tdx[tau];
+    const double sig = c.tsig[(size_t)tau * G + g];
+    const double rate = 2.0 * c.tah[(size_t)tau * G + g];  // dx / (v dt)
+    tally[0] = rate / 2.0 * ((ph[2] - pp[0]) + (ph[3] - pp[1]));
+    tally[1] = rate * ((ph[2] - ph[0]) + (ph[3] - ph[1]));
+    tally[2] = dx / 2.0 * sig * (ph[0] + ph[1]);
+    tally[3] = dx / 2.0 * sig * (ph[2] + ph[3]);
+    for (int gp = 0; gp < G; gp++) {
+      const double k2 = 2.0 * c.Kap[((size_t)tau * G + gp) * G + g];
+      tally[4] += k2 * (ph_s[gp * 4 + 0][cl] + ph_s[gp * 4 + 1][cl]);
+      tally[5] += k2 * (ph_s[gp * 4 + 2][cl] + ph_s[gp * 4 + 3][cl]);
+    }
+    if (c.Q) {
+      tally[6] = dx / 2.0 * (c.Q[(size_t)(g * 4 + 0) * Jc + j] + c.Q[(size_t)(g * 4 + 1) * Jc + j]);
+      tally[7] = dx / 2.0 * (c.Q[(size_t)(g * 4 + 2) * Jc + j] + c.Q[(size_t)(g * 4 + 3) * Jc + j]);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 8; k++) {
+    double x = tally[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (cl == 0) c.bal_partials[((size_t)blockIdx.x * G + g) * 8 + k] = x;
+  }
+}
+
+// Per (slab, group): fixed-order sum of the slab's carry blocks plus leakage.
+__global__ void k_b_balance_final(BatchClassDev c, const DevState *__restrict__ ds) {
+  const int s = blockIdx.x, g = blockIdx.y;
+  if (threadIdx.x != 0 || ds[s].status != OCI_OK) return;
+  const int N = c.N, G = c.G, Jc = c.Jc;
+  const int b0 = c.slab_start[s] / 32, b1 = (c.slab_start[s] + c.slab_J[s] + 31) / 32;
+  double tot[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int b = b0; b < b1; b++)
+    for (int k = 0; k < 8; k++) tot[k] += c.bal_partials[((size_t)b * G + g) * 8 + k];
+  const double *P = ds[s].cur ? c.Psi1 : c.Psi0;
+  const double *inc = c.inc + (size_t)s * 2 * G * N * 2;
+  const int jf = c.slab_start[s], jlast = c.slab_start[s] + c.slab_J[s] - 1;
+  double lA = 0.0, lE = 0.0;
+  for (int m = 0; m < N; m++) {
+    const int gm = g * N + m;
+    double rk, rh, lk, lh;
+    if (c.mu[m] > 0) {
+      rk = P[(size_t)(gm * 4 + 1) * Jc + jlast];
+      rh = P[(size_t)(gm * 4 + 3) * Jc + jlast];
+      lk = inc[gm * 2 + 0];
+      lh = inc[gm * 2 + 1];
+    } else {
+      lk = P[(size_t)(gm * 4 + 0) * Jc + jf];
+      lh = P[(size_t)(gm * 4 + 2) * Jc + jf];
+      rk = inc[(G * N + gm) * 2 + 0];
+      rh = inc[(G * N + gm) * 2 + 1];
+    }
+    lA += c.w[m] * c.mu[m] * (rk - lk);
+    lE += c.w[m] * c.mu[m] * (rh - lh);
+  }
+  double *bg = c.bal + ((size_t)s * G + g) * 10;
+  bg[0] = tot[0]; bg[1] = lA; bg[2] = tot[2]; bg[3] = tot[4]; bg[4] = tot[6];
+  bg[5] = tot[1]; bg[6] = lE; bg[7] = tot[3]; bg[8] = tot[5]; bg[9] = tot[7];
+}
+
+// ---------------------------------------------------------------- launches
+size_t b_sweep_smem(int N, int G, int cb) {
+  return (size_t)cb * ((size_t)G * N * 4 * 8 + (size_t)G * 4 * 8);
+}
+
+void launch_b_step_const(BatchClass &c, cudaStream_t st) {
+  dim3 grid((c.d.Jc + 255) / 256, c.d.G * c.d.N);
+  k_b_step_const<<<grid, 256, 0, st>>>(c.d.Jc, c.d.N, c.d.G, c.d.type, c.d.seg, c.d.tdx, c.d.tah, c.d.Q,
+                                       c.d.psi_prev, c.d.Linv, c.d.tc);
+}
+
+void launch_b_sweep(BatchClass &c, DevState *ds, cudaStream_t st) {
+  dim3 block(c.cb, c.d.G);
+  k_b_sweep<<<c.grid, block, b_sweep_smem(c.d.N, c.d.G, c.cb), st>>>(c.d, ds);
+}
+
+void launch_b_finalize(BatchClass &c, DevState *ds, int *active, int use_cond, cudaGraphConditionalHandle cond,
+                       cudaStream_t st) {
+  const int warps = 4;
+  k_b_finalize<<<(c.d.n_slabs + warps - 1) / warps, 32 * warps, 0, st>>>(c.d, ds, active, use_cond, cond);
+}
+
+void launch_b_carry(BatchClass &c, DevState *ds, cudaStream_t st) {
+  k_b_carry<<<c.d.Jc / 32, dim3(32, c.d.G), 0, st>>>(c.d, ds);
+  k_b_balance_final<<<dim3(c.d.n_slabs, c.d.G), 32, 0, st>>>(c.d, ds);
+}
+
+const void *k_b_sweep_ptr() { return (const void *)k_b_sweep; }
+
+int b_max_grid(int N, int G, int cb) {
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_b_sweep, cb * G, b_sweep_smem(N, G, cb));
+  return sms * (per > 0 ? per : 1);
+}
+
+}  // namespace oci

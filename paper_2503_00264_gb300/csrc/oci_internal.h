@@ -59,7 +59,10 @@ struct TypeTables {
   float *Mp32 = nullptr;
 };
 
+struct Batch;
+
 struct Handle {
+  Batch *batch = nullptr;          // set on handles made by oci_batch_setup
   int J = 0, N = 0, G = 0, n_mat = 0, Jp = 0;
   double dt = 0, tol = 0, t = 0;
   int max_iter = 0, precision = 0, guess = 0, solver = 0;
@@ -161,4 +164,13 @@ void launch_dense_sweep(Handle &h);
 void set_error(const std::string &msg);
 int cuda_fail(cudaError_t e, const char *what);
 
+// setup helpers shared with the batched form
+int validate(const oci_problem *p);
+void gauss_legendre(int N, std::vector<double> &x, std::vector<double> &wt);
+int build_tables(Handle &h, std::vector<double> &Linv, std::vector<double> &Cin, std::vector<double> &Mp,
+                 std::vector<double> &Kap, std::vector<double> &tdx, std::vector<double> &tsig,
+                 std::vector<double> &Lco);
+
 }  // namespace oci
+
+struct oci_handle : public oci::Handle {};

@@ -26,7 +26,8 @@ SOLVER_AUTO, SOLVER_STRUCTURED, SOLVER_DENSE_LU = 0, 1, 2
 EXPORTS = ["oci_setup", "oci_step", "oci_solve_transient", "si_sweep", "oci_iterate", "si_iterate",
            "oci_get_psi", "oci_set_psi", "oci_get_phi", "oci_get_state", "oci_set_state", "oci_get_balance",
            "oci_set_boundary", "oci_get_e_hist", "oci_get_edges", "oci_commit", "oci_destroy", "oci_last_error",
-           "oci_probe_fp64_peak"]
+           "oci_probe_fp64_peak", "oci_batch_setup", "oci_batch_step", "oci_batch_size", "oci_batch_get_psi",
+           "oci_batch_get_phi", "oci_batch_get_balance"]
 
 
 class OCIError(RuntimeError):
@@ -86,6 +87,11 @@ def load(path: Optional[str] = None):
     L.oci_destroy.restype = None
     L.oci_last_error.restype = ctypes.c_char_p
     L.oci_probe_fp64_peak.argtypes = [ctypes.POINTER(dbl)]
+    L.oci_batch_setup.argtypes = [ctypes.POINTER(Problem), i32, ctypes.POINTER(vp)]
+    L.oci_batch_step.argtypes = [vp, ctypes.POINTER(Stats)]
+    L.oci_batch_size.argtypes = [vp, ctypes.POINTER(i32)]
+    for f in ("oci_batch_get_psi", "oci_batch_get_phi", "oci_batch_get_balance"):
+        getattr(L, f).argtypes = [vp, i32, vp]
     for f in EXPORTS:
         if f not in ("oci_destroy", "oci_last_error"):
             getattr(L, f).restype = ctypes.c_int
@@ -129,6 +135,71 @@ def fp64_peak() -> float:
     v = ctypes.c_double(0.0)
     _check(L.oci_probe_fp64_peak(ctypes.byref(v)))
     return v.value
+
+
+def _problem_struct(P, keep, precision, solver, stream, tol=None, max_iter=None, guess=None):
+    k = [np.ascontiguousarray(a) if a is not None else None
+         for a in (P.dx, P.mat, P.sigma_t, P.sigma_s, P.v, P.Q, P.psi_init, P.inc_left, P.inc_right)]
+    keep.append(k)
+    return Problem(P.J, P.N, P.G, P.n_mat, _ptr(k[0]), _ptr(k[1], np.int32), _ptr(k[2]), _ptr(k[3]),
+                   _ptr(k[4]), _ptr(k[5]), float(P.dt), _ptr(k[6]), _ptr(k[7]), _ptr(k[8]),
+                   float(P.tol if tol is None else tol), int(P.max_iter if max_iter is None else max_iter),
+                   int(precision), int(P.guess if guess is None else guess), int(solver), stream)
+
+
+class BatchSolver:
+    """Many independent slabs advanced together (oci_batch_* calls)."""
+
+    def __init__(self, probs, stream=None):
+        self.L = load()
+        self.probs = list(probs)
+        self._keep = []
+        st = current_stream() if stream is None else stream
+        arr = (Problem * len(self.probs))(*[_problem_struct(p, self._keep, FP64, SOLVER_AUTO, st) for p in self.probs])
+        self._arr = arr
+        h = ctypes.c_void_p()
+        _check(self.L.oci_batch_setup(arr, len(self.probs), ctypes.byref(h)))
+        self.h = h
+
+    def step(self, allow_noconv: bool = False):
+        st = (Stats * len(self.probs))()
+        _check(self.L.oci_batch_step(self.h, st), (E_NOCONV,) if allow_noconv else ())
+        return [st[i].as_dict() for i in range(len(self.probs))]
+
+    def psi(self, s: int):
+        P = self.probs[s]
+        out = np.zeros((P.J, P.G, P.N, 4))
+        _check(self.L.oci_batch_get_psi(self.h, int(s), _ptr(out, writable=True)))
+        return out
+
+    def phi(self, s: int):
+        P = self.probs[s]
+        out = np.zeros((P.J, P.G, 4))
+        _check(self.L.oci_batch_get_phi(self.h, int(s), _ptr(out, writable=True)))
+        return out
+
+    def balance(self, s: int):
+        P = self.probs[s]
+        out = np.zeros((P.G, 2, 5))
+        _check(self.L.oci_batch_get_balance(self.h, int(s), _ptr(out, writable=True)))
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.oci_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Solver:

@@ -76,3 +76,13 @@ def test_null_handle_rejected(lib):
     st = oci.Stats()
     assert lib.oci_step(None, ctypes.byref(st)) == oci.E_INVAL
     lib.oci_destroy(None)
+
+
+def test_batch_setup_validates_before_device_work(lib):
+    p = W.random_slab(3, 8, 4, 1)
+    keep = []
+    arr = (oci.Problem * 2)(oci._problem_struct(p, keep, oci.FP64, 0, None),
+                            oci._problem_struct(p, keep, oci.FP32_IR, 0, None))
+    h = ctypes.c_void_p()
+    assert lib.oci_batch_setup(arr, 2, ctypes.byref(h)) == oci.E_INVAL
+    assert lib.oci_batch_setup(arr, 0, ctypes.byref(h)) == oci.E_INVAL

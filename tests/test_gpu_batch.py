@@ -1,0 +1,56 @@
+"""Batched form (many slabs, one graph launch per time step) against the FP64
+oracle slab by slab: identical sweep counts, scalar flux within 1e-12."""
+import numpy as np
+import pytest
+
+from oracle import OCI, Oracle
+from paper_2503_00264_gb300 import oci
+from paper_2503_00264_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def test_batch_matches_oracle_per_slab():
+    specs = [(41, 50, 4, 1), (42, 130, 8, 1), (43, 257, 8, 2), (44, 1, 4, 1), (45, 400, 16, 1), (46, 33, 8, 2),
+             (47, 128, 4, 3), (48, 77, 8, 1)]
+    probs = [W.random_slab(*sp).replace(tol=1e-11) for sp in specs]
+    orcs = [Oracle(p) for p in probs]
+    with oci.BatchSolver(probs) as b:
+        for k in range(3):
+            sts = b.step()
+            for i, (p, o) in enumerate(zip(probs, orcs)):
+                r = o.step(OCI)
+                assert sts[i]["status"] == 0
+                assert sts[i]["iters"] == r["iters"], (i, k, sts[i]["iters"], r["iters"])
+                assert rel(b.phi(i), r["phi"]) < 1e-12
+                assert rel(b.psi(i), r["Psi"]) < 1e-11
+                assert np.abs(b.balance(i) - r["bal"]).max() <= 1e-11 * np.abs(r["bal"]).max()
+
+
+def test_batch_uneven_slabs_match_single_slab_path():
+    """64 slabs shaped like the 256-slab batch (N in {4,8,16,32}, G in {1,4},
+    1-4 materials, random widths and mean free times), J in [1k, 4k]."""
+    probs = [p.replace(max_iter=3000) for p in W.batch_of_slabs(64, j_lo=1024, j_hi=4096)]
+    with oci.BatchSolver(probs) as b:
+        sts = b.step(allow_noconv=True)
+        for i in (0, 7, 21, 40, 63):
+            with oci.Solver(probs[i]) as s:
+                st = s.step(allow_noconv=True)
+                assert st["status"] == sts[i]["status"]
+                assert st["iters"] == sts[i]["iters"]
+                if st["status"] == 0:
+                    assert rel(b.phi(i), s.phi()) < 1e-12
+        ok = [st for st in sts if st["status"] == 0]
+        assert len(ok) > 32
+        assert max(max(st["balance_rel"]) for st in ok) < 1e-8
+
+
+def test_batch_rejects_single_slab_calls():
+    probs = [W.random_slab(49, 20, 4, 1)]
+    with oci.BatchSolver(probs) as b:
+        st = oci.Stats()
+        assert b.L.oci_step(b.h, st) == oci.E_STATE
