@@ -91,32 +91,39 @@ __global__ void __launch_bounds__(128) k_tc_inner(int J, int Jp, int N, int G, c
     const int nv = parts * opb / 16;
     for (int i = t; i < nv; i += 128) dst[i] = src[i];
   }
-  // RHS tile: thread t owns cell j = j0 + t (row t of the N x K operand)
+  // RHS tile: thread t owns cell j = j0 + t (row t of the N x K operand).
+  // Eight independent loads are issued before any is used (memory-level parallelism).
   {
     const int j = j0 + t;
     const bool act = j < J;
     const int N2 = N / 2;
-    for (int k = 0; k < n; k++) {
-      float v = 0.f;
-      if (act) {
-        v = r32[(size_t)k * Jp + j];
-        if (!zero) {
+    for (int k0 = 0; k0 < n; k0 += 8) {
+      float v[8];
+#pragma unroll
+      for (int i = 0; i < 8; i++) v[i] = act ? r32[(size_t)(k0 + i) * Jp + j] : 0.f;
+      if (act && !zero) {
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+          const int k = k0 + i;
           const int gm = k >> 2, p = k & 3, m = gm % N;
           if (m >= N2) {
-            if ((p == 0 || p == 2) && j > 0) v = fmaf((float)mu[m], Din[(size_t)(k + 1) * Jp + j - 1], v);
+            if ((p == 0 || p == 2) && j > 0) v[i] = fmaf((float)mu[m], Din[(size_t)(k + 1) * Jp + j - 1], v[i]);
           } else {
-            if ((p == 1 || p == 3) && j < J - 1) v = fmaf(-(float)mu[m], Din[(size_t)(k - 1) * Jp + j + 1], v);
+            if ((p == 1 || p == 3) && j < J - 1) v[i] = fmaf(-(float)mu[m], Din[(size_t)(k - 1) * Jp + j + 1], v[i]);
           }
         }
       }
-      const uint32_t off = kmajor_off(t, k, es, kbytes);
-      if (KIND == 1) {
-        *(float *)(sB + off) = v;
-      } else {
-        const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-        const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
-        *(__nv_bfloat16 *)(sB + off) = hi;
-        *(__nv_bfloat16 *)(sB + opb + off) = lo;
+#pragma unroll
+      for (int i = 0; i < 8; i++) {
+        const uint32_t off = kmajor_off(t, k0 + i, es, kbytes);
+        if (KIND == 1) {
+          *(float *)(sB + off) = v[i];
+        } else {
+          const __nv_bfloat16 hi = __float2bfloat16_rn(v[i]);
+          const __nv_bfloat16 lo = __float2bfloat16_rn(v[i] - __bfloat162float(hi));
+          *(__nv_bfloat16 *)(sB + off) = hi;
+          *(__nv_bfloat16 *)(sB + opb + off) = lo;
+        }
       }
     }
   }
@@ -191,11 +198,17 @@ __global__ void __launch_bounds__(128) k_tc_inner(int J, int Jp, int N, int G, c
     const int j = j0 + t;
     if (j < J) {
       float acc = 0.f;
-      for (int k = 0; k < n; k++) {
-        const float o = Dt[k * (kTcN + 1) + t];
-        const float d = zero ? o : o - Din[(size_t)k * Jp + j];
-        acc = fmaf(d, d, acc);
-        Dout[(size_t)k * Jp + j] = o;
+      for (int k0 = 0; k0 < n; k0 += 8) {
+        float old[8];
+#pragma unroll
+        for (int i = 0; i < 8; i++) old[i] = zero ? 0.f : Din[(size_t)(k0 + i) * Jp + j];
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+          const float o = Dt[(k0 + i) * (kTcN + 1) + t];
+          const float d = o - old[i];
+          acc = fmaf(d, d, acc);
+          Dout[(size_t)(k0 + i) * Jp + j] = o;
+        }
       }
       e2 = (double)acc;
     }
