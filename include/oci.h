@@ -91,6 +91,15 @@ enum {
                                 the paper's gesv/getrs scheme (Algorithm 2)       */
 };
 
+/* cell ordering of the sweeps (oci_set_ordering) */
+enum {
+  OCI_ORDER_JACOBI = 0,    /* block Jacobi: every cell from the previous iterate (Eq. oci)  */
+  OCI_ORDER_RED_BLACK = 1  /* cell-wise block Gauss-Seidel in red-black order (the other
+                              OCI ordering the paper names, Sec. 1): even cells from the
+                              previous iterate, then odd cells from the new even cells;
+                              one sweep = both halves                                      */
+};
+
 /* Problem description -- the arguments of Eq. sn_nte plus the iteration
  * controls of Sec. 2.1.  Sizes: J cells, N ordinates, G groups. */
 typedef struct {
@@ -185,6 +194,11 @@ int oci_set_boundary(oci_handle *h, const double *inc_left, const double *inc_ri
 /* e of every sweep of the last oci_step / si_sweep: e_hist [max_iter] (host or
  * device); *n receives the number of valid entries. */
 int oci_get_e_hist(const oci_handle *h, double *e_hist, int32_t *n);
+
+/* Cell ordering of the following OCI sweeps (OCI_ORDER_*; default Jacobi).
+ * Red-black needs the FP64 structured solver (else OCI_E_INVAL).  The norm and
+ * the stop rule are those of Sec. 2.1 over one full (red + black) sweep. */
+int oci_set_ordering(oci_handle *h, int32_t ordering);
 
 /* Edge values for a domain-decomposed driver (Sec. 4 of the paper proposes
  * exchanging them between subdomains every iteration): left [G][N][2] receives

@@ -7,8 +7,9 @@ links or calls it, and it shares no code with the CUDA path.
 Contents
   oci_oracle.c  plain C: Gauss-Legendre quadrature, dense A_j (Eqs. Aja, Aj,
                 scatter, fullOCIlhs), LU with partial pivoting, OCI sweep
-                (Eq. oci, Algorithm 2), SI sweep (Algorithm 1, App. A), stop
-                rule (Sec. 2.1), balance tallies (sums of Eqs. scb-mb-a..d).
+                (Eq. oci, Algorithm 2), red-black OCI sweep (block Gauss-Seidel
+                in red-black cell order, Sec. 1), SI sweep (Algorithm 1, App. A),
+                stop rule (Sec. 2.1), balance tallies (sums of Eqs. scb-mb-a..d).
   brute.py      global direct solve assembled straight from Eqs. scb-mb-a..d
                 and the two closures (no iteration, no lagging).
   fourier.py    Fourier iteration matrices T_OCI, T_SI (Sec. 2.3) and the
@@ -32,7 +33,7 @@ _lock = threading.Lock()
 _lib = None
 
 OK, INVAL, NOMEM, NOCONV, SINGULAR = 0, -1, -2, -4, -5
-OCI, SI = 0, 1
+OCI, SI, RB = 0, 1, 2
 
 
 def build(force: bool = False) -> str:
@@ -152,7 +153,7 @@ class Oracle:
         stats = np.zeros(3)
         eh = np.zeros(max_iter)
         rc = lib().orc_step(ctypes.byref(self.cp), method, float(tol), int(max_iter),
-                            _p(self.LU) if method == OCI else None, _p(self.piv) if method == OCI else None,
+                            _p(self.LU) if method != SI else None, _p(self.piv) if method != SI else None,
                             _p(self.psi_prev), _p(self.Psi), _p(phi), _p(bal), _p(stats), _p(eh))
         it = int(stats[0])
         if rc == OK:
@@ -163,7 +164,7 @@ class Oracle:
     def iterate(self, n: int, method: int = OCI):
         eh = np.zeros(max(n, 1))
         rc = lib().orc_iterate(ctypes.byref(self.cp), method, int(n),
-                               _p(self.LU) if method == OCI else None, _p(self.piv) if method == OCI else None,
+                               _p(self.LU) if method != SI else None, _p(self.piv) if method != SI else None,
                                _p(self.psi_prev), _p(self.Psi), _p(eh))
         if rc != OK:
             raise RuntimeError(f"oracle iterate failed ({rc})")

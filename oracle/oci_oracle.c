@@ -283,6 +283,31 @@ double orc_oci_sweep(const orc_problem *p, const double *mu, const double *LU, c
   return sqrt(s);
 }
 
+/* One red-black OCI sweep (cell-wise block Gauss-Seidel in red-black order,
+ * Sec. 1 of the paper names it beside block Jacobi): first every even cell is
+ * solved with the inflow of the current (old) odd cells, then every odd cell
+ * with the inflow of the just-updated even cells.  Psi_new starts as a copy of
+ * Psi_l and is updated in place; returns ||Psi_new - Psi_l||_2.              */
+double orc_rb_sweep(const orc_problem *p, const double *mu, const double *LU, const int32_t *piv,
+                    const double *psi_prev, const double *Psi_l, double *Psi_new) {
+  const size_t n = (size_t)4 * p->N * p->G;
+  memcpy(Psi_new, Psi_l, (size_t)p->J * n * sizeof(double));
+  double *b = (double *)malloc(n * sizeof(double));
+  for (int color = 0; color < 2; color++)
+    for (int j = color; j < p->J; j += 2) {
+      orc_rhs(p, mu, j, psi_prev, Psi_new, b);
+      orc_lu_solve((int32_t)n, LU + (size_t)j * n * n, piv + (size_t)j * n, b);
+      memcpy(Psi_new + (size_t)j * n, b, n * sizeof(double));
+    }
+  free(b);
+  double s = 0.0;
+  for (size_t i = 0; i < (size_t)p->J * n; i++) {
+    double d = Psi_new[i] - Psi_l[i];
+    s += d * d;
+  }
+  return sqrt(s);
+}
+
 /* Per-cell solve for a list of cells only (sampled checks at full size).      */
 int orc_oci_cells(const orc_problem *p, const double *mu, const double *w, const double *psi_prev,
                   const double *Psi_l, int32_t ncells, const int32_t *cells, double *out) {
@@ -467,7 +492,7 @@ static int stop_rule(int l, double e, double e_prev, double tol, double *rho) {
   return 0;
 }
 
-/* One time step by OCI (method 0) or SI (method 1).
+/* One time step by OCI (method 0), SI (method 1) or red-black OCI (method 2).
  *  Psi_io   in: the initial iterate Psi^(0) (the caller applies its guess policy)
  *           out: the last iterate (the converged Psi_k on success)
  *  psi_prev in: psi_{k-1/2}; out on success: psi_{k+1/2} = (Psi hL, Psi hR)
@@ -496,8 +521,9 @@ int orc_step(const orc_problem *p, int32_t method, double tol, int32_t max_iter,
   int conv = 0, l = 0;
   if (method == 1) orc_scalar_flux(p, w, Psi_io, phi_a);
   for (l = 0; l < max_iter; l++) {
-    if (method == 0) {
-      e = orc_oci_sweep(p, mu, LU, piv, psi_prev, Psi_io, Psi_a);
+    if (method == 0 || method == 2) {
+      e = method == 0 ? orc_oci_sweep(p, mu, LU, piv, psi_prev, Psi_io, Psi_a)
+                      : orc_rb_sweep(p, mu, LU, piv, psi_prev, Psi_io, Psi_a);
       memcpy(Psi_io, Psi_a, nPsi * sizeof(double));
     } else {
       e = orc_si_sweep(p, mu, w, psi_prev, phi_a, Psi_io, phi_b);
@@ -548,8 +574,9 @@ int orc_iterate(const orc_problem *p, int32_t method, int32_t n, const double *L
   if (method == 1) orc_scalar_flux(p, w, Psi_io, phi_a);
   for (int l = 0; l < n; l++) {
     double e;
-    if (method == 0) {
-      e = orc_oci_sweep(p, mu, LU, piv, psi_prev, Psi_io, Psi_a);
+    if (method == 0 || method == 2) {
+      e = method == 0 ? orc_oci_sweep(p, mu, LU, piv, psi_prev, Psi_io, Psi_a)
+                      : orc_rb_sweep(p, mu, LU, piv, psi_prev, Psi_io, Psi_a);
       memcpy(Psi_io, Psi_a, nPsi * sizeof(double));
     } else {
       e = orc_si_sweep(p, mu, w, psi_prev, phi_a, Psi_io, phi_b);

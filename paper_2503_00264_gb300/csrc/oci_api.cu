@@ -469,6 +469,7 @@ static int setup_impl(const oci_problem *p, oci_handle *h) {
     if ((rc = dense_setup(*h))) return rc;
   }
   CK(cudaFuncSetAttribute(k_oci_sweep_ptr(), cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  CK(cudaFuncSetAttribute(k_oci_sweep_rb_ptr(), cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   if (h->precision != OCI_FP64) {
     auto to32 = [](const std::vector<double> &a) {
       std::vector<float> f(a.size());
@@ -560,7 +561,7 @@ static void launch_body(Handle &h, bool si, cudaGraphConditionalHandle cond, int
     launch_finalize(h, h.partials, dense_partials(h), cond, use_cond);
   } else {
     launch_oci_sweep(h);
-    launch_finalize(h, h.partials, sweep_config(h).grid, cond, use_cond);
+    launch_finalize(h, h.partials, sweep_partials(h), cond, use_cond);
   }
 }
 
@@ -616,6 +617,7 @@ static int begin_iteration(Handle &h, int fixed, int cap) {
   d.n_refine = 0;
   d.theta = h.mx_theta;
   d.e_blk0 = 0.0;
+  d.inplace = h.ordering == OCI_ORDER_RED_BLACK && h.precision == OCI_FP64 && h.solver != OCI_SOLVER_DENSE_LU;
   CK(cudaMemcpyAsync(h.ds, h.h_ds, sizeof(DevState), cudaMemcpyHostToDevice, h.stream));
   return OCI_OK;
 }
@@ -924,6 +926,21 @@ int oci_get_e_hist(const oci_handle *h, double *e_hist, int32_t *n) {
     CK(cudaStreamSynchronize(h->stream));
   }
   return OCI_OK;
+}
+
+int oci_set_ordering(oci_handle *h, int32_t ordering) {
+  GUARD(h);
+  if (ordering != OCI_ORDER_JACOBI && ordering != OCI_ORDER_RED_BLACK)
+    return set_error("bad ordering"), OCI_E_INVAL;
+  if (ordering == OCI_ORDER_RED_BLACK && (h->precision != OCI_FP64 || h->solver == OCI_SOLVER_DENSE_LU))
+    return set_error("red-black ordering needs the FP64 structured solver"), OCI_E_INVAL;
+  if (ordering == h->ordering) return OCI_OK;
+  h->ordering = ordering;
+  if (h->g_oci) {
+    cudaGraphExecDestroy(h->g_oci);
+    h->g_oci = nullptr;
+  }
+  return build_graph(*h, false, &h->g_oci);
 }
 
 int oci_get_edges(const oci_handle *hc, double *left, double *right) {

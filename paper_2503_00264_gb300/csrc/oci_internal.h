@@ -42,6 +42,7 @@ struct DevState {
   int n_refine;   // refinements in this step
   double theta;   // refine once e < theta * (first e of the block)
   double e_blk0;
+  int inplace;    // 1: the sweep updates Psi[cur] in place (red-black ordering)
 };
 
 // Per-cell-type tables of the structured solve (all FP64, device).
@@ -66,6 +67,7 @@ struct Handle {
   int J = 0, N = 0, G = 0, n_mat = 0, Jp = 0;
   double dt = 0, tol = 0, t = 0;
   int max_iter = 0, precision = 0, guess = 0, solver = 0;
+  int ordering = OCI_ORDER_JACOBI;  // cell ordering of the FP64 structured sweep
   cudaStream_t stream = nullptr;
   int device = 0;
 
@@ -135,6 +137,8 @@ size_t sweep_smem(int N, int G, int cb, int P, size_t es);
 void launch_step_const(Handle &h);
 void launch_oci_sweep(Handle &h);
 const void *k_oci_sweep_ptr();
+const void *k_oci_sweep_rb_ptr();
+int sweep_partials(const Handle &h);
 void launch_finalize(Handle &h, const double *partials, int n, cudaGraphConditionalHandle cond,
                      int use_cond);
 void launch_carry(Handle &h);

@@ -10,7 +10,8 @@
 // so the serial dependency of the sweep is only the two outgoing edge values,
 //   u_{next} = z_j[out] + Cin_j[out,:] u_j       (2 dependent FMA levels per cell).
 // The sweep is split into a parallel pre-pass (z), a serial chain per (g,m)
-// (one thread each), and a parallel post-pass (psi, phi, ||phi^{l+1}-phi^l||^2).
+// (one block each, one walking thread fed from shared memory), and a parallel
+// post-pass (psi, phi, ||phi^{l+1}-phi^l||^2).
 #include <math.h>
 
 #include "oci_internal.h"
@@ -51,53 +52,82 @@ __global__ void k_si_pre(int J, int Jp, int N, int G, const int32_t *__restrict_
   }
 }
 
-// Serial chain of one (g,m): store the incoming edge of every cell.
-constexpr int kChainUnroll = 8;
-__global__ void k_si_chain(int J, int Jp, int N, int G, const int32_t *__restrict__ type,
-                           const double *__restrict__ Cin, const double *__restrict__ inc,
-                           const double *__restrict__ z, const DevState *__restrict__ ds,
-                           double *__restrict__ uin) {
-  const int gm = blockIdx.x * blockDim.x + threadIdx.x;
+// Serial chain of one (g,m), one block per chain: the block's threads stage the
+// next chunk of cells (the two outgoing rows of z and of Cin, in sweep order)
+// into shared memory while thread 0 walks the current chunk, so the walk sees
+// only shared-memory loads and its 2 dependent FMA levels per cell.  The
+// incoming edge of every cell is buffered and written back by all threads.
+constexpr int kChainChunk = 256;
+constexpr int kChainThreads = 128;
+__global__ void __launch_bounds__(kChainThreads) k_si_chain(int J, int Jp, int N, int G, const int32_t *__restrict__ type,
+                                                            const double *__restrict__ Cin,
+                                                            const double *__restrict__ inc,
+                                                            const double *__restrict__ z,
+                                                            const DevState *__restrict__ ds,
+                                                            double *__restrict__ uin) {
+  __shared__ double sa[2][kChainChunk], sb[2][kChainChunk], sc[2][4][kChainChunk];
+  __shared__ double su[2][kChainChunk];
+  const int gm = blockIdx.x;
   if (gm >= G * N || ds->done) return;
   const int m = gm % N;
-  const bool fwd = m >= N / 2;       // mu > 0: sweep j = 0 .. J-1
-  const int oa = fwd ? 1 : 0;         // outgoing rows: R corners (mu > 0) or L corners (mu < 0)
+  const bool fwd = m >= N / 2;  // mu > 0: sweep j = 0 .. J-1
+  const int oa = fwd ? 1 : 0;   // outgoing rows: R corners (mu > 0) or L corners (mu < 0)
   const int ob = fwd ? 3 : 2;
-  const double *incp = inc + (fwd ? 0 : (size_t)G * N * 2) + gm * 2;
-  double uk = incp[0], uh = incp[1];
   const double *za = z + (size_t)(gm * 4 + oa) * Jp;
   const double *zb = z + (size_t)(gm * 4 + ob) * Jp;
   double *uk_out = uin + (size_t)(gm * 2 + 0) * Jp;
   double *uh_out = uin + (size_t)(gm * 2 + 1) * Jp;
-  for (int s0 = 0; s0 < J; s0 += kChainUnroll) {
-    double a[kChainUnroll], b[kChainUnroll], c[kChainUnroll][4];
-#pragma unroll
-    for (int k = 0; k < kChainUnroll; k++) {
-      const int s = s0 + k;
+  const int nchunk = (J + kChainChunk - 1) / kChainChunk;
+  auto stage = [&](int ck, int buf) {
+    for (int i = threadIdx.x; i < kChainChunk; i += kChainThreads) {
+      const int s = ck * kChainChunk + i;
       if (s < J) {
         const int j = fwd ? s : J - 1 - s;
-        a[k] = za[j];
-        b[k] = zb[j];
+        sa[buf][i] = za[j];
+        sb[buf][i] = zb[j];
         const double *C = Cin + ((size_t)type[j] * G * N + gm) * 8;
-        c[k][0] = C[oa * 2 + 0];
-        c[k][1] = C[oa * 2 + 1];
-        c[k][2] = C[ob * 2 + 0];
-        c[k][3] = C[ob * 2 + 1];
+        sc[buf][0][i] = C[oa * 2 + 0];
+        sc[buf][1][i] = C[oa * 2 + 1];
+        sc[buf][2][i] = C[ob * 2 + 0];
+        sc[buf][3][i] = C[ob * 2 + 1];
       }
     }
-#pragma unroll
-    for (int k = 0; k < kChainUnroll; k++) {
-      const int s = s0 + k;
+  };
+  auto flush = [&](int ck, int buf) {  // write back the incoming edges of chunk ck
+    for (int i = threadIdx.x; i < kChainChunk; i += kChainThreads) {
+      const int s = ck * kChainChunk + i;
       if (s < J) {
         const int j = fwd ? s : J - 1 - s;
-        uk_out[j] = uk;
-        uh_out[j] = uh;
-        const double nk = fma(c[k][1], uh, fma(c[k][0], uk, a[k]));
-        const double nh = fma(c[k][3], uh, fma(c[k][2], uk, b[k]));
+        uk_out[j] = su[buf][i];
+      }
+    }
+  };
+  const double *incp = inc + (fwd ? 0 : (size_t)G * N * 2) + gm * 2;
+  double uk = incp[0], uh = incp[1];
+  stage(0, 0);
+  __syncthreads();
+  __shared__ double suh[2][kChainChunk];
+  for (int ck = 0; ck < nchunk; ck++) {
+    const int buf = ck & 1;
+    if (ck + 1 < nchunk) stage(ck + 1, buf ^ 1);
+    if (threadIdx.x == 0) {
+      const int cnt = min(kChainChunk, J - ck * kChainChunk);
+      for (int i = 0; i < cnt; i++) {
+        su[buf][i] = uk;
+        suh[buf][i] = uh;
+        const double nk = fma(sc[buf][1][i], uh, fma(sc[buf][0][i], uk, sa[buf][i]));
+        const double nh = fma(sc[buf][3][i], uh, fma(sc[buf][2][i], uk, sb[buf][i]));
         uk = nk;
         uh = nh;
       }
     }
+    __syncthreads();
+    flush(ck, buf);
+    for (int i = threadIdx.x; i < kChainChunk; i += kChainThreads) {
+      const int s = ck * kChainChunk + i;
+      if (s < J) uh_out[fwd ? s : J - 1 - s] = suh[buf][i];
+    }
+    __syncthreads();
   }
 }
 
@@ -174,9 +204,8 @@ void launch_si_sweep(Handle &h) {
   dim3 g1((h.J + 255) / 256, h.G);
   k_si_pre<<<g1, 256, 0, h.stream>>>(h.J, h.Jp, h.N, h.G, h.type, h.tt.dx, h.tt.Kap, h.v, h.dt, h.Q, h.psi_prev,
                                      h.tt.Linv, h.phi_si[0], h.phi_si[1], h.ds, h.si_z);
-  const int chains = h.G * h.N;
-  k_si_chain<<<(chains + 31) / 32, 32, 0, h.stream>>>(h.J, h.Jp, h.N, h.G, h.type, h.tt.Cin, h.inc, h.si_z, h.ds,
-                                                      h.si_uin);
+  k_si_chain<<<h.G * h.N, kChainThreads, 0, h.stream>>>(h.J, h.Jp, h.N, h.G, h.type, h.tt.Cin, h.inc, h.si_z, h.ds,
+                                                          h.si_uin);
   k_si_post<<<g1, 256, 0, h.stream>>>(h.J, h.Jp, h.N, h.G, h.type, h.tt.Cin, h.w, h.si_z, h.si_uin, h.Psi[0],
                                       h.Psi[1], h.phi_si[0], h.phi_si[1], h.ds, h.partials);
 }

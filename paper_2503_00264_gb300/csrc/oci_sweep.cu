@@ -63,23 +63,35 @@ __device__ __forceinline__ double block_sum(double v, double *red) {
 // ------------------------------------------------------------------ a2..a4
 // One OCI sweep.  Block = CB cells x (G groups x P angle chunks); thread
 // (cell, g, c) handles the angles m in [c N/P, (c+1) N/P) of group g.
-// Reads Psi[cur], writes Psi[cur^1] and this block's sum of (Psi_new - Psi_old)^2.
+// Block Jacobi (RB = false): reads Psi[cur], writes Psi[cur^1].
+// Red-black (RB = true, half sweep of one colour): thread i handles cell
+// 2i + colour and updates Psi[cur] in place -- its neighbours have the other
+// colour and are not written by this launch; red-black uses one plain pointer so
+// that the compiler keeps each cell's read of its old value before its write.
+// Writes this block's sum of (Psi_new - Psi_old)^2 (per colour for red-black).
 // Shared memory: t [G*N*4][CB], partial y [G*P*4][CB], reduction scratch.
-__global__ void __launch_bounds__(256) k_oci_sweep(
-    int J, int Jp, int N, int G, int P, const int32_t *__restrict__ type, const double *__restrict__ Linv,
-    const double *__restrict__ Cin, const double *__restrict__ Mp, const double *__restrict__ w,
-    const double *__restrict__ inc, const double *__restrict__ tc, double *Psi0, double *Psi1,
-    const DevState *__restrict__ ds, double *__restrict__ partials) {
+template <bool RB>
+__global__ void __launch_bounds__(256) k_oci_sweep_t(
+    int J, int Jp, int N, int G, int P, int color, const int32_t *__restrict__ type,
+    const double *__restrict__ Linv, const double *__restrict__ Cin, const double *__restrict__ Mp,
+    const double *__restrict__ w, const double *__restrict__ inc, const double *__restrict__ tc, double *Psi0,
+    double *Psi1, const DevState *__restrict__ ds, double *__restrict__ partials) {
   extern __shared__ double sm[];
   const int CB = blockDim.x;
   const int cl = threadIdx.x, gy = threadIdx.y;
   const int g = gy / P, ch = gy % P;
   const int NP = N / P, m0 = ch * NP;
-  const int j = blockIdx.x * CB + cl;
+  const int j = RB ? 2 * (blockIdx.x * CB + cl) + color : blockIdx.x * CB + cl;
   if (ds->done) return;  // uniform across the grid
   const int cur = ds->cur;
-  const double *__restrict__ Pin = cur ? Psi1 : Psi0;
-  double *__restrict__ Pout = cur ? Psi0 : Psi1;
+  double *Pself = cur ? Psi1 : Psi0;
+  const double *__restrict__ PinJ = cur ? Psi1 : Psi0;
+  double *__restrict__ PoutJ = cur ? Psi0 : Psi1;
+  auto Pin = [&](size_t i) -> double { return RB ? Pself[i] : PinJ[i]; };
+  auto Pput = [&](size_t i, double v) {
+    if (RB) Pself[i] = v;
+    else PoutJ[i] = v;
+  };
   double *t_s = sm;
   double *y_s = sm + (size_t)G * N * 4 * CB;
   double *red = y_s + (size_t)G * P * 4 * CB;
@@ -97,16 +109,16 @@ __global__ void __launch_bounds__(256) k_oci_sweep(
       double uk, uh;
       if (m >= N2) {  // mu > 0: upstream edge is the R corner of cell j-1
         if (j > 0) {
-          uk = Pin[base + 1 * (size_t)Jp - 1];
-          uh = Pin[base + 3 * (size_t)Jp - 1];
+          uk = Pin(base + 1 * (size_t)Jp - 1);
+          uh = Pin(base + 3 * (size_t)Jp - 1);
         } else {
           uk = inc[gm * 2 + 0];
           uh = inc[gm * 2 + 1];
         }
       } else {  // mu < 0: upstream edge is the L corner of cell j+1
         if (j < J - 1) {
-          uk = Pin[base + 0 * (size_t)Jp + 1];
-          uh = Pin[base + 2 * (size_t)Jp + 1];
+          uk = Pin(base + 0 * (size_t)Jp + 1);
+          uh = Pin(base + 2 * (size_t)Jp + 1);
         } else {
           uk = inc[(G * N + gm) * 2 + 0];
           uh = inc[(G * N + gm) * 2 + 1];
@@ -160,19 +172,23 @@ __global__ void __launch_bounds__(256) k_oci_sweep(
 #pragma unroll
       for (int p = 0; p < 4; p++)
         o[p] = fma(L[p * 4 + 3], s3, fma(L[p * 4 + 2], s2, fma(L[p * 4 + 1], s1, fma(L[p * 4 + 0], s0, ts[p * CB]))));
+      double old[4];
+#pragma unroll
+      for (int p = 0; p < 4; p++) old[p] = Pin(base + (size_t)p * Jp);
 #pragma unroll
       for (int p = 0; p < 4; p++) {
-        const double d = o[p] - Pin[base + (size_t)p * Jp];
+        const double d = o[p] - old[p];
         e2 = fma(d, d, e2);
-        Pout[base + (size_t)p * Jp] = o[p];
+        Pput(base + (size_t)p * Jp, o[p]);
       }
     }
   }
   const double bs = block_sum(e2, red);
-  if (threadIdx.x == 0 && threadIdx.y == 0) partials[blockIdx.x] = bs;
+  if (threadIdx.x == 0 && threadIdx.y == 0) partials[blockIdx.x + (RB ? color * gridDim.x : 0)] = bs;
 }
 
-const void *k_oci_sweep_ptr() { return (const void *)k_oci_sweep; }
+const void *k_oci_sweep_ptr() { return (const void *)k_oci_sweep_t<false>; }
+const void *k_oci_sweep_rb_ptr() { return (const void *)k_oci_sweep_t<true>; }
 
 size_t sweep_smem(int N, int G, int cb, int P, size_t es) {
   return (size_t)cb * ((size_t)G * N * 4 + (size_t)G * P * 4) * es + 64 * sizeof(double);
@@ -204,8 +220,28 @@ void launch_step_const(Handle &h) {
 void launch_oci_sweep(Handle &h) {
   SweepCfg c = sweep_config(h);
   dim3 block(c.cells_per_block, h.G * c.chunks);
-  k_oci_sweep<<<c.grid, block, c.smem, h.stream>>>(h.J, h.Jp, h.N, h.G, c.chunks, h.type, h.tt.Linv, h.tt.Cin, h.tt.Mp,
-                                                   h.w, h.inc, h.tc, h.Psi[0], h.Psi[1], h.ds, h.partials);
+  if (h.ordering == OCI_ORDER_RED_BLACK) {
+    // two half sweeps, even cells then odd cells, each over ceil(J/2) threads
+    const int half = (h.J + 1) / 2;
+    const int grid = (half + c.cells_per_block - 1) / c.cells_per_block;
+    for (int color = 0; color < 2; color++)
+      k_oci_sweep_t<true><<<grid, block, c.smem, h.stream>>>(h.J, h.Jp, h.N, h.G, c.chunks, color, h.type, h.tt.Linv,
+                                                             h.tt.Cin, h.tt.Mp, h.w, h.inc, h.tc, h.Psi[0], h.Psi[1],
+                                                             h.ds, h.partials);
+    return;
+  }
+  k_oci_sweep_t<false><<<c.grid, block, c.smem, h.stream>>>(h.J, h.Jp, h.N, h.G, c.chunks, -1, h.type, h.tt.Linv,
+                                                            h.tt.Cin, h.tt.Mp, h.w, h.inc, h.tc, h.Psi[0], h.Psi[1],
+                                                            h.ds, h.partials);
+}
+
+int sweep_partials(const Handle &h) {
+  SweepCfg c = sweep_config(h);
+  if (h.ordering == OCI_ORDER_RED_BLACK) {
+    const int half = (h.J + 1) / 2;
+    return 2 * ((half + c.cells_per_block - 1) / c.cells_per_block);
+  }
+  return c.grid;
 }
 
 // ------------------------------------------------------------------ a4, a5
@@ -249,7 +285,7 @@ __global__ void __launch_bounds__(kFinalizeThreads) k_finalize(const double *__r
     d.rho = rho;
     d.e_prev = e;
     d.l = l + 1;
-    d.cur ^= 1;
+    if (!d.inplace) d.cur ^= 1;
     if (!d.fixed && !d.done) {
       if (conv) {
         d.status = OCI_OK;

@@ -22,10 +22,11 @@ OK, E_INVAL, E_NOMEM, E_CUDA, E_NOCONV, E_SINGULAR, E_NONFINITE, E_TIMEOUT, E_ST
 FP64, TF32_IR, BF16X3_IR, FP32_IR = 0, 1, 2, 3
 GUESS_PREV, GUESS_ZERO = 0, 1
 SOLVER_AUTO, SOLVER_STRUCTURED, SOLVER_DENSE_LU = 0, 1, 2
+ORDER_JACOBI, ORDER_RED_BLACK = 0, 1
 
 EXPORTS = ["oci_setup", "oci_step", "oci_solve_transient", "si_sweep", "oci_iterate", "si_iterate",
            "oci_get_psi", "oci_set_psi", "oci_get_phi", "oci_get_state", "oci_set_state", "oci_get_balance",
-           "oci_set_boundary", "oci_get_e_hist", "oci_get_edges", "oci_commit", "oci_destroy", "oci_last_error",
+           "oci_set_boundary", "oci_set_ordering", "oci_get_e_hist", "oci_get_edges", "oci_commit", "oci_destroy", "oci_last_error",
            "oci_probe_fp64_peak", "oci_batch_setup", "oci_batch_step", "oci_batch_size", "oci_batch_get_psi",
            "oci_batch_get_phi", "oci_batch_get_balance"]
 
@@ -82,6 +83,7 @@ def load(path: Optional[str] = None):
     L.oci_set_boundary.argtypes = [vp, vp, vp]
     L.oci_get_e_hist.argtypes = [vp, vp, ctypes.POINTER(i32)]
     L.oci_get_edges.argtypes = [vp, vp, vp]
+    L.oci_set_ordering.argtypes = [vp, i32]
     L.oci_commit.argtypes = [vp, ctypes.POINTER(Stats)]
     L.oci_destroy.argtypes = [vp]
     L.oci_destroy.restype = None
@@ -292,6 +294,9 @@ class Solver:
         out = np.zeros(max(n.value, 1))
         _check(self.L.oci_get_e_hist(self.h, _ptr(out, writable=True), ctypes.byref(n)))
         return out[: n.value]
+
+    def set_ordering(self, ordering: int):
+        _check(self.L.oci_set_ordering(self.h, int(ordering)))
 
     def edges(self):
         left = np.zeros((self.G, self.N, 2))

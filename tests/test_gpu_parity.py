@@ -186,3 +186,29 @@ def test_full_size_step_balance():
         st = s.step()
         assert st["status"] == 0
         assert max(st["balance_rel"]) < 1e-9
+
+
+@pytest.mark.parametrize("seed,J,N,G", [(51, 33, 8, 1), (52, 129, 8, 2), (53, 1, 4, 1), (54, 300, 16, 1)])
+def test_red_black_ordering_matches_oracle(seed, J, N, G):
+    """Red-black OCI (block Gauss-Seidel in red-black cell order) against the
+    oracle's red-black sweep: same sweep counts, flux within 1e-12."""
+    from oracle import RB
+    p = W.random_slab(seed, J, N, G).replace(tol=1e-11)
+    o = Oracle(p)
+    with oci.Solver(p) as s:
+        s.set_ordering(oci.ORDER_RED_BLACK)
+        for k in range(2):
+            r = o.step(RB)
+            st = s.step()
+            assert st["status"] == 0 and st["iters"] == r["iters"], (st["iters"], r["iters"])
+            assert rel(s.phi(), r["phi"]) < 1e-12
+            assert rel(s.psi(), r["Psi"]) < 1e-11
+
+
+def test_red_black_full_size_fewer_sweeps_same_answer():
+    p = W.slab_3region(c=0.9, tau=0.1)
+    with oci.Solver(p) as a, oci.Solver(p) as b:
+        b.set_ordering(oci.ORDER_RED_BLACK)
+        sa, sb = a.step(), b.step()
+        assert sb["iters"] < 0.7 * sa["iters"]
+        assert rel(b.phi(), a.phi()) < 1e-9

@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 import oracle
-from oracle import OCI, SI, Oracle, balance_residual
+from oracle import OCI, RB, SI, Oracle, balance_residual
 from oracle import brute
 from oracle import fourier as F
 from paper_2503_00264_gb300 import workloads as W
@@ -346,3 +346,46 @@ def test_iteration_counts_fall_with_mean_free_time():
         rhos.append(F.spectral_radius("oci", N, 0.3, tau, 0.9, n_theta=61))
     assert all(a > b for a, b in zip(counts, counts[1:])), counts
     assert all(a > b for a, b in zip(rhos, rhos[1:])), rhos
+
+
+# ------------------------------------------------- red-black ordering (block GS)
+@pytest.mark.parametrize("seed,J,N,G", CASES[1:4])
+def test_red_black_converges_to_global_solve(seed, J, N, G):
+    """Red-black OCI has the fixed point of the discrete system (same as block
+    Jacobi OCI); only the order of the cell solves differs."""
+    p = W.random_slab(seed, J, N, G)
+    o = Oracle(p)
+    ref = brute.transient(p, 2)
+    for k in range(2):
+        r = o.step(RB, tol=1e-12)
+        assert r["status"] == 0
+        assert _rel(r["Psi"], ref[k]) < 1e-11
+
+
+def test_red_black_rate_is_jacobi_rate_squared():
+    """The cell coupling is block tridiagonal (block 2-cyclic), so red-black
+    block Gauss-Seidel is consistently ordered and its asymptotic rate is the
+    square of block Jacobi's (Young's theorem); measured on a long slab."""
+    J = 400
+    p = W.Problem(J=J, N=8, G=1, n_mat=1, dx=np.full(J, 0.1), mat=np.zeros(J, np.int32), sigma_t=[[1.0]],
+                  sigma_s=[[[0.9]]], v=[1.0], dt=1.0, tol=1e-30, max_iter=400)
+    rates = {}
+    for method in (OCI, RB):
+        o = Oracle(p)
+        o.Psi[...] = W.random_guess(p, 4)
+        e = o.iterate(160, method=method)
+        rates[method] = np.exp(np.mean(np.log(e[120:160] / e[119:159])))
+    assert abs(rates[RB] - rates[OCI] ** 2) < 0.02 * rates[OCI] ** 2, rates
+
+
+def test_red_black_c0_exact_in_fewer_sweeps():
+    """Without scattering information still moves one red-black pair of cells
+    per half sweep in the direction of flight, so the exact solution is reached
+    in at most about half the Jacobi sweep count."""
+    J, N = 20, 4
+    p = W.Problem(J=J, N=N, G=1, n_mat=1, dx=np.full(J, 0.3), mat=np.zeros(J, np.int32), sigma_t=[[1.0]],
+                  sigma_s=[[[0.0]]], v=[1.0], dt=0.5, Q=np.ones((J, 1, 4)),
+                  inc_left=W.isotropic_inflow(1, N, 1.0, "left"), tol=0.0)
+    r = Oracle(p).step(RB, tol=0.0, guess=1)
+    assert r["status"] == 0 and r["e"] == 0.0
+    assert r["iters"] <= J // 2 + 2
