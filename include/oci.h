@@ -238,6 +238,24 @@ int oci_batch_get_psi(const oci_handle *h, int32_t s, double *psi);
 int oci_batch_get_phi(const oci_handle *h, int32_t s, double *phi);
 int oci_batch_get_balance(const oci_handle *h, int32_t s, double *bal);
 
+/* Convergence norm e = ||a - b||_2 over n FP64 values, for callers that cannot
+ * allocate device memory when they need it (allocator callbacks, loops whose
+ * memory is budgeted once at start-up, applications whose device memory is
+ * owned by another framework).  The paper has no counterpart: this is a
+ * standalone form of the norm of Sec. 2.1 that oci_step takes internally.
+ *   a, b   device pointers to n values each (any layout, same for both)
+ *   n      0 <= n <= 33,554,432 (the fixed scratch holds 16,384 partial sums of
+ *          2,048 values each); larger n returns OCI_E_INVAL
+ *   e_out  device pointer; receives e when the stream reaches it
+ *   stream cudaStream_t or NULL (legacy default stream); the call returns
+ *          without waiting for the GPU
+ * Nothing is allocated: the partial sums live in one fixed 128 KiB device array
+ * per GPU, held until the process exits.  The first call on a device looks up
+ * that array's device address (cudaGetSymbolAddress); make that first call
+ * before capturing a stream.  Calls that overlap on the GPU share the array
+ * and race; the result is deterministic for a given n. */
+int oci_diff_norm_noalloc(const double *a, const double *b, int64_t n, double *e_out, void *stream);
+
 /* Release the handle and its device memory.  NULL is accepted. */
 void oci_destroy(oci_handle *h);
 

@@ -28,7 +28,7 @@ EXPORTS = ["oci_setup", "oci_step", "oci_solve_transient", "si_sweep", "oci_iter
            "oci_get_psi", "oci_set_psi", "oci_get_phi", "oci_get_state", "oci_set_state", "oci_get_balance",
            "oci_set_boundary", "oci_set_ordering", "oci_get_e_hist", "oci_get_edges", "oci_commit", "oci_destroy", "oci_last_error",
            "oci_probe_fp64_peak", "oci_batch_setup", "oci_batch_step", "oci_batch_size", "oci_batch_get_psi",
-           "oci_batch_get_phi", "oci_batch_get_balance"]
+           "oci_batch_get_phi", "oci_batch_get_balance", "oci_diff_norm_noalloc"]
 
 
 class OCIError(RuntimeError):
