@@ -100,6 +100,17 @@ enum {
                               one sweep = both halves                                      */
 };
 
+/* how si_sweep / si_iterate march through the cells (oci_set_si_mode) */
+enum {
+  OCI_SI_SEQUENTIAL = 0,  /* the paper's SI: each (g,m) sweeps the cells one after another
+                             (Algorithm 1), here one GPU thread per (g,m) fed from shared memory */
+  OCI_SI_SCAN = 1         /* the same sweep as a parallel scan: the outgoing edge of a cell is
+                             an affine function of its incoming edge, affine maps compose
+                             associatively, so segments of cells are composed in parallel, the
+                             segment maps are scanned, and every segment is walked again from
+                             its incoming edge (identical result up to rounding)              */
+};
+
 /* Problem description -- the arguments of Eq. sn_nte plus the iteration
  * controls of Sec. 2.1.  Sizes: J cells, N ordinates, G groups. */
 typedef struct {
@@ -199,6 +210,9 @@ int oci_get_e_hist(const oci_handle *h, double *e_hist, int32_t *n);
  * Red-black needs the FP64 structured solver (else OCI_E_INVAL).  The norm and
  * the stop rule are those of Sec. 2.1 over one full (red + black) sweep. */
 int oci_set_ordering(oci_handle *h, int32_t ordering);
+
+/* March of the following SI sweeps (OCI_SI_*; default sequential). */
+int oci_set_si_mode(oci_handle *h, int32_t mode);
 
 /* Edge values for a domain-decomposed driver (Sec. 4 of the paper proposes
  * exchanging them between subdomains every iteration): left [G][N][2] receives

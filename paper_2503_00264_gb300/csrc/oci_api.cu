@@ -362,7 +362,7 @@ static void free_handle(Handle *h) {
                   h->tt.Cin, h->tt.Mp,  h->tt.Kap,    h->tt.dx,     h->tt.sig,       h->si_z,      h->si_uin,
                   h->LU,     h->piv,    h->partials,  h->bal_partials, h->bal,       h->e_hist,    h->ds,
                   h->stage,  h->delta[0], h->delta[1], h->z32, h->w32, h->tt.Lco, h->tt.Linv32, h->tt.Cin32,
-                  h->tt.Mp32, h->tc_img};
+                  h->tt.Mp32, h->tc_img, h->si_maps, h->si_segin};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (h->h_ds) cudaFreeHost(h->h_ds);
@@ -834,11 +834,15 @@ int oci_solve_transient(oci_handle *h, int32_t n_steps, double *phi_out, oci_sta
 
 static int ensure_si(Handle &h) {
   if (h.g_si) return OCI_OK;
+  if (h.si_z) return build_graph(h, true, &h.g_si);
   const size_t G = h.G, N = h.N, Jp = h.Jp;
   CK(cudaMalloc(&h.si_z, G * N * 4 * Jp * 8));
   CK(cudaMalloc(&h.si_uin, G * N * 2 * Jp * 8));
   CK(cudaMalloc(&h.phi_si[0], G * 4 * Jp * 8));
   CK(cudaMalloc(&h.phi_si[1], G * 4 * Jp * 8));
+  const size_t nm = si_scan_maps(h);
+  CK(cudaMalloc(&h.si_maps, nm * 6 * 8));
+  CK(cudaMalloc(&h.si_segin, nm * 2 * 8));
   return build_graph(h, true, &h.g_si);
 }
 
@@ -941,6 +945,19 @@ int oci_set_ordering(oci_handle *h, int32_t ordering) {
     h->g_oci = nullptr;
   }
   return build_graph(*h, false, &h->g_oci);
+}
+
+int oci_set_si_mode(oci_handle *h, int32_t mode) {
+  GUARD(h);
+  if (mode != OCI_SI_SEQUENTIAL && mode != OCI_SI_SCAN) return set_error("bad SI mode"), OCI_E_INVAL;
+  if (mode == h->si_mode) return OCI_OK;
+  h->si_mode = mode;
+  if (h->g_si) {
+    cudaGraphExecDestroy(h->g_si);
+    h->g_si = nullptr;
+    return build_graph(*h, true, &h->g_si);
+  }
+  return OCI_OK;
 }
 
 int oci_get_edges(const oci_handle *hc, double *left, double *right) {

@@ -99,6 +99,9 @@ struct Handle {
   // SI scratch
   double *si_z = nullptr;        // [G][N][4][Jp]   Linv * d0
   double *si_uin = nullptr;      // [G][N][2][Jp]   incoming edge of every cell
+  double *si_maps = nullptr;     // [G*N][K][6]     scan form: segment affine maps
+  double *si_segin = nullptr;    // [G*N][K][2]     scan form: incoming edge of each segment
+  int si_mode = 0;               // 0 sequential chain (the paper's SI), 1 scan form
   // dense path
   double *LU = nullptr;          // [J][n][n] column-major per cell
   int32_t *piv = nullptr;        // [J][n]
@@ -149,6 +152,7 @@ void launch_edges(Handle &h, const double *Psi, double *out);
 // SI
 void launch_si_sweep(Handle &h);
 void launch_si_phi_from_psi(Handle &h, double *phi_dst);
+size_t si_scan_maps(const Handle &h);
 // mixed-precision form
 void launch_mx_inner(Handle &h);
 void launch_mx_outer(Handle &h, int mode);

@@ -131,6 +131,117 @@ __global__ void __launch_bounds__(kChainThreads) k_si_chain(int J, int Jp, int N
   }
 }
 
+// ---------------------------------------------------------------- scan form
+// The chain of one (g,m) is a composition of affine maps of the outgoing edge,
+//   u_{s+1} = F_s(u_s) = B_s u_s + a_s,   B_s = Cin_j[out rows], a_s = z_j[out rows],
+// and affine maps compose associatively: (F2 o F1)(u) = B2 B1 u + (B2 a1 + a2).
+// The scan form computes the same incoming edges in three parallel passes:
+//   1. every segment of kScanSeg cells (one thread per (g,m), segment) composes
+//      its maps into one affine map;
+//   2. one thread per (g,m) applies the segment maps in order to get each
+//      segment's incoming edge;
+//   3. every segment walks its cells again from its incoming edge.
+// The result equals the sequential sweep up to rounding (a different
+// association of the same products).
+constexpr int kScanSeg = 128;
+
+__device__ __forceinline__ void si_cell_map(int j, int gm, int G, int N, int oa, int ob,
+                                            const int32_t *__restrict__ type, const double *__restrict__ Cin,
+                                            const double *__restrict__ za, const double *__restrict__ zb,
+                                            double B[4], double a[2]) {
+  const double *C = Cin + ((size_t)type[j] * G * N + gm) * 8;
+  B[0] = C[oa * 2 + 0];
+  B[1] = C[oa * 2 + 1];
+  B[2] = C[ob * 2 + 0];
+  B[3] = C[ob * 2 + 1];
+  a[0] = za[j];
+  a[1] = zb[j];
+}
+
+__global__ void k_si_seg_maps(int J, int Jp, int N, int G, const int32_t *__restrict__ type,
+                              const double *__restrict__ Cin, const double *__restrict__ z,
+                              const DevState *__restrict__ ds, double *__restrict__ maps) {
+  const int K = (J + kScanSeg - 1) / kScanSeg;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= G * N * K || ds->done) return;
+  const int gm = tid / K, seg = tid % K;
+  const int m = gm % N;
+  const bool fwd = m >= N / 2;
+  const int oa = fwd ? 1 : 0, ob = fwd ? 3 : 2;
+  const double *za = z + (size_t)(gm * 4 + oa) * Jp;
+  const double *zb = z + (size_t)(gm * 4 + ob) * Jp;
+  double M0 = 1.0, M1 = 0.0, M2 = 0.0, M3 = 1.0, m0 = 0.0, m1 = 0.0;  // identity map
+  const int s1 = min(J, (seg + 1) * kScanSeg);
+  for (int s = seg * kScanSeg; s < s1; s++) {
+    const int j = fwd ? s : J - 1 - s;
+    double B[4], a[2];
+    si_cell_map(j, gm, G, N, oa, ob, type, Cin, za, zb, B, a);
+    // M <- F_s o M
+    const double n0 = fma(B[0], M0, B[1] * M2), n1 = fma(B[0], M1, B[1] * M3);
+    const double n2 = fma(B[2], M0, B[3] * M2), n3 = fma(B[2], M1, B[3] * M3);
+    const double v0 = fma(B[0], m0, fma(B[1], m1, a[0]));
+    const double v1 = fma(B[2], m0, fma(B[3], m1, a[1]));
+    M0 = n0; M1 = n1; M2 = n2; M3 = n3; m0 = v0; m1 = v1;
+  }
+  double *o = maps + (size_t)tid * 6;
+  o[0] = M0; o[1] = M1; o[2] = M2; o[3] = M3; o[4] = m0; o[5] = m1;
+}
+
+__global__ void k_si_seg_scan(int J, int N, int G, const double *__restrict__ inc, const double *__restrict__ maps,
+                              const DevState *__restrict__ ds, double *__restrict__ segin) {
+  const int K = (J + kScanSeg - 1) / kScanSeg;
+  const int gm = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gm >= G * N || ds->done) return;
+  const int m = gm % N;
+  const bool fwd = m >= N / 2;
+  const double *incp = inc + (fwd ? 0 : (size_t)G * N * 2) + gm * 2;
+  double uk = incp[0], uh = incp[1];
+  for (int seg = 0; seg < K; seg++) {
+    const double *M = maps + ((size_t)gm * K + seg) * 6;
+    segin[((size_t)gm * K + seg) * 2 + 0] = uk;
+    segin[((size_t)gm * K + seg) * 2 + 1] = uh;
+    const double nk = fma(M[0], uk, fma(M[1], uh, M[4]));
+    const double nh = fma(M[2], uk, fma(M[3], uh, M[5]));
+    uk = nk;
+    uh = nh;
+  }
+}
+
+__global__ void k_si_seg_walk(int J, int Jp, int N, int G, const int32_t *__restrict__ type,
+                              const double *__restrict__ Cin, const double *__restrict__ z,
+                              const double *__restrict__ segin, const DevState *__restrict__ ds,
+                              double *__restrict__ uin) {
+  const int K = (J + kScanSeg - 1) / kScanSeg;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= G * N * K || ds->done) return;
+  const int gm = tid / K, seg = tid % K;
+  const int m = gm % N;
+  const bool fwd = m >= N / 2;
+  const int oa = fwd ? 1 : 0, ob = fwd ? 3 : 2;
+  const double *za = z + (size_t)(gm * 4 + oa) * Jp;
+  const double *zb = z + (size_t)(gm * 4 + ob) * Jp;
+  double *uk_out = uin + (size_t)(gm * 2 + 0) * Jp;
+  double *uh_out = uin + (size_t)(gm * 2 + 1) * Jp;
+  double uk = segin[(size_t)tid * 2 + 0], uh = segin[(size_t)tid * 2 + 1];
+  const int s1 = min(J, (seg + 1) * kScanSeg);
+  for (int s = seg * kScanSeg; s < s1; s++) {
+    const int j = fwd ? s : J - 1 - s;
+    double B[4], a[2];
+    si_cell_map(j, gm, G, N, oa, ob, type, Cin, za, zb, B, a);
+    uk_out[j] = uk;
+    uh_out[j] = uh;
+    const double nk = fma(B[1], uh, fma(B[0], uk, a[0]));
+    const double nh = fma(B[3], uh, fma(B[2], uk, a[1]));
+    uk = nk;
+    uh = nh;
+  }
+}
+
+size_t si_scan_maps(const Handle &h) {
+  const size_t K = (h.J + kScanSeg - 1) / kScanSeg;
+  return (size_t)h.G * h.N * K;
+}
+
 // psi_j = z_j + Cin_j u_j for all (g,m); phi^{l+1}; block sum of (phi^{l+1} - phi^l)^2.
 __global__ void __launch_bounds__(256) k_si_post(int J, int Jp, int N, int G, const int32_t *__restrict__ type,
                                                  const double *__restrict__ Cin, const double *__restrict__ w,
@@ -204,8 +315,17 @@ void launch_si_sweep(Handle &h) {
   dim3 g1((h.J + 255) / 256, h.G);
   k_si_pre<<<g1, 256, 0, h.stream>>>(h.J, h.Jp, h.N, h.G, h.type, h.tt.dx, h.tt.Kap, h.v, h.dt, h.Q, h.psi_prev,
                                      h.tt.Linv, h.phi_si[0], h.phi_si[1], h.ds, h.si_z);
-  k_si_chain<<<h.G * h.N, kChainThreads, 0, h.stream>>>(h.J, h.Jp, h.N, h.G, h.type, h.tt.Cin, h.inc, h.si_z, h.ds,
-                                                          h.si_uin);
+  if (h.si_mode == OCI_SI_SCAN) {
+    const int nmaps = (int)si_scan_maps(h);
+    k_si_seg_maps<<<(nmaps + 127) / 128, 128, 0, h.stream>>>(h.J, h.Jp, h.N, h.G, h.type, h.tt.Cin, h.si_z, h.ds,
+                                                             h.si_maps);
+    k_si_seg_scan<<<(h.G * h.N + 31) / 32, 32, 0, h.stream>>>(h.J, h.N, h.G, h.inc, h.si_maps, h.ds, h.si_segin);
+    k_si_seg_walk<<<(nmaps + 127) / 128, 128, 0, h.stream>>>(h.J, h.Jp, h.N, h.G, h.type, h.tt.Cin, h.si_z,
+                                                             h.si_segin, h.ds, h.si_uin);
+  } else {
+    k_si_chain<<<h.G * h.N, kChainThreads, 0, h.stream>>>(h.J, h.Jp, h.N, h.G, h.type, h.tt.Cin, h.inc, h.si_z,
+                                                            h.ds, h.si_uin);
+  }
   k_si_post<<<g1, 256, 0, h.stream>>>(h.J, h.Jp, h.N, h.G, h.type, h.tt.Cin, h.w, h.si_z, h.si_uin, h.Psi[0],
                                       h.Psi[1], h.phi_si[0], h.phi_si[1], h.ds, h.partials);
 }

@@ -23,10 +23,11 @@ FP64, TF32_IR, BF16X3_IR, FP32_IR = 0, 1, 2, 3
 GUESS_PREV, GUESS_ZERO = 0, 1
 SOLVER_AUTO, SOLVER_STRUCTURED, SOLVER_DENSE_LU = 0, 1, 2
 ORDER_JACOBI, ORDER_RED_BLACK = 0, 1
+SI_SEQUENTIAL, SI_SCAN = 0, 1
 
 EXPORTS = ["oci_setup", "oci_step", "oci_solve_transient", "si_sweep", "oci_iterate", "si_iterate",
            "oci_get_psi", "oci_set_psi", "oci_get_phi", "oci_get_state", "oci_set_state", "oci_get_balance",
-           "oci_set_boundary", "oci_set_ordering", "oci_get_e_hist", "oci_get_edges", "oci_commit", "oci_destroy", "oci_last_error",
+           "oci_set_boundary", "oci_set_ordering", "oci_set_si_mode", "oci_get_e_hist", "oci_get_edges", "oci_commit", "oci_destroy", "oci_last_error",
            "oci_probe_fp64_peak", "oci_batch_setup", "oci_batch_step", "oci_batch_size", "oci_batch_get_psi",
            "oci_batch_get_phi", "oci_batch_get_balance", "oci_diff_norm_noalloc"]
 
@@ -84,6 +85,7 @@ def load(path: Optional[str] = None):
     L.oci_get_e_hist.argtypes = [vp, vp, ctypes.POINTER(i32)]
     L.oci_get_edges.argtypes = [vp, vp, vp]
     L.oci_set_ordering.argtypes = [vp, i32]
+    L.oci_set_si_mode.argtypes = [vp, i32]
     L.oci_commit.argtypes = [vp, ctypes.POINTER(Stats)]
     L.oci_destroy.argtypes = [vp]
     L.oci_destroy.restype = None
@@ -294,6 +296,9 @@ class Solver:
         out = np.zeros(max(n.value, 1))
         _check(self.L.oci_get_e_hist(self.h, _ptr(out, writable=True), ctypes.byref(n)))
         return out[: n.value]
+
+    def set_si_mode(self, mode: int):
+        _check(self.L.oci_set_si_mode(self.h, int(mode)))
 
     def set_ordering(self, ordering: int):
         _check(self.L.oci_set_ordering(self.h, int(ordering)))

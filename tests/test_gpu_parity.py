@@ -212,3 +212,28 @@ def test_red_black_full_size_fewer_sweeps_same_answer():
         sa, sb = a.step(), b.step()
         assert sb["iters"] < 0.7 * sa["iters"]
         assert rel(b.phi(), a.phi()) < 1e-9
+
+
+@pytest.mark.parametrize("seed,J,N,G", [(61, 1, 2, 1), (62, 129, 8, 1), (63, 300, 8, 2), (64, 1000, 16, 1)])
+def test_scan_si_matches_oracle(seed, J, N, G):
+    """SI marched as a parallel scan of the cells' affine edge maps gives the
+    sweep-by-sweep result of the sequential SI (oracle) up to rounding."""
+    p = W.random_slab(seed, J, N, G).replace(tol=1e-11)
+    o = Oracle(p, factor=False)
+    with oci.Solver(p) as s:
+        s.set_si_mode(oci.SI_SCAN)
+        for k in range(2):
+            r = o.step(SI)
+            st = s.si_step()
+            assert st["status"] == 0 and st["iters"] == r["iters"]
+            assert rel(s.phi(), r["phi"]) < 1e-12
+            assert rel(s.psi(), r["Psi"]) < 1e-11
+
+
+def test_scan_si_full_size_matches_sequential():
+    p = W.slab_3region(c=0.9, tau=0.1)
+    with oci.Solver(p) as a, oci.Solver(p) as b:
+        b.set_si_mode(oci.SI_SCAN)
+        sa, sb = a.si_step(), b.si_step()
+        assert sa["iters"] == sb["iters"]
+        assert rel(b.phi(), a.phi()) < 1e-12
