@@ -257,9 +257,14 @@ def run_ours(args):
         for tau in (0.01, 0.1):
             q = W.slab_3region(c=args.c, tau=tau, J=args.J)
             row = {"tau": tau}
-            for name, kw, si in (("oci_fp64", {}, False), ("oci_fp32ir", {"precision": oci.FP32_IR}, False),
-                                 ("si_fp64", {}, True)):
+            for name, kw, si, mode in (("oci_fp64", {}, False, None), ("oci_fp32ir", {"precision": oci.FP32_IR}, False, None),
+                                       ("oci_rb_fp64", {}, False, "rb"), ("si_fp64", {}, True, None),
+                                       ("si_scan_fp64", {}, True, "scan")):
                 with oci.Solver(q, stream=stream.cuda_stream, **kw) as sv:
+                    if mode == "rb":
+                        sv.set_ordering(oci.ORDER_RED_BLACK)
+                    elif mode == "scan":
+                        sv.set_si_mode(oci.SI_SCAN)
                     (sv.si_step if si else sv.step)()  # warm step (builds graphs, touches memory)
                     t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                     nst, its = 2, 0
@@ -271,6 +276,7 @@ def run_ours(args):
                     row[name] = {"s_per_step": t0e.elapsed_time(t1e) / nst / 1e3, "sweeps_per_step": its / nst}
             row["oci_fp64_speedup_vs_si"] = row["si_fp64"]["s_per_step"] / row["oci_fp64"]["s_per_step"]
             row["oci_fp32ir_speedup_vs_si"] = row["si_fp64"]["s_per_step"] / row["oci_fp32ir"]["s_per_step"]
+            row["oci_fp32ir_speedup_vs_si_scan"] = row["si_scan_fp64"]["s_per_step"] / row["oci_fp32ir"]["s_per_step"]
             si_cmp.append(row)
 
     # dominant kernel: the fused sweep; its launch time from a run of n sweeps
