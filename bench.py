@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-si", action="store_true")
+    ap.add_argument("--no-multigroup", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batch-max-iter", type=int, default=600)
     return ap.parse_args()
 
 
@@ -279,6 +282,51 @@ def run_ours(args):
             row["oci_fp32ir_speedup_vs_si_scan"] = row["si_scan_fp64"]["s_per_step"] / row["oci_fp32ir"]["s_per_step"]
             si_cmp.append(row)
 
+    # multigroup slab (G = 8, S16, 2^16 cells): FP64 and the FP32-inner mixed form
+    multigroup = None
+    if not args.no_multigroup:
+        q = W.slab_multigroup()
+        multigroup = {"workload": q.name, "J": q.J, "N": q.N, "G": q.G, "unknowns_per_cell": 4 * q.N * q.G}
+        for name, kw in (("fp64", {}), ("fp32ir", {"precision": oci.FP32_IR})):
+            with oci.Solver(q, stream=stream.cuda_stream, **kw) as sv:
+                sv.step()  # warm step
+                t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                nst, its = 2, 0
+                t0e.record(stream)
+                for _ in range(nst):
+                    its += sv.step()["iters"]
+                t1e.record(stream)
+                torch.cuda.synchronize()
+                ms_mg = t0e.elapsed_time(t1e)
+                multigroup[name] = {"value": q.unknowns * its / (ms_mg * 1e-3), "unit": UNIT,
+                                    "ms_per_step": ms_mg / nst, "sweeps_per_step": its / nst}
+                if name == "fp64":
+                    phi_mg = sv.phi()
+                else:
+                    multigroup[name]["phi_rel_vs_fp64"] = float(np.abs(sv.phi() - phi_mg).max() / np.abs(phi_mg).max())
+
+    # batched form: 256 independent slabs (J in [1k, 64k], N in {4..32}, G in {1,4}) in one
+    # graph launch per time step; one step, sweeps capped per slab
+    batched = None
+    if not args.no_batched:
+        probs = [b.replace(max_iter=args.batch_max_iter) for b in W.batch_of_slabs(256)]
+        with oci.BatchSolver(probs, stream=stream.cuda_stream) as bs:
+            t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            t0e.record(stream)
+            sts = bs.step(allow_noconv=True)
+            t1e.record(stream)
+            torch.cuda.synchronize()
+            ms_b = t0e.elapsed_time(t1e)
+        upd = sum(p_.unknowns * st["iters"] for p_, st in zip(probs, sts))
+        batched = {"slabs": len(probs), "cells": int(sum(p_.J for p_ in probs)),
+                   "unknowns": int(sum(p_.unknowns for p_ in probs)),
+                   "value": upd / (ms_b * 1e-3), "unit": UNIT, "ms_per_step": ms_b,
+                   "converged": int(sum(st["status"] == 0 for st in sts)), "max_iter": args.batch_max_iter,
+                   "sweeps_min_median_max": [int(np.min([st["iters"] for st in sts])),
+                                             int(np.median([st["iters"] for st in sts])),
+                                             int(np.max([st["iters"] for st in sts]))],
+                   "max_balance_rel": float(max(max(st["balance_rel"]) for st in sts if st["status"] == 0))}
+
     # dominant kernel: the fused sweep; its launch time from a run of n sweeps
     n_sw = 50
     psi_keep = s.psi()
@@ -337,7 +385,9 @@ def run_ours(args):
             "gpu_launches": launches,
             "clocks": clocks,
             "precision_forms": mixed,
-            "si_comparison": si_cmp}
+            "si_comparison": si_cmp,
+            "multigroup": multigroup,
+            "batched_form": batched}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args)
     if rank == 0:

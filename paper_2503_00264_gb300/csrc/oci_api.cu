@@ -291,6 +291,9 @@ static int autotune(Handle &h) {
       if (sweep_smem(h.N, h.G, cb, P, es) > 100 * 1024) continue;
       cands.emplace_back(cb, P);
     }
+  if (mx && h.tma_ok)
+    for (int P : {1, 2, 4, 8})
+      if (h.N % P == 0 && 64 * h.G * P <= 256 && mx_tma_smem(h, P) <= 200 * 1024) cands.emplace_back(-1, P);
   if (cands.size() < 2) return OCI_OK;
   DevState &d = *h.h_ds;
   d.done = 0;
@@ -305,7 +308,8 @@ static int autotune(Handle &h) {
   const int reps = 3;
   for (auto &c : cands) {
     if (mx) {
-      h.mx_cb = c.first;
+      h.mx_tma = c.first < 0;
+      h.mx_cb = c.first < 0 ? 0 : c.first;
       h.mx_P = c.second;
       launch_mx_inner(h);
     } else {
@@ -327,7 +331,8 @@ static int autotune(Handle &h) {
     }
   }
   if (mx) {
-    h.mx_cb = bcb;
+    h.mx_tma = bcb < 0;
+    h.mx_cb = bcb < 0 ? 0 : bcb;
     h.mx_P = bP;
   } else {
     h.tune_cb = bcb;
@@ -489,6 +494,7 @@ static int setup_impl(const oci_problem *p, oci_handle *h) {
     CK(cudaMemsetAsync(h->delta[1], 0, nPsi * 4, s));
     CK(cudaMemsetAsync(h->z32, 0, nPsi * 4, s));
     CK(cudaFuncSetAttribute(k_mx_inner_ptr(), cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    if (h->precision == OCI_FP32_IR && (rc = mx_tma_setup(*h))) return rc;
     if (h->precision == OCI_TF32_IR) {
       h->mx_theta = 2e-2;
       h->mx_kmax = 24;

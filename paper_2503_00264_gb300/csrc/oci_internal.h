@@ -8,6 +8,7 @@
 // Jp = J rounded up to a multiple of 32.  The ABI's [J][G][N][*] order is
 // converted by transpose kernels in oci_api.cu.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -94,6 +95,9 @@ struct Handle {
   float *w32 = nullptr;
   int mx_kmax = 64;
   double mx_theta = 1e-3;
+  CUtensorMap tm_z, tm_d[2];          // TMA descriptors of z32 and delta[0/1] ([R][Jp] FP32)
+  bool tma_ok = false;                 // tensor maps encoded (4NG <= 256)
+  bool mx_tma = false;                 // the autotuner picked the TMA-staged inner sweep
   unsigned char *tc_img = nullptr;     // [T] x (A^{-1} image(s) in the tcgen05 K-major layout)
   size_t tc_img_bytes = 0;             // bytes per type
   // SI scratch
@@ -158,6 +162,8 @@ void launch_mx_inner(Handle &h);
 void launch_mx_outer(Handle &h, int mode);
 void launch_mx_finalize(Handle &h, cudaGraphConditionalHandle cond, int use_cond);
 int mx_partials(const Handle &h);
+int mx_tma_setup(Handle &h);
+size_t mx_tma_smem(const Handle &h, int P);
 // tensor-core block apply (TF32 / BF16x3 forms)
 int tc_prepare(Handle &h);
 int tc_partials(const Handle &h);

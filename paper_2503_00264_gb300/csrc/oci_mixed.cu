@@ -21,6 +21,7 @@
 // the committed iterate carries no more than low-precision rounding of a tiny
 // correction; this costs at most one extra sweep per step.  FP64 is kept for Psi,
 // the residual, the norm accumulation, the balance tallies and the carry.
+#include <cuda.h>
 #include <math.h>
 
 #include "oci_internal.h"
@@ -139,6 +140,219 @@ __global__ void __launch_bounds__(256) k_mx_inner(int J, int Jp, int N, int G, i
     for (int i = 0; i < (nthr + 31) / 32; i++) s += red[i];
     partials[blockIdx.x] = s;
   }
+}
+
+// ---------------------------------------------------------------- inner sweep, TMA-staged
+// The same FP32 inner sweep with the tile's operands brought in by the tensor
+// memory accelerator: per tile of kTmaCells cells, one 2D bulk tensor copy
+// moves z[0:R][j0:j0+64] and one moves delta_in[0:R][j0-4:j0+68] (the halo
+// columns j0-1 and j0+64 are inside; x starts on a 16-byte boundary; columns
+// outside the array read as zero, which is the correction's zero inflow at the
+// slab ends) into shared memory, completing on an mbarrier.  A persistent CTA
+// double-buffers the stages: the copy of its next tile is in flight while the
+// current one is computed.  R = 4NG <= 256 (one box per operand).
+constexpr int kTmaCells = 64;
+constexpr int kTmaHalo = 4;                    // columns each side of the delta box
+constexpr int kTmaDW = kTmaCells + 2 * kTmaHalo;  // delta box width
+constexpr long long kTmaSpin = 1 << 22;
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(mbar)
+      : "memory");
+}
+
+__global__ void __launch_bounds__(256) k_mx_inner_tma(const __grid_constant__ CUtensorMap tmZ,
+                                                      const __grid_constant__ CUtensorMap tmD0,
+                                                      const __grid_constant__ CUtensorMap tmD1, int J, int Jp, int N,
+                                                      int G, int P, const int32_t *__restrict__ type,
+                                                      const float *__restrict__ Linv, const float *__restrict__ Cin,
+                                                      const float *__restrict__ Mp, const float *__restrict__ w,
+                                                      float *D0, float *D1, DevState *ds,
+                                                      double *__restrict__ partials) {
+  extern __shared__ __align__(1024) unsigned char smraw_[];
+  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ double red[8];
+  // stage buffers start on a 1024-byte boundary (the launch reserves 1 KiB extra)
+  unsigned char *smraw = (unsigned char *)(((uintptr_t)smraw_ + 1023) & ~(uintptr_t)1023);
+  const int R = 4 * N * G;
+  const int cl = threadIdx.x, gy = threadIdx.y;
+  const int g = gy / P, ch = gy % P;
+  const int NP = N / P, m0 = ch * NP;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int nthr = blockDim.x * blockDim.y;
+  if (ds->done) return;  // uniform
+  const bool zero = ds->refine || ds->blk_i == 0;
+  const int dcur = ds->dcur;
+  const CUtensorMap *tmDin = dcur ? &tmD1 : &tmD0;
+  float *__restrict__ Dout = dcur ? D0 : D1;
+  // stage layout: z [R][64] then delta [R][72], each stage 1024-aligned
+  const size_t zbytes = (size_t)R * kTmaCells * 4, dbytes = (size_t)R * kTmaDW * 4;
+  const size_t stage_bytes = (zbytes + dbytes + 1023) / 1024 * 1024;
+  float *y_s = (float *)(smraw + 2 * stage_bytes);  // [G*P*4][64]
+  const uint32_t tx = (uint32_t)(zbytes + (zero ? 0 : dbytes));
+  const int ntiles = (J + kTmaCells - 1) / kTmaCells;
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&mbar[0])), "r"(1));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&mbar[1])), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  __syncthreads();
+  auto issue = [&](int tile, int st) {
+    const uint32_t bar = smem_addr(&mbar[st]);
+    unsigned char *base = smraw + st * stage_bytes;
+    asm volatile("fence.proxy.async.shared::cta;");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(tx) : "memory");
+    tma_load_2d(smem_addr(base), &tmZ, tile * kTmaCells, 0, bar);
+    if (!zero) tma_load_2d(smem_addr(base + zbytes), tmDin, tile * kTmaCells - kTmaHalo, 0, bar);
+  };
+  const int N2 = N / 2;
+  const int G4 = 4 * G;
+  float e2 = 0.f;
+  int it = 0;
+  bool failed = false;
+  if (tid == 0 && (int)blockIdx.x < ntiles) issue(blockIdx.x, 0);
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, it++) {
+    const int st = it & 1;
+    const uint32_t parity = (uint32_t)((it >> 1) & 1);
+    if (tid == 0 && tile + (int)gridDim.x < ntiles) issue(tile + gridDim.x, st ^ 1);
+    uint32_t ok = 0;
+    for (long long k = 0; k < kTmaSpin && !ok; k++) {
+      asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+                   : "=r"(ok)
+                   : "r"(smem_addr(&mbar[st])), "r"(parity)
+                   : "memory");
+    }
+    if (!__syncthreads_and(ok)) {  // the same decision in every thread
+      failed = true;
+      break;
+    }
+    const float *zs = (const float *)(smraw + st * stage_bytes);
+    const float *ds_ = (const float *)(smraw + st * stage_bytes + zbytes);
+    const int j = tile * kTmaCells + cl;
+    const bool active = j < J;
+    const int tau = active ? type[j] : 0;
+    const size_t tb = (size_t)tau * G * N;
+    auto dval = [&](int r, int col) -> float { return zero ? 0.f : ds_[r * kTmaDW + col]; };
+    float y0 = 0.f, y1 = 0.f, y2 = 0.f, y3 = 0.f;
+    if (active) {
+      for (int m = m0; m < m0 + NP; m++) {
+        const int gm = g * N + m;
+        float uk, uh;
+        if (m >= N2) {  // upstream R corner of cell j-1 (zero beyond the slab end)
+          uk = dval(gm * 4 + 1, cl + kTmaHalo - 1);
+          uh = dval(gm * 4 + 3, cl + kTmaHalo - 1);
+        } else {  // upstream L corner of cell j+1
+          uk = (j < J - 1) ? dval(gm * 4 + 0, cl + kTmaHalo + 1) : 0.f;
+          uh = (j < J - 1) ? dval(gm * 4 + 2, cl + kTmaHalo + 1) : 0.f;
+        }
+        const float *C = Cin + (tb + gm) * 8;
+        const float wm = w[m];
+        y0 = fmaf(wm, fmaf(C[1], uh, fmaf(C[0], uk, zs[(gm * 4 + 0) * kTmaCells + cl])), y0);
+        y1 = fmaf(wm, fmaf(C[3], uh, fmaf(C[2], uk, zs[(gm * 4 + 1) * kTmaCells + cl])), y1);
+        y2 = fmaf(wm, fmaf(C[5], uh, fmaf(C[4], uk, zs[(gm * 4 + 2) * kTmaCells + cl])), y2);
+        y3 = fmaf(wm, fmaf(C[7], uh, fmaf(C[6], uk, zs[(gm * 4 + 3) * kTmaCells + cl])), y3);
+      }
+    }
+    y_s[(gy * 4 + 0) * kTmaCells + cl] = y0;
+    y_s[(gy * 4 + 1) * kTmaCells + cl] = y1;
+    y_s[(gy * 4 + 2) * kTmaCells + cl] = y2;
+    y_s[(gy * 4 + 3) * kTmaCells + cl] = y3;
+    __syncthreads();
+    if (active) {
+      const float *M = Mp + (size_t)tau * G4 * G4 + (size_t)(g * 4) * G4;
+      float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+      for (int k = 0; k < G4; k++) {
+        const int gp = k >> 2, q = k & 3;
+        float yk = 0.f;
+        for (int c = 0; c < P; c++) yk += y_s[((gp * P + c) * 4 + q) * kTmaCells + cl];
+        s0 = fmaf(M[k], yk, s0);
+        s1 = fmaf(M[G4 + k], yk, s1);
+        s2 = fmaf(M[2 * G4 + k], yk, s2);
+        s3 = fmaf(M[3 * G4 + k], yk, s3);
+      }
+      for (int m = m0; m < m0 + NP; m++) {
+        const int gm = g * N + m;
+        float uk, uh;
+        if (m >= N2) {
+          uk = dval(gm * 4 + 1, cl + kTmaHalo - 1);
+          uh = dval(gm * 4 + 3, cl + kTmaHalo - 1);
+        } else {
+          uk = (j < J - 1) ? dval(gm * 4 + 0, cl + kTmaHalo + 1) : 0.f;
+          uh = (j < J - 1) ? dval(gm * 4 + 2, cl + kTmaHalo + 1) : 0.f;
+        }
+        const float *C = Cin + (tb + gm) * 8;
+        const float *L = Linv + (tb + gm) * 16;
+#pragma unroll
+        for (int p = 0; p < 4; p++) {
+          const float t = fmaf(C[p * 2 + 1], uh, fmaf(C[p * 2 + 0], uk, zs[(gm * 4 + p) * kTmaCells + cl]));
+          const float o = fmaf(L[p * 4 + 3], s3, fmaf(L[p * 4 + 2], s2, fmaf(L[p * 4 + 1], s1, fmaf(L[p * 4 + 0], s0, t))));
+          const float d = o - dval(gm * 4 + p, cl + kTmaHalo);
+          e2 = fmaf(d, d, e2);
+          Dout[(size_t)(gm * 4 + p) * Jp + j] = o;
+        }
+      }
+    }
+    __syncthreads();  // stage st and y_s are free for the next tile
+  }
+  if (failed && tid == 0) {
+    atomicExch(&ds->status, OCI_E_TIMEOUT);
+    ds->done = 1;
+  }
+  double v = (double)e2;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((tid & 31) == 0) red[tid >> 5] = v;
+  __syncthreads();
+  if (tid == 0) {
+    double s = 0.0;
+    for (int i = 0; i < (nthr + 31) / 32; i++) s += red[i];
+    partials[blockIdx.x] = s;
+  }
+}
+
+size_t mx_tma_smem(const Handle &h, int P) {
+  const int R = 4 * h.N * h.G;
+  const size_t zbytes = (size_t)R * kTmaCells * 4, dbytes = (size_t)R * kTmaDW * 4;
+  const size_t stage_bytes = (zbytes + dbytes + 1023) / 1024 * 1024;
+  return 2 * stage_bytes + (size_t)h.G * P * 4 * kTmaCells * 4 + 1024;
+}
+
+const void *k_mx_inner_tma_ptr() { return (const void *)k_mx_inner_tma; }
+
+// Encode the three tensor maps (z and the two delta buffers, [R rows][Jp cols] FP32).
+int mx_tma_setup(Handle &h) {
+  const int R = 4 * h.N * h.G;
+  if (R > 256) return OCI_OK;  // one box per operand only
+  typedef CUresult (*Encode)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                             const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                             CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  Encode enc = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", (void **)&enc, 12000, cudaEnableDefault, &q);
+  if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !enc) return OCI_OK;  // no TMA path: keep the plain kernel
+  const cuuint64_t dims[2] = {(cuuint64_t)h.Jp, (cuuint64_t)R};
+  const cuuint64_t strides[1] = {(cuuint64_t)h.Jp * 4};
+  const cuuint32_t estr[2] = {1, 1};
+  const cuuint32_t boxz[2] = {(cuuint32_t)kTmaCells, (cuuint32_t)R};
+  const cuuint32_t boxd[2] = {(cuuint32_t)kTmaDW, (cuuint32_t)R};
+  CUresult r1 = enc(&h.tm_z, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, h.z32, dims, strides, boxz, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CUresult r2 = enc(&h.tm_d[0], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, h.delta[0], dims, strides, boxd, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CUresult r3 = enc(&h.tm_d[1], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, h.delta[1], dims, strides, boxd, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r1 != CUDA_SUCCESS || r2 != CUDA_SUCCESS || r3 != CUDA_SUCCESS) return OCI_OK;
+  e = cudaFuncSetAttribute(k_mx_inner_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_mx_inner_tma)");
+  h.tma_ok = true;
+  return OCI_OK;
 }
 
 // ---------------------------------------------------------------- outer (FP64)
@@ -367,12 +581,37 @@ static void mx_shape(const Handle &h, int &cb, int &P) {
 int tc_partials(const Handle &h);
 int mx_partials(const Handle &h) {
   if (h.precision != OCI_FP32_IR) return tc_partials(h);
+  if (h.mx_tma) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mx_inner_tma, kTmaCells * h.G * h.mx_P,
+                                                  mx_tma_smem(h, h.mx_P));
+    const int ntiles = (h.J + kTmaCells - 1) / kTmaCells;
+    const int grid = sms * (per > 0 ? per : 1);
+    return grid < ntiles ? grid : ntiles;
+  }
   int cb, P;
   mx_shape(h, cb, P);
   return (h.J + cb - 1) / cb;
 }
 
 void launch_mx_inner(Handle &h) {
+  if (h.mx_tma) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int P = h.mx_P;
+    const size_t smem = mx_tma_smem(h, P);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mx_inner_tma, kTmaCells * h.G * P, smem);
+    const int ntiles = (h.J + kTmaCells - 1) / kTmaCells;
+    int grid = sms * (per > 0 ? per : 1);
+    if (grid > ntiles) grid = ntiles;
+    k_mx_inner_tma<<<grid, dim3(kTmaCells, h.G * P), smem, h.stream>>>(
+        h.tm_z, h.tm_d[0], h.tm_d[1], h.J, h.Jp, h.N, h.G, P, h.type, h.tt.Linv32, h.tt.Cin32, h.tt.Mp32, h.w32,
+        h.delta[0], h.delta[1], h.ds, h.partials);
+    return;
+  }
   int cb, P;
   mx_shape(h, cb, P);
   dim3 block(cb, h.G * P);
