@@ -152,6 +152,16 @@ typedef struct {
   double seconds;           /* wall time of the convergence loop (CUDA events)        */
 } oci_stats;
 
+/* Setup facts of a handle (oci_get_info). */
+typedef struct {
+  int32_t n_types;           /* distinct cell types (material, dx) sharing their tables          */
+  int32_t cells_per_block;   /* launch shape of the sweep kernel picked by the autotuner         */
+  int32_t angle_chunks;      /* threads per (cell, group): angles split into this many chunks    */
+  int32_t inner_kernel;      /* mixed forms: 0 plain FP32 sweep, 1 TMA-staged FP32 sweep,
+                                2 tcgen05 tensor-core block apply; -1 for the FP64 form            */
+  double tuned_sweep_us;     /* measured time of one sweep with the chosen shape (0 if not tuned) */
+} oci_info;
+
 typedef struct oci_handle oci_handle;
 
 /* Validate and copy the problem, build the quadrature and the per-cell-type
@@ -269,6 +279,9 @@ int oci_batch_get_balance(const oci_handle *h, int32_t s, double *bal);
  * before capturing a stream.  Calls that overlap on the GPU share the array
  * and race; the result is deterministic for a given n. */
 int oci_diff_norm_noalloc(const double *a, const double *b, int64_t n, double *e_out, void *stream);
+
+/* Facts of the setup of a single-slab handle (see oci_info). */
+int oci_get_info(const oci_handle *h, oci_info *info);
 
 /* Release the handle and its device memory.  NULL is accepted. */
 void oci_destroy(oci_handle *h);

@@ -294,7 +294,23 @@ static int autotune(Handle &h) {
   if (mx && h.tma_ok)
     for (int P : {1, 2, 4, 8})
       if (h.N % P == 0 && 64 * h.G * P <= 256 && mx_tma_smem(h, P) <= 200 * 1024) cands.emplace_back(-1, P);
-  if (cands.size() < 2) return OCI_OK;
+  // OCI_MX_INNER=plain|tma restricts the FP32 inner sweep to one kernel (for profiling)
+  const char *only = getenv("OCI_MX_INNER");
+  if (mx && only) {
+    const bool want_tma = std::string(only) == "tma";
+    std::vector<std::pair<int, int>> keep;
+    for (auto &c : cands)
+      if ((c.first < 0) == want_tma) keep.push_back(c);
+    if (!keep.empty()) cands.swap(keep);
+  }
+  if (cands.size() < 2) {
+    if (cands.size() == 1 && mx) {
+      h.mx_tma = cands[0].first < 0;
+      h.mx_cb = cands[0].first < 0 ? 0 : cands[0].first;
+      h.mx_P = cands[0].second;
+    }
+    return OCI_OK;
+  }
   DevState &d = *h.h_ds;
   d.done = 0;
   d.fixed = 1;
@@ -1001,6 +1017,28 @@ int oci_commit(oci_handle *h, oci_stats *st) {
         if (rel > st->balance_rel[b]) st->balance_rel[b] = rel;
       }
   }
+  return OCI_OK;
+}
+
+int oci_get_info(const oci_handle *h, oci_info *info) {
+  GUARD(h);
+  if (!info) return set_error("info is NULL"), OCI_E_INVAL;
+  info->n_types = h->tt.n_types;
+  if (h->precision == OCI_FP64) {
+    SweepCfg c = sweep_config(*h);
+    info->cells_per_block = c.cells_per_block;
+    info->angle_chunks = c.chunks;
+    info->inner_kernel = -1;
+  } else if (h->precision == OCI_FP32_IR) {
+    info->cells_per_block = h->mx_tma ? 64 : h->mx_cb;
+    info->angle_chunks = h->mx_P;
+    info->inner_kernel = h->mx_tma ? 1 : 0;
+  } else {
+    info->cells_per_block = 128;
+    info->angle_chunks = 1;
+    info->inner_kernel = 2;
+  }
+  info->tuned_sweep_us = h->tune_us;
   return OCI_OK;
 }
 

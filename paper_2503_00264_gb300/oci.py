@@ -27,7 +27,7 @@ SI_SEQUENTIAL, SI_SCAN = 0, 1
 
 EXPORTS = ["oci_setup", "oci_step", "oci_solve_transient", "si_sweep", "oci_iterate", "si_iterate",
            "oci_get_psi", "oci_set_psi", "oci_get_phi", "oci_get_state", "oci_set_state", "oci_get_balance",
-           "oci_set_boundary", "oci_set_ordering", "oci_set_si_mode", "oci_get_e_hist", "oci_get_edges", "oci_commit", "oci_destroy", "oci_last_error",
+           "oci_set_boundary", "oci_set_ordering", "oci_set_si_mode", "oci_get_e_hist", "oci_get_edges", "oci_commit", "oci_get_info", "oci_destroy", "oci_last_error",
            "oci_probe_fp64_peak", "oci_batch_setup", "oci_batch_step", "oci_batch_size", "oci_batch_get_psi",
            "oci_batch_get_phi", "oci_batch_get_balance", "oci_diff_norm_noalloc"]
 
@@ -46,6 +46,11 @@ class Problem(ctypes.Structure):
                 ("inc_right", ctypes.c_void_p), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("guess", ctypes.c_int32), ("solver", ctypes.c_int32),
                 ("stream", ctypes.c_void_p)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("n_types", ctypes.c_int32), ("cells_per_block", ctypes.c_int32), ("angle_chunks", ctypes.c_int32),
+                ("inner_kernel", ctypes.c_int32), ("tuned_sweep_us", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -85,6 +90,7 @@ def load(path: Optional[str] = None):
     L.oci_get_e_hist.argtypes = [vp, vp, ctypes.POINTER(i32)]
     L.oci_get_edges.argtypes = [vp, vp, vp]
     L.oci_set_ordering.argtypes = [vp, i32]
+    L.oci_get_info.argtypes = [vp, ctypes.POINTER(Info)]
     L.oci_set_si_mode.argtypes = [vp, i32]
     L.oci_commit.argtypes = [vp, ctypes.POINTER(Stats)]
     L.oci_destroy.argtypes = [vp]
@@ -296,6 +302,11 @@ class Solver:
         out = np.zeros(max(n.value, 1))
         _check(self.L.oci_get_e_hist(self.h, _ptr(out, writable=True), ctypes.byref(n)))
         return out[: n.value]
+
+    def info(self) -> dict:
+        i = Info()
+        _check(self.L.oci_get_info(self.h, ctypes.byref(i)))
+        return {f: getattr(i, f) for f, _ in Info._fields_}
 
     def set_si_mode(self, mode: int):
         _check(self.L.oci_set_si_mode(self.h, int(mode)))

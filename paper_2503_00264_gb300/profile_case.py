@@ -48,6 +48,7 @@ def main():
     stream = torch.cuda.Stream()
     prec = {"fp64": oci.FP64, "fp32": oci.FP32_IR, "tf32": oci.TF32_IR, "bf16x3": oci.BF16X3_IR}[a.precision]
     with oci.Solver(p, solver=solver, precision=prec, stream=stream.cuda_stream) as s:
+        print("setup:", s.info())
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         if a.steps:
             e0.record(stream)
