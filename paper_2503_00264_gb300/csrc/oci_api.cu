@@ -318,6 +318,9 @@ static int autotune(Handle &h) {
   d.blk_i = 1;
   d.cur = 0;
   d.dcur = 0;
+  d.max_iter = 0;        // no e history while timing
+  d.k_max = 1 << 30;     // and no refinement decisions
+  d.theta = 0.0;
   CK(cudaMemcpyAsync(h.ds, h.h_ds, sizeof(DevState), cudaMemcpyHostToDevice, h.stream));
   float best = 1e30f;
   int bcb = 0, bP = 0;
@@ -327,14 +330,15 @@ static int autotune(Handle &h) {
       h.mx_tma = c.first < 0;
       h.mx_cb = c.first < 0 ? 0 : c.first;
       h.mx_P = c.second;
-      launch_mx_inner(h);
+      launch_mx_inner(h, cudaGraphConditionalHandle{}, 0);
     } else {
       h.tune_cb = c.first;
       h.tune_P = c.second;
-      launch_oci_sweep(h);
+      launch_oci_sweep(h, cudaGraphConditionalHandle{}, 0);
     }
     CK(cudaEventRecord(h.ev0, h.stream));
-    for (int r = 0; r < reps; r++) mx ? launch_mx_inner(h) : launch_oci_sweep(h);
+    for (int r = 0; r < reps; r++)
+      mx ? launch_mx_inner(h, cudaGraphConditionalHandle{}, 0) : launch_oci_sweep(h, cudaGraphConditionalHandle{}, 0);
     CK(cudaEventRecord(h.ev1, h.stream));
     CK(cudaEventSynchronize(h.ev1));
     CK(cudaGetLastError());
@@ -383,7 +387,7 @@ static void free_handle(Handle *h) {
                   h->tt.Cin, h->tt.Mp,  h->tt.Kap,    h->tt.dx,     h->tt.sig,       h->si_z,      h->si_uin,
                   h->LU,     h->piv,    h->partials,  h->bal_partials, h->bal,       h->e_hist,    h->ds,
                   h->stage,  h->delta[0], h->delta[1], h->z32, h->w32, h->tt.Lco, h->tt.Linv32, h->tt.Cin32,
-                  h->tt.Mp32, h->tc_img, h->si_maps, h->si_segin};
+                  h->tt.Mp32, h->tc_img, h->si_maps, h->si_segin, h->counter};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (h->h_ds) cudaFreeHost(h->h_ds);
@@ -472,6 +476,8 @@ static int setup_impl(const oci_problem *p, oci_handle *h) {
   np = std::max(np, h->J + 64);  // any sweep shape down to one cell per block
   h->n_partials = np;
   CK(cudaMalloc(&h->partials, (size_t)np * 8));
+  CK(cudaMalloc(&h->counter, sizeof(unsigned)));
+  CK(cudaMemsetAsync(h->counter, 0, sizeof(unsigned), s));
   const int nblk_carry = (h->J + 31) / 32;
   CK(cudaMalloc(&h->bal_partials, (size_t)nblk_carry * G * 8 * 8));
   CK(cudaMalloc(&h->bal, G * 10 * 8));
@@ -572,18 +578,18 @@ static void launch_body(Handle &h, bool si, cudaGraphConditionalHandle cond, int
     launch_si_sweep(h);
     launch_finalize(h, h.partials, si_partials(h), cond, use_cond);
   } else if (h.precision != OCI_FP64) {
-    if (h.precision == OCI_FP32_IR)
-      launch_mx_inner(h);
-    else
+    if (h.precision == OCI_FP32_IR) {
+      launch_mx_inner(h, cond, use_cond);  // norm and stop rule fused in
+    } else {
       launch_tc_inner(h);
-    launch_mx_finalize(h, cond, use_cond);
+      launch_mx_finalize(h, cond, use_cond);
+    }
     launch_mx_outer(h, 1);
   } else if (h.solver == OCI_SOLVER_DENSE_LU) {
     launch_dense_sweep(h);
     launch_finalize(h, h.partials, dense_partials(h), cond, use_cond);
   } else {
-    launch_oci_sweep(h);
-    launch_finalize(h, h.partials, sweep_partials(h), cond, use_cond);
+    launch_oci_sweep(h, cond, use_cond);  // norm and stop rule fused in
   }
 }
 

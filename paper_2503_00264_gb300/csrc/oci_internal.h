@@ -111,6 +111,7 @@ struct Handle {
   int32_t *piv = nullptr;        // [J][n]
   // reductions
   double *partials = nullptr;    // [max blocks]
+  unsigned *counter = nullptr;   // blocks finished in the current sweep launch (last block resets it)
   int n_partials = 0;
   double *bal_partials = nullptr;  // [max blocks][G][8]
   double *bal = nullptr;           // [G][2][5]
@@ -142,7 +143,7 @@ SweepCfg sweep_config(const Handle &h);
 size_t sweep_smem(int N, int G, int cb, int P, size_t es);
 
 void launch_step_const(Handle &h);
-void launch_oci_sweep(Handle &h);
+void launch_oci_sweep(Handle &h, cudaGraphConditionalHandle cond, int use_cond);
 const void *k_oci_sweep_ptr();
 const void *k_oci_sweep_rb_ptr();
 int sweep_partials(const Handle &h);
@@ -158,7 +159,7 @@ void launch_si_sweep(Handle &h);
 void launch_si_phi_from_psi(Handle &h, double *phi_dst);
 size_t si_scan_maps(const Handle &h);
 // mixed-precision form
-void launch_mx_inner(Handle &h);
+void launch_mx_inner(Handle &h, cudaGraphConditionalHandle cond, int use_cond);
 void launch_mx_outer(Handle &h, int mode);
 void launch_mx_finalize(Handle &h, cudaGraphConditionalHandle cond, int use_cond);
 int mx_partials(const Handle &h);

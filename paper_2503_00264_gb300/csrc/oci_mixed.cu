@@ -24,7 +24,7 @@
 #include <cuda.h>
 #include <math.h>
 
-#include "oci_internal.h"
+#include "oci_device.cuh"
 
 namespace oci {
 
@@ -37,10 +37,12 @@ __global__ void __launch_bounds__(256) k_mx_inner(int J, int Jp, int N, int G, i
                                                   const int32_t *__restrict__ type, const float *__restrict__ Linv,
                                                   const float *__restrict__ Cin, const float *__restrict__ Mp,
                                                   const float *__restrict__ w, const float *__restrict__ z, float *D0,
-                                                  float *D1, const DevState *__restrict__ ds,
-                                                  double *__restrict__ partials) {
+                                                  float *D1, DevState *ds, double *__restrict__ partials,
+                                                  unsigned *counter, double *e_hist,
+                                                  cudaGraphConditionalHandle cond, int use_cond) {
   extern __shared__ float smf[];
   __shared__ double red[32];
+  __shared__ bool s_last;
   const int CB = blockDim.x;
   const int cl = threadIdx.x, gy = threadIdx.y;
   const int g = gy / P, ch = gy % P;
@@ -135,10 +137,16 @@ __global__ void __launch_bounds__(256) k_mx_inner(int J, int Jp, int N, int G, i
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   if ((tid & 31) == 0) red[tid >> 5] = v;
   __syncthreads();
-  if (tid == 0) {
-    double s = 0.0;
-    for (int i = 0; i < (nthr + 31) / 32; i++) s += red[i];
-    partials[blockIdx.x] = s;
+  double bs = 0.0;
+  if (tid == 0)
+    for (int i = 0; i < (nthr + 31) / 32; i++) bs += red[i];
+  // the block that finishes last reduces all partials and applies the stop rule
+  if (publish_partial(partials, blockIdx.x, bs, counter, gridDim.x, &s_last)) {
+    const double tot = block_sum_fixed(partials, gridDim.x, red);
+    if (tid == 0) {
+      *counter = 0;
+      finish_mixed(ds, e_hist, sqrt(tot), cond, use_cond);
+    }
   }
 }
 
@@ -172,10 +180,13 @@ __global__ void __launch_bounds__(256) k_mx_inner_tma(const __grid_constant__ CU
                                                       const float *__restrict__ Linv, const float *__restrict__ Cin,
                                                       const float *__restrict__ Mp, const float *__restrict__ w,
                                                       float *D0, float *D1, DevState *ds,
-                                                      double *__restrict__ partials) {
+                                                      double *__restrict__ partials, unsigned *counter,
+                                                      double *e_hist, cudaGraphConditionalHandle cond,
+                                                      int use_cond) {
   extern __shared__ __align__(1024) unsigned char smraw_[];
   __shared__ __align__(8) uint64_t mbar[2];
-  __shared__ double red[8];
+  __shared__ double red[32];
+  __shared__ bool s_last;
   // stage buffers start on a 1024-byte boundary (the launch reserves 1 KiB extra)
   unsigned char *smraw = (unsigned char *)(((uintptr_t)smraw_ + 1023) & ~(uintptr_t)1023);
   const int R = 4 * N * G;
@@ -307,10 +318,15 @@ __global__ void __launch_bounds__(256) k_mx_inner_tma(const __grid_constant__ CU
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   if ((tid & 31) == 0) red[tid >> 5] = v;
   __syncthreads();
-  if (tid == 0) {
-    double s = 0.0;
-    for (int i = 0; i < (nthr + 31) / 32; i++) s += red[i];
-    partials[blockIdx.x] = s;
+  double bs = 0.0;
+  if (tid == 0)
+    for (int i = 0; i < (nthr + 31) / 32; i++) bs += red[i];
+  if (publish_partial(partials, blockIdx.x, bs, counter, gridDim.x, &s_last)) {
+    const double tot = block_sum_fixed(partials, gridDim.x, red);
+    if (tid == 0) {
+      *counter = 0;
+      finish_mixed(ds, e_hist, sqrt(tot), cond, use_cond);
+    }
   }
 }
 
@@ -486,72 +502,13 @@ __global__ void __launch_bounds__(256) k_mx_outer(int J, int Jp, int N, int G, c
 __global__ void __launch_bounds__(kFinalizeThreads) k_mx_finalize(const double *__restrict__ partials, int n,
                                                                     DevState *ds, double *e_hist,
                                                                     cudaGraphConditionalHandle cond, int use_cond) {
-  __shared__ double sh[kFinalizeThreads];
+  __shared__ double red[32];
   if (ds->done) {
     if (threadIdx.x == 0 && use_cond) cudaGraphSetConditional(cond, 0);
     return;
   }
-  double s = 0.0;
-  for (int i = threadIdx.x; i < n; i += kFinalizeThreads) s += partials[i];
-  sh[threadIdx.x] = s;
-  __syncthreads();
-  for (int o = kFinalizeThreads / 2; o > 0; o >>= 1) {
-    if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
-    __syncthreads();
-  }
-  if (threadIdx.x != 0) return;
-  DevState d = *ds;  // one load of the state, one store below
-  // settle the refinement made by the previous body's outer kernel
-  if (d.refine) {
-    d.cur ^= 1;
-    d.refine = 0;
-    d.blk_i = 0;
-  }
-  const double e = sqrt(sh[0]);
-  const int l = d.l;
-  if (e_hist && l < d.max_iter) e_hist[l] = e;
-  double rho = 0.0;
-  int conv = 0;
-  if (!isfinite(e)) {
-    d.status = OCI_E_NONFINITE;
-    d.done = 1;
-  } else {
-    if (l >= 1 && d.e_prev > 0.0) rho = e / d.e_prev;
-    if (!d.fixed) {
-      if (e == 0.0) conv = 1;
-      else if (l >= 1) conv = e < d.tol * (1.0 - rho);
-    }
-  }
-  d.e = e;
-  d.rho = rho;
-  d.e_prev = e;
-  d.l = l + 1;
-  d.dcur ^= 1;
-  d.blk_i += 1;
-  if (d.blk_i == 1) d.e_blk0 = e;
-  // The stop rule is accepted only where the low-precision correction is
-  // small: on the first sweep after a refinement (delta = A~^{-1} r from a fresh
-  // FP64 residual) or in a block that began below tol.  Otherwise refine first
-  // and test the next sweep again.
-  int verify = 0;
-  if (conv && !(d.blk_i == 1 || d.e_blk0 <= d.tol)) {
-    conv = 0;
-    verify = 1;
-  }
-  if (!d.fixed && !d.done) {
-    if (conv) {
-      d.status = OCI_OK;
-      d.done = 1;
-    } else if (l + 1 >= d.max_iter) {
-      d.status = OCI_E_NOCONV;
-      d.done = 1;
-    }
-  }
-  const int refine = d.done || verify || d.blk_i >= d.k_max || e < d.theta * d.e_blk0;
-  d.refine = refine;
-  if (refine) d.n_refine += 1;
-  *ds = d;
-  if (use_cond && d.done) cudaGraphSetConditional(cond, 0);
+  const double tot = block_sum_fixed(partials, n, red);
+  if (threadIdx.x == 0) finish_mixed(ds, e_hist, sqrt(tot), cond, use_cond);
 }
 
 // kind 0: settle a pending refinement (flip Psi, zero correction)
@@ -596,7 +553,9 @@ int mx_partials(const Handle &h) {
   return (h.J + cb - 1) / cb;
 }
 
-void launch_mx_inner(Handle &h) {
+// One inner sweep including its norm reduction, stop rule and refinement
+// decision (fused into the last block).
+void launch_mx_inner(Handle &h, cudaGraphConditionalHandle cond, int use_cond) {
   if (h.mx_tma) {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
@@ -609,7 +568,7 @@ void launch_mx_inner(Handle &h) {
     if (grid > ntiles) grid = ntiles;
     k_mx_inner_tma<<<grid, dim3(kTmaCells, h.G * P), smem, h.stream>>>(
         h.tm_z, h.tm_d[0], h.tm_d[1], h.J, h.Jp, h.N, h.G, P, h.type, h.tt.Linv32, h.tt.Cin32, h.tt.Mp32, h.w32,
-        h.delta[0], h.delta[1], h.ds, h.partials);
+        h.delta[0], h.delta[1], h.ds, h.partials, h.counter, h.e_hist, cond, use_cond);
     return;
   }
   int cb, P;
@@ -617,7 +576,7 @@ void launch_mx_inner(Handle &h) {
   dim3 block(cb, h.G * P);
   k_mx_inner<<<(h.J + cb - 1) / cb, block, sweep_smem(h.N, h.G, cb, P, 4), h.stream>>>(
       h.J, h.Jp, h.N, h.G, P, h.type, h.tt.Linv32, h.tt.Cin32, h.tt.Mp32, h.w32, h.z32, h.delta[0], h.delta[1], h.ds,
-      h.partials);
+      h.partials, h.counter, h.e_hist, cond, use_cond);
 }
 
 void launch_mx_outer(Handle &h, int mode) {

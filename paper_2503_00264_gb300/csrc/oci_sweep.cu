@@ -15,7 +15,7 @@
 // computed once per step (k_step_const) and u the two upstream edge values.
 #include <math.h>
 
-#include "oci_internal.h"
+#include "oci_device.cuh"
 
 namespace oci {
 
@@ -75,8 +75,10 @@ __global__ void __launch_bounds__(256) k_oci_sweep_t(
     int J, int Jp, int N, int G, int P, int color, const int32_t *__restrict__ type,
     const double *__restrict__ Linv, const double *__restrict__ Cin, const double *__restrict__ Mp,
     const double *__restrict__ w, const double *__restrict__ inc, const double *__restrict__ tc, double *Psi0,
-    double *Psi1, const DevState *__restrict__ ds, double *__restrict__ partials) {
+    double *Psi1, DevState *ds, double *__restrict__ partials, unsigned *counter, double *e_hist,
+    cudaGraphConditionalHandle cond, int use_cond, int fuse, int nparts) {
   extern __shared__ double sm[];
+  __shared__ bool s_last;
   const int CB = blockDim.x;
   const int cl = threadIdx.x, gy = threadIdx.y;
   const int g = gy / P, ch = gy % P;
@@ -184,7 +186,19 @@ __global__ void __launch_bounds__(256) k_oci_sweep_t(
     }
   }
   const double bs = block_sum(e2, red);
-  if (threadIdx.x == 0 && threadIdx.y == 0) partials[blockIdx.x + (RB ? color * gridDim.x : 0)] = bs;
+  const int slot = blockIdx.x + (RB ? color * gridDim.x : 0);
+  if (!fuse) {
+    if (threadIdx.x == 0 && threadIdx.y == 0) partials[slot] = bs;
+    return;
+  }
+  // the block that finishes last reduces all partials and applies the stop rule
+  if (publish_partial(partials, slot, bs, counter, gridDim.x, &s_last)) {
+    const double tot = block_sum_fixed(partials, nparts, red);
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+      *counter = 0;
+      finish_fp64(ds, e_hist, sqrt(tot), cond, use_cond);
+    }
+  }
 }
 
 const void *k_oci_sweep_ptr() { return (const void *)k_oci_sweep_t<false>; }
@@ -217,22 +231,25 @@ void launch_step_const(Handle &h) {
                                            h.tt.Linv, h.tc);
 }
 
-void launch_oci_sweep(Handle &h) {
+// One sweep including its norm reduction and stop rule (fused into the last block).
+void launch_oci_sweep(Handle &h, cudaGraphConditionalHandle cond, int use_cond) {
   SweepCfg c = sweep_config(h);
   dim3 block(c.cells_per_block, h.G * c.chunks);
   if (h.ordering == OCI_ORDER_RED_BLACK) {
-    // two half sweeps, even cells then odd cells, each over ceil(J/2) threads
+    // two half sweeps, even cells then odd cells, each over ceil(J/2) threads;
+    // the odd half reduces the partials of both
     const int half = (h.J + 1) / 2;
     const int grid = (half + c.cells_per_block - 1) / c.cells_per_block;
     for (int color = 0; color < 2; color++)
-      k_oci_sweep_t<true><<<grid, block, c.smem, h.stream>>>(h.J, h.Jp, h.N, h.G, c.chunks, color, h.type, h.tt.Linv,
-                                                             h.tt.Cin, h.tt.Mp, h.w, h.inc, h.tc, h.Psi[0], h.Psi[1],
-                                                             h.ds, h.partials);
+      k_oci_sweep_t<true><<<grid, block, c.smem, h.stream>>>(
+          h.J, h.Jp, h.N, h.G, c.chunks, color, h.type, h.tt.Linv, h.tt.Cin, h.tt.Mp, h.w, h.inc, h.tc, h.Psi[0],
+          h.Psi[1], h.ds, h.partials, h.counter, h.e_hist, cond, use_cond, color == 1, 2 * grid);
     return;
   }
   k_oci_sweep_t<false><<<c.grid, block, c.smem, h.stream>>>(h.J, h.Jp, h.N, h.G, c.chunks, -1, h.type, h.tt.Linv,
                                                             h.tt.Cin, h.tt.Mp, h.w, h.inc, h.tc, h.Psi[0], h.Psi[1],
-                                                            h.ds, h.partials);
+                                                            h.ds, h.partials, h.counter, h.e_hist, cond, use_cond, 1,
+                                                            c.grid);
 }
 
 int sweep_partials(const Handle &h) {
@@ -251,53 +268,13 @@ int sweep_partials(const Handle &h) {
 __global__ void __launch_bounds__(kFinalizeThreads) k_finalize(const double *__restrict__ partials, int n,
                                                                  DevState *ds, double *e_hist,
                                                                  cudaGraphConditionalHandle cond, int use_cond) {
-  __shared__ double sh[kFinalizeThreads];
+  __shared__ double red[32];
   if (ds->done) {
     if (threadIdx.x == 0 && use_cond) cudaGraphSetConditional(cond, 0);
     return;
   }
-  double s = 0.0;
-  for (int i = threadIdx.x; i < n; i += kFinalizeThreads) s += partials[i];
-  sh[threadIdx.x] = s;
-  __syncthreads();
-  for (int o = kFinalizeThreads / 2; o > 0; o >>= 1) {
-    if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    DevState d = *ds;  // one load of the state, one store below
-    const double e = sqrt(sh[0]);
-    const int l = d.l;
-    if (e_hist && l < d.max_iter) e_hist[l] = e;
-    double rho = 0.0;
-    int conv = 0;
-    if (!isfinite(e)) {
-      d.status = OCI_E_NONFINITE;
-      d.done = 1;
-    } else {
-      if (l >= 1 && d.e_prev > 0.0) rho = e / d.e_prev;
-      if (!d.fixed) {
-        if (e == 0.0) conv = 1;
-        else if (l >= 1) conv = e < d.tol * (1.0 - rho);
-      }
-    }
-    d.e = e;
-    d.rho = rho;
-    d.e_prev = e;
-    d.l = l + 1;
-    if (!d.inplace) d.cur ^= 1;
-    if (!d.fixed && !d.done) {
-      if (conv) {
-        d.status = OCI_OK;
-        d.done = 1;
-      } else if (l + 1 >= d.max_iter) {
-        d.status = OCI_E_NOCONV;
-        d.done = 1;
-      }
-    }
-    *ds = d;
-    if (use_cond && d.done) cudaGraphSetConditional(cond, 0);
-  }
+  const double tot = block_sum_fixed(partials, n, red);
+  if (threadIdx.x == 0) finish_fp64(ds, e_hist, sqrt(tot), cond, use_cond);
 }
 
 void launch_finalize(Handle &h, const double *partials, int n, cudaGraphConditionalHandle cond, int use_cond) {
