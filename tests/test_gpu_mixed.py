@@ -120,3 +120,20 @@ def test_tensor_core_full_size_matches_fp64_path(prec):
             assert max(sb["balance_rel"]) < 1e-9
         assert rel(b.phi(), a.phi()) < 1e-10
         assert rel(b.psi(), a.psi()) < 1e-10
+
+
+@pytest.mark.parametrize("kernel", ["plain", "tma"])
+def test_fp32_inner_kernels_both_match_oracle(kernel, monkeypatch):
+    """Both FP32 inner-sweep kernels (plain, and tiles staged by 2D TMA bulk
+    copies) give the FP64 oracle's answer, whichever the autotuner would pick."""
+    monkeypatch.setenv("OCI_MX_INNER", kernel)
+    p = W.random_slab(28, 300, 16, 2).replace(tol=1e-11)
+    o = Oracle(p)
+    with oci.Solver(p, precision=oci.FP32_IR) as s:
+        info = s.info()
+        assert info["inner_kernel"] == (1 if kernel == "tma" else 0)
+        for k in range(2):
+            r = o.step(OCI)
+            st = s.step()
+            assert st["status"] == 0 and abs(st["iters"] - r["iters"]) <= 2
+            assert rel(s.phi(), r["phi"]) < 1e-10
