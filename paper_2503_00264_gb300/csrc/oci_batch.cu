@@ -56,108 +56,115 @@ __global__ void __launch_bounds__(256) k_b_sweep(BatchClassDev c, DevState *__re
   double *y_s = sm + (size_t)G * N * 4 * CB;
   __shared__ double red[8];
   const int N2 = N / 2;
-  for (int tile = blockIdx.x; tile < c.n_tiles; tile += gridDim.x) {
-    const int s = c.tile_slab[tile];
+  // Tiles are dealt round-robin (tile t to block t mod grid); walk the slabs and
+  // jump straight to this block's tiles of every slab that has not converged,
+  // so converged slabs cost one flag read instead of one per tile.
+  for (int s = 0; s < c.n_slabs; s++) {
     if (ds[s].done) continue;  // uniform over the block
-    const int cur = ds[s].cur;
-    const double *__restrict__ Pin = cur ? c.Psi1 : c.Psi0;
-    double *__restrict__ Pout = cur ? c.Psi0 : c.Psi1;
-    const int j = c.tile_first_cell[tile] + cl;
-    const int jl = j - c.slab_start[s];
-    const int Js = c.slab_J[s];
-    const bool active = jl < Js;
-    const int tau = active ? c.type[j] : 0;
-    const size_t tb = (size_t)tau * G * N;
-    const double *inc = c.inc + (size_t)s * 2 * G * N * 2;
-    double y0 = 0.0, y1 = 0.0, y2 = 0.0, y3 = 0.0;
-    if (active) {
-#pragma unroll 2
-      for (int m = 0; m < N; m++) {
-        const int gm = g * N + m;
-        const size_t base = (size_t)gm * 4 * Jc + j;
-        double uk, uh;
-        if (m >= N2) {
-          if (jl > 0) {
-            uk = Pin[base + (size_t)Jc - 1];
-            uh = Pin[base + 3 * (size_t)Jc - 1];
+    const int t0 = c.slab_tile0[s], t1 = c.slab_tile1[s];
+    const int G_ = gridDim.x;
+    const int first = t0 + (((int)blockIdx.x - t0 % G_) % G_ + G_) % G_;
+    for (int tile = first; tile < t1; tile += G_) {
+      const int cur = ds[s].cur;
+      const double *__restrict__ Pin = cur ? c.Psi1 : c.Psi0;
+      double *__restrict__ Pout = cur ? c.Psi0 : c.Psi1;
+      const int j = c.tile_first_cell[tile] + cl;
+      const int jl = j - c.slab_start[s];
+      const int Js = c.slab_J[s];
+      const bool active = jl < Js;
+      const int tau = active ? c.type[j] : 0;
+      const size_t tb = (size_t)tau * G * N;
+      const double *inc = c.inc + (size_t)s * 2 * G * N * 2;
+      double y0 = 0.0, y1 = 0.0, y2 = 0.0, y3 = 0.0;
+      if (active) {
+  #pragma unroll 2
+        for (int m = 0; m < N; m++) {
+          const int gm = g * N + m;
+          const size_t base = (size_t)gm * 4 * Jc + j;
+          double uk, uh;
+          if (m >= N2) {
+            if (jl > 0) {
+              uk = Pin[base + (size_t)Jc - 1];
+              uh = Pin[base + 3 * (size_t)Jc - 1];
+            } else {
+              uk = inc[gm * 2 + 0];
+              uh = inc[gm * 2 + 1];
+            }
           } else {
-            uk = inc[gm * 2 + 0];
-            uh = inc[gm * 2 + 1];
+            if (jl < Js - 1) {
+              uk = Pin[base + 1];
+              uh = Pin[base + 2 * (size_t)Jc + 1];
+            } else {
+              uk = inc[(G * N + gm) * 2 + 0];
+              uh = inc[(G * N + gm) * 2 + 1];
+            }
           }
-        } else {
-          if (jl < Js - 1) {
-            uk = Pin[base + 1];
-            uh = Pin[base + 2 * (size_t)Jc + 1];
-          } else {
-            uk = inc[(G * N + gm) * 2 + 0];
-            uh = inc[(G * N + gm) * 2 + 1];
+          const double *C = c.Cin + (tb + gm) * 8;
+          const double t0 = fma(C[1], uh, fma(C[0], uk, c.tc[base]));
+          const double t1 = fma(C[3], uh, fma(C[2], uk, c.tc[base + (size_t)Jc]));
+          const double t2 = fma(C[5], uh, fma(C[4], uk, c.tc[base + 2 * (size_t)Jc]));
+          const double t3 = fma(C[7], uh, fma(C[6], uk, c.tc[base + 3 * (size_t)Jc]));
+          double *ts = t_s + (size_t)(gm * 4) * CB + cl;
+          ts[0] = t0;
+          ts[CB] = t1;
+          ts[2 * CB] = t2;
+          ts[3 * CB] = t3;
+          const double wm = c.w[m];
+          y0 = fma(wm, t0, y0);
+          y1 = fma(wm, t1, y1);
+          y2 = fma(wm, t2, y2);
+          y3 = fma(wm, t3, y3);
+        }
+        double *ys = y_s + (size_t)(g * 4) * CB + cl;
+        ys[0] = y0;
+        ys[CB] = y1;
+        ys[2 * CB] = y2;
+        ys[3 * CB] = y3;
+      }
+      __syncthreads();
+      double e2 = 0.0;
+      if (active) {
+        const int G4 = 4 * G;
+        const double *M = c.Mp + (size_t)tau * G4 * G4 + (size_t)(g * 4) * G4;
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        for (int k = 0; k < G4; k++) {
+          const double yk = y_s[(size_t)k * CB + cl];
+          s0 = fma(M[k], yk, s0);
+          s1 = fma(M[G4 + k], yk, s1);
+          s2 = fma(M[2 * G4 + k], yk, s2);
+          s3 = fma(M[3 * G4 + k], yk, s3);
+        }
+  #pragma unroll 2
+        for (int m = 0; m < N; m++) {
+          const int gm = g * N + m;
+          const size_t base = (size_t)gm * 4 * Jc + j;
+          const double *L = c.Linv + (tb + gm) * 16;
+          const double *ts = t_s + (size_t)(gm * 4) * CB + cl;
+          double o[4];
+  #pragma unroll
+          for (int p = 0; p < 4; p++)
+            o[p] = fma(L[p * 4 + 3], s3, fma(L[p * 4 + 2], s2, fma(L[p * 4 + 1], s1, fma(L[p * 4 + 0], s0, ts[p * CB]))));
+  #pragma unroll
+          for (int p = 0; p < 4; p++) {
+            const double d = o[p] - Pin[base + (size_t)p * Jc];
+            e2 = fma(d, d, e2);
+            Pout[base + (size_t)p * Jc] = o[p];
           }
         }
-        const double *C = c.Cin + (tb + gm) * 8;
-        const double t0 = fma(C[1], uh, fma(C[0], uk, c.tc[base]));
-        const double t1 = fma(C[3], uh, fma(C[2], uk, c.tc[base + (size_t)Jc]));
-        const double t2 = fma(C[5], uh, fma(C[4], uk, c.tc[base + 2 * (size_t)Jc]));
-        const double t3 = fma(C[7], uh, fma(C[6], uk, c.tc[base + 3 * (size_t)Jc]));
-        double *ts = t_s + (size_t)(gm * 4) * CB + cl;
-        ts[0] = t0;
-        ts[CB] = t1;
-        ts[2 * CB] = t2;
-        ts[3 * CB] = t3;
-        const double wm = c.w[m];
-        y0 = fma(wm, t0, y0);
-        y1 = fma(wm, t1, y1);
-        y2 = fma(wm, t2, y2);
-        y3 = fma(wm, t3, y3);
       }
-      double *ys = y_s + (size_t)(g * 4) * CB + cl;
-      ys[0] = y0;
-      ys[CB] = y1;
-      ys[2 * CB] = y2;
-      ys[3 * CB] = y3;
-    }
-    __syncthreads();
-    double e2 = 0.0;
-    if (active) {
-      const int G4 = 4 * G;
-      const double *M = c.Mp + (size_t)tau * G4 * G4 + (size_t)(g * 4) * G4;
-      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-      for (int k = 0; k < G4; k++) {
-        const double yk = y_s[(size_t)k * CB + cl];
-        s0 = fma(M[k], yk, s0);
-        s1 = fma(M[G4 + k], yk, s1);
-        s2 = fma(M[2 * G4 + k], yk, s2);
-        s3 = fma(M[3 * G4 + k], yk, s3);
+      // fixed-order block sum
+      const int tid = threadIdx.y * CB + threadIdx.x;
+  #pragma unroll
+      for (int o = 16; o > 0; o >>= 1) e2 += __shfl_down_sync(0xffffffffu, e2, o);
+      if ((tid & 31) == 0) red[tid >> 5] = e2;
+      __syncthreads();
+      if (tid == 0) {
+        double v = 0.0;
+        for (int i = 0; i < (CB * G + 31) / 32; i++) v += red[i];
+        c.partials[tile] = v;
       }
-#pragma unroll 2
-      for (int m = 0; m < N; m++) {
-        const int gm = g * N + m;
-        const size_t base = (size_t)gm * 4 * Jc + j;
-        const double *L = c.Linv + (tb + gm) * 16;
-        const double *ts = t_s + (size_t)(gm * 4) * CB + cl;
-        double o[4];
-#pragma unroll
-        for (int p = 0; p < 4; p++)
-          o[p] = fma(L[p * 4 + 3], s3, fma(L[p * 4 + 2], s2, fma(L[p * 4 + 1], s1, fma(L[p * 4 + 0], s0, ts[p * CB]))));
-#pragma unroll
-        for (int p = 0; p < 4; p++) {
-          const double d = o[p] - Pin[base + (size_t)p * Jc];
-          e2 = fma(d, d, e2);
-          Pout[base + (size_t)p * Jc] = o[p];
-        }
-      }
+      __syncthreads();  // t_s / y_s / red reused by the next tile
     }
-    // fixed-order block sum
-    const int tid = threadIdx.y * CB + threadIdx.x;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) e2 += __shfl_down_sync(0xffffffffu, e2, o);
-    if ((tid & 31) == 0) red[tid >> 5] = e2;
-    __syncthreads();
-    if (tid == 0) {
-      double v = 0.0;
-      for (int i = 0; i < (CB * G + 31) / 32; i++) v += red[i];
-      c.partials[tile] = v;
-    }
-    __syncthreads();  // t_s / y_s / red reused by the next tile
   }
 }
 
