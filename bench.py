@@ -306,26 +306,37 @@ def run_ours(args):
                     multigroup[name]["phi_rel_vs_fp64"] = float(np.abs(sv.phi() - phi_mg).max() / np.abs(phi_mg).max())
 
     # batched form: 256 independent slabs (J in [1k, 64k], N in {4..32}, G in {1,4}) in one
-    # graph launch per time step; one step, sweeps capped per slab
+    # graph launch per time step; one step, sweeps capped per slab; FP64 and the mixed form
     batched = None
     if not args.no_batched:
         probs = [b.replace(max_iter=args.batch_max_iter) for b in W.batch_of_slabs(256)]
-        with oci.BatchSolver(probs, stream=stream.cuda_stream) as bs:
-            t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            t0e.record(stream)
-            sts = bs.step(allow_noconv=True)
-            t1e.record(stream)
-            torch.cuda.synchronize()
-            ms_b = t0e.elapsed_time(t1e)
-        upd = sum(p_.unknowns * st["iters"] for p_, st in zip(probs, sts))
         batched = {"slabs": len(probs), "cells": int(sum(p_.J for p_ in probs)),
-                   "unknowns": int(sum(p_.unknowns for p_ in probs)),
-                   "value": upd / (ms_b * 1e-3), "unit": UNIT, "ms_per_step": ms_b,
-                   "converged": int(sum(st["status"] == 0 for st in sts)), "max_iter": args.batch_max_iter,
-                   "sweeps_min_median_max": [int(np.min([st["iters"] for st in sts])),
-                                             int(np.median([st["iters"] for st in sts])),
-                                             int(np.max([st["iters"] for st in sts]))],
-                   "max_balance_rel": float(max(max(st["balance_rel"]) for st in sts if st["status"] == 0))}
+                   "unknowns": int(sum(p_.unknowns for p_ in probs)), "max_iter": args.batch_max_iter}
+        sample = list(range(0, len(probs), 16))
+        phi_b = {}
+        for name, prec in (("fp64", oci.FP64), ("fp32_ir", oci.FP32_IR)):
+            with oci.BatchSolver(probs, stream=stream.cuda_stream, precision=prec) as bs:
+                t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                t0e.record(stream)
+                sts = bs.step(allow_noconv=True)
+                t1e.record(stream)
+                torch.cuda.synchronize()
+                ms_b = t0e.elapsed_time(t1e)
+                upd = sum(p_.unknowns * st["iters"] for p_, st in zip(probs, sts))
+                ent = {"value": upd / (ms_b * 1e-3), "unit": UNIT, "ms_per_step": ms_b,
+                       "converged": int(sum(st["status"] == 0 for st in sts)),
+                       "sweeps_min_median_max": [int(np.min([st["iters"] for st in sts])),
+                                                 int(np.median([st["iters"] for st in sts])),
+                                                 int(np.max([st["iters"] for st in sts]))],
+                       "max_balance_rel": float(max(max(st["balance_rel"]) for st in sts if st["status"] == 0))}
+                ok = [i for i in sample if sts[i]["status"] == 0]
+                if name == "fp64":
+                    phi_b = {i: bs.phi(i) for i in ok}
+                else:
+                    both = [i for i in ok if i in phi_b]
+                    ent["phi_rel_vs_fp64_sampled"] = float(max(
+                        (np.abs(bs.phi(i) - phi_b[i]).max() / np.abs(phi_b[i]).max() for i in both), default=0.0))
+                batched[name] = ent
 
     # dominant kernel: the fused sweep; its launch time from a run of n sweeps
     n_sw = 50

@@ -18,7 +18,10 @@
 // cell by the slab's incident flux.
 #include <math.h>
 
+#include <algorithm>
+
 #include "oci_batch.h"
+#include "oci_device.cuh"
 
 namespace oci {
 
@@ -314,6 +317,293 @@ __global__ void k_b_balance_final(BatchClassDev c, const DevState *__restrict__ 
   bg[5] = tot[1]; bg[6] = lE; bg[7] = tot[3]; bg[8] = tot[5]; bg[9] = tot[7];
 }
 
+// ---------------------------------------------------------------- mixed form
+// The mixed-precision form of oci_mixed.cu per slab: every slab has its own
+// FP32 correction state (ping-pong index, block count, refinement flag) in its
+// DevState and the same stop rule / refinement decisions (finish_mixed).
+
+// c = dx/4 Q + dx/(2 v dt) psi_prev on rows kL, kR (Eq. rhs_sg), not pre-multiplied.
+__global__ void k_b_mx_step_const(BatchClassDev c) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int gm = blockIdx.y;
+  const int N = c.N, G = c.G, Jc = c.Jc;
+  if (j >= Jc || c.seg[j] < 0) return;
+  const int g = gm / N;
+  const int tau = c.type[j];
+  const double dx = c.tdx[tau];
+  const double ah = c.tah[(size_t)tau * G + g];
+#pragma unroll
+  for (int p = 0; p < 4; p++) {
+    double v = c.Q ? dx / 4.0 * c.Q[(size_t)(g * 4 + p) * Jc + j] : 0.0;
+    if (p < 2) v += ah * c.psi_prev[(size_t)(gm * 2 + p) * Jc + j];
+    c.cvec[(size_t)(gm * 4 + p) * Jc + j] = v;
+  }
+}
+
+// FP32 inner sweep on the tiles of the slabs still iterating (layout of k_b_sweep).
+__global__ void __launch_bounds__(256) k_b_mx_inner(BatchClassDev c, const DevState *__restrict__ ds) {
+  extern __shared__ float smf[];
+  __shared__ double red[8];
+  const int CB = blockDim.x, N = c.N, G = c.G, Jc = c.Jc;
+  const int cl = threadIdx.x, g = threadIdx.y;
+  float *t_s = smf;
+  float *y_s = smf + (size_t)G * N * 4 * CB;
+  const int N2 = N / 2;
+  for (int s = 0; s < c.n_slabs; s++) {
+    if (ds[s].done) continue;  // uniform
+    const bool zero = ds[s].refine || ds[s].blk_i == 0;
+    const int dcur = ds[s].dcur;
+    const float *__restrict__ Din = dcur ? c.D1 : c.D0;
+    float *__restrict__ Dout = dcur ? c.D0 : c.D1;
+    const int t0 = c.slab_tile0[s], t1 = c.slab_tile1[s];
+    const int G_ = gridDim.x;
+    const int first = t0 + (((int)blockIdx.x - t0 % G_) % G_ + G_) % G_;
+    for (int tile = first; tile < t1; tile += G_) {
+      const int j = c.tile_first_cell[tile] + cl;
+      const int jl = j - c.slab_start[s];
+      const int Js = c.slab_J[s];
+      const bool active = jl < Js;
+      const int tau = active ? c.type[j] : 0;
+      const size_t tb = (size_t)tau * G * N;
+      float y0 = 0.f, y1 = 0.f, y2 = 0.f, y3 = 0.f;
+      if (active) {
+        for (int m = 0; m < N; m++) {
+          const int gm = g * N + m;
+          const size_t base = (size_t)gm * 4 * Jc + j;
+          float uk = 0.f, uh = 0.f;
+          if (!zero) {
+            if (m >= N2) {
+              if (jl > 0) {
+                uk = Din[base + (size_t)Jc - 1];
+                uh = Din[base + 3 * (size_t)Jc - 1];
+              }
+            } else if (jl < Js - 1) {
+              uk = Din[base + 1];
+              uh = Din[base + 2 * (size_t)Jc + 1];
+            }
+          }
+          const float *C = c.Cin32 + (tb + gm) * 8;
+          const float t0v = fmaf(C[1], uh, fmaf(C[0], uk, c.z32[base]));
+          const float t1v = fmaf(C[3], uh, fmaf(C[2], uk, c.z32[base + (size_t)Jc]));
+          const float t2v = fmaf(C[5], uh, fmaf(C[4], uk, c.z32[base + 2 * (size_t)Jc]));
+          const float t3v = fmaf(C[7], uh, fmaf(C[6], uk, c.z32[base + 3 * (size_t)Jc]));
+          float *ts = t_s + (size_t)(gm * 4) * CB + cl;
+          ts[0] = t0v;
+          ts[CB] = t1v;
+          ts[2 * CB] = t2v;
+          ts[3 * CB] = t3v;
+          const float wm = c.w32[m];
+          y0 = fmaf(wm, t0v, y0);
+          y1 = fmaf(wm, t1v, y1);
+          y2 = fmaf(wm, t2v, y2);
+          y3 = fmaf(wm, t3v, y3);
+        }
+        float *ys = y_s + (size_t)(g * 4) * CB + cl;
+        ys[0] = y0;
+        ys[CB] = y1;
+        ys[2 * CB] = y2;
+        ys[3 * CB] = y3;
+      }
+      __syncthreads();
+      float e2 = 0.f;
+      if (active) {
+        const int G4 = 4 * G;
+        const float *M = c.Mp32 + (size_t)tau * G4 * G4 + (size_t)(g * 4) * G4;
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+        for (int k = 0; k < G4; k++) {
+          const float yk = y_s[(size_t)k * CB + cl];
+          s0 = fmaf(M[k], yk, s0);
+          s1 = fmaf(M[G4 + k], yk, s1);
+          s2 = fmaf(M[2 * G4 + k], yk, s2);
+          s3 = fmaf(M[3 * G4 + k], yk, s3);
+        }
+        for (int m = 0; m < N; m++) {
+          const int gm = g * N + m;
+          const size_t base = (size_t)gm * 4 * Jc + j;
+          const float *L = c.Linv32 + (tb + gm) * 16;
+          const float *ts = t_s + (size_t)(gm * 4) * CB + cl;
+#pragma unroll
+          for (int p = 0; p < 4; p++) {
+            const float o = fmaf(L[p * 4 + 3], s3, fmaf(L[p * 4 + 2], s2, fmaf(L[p * 4 + 1], s1, fmaf(L[p * 4 + 0], s0, ts[p * CB]))));
+            const float d = zero ? o : o - Din[base + (size_t)p * Jc];
+            e2 = fmaf(d, d, e2);
+            Dout[base + (size_t)p * Jc] = o;
+          }
+        }
+      }
+      double v = (double)e2;
+      const int tid = threadIdx.y * CB + threadIdx.x;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      if ((tid & 31) == 0) red[tid >> 5] = v;
+      __syncthreads();
+      if (tid == 0) {
+        double acc = 0.0;
+        for (int i = 0; i < (CB * G + 31) / 32; i++) acc += red[i];
+        c.partials[tile] = acc;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// One warp per slab: fixed-order sum of its tile partials, then the mixed-form
+// stop rule and refinement decision; the last slab to finish ends the loop.
+__global__ void k_b_mx_finalize(BatchClassDev c, DevState *__restrict__ ds, int *active, int use_cond,
+                                cudaGraphConditionalHandle cond) {
+  const int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (s >= c.n_slabs) return;
+  if (ds[s].done) {
+    // a slab that finished in the previous body: its last refinement has been
+    // applied by that body's outer kernel; settle it so no later body repeats it
+    if (lane == 0 && ds[s].refine) {
+      ds[s].cur ^= 1;
+      ds[s].refine = 0;
+      ds[s].blk_i = 0;
+    }
+    return;
+  }
+  double v = 0.0;
+  for (int t = c.slab_tile0[s] + lane; t < c.slab_tile1[s]; t += 32) v += c.partials[t];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if (lane != 0) return;
+  finish_mixed(&ds[s], nullptr, sqrt(v), cond, 0);
+  if (ds[s].done) {
+    const int before = atomicSub(active, 1);
+    if (before == 1 && use_cond) cudaGraphSetConditional(cond, 0);
+  }
+}
+
+// FP64 refinement per slab (k_mx_outer with slab ends): mode 0 residual of
+// Psi[cur] for every slab; mode 1 for slabs that asked for it: Psi[cur^1] =
+// Psi[cur] + delta[dcur] and, unless the slab is done, its residual.
+__global__ void __launch_bounds__(256) k_b_mx_outer(BatchClassDev c, const DevState *__restrict__ ds, int mode) {
+  extern __shared__ double smd[];
+  const int CB = blockDim.x, N = c.N, G = c.G, Jc = c.Jc;
+  const int cl = threadIdx.x, g = threadIdx.y;
+  const int N2 = N / 2;
+  for (int s = 0; s < c.n_slabs; s++) {
+    if (mode == 1 && !ds[s].refine) continue;  // uniform
+    if (mode == 0 && ds[s].done) continue;
+    const bool apply = mode != 0;
+    const bool resid = mode == 0 || !ds[s].done;
+    const int cur = ds[s].cur;
+    const double *__restrict__ Pin = cur ? c.Psi1 : c.Psi0;
+    double *__restrict__ Pout = cur ? c.Psi0 : c.Psi1;
+    const float *__restrict__ Dl = ds[s].dcur ? c.D1 : c.D0;
+    const double *inc = c.inc + (size_t)s * 2 * G * N * 2;
+    const int t0 = c.slab_tile0[s], t1 = c.slab_tile1[s];
+    const int G_ = gridDim.x;
+    const int first = t0 + (((int)blockIdx.x - t0 % G_) % G_ + G_) % G_;
+    for (int tile = first; tile < t1; tile += G_) {
+      const int j = c.tile_first_cell[tile] + cl;
+      const int jl = j - c.slab_start[s];
+      const int Js = c.slab_J[s];
+      const bool active = jl < Js;
+      const int tau = active ? c.type[j] : 0;
+      double ph[4] = {0.0, 0.0, 0.0, 0.0};
+      if (active) {
+        for (int m = 0; m < N; m++) {
+          const int gm = g * N + m;
+          const size_t base = (size_t)gm * 4 * Jc + j;
+          const double wm = c.w[m];
+#pragma unroll
+          for (int p = 0; p < 4; p++) {
+            double v = Pin[base + (size_t)p * Jc];
+            if (apply) {
+              v += (double)Dl[base + (size_t)p * Jc];
+              Pout[base + (size_t)p * Jc] = v;
+            }
+            ph[p] = fma(wm, v, ph[p]);
+          }
+        }
+      }
+      if (!resid) continue;  // uniform over the block
+      double *ph_s = smd;
+      __syncthreads();
+#pragma unroll
+      for (int p = 0; p < 4; p++) ph_s[(size_t)(g * 4 + p) * CB + cl] = ph[p];
+      __syncthreads();
+      if (!active) continue;
+      double sv[4] = {0.0, 0.0, 0.0, 0.0};
+      for (int gp = 0; gp < G; gp++) {
+        const double k = c.Kap[((size_t)tau * G + gp) * G + g];
+#pragma unroll
+        for (int p = 0; p < 4; p++) sv[p] = fma(k, ph_s[(size_t)(gp * 4 + p) * CB + cl], sv[p]);
+      }
+      const double *__restrict__ P = apply ? Pout : Pin;
+      for (int m = 0; m < N; m++) {
+        const int gm = g * N + m;
+        const size_t base = (size_t)gm * 4 * Jc + j;
+        const double v0 = P[base], v1 = P[base + (size_t)Jc], v2 = P[base + 2 * (size_t)Jc],
+                     v3 = P[base + 3 * (size_t)Jc];
+        const double *L = c.Lco + ((size_t)tau * G * N + gm) * 5;
+        const double a = L[0], hm = L[1], ha = L[2], al = L[3], aa = L[4];
+        double r0 = c.cvec[base] + sv[0];
+        double r1 = c.cvec[base + (size_t)Jc] + sv[1];
+        double r2 = c.cvec[base + 2 * (size_t)Jc] + sv[2];
+        double r3 = c.cvec[base + 3 * (size_t)Jc] + sv[3];
+        if (m >= N2) {
+          double uk, uh;
+          if (jl > 0) {
+            const size_t nb = base - 1;
+            uk = Pin[nb + (size_t)Jc];
+            uh = Pin[nb + 3 * (size_t)Jc];
+            if (apply) {
+              uk += (double)Dl[nb + (size_t)Jc];
+              uh += (double)Dl[nb + 3 * (size_t)Jc];
+            }
+          } else {
+            uk = inc[gm * 2 + 0];
+            uh = inc[gm * 2 + 1];
+          }
+          r0 = fma(c.mu[m], uk, r0);
+          r2 = fma(c.mu[m], uh, r2);
+        } else {
+          double uk, uh;
+          if (jl < Js - 1) {
+            const size_t nb = base + 1;
+            uk = Pin[nb];
+            uh = Pin[nb + 2 * (size_t)Jc];
+            if (apply) {
+              uk += (double)Dl[nb];
+              uh += (double)Dl[nb + 2 * (size_t)Jc];
+            }
+          } else {
+            uk = inc[(G * N + gm) * 2 + 0];
+            uh = inc[(G * N + gm) * 2 + 1];
+          }
+          r1 = fma(-c.mu[m], uk, r1);
+          r3 = fma(-c.mu[m], uh, r3);
+        }
+        r0 = fma(-a, v0, fma(-hm, v1, fma(-ha, v2, r0)));
+        r1 = fma(hm, v0, fma(-a, v1, fma(-ha, v3, r1)));
+        r2 = fma(al, v0, fma(-aa, v2, fma(-hm, v3, r2)));
+        r3 = fma(al, v1, fma(hm, v2, fma(-aa, v3, r3)));
+        const float f0 = (float)r0, f1 = (float)r1, f2 = (float)r2, f3 = (float)r3;
+        const float *Li = c.Linv32 + ((size_t)tau * G * N + gm) * 16;
+#pragma unroll
+        for (int p = 0; p < 4; p++)
+          c.z32[base + (size_t)p * Jc] =
+              fmaf(Li[p * 4 + 3], f3, fmaf(Li[p * 4 + 2], f2, fmaf(Li[p * 4 + 1], f1, Li[p * 4 + 0] * f0)));
+      }
+    }
+  }
+}
+
+// After the loop: settle a refinement made by the last body (flip Psi, zero correction).
+__global__ void k_b_mx_settle(int n_slabs, DevState *ds) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n_slabs) return;
+  if (ds[s].refine) {
+    ds[s].cur ^= 1;
+    ds[s].refine = 0;
+    ds[s].blk_i = 0;
+  }
+}
+
 // ---------------------------------------------------------------- launches
 size_t b_sweep_smem(int N, int G, int cb) {
   return (size_t)cb * ((size_t)G * N * 4 * 8 + (size_t)G * 4 * 8);
@@ -342,12 +632,51 @@ void launch_b_carry(BatchClass &c, DevState *ds, cudaStream_t st) {
 }
 
 const void *k_b_sweep_ptr() { return (const void *)k_b_sweep; }
+const void *k_b_mx_inner_ptr() { return (const void *)k_b_mx_inner; }
+
+size_t b_mx_smem(int N, int G, int cb) { return (size_t)cb * ((size_t)G * N * 4 + (size_t)G * 4) * 4; }
+
+void launch_b_mx_step_const(BatchClass &c, cudaStream_t st) {
+  dim3 grid((c.d.Jc + 255) / 256, c.d.G * c.d.N);
+  k_b_mx_step_const<<<grid, 256, 0, st>>>(c.d);
+}
+
+void launch_b_mx_inner(BatchClass &c, DevState *ds, cudaStream_t st) {
+  k_b_mx_inner<<<c.grid, dim3(c.cb, c.d.G), b_mx_smem(c.d.N, c.d.G, c.cb), st>>>(c.d, ds);
+}
+
+void launch_b_mx_finalize(BatchClass &c, DevState *ds, int *active, int use_cond, cudaGraphConditionalHandle cond,
+                          cudaStream_t st) {
+  const int warps = 4;
+  k_b_mx_finalize<<<(c.d.n_slabs + warps - 1) / warps, 32 * warps, 0, st>>>(c.d, ds, active, use_cond, cond);
+}
+
+void launch_b_mx_outer(BatchClass &c, DevState *ds, int mode, cudaStream_t st) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = std::min(c.d.n_tiles, 4 * sms);
+  k_b_mx_outer<<<grid > 0 ? grid : 1, dim3(c.cb, c.d.G), (size_t)c.cb * c.d.G * 4 * sizeof(double), st>>>(c.d, ds,
+                                                                                                         mode);
+}
+
+void launch_b_mx_settle(BatchClass &c, DevState *ds, cudaStream_t st) {
+  k_b_mx_settle<<<(c.d.n_slabs + 127) / 128, 128, 0, st>>>(c.d.n_slabs, ds);
+}
 
 int b_max_grid(int N, int G, int cb) {
   int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_b_sweep, cb * G, b_sweep_smem(N, G, cb));
+  return sms * (per > 0 ? per : 1);
+}
+
+int b_mx_max_grid(int N, int G, int cb) {
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_b_mx_inner, cb * G, b_mx_smem(N, G, cb));
   return sms * (per > 0 ? per : 1);
 }
 

@@ -27,10 +27,16 @@ struct BatchClassDev {
   double *partials;                // [n_tiles]
   double *bal_partials;            // [Jc/32][G][8]
   double *bal;                     // [n_slabs][G][10]
+  // mixed-precision form (FP32 inner sweeps on a correction, FP64 refinement)
+  float *D0, *D1, *z32;            // [G][N][4][Jc]
+  double *cvec;                    // [G][N][4][Jc] per-step constant c (not pre-multiplied); aliases tc
+  const float *Linv32, *Cin32, *Mp32, *w32;
+  const double *Lco;               // [T][G][N][5] {a, mu/2, alpha/2, alpha, alpha+a}
 };
 
 struct BatchClass {
   BatchClassDev d{};
+  bool mixed = false;
   int cb = 128;     // cells per tile (autotuned)
   int grid = 0;     // persistent grid size
   int slab0 = 0;    // index of the class's first slab in the batch
@@ -41,6 +47,7 @@ struct BatchClass {
 
 struct Batch {
   int n = 0;
+  int precision = OCI_FP64;
   std::vector<BatchClass> cls;
   std::vector<int> slab_class, slab_local;  // batch slab -> (class, local index)
   std::vector<int> J, N, G, max_iter;
@@ -63,5 +70,15 @@ void launch_b_finalize(BatchClass &c, DevState *ds, int *active, int use_cond, c
                        cudaStream_t st);
 void launch_b_carry(BatchClass &c, DevState *ds, cudaStream_t st);
 const void *k_b_sweep_ptr();
+// mixed-precision batched form
+void launch_b_mx_step_const(BatchClass &c, cudaStream_t st);
+void launch_b_mx_inner(BatchClass &c, DevState *ds, cudaStream_t st);
+void launch_b_mx_finalize(BatchClass &c, DevState *ds, int *active, int use_cond, cudaGraphConditionalHandle cond,
+                          cudaStream_t st);
+void launch_b_mx_outer(BatchClass &c, DevState *ds, int mode, cudaStream_t st);
+void launch_b_mx_settle(BatchClass &c, DevState *ds, cudaStream_t st);
+size_t b_mx_smem(int N, int G, int cb);
+int b_mx_max_grid(int N, int G, int cb);
+const void *k_b_mx_inner_ptr();
 
 }  // namespace oci

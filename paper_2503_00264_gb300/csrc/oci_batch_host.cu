@@ -21,7 +21,11 @@ namespace oci {
     if (e_ != cudaSuccess) return cuda_fail(e_, #call);  \
   } while (0)
 
-constexpr int kPad = 128;  // slab padding (multiple of every tile size and of the 32-cell carry block)
+constexpr int kPad = 128;
+// refinement schedule of the mixed form (as the single-slab FP32 form): refine
+// after kBatchMxKmax inner sweeps or once e fell below kBatchMxTheta of the block's first
+constexpr int kBatchMxKmax = 64;
+constexpr double kBatchMxTheta = 1e-3;  // slab padding (multiple of every tile size and of the 32-cell carry block)
 
 // [J][K] host/device rows -> class SoA column block: dst[k*stride + j], j < J only.
 __global__ void k_bt_in(int J, int stride, int K, const double *__restrict__ src, double *__restrict__ dst) {
@@ -69,7 +73,7 @@ static int build_tiles(BatchClass &c, int cb, int32_t *tile_slab, int32_t *tile_
   BCK(cudaMemcpyAsync(t1, b.data(), b.size() * 4, cudaMemcpyHostToDevice, st));
   BCK(cudaStreamSynchronize(st));  // host vectors go out of scope
   c.cb = cb;
-  c.grid = std::min(c.d.n_tiles, b_max_grid(c.d.N, c.d.G, cb));
+  c.grid = std::min(c.d.n_tiles, c.mixed ? b_mx_max_grid(c.d.N, c.d.G, cb) : b_max_grid(c.d.N, c.d.G, cb));
   if (c.grid < 1) c.grid = 1;
   return OCI_OK;
 }
@@ -82,7 +86,7 @@ static int setup_class(Batch &B, BatchClass &c, const oci_problem *probs) {
   c.d.n_slabs = (int)c.slabs.size();
   std::vector<double> mu, w;
   gauss_legendre(N, mu, w);
-  std::vector<double> Linv, Cin, Mp, Kap, tdx, tsig, tah, incv;
+  std::vector<double> Linv, Cin, Mp, Kap, tdx, tsig, tah, incv, Lcov;
   std::vector<int32_t> type, seg;
   int offset = 0, T = 0;
   for (size_t i = 0; i < c.slabs.size(); i++) {
@@ -109,6 +113,7 @@ static int setup_class(Batch &B, BatchClass &c, const oci_problem *probs) {
     Kap.insert(Kap.end(), K.begin(), K.end());
     tdx.insert(tdx.end(), dx.begin(), dx.end());
     tsig.insert(tsig.end(), sg.begin(), sg.end());
+    Lcov.insert(Lcov.end(), Lco.begin(), Lco.end());
     for (int t = 0; t < Ts; t++)
       for (int g = 0; g < G; g++) tah.push_back(dx[t] / (2.0 * p.v[g] * p.dt));
     const int Jpad = (p.J + kPad - 1) / kPad * kPad;
@@ -173,10 +178,30 @@ static int setup_class(Batch &B, BatchClass &c, const oci_problem *probs) {
   d.w = d_w; d.mu = d_mu; d.inc = d_inc; d.Q = Q;
   d.Psi0 = Psi0; d.Psi1 = Psi1; d.tc = tc; d.psi_prev = pp; d.phi = phi; d.partials = parts;
   d.bal_partials = bparts; d.bal = bal;
+  if (c.mixed) {
+    // FP32 copies of the cell tables, FP32 correction ping-pong and z = Linv r
+    auto to32 = [](const std::vector<double> &a) {
+      std::vector<float> f(a.size());
+      for (size_t i = 0; i < a.size(); i++) f[i] = (float)a[i];
+      return f;
+    };
+    float *L32, *C32, *M32, *W32, *D0, *D1, *z32;
+    double *d_Lco;
+    const std::vector<float> L32v = to32(Linv), C32v = to32(Cin), M32v = to32(Mp), W32v = to32(w);
+    if ((rc = bupload(c, &L32, L32v, st)) || (rc = bupload(c, &C32, C32v, st)) || (rc = bupload(c, &M32, M32v, st)) ||
+        (rc = bupload(c, &W32, W32v, st)) ||
+        (rc = bupload(c, &d_Lco, Lcov, st)) || (rc = balloc(c, &D0, nPsi, st)) || (rc = balloc(c, &D1, nPsi, st)) ||
+        (rc = balloc(c, &z32, nPsi, st)))
+      return rc;
+    BCK(cudaStreamSynchronize(st));  // host vectors of the uploads go out of scope
+    d.Linv32 = L32; d.Cin32 = C32; d.Mp32 = M32; d.w32 = W32; d.Lco = d_Lco;
+    d.D0 = D0; d.D1 = D1; d.z32 = z32;
+    d.cvec = tc;  // the mixed form keeps c itself where the FP64 form keeps Linv c
+  }
   // ---- autotune the tile size of this class (CUDA events over a few sweeps)
   std::vector<int> cands;
   for (int cb : {32, 64, 128})
-    if (cb * G <= 256 && b_sweep_smem(N, G, cb) <= 100 * 1024) cands.push_back(cb);
+    if (cb * G <= 256 && (c.mixed ? b_mx_smem(N, G, cb) : b_sweep_smem(N, G, cb)) <= 100 * 1024) cands.push_back(cb);
   if (cands.empty()) cands.push_back(32);
   int best_cb = cands.back();
   const char *at = getenv("OCI_AUTOTUNE");
@@ -185,14 +210,21 @@ static int setup_class(Batch &B, BatchClass &c, const oci_problem *probs) {
       DevState &x = B.h_ds[c.slab0 + i];
       x.done = 0;
       x.cur = 0;
+      x.refine = 0;
+      x.blk_i = 0;  // the mixed inner sweep starts from a zero correction
+      x.dcur = 0;
     }
     BCK(cudaMemcpyAsync(B.ds + c.slab0, B.h_ds + c.slab0, sizeof(DevState) * c.d.n_slabs, cudaMemcpyHostToDevice, st));
     float best = 1e30f;
     for (int cb : cands) {
       if ((rc = build_tiles(c, cb, d_ts, d_tf, d_t0, d_t1, st))) return rc;
-      launch_b_sweep(c, B.ds + c.slab0, st);
+      auto sweep = [&]() {
+        if (c.mixed) launch_b_mx_inner(c, B.ds + c.slab0, st);
+        else launch_b_sweep(c, B.ds + c.slab0, st);
+      };
+      sweep();
       BCK(cudaEventRecord(B.ev0, st));
-      for (int r = 0; r < 3; r++) launch_b_sweep(c, B.ds + c.slab0, st);
+      for (int r = 0; r < 3; r++) sweep();
       BCK(cudaEventRecord(B.ev1, st));
       BCK(cudaEventSynchronize(B.ev1));
       BCK(cudaGetLastError());
@@ -205,6 +237,10 @@ static int setup_class(Batch &B, BatchClass &c, const oci_problem *probs) {
     }
     BCK(cudaMemsetAsync(Psi0, 0, nPsi * 8, st));
     BCK(cudaMemsetAsync(Psi1, 0, nPsi * 8, st));
+    if (c.mixed) {
+      BCK(cudaMemsetAsync(c.d.D0, 0, nPsi * 4, st));
+      BCK(cudaMemsetAsync(c.d.D1, 0, nPsi * 4, st));
+    }
     for (int i = 0; i < c.d.n_slabs; i++) B.h_ds[c.slab0 + i].done = 1;
     BCK(cudaMemcpyAsync(B.ds + c.slab0, B.h_ds + c.slab0, sizeof(DevState) * c.d.n_slabs, cudaMemcpyHostToDevice, st));
   }
@@ -228,8 +264,14 @@ static int build_batch_graph(Batch &B) {
   BCK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
   cudaError_t e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
-    for (auto &c : B.cls) launch_b_sweep(c, B.ds + c.slab0, cs);
-    for (auto &c : B.cls) launch_b_finalize(c, B.ds + c.slab0, B.active, 1, cond, cs);
+    if (B.precision == OCI_FP64) {
+      for (auto &c : B.cls) launch_b_sweep(c, B.ds + c.slab0, cs);
+      for (auto &c : B.cls) launch_b_finalize(c, B.ds + c.slab0, B.active, 1, cond, cs);
+    } else {
+      for (auto &c : B.cls) launch_b_mx_inner(c, B.ds + c.slab0, cs);
+      for (auto &c : B.cls) launch_b_mx_finalize(c, B.ds + c.slab0, B.active, 1, cond, cs);
+      for (auto &c : B.cls) launch_b_mx_outer(c, B.ds + c.slab0, 1, cs);
+    }
     e = cudaStreamEndCapture(cs, &body);
   }
   cudaStreamDestroy(cs);
@@ -262,6 +304,7 @@ void free_batch(Batch *B) {
 static int batch_setup(const oci_problem *probs, int n, Batch &B) {
   B.n = n;
   B.stream = (cudaStream_t)probs[0].stream;
+  B.precision = probs[0].precision;
   std::map<std::pair<int, int>, int> key;
   size_t stage = 0;
   for (int s = 0; s < n; s++) {
@@ -287,6 +330,7 @@ static int batch_setup(const oci_problem *probs, int n, Batch &B) {
     B.slab_class.push_back(ci);
     B.slab_local.push_back((int)B.cls[ci].slabs.size());
     B.cls[ci].slabs.push_back(s);
+    B.cls[ci].mixed = B.precision != OCI_FP64;
   }
   // class-contiguous slab order for the device states
   std::vector<int> order;
@@ -304,6 +348,7 @@ static int batch_setup(const oci_problem *probs, int n, Batch &B) {
   for (int i = 0; i < n; i++) B.h_ds[i].done = 1;
   BCK(cudaMemcpyAsync(B.ds, B.h_ds, sizeof(DevState) * n, cudaMemcpyHostToDevice, B.stream));
   BCK(cudaFuncSetAttribute(k_b_sweep_ptr(), cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  BCK(cudaFuncSetAttribute(k_b_mx_inner_ptr(), cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   size_t nbal = 0;
   for (auto &c : B.cls) {
     int rc = setup_class(B, c, probs);
@@ -332,14 +377,33 @@ static int batch_step(Batch &B, oci_stats *st) {
     d.max_iter = B.max_iter[i];
     d.tol = B.tol[i];
     d.e = d.e_prev = d.rho = 0.0;
+    d.dcur = 0;
+    d.blk_i = 0;
+    d.refine = 0;
+    d.applied = 0;
+    d.k_max = kBatchMxKmax;
+    d.n_refine = 0;
+    d.theta = kBatchMxTheta;
+    d.e_blk0 = 0.0;
+    d.inplace = 0;
   }
   BCK(cudaMemcpyAsync(B.ds, B.h_ds, sizeof(DevState) * B.n, cudaMemcpyHostToDevice, s));
   const int active = B.n;
   BCK(cudaMemcpyAsync(B.active, &active, sizeof(int), cudaMemcpyHostToDevice, s));
-  for (auto &c : B.cls) launch_b_step_const(c, s);
+  const bool mixed = B.precision != OCI_FP64;
+  for (auto &c : B.cls) {
+    if (mixed) {
+      launch_b_mx_step_const(c, s);        // c (not pre-multiplied)
+      launch_b_mx_outer(c, B.ds + c.slab0, 0, s);  // FP64 residual of the initial iterate
+    } else {
+      launch_b_step_const(c, s);
+    }
+  }
   BCK(cudaEventRecord(B.ev0, s));
   BCK(cudaGraphLaunch(B.graph, s));
   BCK(cudaEventRecord(B.ev1, s));
+  if (mixed)
+    for (auto &c : B.cls) launch_b_mx_settle(c, B.ds + c.slab0, s);
   for (auto &c : B.cls) launch_b_carry(c, B.ds + c.slab0, s);
   BCK(cudaMemcpyAsync(B.h_ds, B.ds, sizeof(DevState) * B.n, cudaMemcpyDeviceToHost, s));
   size_t off = 0;
@@ -428,8 +492,11 @@ int oci_batch_setup(const oci_problem *probs, int32_t n, oci_handle **out) {
   for (int s = 0; s < n; s++) {
     int rc = validate(&probs[s]);
     if (rc) return rc;
-    if (probs[s].precision != OCI_FP64 || probs[s].solver == OCI_SOLVER_DENSE_LU || probs[s].guess != OCI_GUESS_PREV)
-      return set_error("the batched form is FP64, structured solver, GUESS_PREV"), OCI_E_INVAL;
+    if ((probs[s].precision != OCI_FP64 && probs[s].precision != OCI_FP32_IR) ||
+        probs[s].solver == OCI_SOLVER_DENSE_LU || probs[s].guess != OCI_GUESS_PREV)
+      return set_error("the batched form is FP64 or FP32_IR, structured solver, GUESS_PREV"), OCI_E_INVAL;
+    if (probs[s].precision != probs[0].precision)
+      return set_error("all slabs of a batch share one precision"), OCI_E_INVAL;
     if (probs[s].stream != probs[0].stream) return set_error("all slabs of a batch share one stream"), OCI_E_INVAL;
   }
   oci_handle *h = new (std::nothrow) oci_handle();

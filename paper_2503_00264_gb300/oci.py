@@ -158,14 +158,16 @@ def _problem_struct(P, keep, precision, solver, stream, tol=None, max_iter=None,
 
 
 class BatchSolver:
-    """Many independent slabs advanced together (oci_batch_* calls)."""
+    """Many independent slabs advanced together (oci_batch_* calls); precision
+    FP64 or FP32_IR (one for the whole batch)."""
 
-    def __init__(self, probs, stream=None):
+    def __init__(self, probs, stream=None, precision: int = FP64):
         self.L = load()
         self.probs = list(probs)
         self._keep = []
         st = current_stream() if stream is None else stream
-        arr = (Problem * len(self.probs))(*[_problem_struct(p, self._keep, FP64, SOLVER_AUTO, st) for p in self.probs])
+        arr = (Problem * len(self.probs))(
+            *[_problem_struct(p, self._keep, precision, SOLVER_AUTO, st) for p in self.probs])
         self._arr = arr
         h = ctypes.c_void_p()
         _check(self.L.oci_batch_setup(arr, len(self.probs), ctypes.byref(h)))

@@ -85,4 +85,7 @@ def test_batch_setup_validates_before_device_work(lib):
                             oci._problem_struct(p, keep, oci.FP32_IR, 0, None))
     h = ctypes.c_void_p()
     assert lib.oci_batch_setup(arr, 2, ctypes.byref(h)) == oci.E_INVAL
+    assert b"one precision" in lib.oci_last_error()
     assert lib.oci_batch_setup(arr, 0, ctypes.byref(h)) == oci.E_INVAL
+    tc = (oci.Problem * 1)(oci._problem_struct(p, keep, oci.TF32_IR, 0, None))
+    assert lib.oci_batch_setup(tc, 1, ctypes.byref(h)) == oci.E_INVAL
