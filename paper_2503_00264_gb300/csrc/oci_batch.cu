@@ -171,20 +171,18 @@ __global__ void __launch_bounds__(256) k_b_sweep(BatchClassDev c, DevState *__re
   }
 }
 
-// One warp per slab: fixed-order sum of the slab's tile partials, stop rule,
+// One block per slab: fixed-order sum of the slab's tile partials, stop rule,
 // ping-pong flip; the last slab to finish ends the WHILE loop.
-__global__ void k_b_finalize(BatchClassDev c, DevState *__restrict__ ds, int *active, int use_cond,
-                             cudaGraphConditionalHandle cond) {
-  const int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (s >= c.n_slabs) return;
+constexpr int kBFinThreads = 128;
+__global__ void __launch_bounds__(kBFinThreads) k_b_finalize(BatchClassDev c, DevState *__restrict__ ds, int *active,
+                                                            int use_cond, cudaGraphConditionalHandle cond) {
+  __shared__ double red[kBFinThreads / 32];
+  const int s = blockIdx.x;
   DevState &d = ds[s];
-  if (d.done) return;
-  double v = 0.0;
-  for (int t = c.slab_tile0[s] + lane; t < c.slab_tile1[s]; t += 32) v += c.partials[t];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  if (lane != 0) return;
+  if (d.done) return;  // uniform: thread 0 writes the state only after the barriers below
+  const int t0 = c.slab_tile0[s];
+  const double v = block_sum_fixed(c.partials + t0, c.slab_tile1[s] - t0, red);
+  if (threadIdx.x != 0) return;
   const double e = sqrt(v);
   const int l = d.l;
   double rho = 0.0;
@@ -447,28 +445,26 @@ __global__ void __launch_bounds__(256) k_b_mx_inner(BatchClassDev c, const DevSt
   }
 }
 
-// One warp per slab: fixed-order sum of its tile partials, then the mixed-form
+// One block per slab: fixed-order sum of its tile partials, then the mixed-form
 // stop rule and refinement decision; the last slab to finish ends the loop.
-__global__ void k_b_mx_finalize(BatchClassDev c, DevState *__restrict__ ds, int *active, int use_cond,
-                                cudaGraphConditionalHandle cond) {
-  const int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (s >= c.n_slabs) return;
+__global__ void __launch_bounds__(kBFinThreads) k_b_mx_finalize(BatchClassDev c, DevState *__restrict__ ds,
+                                                               int *active, int use_cond,
+                                                               cudaGraphConditionalHandle cond) {
+  __shared__ double red[kBFinThreads / 32];
+  const int s = blockIdx.x;
   if (ds[s].done) {
     // a slab that finished in the previous body: its last refinement has been
     // applied by that body's outer kernel; settle it so no later body repeats it
-    if (lane == 0 && ds[s].refine) {
+    if (threadIdx.x == 0 && ds[s].refine) {
       ds[s].cur ^= 1;
       ds[s].refine = 0;
       ds[s].blk_i = 0;
     }
     return;
   }
-  double v = 0.0;
-  for (int t = c.slab_tile0[s] + lane; t < c.slab_tile1[s]; t += 32) v += c.partials[t];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  if (lane != 0) return;
+  const int t0 = c.slab_tile0[s];
+  const double v = block_sum_fixed(c.partials + t0, c.slab_tile1[s] - t0, red);
+  if (threadIdx.x != 0) return;
   finish_mixed(&ds[s], nullptr, sqrt(v), cond, 0);
   if (ds[s].done) {
     const int before = atomicSub(active, 1);
@@ -604,6 +600,186 @@ __global__ void k_b_mx_settle(int n_slabs, DevState *ds) {
   }
 }
 
+// ---------------------------------------------------------------- register form
+// The same sweep with the angles of a cell split over P = N/NP threads, each
+// keeping its NP angles' t = tc + Cin u in registers (no per-angle staging in
+// shared memory, so large N*G no longer limits the block to a few cells).
+// Block = CB cells x (G*P) threads; the angle sum y is reduced across the
+// chunks in a fixed order, then the (4G x 4G) apply s = Mp y is split over the
+// chunk threads of each group.  MX = false: the FP64 sweep (Psi ping-pong,
+// incident flux at slab ends); MX = true: the FP32 correction sweep of the mixed
+// form (delta ping-pong, zero inflow at slab ends, zero input on a new block).
+template <typename T>
+struct BRegIO;
+template <>
+struct BRegIO<double> {
+  __device__ static const double *base(const BatchClassDev &c) { return c.tc; }
+  __device__ static const double *cin(const BatchClassDev &c) { return c.Cin; }
+  __device__ static const double *linv(const BatchClassDev &c) { return c.Linv; }
+  __device__ static const double *mp(const BatchClassDev &c) { return c.Mp; }
+  __device__ static const double *w(const BatchClassDev &c) { return c.w; }
+  __device__ static double fm(double a, double b, double x) { return fma(a, b, x); }
+};
+template <>
+struct BRegIO<float> {
+  __device__ static const float *base(const BatchClassDev &c) { return c.z32; }
+  __device__ static const float *cin(const BatchClassDev &c) { return c.Cin32; }
+  __device__ static const float *linv(const BatchClassDev &c) { return c.Linv32; }
+  __device__ static const float *mp(const BatchClassDev &c) { return c.Mp32; }
+  __device__ static const float *w(const BatchClassDev &c) { return c.w32; }
+  __device__ static float fm(float a, float b, float x) { return fmaf(a, b, x); }
+};
+
+template <typename T, int NP>
+__global__ void __launch_bounds__(256) k_b_sweep_reg(BatchClassDev c, const DevState *__restrict__ ds) {
+  using IO = BRegIO<T>;
+  constexpr bool MX = sizeof(T) == 4;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ double red[8];
+  const int CB = blockDim.x, N = c.N, G = c.G, Jc = c.Jc;
+  const int P = N / NP;
+  const int cl = threadIdx.x, gy = threadIdx.y;
+  const int g = gy / P, ch = gy % P, m0 = ch * NP;
+  const int G4 = 4 * G;
+  T *y_s = (T *)smraw;                      // [G*P*4][CB] chunk partials of y
+  T *yr_s = y_s + (size_t)G * P * 4 * CB;   // [4G][CB] y
+  T *s_s = yr_s + (size_t)G4 * CB;          // [4G][CB] s = Mp y
+  const int N2 = N / 2;
+  const T *__restrict__ Bv = IO::base(c);
+  const T *__restrict__ Cin = IO::cin(c);
+  const T *__restrict__ Linv = IO::linv(c);
+  const T *__restrict__ Mp = IO::mp(c);
+  const T *__restrict__ w = IO::w(c);
+  const int tid = threadIdx.y * CB + threadIdx.x;
+  const int nthr = CB * G * P;
+  for (int s = 0; s < c.n_slabs; s++) {
+    if (ds[s].done) continue;  // uniform over the block
+    bool zero = false;
+    const T *In;
+    T *Out;
+    if (MX) {
+      zero = ds[s].refine || ds[s].blk_i == 0;
+      const int dc = ds[s].dcur;
+      In = (const T *)(dc ? (const void *)c.D1 : (const void *)c.D0);
+      Out = (T *)(dc ? (void *)c.D0 : (void *)c.D1);
+    } else {
+      const int cur = ds[s].cur;
+      In = (const T *)(cur ? (const void *)c.Psi1 : (const void *)c.Psi0);
+      Out = (T *)(cur ? (void *)c.Psi0 : (void *)c.Psi1);
+    }
+    const double *inc = c.inc + (size_t)s * 2 * G * N * 2;
+    const int t0 = c.slab_tile0[s], t1 = c.slab_tile1[s];
+    const int Gd = gridDim.x;
+    const int first = t0 + (((int)blockIdx.x - t0 % Gd) % Gd + Gd) % Gd;
+    const int s0c = c.slab_start[s], Js = c.slab_J[s];
+    for (int tile = first; tile < t1; tile += Gd) {
+      const int j = c.tile_first_cell[tile] + cl;
+      const int jl = j - s0c;
+      const bool active = jl < Js;
+      const int tau = active ? c.type[j] : 0;
+      const size_t tb = (size_t)tau * G * N;
+      T t[NP][4];
+      T y0 = T(0), y1 = T(0), y2 = T(0), y3 = T(0);
+      if (active) {
+#pragma unroll
+        for (int i = 0; i < NP; i++) {
+          const int m = m0 + i;
+          const int gm = g * N + m;
+          const size_t base = (size_t)gm * 4 * Jc + j;
+          T uk = T(0), uh = T(0);
+          if (m >= N2) {
+            if (jl > 0) {
+              if (!zero) {
+                uk = In[base + (size_t)Jc - 1];
+                uh = In[base + 3 * (size_t)Jc - 1];
+              }
+            } else if (!MX) {
+              uk = (T)inc[gm * 2 + 0];
+              uh = (T)inc[gm * 2 + 1];
+            }
+          } else {
+            if (jl < Js - 1) {
+              if (!zero) {
+                uk = In[base + 1];
+                uh = In[base + 2 * (size_t)Jc + 1];
+              }
+            } else if (!MX) {
+              uk = (T)inc[(G * N + gm) * 2 + 0];
+              uh = (T)inc[(G * N + gm) * 2 + 1];
+            }
+          }
+          const T *C = Cin + (tb + gm) * 8;
+          t[i][0] = IO::fm(C[1], uh, IO::fm(C[0], uk, Bv[base]));
+          t[i][1] = IO::fm(C[3], uh, IO::fm(C[2], uk, Bv[base + (size_t)Jc]));
+          t[i][2] = IO::fm(C[5], uh, IO::fm(C[4], uk, Bv[base + 2 * (size_t)Jc]));
+          t[i][3] = IO::fm(C[7], uh, IO::fm(C[6], uk, Bv[base + 3 * (size_t)Jc]));
+          const T wm = w[m];
+          y0 = IO::fm(wm, t[i][0], y0);
+          y1 = IO::fm(wm, t[i][1], y1);
+          y2 = IO::fm(wm, t[i][2], y2);
+          y3 = IO::fm(wm, t[i][3], y3);
+        }
+      }
+      {
+        T *ys = y_s + (size_t)(gy * 4) * CB + cl;
+        ys[0] = y0;
+        ys[CB] = y1;
+        ys[2 * CB] = y2;
+        ys[3 * CB] = y3;
+      }
+      __syncthreads();
+      // y_{g,q} = sum over the group's chunks (fixed order)
+      for (int q = ch; q < 4; q += P) {
+        T v = y_s[(size_t)((g * P) * 4 + q) * CB + cl];
+        for (int k = 1; k < P; k++) v += y_s[(size_t)((g * P + k) * 4 + q) * CB + cl];
+        yr_s[(size_t)(g * 4 + q) * CB + cl] = v;
+      }
+      __syncthreads();
+      // s_{g,q} = sum_k Mp[g*4+q][k] y_k
+      if (active) {
+        for (int q = ch; q < 4; q += P) {
+          const T *M = Mp + (size_t)tau * G4 * G4 + (size_t)(g * 4 + q) * G4;
+          T v = T(0);
+          for (int k = 0; k < G4; k++) v = IO::fm(M[k], yr_s[(size_t)k * CB + cl], v);
+          s_s[(size_t)(g * 4 + q) * CB + cl] = v;
+        }
+      }
+      __syncthreads();
+      T e2 = T(0);
+      if (active) {
+        const T sv0 = s_s[(size_t)(g * 4 + 0) * CB + cl], sv1 = s_s[(size_t)(g * 4 + 1) * CB + cl];
+        const T sv2 = s_s[(size_t)(g * 4 + 2) * CB + cl], sv3 = s_s[(size_t)(g * 4 + 3) * CB + cl];
+#pragma unroll
+        for (int i = 0; i < NP; i++) {
+          const int gm = g * N + m0 + i;
+          const size_t base = (size_t)gm * 4 * Jc + j;
+          const T *L = Linv + (tb + gm) * 16;
+#pragma unroll
+          for (int p = 0; p < 4; p++) {
+            const T o = IO::fm(L[p * 4 + 3], sv3,
+                               IO::fm(L[p * 4 + 2], sv2, IO::fm(L[p * 4 + 1], sv1, IO::fm(L[p * 4 + 0], sv0, t[i][p]))));
+            const T d = zero ? o : o - In[base + (size_t)p * Jc];
+            e2 = IO::fm(d, d, e2);
+            Out[base + (size_t)p * Jc] = o;
+          }
+        }
+      }
+      double v = (double)e2;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      if ((tid & 31) == 0) red[tid >> 5] = v;
+      __syncthreads();
+      if (tid == 0) {
+        double acc = 0.0;
+        for (int i = 0; i < (nthr + 31) / 32; i++) acc += red[i];
+        c.partials[tile] = acc;
+      }
+      // the next tile's first shared-memory writes come after the y_s barrier;
+      // red is rewritten only after two more barriers
+    }
+  }
+}
+
 // ---------------------------------------------------------------- launches
 size_t b_sweep_smem(int N, int G, int cb) {
   return (size_t)cb * ((size_t)G * N * 4 * 8 + (size_t)G * 4 * 8);
@@ -615,15 +791,47 @@ void launch_b_step_const(BatchClass &c, cudaStream_t st) {
                                        c.d.psi_prev, c.d.Linv, c.d.tc);
 }
 
+size_t b_reg_smem(int N, int G, int cb, int np, int es) {
+  const int P = N / np;
+  return (size_t)cb * ((size_t)G * P * 4 + 8 * (size_t)G) * es;
+}
+
+template <typename T>
+static const void *reg_kernel(int np) {
+  switch (np) {
+    case 2: return (const void *)k_b_sweep_reg<T, 2>;
+    case 4: return (const void *)k_b_sweep_reg<T, 4>;
+    case 8: return (const void *)k_b_sweep_reg<T, 8>;
+    default: return nullptr;
+  }
+}
+const void *k_b_reg_ptr(int np, bool mixed) { return mixed ? reg_kernel<float>(np) : reg_kernel<double>(np); }
+
+template <typename T>
+static void launch_reg(BatchClass &c, const DevState *ds, cudaStream_t st) {
+  const int P = c.d.N / c.np;
+  dim3 block(c.cb, c.d.G * P);
+  const size_t smem = b_reg_smem(c.d.N, c.d.G, c.cb, c.np, (int)sizeof(T));
+  switch (c.np) {
+    case 2: k_b_sweep_reg<T, 2><<<c.grid, block, smem, st>>>(c.d, ds); break;
+    case 4: k_b_sweep_reg<T, 4><<<c.grid, block, smem, st>>>(c.d, ds); break;
+    case 8: k_b_sweep_reg<T, 8><<<c.grid, block, smem, st>>>(c.d, ds); break;
+    default: break;
+  }
+}
+
 void launch_b_sweep(BatchClass &c, DevState *ds, cudaStream_t st) {
+  if (c.np) {
+    launch_reg<double>(c, ds, st);
+    return;
+  }
   dim3 block(c.cb, c.d.G);
   k_b_sweep<<<c.grid, block, b_sweep_smem(c.d.N, c.d.G, c.cb), st>>>(c.d, ds);
 }
 
 void launch_b_finalize(BatchClass &c, DevState *ds, int *active, int use_cond, cudaGraphConditionalHandle cond,
                        cudaStream_t st) {
-  const int warps = 4;
-  k_b_finalize<<<(c.d.n_slabs + warps - 1) / warps, 32 * warps, 0, st>>>(c.d, ds, active, use_cond, cond);
+  k_b_finalize<<<c.d.n_slabs, kBFinThreads, 0, st>>>(c.d, ds, active, use_cond, cond);
 }
 
 void launch_b_carry(BatchClass &c, DevState *ds, cudaStream_t st) {
@@ -642,13 +850,16 @@ void launch_b_mx_step_const(BatchClass &c, cudaStream_t st) {
 }
 
 void launch_b_mx_inner(BatchClass &c, DevState *ds, cudaStream_t st) {
+  if (c.np) {
+    launch_reg<float>(c, ds, st);
+    return;
+  }
   k_b_mx_inner<<<c.grid, dim3(c.cb, c.d.G), b_mx_smem(c.d.N, c.d.G, c.cb), st>>>(c.d, ds);
 }
 
 void launch_b_mx_finalize(BatchClass &c, DevState *ds, int *active, int use_cond, cudaGraphConditionalHandle cond,
                           cudaStream_t st) {
-  const int warps = 4;
-  k_b_mx_finalize<<<(c.d.n_slabs + warps - 1) / warps, 32 * warps, 0, st>>>(c.d, ds, active, use_cond, cond);
+  k_b_mx_finalize<<<c.d.n_slabs, kBFinThreads, 0, st>>>(c.d, ds, active, use_cond, cond);
 }
 
 void launch_b_mx_outer(BatchClass &c, DevState *ds, int mode, cudaStream_t st) {
@@ -669,6 +880,15 @@ int b_max_grid(int N, int G, int cb) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_b_sweep, cb * G, b_sweep_smem(N, G, cb));
+  return sms * (per > 0 ? per : 1);
+}
+
+int b_reg_max_grid(int N, int G, int cb, int np, bool mixed) {
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_b_reg_ptr(np, mixed), cb * G * (N / np),
+                                                b_reg_smem(N, G, cb, np, mixed ? 4 : 8));
   return sms * (per > 0 ? per : 1);
 }
 

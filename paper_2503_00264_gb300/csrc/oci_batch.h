@@ -38,6 +38,7 @@ struct BatchClass {
   BatchClassDev d{};
   bool mixed = false;
   int cb = 128;     // cells per tile (autotuned)
+  int np = 0;       // angles per thread of the register sweep; 0 = shared-memory sweep (autotuned)
   int grid = 0;     // persistent grid size
   int slab0 = 0;    // index of the class's first slab in the batch
   std::vector<int> slabs;  // batch slab index of each class-local slab
@@ -79,6 +80,10 @@ void launch_b_mx_outer(BatchClass &c, DevState *ds, int mode, cudaStream_t st);
 void launch_b_mx_settle(BatchClass &c, DevState *ds, cudaStream_t st);
 size_t b_mx_smem(int N, int G, int cb);
 int b_mx_max_grid(int N, int G, int cb);
+// register sweep (angles split over N/np threads per cell; FP64 or the FP32 inner sweep)
+size_t b_reg_smem(int N, int G, int cb, int np, int es);
+int b_reg_max_grid(int N, int G, int cb, int np, bool mixed);
+const void *k_b_reg_ptr(int np, bool mixed);
 const void *k_b_mx_inner_ptr();
 
 }  // namespace oci

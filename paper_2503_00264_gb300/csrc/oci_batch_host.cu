@@ -2,6 +2,7 @@
 // per-slab type tables, per-class autotuned tile size), the per-time-step graph
 // and the batch entry points of the C ABI.
 #include <math.h>
+#include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -22,6 +23,7 @@ namespace oci {
   } while (0)
 
 constexpr int kPad = 128;
+constexpr int kMinTile = 8;  // smallest tile (cells) of any sweep candidate
 // refinement schedule of the mixed form (as the single-slab FP32 form): refine
 // after kBatchMxKmax inner sweeps or once e fell below kBatchMxTheta of the block's first
 constexpr int kBatchMxKmax = 64;
@@ -55,8 +57,8 @@ static int bupload(BatchClass &c, T **p, const std::vector<T> &v, cudaStream_t s
 }
 
 // tile arrays for tile size cb (tiles never straddle slabs)
-static int build_tiles(BatchClass &c, int cb, int32_t *tile_slab, int32_t *tile_first, int32_t *t0, int32_t *t1,
-                       cudaStream_t st) {
+static int build_tiles(BatchClass &c, int np, int cb, int32_t *tile_slab, int32_t *tile_first, int32_t *t0,
+                       int32_t *t1, cudaStream_t st) {
   std::vector<int32_t> ts, tf, a, b;
   for (size_t i = 0; i < c.h_J.size(); i++) {
     a.push_back((int32_t)ts.size());
@@ -73,7 +75,10 @@ static int build_tiles(BatchClass &c, int cb, int32_t *tile_slab, int32_t *tile_
   BCK(cudaMemcpyAsync(t1, b.data(), b.size() * 4, cudaMemcpyHostToDevice, st));
   BCK(cudaStreamSynchronize(st));  // host vectors go out of scope
   c.cb = cb;
-  c.grid = std::min(c.d.n_tiles, c.mixed ? b_mx_max_grid(c.d.N, c.d.G, cb) : b_max_grid(c.d.N, c.d.G, cb));
+  c.np = np;
+  const int maxg = np ? b_reg_max_grid(c.d.N, c.d.G, cb, np, c.mixed)
+                      : (c.mixed ? b_mx_max_grid(c.d.N, c.d.G, cb) : b_max_grid(c.d.N, c.d.G, cb));
+  c.grid = std::min(c.d.n_tiles, maxg);
   if (c.grid < 1) c.grid = 1;
   return OCI_OK;
 }
@@ -145,7 +150,7 @@ static int setup_class(Batch &B, BatchClass &c, const oci_problem *probs) {
       (rc = bupload(c, &d_tah, tah, st)) || (rc = bupload(c, &d_w, w, st)) || (rc = bupload(c, &d_mu, mu, st)) ||
       (rc = bupload(c, &d_inc, incv, st)))
     return rc;
-  const int max_tiles = Jc / 32 + (int)c.slabs.size();
+  const int max_tiles = Jc / kMinTile + (int)c.slabs.size();
   if ((rc = balloc(c, &d_t0, c.slabs.size(), st)) || (rc = balloc(c, &d_t1, c.slabs.size(), st)) ||
       (rc = balloc(c, &d_ts, max_tiles, st)) || (rc = balloc(c, &d_tf, max_tiles, st)))
     return rc;
@@ -198,12 +203,21 @@ static int setup_class(Batch &B, BatchClass &c, const oci_problem *probs) {
     d.D0 = D0; d.D1 = D1; d.z32 = z32;
     d.cvec = tc;  // the mixed form keeps c itself where the FP64 form keeps Linv c
   }
-  // ---- autotune the tile size of this class (CUDA events over a few sweeps)
-  std::vector<int> cands;
+  // ---- autotune the sweep of this class (CUDA events over a few sweeps):
+  // the shared-memory sweep over cb cells, or the register sweep with np
+  // angles per thread over cb cells
+  std::vector<std::pair<int, int>> cands;  // (np, cb)
   for (int cb : {32, 64, 128})
-    if (cb * G <= 256 && (c.mixed ? b_mx_smem(N, G, cb) : b_sweep_smem(N, G, cb)) <= 100 * 1024) cands.push_back(cb);
-  if (cands.empty()) cands.push_back(32);
-  int best_cb = cands.back();
+    if (cb * G <= 256 && (c.mixed ? b_mx_smem(N, G, cb) : b_sweep_smem(N, G, cb)) <= 100 * 1024)
+      cands.emplace_back(0, cb);
+  for (int np : {2, 4, 8}) {
+    if (N % np) continue;
+    const int P = N / np;
+    for (int cb = kMinTile; cb <= 128; cb *= 2)
+      if (cb * G * P <= 256 && cb * G * P >= 64 && (cb * G * P) % 32 == 0) cands.emplace_back(np, cb);
+  }
+  if (cands.empty()) cands.emplace_back(0, 32);
+  std::pair<int, int> best = cands.back();
   const char *at = getenv("OCI_AUTOTUNE");
   if (cands.size() > 1 && !(at && at[0] == '0')) {
     for (int i = 0; i < c.d.n_slabs; i++) {
@@ -215,9 +229,9 @@ static int setup_class(Batch &B, BatchClass &c, const oci_problem *probs) {
       x.dcur = 0;
     }
     BCK(cudaMemcpyAsync(B.ds + c.slab0, B.h_ds + c.slab0, sizeof(DevState) * c.d.n_slabs, cudaMemcpyHostToDevice, st));
-    float best = 1e30f;
-    for (int cb : cands) {
-      if ((rc = build_tiles(c, cb, d_ts, d_tf, d_t0, d_t1, st))) return rc;
+    float best_ms = 1e30f;
+    for (auto cand : cands) {
+      if ((rc = build_tiles(c, cand.first, cand.second, d_ts, d_tf, d_t0, d_t1, st))) return rc;
       auto sweep = [&]() {
         if (c.mixed) launch_b_mx_inner(c, B.ds + c.slab0, st);
         else launch_b_sweep(c, B.ds + c.slab0, st);
@@ -230,9 +244,9 @@ static int setup_class(Batch &B, BatchClass &c, const oci_problem *probs) {
       BCK(cudaGetLastError());
       float ms = 0.f;
       cudaEventElapsedTime(&ms, B.ev0, B.ev1);
-      if (ms < best) {
-        best = ms;
-        best_cb = cb;
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = cand;
       }
     }
     BCK(cudaMemsetAsync(Psi0, 0, nPsi * 8, st));
@@ -244,7 +258,25 @@ static int setup_class(Batch &B, BatchClass &c, const oci_problem *probs) {
     for (int i = 0; i < c.d.n_slabs; i++) B.h_ds[c.slab0 + i].done = 1;
     BCK(cudaMemcpyAsync(B.ds + c.slab0, B.h_ds + c.slab0, sizeof(DevState) * c.d.n_slabs, cudaMemcpyHostToDevice, st));
   }
-  return build_tiles(c, best_cb, d_ts, d_tf, d_t0, d_t1, st);
+  // "np,cb" in OCI_BATCH_SWEEP forces a sweep shape (tests and profiling) where
+  // it is valid for the class: np = 0 or np | N; cb a power of two in
+  // [kMinTile, 128]; whole warps (the reductions shuffle over full warps), at
+  // most 256 threads; shared memory within the set limit
+  const char *force = getenv("OCI_BATCH_SWEEP");
+  if (force) {
+    int fnp = -1, fcb = -1;
+    if (sscanf(force, "%d,%d", &fnp, &fcb) == 2 && fcb >= kMinTile && fcb <= 128 && (fcb & (fcb - 1)) == 0) {
+      bool ok;
+      if (fnp == 0)
+        ok = fcb * G <= 256 && (fcb * G) % 32 == 0 &&
+             (c.mixed ? b_mx_smem(N, G, fcb) : b_sweep_smem(N, G, fcb)) <= 200 * 1024;
+      else
+        ok = (fnp == 2 || fnp == 4 || fnp == 8) && N % fnp == 0 && fcb * G * (N / fnp) <= 256 &&
+             (fcb * G * (N / fnp)) % 32 == 0;
+      if (ok) best = std::make_pair(fnp, fcb);
+    }
+  }
+  return build_tiles(c, best.first, best.second, d_ts, d_tf, d_t0, d_t1, st);
 }
 
 static int build_batch_graph(Batch &B) {
@@ -260,21 +292,45 @@ static int build_batch_graph(Batch &B) {
   cudaGraphNode_t node;
   BCK(cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np));
   cudaGraph_t body = np.conditional.phGraph_out[0];
-  cudaStream_t cs;
-  BCK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-  cudaError_t e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
-  if (e == cudaSuccess) {
-    if (B.precision == OCI_FP64) {
-      for (auto &c : B.cls) launch_b_sweep(c, B.ds + c.slab0, cs);
-      for (auto &c : B.cls) launch_b_finalize(c, B.ds + c.slab0, B.active, 1, cond, cs);
-    } else {
-      for (auto &c : B.cls) launch_b_mx_inner(c, B.ds + c.slab0, cs);
-      for (auto &c : B.cls) launch_b_mx_finalize(c, B.ds + c.slab0, B.active, 1, cond, cs);
-      for (auto &c : B.cls) launch_b_mx_outer(c, B.ds + c.slab0, 1, cs);
-    }
-    e = cudaStreamEndCapture(cs, &body);
+  // The classes are independent until the loop test: capture each class's
+  // sweep and finalize as its own branch (fork/join through events) so that
+  // classes with few unconverged slabs share the GPU instead of running in turn.
+  const int nc = (int)B.cls.size();
+  std::vector<cudaStream_t> br(nc, nullptr);
+  std::vector<cudaEvent_t> join(nc, nullptr);
+  cudaEvent_t fork = nullptr;
+  cudaError_t e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+  for (int i = 0; i < nc && e == cudaSuccess; i++) {
+    e = cudaStreamCreateWithFlags(&br[i], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join[i], cudaEventDisableTiming);
   }
-  cudaStreamDestroy(cs);
+  if (e == cudaSuccess)
+    e = cudaStreamBeginCaptureToGraph(br[0], body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaEventRecord(fork, br[0]);
+    for (int i = 1; i < nc; i++) cudaStreamWaitEvent(br[i], fork, 0);
+    for (int i = 0; i < nc; i++) {
+      BatchClass &c = B.cls[i];
+      if (B.precision == OCI_FP64) {
+        launch_b_sweep(c, B.ds + c.slab0, br[i]);
+        launch_b_finalize(c, B.ds + c.slab0, B.active, 1, cond, br[i]);
+      } else {
+        launch_b_mx_inner(c, B.ds + c.slab0, br[i]);
+        launch_b_mx_finalize(c, B.ds + c.slab0, B.active, 1, cond, br[i]);
+        launch_b_mx_outer(c, B.ds + c.slab0, 1, br[i]);
+      }
+    }
+    for (int i = 1; i < nc; i++) {
+      cudaEventRecord(join[i], br[i]);
+      cudaStreamWaitEvent(br[0], join[i], 0);
+    }
+    e = cudaStreamEndCapture(br[0], &body);
+  }
+  for (int i = 0; i < nc; i++) {
+    if (br[i]) cudaStreamDestroy(br[i]);
+    if (join[i]) cudaEventDestroy(join[i]);
+  }
+  if (fork) cudaEventDestroy(fork);
   if (e != cudaSuccess) {
     cudaGraphDestroy(graph);
     return cuda_fail(e, "capturing the batched convergence loop");

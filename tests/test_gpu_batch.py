@@ -103,3 +103,28 @@ def test_batch_fp32ir_uneven_slabs_match_fp64_batch():
                 assert rel(b.phi(i), s.phi()) < 1e-9
         ok = [st for st in sts if st["status"] == 0]
         assert max(max(st["balance_rel"]) for st in ok) < 1e-8
+
+
+@pytest.mark.parametrize("shape", ["0,32", "0,64", "2,8", "4,8", "8,8", "2,32", "4,16"])
+@pytest.mark.parametrize("precision", [oci.FP64, oci.FP32_IR])
+def test_batch_sweep_shapes_match_oracle(monkeypatch, shape, precision):
+    """Every sweep shape the autotuner can pick (shared-memory sweep, or the
+    register sweep with np angles per thread; cb cells per tile), forced through
+    OCI_BATCH_SWEEP, against the FP64 oracle: sweep counts equal (FP64) or within
+    2 (3 for J = 1) (FP32_IR), scalar flux within 1e-12 / 1e-10."""
+    monkeypatch.setenv("OCI_BATCH_SWEEP", shape)
+    specs = [(51, 70, 4, 1), (52, 131, 8, 1), (53, 66, 16, 2), (54, 1, 8, 2), (55, 90, 16, 1), (56, 45, 8, 3)]
+    probs = [W.random_slab(*sp).replace(tol=1e-11) for sp in specs]
+    orcs = [Oracle(p) for p in probs]
+    with oci.BatchSolver(probs, precision=precision) as b:
+        for k in range(2):
+            sts = b.step()
+            for i, (p, o) in enumerate(zip(probs, orcs)):
+                r = o.step(OCI)
+                assert sts[i]["status"] == 0
+                if precision == oci.FP64:
+                    assert sts[i]["iters"] == r["iters"], (i, k)
+                    assert rel(b.phi(i), r["phi"]) < 1e-12
+                else:
+                    assert abs(sts[i]["iters"] - r["iters"]) <= (3 if p.J == 1 else 2), (i, k)
+                    assert rel(b.phi(i), r["phi"]) < 1e-10
