@@ -197,6 +197,9 @@ def run_ours(args):
         s.step()
         if smx is not None:
             smx.step()
+    # starting state of the timed region, replayed by the end-to-end leg below
+    start_pp, start_t = s.state()
+    start_psi = s.psi()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clk = Clocks(local)
     barrier()
@@ -207,7 +210,7 @@ def run_ours(args):
         st = s.step()
         stats.append(st)
         sweeps += st["iters"]
-        launches += 1 + 2 * st["iters"] + 2
+        launches += 1 + st["iters"] + 2  # step constant, fused sweeps, carry + balance
     e1.record(stream)
     barrier()
     clocks = clk.stop()
@@ -358,18 +361,22 @@ def run_ours(args):
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"hbm_gbs": 6800.0}
     hbm_gbs = bytes_cell * p.J / (sweep_ms * 1e-3) / 1e9
 
-    # end to end: host psi_prev in, host phi out, every step
-    pp_host = torch.zeros((p.J, p.G, p.N, 2), dtype=torch.float64).pin_memory()
+    # end to end: the timed region's K steps again from its starting state, with
+    # the transport state held on the host: every step uploads psi_prev from
+    # pinned memory, solves, and reads psi_prev and phi back (the sweep counts
+    # must equal the device-timed ones: same steps, same arithmetic)
+    pp_host = torch.from_numpy(start_pp).pin_memory()
     phi_host = torch.zeros((p.J, p.G, 4), dtype=torch.float64).pin_memory()
-    pp0, t0 = s.state()
-    pp_host.copy_(torch.from_numpy(pp0))
+    s.set_psi(start_psi)
+    t_host = start_t
     barrier()
     g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     g0.record(stream)
     e2e_sweeps = 0
     for _ in range(args.steps):
-        s.set_state(pp_host, t0)
+        s.set_state(pp_host, t_host)
         st = s.step()
+        t_host = s.state_into(pp_host)
         s.phi(phi_host)
         e2e_sweeps += st["iters"]
     g1.record(stream)
@@ -392,7 +399,8 @@ def run_ours(args):
                          "hbm_frac": hbm_gbs / peaks.get("hbm_gbs", 6800.0),
                          "sweep_us": sweep_ms * 1e3, "flops_per_cell": flops_cell, "bytes_per_cell": bytes_cell},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": p.J * p.G * p.N * 2 * 8,
-                    "d2h_bytes_per_step": p.J * p.G * 4 * 8},
+                    "sweeps_equal_device_timed": e2e_sweeps == sweeps,
+                    "d2h_bytes_per_step": p.J * p.G * p.N * 2 * 8 + p.J * p.G * 4 * 8},
             "gpu_launches": launches,
             "clocks": clocks,
             "precision_forms": mixed,

@@ -76,7 +76,10 @@ enum {
 enum {
   OCI_GUESS_PREV = 0, /* the handle's current Psi: the previous step's converged
                          Psi, zero before the first step, or what oci_set_psi set */
-  OCI_GUESS_ZERO = 1  /* zero                                                      */
+  OCI_GUESS_ZERO = 1, /* zero                                                      */
+  OCI_GUESS_USER = 2  /* the iterate the caller last passed to oci_set_psi (zero
+                         before the first call), restored at the start of every
+                         step; the handle keeps a device copy of it              */
 };
 
 /* local solver of the FP64 form (oci_problem.solver) */
@@ -132,8 +135,8 @@ typedef struct {
   const double *inc_right;  /* [G][N][2] same at x = X for mu < 0.  NULL = vacuum     */
   double tol;               /* eps of the stop rule, >= 0 (absolute 2-norm)           */
   int32_t max_iter;         /* >= 1 sweeps per step                                   */
-  int32_t precision;        /* OCI_FP64 | OCI_TF32_IR | OCI_BF16X3_IR                 */
-  int32_t guess;            /* OCI_GUESS_PREV | OCI_GUESS_ZERO                        */
+  int32_t precision;        /* OCI_FP64 | OCI_TF32_IR | OCI_BF16X3_IR | OCI_FP32_IR   */
+  int32_t guess;            /* OCI_GUESS_PREV | OCI_GUESS_ZERO | OCI_GUESS_USER       */
   int32_t solver;           /* OCI_SOLVER_*                                           */
   void *stream;             /* cudaStream_t for all work of the handle; NULL = the
                                legacy default stream                                 */
@@ -202,7 +205,8 @@ int si_iterate(oci_handle *h, int32_t n, double *e_hist);
  * step (residual = time + leak + collision - scatter_in - source).
  * All buffers host or device. */
 int oci_get_psi(const oci_handle *h, double *psi);
-int oci_set_psi(oci_handle *h, const double *psi);
+int oci_set_psi(oci_handle *h, const double *psi); /* with OCI_GUESS_USER also the
+                                                      initial iterate of every later step */
 int oci_get_phi(const oci_handle *h, double *phi);
 int oci_get_state(const oci_handle *h, double *psi_prev, double *t);
 int oci_set_state(oci_handle *h, const double *psi_prev, double t);

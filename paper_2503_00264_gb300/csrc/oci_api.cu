@@ -152,7 +152,7 @@ int validate(const oci_problem *p) {
   if (!(std::isfinite(p->tol) && p->tol >= 0)) return set_error("tol must be finite and >= 0"), OCI_E_INVAL;
   if (p->max_iter < 1) return set_error("max_iter must be >= 1"), OCI_E_INVAL;
   if (p->precision < OCI_FP64 || p->precision > OCI_FP32_IR) return set_error("bad precision"), OCI_E_INVAL;
-  if (p->guess < OCI_GUESS_PREV || p->guess > OCI_GUESS_ZERO) return set_error("bad guess policy"), OCI_E_INVAL;
+  if (p->guess < OCI_GUESS_PREV || p->guess > OCI_GUESS_USER) return set_error("bad guess policy"), OCI_E_INVAL;
   if (p->solver < OCI_SOLVER_AUTO || p->solver > OCI_SOLVER_DENSE_LU) return set_error("bad solver"), OCI_E_INVAL;
   if (p->precision != OCI_FP64 && p->solver == OCI_SOLVER_DENSE_LU)
     return set_error("the dense per-cell solver is FP64 only"), OCI_E_INVAL;
@@ -387,7 +387,7 @@ static void free_handle(Handle *h) {
                   h->tt.Cin, h->tt.Mp,  h->tt.Kap,    h->tt.dx,     h->tt.sig,       h->si_z,      h->si_uin,
                   h->LU,     h->piv,    h->partials,  h->bal_partials, h->bal,       h->e_hist,    h->ds,
                   h->stage,  h->delta[0], h->delta[1], h->z32, h->w32, h->tt.Lco, h->tt.Linv32, h->tt.Cin32,
-                  h->tt.Mp32, h->tc_img, h->si_maps, h->si_segin, h->counter};
+                  h->tt.Mp32, h->tc_img, h->si_maps, h->si_segin, h->counter, h->psi_user};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (h->h_ds) cudaFreeHost(h->h_ds);
@@ -436,6 +436,10 @@ static int setup_impl(const oci_problem *p, oci_handle *h) {
   CK(cudaMalloc(&h->psi_prev, G * N * 2 * Jp * 8));
   CK(cudaMalloc(&h->phi, G * 4 * Jp * 8));
   CK(cudaMalloc(&h->stage, nPsi * 8));
+  if (h->guess == OCI_GUESS_USER) {
+    CK(cudaMalloc(&h->psi_user, nPsi * 8));
+    CK(cudaMemsetAsync(h->psi_user, 0, nPsi * 8, s));
+  }
   CK(cudaMemsetAsync(h->Psi[0], 0, nPsi * 8, s));
   CK(cudaMemsetAsync(h->Psi[1], 0, nPsi * 8, s));
   CK(cudaMemsetAsync(h->tc, 0, nPsi * 8, s));
@@ -654,6 +658,8 @@ static int run_step(Handle &h, bool si, oci_stats *st) {
   const size_t nPsi = (size_t)h.G * h.N * 4 * h.Jp;
   cudaStream_t s = h.stream;
   if (h.guess == OCI_GUESS_ZERO) CK(cudaMemsetAsync(h.Psi[h.h_ds->cur], 0, nPsi * 8, s));
+  if (h.guess == OCI_GUESS_USER)
+    CK(cudaMemcpyAsync(h.Psi[h.h_ds->cur], h.psi_user, nPsi * 8, cudaMemcpyDeviceToDevice, s));
   int rc = begin_iteration(h, 0, h.max_iter);
   if (rc) return rc;
   if (si) {
@@ -902,7 +908,13 @@ int oci_get_psi(const oci_handle *h, double *psi) {
 int oci_set_psi(oci_handle *h, const double *psi) {
   GUARD(h);
   if (!psi) return set_error("psi is NULL"), OCI_E_INVAL;
-  return put_soa(*h, psi, h->Psi[h->h_ds->cur], h->G * h->N * 4);
+  int rc = put_soa(*h, psi, h->Psi[h->h_ds->cur], h->G * h->N * 4);
+  if (rc || h->guess != OCI_GUESS_USER) return rc;
+  // GUESS_USER: keep the caller's iterate as the initial iterate of every step
+  const size_t nPsi = (size_t)h->G * h->N * 4 * h->Jp;
+  CK(cudaMemcpyAsync(h->psi_user, h->Psi[h->h_ds->cur], nPsi * 8, cudaMemcpyDeviceToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return OCI_OK;
 }
 
 int oci_get_phi(const oci_handle *h, double *phi) {

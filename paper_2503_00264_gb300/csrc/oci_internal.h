@@ -118,6 +118,7 @@ struct Handle {
   double *e_hist = nullptr;        // [e_hist_cap]
   int e_hist_cap = 0;
   double *stage = nullptr;         // device staging buffer, size of one Psi
+  double *psi_user = nullptr;      // GUESS_USER: the caller's initial iterate (device SoA)
   DevState *ds = nullptr;
   // pinned host mirrors
   DevState *h_ds = nullptr;

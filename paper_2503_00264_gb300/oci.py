@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "liboci.so")
 
 OK, E_INVAL, E_NOMEM, E_CUDA, E_NOCONV, E_SINGULAR, E_NONFINITE, E_TIMEOUT, E_STATE = 0, -1, -2, -3, -4, -5, -6, -7, -8
 FP64, TF32_IR, BF16X3_IR, FP32_IR = 0, 1, 2, 3
-GUESS_PREV, GUESS_ZERO = 0, 1
+GUESS_PREV, GUESS_ZERO, GUESS_USER = 0, 1, 2
 SOLVER_AUTO, SOLVER_STRUCTURED, SOLVER_DENSE_LU = 0, 1, 2
 ORDER_JACOBI, ORDER_RED_BLACK = 0, 1
 SI_SEQUENTIAL, SI_SCAN = 0, 1
@@ -282,6 +282,12 @@ class Solver:
         t = ctypes.c_double()
         _check(self.L.oci_get_state(self.h, _ptr(pp, writable=True), ctypes.byref(t)))
         return pp, t.value
+
+    def state_into(self, out) -> float:
+        """psi_prev into a caller buffer ([J][G][N][2], host or device); returns t."""
+        t = ctypes.c_double()
+        _check(self.L.oci_get_state(self.h, _ptr(out, writable=True), ctypes.byref(t)))
+        return t.value
 
     def set_state(self, psi_prev, t: float):
         arr = None if psi_prev is None else (np.ascontiguousarray(psi_prev, np.float64)

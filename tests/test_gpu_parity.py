@@ -65,6 +65,29 @@ def test_guess_zero_policy():
     compare_steps(W.random_slab(12, 50, 8, 2).replace(tol=1e-11), 2, guess=oci.GUESS_ZERO)
 
 
+def test_guess_user_policy():
+    """GUESS_USER: every step starts from the iterate last given to set_psi
+    (oracle: the same array put in before each step); without set_psi, zero."""
+    p = W.random_slab(17, 90, 8, 2).replace(tol=1e-11)
+    U = W.random_guess(p, 21)
+    o = Oracle(p)
+    with oci.Solver(p, guess=oci.GUESS_USER) as s:
+        s.set_psi(U)
+        for k in range(3):
+            st = s.step()
+            o.Psi[...] = U
+            r = o.step(OCI)
+            assert st["iters"] == r["iters"], k
+            assert rel(s.phi(), r["phi"]) < 1e-12
+    o0 = Oracle(p)
+    with oci.Solver(p, guess=oci.GUESS_USER) as s:
+        for k in range(2):
+            st = s.step()
+            r = o0.step(OCI, guess=1)
+            assert st["iters"] == r["iters"], k
+            assert rel(s.phi(), r["phi"]) < 1e-12
+
+
 def test_max_sizes():
     """Largest angular order (N = 128) and many groups (G = 16)."""
     compare_steps(W.random_slab(13, 4, 128, 1).replace(tol=1e-10), 1)
