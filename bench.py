@@ -32,8 +32,12 @@ METRIC = "OCI cell-unknown updates/s"
 UNIT = "updates/s"
 SAMPLE_J = 3072
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_oci_sweep launch on this workload
-# (2^18 cells, S16, G = 1), from the ncu --set full capture summarised in profiles/.
-SWEEP_DRAM_BYTES_NCU = 273.335552e6 + 100.828416e6
+# (2^18 cells, S16, G = 1, tuned shape 64 cells x 2 angle chunks), from the ncu --set full
+# capture summarised in profiles/.
+SWEEP_DRAM_BYTES_NCU = 271.808768e6 + 100.235776e6
+# FP64 issue rate of one SM: 2 DFMA per clock (GB300: 1.25 TFLOP/s FP64 = 152 SMs x 2 x 2 flops
+# x 2.07 GHz); the ALU roofline's peak = SMs x this x 2 flops x the maximum SM clock.
+FP64_FMA_PER_SM_CLK = 2
 
 
 def parse():
@@ -341,7 +345,10 @@ def run_ours(args):
                         (np.abs(bs.phi(i) - phi_b[i]).max() / np.abs(phi_b[i]).max() for i in both), default=0.0))
                 batched[name] = ent
 
-    # dominant kernel: the fused sweep; its launch time from a run of n sweeps
+    # dominant kernel: the fused sweep.  Its average launch duration over the timed
+    # region = device time of the K steps / sweeps (an upper bound: includes the
+    # per-step constant, carry and balance kernels, < 1 %); cross-checked by a run
+    # of n sweeps through oci_iterate
     n_sw = 50
     psi_keep = s.psi()
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -350,13 +357,17 @@ def run_ours(args):
     s.iterate(n_sw)
     f1.record(stream)
     torch.cuda.synchronize()
-    sweep_ms = f0.elapsed_time(f1) / n_sw
+    sweep_ms_iter = f0.elapsed_time(f1) / n_sw
+    sweep_ms = ms / sweeps
     s.set_psi(psi_keep)
     NG = p.N * p.G
     flops_cell = 68 * NG + 32 * p.G * p.G
     bytes_cell = 96 * NG + 4
     flops = flops_cell * p.J
     achieved_tf = flops / (sweep_ms * 1e-3) / 1e12
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    clk_mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
+    peak_alu = n_sm * FP64_FMA_PER_SM_CLK * 2 * clk_mhz * 1e6
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"hbm_gbs": 6800.0}
     hbm_gbs = bytes_cell * p.J / (sweep_ms * 1e-3) / 1e9
@@ -388,13 +399,17 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config(args, p),
             "sweeps_per_step": sweeps / args.steps,
-            "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": peak_fp64 / 1e12, "unit": "TFLOP/s",
-                         "frac": achieved_tf * 1e12 / peak_fp64,
+            "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": peak_alu / 1e12, "unit": "TFLOP/s",
+                         "frac": achieved_tf * 1e12 / peak_alu,
                          "traffic": SWEEP_DRAM_BYTES_NCU if (p.J == 2 ** 18 and p.N == 16 and p.G == 1) else None,
                          "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
                          "algorithmic_bytes": bytes_cell * p.J,
                          "kernel": "k_oci_sweep (FP64 structured cell solve)",
-                         "peak_source": "measured live: register-only DFMA loop (oci_probe_fp64_peak)",
+                         "peak_source": f"derived: {n_sm} SMs x {FP64_FMA_PER_SM_CLK} FP64 FMA/clk x 2 flops x "
+                                        f"{clk_mhz:.0f} MHz max SM clock",
+                         "peak_measured_dfma_loop": peak_fp64 / 1e12,
+                         "frac_of_measured_dfma_loop": achieved_tf * 1e12 / peak_fp64,
+                         "sweep_us_oci_iterate": sweep_ms_iter * 1e3,
                          "hbm_achieved_gbs": hbm_gbs, "hbm_peak_gbs": peaks.get("hbm_gbs"),
                          "hbm_frac": hbm_gbs / peaks.get("hbm_gbs", 6800.0),
                          "sweep_us": sweep_ms * 1e3, "flops_per_cell": flops_cell, "bytes_per_cell": bytes_cell},

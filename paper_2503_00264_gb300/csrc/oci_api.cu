@@ -303,11 +303,26 @@ static int autotune(Handle &h) {
       if ((c.first < 0) == want_tma) keep.push_back(c);
     if (!keep.empty()) cands.swap(keep);
   }
+  // OCI_SWEEP_SHAPE="cb,P" keeps one legal shape (cb = -1: the TMA inner
+  // sweep) without timing, so a profiler sees no tuning launches
+  const char *shape = getenv("OCI_SWEEP_SHAPE");
+  if (shape) {
+    int fcb = 0, fP = 0;
+    if (sscanf(shape, "%d,%d", &fcb, &fP) == 2)
+      for (auto &c : cands)
+        if (c.first == fcb && c.second == fP) {
+          cands.assign(1, c);
+          break;
+        }
+  }
   if (cands.size() < 2) {
     if (cands.size() == 1 && mx) {
       h.mx_tma = cands[0].first < 0;
       h.mx_cb = cands[0].first < 0 ? 0 : cands[0].first;
       h.mx_P = cands[0].second;
+    } else if (cands.size() == 1) {
+      h.tune_cb = cands[0].first;
+      h.tune_P = cands[0].second;
     }
     return OCI_OK;
   }

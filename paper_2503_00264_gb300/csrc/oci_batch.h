@@ -57,6 +57,8 @@ struct Batch {
   DevState *h_ds = nullptr;   // [n] pinned
   int *active = nullptr;      // device counter of unconverged slabs
   double *h_bal = nullptr;    // pinned, per class concatenated
+  int *h_active = nullptr;    // pinned copy of the unconverged count (host-driven loop)
+  bool no_graph = false;      // drive the loop from the host (OCI_NO_GRAPH=1)
   cudaStream_t stream = nullptr;
   cudaGraphExec_t graph = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
