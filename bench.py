@@ -227,6 +227,8 @@ def run_ours(args):
         smx.close()
         mixed = []
         phi64, psi64, b64 = s.phi(), s.psi(), s.balance()
+        peaks_hbm = (json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+            os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"hbm_gbs": 6800.0}).get("hbm_gbs", 6800.0)
         forms = (("FP32_IR", oci.FP32_IR, "FP32 structured block apply on CUDA cores"),
                  ("TF32_IR", oci.TF32_IR, "TF32 dense block apply on tcgen05 tensor cores"),
                  ("BF16X3_IR", oci.BF16X3_IR, "BF16 hi/lo x3 dense block apply on tcgen05 tensor cores"))
@@ -238,15 +240,23 @@ def run_ours(args):
             clk2 = Clocks(local)
             barrier()
             m0.record(stream)
-            mx_sweeps = 0
+            mx_sweeps, mx_ref = 0, 0
             for _ in range(args.steps):
-                mx_sweeps += sv.step()["iters"]
+                st_mx = sv.step()
+                mx_sweeps += st_mx["iters"]
+                mx_ref += st_mx["refinements"]
             m1.record(stream)
             barrier()
             clk_mx = clk2.stop()
             mx_ms = max_over_ranks(m0.elapsed_time(m1))
             phimx, psimx, bmx = sv.phi(), sv.psi(), sv.balance()
+            info_mx = sv.info()
             sv.close()
+            # HBM traffic of the form's step (algorithmic): per inner sweep the FP32
+            # operand z, delta_in and delta_out (12 B per unknown); per FP64 refinement
+            # (and the initial residual) Psi in/out, c, delta in, z out (32 B per unknown)
+            step_bytes = (mx_sweeps * 12 + (mx_ref + args.steps) * 32) * p.unknowns / args.steps
+            step_gbs = step_bytes / (mx_ms / args.steps * 1e-3) / 1e9
             mixed.append({
                 "form": name, "block_apply": what,
                 "fp64_kept_for": "iterate, residual, norm accumulation, balance tallies, carry",
@@ -258,6 +268,12 @@ def run_ours(args):
                                 "psi_rel": float(np.abs(psimx - psi64).max() / np.abs(psi64).max()),
                                 "balance_rel": float(np.abs(bmx - b64).max() / np.abs(b64).max()),
                                 "sweeps_diff_total": int(mx_sweeps - sweeps)},
+                "refinements_per_step": mx_ref / args.steps,
+                "inner_kernel": info_mx["inner_kernel"],
+                "hbm": {"bytes_per_step": step_bytes, "achieved_gbs": step_gbs,
+                        "peak_gbs": peaks_hbm, "frac": step_gbs / peaks_hbm,
+                        "note": "whole step incl. refinements, FP64 norm/stop rule and carry"}
+                if prec == oci.FP32_IR else None,
                 "clocks": clk_mx})
 
     # seconds per converged time step: OCI (FP64 and mixed) against GPU SI

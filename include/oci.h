@@ -153,6 +153,10 @@ typedef struct {
                                [1] time-edge balance (Eqs. scb-mb-c + d summed)       */
   double t;                 /* simulated time after the step                          */
   double seconds;           /* wall time of the convergence loop (CUDA events)        */
+  int32_t refinements;      /* mixed forms: passes of the FP64 refinement that fold the
+                               correction into Psi (the last one at convergence; the
+                               initial residual not counted); 0 for FP64 and SI      */
+  int32_t reserved;
 } oci_stats;
 
 /* Setup facts of a handle (oci_get_info). */
@@ -161,7 +165,10 @@ typedef struct {
   int32_t cells_per_block;   /* launch shape of the sweep kernel picked by the autotuner         */
   int32_t angle_chunks;      /* threads per (cell, group): angles split into this many chunks    */
   int32_t inner_kernel;      /* mixed forms: 0 plain FP32 sweep, 1 TMA-staged FP32 sweep,
-                                2 tcgen05 tensor-core block apply; -1 for the FP64 form            */
+                                2 tcgen05 tensor-core block apply, 3 register FP32 sweep (angles
+                                split over threads), 4 the register sweep on tile-major FP32
+                                correction arrays, 5 the same as a persistent kernel, 6 that with
+                                the tiles moved by 1D bulk copies (TMA); -1 for the FP64 form     */
   double tuned_sweep_us;     /* measured time of one sweep with the chosen shape (0 if not tuned) */
 } oci_info;
 

@@ -282,48 +282,76 @@ static int autotune(Handle &h) {
   const bool mx = h.precision == OCI_FP32_IR;
   if (h.solver == OCI_SOLVER_DENSE_LU || (h.precision != OCI_FP64 && !mx)) return OCI_OK;
   const size_t es = mx ? 4 : 8;
-  std::vector<std::pair<int, int>> cands;
+  struct Cand {
+    int kind, cb, P;  // kind: kMxPlain (and the FP64 sweep), kMxTma, kMxReg
+  };
+  std::vector<Cand> cands;
   for (int cb : {32, 64, 128, 256})
     for (int P : {1, 2, 4, 8}) {
       if (h.N % P) continue;
       const int thr = cb * h.G * P;
       if (thr < 32 || thr > 256) continue;
       if (sweep_smem(h.N, h.G, cb, P, es) > 100 * 1024) continue;
-      cands.emplace_back(cb, P);
+      cands.push_back({kMxPlain, cb, P});
     }
   if (mx && h.tma_ok)
     for (int P : {1, 2, 4, 8})
-      if (h.N % P == 0 && 64 * h.G * P <= 256 && mx_tma_smem(h, P) <= 200 * 1024) cands.emplace_back(-1, P);
-  // OCI_MX_INNER=plain|tma restricts the FP32 inner sweep to one kernel (for profiling)
+      if (h.N % P == 0 && 64 * h.G * P <= 256 && mx_tma_smem(h, P) <= 200 * 1024) cands.push_back({kMxTma, 64, P});
+  if (mx)
+    for (int np : {2, 4, 8}) {
+      if (h.N % np) continue;
+      const int P = h.N / np;
+      for (int cb : {32, 64, 128}) {
+        const int thr = cb * h.G * P;
+        if (thr <= 256 && thr % 32 == 0) cands.push_back({kMxReg, cb, P});
+        if (thr <= 256 && cb <= 64) {
+          cands.push_back({kMxTiled, cb, P});
+          cands.push_back({kMxTiledP, cb, P});
+          if (mx_tb_smem(h, cb, P, mx_tables_floats(h) * 4 <= 64 * 1024) <= 200 * 1024)
+            cands.push_back({kMxTiledB, cb, P});
+        }
+      }
+    }
+  // OCI_MX_INNER=plain|tma|reg|tiled|tiledp|tiledb restricts the FP32 inner sweep to one kernel (for profiling)
   const char *only = getenv("OCI_MX_INNER");
   if (mx && only) {
-    const bool want_tma = std::string(only) == "tma";
-    std::vector<std::pair<int, int>> keep;
+    const std::string o(only);
+    const int want = o == "tma"      ? kMxTma
+                     : o == "reg"    ? kMxReg
+                     : o == "tiled"  ? kMxTiled
+                     : o == "tiledp" ? kMxTiledP
+                     : o == "tiledb" ? kMxTiledB
+                                     : kMxPlain;
+    std::vector<Cand> keep;
     for (auto &c : cands)
-      if ((c.first < 0) == want_tma) keep.push_back(c);
+      if (c.kind == want) keep.push_back(c);
     if (!keep.empty()) cands.swap(keep);
   }
-  // OCI_SWEEP_SHAPE="cb,P" keeps one legal shape (cb = -1: the TMA inner
-  // sweep) without timing, so a profiler sees no tuning launches
+  // OCI_SWEEP_SHAPE="cb,P" keeps one legal shape (the first of the remaining
+  // candidates with that shape) without timing, so a profiler sees no tuning launches
   const char *shape = getenv("OCI_SWEEP_SHAPE");
   if (shape) {
     int fcb = 0, fP = 0;
     if (sscanf(shape, "%d,%d", &fcb, &fP) == 2)
       for (auto &c : cands)
-        if (c.first == fcb && c.second == fP) {
-          cands.assign(1, c);
+        if (c.cb == fcb && c.P == fP) {
+          const Cand keep = c;
+          cands.assign(1, keep);
           break;
         }
   }
-  if (cands.size() < 2) {
-    if (cands.size() == 1 && mx) {
-      h.mx_tma = cands[0].first < 0;
-      h.mx_cb = cands[0].first < 0 ? 0 : cands[0].first;
-      h.mx_P = cands[0].second;
-    } else if (cands.size() == 1) {
-      h.tune_cb = cands[0].first;
-      h.tune_P = cands[0].second;
+  auto apply = [&](const Cand &c) {
+    if (mx) {
+      h.mx_kind = c.kind;
+      h.mx_cb = c.cb;
+      h.mx_P = c.P;
+    } else {
+      h.tune_cb = c.cb;
+      h.tune_P = c.P;
     }
+  };
+  if (cands.size() < 2) {
+    if (cands.size() == 1) apply(cands[0]);
     return OCI_OK;
   }
   DevState &d = *h.h_ds;
@@ -338,22 +366,17 @@ static int autotune(Handle &h) {
   d.theta = 0.0;
   CK(cudaMemcpyAsync(h.ds, h.h_ds, sizeof(DevState), cudaMemcpyHostToDevice, h.stream));
   float best = 1e30f;
-  int bcb = 0, bP = 0;
+  Cand bc = cands[0];
   const int reps = 3;
   for (auto &c : cands) {
-    if (mx) {
-      h.mx_tma = c.first < 0;
-      h.mx_cb = c.first < 0 ? 0 : c.first;
-      h.mx_P = c.second;
-      launch_mx_inner(h, cudaGraphConditionalHandle{}, 0);
-    } else {
-      h.tune_cb = c.first;
-      h.tune_P = c.second;
-      launch_oci_sweep(h, cudaGraphConditionalHandle{}, 0);
-    }
+    apply(c);
+    auto sweep = [&]() {
+      if (mx) launch_mx_inner(h, cudaGraphConditionalHandle{}, 0);
+      else launch_oci_sweep(h, cudaGraphConditionalHandle{}, 0);
+    };
+    sweep();
     CK(cudaEventRecord(h.ev0, h.stream));
-    for (int r = 0; r < reps; r++)
-      mx ? launch_mx_inner(h, cudaGraphConditionalHandle{}, 0) : launch_oci_sweep(h, cudaGraphConditionalHandle{}, 0);
+    for (int r = 0; r < reps; r++) sweep();
     CK(cudaEventRecord(h.ev1, h.stream));
     CK(cudaEventSynchronize(h.ev1));
     CK(cudaGetLastError());
@@ -361,25 +384,18 @@ static int autotune(Handle &h) {
     cudaEventElapsedTime(&ms, h.ev0, h.ev1);
     if (ms < best) {
       best = ms;
-      bcb = c.first;
-      bP = c.second;
+      bc = c;
     }
   }
-  if (mx) {
-    h.mx_tma = bcb < 0;
-    h.mx_cb = bcb < 0 ? 0 : bcb;
-    h.mx_P = bP;
-  } else {
-    h.tune_cb = bcb;
-    h.tune_P = bP;
-  }
+  apply(bc);
   h.tune_us = 1e3 * best / reps;
   const size_t nPsi = (size_t)h.G * h.N * 4 * h.Jp;
   CK(cudaMemsetAsync(h.Psi[0], 0, nPsi * 8, h.stream));
   CK(cudaMemsetAsync(h.Psi[1], 0, nPsi * 8, h.stream));
   if (mx) {
-    CK(cudaMemsetAsync(h.delta[0], 0, nPsi * 4, h.stream));
-    CK(cudaMemsetAsync(h.delta[1], 0, nPsi * 4, h.stream));
+    const size_t nPsi32 = (size_t)h.G * h.N * 4 * std::max<size_t>(h.Jp, (h.J + 63) / 64 * 64);
+    CK(cudaMemsetAsync(h.delta[0], 0, nPsi32 * 4, h.stream));
+    CK(cudaMemsetAsync(h.delta[1], 0, nPsi32 * 4, h.stream));
   }
   std::memset(h.h_ds, 0, sizeof(DevState));
   h.h_ds->done = 1;
@@ -402,7 +418,7 @@ static void free_handle(Handle *h) {
                   h->tt.Cin, h->tt.Mp,  h->tt.Kap,    h->tt.dx,     h->tt.sig,       h->si_z,      h->si_uin,
                   h->LU,     h->piv,    h->partials,  h->bal_partials, h->bal,       h->e_hist,    h->ds,
                   h->stage,  h->delta[0], h->delta[1], h->z32, h->w32, h->tt.Lco, h->tt.Linv32, h->tt.Cin32,
-                  h->tt.Mp32, h->tc_img, h->si_maps, h->si_segin, h->counter, h->psi_user};
+                  h->tt.Mp32, h->tc_img, h->si_maps, h->si_segin, h->counter, h->psi_user, h->gbar};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (h->h_ds) cudaFreeHost(h->h_ds);
@@ -497,6 +513,12 @@ static int setup_impl(const oci_problem *p, oci_handle *h) {
   CK(cudaMalloc(&h->partials, (size_t)np * 8));
   CK(cudaMalloc(&h->counter, sizeof(unsigned)));
   CK(cudaMemsetAsync(h->counter, 0, sizeof(unsigned), s));
+  CK(cudaMalloc(&h->gbar, 2 * sizeof(unsigned)));
+  CK(cudaMemsetAsync(h->gbar, 0, 2 * sizeof(unsigned), s));
+  {
+    const char *mm = getenv("OCI_MX_MULTI");  // 0: one inner sweep per launch in the graph as well
+    h->mx_multi = !(mm && mm[0] == '0');
+  }
   const int nblk_carry = (h->J + 31) / 32;
   CK(cudaMalloc(&h->bal_partials, (size_t)nblk_carry * G * 8 * 8));
   CK(cudaMalloc(&h->bal, G * 10 * 8));
@@ -528,13 +550,16 @@ static int setup_impl(const oci_problem *p, oci_handle *h) {
     if ((rc = dev_upload(&h->tt.Cin32, C32.data(), C32.size(), s))) return rc;
     if ((rc = dev_upload(&h->tt.Mp32, M32.data(), M32.size(), s))) return rc;
     if ((rc = dev_upload(&h->w32, W32.data(), W32.size(), s))) return rc;
-    CK(cudaMalloc(&h->delta[0], nPsi * 4));
-    CK(cudaMalloc(&h->delta[1], nPsi * 4));
-    CK(cudaMalloc(&h->z32, nPsi * 4));
-    CK(cudaMemsetAsync(h->delta[0], 0, nPsi * 4, s));
-    CK(cudaMemsetAsync(h->delta[1], 0, nPsi * 4, s));
-    CK(cudaMemsetAsync(h->z32, 0, nPsi * 4, s));
-    CK(cudaFuncSetAttribute(k_mx_inner_ptr(), cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    // FP32 correction arrays: room for both layouts ([R][Jp], and tile-major
+    // with tiles of up to 64 cells)
+    const size_t nPsi32 = (size_t)G * N * 4 * std::max<size_t>(Jp, (h->J + 63) / 64 * 64);
+    CK(cudaMalloc(&h->delta[0], nPsi32 * 4));
+    CK(cudaMalloc(&h->delta[1], nPsi32 * 4));
+    CK(cudaMalloc(&h->z32, nPsi32 * 4));
+    CK(cudaMemsetAsync(h->delta[0], 0, nPsi32 * 4, s));
+    CK(cudaMemsetAsync(h->delta[1], 0, nPsi32 * 4, s));
+    CK(cudaMemsetAsync(h->z32, 0, nPsi32 * 4, s));
+    if ((rc = mx_set_attributes())) return rc;
     if (h->precision == OCI_FP32_IR && (rc = mx_tma_setup(*h))) return rc;
     if (h->precision == OCI_TF32_IR) {
       h->mx_theta = 2e-2;
@@ -592,17 +617,22 @@ static int setup_impl(const oci_problem *p, oci_handle *h) {
 }
 
 // Body of one iteration of the convergence loop (sweep + finalize).
+// Inner sweep of a mixed form with its norm, stop rule and refinement decision.
+static void launch_mx_sweep(Handle &h, cudaGraphConditionalHandle cond, int use_cond) {
+  if (h.precision == OCI_FP32_IR) {
+    launch_mx_inner(h, cond, use_cond);  // norm and stop rule fused in
+  } else {
+    launch_tc_inner(h);
+    launch_mx_finalize(h, cond, use_cond);
+  }
+}
+
 static void launch_body(Handle &h, bool si, cudaGraphConditionalHandle cond, int use_cond) {
   if (si) {
     launch_si_sweep(h);
     launch_finalize(h, h.partials, si_partials(h), cond, use_cond);
   } else if (h.precision != OCI_FP64) {
-    if (h.precision == OCI_FP32_IR) {
-      launch_mx_inner(h, cond, use_cond);  // norm and stop rule fused in
-    } else {
-      launch_tc_inner(h);
-      launch_mx_finalize(h, cond, use_cond);
-    }
+    launch_mx_sweep(h, cond, use_cond);
     launch_mx_outer(h, 1);
   } else if (h.solver == OCI_SOLVER_DENSE_LU) {
     launch_dense_sweep(h);
@@ -630,9 +660,43 @@ static int build_graph(Handle &h, bool si, cudaGraphExec_t *out) {
   cudaStream_t saved = h.stream;
   h.stream = cs;
   cudaError_t e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
-  if (e == cudaSuccess) {
+  const bool mx = !si && h.precision != OCI_FP64;
+  if (e == cudaSuccess && !mx) {
     launch_body(h, si, cond, 1);
     e = cudaStreamEndCapture(cs, &body);
+  } else if (e == cudaSuccess) {
+    // mixed forms: the FP64 refinement sits under an IF node whose value the
+    // sweep's stop-rule block sets, so a sweep without refinement launches
+    // nothing after the inner kernel
+    launch_mx_sweep(h, cond, 1);
+    cudaStreamCaptureStatus cst;
+    cudaGraph_t cg = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t nd = 0;
+    cudaGraphConditionalHandle cref{};
+    cudaGraphNodeParams ip = {};
+    cudaGraphNode_t ifn;
+    e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, &cg, &deps, nullptr, &nd);
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&cref, cg, 0, cudaGraphCondAssignDefault);
+    if (e == cudaSuccess) {
+      ip.type = cudaGraphNodeTypeConditional;
+      ip.conditional.handle = cref;
+      ip.conditional.type = cudaGraphCondTypeIf;
+      ip.conditional.size = 1;
+      e = cudaGraphAddNode(&ifn, cg, deps, nullptr, nd, &ip);
+    }
+    if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(cs, &ifn, nullptr, 1, cudaStreamSetCaptureDependencies);
+    cudaError_t e2 = cudaStreamEndCapture(cs, &body);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) {
+      cudaGraph_t ifbody = ip.conditional.phGraph_out[0];
+      e = cudaStreamBeginCaptureToGraph(cs, ifbody, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        launch_mx_outer(h, 1);
+        e = cudaStreamEndCapture(cs, &ifbody);
+      }
+    }
+    if (e == cudaSuccess) h.mx_cond_ref = (unsigned long long)cref;
   }
   h.stream = saved;
   cudaStreamDestroy(cs);
@@ -665,7 +729,9 @@ static int begin_iteration(Handle &h, int fixed, int cap) {
   d.theta = h.mx_theta;
   d.e_blk0 = 0.0;
   d.inplace = h.ordering == OCI_ORDER_RED_BLACK && h.precision == OCI_FP64 && h.solver != OCI_SOLVER_DENSE_LU;
+  d.cond_ref = h.mx_cond_ref;  // read only by kernels launched from the graph (use_cond)
   CK(cudaMemcpyAsync(h.ds, h.h_ds, sizeof(DevState), cudaMemcpyHostToDevice, h.stream));
+  if (h.gbar) CK(cudaMemsetAsync(h.gbar, 0, 2 * sizeof(unsigned), h.stream));  // grid barrier count
   return OCI_OK;
 }
 
@@ -724,6 +790,8 @@ static int run_step(Handle &h, bool si, oci_stats *st) {
     st->rho_e_last = d.rho;
     st->t = h.t;
     st->seconds = ms * 1e-3;
+    st->refinements = (si || h.precision == OCI_FP64) ? 0 : d.n_refine;
+    st->reserved = 0;
     st->balance_rel[0] = st->balance_rel[1] = 0.0;
     if (d.status == OCI_OK) {
       for (int g = 0; g < h.G; g++)
@@ -1063,9 +1131,11 @@ int oci_get_info(const oci_handle *h, oci_info *info) {
     info->angle_chunks = c.chunks;
     info->inner_kernel = -1;
   } else if (h->precision == OCI_FP32_IR) {
-    info->cells_per_block = h->mx_tma ? 64 : h->mx_cb;
-    info->angle_chunks = h->mx_P;
-    info->inner_kernel = h->mx_tma ? 1 : 0;
+    int cb = 0, P = 0;
+    mx_shape(*h, cb, P);
+    info->cells_per_block = cb;
+    info->angle_chunks = P;
+    info->inner_kernel = h->mx_kind;
   } else {
     info->cells_per_block = 128;
     info->angle_chunks = 1;

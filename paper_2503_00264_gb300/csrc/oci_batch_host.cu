@@ -524,6 +524,8 @@ static int batch_step(Batch &B, oci_stats *st) {
     o.rho_e_last = d.rho;
     o.t = B.t[i];
     o.seconds = ms * 1e-3;
+    o.refinements = B.precision == OCI_FP64 ? 0 : d.n_refine;
+    o.reserved = 0;
     o.balance_rel[0] = o.balance_rel[1] = 0.0;
     if (d.status != OCI_OK) continue;
     const int ci = B.slab_class[i], G = B.G[i];

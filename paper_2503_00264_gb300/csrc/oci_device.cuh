@@ -133,6 +133,8 @@ __device__ __forceinline__ void finish_mixed(DevState *ds, double *e_hist, doubl
   if (refine) d.n_refine += 1;
   *ds = d;
   if (use_cond && d.done) cudaGraphSetConditional(cond, 0);
+  // in the graph the refinement kernel runs under an IF node (no handle: always launched)
+  if (use_cond && d.cond_ref) cudaGraphSetConditional((cudaGraphConditionalHandle)d.cond_ref, refine);
 }
 
 }  // namespace oci

@@ -44,6 +44,7 @@ struct DevState {
   double theta;   // refine once e < theta * (first e of the block)
   double e_blk0;
   int inplace;    // 1: the sweep updates Psi[cur] in place (red-black ordering)
+  unsigned long long cond_ref;  // mixed forms in a graph: handle of the IF node of the refinement
 };
 
 // Per-cell-type tables of the structured solve (all FP64, device).
@@ -97,7 +98,10 @@ struct Handle {
   double mx_theta = 1e-3;
   CUtensorMap tm_z, tm_d[2];          // TMA descriptors of z32 and delta[0/1] ([R][Jp] FP32)
   bool tma_ok = false;                 // tensor maps encoded (4NG <= 256)
-  bool mx_tma = false;                 // the autotuner picked the TMA-staged inner sweep
+  unsigned long long mx_cond_ref = 0;  // IF-node handle of the refinement in the mixed-form graph
+  bool mx_multi = true;                // graph runs the persistent tiled FP32 sweep several sweeps per launch
+  unsigned *gbar = nullptr;            // {count, generation} of the multi-sweep kernel's grid barrier
+  int mx_kind = 0;                     // FP32 inner sweep picked by the autotuner: kMxPlain, kMxTma, kMxReg, kMxTiled
   unsigned char *tc_img = nullptr;     // [T] x (A^{-1} image(s) in the tcgen05 K-major layout)
   size_t tc_img_bytes = 0;             // bytes per type
   // SI scratch
@@ -165,6 +169,16 @@ void launch_mx_outer(Handle &h, int mode);
 void launch_mx_finalize(Handle &h, cudaGraphConditionalHandle cond, int use_cond);
 int mx_partials(const Handle &h);
 int mx_tma_setup(Handle &h);
+// FP32 inner sweeps of the mixed form (values of Handle::mx_kind and oci_info.inner_kernel);
+// kMxTiled, kMxTiledP (persistent) and kMxTiledB (persistent, tiles moved by
+// 1D bulk copies) keep the FP32 correction arrays tile-major
+// ([J/T][4NG][T], T = mx_cb)
+constexpr int kMxPlain = 0, kMxTma = 1, kMxReg = 3, kMxTiled = 4, kMxTiledP = 5, kMxTiledB = 6;
+size_t mx_tb_smem(const Handle &h, int T, int P, bool stage);
+size_t mx_tables_floats(const Handle &h);
+int mx_tile_shift(const Handle &h);
+int mx_set_attributes();
+void mx_shape(const Handle &h, int &cb, int &P);
 size_t mx_tma_smem(const Handle &h, int P);
 // tensor-core block apply (TF32 / BF16x3 forms)
 int tc_prepare(Handle &h);

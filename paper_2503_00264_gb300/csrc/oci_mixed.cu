@@ -28,6 +28,19 @@
 
 namespace oci {
 
+// Index of row r, cell j of an FP32 correction array: [R][Jp] (tsh = 0) or
+// tile-major [J/T][R][T] with T = 2^tsh.
+__device__ __forceinline__ size_t fidx(int tsh, int R, size_t Jp, int r, int j) {
+  if (!tsh) return (size_t)r * Jp + j;
+  return ((((size_t)(j >> tsh)) * R + r) << tsh) + (size_t)(j & ((1 << tsh) - 1));
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+int mx_tile_shift(const Handle &h) {
+  return (h.mx_kind == kMxTiled || h.mx_kind == kMxTiledP || h.mx_kind == kMxTiledB) ? (h.mx_cb == 32 ? 5 : 6) : 0;
+}
+
 // ---------------------------------------------------------------- inner sweep
 // delta_out = A~^{-1}(r + B delta_in) through the structured solve in FP32:
 // t = z + Cin u, y = sum_m w t, s = Mp y, delta = t + Linv s, where z = A~-block
@@ -150,6 +163,863 @@ __global__ void __launch_bounds__(256) k_mx_inner(int J, int Jp, int N, int G, i
   }
 }
 
+// ---------------------------------------------------------------- inner sweep, register form
+// The same FP32 inner sweep with the N angles of a cell split over P = N/NP
+// threads, each keeping its NP angles' t and delta_in in registers: all of a
+// thread's loads (z, the upstream edges, its own delta_in for the norm) are
+// issued before any arithmetic, so more bytes are in flight per SM than in the
+// staged form.  The angle sum y is reduced over the chunks in a fixed order and
+// s = Mp y is split over the chunk threads of each group.
+size_t mx_reg_smem(int G, int cb, int P) { return (size_t)cb * ((size_t)G * P * 4 + 8 * (size_t)G) * 4; }
+
+template <int NP>
+__global__ void __launch_bounds__(256) k_mx_inner_reg(int J, int Jp, int N, int G, const int32_t *__restrict__ type,
+                                                      const float *__restrict__ Linv, const float *__restrict__ Cin,
+                                                      const float *__restrict__ Mp, const float *__restrict__ w,
+                                                      const float *__restrict__ z, float *D0, float *D1,
+                                                      DevState *ds, double *__restrict__ partials,
+                                                      unsigned *counter, double *e_hist,
+                                                      cudaGraphConditionalHandle cond, int use_cond) {
+  extern __shared__ float smr[];
+  __shared__ double red[8];
+  __shared__ bool s_last;
+  const int CB = blockDim.x, P = N / NP, G4 = 4 * G;
+  const int cl = threadIdx.x, gy = threadIdx.y;
+  const int g = gy / P, ch = gy % P, m0 = ch * NP;
+  const int j = blockIdx.x * CB + cl;
+  if (ds->done) return;  // uniform across the grid
+  const bool zero = ds->refine || ds->blk_i == 0;
+  const int dcur = ds->dcur;
+  const float *__restrict__ Din = dcur ? D1 : D0;
+  float *__restrict__ Dout = dcur ? D0 : D1;
+  float *y_s = smr;                          // [G*P*4][CB] chunk partials of y
+  float *yr_s = y_s + (size_t)G * P * 4 * CB;  // [4G][CB] y
+  float *s_s = yr_s + (size_t)G4 * CB;        // [4G][CB] s
+  const bool active = j < J;
+  const int tau = active ? type[j] : 0;
+  const int N2 = N / 2;
+  const size_t tb = (size_t)tau * G * N;
+  float t[NP][4], old[NP][4];
+  float y0 = 0.f, y1 = 0.f, y2 = 0.f, y3 = 0.f;
+  if (active) {
+    float uk[NP], uh[NP];
+#pragma unroll
+    for (int i = 0; i < NP; i++) {
+      const int m = m0 + i;
+      const size_t base = (size_t)(g * N + m) * 4 * Jp + j;
+      uk[i] = 0.f;
+      uh[i] = 0.f;
+#pragma unroll
+      for (int p = 0; p < 4; p++) {
+        t[i][p] = z[base + (size_t)p * Jp];
+        old[i][p] = 0.f;
+      }
+      if (!zero) {
+#pragma unroll
+        for (int p = 0; p < 4; p++) old[i][p] = Din[base + (size_t)p * Jp];
+        if (m >= N2) {
+          if (j > 0) {
+            uk[i] = Din[base + (size_t)Jp - 1];
+            uh[i] = Din[base + 3 * (size_t)Jp - 1];
+          }
+        } else if (j < J - 1) {
+          uk[i] = Din[base + 1];
+          uh[i] = Din[base + 2 * (size_t)Jp + 1];
+        }
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < NP; i++) {
+      const int m = m0 + i;
+      const float *C = Cin + (tb + g * N + m) * 8;
+#pragma unroll
+      for (int p = 0; p < 4; p++) t[i][p] = fmaf(C[2 * p + 1], uh[i], fmaf(C[2 * p], uk[i], t[i][p]));
+      const float wm = w[m];
+      y0 = fmaf(wm, t[i][0], y0);
+      y1 = fmaf(wm, t[i][1], y1);
+      y2 = fmaf(wm, t[i][2], y2);
+      y3 = fmaf(wm, t[i][3], y3);
+    }
+  }
+  {
+    float *ys = y_s + (size_t)(gy * 4) * CB + cl;
+    ys[0] = y0;
+    ys[CB] = y1;
+    ys[2 * CB] = y2;
+    ys[3 * CB] = y3;
+  }
+  __syncthreads();
+  for (int q = ch; q < 4; q += P) {  // y_{g,q}: fixed-order sum over the group's chunks
+    float v = y_s[(size_t)((g * P) * 4 + q) * CB + cl];
+    for (int k = 1; k < P; k++) v += y_s[(size_t)((g * P + k) * 4 + q) * CB + cl];
+    yr_s[(size_t)(g * 4 + q) * CB + cl] = v;
+  }
+  __syncthreads();
+  if (active)
+    for (int q = ch; q < 4; q += P) {  // s_{g,q} = sum_k Mp[g*4+q][k] y_k
+      const float *M = Mp + (size_t)tau * G4 * G4 + (size_t)(g * 4 + q) * G4;
+      float v = 0.f;
+      for (int k = 0; k < G4; k++) v = fmaf(M[k], yr_s[(size_t)k * CB + cl], v);
+      s_s[(size_t)(g * 4 + q) * CB + cl] = v;
+    }
+  __syncthreads();
+  float e2 = 0.f;
+  if (active) {
+    const float s0 = s_s[(size_t)(g * 4 + 0) * CB + cl], s1 = s_s[(size_t)(g * 4 + 1) * CB + cl];
+    const float s2 = s_s[(size_t)(g * 4 + 2) * CB + cl], s3 = s_s[(size_t)(g * 4 + 3) * CB + cl];
+#pragma unroll
+    for (int i = 0; i < NP; i++) {
+      const int gm = g * N + m0 + i;
+      const size_t base = (size_t)gm * 4 * Jp + j;
+      const float *L = Linv + (tb + gm) * 16;
+#pragma unroll
+      for (int p = 0; p < 4; p++) {
+        const float o = fmaf(L[p * 4 + 3], s3, fmaf(L[p * 4 + 2], s2, fmaf(L[p * 4 + 1], s1, fmaf(L[p * 4 + 0], s0, t[i][p]))));
+        const float d = o - old[i][p];
+        e2 = fmaf(d, d, e2);
+        Dout[base + (size_t)p * Jp] = o;
+      }
+    }
+  }
+  // FP64 accumulation of the per-thread FP32 partial sums
+  double v = (double)e2;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int nthr = blockDim.x * blockDim.y;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((tid & 31) == 0) red[tid >> 5] = v;
+  __syncthreads();
+  double bs = 0.0;
+  if (tid == 0)
+    for (int i = 0; i < (nthr + 31) / 32; i++) bs += red[i];
+  if (publish_partial(partials, blockIdx.x, bs, counter, gridDim.x, &s_last)) {
+    const double tot = block_sum_fixed(partials, gridDim.x, red);
+    if (tid == 0) {
+      *counter = 0;
+      finish_mixed(ds, e_hist, sqrt(tot), cond, use_cond);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- inner sweep, tiled layout
+// The register form on the tile-major FP32 layout [J/T][4NG][T] (T cells per
+// tile, one tile per block): all rows of a thread's angles are at fixed
+// offsets (i*4 + p)*T from one base pointer, so the loads and stores need no
+// per-element address arithmetic, and a tile's operands are contiguous in HBM.
+// The per-type tables are fetched as float4.  Neighbour edges across a tile
+// boundary come from the adjacent tile's first / last column.
+size_t mx_tiled_smem(int G, int T, int P) { return mx_reg_smem(G, T, P); }
+
+template <int T, int NP>
+__global__ void __launch_bounds__(256) k_mx_inner_tiled(int J, int N, int G, const int32_t *__restrict__ type,
+                                                        const float *__restrict__ Linv,
+                                                        const float *__restrict__ Cin, const float *__restrict__ Mp,
+                                                        const float *__restrict__ w, const float *__restrict__ z,
+                                                        float *D0, float *D1, DevState *ds,
+                                                        double *__restrict__ partials, unsigned *counter,
+                                                        double *e_hist, cudaGraphConditionalHandle cond,
+                                                        int use_cond) {
+  extern __shared__ float smr[];
+  __shared__ double red[8];
+  __shared__ bool s_last;
+  const int P = N / NP, G4 = 4 * G, R = 4 * N * G;
+  const int cl = threadIdx.x, gy = threadIdx.y;
+  const int g = gy / P, ch = gy % P, m0 = ch * NP;
+  const int j = blockIdx.x * T + cl;
+  if (ds->done) return;  // uniform across the grid
+  const bool zero = ds->refine || ds->blk_i == 0;
+  const int dcur = ds->dcur;
+  const float *__restrict__ Din = dcur ? D1 : D0;
+  float *__restrict__ Dout = dcur ? D0 : D1;
+  float *y_s = smr;
+  float *yr_s = y_s + (size_t)G * P * 4 * T;
+  float *s_s = yr_s + (size_t)G4 * T;
+  const bool active = j < J;
+  const int tau = active ? type[j] : 0;
+  const int N2 = N / 2;
+  const size_t tb = (size_t)tau * G * N;
+  const size_t off = ((size_t)blockIdx.x * R + (size_t)(g * N + m0) * 4) * T + cl;
+  const float *__restrict__ zb = z + off;
+  const float *__restrict__ db = Din + off;
+  float *__restrict__ ob = Dout + off;
+  float t[NP][4], old[NP][4];
+  float y0 = 0.f, y1 = 0.f, y2 = 0.f, y3 = 0.f;
+  if (active) {
+    float uk[NP], uh[NP];
+    // upstream cell j-1 / j+1: same tile, or the last / first column of the adjacent tile
+    const long long offL = cl > 0 ? -1 : (T - 1) - (long long)R * T;
+    const long long offR = cl < T - 1 ? 1 : (long long)R * T - (T - 1);
+#pragma unroll
+    for (int i = 0; i < NP; i++) {
+      const int m = m0 + i;
+#pragma unroll
+      for (int p = 0; p < 4; p++) {
+        t[i][p] = zb[(i * 4 + p) * T];
+        old[i][p] = zero ? 0.f : db[(i * 4 + p) * T];
+      }
+      uk[i] = 0.f;
+      uh[i] = 0.f;
+      if (!zero) {
+        if (m >= N2) {
+          if (j > 0) {
+            uk[i] = db[offL + (i * 4 + 1) * T];
+            uh[i] = db[offL + (i * 4 + 3) * T];
+          }
+        } else if (j < J - 1) {
+          uk[i] = db[offR + (i * 4 + 0) * T];
+          uh[i] = db[offR + (i * 4 + 2) * T];
+        }
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < NP; i++) {
+      const int m = m0 + i;
+      const float4 *C4 = reinterpret_cast<const float4 *>(Cin + (tb + g * N + m) * 8);
+      const float4 ca = C4[0], cb = C4[1];
+      t[i][0] = fmaf(ca.y, uh[i], fmaf(ca.x, uk[i], t[i][0]));
+      t[i][1] = fmaf(ca.w, uh[i], fmaf(ca.z, uk[i], t[i][1]));
+      t[i][2] = fmaf(cb.y, uh[i], fmaf(cb.x, uk[i], t[i][2]));
+      t[i][3] = fmaf(cb.w, uh[i], fmaf(cb.z, uk[i], t[i][3]));
+      const float wm = w[m];
+      y0 = fmaf(wm, t[i][0], y0);
+      y1 = fmaf(wm, t[i][1], y1);
+      y2 = fmaf(wm, t[i][2], y2);
+      y3 = fmaf(wm, t[i][3], y3);
+    }
+  }
+  {
+    float *ys = y_s + (size_t)(gy * 4) * T + cl;
+    ys[0] = y0;
+    ys[T] = y1;
+    ys[2 * T] = y2;
+    ys[3 * T] = y3;
+  }
+  __syncthreads();
+  for (int q = ch; q < 4; q += P) {
+    float v = y_s[(size_t)((g * P) * 4 + q) * T + cl];
+    for (int k = 1; k < P; k++) v += y_s[(size_t)((g * P + k) * 4 + q) * T + cl];
+    yr_s[(size_t)(g * 4 + q) * T + cl] = v;
+  }
+  __syncthreads();
+  if (active)
+    for (int q = ch; q < 4; q += P) {
+      const float *M = Mp + (size_t)tau * G4 * G4 + (size_t)(g * 4 + q) * G4;
+      float v = 0.f;
+      for (int k = 0; k < G4; k++) v = fmaf(M[k], yr_s[(size_t)k * T + cl], v);
+      s_s[(size_t)(g * 4 + q) * T + cl] = v;
+    }
+  __syncthreads();
+  float e2 = 0.f;
+  if (active) {
+    const float s0 = s_s[(size_t)(g * 4 + 0) * T + cl], s1 = s_s[(size_t)(g * 4 + 1) * T + cl];
+    const float s2 = s_s[(size_t)(g * 4 + 2) * T + cl], s3 = s_s[(size_t)(g * 4 + 3) * T + cl];
+#pragma unroll
+    for (int i = 0; i < NP; i++) {
+      const float4 *L4 = reinterpret_cast<const float4 *>(Linv + (tb + g * N + m0 + i) * 16);
+#pragma unroll
+      for (int p = 0; p < 4; p++) {
+        const float4 L = L4[p];
+        const float o = fmaf(L.w, s3, fmaf(L.z, s2, fmaf(L.y, s1, fmaf(L.x, s0, t[i][p]))));
+        const float d = o - old[i][p];
+        e2 = fmaf(d, d, e2);
+        ob[(i * 4 + p) * T] = o;
+      }
+    }
+  }
+  double v = (double)e2;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int nthr = blockDim.x * blockDim.y;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((tid & 31) == 0) red[tid >> 5] = v;
+  __syncthreads();
+  double bs = 0.0;
+  if (tid == 0)
+    for (int i = 0; i < (nthr + 31) / 32; i++) bs += red[i];
+  if (publish_partial(partials, blockIdx.x, bs, counter, gridDim.x, &s_last)) {
+    const double tot = block_sum_fixed(partials, gridDim.x, red);
+    if (tid == 0) {
+      *counter = 0;
+      finish_mixed(ds, e_hist, sqrt(tot), cond, use_cond);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- inner sweep, tiled + persistent
+// The tiled register sweep as a persistent kernel: each block reads the device
+// state once, stages the per-type tables (Linv, Cin, w, Mp) in shared memory
+// when they fit (else reads them from global memory through the same generic
+// pointers), walks the tiles tile = blockIdx.x, blockIdx.x + gridDim.x, ...
+// and publishes one partial of the norm (its tiles summed in a fixed order).
+// This removes the per-tile state read, table latency and end-of-block fence
+// and atomic of the one-tile-per-block form.
+size_t mx_tables_floats(const Handle &h) {
+  const size_t T = h.tt.n_types, G = h.G, N = h.N;
+  return T * G * N * 24 + N + T * 16 * G * G;
+}
+size_t mx_tp_smem(const Handle &h, int T, int P, bool stage) {
+  return mx_reg_smem(h.G, T, P) + (stage ? mx_tables_floats(h) * 4 + 16 : 0);
+}
+
+// Per-type tables into shared memory (16-byte aligned sections); the pointers
+// are redirected to the copies.  All threads; no barrier.
+__device__ __forceinline__ void stage_tables(float *tab, int n_types, int N, int G, int tid, int nthr,
+                                             const float *&Linv, const float *&Cin, const float *&Mp,
+                                             const float *&w) {
+  const int G4 = 4 * G;
+  const size_t nL = (size_t)n_types * G * N * 16, nC = (size_t)n_types * G * N * 8;
+  const size_t nM = (size_t)n_types * G4 * G4;
+  float *sL = tab, *sC = sL + nL, *sM = sC + nC, *sw = sM + nM;
+  for (size_t i = tid; i < nL; i += nthr) sL[i] = Linv[i];
+  for (size_t i = tid; i < nC; i += nthr) sC[i] = Cin[i];
+  for (size_t i = tid; i < nM; i += nthr) sM[i] = Mp[i];
+  for (int i = tid; i < N; i += nthr) sw[i] = w[i];
+  Linv = sL;
+  Cin = sC;
+  Mp = sM;
+  w = sw;
+}
+
+// One tile of the tiled register sweep by the whole block; returns this
+// thread's sum of squared changes.  Contains three block barriers; shared
+// memory y_s / yr_s / s_s may be reused by the next call.
+template <int T, int NP>
+__device__ __forceinline__ float tiled_tile(int tile, int J, int N, int G, int cl, int gy, bool zero,
+                                            const int32_t *__restrict__ type, const float *Linv, const float *Cin,
+                                            const float *Mp, const float *w, const float *__restrict__ z,
+                                            const float *__restrict__ Din, float *__restrict__ Dout, float *y_s,
+                                            float *yr_s, float *s_s) {
+  const int P = N / NP, G4 = 4 * G, R = 4 * N * G;
+  const int g = gy / P, ch = gy % P, m0 = ch * NP;
+  const int N2 = N / 2;
+  const long long offL = cl > 0 ? -1 : (T - 1) - (long long)R * T;
+  const long long offR = cl < T - 1 ? 1 : (long long)R * T - (T - 1);
+  const int j = tile * T + cl;
+  const bool active = j < J;
+  const int tau = active ? type[j] : 0;
+  const size_t tb = (size_t)tau * G * N;
+  const size_t off = ((size_t)tile * R + (size_t)(g * N + m0) * 4) * T + cl;
+  const float *__restrict__ zb = z + off;
+  const float *__restrict__ db = Din + off;
+  float *__restrict__ ob = Dout + off;
+  float t[NP][4], old[NP][4];
+  float y0 = 0.f, y1 = 0.f, y2 = 0.f, y3 = 0.f;
+  if (active) {
+    float uk[NP], uh[NP];
+#pragma unroll
+    for (int i = 0; i < NP; i++) {
+      const int m = m0 + i;
+#pragma unroll
+      for (int p = 0; p < 4; p++) {
+        t[i][p] = zb[(i * 4 + p) * T];
+        old[i][p] = zero ? 0.f : db[(i * 4 + p) * T];
+      }
+      uk[i] = 0.f;
+      uh[i] = 0.f;
+      if (!zero) {
+        if (m >= N2) {
+          if (j > 0) {
+            uk[i] = db[offL + (i * 4 + 1) * T];
+            uh[i] = db[offL + (i * 4 + 3) * T];
+          }
+        } else if (j < J - 1) {
+          uk[i] = db[offR + (i * 4 + 0) * T];
+          uh[i] = db[offR + (i * 4 + 2) * T];
+        }
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < NP; i++) {
+      const int m = m0 + i;
+      const float4 *C4 = reinterpret_cast<const float4 *>(Cin + (tb + g * N + m) * 8);
+      const float4 ca = C4[0], cb = C4[1];
+      t[i][0] = fmaf(ca.y, uh[i], fmaf(ca.x, uk[i], t[i][0]));
+      t[i][1] = fmaf(ca.w, uh[i], fmaf(ca.z, uk[i], t[i][1]));
+      t[i][2] = fmaf(cb.y, uh[i], fmaf(cb.x, uk[i], t[i][2]));
+      t[i][3] = fmaf(cb.w, uh[i], fmaf(cb.z, uk[i], t[i][3]));
+      const float wm = w[m];
+      y0 = fmaf(wm, t[i][0], y0);
+      y1 = fmaf(wm, t[i][1], y1);
+      y2 = fmaf(wm, t[i][2], y2);
+      y3 = fmaf(wm, t[i][3], y3);
+    }
+  }
+  {
+    float *ys = y_s + (size_t)(gy * 4) * T + cl;
+    ys[0] = y0;
+    ys[T] = y1;
+    ys[2 * T] = y2;
+    ys[3 * T] = y3;
+  }
+  __syncthreads();
+  for (int q = ch; q < 4; q += P) {
+    float v = y_s[(size_t)((g * P) * 4 + q) * T + cl];
+    for (int k = 1; k < P; k++) v += y_s[(size_t)((g * P + k) * 4 + q) * T + cl];
+    yr_s[(size_t)(g * 4 + q) * T + cl] = v;
+  }
+  __syncthreads();
+  if (active)
+    for (int q = ch; q < 4; q += P) {
+      const float *M = Mp + (size_t)tau * G4 * G4 + (size_t)(g * 4 + q) * G4;
+      float v = 0.f;
+      for (int k = 0; k < G4; k++) v = fmaf(M[k], yr_s[(size_t)k * T + cl], v);
+      s_s[(size_t)(g * 4 + q) * T + cl] = v;
+    }
+  __syncthreads();
+  float e2 = 0.f;
+  if (active) {
+    const float s0 = s_s[(size_t)(g * 4 + 0) * T + cl], s1 = s_s[(size_t)(g * 4 + 1) * T + cl];
+    const float s2 = s_s[(size_t)(g * 4 + 2) * T + cl], s3 = s_s[(size_t)(g * 4 + 3) * T + cl];
+#pragma unroll
+    for (int i = 0; i < NP; i++) {
+      const float4 *L4 = reinterpret_cast<const float4 *>(Linv + (tb + g * N + m0 + i) * 16);
+#pragma unroll
+      for (int p = 0; p < 4; p++) {
+        const float4 L = L4[p];
+        const float o = fmaf(L.w, s3, fmaf(L.z, s2, fmaf(L.y, s1, fmaf(L.x, s0, t[i][p]))));
+        const float d = o - old[i][p];
+        e2 = fmaf(d, d, e2);
+        ob[(i * 4 + p) * T] = o;
+      }
+    }
+  }
+  // y_s of the next call is written only after the s_s barrier of this one;
+  // s_s is rewritten two barriers later
+  return e2;
+}
+
+// Fixed-order block sum of per-thread values (the result in thread 0).
+__device__ __forceinline__ double block_reduce_fixed(float e2, double *red, int tid, int nthr) {
+  double v = (double)e2;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  __syncthreads();  // red may still be read by a previous reduction
+  if ((tid & 31) == 0) red[tid >> 5] = v;
+  __syncthreads();
+  double bs = 0.0;
+  if (tid == 0)
+    for (int i = 0; i < (nthr + 31) / 32; i++) bs += red[i];
+  return bs;
+}
+
+template <int T, int NP>
+__global__ void __launch_bounds__(256) k_mx_inner_tp(int J, int N, int G, int n_types, int stage,
+                                                     const int32_t *__restrict__ type, const float *Linv_g,
+                                                     const float *Cin_g, const float *Mp_g, const float *w_g,
+                                                     const float *__restrict__ z, float *D0, float *D1, DevState *ds,
+                                                     double *__restrict__ partials, unsigned *counter,
+                                                     double *e_hist, cudaGraphConditionalHandle cond, int use_cond) {
+  extern __shared__ __align__(16) float smr[];
+  __shared__ double red[8];
+  __shared__ bool s_last;
+  const int P = N / NP, G4 = 4 * G;
+  const int cl = threadIdx.x, gy = threadIdx.y;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int nthr = blockDim.x * blockDim.y;
+  if (ds->done) return;  // uniform across the grid
+  const bool zero = ds->refine || ds->blk_i == 0;
+  const int dcur = ds->dcur;
+  const float *__restrict__ Din = dcur ? D1 : D0;
+  float *__restrict__ Dout = dcur ? D0 : D1;
+  float *y_s = smr;
+  float *yr_s = y_s + (size_t)G * P * 4 * T;
+  float *s_s = yr_s + (size_t)G4 * T;
+  const float *Linv = Linv_g, *Cin = Cin_g, *Mp = Mp_g, *w = w_g;
+  if (stage) {
+    stage_tables(s_s + (size_t)G4 * T, n_types, N, G, tid, nthr, Linv, Cin, Mp, w);
+    __syncthreads();
+  }
+  const int ntiles = (J + T - 1) / T;
+  float e2 = 0.f;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
+    e2 += tiled_tile<T, NP>(tile, J, N, G, cl, gy, zero, type, Linv, Cin, Mp, w, z, Din, Dout, y_s, yr_s, s_s);
+  const double bs = block_reduce_fixed(e2, red, tid, nthr);
+  if (publish_partial(partials, blockIdx.x, bs, counter, gridDim.x, &s_last)) {
+    const double tot = block_sum_fixed(partials, gridDim.x, red);
+    if (tid == 0) {
+      *counter = 0;
+      finish_mixed(ds, e_hist, sqrt(tot), cond, use_cond);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- inner sweeps, multi-sweep
+// Consecutive inner sweeps of the persistent tiled form in one cooperative
+// launch (all blocks resident): after each sweep a grid barrier, then every
+// block sums the per-block partials in the same fixed order, so all blocks
+// reach the same e and take the same stop-rule and refinement decision on
+// their copy of the device state.  The launch ends when the stop rule holds
+// or a refinement is due (the graph's IF node then runs the FP64 refinement
+// and the WHILE loop relaunches).  Partials are double-buffered by sweep
+// parity: a block that starts the next sweep cannot overwrite values another
+// block is still summing.  The barrier spin is bounded; a timeout records
+// OCI_E_TIMEOUT and ends the step.
+constexpr long long kGridSpin = 1 << 21;
+
+// Sense-reversing grid barrier on {count, generation}; thread 0 of every block.
+__device__ __forceinline__ bool grid_barrier(unsigned *gbar, unsigned nblocks) {
+  volatile unsigned *vgen = gbar + 1;
+  const unsigned g0 = *vgen;  // cannot advance before this block arrives
+  __threadfence();
+  const unsigned arrived = atomicAdd(gbar, 1u);
+  if (arrived == nblocks - 1) {
+    gbar[0] = 0;
+    __threadfence();
+    atomicAdd(gbar + 1, 1u);
+    return true;
+  }
+  for (long long k = 0; k < kGridSpin; k++) {
+    if (*vgen != g0) {
+      __threadfence();
+      return true;
+    }
+    __nanosleep(64);
+  }
+  return false;
+}
+
+template <int T, int NP>
+__global__ void __launch_bounds__(256) k_mx_inner_ms(int J, int N, int G, int n_types, int stage,
+                                                     const int32_t *__restrict__ type, const float *Linv_g,
+                                                     const float *Cin_g, const float *Mp_g, const float *w_g,
+                                                     const float *__restrict__ z, float *D0, float *D1, DevState *ds,
+                                                     double *__restrict__ partials, unsigned *gbar, double *e_hist,
+                                                     cudaGraphConditionalHandle cond) {
+  extern __shared__ __align__(16) float smr[];
+  __shared__ double red[8];
+  __shared__ DevState sd;
+  __shared__ int s_ok;
+  const int P = N / NP, G4 = 4 * G;
+  const int cl = threadIdx.x, gy = threadIdx.y;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int nthr = blockDim.x * blockDim.y;
+  if (tid == 0) sd = *ds;
+  __syncthreads();
+  if (sd.done) return;  // uniform across the grid
+  float *y_s = smr;
+  float *yr_s = y_s + (size_t)G * P * 4 * T;
+  float *s_s = yr_s + (size_t)G4 * T;
+  const float *Linv = Linv_g, *Cin = Cin_g, *Mp = Mp_g, *w = w_g;
+  if (stage) {
+    stage_tables(s_s + (size_t)G4 * T, n_types, N, G, tid, nthr, Linv, Cin, Mp, w);
+    __syncthreads();
+  }
+  const int ntiles = (J + T - 1) / T;
+  bool failed = false;
+  for (int sw = 0;; sw++) {
+    const bool zero = sd.refine || sd.blk_i == 0;
+    const float *__restrict__ Din = sd.dcur ? D1 : D0;
+    float *__restrict__ Dout = sd.dcur ? D0 : D1;
+    float e2 = 0.f;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
+      e2 += tiled_tile<T, NP>(tile, J, N, G, cl, gy, zero, type, Linv, Cin, Mp, w, z, Din, Dout, y_s, yr_s, s_s);
+    const double bs = block_reduce_fixed(e2, red, tid, nthr);
+    double *part = partials + (size_t)(sw & 1) * gridDim.x;
+    if (tid == 0) {
+      part[blockIdx.x] = bs;
+      s_ok = grid_barrier(gbar, gridDim.x);
+    }
+    __syncthreads();
+    if (!s_ok) {
+      failed = true;
+      break;
+    }
+    const double tot = block_sum_fixed(part, gridDim.x, red);
+    if (tid == 0) finish_mixed(&sd, blockIdx.x == 0 ? e_hist : nullptr, sqrt(tot), cond, 0);
+    __syncthreads();
+    if (sd.done || sd.refine) break;  // uniform: every block holds the same state
+  }
+  if (blockIdx.x == 0 && tid == 0) {
+    if (failed) {
+      sd.status = OCI_E_TIMEOUT;
+      sd.done = 1;
+      sd.refine = 0;
+    }
+    *ds = sd;
+    if (sd.done) cudaGraphSetConditional(cond, 0);
+    if (sd.cond_ref) cudaGraphSetConditional((cudaGraphConditionalHandle)sd.cond_ref, sd.refine);
+  }
+}
+
+template <int T, int NP>
+static int ms_grid(const Handle &h, int P, size_t smem) {
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mx_inner_ms<T, NP>, T * h.G * P, smem);
+  const int ntiles = (h.J + T - 1) / T;
+  const int grid = sms * (per > 0 ? per : 1);
+  return grid < ntiles ? grid : ntiles;
+}
+
+template <int T, int NP>
+static void launch_ms(Handle &h, int P, size_t smem, bool stage, cudaGraphConditionalHandle cond) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(ms_grid<T, NP>(h, P, smem));
+  cfg.blockDim = dim3(T, h.G * P);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = h.stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;  // all blocks resident: they wait on one another
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k_mx_inner_ms<T, NP>, h.J, h.N, h.G, h.tt.n_types, (int)stage, (const int32_t *)h.type,
+                     (const float *)h.tt.Linv32, (const float *)h.tt.Cin32, (const float *)h.tt.Mp32,
+                     (const float *)h.w32, (const float *)h.z32, h.delta[0], h.delta[1], h.ds, h.partials, h.gbar,
+                     h.e_hist, cond);
+}
+
+template <int T, int NP>
+static int tp_grid(const Handle &h, int P, size_t smem) {
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mx_inner_tp<T, NP>, T * h.G * P, smem);
+  const int ntiles = (h.J + T - 1) / T;
+  const int grid = sms * (per > 0 ? per : 1);
+  return grid < ntiles ? grid : ntiles;
+}
+
+// ---------------------------------------------------------------- inner sweep, tiled + bulk copies
+// The persistent tiled sweep with each tile's operands brought into shared
+// memory by the tensor memory accelerator: in the tile-major layout a tile's
+// z and delta_in are each one contiguous chunk of 4NG*T floats, so one 1D bulk
+// copy (cp.async.bulk, completing on an mbarrier) per array moves them.  Two
+// stages: the copies of the block's next tile are in flight while the current
+// tile is computed.  Only the upstream edge of a tile's first / last column is
+// read from global memory (the adjacent tile).  Every wait is bounded: on a
+// timeout the block records OCI_E_TIMEOUT, waits (bounded) for its copies still
+// in flight and leaves.
+constexpr long long kBulkSpin = 1 << 22;
+
+__device__ __forceinline__ void bulk_load_1d(uint32_t dst, const void *src, uint32_t bytes, uint32_t mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(mbar)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+  uint32_t ok = 0;
+  for (long long k = 0; k < kBulkSpin && !ok; k++)
+    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(ok)
+                 : "r"(bar), "r"(parity)
+                 : "memory");
+  return ok != 0;
+}
+
+size_t mx_tb_smem(const Handle &h, int T, int P, bool stage) {
+  const size_t chunk = (size_t)4 * h.N * h.G * T;
+  return 4 * chunk * 4 + mx_tp_smem(h, T, P, stage) + 128;
+}
+
+template <int T, int NP>
+__global__ void __launch_bounds__(256) k_mx_inner_tb(int J, int N, int G, int n_types, int stage,
+                                                     const int32_t *__restrict__ type, const float *Linv_g,
+                                                     const float *Cin_g, const float *Mp_g, const float *w_g,
+                                                     const float *__restrict__ z, float *D0, float *D1, DevState *ds,
+                                                     double *__restrict__ partials, unsigned *counter,
+                                                     double *e_hist, cudaGraphConditionalHandle cond, int use_cond) {
+  extern __shared__ __align__(128) unsigned char smb_[];
+  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ double red[8];
+  __shared__ bool s_last;
+  const int P = N / NP, G4 = 4 * G, R = 4 * N * G;
+  const int cl = threadIdx.x, gy = threadIdx.y;
+  const int g = gy / P, ch = gy % P, m0 = ch * NP;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int nthr = blockDim.x * blockDim.y;
+  if (ds->done) return;  // uniform across the grid
+  const bool zero = ds->refine || ds->blk_i == 0;
+  const int dcur = ds->dcur;
+  const float *__restrict__ Din = dcur ? D1 : D0;
+  float *__restrict__ Dout = dcur ? D0 : D1;
+  float *smb = (float *)(((uintptr_t)smb_ + 127) & ~(uintptr_t)127);
+  const size_t chunk = (size_t)R * T;  // floats of one array in one tile
+  const uint32_t cbytes = (uint32_t)(chunk * 4);
+  const uint32_t tx = zero ? cbytes : 2 * cbytes;
+  float *y_s = smb + 4 * chunk;  // stages: [st][z, delta][chunk]
+  float *yr_s = y_s + (size_t)G * P * 4 * T;
+  float *s_s = yr_s + (size_t)G4 * T;
+  const float *Linv = Linv_g, *Cin = Cin_g, *Mp = Mp_g, *w = w_g;
+  if (stage) {
+    float *tab = s_s + (size_t)G4 * T;
+    const size_t nL = (size_t)n_types * G * N * 16, nC = (size_t)n_types * G * N * 8;
+    const size_t nM = (size_t)n_types * G4 * G4;
+    float *sL = tab, *sC = sL + nL, *sM = sC + nC, *sw = sM + nM;
+    for (size_t i = tid; i < nL; i += nthr) sL[i] = Linv_g[i];
+    for (size_t i = tid; i < nC; i += nthr) sC[i] = Cin_g[i];
+    for (size_t i = tid; i < nM; i += nthr) sM[i] = Mp_g[i];
+    for (int i = tid; i < N; i += nthr) sw[i] = w_g[i];
+    Linv = sL;
+    Cin = sC;
+    Mp = sM;
+    w = sw;
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&mbar[0])), "r"(1));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&mbar[1])), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  __syncthreads();
+  const int ntiles = (J + T - 1) / T;
+  auto issue = [&](int tile, int st) {  // thread 0
+    const uint32_t bar = smem_addr(&mbar[st]);
+    float *dst = smb + (size_t)st * 2 * chunk;
+    asm volatile("fence.proxy.async.shared::cta;");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(tx) : "memory");
+    bulk_load_1d(smem_addr(dst), z + (size_t)tile * chunk, cbytes, bar);
+    if (!zero) bulk_load_1d(smem_addr(dst + chunk), Din + (size_t)tile * chunk, cbytes, bar);
+  };
+  const int N2 = N / 2;
+  float e2 = 0.f;
+  int it = 0;
+  bool failed = false;
+  if (tid == 0 && (int)blockIdx.x < ntiles) issue(blockIdx.x, 0);
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, it++) {
+    const int st = it & 1;
+    // stage st^1 was last read before the y_s barrier of the previous tile
+    if (tid == 0 && tile + (int)gridDim.x < ntiles) issue(tile + gridDim.x, st ^ 1);
+    const bool ok = mbar_wait_bounded(smem_addr(&mbar[st]), (uint32_t)((it >> 1) & 1));
+    if (!__syncthreads_and(ok)) {  // the same decision in every thread
+      failed = true;
+      break;
+    }
+    const float *zs = smb + (size_t)st * 2 * chunk;
+    const float *dsm = zs + chunk;
+    const int j = tile * T + cl;
+    const bool active = j < J;
+    const int tau = active ? type[j] : 0;
+    const size_t tb = (size_t)tau * G * N;
+    const int row0 = (g * N + m0) * 4;
+    float t[NP][4], old[NP][4];
+    float y0 = 0.f, y1 = 0.f, y2 = 0.f, y3 = 0.f;
+    if (active) {
+#pragma unroll
+      for (int i = 0; i < NP; i++) {
+        const int m = m0 + i;
+        const int r = row0 + i * 4;
+#pragma unroll
+        for (int p = 0; p < 4; p++) {
+          t[i][p] = zs[(r + p) * T + cl];
+          old[i][p] = zero ? 0.f : dsm[(r + p) * T + cl];
+        }
+        float uk = 0.f, uh = 0.f;
+        if (!zero) {
+          if (m >= N2) {  // R corner of cell j-1
+            if (cl > 0) {
+              uk = dsm[(r + 1) * T + cl - 1];
+              uh = dsm[(r + 3) * T + cl - 1];
+            } else if (j > 0) {
+              const float *prev = Din + ((size_t)(tile - 1) * R) * T + (T - 1);
+              uk = prev[(size_t)(r + 1) * T];
+              uh = prev[(size_t)(r + 3) * T];
+            }
+          } else {  // L corner of cell j+1
+            if (j < J - 1) {
+              if (cl < T - 1) {
+                uk = dsm[(r + 0) * T + cl + 1];
+                uh = dsm[(r + 2) * T + cl + 1];
+              } else {
+                const float *next = Din + ((size_t)(tile + 1) * R) * T;
+                uk = next[(size_t)(r + 0) * T];
+                uh = next[(size_t)(r + 2) * T];
+              }
+            }
+          }
+        }
+        const float4 *C4 = reinterpret_cast<const float4 *>(Cin + (tb + g * N + m) * 8);
+        const float4 ca = C4[0], cb = C4[1];
+        t[i][0] = fmaf(ca.y, uh, fmaf(ca.x, uk, t[i][0]));
+        t[i][1] = fmaf(ca.w, uh, fmaf(ca.z, uk, t[i][1]));
+        t[i][2] = fmaf(cb.y, uh, fmaf(cb.x, uk, t[i][2]));
+        t[i][3] = fmaf(cb.w, uh, fmaf(cb.z, uk, t[i][3]));
+        const float wm = w[m];
+        y0 = fmaf(wm, t[i][0], y0);
+        y1 = fmaf(wm, t[i][1], y1);
+        y2 = fmaf(wm, t[i][2], y2);
+        y3 = fmaf(wm, t[i][3], y3);
+      }
+    }
+    {
+      float *ys = y_s + (size_t)(gy * 4) * T + cl;
+      ys[0] = y0;
+      ys[T] = y1;
+      ys[2 * T] = y2;
+      ys[3 * T] = y3;
+    }
+    __syncthreads();
+    for (int q = ch; q < 4; q += P) {
+      float v = y_s[(size_t)((g * P) * 4 + q) * T + cl];
+      for (int k = 1; k < P; k++) v += y_s[(size_t)((g * P + k) * 4 + q) * T + cl];
+      yr_s[(size_t)(g * 4 + q) * T + cl] = v;
+    }
+    __syncthreads();
+    if (active)
+      for (int q = ch; q < 4; q += P) {
+        const float *M = Mp + (size_t)tau * G4 * G4 + (size_t)(g * 4 + q) * G4;
+        float v = 0.f;
+        for (int k = 0; k < G4; k++) v = fmaf(M[k], yr_s[(size_t)k * T + cl], v);
+        s_s[(size_t)(g * 4 + q) * T + cl] = v;
+      }
+    __syncthreads();
+    if (active) {
+      const float s0 = s_s[(size_t)(g * 4 + 0) * T + cl], s1 = s_s[(size_t)(g * 4 + 1) * T + cl];
+      const float s2 = s_s[(size_t)(g * 4 + 2) * T + cl], s3 = s_s[(size_t)(g * 4 + 3) * T + cl];
+      float *ob = Dout + (size_t)tile * chunk + (size_t)row0 * T + cl;
+#pragma unroll
+      for (int i = 0; i < NP; i++) {
+        const float4 *L4 = reinterpret_cast<const float4 *>(Linv + (tb + g * N + m0 + i) * 16);
+#pragma unroll
+        for (int p = 0; p < 4; p++) {
+          const float4 L = L4[p];
+          const float o = fmaf(L.w, s3, fmaf(L.z, s2, fmaf(L.y, s1, fmaf(L.x, s0, t[i][p]))));
+          const float d = o - old[i][p];
+          e2 = fmaf(d, d, e2);
+          ob[(i * 4 + p) * T] = o;
+        }
+      }
+    }
+  }
+  if (failed) {
+    if (tid == 0) {  // let the copies still in flight land before the block's memory is released
+      mbar_wait_bounded(smem_addr(&mbar[it & 1]), (uint32_t)((it >> 1) & 1));
+      if (blockIdx.x + (it + 1) * gridDim.x < (unsigned)ntiles)
+        mbar_wait_bounded(smem_addr(&mbar[(it + 1) & 1]), (uint32_t)(((it + 1) >> 1) & 1));
+      atomicExch(&ds->status, OCI_E_TIMEOUT);
+      ds->done = 1;
+    }
+    __syncthreads();
+  }
+  double v = (double)e2;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((tid & 31) == 0) red[tid >> 5] = v;
+  __syncthreads();
+  double bs = 0.0;
+  if (tid == 0)
+    for (int i = 0; i < (nthr + 31) / 32; i++) bs += red[i];
+  if (publish_partial(partials, blockIdx.x, bs, counter, gridDim.x, &s_last)) {
+    const double tot = block_sum_fixed(partials, gridDim.x, red);
+    if (tid == 0) {
+      *counter = 0;
+      finish_mixed(ds, e_hist, sqrt(tot), cond, use_cond);
+    }
+  }
+}
+
+template <int T, int NP>
+static int tb_grid(const Handle &h, int P, size_t smem) {
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mx_inner_tb<T, NP>, T * h.G * P, smem);
+  const int ntiles = (h.J + T - 1) / T;
+  const int grid = sms * (per > 0 ? per : 1);
+  return grid < ntiles ? grid : ntiles;
+}
+
 // ---------------------------------------------------------------- inner sweep, TMA-staged
 // The same FP32 inner sweep with the tile's operands brought in by the tensor
 // memory accelerator: per tile of kTmaCells cells, one 2D bulk tensor copy
@@ -164,7 +1034,6 @@ constexpr int kTmaHalo = 4;                    // columns each side of the delta
 constexpr int kTmaDW = kTmaCells + 2 * kTmaHalo;  // delta box width
 constexpr long long kTmaSpin = 1 << 22;
 
-__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t mbar) {
   asm volatile(
@@ -384,9 +1253,10 @@ __global__ void __launch_bounds__(256) k_mx_outer(int J, int Jp, int N, int G, c
                                                   const double *__restrict__ mu, const double *__restrict__ inc,
                                                   const double *__restrict__ cvec, double *Psi0, double *Psi1,
                                                   const float *D0, const float *D1, const DevState *__restrict__ ds,
-                                                  int mode, int store_r, float *__restrict__ z32) {
+                                                  int mode, int store_r, float *__restrict__ z32, int tsh) {
   extern __shared__ double smd[];
   const int CB = blockDim.x;
+  const int R = 4 * N * G;
   const int cl = threadIdx.x, g = threadIdx.y;
   if (mode == 1 && !ds->refine) return;  // the common case: a small grid exits at once
   if (mode == 2 && ds->blk_i == 0) return;
@@ -412,7 +1282,7 @@ __global__ void __launch_bounds__(256) k_mx_outer(int J, int Jp, int N, int G, c
         for (int p = 0; p < 4; p++) {
           double v = Pin[base + (size_t)p * Jp];
           if (apply) {
-            v += (double)Dl[base + (size_t)p * Jp];
+            v += (double)Dl[fidx(tsh, R, Jp, gm * 4 + p, j)];
             Pout[base + (size_t)p * Jp] = v;
           }
           ph[p] = fma(wm, v, ph[p]);
@@ -451,8 +1321,8 @@ __global__ void __launch_bounds__(256) k_mx_outer(int J, int Jp, int N, int G, c
           uk = Pin[nb + (size_t)Jp];
           uh = Pin[nb + 3 * (size_t)Jp];
           if (apply) {
-            uk += (double)Dl[nb + (size_t)Jp];
-            uh += (double)Dl[nb + 3 * (size_t)Jp];
+            uk += (double)Dl[fidx(tsh, R, Jp, gm * 4 + 1, j - 1)];
+            uh += (double)Dl[fidx(tsh, R, Jp, gm * 4 + 3, j - 1)];
           }
         } else {
           uk = inc[gm * 2 + 0];
@@ -467,8 +1337,8 @@ __global__ void __launch_bounds__(256) k_mx_outer(int J, int Jp, int N, int G, c
           uk = Pin[nb];
           uh = Pin[nb + 2 * (size_t)Jp];
           if (apply) {
-            uk += (double)Dl[nb];
-            uh += (double)Dl[nb + 2 * (size_t)Jp];
+            uk += (double)Dl[fidx(tsh, R, Jp, gm * 4 + 0, j + 1)];
+            uh += (double)Dl[fidx(tsh, R, Jp, gm * 4 + 2, j + 1)];
           }
         } else {
           uk = inc[(G * N + gm) * 2 + 0];
@@ -484,16 +1354,16 @@ __global__ void __launch_bounds__(256) k_mx_outer(int J, int Jp, int N, int G, c
       r3 = fma(al, v1, fma(hm, v2, fma(-aa, v3, r3)));
       const float f0 = (float)r0, f1 = (float)r1, f2 = (float)r2, f3 = (float)r3;
       if (store_r) {  // the tensor-core inner sweep applies the dense inverse to r itself
-        z32[base] = f0;
-        z32[base + (size_t)Jp] = f1;
-        z32[base + 2 * (size_t)Jp] = f2;
-        z32[base + 3 * (size_t)Jp] = f3;
+        z32[fidx(tsh, R, Jp, gm * 4 + 0, j)] = f0;
+        z32[fidx(tsh, R, Jp, gm * 4 + 1, j)] = f1;
+        z32[fidx(tsh, R, Jp, gm * 4 + 2, j)] = f2;
+        z32[fidx(tsh, R, Jp, gm * 4 + 3, j)] = f3;
         continue;
       }
       const float *Li = Linv32 + ((size_t)tau * G * N + gm) * 16;
 #pragma unroll
       for (int p = 0; p < 4; p++)
-        z32[base + (size_t)p * Jp] = fmaf(Li[p * 4 + 3], f3, fmaf(Li[p * 4 + 2], f2, fmaf(Li[p * 4 + 1], f1, Li[p * 4 + 0] * f0)));
+        z32[fidx(tsh, R, Jp, gm * 4 + p, j)] = fmaf(Li[p * 4 + 3], f3, fmaf(Li[p * 4 + 2], f2, fmaf(Li[p * 4 + 1], f1, Li[p * 4 + 0] * f0)));
     }
   }
 }
@@ -526,8 +1396,8 @@ __global__ void k_mx_settle(DevState *ds, int kind) {
   }
 }
 
-static void mx_shape(const Handle &h, int &cb, int &P) {
-  cb = h.mx_cb;
+void mx_shape(const Handle &h, int &cb, int &P) {
+  cb = h.mx_kind == kMxTma ? kTmaCells : h.mx_cb;
   P = h.mx_P;
   if (cb > 0) return;
   P = 1;
@@ -538,7 +1408,7 @@ static void mx_shape(const Handle &h, int &cb, int &P) {
 int tc_partials(const Handle &h);
 int mx_partials(const Handle &h) {
   if (h.precision != OCI_FP32_IR) return tc_partials(h);
-  if (h.mx_tma) {
+  if (h.mx_kind == kMxTma) {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -556,7 +1426,98 @@ int mx_partials(const Handle &h) {
 // One inner sweep including its norm reduction, stop rule and refinement
 // decision (fused into the last block).
 void launch_mx_inner(Handle &h, cudaGraphConditionalHandle cond, int use_cond) {
-  if (h.mx_tma) {
+  if (h.mx_kind == kMxTiledB) {
+    const int T = h.mx_cb, P = h.mx_P, np = h.N / P;
+    const bool stage = mx_tables_floats(h) * 4 <= 64 * 1024;
+    const size_t smem = mx_tb_smem(h, T, P, stage);
+    const dim3 block(T, h.G * P);
+#define OCI_MX_TB(TT, NP)                                                                                        \
+  k_mx_inner_tb<TT, NP><<<tb_grid<TT, NP>(h, P, smem), block, smem, h.stream>>>(                                 \
+      h.J, h.N, h.G, h.tt.n_types, stage, h.type, h.tt.Linv32, h.tt.Cin32, h.tt.Mp32, h.w32, h.z32, h.delta[0], \
+      h.delta[1], h.ds, h.partials, h.counter, h.e_hist, cond, use_cond)
+    if (T == 32) {
+      if (np == 2) OCI_MX_TB(32, 2);
+      else if (np == 4) OCI_MX_TB(32, 4);
+      else OCI_MX_TB(32, 8);
+    } else {
+      if (np == 2) OCI_MX_TB(64, 2);
+      else if (np == 4) OCI_MX_TB(64, 4);
+      else OCI_MX_TB(64, 8);
+    }
+#undef OCI_MX_TB
+    return;
+  }
+  if (h.mx_kind == kMxTiledP && use_cond && h.mx_multi) {  // in the graph: several sweeps per launch
+    const int T = h.mx_cb, P = h.mx_P, np = h.N / P;
+    const bool stage = mx_tables_floats(h) * 4 <= 64 * 1024;
+    const size_t smem = mx_tp_smem(h, T, P, stage);
+    if (T == 32) {
+      if (np == 2) launch_ms<32, 2>(h, P, smem, stage, cond);
+      else if (np == 4) launch_ms<32, 4>(h, P, smem, stage, cond);
+      else launch_ms<32, 8>(h, P, smem, stage, cond);
+    } else {
+      if (np == 2) launch_ms<64, 2>(h, P, smem, stage, cond);
+      else if (np == 4) launch_ms<64, 4>(h, P, smem, stage, cond);
+      else launch_ms<64, 8>(h, P, smem, stage, cond);
+    }
+    return;
+  }
+  if (h.mx_kind == kMxTiledP) {
+    const int T = h.mx_cb, P = h.mx_P, np = h.N / P;
+    const bool stage = mx_tables_floats(h) * 4 <= 64 * 1024;
+    const size_t smem = mx_tp_smem(h, T, P, stage);
+    const dim3 block(T, h.G * P);
+#define OCI_MX_TP(TT, NP)                                                                                        \
+  k_mx_inner_tp<TT, NP><<<tp_grid<TT, NP>(h, P, smem), block, smem, h.stream>>>(                                 \
+      h.J, h.N, h.G, h.tt.n_types, stage, h.type, h.tt.Linv32, h.tt.Cin32, h.tt.Mp32, h.w32, h.z32, h.delta[0], \
+      h.delta[1], h.ds, h.partials, h.counter, h.e_hist, cond, use_cond)
+    if (T == 32) {
+      if (np == 2) OCI_MX_TP(32, 2);
+      else if (np == 4) OCI_MX_TP(32, 4);
+      else OCI_MX_TP(32, 8);
+    } else {
+      if (np == 2) OCI_MX_TP(64, 2);
+      else if (np == 4) OCI_MX_TP(64, 4);
+      else OCI_MX_TP(64, 8);
+    }
+#undef OCI_MX_TP
+    return;
+  }
+  if (h.mx_kind == kMxTiled) {
+    const int T = h.mx_cb, P = h.mx_P, np = h.N / P;
+    const dim3 block(T, h.G * P), grid((h.J + T - 1) / T);
+    const size_t smem = mx_tiled_smem(h.G, T, P);
+#define OCI_MX_TILED(TT, NP)                                                                                     \
+  k_mx_inner_tiled<TT, NP><<<grid, block, smem, h.stream>>>(h.J, h.N, h.G, h.type, h.tt.Linv32, h.tt.Cin32,      \
+                                                            h.tt.Mp32, h.w32, h.z32, h.delta[0], h.delta[1], h.ds, \
+                                                            h.partials, h.counter, h.e_hist, cond, use_cond)
+    if (T == 32) {
+      if (np == 2) OCI_MX_TILED(32, 2);
+      else if (np == 4) OCI_MX_TILED(32, 4);
+      else OCI_MX_TILED(32, 8);
+    } else {
+      if (np == 2) OCI_MX_TILED(64, 2);
+      else if (np == 4) OCI_MX_TILED(64, 4);
+      else OCI_MX_TILED(64, 8);
+    }
+#undef OCI_MX_TILED
+    return;
+  }
+  if (h.mx_kind == kMxReg) {
+    const int cb = h.mx_cb, P = h.mx_P, np = h.N / P;
+    const dim3 block(cb, h.G * P), grid((h.J + cb - 1) / cb);
+    const size_t smem = mx_reg_smem(h.G, cb, P);
+#define OCI_MX_REG(NP)                                                                                        \
+  k_mx_inner_reg<NP><<<grid, block, smem, h.stream>>>(h.J, h.Jp, h.N, h.G, h.type, h.tt.Linv32, h.tt.Cin32,    \
+                                                      h.tt.Mp32, h.w32, h.z32, h.delta[0], h.delta[1], h.ds, \
+                                                      h.partials, h.counter, h.e_hist, cond, use_cond)
+    if (np == 2) OCI_MX_REG(2);
+    else if (np == 4) OCI_MX_REG(4);
+    else OCI_MX_REG(8);
+#undef OCI_MX_REG
+    return;
+  }
+  if (h.mx_kind == kMxTma) {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -592,7 +1553,7 @@ void launch_mx_outer(Handle &h, int mode) {
   k_mx_outer<<<grid, block, smem, h.stream>>>(h.J, h.Jp, h.N, h.G, h.type, h.tt.Lco, h.tt.Kap,
                                                              h.tt.Linv32, h.w, h.mu, h.inc, h.tc, h.Psi[0], h.Psi[1],
                                                              h.delta[0], h.delta[1], h.ds, mode,
-                                                             h.precision != OCI_FP32_IR, h.z32);
+                                                             h.precision != OCI_FP32_IR, h.z32, mx_tile_shift(h));
 }
 
 void launch_mx_finalize(Handle &h, cudaGraphConditionalHandle cond, int use_cond) {
@@ -602,5 +1563,24 @@ void launch_mx_finalize(Handle &h, cudaGraphConditionalHandle cond, int use_cond
 void launch_mx_settle(Handle &h, int kind) { k_mx_settle<<<1, 1, 0, h.stream>>>(h.ds, kind); }
 
 const void *k_mx_inner_ptr() { return (const void *)k_mx_inner; }
+
+// Dynamic shared memory limits of the FP32 inner kernels above 48 KB (set once at setup).
+int mx_set_attributes() {
+  const void *ks[] = {(const void *)k_mx_inner,          (const void *)k_mx_inner_tp<32, 2>,
+                      (const void *)k_mx_inner_tp<32, 4>, (const void *)k_mx_inner_tp<32, 8>,
+                      (const void *)k_mx_inner_tp<64, 2>, (const void *)k_mx_inner_tp<64, 4>,
+                      (const void *)k_mx_inner_tp<64, 8>, (const void *)k_mx_inner_tb<32, 2>,
+                      (const void *)k_mx_inner_tb<32, 4>, (const void *)k_mx_inner_tb<32, 8>,
+                      (const void *)k_mx_inner_tb<64, 2>, (const void *)k_mx_inner_tb<64, 4>,
+                      (const void *)k_mx_inner_tb<64, 8>, (const void *)k_mx_inner_ms<32, 2>,
+                      (const void *)k_mx_inner_ms<32, 4>, (const void *)k_mx_inner_ms<32, 8>,
+                      (const void *)k_mx_inner_ms<64, 2>, (const void *)k_mx_inner_ms<64, 4>,
+                      (const void *)k_mx_inner_ms<64, 8>};
+  for (const void *k : ks) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(FP32 inner sweep)");
+  }
+  return OCI_OK;
+}
 
 }  // namespace oci

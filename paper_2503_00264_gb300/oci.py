@@ -56,11 +56,12 @@ class Info(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("status", ctypes.c_int32), ("e_last", ctypes.c_double),
                 ("rho_e_last", ctypes.c_double), ("balance_rel", ctypes.c_double * 2), ("t", ctypes.c_double),
-                ("seconds", ctypes.c_double)]
+                ("seconds", ctypes.c_double), ("refinements", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
     def as_dict(self):
         return dict(iters=self.iters, status=self.status, e=self.e_last, rho=self.rho_e_last,
-                    balance_rel=(self.balance_rel[0], self.balance_rel[1]), t=self.t, seconds=self.seconds)
+                    balance_rel=(self.balance_rel[0], self.balance_rel[1]), t=self.t, seconds=self.seconds,
+                    refinements=self.refinements)
 
 
 _lib = None

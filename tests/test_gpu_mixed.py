@@ -125,18 +125,71 @@ def test_tensor_core_full_size_matches_fp64_path(prec):
         assert rel(b.psi(), a.psi()) < 1e-10
 
 
-@pytest.mark.parametrize("kernel", ["plain", "tma"])
-def test_fp32_inner_kernels_both_match_oracle(kernel, monkeypatch):
-    """Both FP32 inner-sweep kernels (plain, and tiles staged by 2D TMA bulk
-    copies) give the FP64 oracle's answer, whichever the autotuner would pick."""
+@pytest.mark.parametrize("kernel", ["plain", "tma", "reg", "tiled", "tiledp", "tiledb"])
+def test_fp32_inner_kernels_all_match_oracle(kernel, monkeypatch):
+    """Every FP32 inner-sweep kernel (plain, tiles staged by 2D TMA bulk copies,
+    angles split over threads with t in registers, and that on tile-major
+    correction arrays, one tile per block, persistent, or persistent with the
+    tiles moved by 1D bulk copies) gives the FP64 oracle's answer, whichever the
+    autotuner would pick."""
     monkeypatch.setenv("OCI_MX_INNER", kernel)
     p = W.random_slab(28, 300, 16, 2).replace(tol=1e-11)
     o = Oracle(p)
     with oci.Solver(p, precision=oci.FP32_IR) as s:
         info = s.info()
-        assert info["inner_kernel"] == (1 if kernel == "tma" else 0)
+        assert info["inner_kernel"] == {"plain": 0, "tma": 1, "reg": 3, "tiled": 4, "tiledp": 5,
+                                        "tiledb": 6}[kernel]
         for k in range(2):
             r = o.step(OCI)
             st = s.step()
             assert st["status"] == 0 and abs(st["iters"] - r["iters"]) <= 2
             assert rel(s.phi(), r["phi"]) < 1e-10
+
+
+@pytest.mark.parametrize("kernel,shape", [("reg", "32,8"), ("reg", "64,4"), ("reg", "128,2"), ("reg", "64,2"),
+                                          ("tiled", "32,8"), ("tiled", "64,4"), ("tiled", "64,2"),
+                                          ("tiled", "32,2"), ("tiledp", "32,8"), ("tiledp", "64,4"),
+                                          ("tiledp", "64,2"), ("tiledb", "32,8"), ("tiledb", "64,4"),
+                                          ("tiledb", "64,2"), ("tiledb", "32,2")])
+def test_fp32_register_inner_shapes_match_oracle(kernel, shape, monkeypatch):
+    """Register FP32 inner sweeps (row layout, and tile-major with T = 32 or 64
+    cells) at each angle split (P = 8, 4, 2 chunks of S16 angles, G = 1) on a
+    ragged slab (J = 333: a partial last tile): flux within 1e-10 of the oracle."""
+    monkeypatch.setenv("OCI_MX_INNER", kernel)
+    monkeypatch.setenv("OCI_SWEEP_SHAPE", shape)
+    p = W.random_slab(29, 333, 16, 1).replace(tol=1e-11)
+    o = Oracle(p)
+    with oci.Solver(p, precision=oci.FP32_IR) as s:
+        info = s.info()
+        cb, P = (int(x) for x in shape.split(","))
+        assert (info["inner_kernel"], info["cells_per_block"], info["angle_chunks"]) == (
+            {"reg": 3, "tiled": 4, "tiledp": 5, "tiledb": 6}[kernel], cb, P)
+        for k in range(2):
+            r = o.step(OCI)
+            st = s.step()
+            assert st["status"] == 0 and abs(st["iters"] - r["iters"]) <= 2
+            assert rel(s.phi(), r["phi"]) < 1e-10
+
+
+def test_fp32_multi_sweep_launch_matches_single_sweep(monkeypatch):
+    """In the graph the persistent tiled FP32 sweep runs several sweeps per
+    cooperative launch (grid barrier per sweep, refinement under an IF node);
+    the same steps with one sweep per launch give the same sweep counts and the
+    same iterate (per-tile arithmetic is identical; only the order in which
+    block partials of the norm are formed may differ)."""
+    monkeypatch.setenv("OCI_MX_INNER", "tiledp")
+    monkeypatch.setenv("OCI_SWEEP_SHAPE", "64,4")
+    p = W.random_slab(31, 5000, 16, 1).replace(tol=1e-11)
+    res = {}
+    for multi in ("1", "0"):
+        monkeypatch.setenv("OCI_MX_MULTI", multi)
+        with oci.Solver(p, precision=oci.FP32_IR) as s:
+            its = [s.step()["iters"] for _ in range(3)]
+            res[multi] = (its, s.psi(), s.phi())
+    assert res["1"][0] == res["0"][0]
+    assert rel(res["1"][1], res["0"][1]) < 1e-13
+    o = Oracle(p)
+    for k in range(3):
+        r = o.step(OCI)
+        assert abs(res["1"][0][k] - r["iters"]) <= 2
+    assert rel(res["1"][2], r["phi"]) < 1e-10
