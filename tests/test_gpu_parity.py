@@ -141,7 +141,11 @@ def test_mb_closed_form_with_boundary_updates():
             prev = ph
 
 
-def test_checkpoint_resume_bitwise_and_deterministic():
+def test_checkpoint_resume_bitwise_and_deterministic(monkeypatch):
+    """Bitwise reproducible for a fixed launch shape: the angle-chunk count sets
+    the order of the angle sum, and two handles may otherwise tune to different
+    shapes, so the shape is pinned."""
+    monkeypatch.setenv("OCI_SWEEP_SHAPE", "64,2")
     p = W.random_slab(17, 200, 8, 2).replace(tol=1e-10)
     with oci.Solver(p) as a:
         for _ in range(5):
