@@ -284,8 +284,9 @@ def run_ours(args):
             q = W.slab_3region(c=args.c, tau=tau, J=args.J)
             row = {"tau": tau}
             for name, kw, si, mode in (("oci_fp64", {}, False, None), ("oci_fp32ir", {"precision": oci.FP32_IR}, False, None),
-                                       ("oci_rb_fp64", {}, False, "rb"), ("si_fp64", {}, True, None),
-                                       ("si_scan_fp64", {}, True, "scan")):
+                                       ("oci_rb_fp64", {}, False, "rb"),
+                                       ("oci_rb_fp32ir", {"precision": oci.FP32_IR}, False, "rb"),
+                                       ("si_fp64", {}, True, None), ("si_scan_fp64", {}, True, "scan")):
                 with oci.Solver(q, stream=stream.cuda_stream, **kw) as sv:
                     if mode == "rb":
                         sv.set_ordering(oci.ORDER_RED_BLACK)
@@ -303,6 +304,9 @@ def run_ours(args):
             row["oci_fp64_speedup_vs_si"] = row["si_fp64"]["s_per_step"] / row["oci_fp64"]["s_per_step"]
             row["oci_fp32ir_speedup_vs_si"] = row["si_fp64"]["s_per_step"] / row["oci_fp32ir"]["s_per_step"]
             row["oci_fp32ir_speedup_vs_si_scan"] = row["si_scan_fp64"]["s_per_step"] / row["oci_fp32ir"]["s_per_step"]
+            best_oci = min(row[k]["s_per_step"] for k in ("oci_fp64", "oci_fp32ir", "oci_rb_fp64", "oci_rb_fp32ir"))
+            best_si = min(row[k]["s_per_step"] for k in ("si_fp64", "si_scan_fp64"))
+            row["best_oci_speedup_vs_best_si"] = best_si / best_oci
             si_cmp.append(row)
 
     # multigroup slab (G = 8, S16, 2^16 cells): FP64 and the FP32-inner mixed form

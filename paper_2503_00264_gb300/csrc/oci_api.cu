@@ -404,6 +404,78 @@ static int autotune(Handle &h) {
   return OCI_OK;
 }
 
+// Red-black FP32 inner sweep of the mixed form: shapes (tile T cells, P angle
+// chunks) timed one sweep per launch; the Jacobi choice is kept for a switch back.
+// The handle's state is saved and restored around the timing.
+static int tune_rb(Handle &h) {
+  h.mx_jac_kind = h.mx_kind;
+  h.mx_jac_cb = h.mx_cb;
+  h.mx_jac_P = h.mx_P;
+  std::vector<std::pair<int, int>> cands;
+  for (int T : {32, 64})
+    for (int np : {2, 4, 8}) {
+      if (h.N % np) continue;
+      const int P = h.N / np, thr = (T / 2) * h.G * P;
+      if (thr <= 256 && thr % 32 == 0) cands.emplace_back(T, P);
+    }
+  if (cands.empty()) return set_error("no red-black inner-sweep shape fits this N, G"), OCI_E_INVAL;
+  const char *shape = getenv("OCI_SWEEP_SHAPE");
+  if (shape) {
+    int fT = 0, fP = 0;
+    if (sscanf(shape, "%d,%d", &fT, &fP) == 2)
+      for (auto &c : cands)
+        if (c.first == fT && c.second == fP) {
+          const auto keep = c;
+          cands.assign(1, keep);
+          break;
+        }
+  }
+  h.mx_kind = kMxRB;
+  if (cands.size() == 1) {
+    h.mx_cb = cands[0].first;
+    h.mx_P = cands[0].second;
+    return OCI_OK;
+  }
+  const DevState saved = *h.h_ds;
+  DevState d = saved;
+  d.done = 0;
+  d.fixed = 1;
+  d.refine = 0;
+  d.blk_i = 1;
+  d.dcur = 0;
+  d.max_iter = 0;
+  d.k_max = 1 << 30;
+  d.theta = 0.0;
+  d.inplace = 1;
+  *h.h_ds = d;
+  CK(cudaMemcpyAsync(h.ds, h.h_ds, sizeof(DevState), cudaMemcpyHostToDevice, h.stream));
+  float best = 1e30f;
+  std::pair<int, int> bc = cands[0];
+  for (auto &c : cands) {
+    h.mx_cb = c.first;
+    h.mx_P = c.second;
+    launch_mx_inner(h, cudaGraphConditionalHandle{}, 0);
+    CK(cudaEventRecord(h.ev0, h.stream));
+    for (int r = 0; r < 3; r++) launch_mx_inner(h, cudaGraphConditionalHandle{}, 0);
+    CK(cudaEventRecord(h.ev1, h.stream));
+    CK(cudaEventSynchronize(h.ev1));
+    CK(cudaGetLastError());
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, h.ev0, h.ev1);
+    if (ms < best) {
+      best = ms;
+      bc = c;
+    }
+  }
+  h.mx_cb = bc.first;
+  h.mx_P = bc.second;
+  h.tune_us = 1e3 * best / 3;
+  *h.h_ds = saved;
+  CK(cudaMemcpyAsync(h.ds, h.h_ds, sizeof(DevState), cudaMemcpyHostToDevice, h.stream));
+  CK(cudaStreamSynchronize(h.stream));
+  return OCI_OK;
+}
+
 void free_batch(Batch *b);
 
 static void free_handle(Handle *h) {
@@ -728,7 +800,8 @@ static int begin_iteration(Handle &h, int fixed, int cap) {
   d.n_refine = 0;
   d.theta = h.mx_theta;
   d.e_blk0 = 0.0;
-  d.inplace = h.ordering == OCI_ORDER_RED_BLACK && h.precision == OCI_FP64 && h.solver != OCI_SOLVER_DENSE_LU;
+  d.inplace = (h.ordering == OCI_ORDER_RED_BLACK && h.precision == OCI_FP64 && h.solver != OCI_SOLVER_DENSE_LU) ||
+              h.mx_kind == kMxRB;
   d.cond_ref = h.mx_cond_ref;  // read only by kernels launched from the graph (use_cond)
   CK(cudaMemcpyAsync(h.ds, h.h_ds, sizeof(DevState), cudaMemcpyHostToDevice, h.stream));
   if (h.gbar) CK(cudaMemsetAsync(h.gbar, 0, 2 * sizeof(unsigned), h.stream));  // grid barrier count
@@ -1059,10 +1132,20 @@ int oci_set_ordering(oci_handle *h, int32_t ordering) {
   GUARD(h);
   if (ordering != OCI_ORDER_JACOBI && ordering != OCI_ORDER_RED_BLACK)
     return set_error("bad ordering"), OCI_E_INVAL;
-  if (ordering == OCI_ORDER_RED_BLACK && (h->precision != OCI_FP64 || h->solver == OCI_SOLVER_DENSE_LU))
-    return set_error("red-black ordering needs the FP64 structured solver"), OCI_E_INVAL;
+  if (ordering == OCI_ORDER_RED_BLACK &&
+      !((h->precision == OCI_FP64 && h->solver != OCI_SOLVER_DENSE_LU) || h->precision == OCI_FP32_IR))
+    return set_error("red-black ordering needs the FP64 structured solver or the FP32_IR form"), OCI_E_INVAL;
   if (ordering == h->ordering) return OCI_OK;
   h->ordering = ordering;
+  if (h->precision == OCI_FP32_IR) {
+    int rc = ordering == OCI_ORDER_RED_BLACK ? tune_rb(*h) : OCI_OK;
+    if (rc) return rc;
+    if (ordering == OCI_ORDER_JACOBI) {  // back to the Jacobi inner sweep tuned at setup
+      h->mx_kind = h->mx_jac_kind;
+      h->mx_cb = h->mx_jac_cb;
+      h->mx_P = h->mx_jac_P;
+    }
+  }
   if (h->g_oci) {
     cudaGraphExecDestroy(h->g_oci);
     h->g_oci = nullptr;

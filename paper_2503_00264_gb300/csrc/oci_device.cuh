@@ -111,7 +111,7 @@ __device__ __forceinline__ void finish_mixed(DevState *ds, double *e_hist, doubl
   d.rho = rho;
   d.e_prev = e;
   d.l = l + 1;
-  d.dcur ^= 1;
+  if (!d.inplace) d.dcur ^= 1;  // red-black: one correction buffer updated in place
   d.blk_i += 1;
   if (d.blk_i == 1) d.e_blk0 = e;
   int verify = 0;

@@ -99,6 +99,7 @@ struct Handle {
   CUtensorMap tm_z, tm_d[2];          // TMA descriptors of z32 and delta[0/1] ([R][Jp] FP32)
   bool tma_ok = false;                 // tensor maps encoded (4NG <= 256)
   unsigned long long mx_cond_ref = 0;  // IF-node handle of the refinement in the mixed-form graph
+  int mx_jac_kind = 0, mx_jac_cb = 0, mx_jac_P = 0;  // the Jacobi FP32 inner sweep (kept while red-black)
   bool mx_multi = true;                // graph runs the persistent tiled FP32 sweep several sweeps per launch
   unsigned *gbar = nullptr;            // {count, generation} of the multi-sweep kernel's grid barrier
   int mx_kind = 0;                     // FP32 inner sweep picked by the autotuner: kMxPlain, kMxTma, kMxReg, kMxTiled
@@ -170,10 +171,11 @@ void launch_mx_finalize(Handle &h, cudaGraphConditionalHandle cond, int use_cond
 int mx_partials(const Handle &h);
 int mx_tma_setup(Handle &h);
 // FP32 inner sweeps of the mixed form (values of Handle::mx_kind and oci_info.inner_kernel);
-// kMxTiled, kMxTiledP (persistent) and kMxTiledB (persistent, tiles moved by
-// 1D bulk copies) keep the FP32 correction arrays tile-major
+// kMxTiled, kMxTiledP (persistent), kMxTiledB (persistent, tiles moved by
+// 1D bulk copies) and kMxRB (red-black ordering, columns of a tile ordered by
+// colour) keep the FP32 correction arrays tile-major
 // ([J/T][4NG][T], T = mx_cb)
-constexpr int kMxPlain = 0, kMxTma = 1, kMxReg = 3, kMxTiled = 4, kMxTiledP = 5, kMxTiledB = 6;
+constexpr int kMxPlain = 0, kMxTma = 1, kMxReg = 3, kMxTiled = 4, kMxTiledP = 5, kMxTiledB = 6, kMxRB = 7;
 size_t mx_tb_smem(const Handle &h, int T, int P, bool stage);
 size_t mx_tables_floats(const Handle &h);
 int mx_tile_shift(const Handle &h);

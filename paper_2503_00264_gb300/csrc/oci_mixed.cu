@@ -29,16 +29,23 @@
 namespace oci {
 
 // Index of row r, cell j of an FP32 correction array: [R][Jp] (tsh = 0) or
-// tile-major [J/T][R][T] with T = 2^tsh.
+// tile-major [J/T][R][T] with T = 2^(tsh & 0xff); with bit 0x100 the columns of
+// a tile are ordered by colour (even cells, then odd cells: red-black form).
 __device__ __forceinline__ size_t fidx(int tsh, int R, size_t Jp, int r, int j) {
   if (!tsh) return (size_t)r * Jp + j;
-  return ((((size_t)(j >> tsh)) * R + r) << tsh) + (size_t)(j & ((1 << tsh) - 1));
+  const int sh = tsh & 0xff;
+  int c = j & ((1 << sh) - 1);
+  if (tsh & 0x100) c = (c & 1) * (1 << (sh - 1)) + (c >> 1);
+  return ((((size_t)(j >> sh)) * R + r) << sh) + (size_t)c;
 }
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 int mx_tile_shift(const Handle &h) {
-  return (h.mx_kind == kMxTiled || h.mx_kind == kMxTiledP || h.mx_kind == kMxTiledB) ? (h.mx_cb == 32 ? 5 : 6) : 0;
+  const int sh = h.mx_cb == 32 ? 5 : 6;
+  if (h.mx_kind == kMxTiled || h.mx_kind == kMxTiledP || h.mx_kind == kMxTiledB) return sh;
+  if (h.mx_kind == kMxRB) return sh | 0x100;
+  return 0;
 }
 
 // ---------------------------------------------------------------- inner sweep
@@ -1020,6 +1027,232 @@ static int tb_grid(const Handle &h, int P, size_t smem) {
   return grid < ntiles ? grid : ntiles;
 }
 
+// ---------------------------------------------------------------- inner sweeps, red-black
+// Red-black ordering of the mixed form: each inner sweep updates the even
+// ("red") cells from their odd neighbours, then the odd ("black") cells from the
+// new red values, in place on one correction buffer (two-colour block
+// Gauss-Seidel on the same A and B).  The correction arrays are tile-major with
+// each tile's columns ordered by colour, so a half sweep reads and writes
+// contiguous half-tiles.  A grid barrier separates the colours (a black cell at
+// a tile edge reads a red cell of the adjacent tile), so the kernel is always
+// launched cooperatively: with max_sweeps = 1 outside the graph (one sweep per
+// launch), and in the graph for consecutive sweeps until a refinement or the
+// stop rule, like the Jacobi multi-sweep kernel.  On the first sweep after a
+// refinement the buffer holds the previous block's correction: the red half
+// reads no neighbours and both halves take their old values as zero.
+template <int T, int NP>
+__device__ __forceinline__ float rb_tile(int tile, int color, int J, int N, int G, int cl, int gy, bool zero,
+                                         const int32_t *__restrict__ type, const float *Linv, const float *Cin,
+                                         const float *Mp, const float *w, const float *__restrict__ z, float *D,
+                                         float *y_s, float *yr_s, float *s_s) {
+  constexpr int TH = T / 2;
+  const int P = N / NP, G4 = 4 * G, R = 4 * N * G;
+  const int g = gy / P, ch = gy % P, m0 = ch * NP;
+  const int N2 = N / 2;
+  const int j = tile * T + 2 * cl + color;
+  const bool active = j < J;
+  const int tau = active ? type[j] : 0;
+  const size_t tb = (size_t)tau * G * N;
+  const int row0 = (g * N + m0) * 4;
+  const size_t tbase = (size_t)tile * R * T;
+  const size_t off = tbase + (size_t)row0 * T + color * TH + cl;
+  // columns of the upstream cells j-1 (its R corner) and j+1 (its L corner)
+  long long offL, offR;
+  if (color == 0) {
+    offL = cl > 0 ? (long long)(TH + cl - 1) : (long long)(T - 1) - (long long)R * T;  // black j-1
+    offR = TH + cl;                                                                     // black j+1
+  } else {
+    offL = cl;                                                                      // red j-1
+    offR = cl + 1 < TH ? (long long)(cl + 1) : (long long)R * T;                    // red j+1
+  }
+  const bool read_nb = !zero || color == 1;
+  const float *zb = z + off;
+  float *db = D + off;
+  const float *nb = D + tbase + (size_t)row0 * T;  // + offL / offR + (i*4+p)*T
+  float t[NP][4], old[NP][4];
+  float y0 = 0.f, y1 = 0.f, y2 = 0.f, y3 = 0.f;
+  if (active) {
+    float uk[NP], uh[NP];
+#pragma unroll
+    for (int i = 0; i < NP; i++) {
+      const int m = m0 + i;
+#pragma unroll
+      for (int p = 0; p < 4; p++) {
+        t[i][p] = zb[(i * 4 + p) * T];
+        old[i][p] = zero ? 0.f : db[(i * 4 + p) * T];
+      }
+      uk[i] = 0.f;
+      uh[i] = 0.f;
+      if (read_nb) {
+        if (m >= N2) {
+          if (j > 0) {
+            uk[i] = nb[offL + (i * 4 + 1) * T];
+            uh[i] = nb[offL + (i * 4 + 3) * T];
+          }
+        } else if (j < J - 1) {
+          uk[i] = nb[offR + (i * 4 + 0) * T];
+          uh[i] = nb[offR + (i * 4 + 2) * T];
+        }
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < NP; i++) {
+      const int m = m0 + i;
+      const float4 *C4 = reinterpret_cast<const float4 *>(Cin + (tb + g * N + m) * 8);
+      const float4 ca = C4[0], cb = C4[1];
+      t[i][0] = fmaf(ca.y, uh[i], fmaf(ca.x, uk[i], t[i][0]));
+      t[i][1] = fmaf(ca.w, uh[i], fmaf(ca.z, uk[i], t[i][1]));
+      t[i][2] = fmaf(cb.y, uh[i], fmaf(cb.x, uk[i], t[i][2]));
+      t[i][3] = fmaf(cb.w, uh[i], fmaf(cb.z, uk[i], t[i][3]));
+      const float wm = w[m];
+      y0 = fmaf(wm, t[i][0], y0);
+      y1 = fmaf(wm, t[i][1], y1);
+      y2 = fmaf(wm, t[i][2], y2);
+      y3 = fmaf(wm, t[i][3], y3);
+    }
+  }
+  {
+    float *ys = y_s + (size_t)(gy * 4) * TH + cl;
+    ys[0] = y0;
+    ys[TH] = y1;
+    ys[2 * TH] = y2;
+    ys[3 * TH] = y3;
+  }
+  __syncthreads();
+  for (int q = ch; q < 4; q += P) {
+    float v = y_s[(size_t)((g * P) * 4 + q) * TH + cl];
+    for (int k = 1; k < P; k++) v += y_s[(size_t)((g * P + k) * 4 + q) * TH + cl];
+    yr_s[(size_t)(g * 4 + q) * TH + cl] = v;
+  }
+  __syncthreads();
+  if (active)
+    for (int q = ch; q < 4; q += P) {
+      const float *M = Mp + (size_t)tau * G4 * G4 + (size_t)(g * 4 + q) * G4;
+      float v = 0.f;
+      for (int k = 0; k < G4; k++) v = fmaf(M[k], yr_s[(size_t)k * TH + cl], v);
+      s_s[(size_t)(g * 4 + q) * TH + cl] = v;
+    }
+  __syncthreads();
+  float e2 = 0.f;
+  if (active) {
+    const float s0 = s_s[(size_t)(g * 4 + 0) * TH + cl], s1 = s_s[(size_t)(g * 4 + 1) * TH + cl];
+    const float s2 = s_s[(size_t)(g * 4 + 2) * TH + cl], s3 = s_s[(size_t)(g * 4 + 3) * TH + cl];
+#pragma unroll
+    for (int i = 0; i < NP; i++) {
+      const float4 *L4 = reinterpret_cast<const float4 *>(Linv + (tb + g * N + m0 + i) * 16);
+#pragma unroll
+      for (int p = 0; p < 4; p++) {
+        const float4 L = L4[p];
+        const float o = fmaf(L.w, s3, fmaf(L.z, s2, fmaf(L.y, s1, fmaf(L.x, s0, t[i][p]))));
+        const float d = o - old[i][p];
+        e2 = fmaf(d, d, e2);
+        db[(i * 4 + p) * T] = o;
+      }
+    }
+  }
+  return e2;
+}
+
+template <int T, int NP>
+__global__ void __launch_bounds__(256) k_mx_rb(int J, int N, int G, int n_types, int stage,
+                                               const int32_t *__restrict__ type, const float *Linv_g,
+                                               const float *Cin_g, const float *Mp_g, const float *w_g,
+                                               const float *__restrict__ z, float *D, DevState *ds,
+                                               double *__restrict__ partials, unsigned *gbar, double *e_hist,
+                                               cudaGraphConditionalHandle cond, int use_cond, int max_sweeps) {
+  extern __shared__ __align__(16) float smr[];
+  __shared__ double red[8];
+  __shared__ DevState sd;
+  __shared__ int s_ok;
+  constexpr int TH = T / 2;
+  const int P = N / NP, G4 = 4 * G;
+  const int cl = threadIdx.x, gy = threadIdx.y;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int nthr = blockDim.x * blockDim.y;
+  if (tid == 0) sd = *ds;
+  __syncthreads();
+  if (sd.done) return;  // uniform across the grid
+  float *y_s = smr;
+  float *yr_s = y_s + (size_t)G * P * 4 * TH;
+  float *s_s = yr_s + (size_t)G4 * TH;
+  const float *Linv = Linv_g, *Cin = Cin_g, *Mp = Mp_g, *w = w_g;
+  if (stage) {
+    stage_tables(s_s + (size_t)G4 * TH, n_types, N, G, tid, nthr, Linv, Cin, Mp, w);
+    __syncthreads();
+  }
+  const int ntiles = (J + T - 1) / T;
+  bool failed = false;
+  for (int sw = 0;; sw++) {
+    const bool zero = sd.refine || sd.blk_i == 0;
+    float e2 = 0.f;
+    for (int color = 0; color < 2 && !failed; color++) {
+      for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
+        e2 += rb_tile<T, NP>(tile, color, J, N, G, cl, gy, zero, type, Linv, Cin, Mp, w, z, D, y_s, yr_s, s_s);
+      if (color == 0) {  // every red cell is written before any black cell reads it
+        __syncthreads();
+        if (tid == 0) s_ok = grid_barrier(gbar, gridDim.x);
+        __syncthreads();
+        if (!s_ok) failed = true;
+      }
+    }
+    if (failed) break;
+    const double bs = block_reduce_fixed(e2, red, tid, nthr);
+    double *part = partials + (size_t)(sw & 1) * gridDim.x;
+    if (tid == 0) {
+      part[blockIdx.x] = bs;
+      s_ok = grid_barrier(gbar, gridDim.x);
+    }
+    __syncthreads();
+    if (!s_ok) {
+      failed = true;
+      break;
+    }
+    const double tot = block_sum_fixed(part, gridDim.x, red);
+    if (tid == 0) finish_mixed(&sd, blockIdx.x == 0 ? e_hist : nullptr, sqrt(tot), cond, 0);
+    __syncthreads();
+    if (sd.done || sd.refine || sw + 1 >= max_sweeps) break;  // uniform
+  }
+  if (blockIdx.x == 0 && tid == 0) {
+    if (failed) {
+      sd.status = OCI_E_TIMEOUT;
+      sd.done = 1;
+      sd.refine = 0;
+    }
+    *ds = sd;
+    if (use_cond) {
+      if (sd.done) cudaGraphSetConditional(cond, 0);
+      if (sd.cond_ref) cudaGraphSetConditional((cudaGraphConditionalHandle)sd.cond_ref, sd.refine);
+    }
+  }
+}
+
+template <int T, int NP>
+static void launch_rb(Handle &h, int P, cudaGraphConditionalHandle cond, int use_cond, int max_sweeps) {
+  const bool stage = mx_tables_floats(h) * 4 <= 64 * 1024;
+  const size_t smem = mx_reg_smem(h.G, T / 2, P) + (stage ? mx_tables_floats(h) * 4 + 16 : 0);
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mx_rb<T, NP>, (T / 2) * h.G * P, smem);
+  const int ntiles = (h.J + T - 1) / T;
+  int grid = sms * (per > 0 ? per : 1);
+  if (grid > ntiles) grid = ntiles;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(T / 2, h.G * P);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = h.stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;  // blocks wait on one another (grid barriers)
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k_mx_rb<T, NP>, h.J, h.N, h.G, h.tt.n_types, (int)stage, (const int32_t *)h.type,
+                     (const float *)h.tt.Linv32, (const float *)h.tt.Cin32, (const float *)h.tt.Mp32,
+                     (const float *)h.w32, (const float *)h.z32, h.delta[0], h.ds, h.partials, h.gbar, h.e_hist,
+                     cond, use_cond, max_sweeps);
+}
+
 // ---------------------------------------------------------------- inner sweep, TMA-staged
 // The same FP32 inner sweep with the tile's operands brought in by the tensor
 // memory accelerator: per tile of kTmaCells cells, one 2D bulk tensor copy
@@ -1426,6 +1659,20 @@ int mx_partials(const Handle &h) {
 // One inner sweep including its norm reduction, stop rule and refinement
 // decision (fused into the last block).
 void launch_mx_inner(Handle &h, cudaGraphConditionalHandle cond, int use_cond) {
+  if (h.mx_kind == kMxRB) {  // always cooperative; one sweep per launch outside the graph
+    const int T = h.mx_cb, P = h.mx_P, np = h.N / P;
+    const int ms = use_cond ? (1 << 30) : 1;
+    if (T == 32) {
+      if (np == 2) launch_rb<32, 2>(h, P, cond, use_cond, ms);
+      else if (np == 4) launch_rb<32, 4>(h, P, cond, use_cond, ms);
+      else launch_rb<32, 8>(h, P, cond, use_cond, ms);
+    } else {
+      if (np == 2) launch_rb<64, 2>(h, P, cond, use_cond, ms);
+      else if (np == 4) launch_rb<64, 4>(h, P, cond, use_cond, ms);
+      else launch_rb<64, 8>(h, P, cond, use_cond, ms);
+    }
+    return;
+  }
   if (h.mx_kind == kMxTiledB) {
     const int T = h.mx_cb, P = h.mx_P, np = h.N / P;
     const bool stage = mx_tables_floats(h) * 4 <= 64 * 1024;
@@ -1575,7 +1822,10 @@ int mx_set_attributes() {
                       (const void *)k_mx_inner_tb<64, 8>, (const void *)k_mx_inner_ms<32, 2>,
                       (const void *)k_mx_inner_ms<32, 4>, (const void *)k_mx_inner_ms<32, 8>,
                       (const void *)k_mx_inner_ms<64, 2>, (const void *)k_mx_inner_ms<64, 4>,
-                      (const void *)k_mx_inner_ms<64, 8>};
+                      (const void *)k_mx_inner_ms<64, 8>, (const void *)k_mx_rb<32, 2>,
+                      (const void *)k_mx_rb<32, 4>, (const void *)k_mx_rb<32, 8>,
+                      (const void *)k_mx_rb<64, 2>, (const void *)k_mx_rb<64, 4>,
+                      (const void *)k_mx_rb<64, 8>};
   for (const void *k : ks) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(FP32 inner sweep)");
