@@ -237,3 +237,21 @@ def test_fp32_red_black_full_size_fewer_sweeps_same_answer():
         sa, sb = a.step(), b.step()
         assert abs(sb["iters"] - sa["iters"]) <= 2
         assert rel(b.phi(), a.phi()) < 1e-10
+
+
+@pytest.mark.parametrize("seed,J,N,G", [(81, 40, 128, 1), (82, 37, 8, 16), (83, 70, 32, 4)])
+@pytest.mark.parametrize("ordering", ["jacobi", "rb"])
+def test_fp32_ir_max_sizes(seed, J, N, G, ordering):
+    """The mixed form at the size limits (N = 128; G = 16; N*G = 128), in both
+    orderings: whichever inner kernels fit these shapes (per-type tables staged
+    in shared memory or read from global memory) give the oracle's answer."""
+    from oracle import RB
+    p = W.random_slab(seed, J, N, G).replace(tol=1e-10)
+    o = Oracle(p)
+    with oci.Solver(p, precision=oci.FP32_IR) as s:
+        if ordering == "rb":
+            s.set_ordering(oci.ORDER_RED_BLACK)
+        r = o.step(RB if ordering == "rb" else OCI)
+        st = s.step()
+        assert st["status"] == 0 and abs(st["iters"] - r["iters"]) <= 2, (st["iters"], r["iters"])
+        assert rel(s.phi(), r["phi"]) < 1e-9
