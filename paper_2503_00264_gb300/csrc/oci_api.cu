@@ -490,7 +490,7 @@ static void free_handle(Handle *h) {
                   h->tt.Cin, h->tt.Mp,  h->tt.Kap,    h->tt.dx,     h->tt.sig,       h->si_z,      h->si_uin,
                   h->LU,     h->piv,    h->partials,  h->bal_partials, h->bal,       h->e_hist,    h->ds,
                   h->stage,  h->delta[0], h->delta[1], h->z32, h->w32, h->tt.Lco, h->tt.Linv32, h->tt.Cin32,
-                  h->tt.Mp32, h->tc_img, h->si_maps, h->si_segin, h->counter, h->psi_user, h->gbar};
+                  h->tt.Mp32, h->tc_img, h->si_maps, h->si_segin, h->counter, h->psi_user, h->gbar, h->mu32};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (h->h_ds) cudaFreeHost(h->h_ds);
@@ -622,6 +622,9 @@ static int setup_impl(const oci_problem *p, oci_handle *h) {
     if ((rc = dev_upload(&h->tt.Cin32, C32.data(), C32.size(), s))) return rc;
     if ((rc = dev_upload(&h->tt.Mp32, M32.data(), M32.size(), s))) return rc;
     if ((rc = dev_upload(&h->w32, W32.data(), W32.size(), s))) return rc;
+    const std::vector<float> MU32 = to32(h->h_mu);
+    if ((rc = dev_upload(&h->mu32, MU32.data(), MU32.size(), s))) return rc;
+    CK(cudaStreamSynchronize(s));  // host vectors of the uploads go out of scope
     // FP32 correction arrays: room for both layouts ([R][Jp], and tile-major
     // with tiles of up to 64 cells)
     const size_t nPsi32 = (size_t)G * N * 4 * std::max<size_t>(Jp, (h->J + 63) / 64 * 64);
@@ -693,6 +696,8 @@ static int setup_impl(const oci_problem *p, oci_handle *h) {
 static void launch_mx_sweep(Handle &h, cudaGraphConditionalHandle cond, int use_cond) {
   if (h.precision == OCI_FP32_IR) {
     launch_mx_inner(h, cond, use_cond);  // norm and stop rule fused in
+  } else if (tc_pipe_ok(h)) {
+    launch_tc_pipe(h, cond, use_cond);  // persistent pipelined tensor-core sweep, norm fused in
   } else {
     launch_tc_inner(h);
     launch_mx_finalize(h, cond, use_cond);

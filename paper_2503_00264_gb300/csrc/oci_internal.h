@@ -94,6 +94,7 @@ struct Handle {
   float *delta[2] = {nullptr, nullptr};  // [G][N][4][Jp] correction ping-pong
   float *z32 = nullptr;                  // [G][N][4][Jp] L~^{-1} r of the last refinement
   float *w32 = nullptr;
+  float *mu32 = nullptr;           // mixed forms: FP32 copy of the ordinates
   int mx_kmax = 64;
   double mx_theta = 1e-3;
   CUtensorMap tm_z, tm_d[2];          // TMA descriptors of z32 and delta[0/1] ([R][Jp] FP32)
@@ -184,6 +185,8 @@ void mx_shape(const Handle &h, int &cb, int &P);
 size_t mx_tma_smem(const Handle &h, int P);
 // tensor-core block apply (TF32 / BF16x3 forms)
 int tc_prepare(Handle &h);
+bool tc_pipe_ok(const Handle &h);
+void launch_tc_pipe(Handle &h, cudaGraphConditionalHandle cond, int use_cond);
 int tc_partials(const Handle &h);
 void launch_tc_inner(Handle &h);
 int tc_build_images(Handle &h, const std::vector<double> &Ainv);
