@@ -297,6 +297,15 @@ static int autotune(Handle &h) {
   if (mx && h.tma_ok)
     for (int P : {1, 2, 4, 8})
       if (h.N % P == 0 && 64 * h.G * P <= 256 && mx_tma_smem(h, P) <= 200 * 1024) cands.push_back({kMxTma, 64, P});
+  if (!mx && h.ordering != OCI_ORDER_RED_BLACK)  // FP64 register form
+    for (int np : {2, 4, 8}) {
+      if (h.N % np) continue;
+      const int P = h.N / np;
+      for (int cb : {16, 32, 64}) {
+        const int thr = cb * h.G * P;
+        if (thr <= 256 && thr % 32 == 0 && thr >= 64) cands.push_back({kSweepReg64, cb, P});
+      }
+    }
   if (mx)
     for (int np : {2, 4, 8}) {
       if (h.N % np) continue;
@@ -327,6 +336,15 @@ static int autotune(Handle &h) {
       if (c.kind == want) keep.push_back(c);
     if (!keep.empty()) cands.swap(keep);
   }
+  // OCI_SWEEP_REG=0|1 restricts the FP64 Jacobi sweep to the staged / register form
+  const char *sreg = getenv("OCI_SWEEP_REG");
+  if (!mx && sreg) {
+    const int want = sreg[0] == '1' ? kSweepReg64 : kMxPlain;
+    std::vector<Cand> keep;
+    for (auto &c : cands)
+      if (c.kind == want) keep.push_back(c);
+    if (!keep.empty()) cands.swap(keep);
+  }
   // OCI_SWEEP_SHAPE="cb,P" keeps one legal shape (the first of the remaining
   // candidates with that shape) without timing, so a profiler sees no tuning launches
   const char *shape = getenv("OCI_SWEEP_SHAPE");
@@ -348,6 +366,7 @@ static int autotune(Handle &h) {
     } else {
       h.tune_cb = c.cb;
       h.tune_P = c.P;
+      h.tune_reg = c.kind == kSweepReg64;
     }
   };
   if (cands.size() < 2) {

@@ -135,6 +135,7 @@ struct Handle {
   int last_iters = 0;
   bool no_graph = false;           // OCI_NO_GRAPH=1: host-driven loop instead of the WHILE graph
   int tune_cb = 0, tune_P = 0;     // sweep launch shape picked by the autotuner (0: default)
+  bool tune_reg = false;           // FP64 Jacobi sweep in the register form (k_oci_sweep_reg)
   int mx_cb = 0, mx_P = 0;         // same for the FP32 inner sweep of the mixed form
   double tune_us = 0.0;            // measured sweep time of the chosen shape
 };
@@ -177,10 +178,13 @@ int mx_tma_setup(Handle &h);
 // colour) keep the FP32 correction arrays tile-major
 // ([J/T][4NG][T], T = mx_cb)
 constexpr int kMxPlain = 0, kMxTma = 1, kMxReg = 3, kMxTiled = 4, kMxTiledP = 5, kMxTiledB = 6, kMxRB = 7;
+constexpr int kSweepReg64 = 8;  // autotuner candidate kind of the FP64 register sweep
 size_t mx_tb_smem(const Handle &h, int T, int P, bool stage);
 size_t mx_tables_floats(const Handle &h);
 int mx_tile_shift(const Handle &h);
 int mx_set_attributes();
+size_t sweep_reg_smem(int G, int cb, int P);
+const void *k_oci_sweep_reg_ptr(int np);
 void mx_shape(const Handle &h, int &cb, int &P);
 size_t mx_tma_smem(const Handle &h, int P);
 // tensor-core block apply (TF32 / BF16x3 forms)

@@ -232,7 +232,147 @@ void launch_step_const(Handle &h) {
 }
 
 // One sweep including its norm reduction and stop rule (fused into the last block).
+
+// ---------------------------------------------------------------- register form (FP64)
+// The same FP64 sweep with the N angles of a cell split over P = N/NP threads,
+// each keeping its NP angles' t = tc + Cin u in registers: no per-angle staging
+// in shared memory, so problems with many unknowns per cell (large N*G) keep
+// more warps resident.  The angle sum y is reduced over the chunks in a fixed
+// order and s = Mp y is split over the chunk threads of each group.  Jacobi
+// ordering; the norm and stop rule are fused into the last block.
+template <int NP>
+__global__ void __launch_bounds__(256) k_oci_sweep_reg(
+    int J, int Jp, int N, int G, const int32_t *__restrict__ type, const double *__restrict__ Linv,
+    const double *__restrict__ Cin, const double *__restrict__ Mp, const double *__restrict__ w,
+    const double *__restrict__ inc, const double *__restrict__ tc, double *Psi0, double *Psi1, DevState *ds,
+    double *__restrict__ partials, unsigned *counter, double *e_hist, cudaGraphConditionalHandle cond, int use_cond) {
+  extern __shared__ double smrd[];
+  __shared__ double red[8];
+  __shared__ bool s_last;
+  const int CB = blockDim.x, P = N / NP, G4 = 4 * G;
+  const int cl = threadIdx.x, gy = threadIdx.y;
+  const int g = gy / P, ch = gy % P, m0 = ch * NP;
+  const int j = blockIdx.x * CB + cl;
+  const int tid = threadIdx.y * CB + threadIdx.x;
+  const int nthr = CB * blockDim.y;
+  if (ds->done) return;  // uniform across the grid
+  const int cur = ds->cur;
+  const double *__restrict__ Pin = cur ? Psi1 : Psi0;
+  double *__restrict__ Pout = cur ? Psi0 : Psi1;
+  double *y_s = smrd;                           // [G*P*4][CB]
+  double *yr_s = y_s + (size_t)G * P * 4 * CB;  // [4G][CB]
+  double *s_s = yr_s + (size_t)G4 * CB;         // [4G][CB]
+  const bool active = j < J;
+  const int tau = active ? type[j] : 0;
+  const int N2 = N / 2;
+  const size_t tb = (size_t)tau * G * N;
+  double t[NP][4];
+  double y0 = 0.0, y1 = 0.0, y2 = 0.0, y3 = 0.0;
+  if (active) {
+#pragma unroll
+    for (int i = 0; i < NP; i++) {
+      const int m = m0 + i;
+      const int gm = g * N + m;
+      const size_t base = (size_t)gm * 4 * Jp + j;
+      double uk, uh;
+      if (m >= N2) {
+        if (j > 0) {
+          uk = Pin[base + (size_t)Jp - 1];
+          uh = Pin[base + 3 * (size_t)Jp - 1];
+        } else {
+          uk = inc[gm * 2 + 0];
+          uh = inc[gm * 2 + 1];
+        }
+      } else if (j < J - 1) {
+        uk = Pin[base + 1];
+        uh = Pin[base + 2 * (size_t)Jp + 1];
+      } else {
+        uk = inc[(G * N + gm) * 2 + 0];
+        uh = inc[(G * N + gm) * 2 + 1];
+      }
+      const double *C = Cin + (tb + gm) * 8;
+#pragma unroll
+      for (int p = 0; p < 4; p++) t[i][p] = fma(C[2 * p + 1], uh, fma(C[2 * p], uk, tc[base + (size_t)p * Jp]));
+      const double wm = w[m];
+      y0 = fma(wm, t[i][0], y0);
+      y1 = fma(wm, t[i][1], y1);
+      y2 = fma(wm, t[i][2], y2);
+      y3 = fma(wm, t[i][3], y3);
+    }
+  }
+  {
+    double *ys = y_s + (size_t)(gy * 4) * CB + cl;
+    ys[0] = y0;
+    ys[CB] = y1;
+    ys[2 * CB] = y2;
+    ys[3 * CB] = y3;
+  }
+  __syncthreads();
+  for (int q = ch; q < 4; q += P) {  // y_{g,q}: fixed-order sum over the group's chunks
+    double v = y_s[(size_t)((g * P) * 4 + q) * CB + cl];
+    for (int k = 1; k < P; k++) v += y_s[(size_t)((g * P + k) * 4 + q) * CB + cl];
+    yr_s[(size_t)(g * 4 + q) * CB + cl] = v;
+  }
+  __syncthreads();
+  if (active)
+    for (int q = ch; q < 4; q += P) {  // s_{g,q} = sum_k Mp[g*4+q][k] y_k
+      const double *M = Mp + (size_t)tau * G4 * G4 + (size_t)(g * 4 + q) * G4;
+      double v = 0.0;
+      for (int k = 0; k < G4; k++) v = fma(M[k], yr_s[(size_t)k * CB + cl], v);
+      s_s[(size_t)(g * 4 + q) * CB + cl] = v;
+    }
+  __syncthreads();
+  double e2 = 0.0;
+  if (active) {
+    const double s0 = s_s[(size_t)(g * 4 + 0) * CB + cl], s1 = s_s[(size_t)(g * 4 + 1) * CB + cl];
+    const double s2 = s_s[(size_t)(g * 4 + 2) * CB + cl], s3 = s_s[(size_t)(g * 4 + 3) * CB + cl];
+#pragma unroll
+    for (int i = 0; i < NP; i++) {
+      const int gm = g * N + m0 + i;
+      const size_t base = (size_t)gm * 4 * Jp + j;
+      const double *L = Linv + (tb + gm) * 16;
+#pragma unroll
+      for (int p = 0; p < 4; p++) {
+        const double o = fma(L[p * 4 + 3], s3, fma(L[p * 4 + 2], s2, fma(L[p * 4 + 1], s1, fma(L[p * 4 + 0], s0, t[i][p]))));
+        const double d = o - Pin[base + (size_t)p * Jp];
+        e2 = fma(d, d, e2);
+        Pout[base + (size_t)p * Jp] = o;
+      }
+    }
+  }
+  const double bs = block_sum(e2, red);
+  if (publish_partial(partials, blockIdx.x, bs, counter, gridDim.x, &s_last)) {
+    const double tot = block_sum_fixed(partials, gridDim.x, red);
+    if (tid == 0) {
+      *counter = 0;
+      finish_fp64(ds, e_hist, sqrt(tot), cond, use_cond);
+    }
+  }
+  (void)nthr;
+}
+
+size_t sweep_reg_smem(int G, int cb, int P) { return (size_t)cb * ((size_t)G * P * 4 + 8 * (size_t)G) * 8; }
+
+const void *k_oci_sweep_reg_ptr(int np) {
+  return np == 2 ? (const void *)k_oci_sweep_reg<2> : np == 4 ? (const void *)k_oci_sweep_reg<4>
+                                                               : (const void *)k_oci_sweep_reg<8>;
+}
+
 void launch_oci_sweep(Handle &h, cudaGraphConditionalHandle cond, int use_cond) {
+  if (h.tune_reg && h.ordering != OCI_ORDER_RED_BLACK) {  // register form (Jacobi)
+    const int cb = h.tune_cb, P = h.tune_P, np = h.N / P;
+    const dim3 block(cb, h.G * P), grid((h.J + cb - 1) / cb);
+    const size_t smem = sweep_reg_smem(h.G, cb, P);
+#define OCI_SWEEP_REG(NP)                                                                                        \
+  k_oci_sweep_reg<NP><<<grid, block, smem, h.stream>>>(h.J, h.Jp, h.N, h.G, h.type, h.tt.Linv, h.tt.Cin, h.tt.Mp, \
+                                                       h.w, h.inc, h.tc, h.Psi[0], h.Psi[1], h.ds, h.partials,   \
+                                                       h.counter, h.e_hist, cond, use_cond)
+    if (np == 2) OCI_SWEEP_REG(2);
+    else if (np == 4) OCI_SWEEP_REG(4);
+    else OCI_SWEEP_REG(8);
+#undef OCI_SWEEP_REG
+    return;
+  }
   SweepCfg c = sweep_config(h);
   dim3 block(c.cells_per_block, h.G * c.chunks);
   if (h.ordering == OCI_ORDER_RED_BLACK) {

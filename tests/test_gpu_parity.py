@@ -264,3 +264,17 @@ def test_scan_si_full_size_matches_sequential():
         sa, sb = a.si_step(), b.si_step()
         assert sa["iters"] == sb["iters"]
         assert rel(b.phi(), a.phi()) < 1e-12
+
+
+@pytest.mark.parametrize("seed,J,N,G,shape", [(91, 77, 16, 1, None), (92, 130, 8, 8, None), (93, 1, 4, 2, None),
+                                              (94, 300, 16, 4, "16,2"), (95, 129, 16, 1, "64,2"),
+                                              (96, 95, 32, 2, "32,4")])
+def test_fp64_register_sweep_matches_oracle(seed, J, N, G, shape, monkeypatch):
+    """FP64 sweep with the angles of a cell split over threads and t kept in
+    registers (the autotuner's candidate for large N*G): same sweep counts as
+    the oracle, flux within 1e-12."""
+    monkeypatch.setenv("OCI_SWEEP_REG", "1")
+    if shape:
+        monkeypatch.setenv("OCI_SWEEP_SHAPE", shape)
+    p = W.random_slab(seed, J, N, G).replace(tol=1e-11)
+    compare_steps(p, 2)
