@@ -310,9 +310,13 @@ static int autotune(Handle &h) {
     for (int np : {2, 4, 8}) {
       if (h.N % np) continue;
       const int P = h.N / np;
-      for (int cb : {32, 64, 128}) {
+      for (int cb : {16, 32, 64, 128}) {
         const int thr = cb * h.G * P;
-        if (thr <= 256 && thr % 32 == 0) cands.push_back({kMxReg, cb, P});
+        if (thr <= 256 && thr % 32 == 0 && thr >= 64) cands.push_back({kMxReg, cb, P});
+        if (cb == 16) {  // 16-cell tiles: persistent forms with 8 angles per thread only
+          if (np == 8 && thr <= 256 && thr % 32 == 0 && thr >= 64) cands.push_back({kMxTiledP, cb, P});
+          continue;
+        }
         if (thr <= 256 && cb <= 64) {
           cands.push_back({kMxTiled, cb, P});
           cands.push_back({kMxTiledP, cb, P});

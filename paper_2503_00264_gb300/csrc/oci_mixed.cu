@@ -42,7 +42,7 @@ __device__ __forceinline__ size_t fidx(int tsh, int R, size_t Jp, int r, int j) 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 int mx_tile_shift(const Handle &h) {
-  const int sh = h.mx_cb == 32 ? 5 : 6;
+  const int sh = h.mx_cb == 16 ? 4 : h.mx_cb == 32 ? 5 : 6;
   if (h.mx_kind == kMxTiled || h.mx_kind == kMxTiledP || h.mx_kind == kMxTiledB) return sh;
   if (h.mx_kind == kMxRB) return sh | 0x100;
   return 0;
@@ -1698,7 +1698,9 @@ void launch_mx_inner(Handle &h, cudaGraphConditionalHandle cond, int use_cond) {
     const int T = h.mx_cb, P = h.mx_P, np = h.N / P;
     const bool stage = mx_tables_floats(h) * 4 <= 64 * 1024;
     const size_t smem = mx_tp_smem(h, T, P, stage);
-    if (T == 32) {
+    if (T == 16) {
+      launch_ms<16, 8>(h, P, smem, stage, cond);
+    } else if (T == 32) {
       if (np == 2) launch_ms<32, 2>(h, P, smem, stage, cond);
       else if (np == 4) launch_ms<32, 4>(h, P, smem, stage, cond);
       else launch_ms<32, 8>(h, P, smem, stage, cond);
@@ -1718,7 +1720,9 @@ void launch_mx_inner(Handle &h, cudaGraphConditionalHandle cond, int use_cond) {
   k_mx_inner_tp<TT, NP><<<tp_grid<TT, NP>(h, P, smem), block, smem, h.stream>>>(                                 \
       h.J, h.N, h.G, h.tt.n_types, stage, h.type, h.tt.Linv32, h.tt.Cin32, h.tt.Mp32, h.w32, h.z32, h.delta[0], \
       h.delta[1], h.ds, h.partials, h.counter, h.e_hist, cond, use_cond)
-    if (T == 32) {
+    if (T == 16) {
+      OCI_MX_TP(16, 8);
+    } else if (T == 32) {
       if (np == 2) OCI_MX_TP(32, 2);
       else if (np == 4) OCI_MX_TP(32, 4);
       else OCI_MX_TP(32, 8);
@@ -1813,7 +1817,8 @@ const void *k_mx_inner_ptr() { return (const void *)k_mx_inner; }
 
 // Dynamic shared memory limits of the FP32 inner kernels above 48 KB (set once at setup).
 int mx_set_attributes() {
-  const void *ks[] = {(const void *)k_mx_inner,          (const void *)k_mx_inner_tp<32, 2>,
+  const void *ks[] = {(const void *)k_mx_inner,          (const void *)k_mx_inner_tp<16, 8>,
+                      (const void *)k_mx_inner_ms<16, 8>, (const void *)k_mx_inner_tp<32, 2>,
                       (const void *)k_mx_inner_tp<32, 4>, (const void *)k_mx_inner_tp<32, 8>,
                       (const void *)k_mx_inner_tp<64, 2>, (const void *)k_mx_inner_tp<64, 4>,
                       (const void *)k_mx_inner_tp<64, 8>, (const void *)k_mx_inner_tb<32, 2>,

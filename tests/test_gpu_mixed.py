@@ -255,3 +255,22 @@ def test_fp32_ir_max_sizes(seed, J, N, G, ordering):
         st = s.step()
         assert st["status"] == 0 and abs(st["iters"] - r["iters"]) <= 2, (st["iters"], r["iters"])
         assert rel(s.phi(), r["phi"]) < 1e-9
+
+
+@pytest.mark.parametrize("kernel,kind", [("tiledp", 5), ("reg", 3)])
+def test_fp32_multigroup_16_cell_tiles_match_oracle(kernel, kind, monkeypatch):
+    """G = 8, S16: the FP32 inner sweeps with 16-cell tiles (8 angles per thread,
+    2 chunks x 8 groups x 16 cells = 256 threads), which the autotuner offers
+    for many groups, against the oracle (ragged J: a partial last tile)."""
+    monkeypatch.setenv("OCI_MX_INNER", kernel)
+    monkeypatch.setenv("OCI_SWEEP_SHAPE", "16,2")
+    p = W.random_slab(101, 203, 16, 8).replace(tol=1e-10)
+    o = Oracle(p)
+    with oci.Solver(p, precision=oci.FP32_IR) as s:
+        info = s.info()
+        assert (info["inner_kernel"], info["cells_per_block"], info["angle_chunks"]) == (kind, 16, 2)
+        for k in range(2):
+            r = o.step(OCI)
+            st = s.step()
+            assert st["status"] == 0 and abs(st["iters"] - r["iters"]) <= 2
+            assert rel(s.phi(), r["phi"]) < 1e-10
