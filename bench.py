@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--no-si", action="store_true")
     ap.add_argument("--no-multigroup", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-design-cmp", action="store_true")
     ap.add_argument("--batch-max-iter", type=int, default=600)
     return ap.parse_args()
 
@@ -204,6 +205,7 @@ def run_ours(args):
     # starting state of the timed region, replayed by the end-to-end leg below
     start_pp, start_t = s.state()
     start_psi = s.psi()
+    s_start_state, s_start_psi = (start_pp, start_t), start_psi
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clk = Clocks(local)
     barrier()
@@ -308,6 +310,27 @@ def run_ours(args):
             best_si = min(row[k]["s_per_step"] for k in ("si_fp64", "si_scan_fp64"))
             row["best_oci_speedup_vs_best_si"] = best_si / best_oci
             si_cmp.append(row)
+
+    # the paper's cell solve (dense per-cell LU factors applied every sweep, here as
+    # our own warp-per-cell kernel) against the structured exact solve, same workload
+    design_cmp = None
+    if not args.no_design_cmp:
+        design_cmp = {}
+        for name, solver in (("dense_lu_fp64", oci.SOLVER_DENSE_LU), ("structured_fp64", oci.SOLVER_STRUCTURED)):
+            with oci.Solver(p, solver=solver, stream=stream.cuda_stream) as sv:
+                sv.set_state(*s_start_state)
+                sv.set_psi(s_start_psi)
+                t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                t0e.record(stream)
+                st_d = sv.step()
+                t1e.record(stream)
+                torch.cuda.synchronize()
+                ms_d = t0e.elapsed_time(t1e)
+                design_cmp[name] = {"ms_per_step": ms_d, "sweeps": st_d["iters"],
+                                    "us_per_sweep": 1e3 * ms_d / max(st_d["iters"], 1),
+                                    "value": p.unknowns * st_d["iters"] / (ms_d * 1e-3), "unit": UNIT}
+        design_cmp["structured_speedup"] = (design_cmp["dense_lu_fp64"]["us_per_sweep"]
+                                            / design_cmp["structured_fp64"]["us_per_sweep"])
 
     # multigroup slab (G = 8, S16, 2^16 cells): FP64 and the FP32-inner mixed form
     multigroup = None
@@ -441,7 +464,8 @@ def run_ours(args):
             "precision_forms": mixed,
             "si_comparison": si_cmp,
             "multigroup": multigroup,
-            "batched_form": batched}
+            "batched_form": batched,
+            "paper_scheme_comparison": design_cmp}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args)
     if rank == 0:
