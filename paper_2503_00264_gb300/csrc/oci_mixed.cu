@@ -595,6 +595,148 @@ __device__ __forceinline__ float tiled_tile(int tile, int J, int N, int G, int c
   return e2;
 }
 
+// The tiled tile split in two for software pipelining across a block's tiles:
+// tiled_load issues every global load of a tile into registers, tiled_compute
+// does the rest (three block barriers, stores, the thread's squared change).
+template <int NP>
+struct TileRegs {
+  float t[NP][4], old[NP][4], uk[NP], uh[NP];
+  int tau;
+  bool active;
+};
+
+template <int T, int NP>
+__device__ __forceinline__ void tiled_load(TileRegs<NP> &r, int tile, int J, int N, int G, int cl, int gy, bool zero,
+                                           const int32_t *__restrict__ type, const float *__restrict__ z,
+                                           const float *__restrict__ Din) {
+  const int P = N / NP, R = 4 * N * G;
+  const int g = gy / P, ch = gy % P, m0 = ch * NP;
+  const int N2 = N / 2;
+  const long long offL = cl > 0 ? -1 : (T - 1) - (long long)R * T;
+  const long long offR = cl < T - 1 ? 1 : (long long)R * T - (T - 1);
+  const int j = tile * T + cl;
+  r.active = j < J;
+  r.tau = r.active ? type[j] : 0;
+  const size_t off = ((size_t)tile * R + (size_t)(g * N + m0) * 4) * T + cl;
+  const float *__restrict__ zb = z + off;
+  const float *__restrict__ db = Din + off;
+#pragma unroll
+  for (int i = 0; i < NP; i++) {
+    const int m = m0 + i;
+#pragma unroll
+    for (int p = 0; p < 4; p++) {
+      r.t[i][p] = r.active ? zb[(i * 4 + p) * T] : 0.f;
+      r.old[i][p] = (r.active && !zero) ? db[(i * 4 + p) * T] : 0.f;
+    }
+    r.uk[i] = 0.f;
+    r.uh[i] = 0.f;
+    if (r.active && !zero) {
+      if (m >= N2) {
+        if (j > 0) {
+          r.uk[i] = db[offL + (i * 4 + 1) * T];
+          r.uh[i] = db[offL + (i * 4 + 3) * T];
+        }
+      } else if (j < J - 1) {
+        r.uk[i] = db[offR + (i * 4 + 0) * T];
+        r.uh[i] = db[offR + (i * 4 + 2) * T];
+      }
+    }
+  }
+}
+
+template <int T, int NP>
+__device__ __forceinline__ float tiled_compute(TileRegs<NP> &r, int tile, int N, int G, int cl, int gy,
+                                               const float *Linv, const float *Cin, const float *Mp, const float *w,
+                                               float *__restrict__ Dout, float *y_s, float *yr_s, float *s_s) {
+  const int P = N / NP, G4 = 4 * G, R = 4 * N * G;
+  const int g = gy / P, ch = gy % P, m0 = ch * NP;
+  const size_t tb = (size_t)r.tau * G * N;
+  float y0 = 0.f, y1 = 0.f, y2 = 0.f, y3 = 0.f;
+  if (r.active) {
+#pragma unroll
+    for (int i = 0; i < NP; i++) {
+      const int m = m0 + i;
+      const float4 *C4 = reinterpret_cast<const float4 *>(Cin + (tb + g * N + m) * 8);
+      const float4 ca = C4[0], cb = C4[1];
+      r.t[i][0] = fmaf(ca.y, r.uh[i], fmaf(ca.x, r.uk[i], r.t[i][0]));
+      r.t[i][1] = fmaf(ca.w, r.uh[i], fmaf(ca.z, r.uk[i], r.t[i][1]));
+      r.t[i][2] = fmaf(cb.y, r.uh[i], fmaf(cb.x, r.uk[i], r.t[i][2]));
+      r.t[i][3] = fmaf(cb.w, r.uh[i], fmaf(cb.z, r.uk[i], r.t[i][3]));
+      const float wm = w[m];
+      y0 = fmaf(wm, r.t[i][0], y0);
+      y1 = fmaf(wm, r.t[i][1], y1);
+      y2 = fmaf(wm, r.t[i][2], y2);
+      y3 = fmaf(wm, r.t[i][3], y3);
+    }
+  }
+  {
+    float *ys = y_s + (size_t)(gy * 4) * T + cl;
+    ys[0] = y0;
+    ys[T] = y1;
+    ys[2 * T] = y2;
+    ys[3 * T] = y3;
+  }
+  __syncthreads();
+  for (int q = ch; q < 4; q += P) {
+    float v = y_s[(size_t)((g * P) * 4 + q) * T + cl];
+    for (int k = 1; k < P; k++) v += y_s[(size_t)((g * P + k) * 4 + q) * T + cl];
+    yr_s[(size_t)(g * 4 + q) * T + cl] = v;
+  }
+  __syncthreads();
+  if (r.active)
+    for (int q = ch; q < 4; q += P) {
+      const float *M = Mp + (size_t)r.tau * G4 * G4 + (size_t)(g * 4 + q) * G4;
+      float v = 0.f;
+      for (int k = 0; k < G4; k++) v = fmaf(M[k], yr_s[(size_t)k * T + cl], v);
+      s_s[(size_t)(g * 4 + q) * T + cl] = v;
+    }
+  __syncthreads();
+  float e2 = 0.f;
+  if (r.active) {
+    const float s0 = s_s[(size_t)(g * 4 + 0) * T + cl], s1 = s_s[(size_t)(g * 4 + 1) * T + cl];
+    const float s2 = s_s[(size_t)(g * 4 + 2) * T + cl], s3 = s_s[(size_t)(g * 4 + 3) * T + cl];
+    float *ob = Dout + ((size_t)tile * R + (size_t)(g * N + m0) * 4) * T + cl;
+#pragma unroll
+    for (int i = 0; i < NP; i++) {
+      const float4 *L4 = reinterpret_cast<const float4 *>(Linv + (tb + g * N + m0 + i) * 16);
+#pragma unroll
+      for (int p = 0; p < 4; p++) {
+        const float4 L = L4[p];
+        const float o = fmaf(L.w, s3, fmaf(L.z, s2, fmaf(L.y, s1, fmaf(L.x, s0, r.t[i][p]))));
+        const float d = o - r.old[i][p];
+        e2 = fmaf(d, d, e2);
+        ob[(i * 4 + p) * T] = o;
+      }
+    }
+  }
+  return e2;
+}
+
+// A block's tiles of one sweep with the loads of tile k+1 issued before tile k
+// is computed (the input buffer is read-only within a sweep).
+template <int T, int NP>
+__device__ __forceinline__ float tiled_sweep_pf(int J, int N, int G, int cl, int gy, bool zero,
+                                                const int32_t *__restrict__ type, const float *Linv, const float *Cin,
+                                                const float *Mp, const float *w, const float *__restrict__ z,
+                                                const float *__restrict__ Din, float *__restrict__ Dout, float *y_s,
+                                                float *yr_s, float *s_s) {
+  const int ntiles = (J + T - 1) / T;
+  float e2 = 0.f;
+  int tile = blockIdx.x;
+  if (tile >= ntiles) return e2;
+  TileRegs<NP> a, b;
+  tiled_load<T, NP>(a, tile, J, N, G, cl, gy, zero, type, z, Din);
+  for (;;) {
+    const int nxt = tile + gridDim.x;
+    if (nxt < ntiles) tiled_load<T, NP>(b, nxt, J, N, G, cl, gy, zero, type, z, Din);
+    e2 += tiled_compute<T, NP>(a, tile, N, G, cl, gy, Linv, Cin, Mp, w, Dout, y_s, yr_s, s_s);
+    if (nxt >= ntiles) break;
+    tile = nxt;
+    a = b;
+  }
+  return e2;
+}
+
 // Fixed-order block sum of per-thread values (the result in thread 0).
 __device__ __forceinline__ double block_reduce_fixed(float e2, double *red, int tid, int nthr) {
   double v = (double)e2;
@@ -638,8 +780,11 @@ __global__ void __launch_bounds__(256) k_mx_inner_tp(int J, int N, int G, int n_
   }
   const int ntiles = (J + T - 1) / T;
   float e2 = 0.f;
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
-    e2 += tiled_tile<T, NP>(tile, J, N, G, cl, gy, zero, type, Linv, Cin, Mp, w, z, Din, Dout, y_s, yr_s, s_s);
+  if (NP <= 4)
+    e2 = tiled_sweep_pf<T, NP>(J, N, G, cl, gy, zero, type, Linv, Cin, Mp, w, z, Din, Dout, y_s, yr_s, s_s);
+  else
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
+      e2 += tiled_tile<T, NP>(tile, J, N, G, cl, gy, zero, type, Linv, Cin, Mp, w, z, Din, Dout, y_s, yr_s, s_s);
   const double bs = block_reduce_fixed(e2, red, tid, nthr);
   if (publish_partial(partials, blockIdx.x, bs, counter, gridDim.x, &s_last)) {
     const double tot = block_sum_fixed(partials, gridDim.x, red);
@@ -718,8 +863,11 @@ __global__ void __launch_bounds__(256) k_mx_inner_ms(int J, int N, int G, int n_
     const float *__restrict__ Din = sd.dcur ? D1 : D0;
     float *__restrict__ Dout = sd.dcur ? D0 : D1;
     float e2 = 0.f;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
-      e2 += tiled_tile<T, NP>(tile, J, N, G, cl, gy, zero, type, Linv, Cin, Mp, w, z, Din, Dout, y_s, yr_s, s_s);
+    if (NP <= 4)
+      e2 = tiled_sweep_pf<T, NP>(J, N, G, cl, gy, zero, type, Linv, Cin, Mp, w, z, Din, Dout, y_s, yr_s, s_s);
+    else
+      for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
+        e2 += tiled_tile<T, NP>(tile, J, N, G, cl, gy, zero, type, Linv, Cin, Mp, w, z, Din, Dout, y_s, yr_s, s_s);
     const double bs = block_reduce_fixed(e2, red, tid, nthr);
     double *part = partials + (size_t)(sw & 1) * gridDim.x;
     if (tid == 0) {
