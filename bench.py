@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--no-multigroup", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-design-cmp", action="store_true")
+    ap.add_argument("--no-fourier", action="store_true")
     ap.add_argument("--batch-max-iter", type=int, default=600)
     return ap.parse_args()
 
@@ -332,6 +333,24 @@ def run_ours(args):
         design_cmp["structured_speedup"] = (design_cmp["dense_lu_fp64"]["us_per_sweep"]
                                             / design_cmp["structured_fp64"]["us_per_sweep"])
 
+    # Fourier analysis on the GPU (oci_fourier_rho): rho_OCI and rho_SI of the bench
+    # workload's three regions at the mean free times of the SI comparison, and a
+    # Table-1-shaped grid (c = 1, S8) with its wall time
+    fourier = None
+    if not args.no_fourier:
+        deltas = np.array([0.01, 0.1, 1.0])
+        fourier = {"regions_delta": deltas.tolist(), "c": args.c, "N": p.N, "n_theta": 250, "rho": {}}
+        for tau in (0.01, 0.1):
+            fourier["rho"][str(tau)] = {
+                "oci": oci.fourier_rho(oci.FOURIER_OCI, p.N, deltas, tau, args.c, 250, stream.cuda_stream).tolist(),
+                "si": oci.fourier_rho(oci.FOURIER_SI, p.N, deltas, tau, args.c, 250, stream.cuda_stream).tolist()}
+        tg, dg = np.meshgrid([0.01, 0.1, 1.0, 10.0, np.inf], [0.01, 0.1, 1.0, 10.0], indexing="ij")
+        w0 = time.perf_counter()
+        rho_grid = oci.fourier_rho(oci.FOURIER_OCI, 8, dg.ravel(), tg.ravel(), 1.0, 1001, stream.cuda_stream)
+        fourier["table1_grid_c1_s8"] = {"tau": [0.01, 0.1, 1.0, 10.0, "inf"], "delta": [0.01, 0.1, 1.0, 10.0],
+                                        "rho_oci": rho_grid.reshape(tg.shape).tolist(), "n_theta": 1001,
+                                        "seconds": time.perf_counter() - w0}
+
     # multigroup slab (G = 8, S16, 2^16 cells): FP64 and the FP32-inner mixed form
     multigroup = None
     if not args.no_multigroup:
@@ -465,7 +484,8 @@ def run_ours(args):
             "si_comparison": si_cmp,
             "multigroup": multigroup,
             "batched_form": batched,
-            "paper_scheme_comparison": design_cmp}
+            "paper_scheme_comparison": design_cmp,
+            "fourier": fourier}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args)
     if rank == 0:

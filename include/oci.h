@@ -300,6 +300,27 @@ void oci_destroy(oci_handle *h);
 /* Message of the last failure on the calling thread ("" if none). */
 const char *oci_last_error(void);
 
+/* Fourier (von Neumann) analysis of the iterations (Sec. 2.3), batched on the
+ * GPU.  Model problem: infinite homogeneous medium, one group, Sigma_t = v = 1,
+ * so case i has cell optical thickness delta[i] (= dx), mean free time tau[i]
+ * (= dt; +inf: steady state) and scattering ratio c[i] (= Sigma_s).
+ * rho[i] = max over theta_k = 2 pi k / (n_theta - 1), k = 0 .. n_theta-1 (theta
+ * = 0 alone if n_theta = 1), of the spectral radius of the iteration operator of
+ * a mode e^{i theta j}:
+ *   OCI_FOURIER_OCI: T = (L_c - S)^{-1} B(theta)   (one-cell inversion)
+ *   OCI_FOURIER_SI:  T = (L_c - B(theta))^{-1} S   (source iteration)
+ * with L_c the cell operator (Eq. Aj), S the within-cell scattering (Eq.
+ * scatter, column-angle weight) and B(theta) the lagged inflow.  Computed on
+ * reduced matrices with the same nonzero spectrum (2N x 2N for OCI, 4 x 4 for
+ * SI) as lim ||M^n||^{1/n} with n = 2^30 (normalised repeated squaring, FP64).
+ * N even, 2 <= N <= 32; 1 <= n_cases <= 65535.  delta, tau, c: [n_cases], all host or all device;
+ * rho: [n_cases], host or device.  stream: cudaStream_t or NULL.  Blocks until
+ * the result is written.  Returns OCI_E_INVAL for bad arguments before any
+ * device work. */
+enum { OCI_FOURIER_OCI = 0, OCI_FOURIER_SI = 1 };
+int oci_fourier_rho(int32_t kind, int32_t N, int32_t n_cases, const double *delta, const double *tau,
+                    const double *c, int32_t n_theta, double *rho, void *stream);
+
 /* Measured FP64 fused-multiply-add throughput of the current device in
  * FLOP/s (a register-only DFMA loop, CUDA-event timed): the arithmetic
  * roofline of the FP64 path.  Returns a negative status on failure. */

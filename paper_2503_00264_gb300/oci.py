@@ -29,7 +29,7 @@ EXPORTS = ["oci_setup", "oci_step", "oci_solve_transient", "si_sweep", "oci_iter
            "oci_get_psi", "oci_set_psi", "oci_get_phi", "oci_get_state", "oci_set_state", "oci_get_balance",
            "oci_set_boundary", "oci_set_ordering", "oci_set_si_mode", "oci_get_e_hist", "oci_get_edges", "oci_commit", "oci_get_info", "oci_destroy", "oci_last_error",
            "oci_probe_fp64_peak", "oci_batch_setup", "oci_batch_step", "oci_batch_size", "oci_batch_get_psi",
-           "oci_batch_get_phi", "oci_batch_get_balance", "oci_diff_norm_noalloc"]
+           "oci_batch_get_phi", "oci_batch_get_balance", "oci_diff_norm_noalloc", "oci_fourier_rho"]
 
 
 class OCIError(RuntimeError):
@@ -103,6 +103,7 @@ def load(path: Optional[str] = None):
     L.oci_batch_size.argtypes = [vp, ctypes.POINTER(i32)]
     for f in ("oci_batch_get_psi", "oci_batch_get_phi", "oci_batch_get_balance"):
         getattr(L, f).argtypes = [vp, i32, vp]
+    L.oci_fourier_rho.argtypes = [i32, i32, i32, vp, vp, vp, i32, vp, vp]
     for f in EXPORTS:
         if f not in ("oci_destroy", "oci_last_error"):
             getattr(L, f).restype = ctypes.c_int
@@ -129,6 +130,22 @@ def _ptr(x, dtype=np.float64, writable=False):
     if writable and not x.flags.writeable:
         raise ValueError("array is read-only")
     return x.ctypes.data
+
+
+FOURIER_OCI, FOURIER_SI = 0, 1
+
+
+def fourier_rho(kind: int, N: int, delta, tau, c, n_theta: int = 250, stream=None) -> np.ndarray:
+    """Fourier spectral radius of the OCI or SI iteration (oci_fourier_rho) for the
+    model problems (delta[i], tau[i], c[i]): max over n_theta wave numbers."""
+    L = load()
+    d = np.ascontiguousarray(np.atleast_1d(delta), np.float64)
+    t = np.ascontiguousarray(np.broadcast_to(np.atleast_1d(tau), d.shape), np.float64)
+    cc = np.ascontiguousarray(np.broadcast_to(np.atleast_1d(c), d.shape), np.float64)
+    out = np.zeros(d.shape)
+    _check(L.oci_fourier_rho(int(kind), int(N), int(d.size), _ptr(d), _ptr(t), _ptr(cc), int(n_theta),
+                             _ptr(out, writable=True), stream))
+    return out
 
 
 def current_stream():
