@@ -300,6 +300,21 @@ void oci_destroy(oci_handle *h);
 /* Message of the last failure on the calling thread ("" if none). */
 const char *oci_last_error(void);
 
+/* Krylov acceleration of the FP64 step (beyond the paper, which names Krylov
+ * methods as a route to faster convergence, Sec. 4).  One OCI sweep is the
+ * affine map F(x) = T x + b (T = A^{-1} B, Eq. oci); with OCI_ACCEL_GMRES each
+ * oci_step solves the same fixed point, (I - T) x = b, by restarted GMRES(restart)
+ * from the step's initial iterate, one sweep per Krylov vector, and stops when
+ * ||F(x) - x||_2 (the e one OCI sweep would make, Sec. 2.1) < tol *
+ * residual_factor; it then commits F(x).  oci_stats.iters counts the sweeps,
+ * e_last is that residual, rho_e_last is 0.  Needs the FP64 structured solver
+ * in Jacobi order; restart in [1, 32]; residual_factor in (0, 1] (0.05 suits
+ * contraction rates up to ~0.95: the error is at most the residual / (1 - rho)).
+ * Device storage (restart + 3 vectors of the state's size) is allocated at the
+ * first accelerated step.  OCI_ACCEL_NONE restores plain OCI. */
+enum { OCI_ACCEL_NONE = 0, OCI_ACCEL_GMRES = 1 };
+int oci_set_acceleration(oci_handle *h, int32_t accel, int32_t restart, double residual_factor);
+
 /* Fourier (von Neumann) analysis of the iterations (Sec. 2.3), batched on the
  * GPU.  Model problem: infinite homogeneous medium, one group, Sigma_t = v = 1,
  * so case i has cell optical thickness delta[i] (= dx), mean free time tau[i]

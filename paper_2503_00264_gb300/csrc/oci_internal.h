@@ -136,6 +136,12 @@ struct Handle {
   bool no_graph = false;           // OCI_NO_GRAPH=1: host-driven loop instead of the WHILE graph
   int tune_cb = 0, tune_P = 0;     // sweep launch shape picked by the autotuner (0: default)
   bool tune_reg = false;           // FP64 Jacobi sweep in the register form (k_oci_sweep_reg)
+  // Krylov acceleration of the FP64 step (OCI_ACCEL_GMRES): restart length, residual
+  // factor (stop when ||F(x) - x|| < tol * factor) and device storage
+  int accel = 0, gm_restart = 20;
+  double gm_factor = 0.05;
+  double *gm_V = nullptr, *gm_w = nullptr, *gm_zero = nullptr, *gm_part = nullptr, *gm_h = nullptr;
+  DevState *gm_ds = nullptr;
   int mx_cb = 0, mx_P = 0;         // same for the FP32 inner sweep of the mixed form
   double tune_us = 0.0;            // measured sweep time of the chosen shape
 };
@@ -151,6 +157,10 @@ SweepCfg sweep_config(const Handle &h);
 size_t sweep_smem(int N, int G, int cb, int P, size_t es);
 
 void launch_step_const(Handle &h);
+void launch_oci_apply(Handle &h, const double *in, double *out, const double *tc, const double *inc,
+                      DevState *ds_apply);
+int gmres_solve(Handle &h, double tol_g, int max_sweeps, int &sweeps, double &e_last, int &status);
+void gmres_free(Handle &h);
 void launch_oci_sweep(Handle &h, cudaGraphConditionalHandle cond, int use_cond);
 const void *k_oci_sweep_ptr();
 const void *k_oci_sweep_rb_ptr();

@@ -210,6 +210,21 @@ size_t sweep_smem(int N, int G, int cb, int P, size_t es) {
 
 // Default launch shape (used when the autotuner is off): the largest block of
 // cells that keeps <= 256 threads and <= 96 KB of shared memory, one chunk.
+// One plain Jacobi sweep out = A^{-1}(c + B in) with the given per-step constant
+// (tc = A^{-1}-premultiplied c) and incident flux, on arbitrary buffers: the
+// operator apply of the Krylov acceleration (no norm, no stop rule; ds_apply
+// is a device state with cur = 0 and done = 0, read only).
+void launch_oci_apply(Handle &h, const double *in, double *out, const double *tc, const double *inc,
+                      DevState *ds_apply) {
+  SweepCfg c = sweep_config(h);
+  dim3 block(c.cells_per_block, h.G * c.chunks);
+  cudaGraphConditionalHandle none{};
+  k_oci_sweep_t<false><<<c.grid, block, c.smem, h.stream>>>(h.J, h.Jp, h.N, h.G, c.chunks, -1, h.type, h.tt.Linv,
+                                                            h.tt.Cin, h.tt.Mp, h.w, inc, tc, const_cast<double *>(in),
+                                                            out, ds_apply, h.partials, h.counter, nullptr, none, 0, 0,
+                                                            c.grid);
+}
+
 SweepCfg sweep_config(const Handle &h) {
   SweepCfg c;
   int cb = h.tune_cb, P = h.tune_P;

@@ -29,7 +29,8 @@ EXPORTS = ["oci_setup", "oci_step", "oci_solve_transient", "si_sweep", "oci_iter
            "oci_get_psi", "oci_set_psi", "oci_get_phi", "oci_get_state", "oci_set_state", "oci_get_balance",
            "oci_set_boundary", "oci_set_ordering", "oci_set_si_mode", "oci_get_e_hist", "oci_get_edges", "oci_commit", "oci_get_info", "oci_destroy", "oci_last_error",
            "oci_probe_fp64_peak", "oci_batch_setup", "oci_batch_step", "oci_batch_size", "oci_batch_get_psi",
-           "oci_batch_get_phi", "oci_batch_get_balance", "oci_diff_norm_noalloc", "oci_fourier_rho"]
+           "oci_batch_get_phi", "oci_batch_get_balance", "oci_diff_norm_noalloc", "oci_fourier_rho",
+           "oci_set_acceleration"]
 
 
 class OCIError(RuntimeError):
@@ -104,6 +105,7 @@ def load(path: Optional[str] = None):
     for f in ("oci_batch_get_psi", "oci_batch_get_phi", "oci_batch_get_balance"):
         getattr(L, f).argtypes = [vp, i32, vp]
     L.oci_fourier_rho.argtypes = [i32, i32, i32, vp, vp, vp, i32, vp, vp]
+    L.oci_set_acceleration.argtypes = [vp, i32, i32, dbl]
     for f in EXPORTS:
         if f not in ("oci_destroy", "oci_last_error"):
             getattr(L, f).restype = ctypes.c_int
@@ -133,6 +135,7 @@ def _ptr(x, dtype=np.float64, writable=False):
 
 
 FOURIER_OCI, FOURIER_SI = 0, 1
+ACCEL_NONE, ACCEL_GMRES = 0, 1
 
 
 def fourier_rho(kind: int, N: int, delta, tau, c, n_theta: int = 250, stream=None) -> np.ndarray:
@@ -336,6 +339,9 @@ class Solver:
 
     def set_si_mode(self, mode: int):
         _check(self.L.oci_set_si_mode(self.h, int(mode)))
+
+    def set_acceleration(self, accel: int, restart: int = 20, residual_factor: float = 0.05):
+        _check(self.L.oci_set_acceleration(self.h, int(accel), int(restart), float(residual_factor)))
 
     def set_ordering(self, ordering: int):
         _check(self.L.oci_set_ordering(self.h, int(ordering)))
