@@ -453,9 +453,10 @@ __global__ void __launch_bounds__(32 * kMaxG) k_carry(int J, int Jp, int N, int 
                                                const double *Psi1, const DevState *__restrict__ ds,
                                                double *__restrict__ psi_prev, double *__restrict__ phi,
                                                double *__restrict__ bal_partials) {
-  __shared__ double ph_s[kMaxG * 4][32];
+  extern __shared__ double ph_sm[];  // [G*4][CB]
+  const int CB = blockDim.x;
   const int cl = threadIdx.x, g = threadIdx.y;
-  const int j = blockIdx.x * 32 + cl;
+  const int j = blockIdx.x * CB + cl;
   if (ds->status != OCI_OK) return;  // commit only a converged step (uniform)
   const bool active = j < J;
   const double *__restrict__ P = ds->cur ? Psi1 : Psi0;
@@ -463,6 +464,7 @@ __global__ void __launch_bounds__(32 * kMaxG) k_carry(int J, int Jp, int N, int 
   int tau = 0;
   if (active) {
     tau = type[j];
+#pragma unroll 4
     for (int m = 0; m < N; m++) {
       const int gm = g * N + m;
       const double wm = w[m];
@@ -482,7 +484,7 @@ __global__ void __launch_bounds__(32 * kMaxG) k_carry(int J, int Jp, int N, int 
 #pragma unroll
     for (int p = 0; p < 4; p++) {
       phi[(size_t)(g * 4 + p) * Jp + j] = ph[p];
-      ph_s[g * 4 + p][cl] = ph[p];
+      ph_sm[(size_t)(g * 4 + p) * CB + cl] = ph[p];
     }
   }
   __syncthreads();
@@ -497,8 +499,8 @@ __global__ void __launch_bounds__(32 * kMaxG) k_carry(int J, int Jp, int N, int 
     tally[3] = dx / 2.0 * sig * (ph[2] + ph[3]);
     for (int gp = 0; gp < G; gp++) {
       const double k2 = 2.0 * Kap[((size_t)tau * G + gp) * G + g];  // dx/2 Sigma_s,gp->g
-      tally[4] += k2 * (ph_s[gp * 4 + 0][cl] + ph_s[gp * 4 + 1][cl]);
-      tally[5] += k2 * (ph_s[gp * 4 + 2][cl] + ph_s[gp * 4 + 3][cl]);
+      tally[4] += k2 * (ph_sm[(size_t)(gp * 4 + 0) * CB + cl] + ph_sm[(size_t)(gp * 4 + 1) * CB + cl]);
+      tally[5] += k2 * (ph_sm[(size_t)(gp * 4 + 2) * CB + cl] + ph_sm[(size_t)(gp * 4 + 3) * CB + cl]);
     }
     if (Q) {
       const double *q = Q + j;
@@ -506,38 +508,44 @@ __global__ void __launch_bounds__(32 * kMaxG) k_carry(int J, int Jp, int N, int 
       tally[7] = dx / 2.0 * (q[(size_t)(g * 4 + 2) * Jp] + q[(size_t)(g * 4 + 3) * Jp]);
     }
   }
-  // reduce each tally over the 32 cells of this group's warp (one warp per group)
+  // reduce each tally over the 32 cells of each warp: one partial per 32 cells and group
+  const size_t slot = (size_t)blockIdx.x * (CB / 32) + (cl >> 5);
 #pragma unroll
   for (int k = 0; k < 8; k++) {
     double x = tally[k];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-    if (cl == 0) bal_partials[((size_t)blockIdx.x * G + g) * 8 + k] = x;
+    if ((cl & 31) == 0 && slot < (size_t)((J + 31) / 32))  // warps wholly past J own no slot
+      bal_partials[(slot * G + g) * 8 + k] = x;
   }
 }
 
 // Sum the balance partials in a fixed order and add the leakage
 // sum_m w_m mu_m (psi at x = X - psi at x = 0) with the upstream edge values.
-__global__ void k_balance_final(int J, int Jp, int N, int G, int nblk, const double *__restrict__ bal_partials,
+constexpr int kBalThreads = 256;
+__global__ void __launch_bounds__(kBalThreads) k_balance_final(int J, int Jp, int N, int G, int nblk, const double *__restrict__ bal_partials,
                                 const double *__restrict__ mu, const double *__restrict__ w,
                                 const double *__restrict__ inc, const double *Psi0, const double *Psi1,
                                 const DevState *__restrict__ ds, double *__restrict__ bal) {
   const int g = blockIdx.x;
-  __shared__ double acc[8][64];
+  constexpr int kT = kBalThreads;
+  __shared__ double acc[8][kT];
   if (ds->status != OCI_OK) return;
-  const int t = threadIdx.x;  // 64 threads
+  const int t = threadIdx.x;
   double s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  for (int b = t; b < nblk; b += 64)
+  for (int b = t; b < nblk; b += kT)
+#pragma unroll
     for (int k = 0; k < 8; k++) s[k] += bal_partials[((size_t)b * G + g) * 8 + k];
   for (int k = 0; k < 8; k++) acc[k][t] = s[k];
   __syncthreads();
+  for (int half = kT / 2; half > 0; half >>= 1) {  // fixed-order tree
+    if (t < half)
+      for (int k = 0; k < 8; k++) acc[k][t] += acc[k][t + half];
+    __syncthreads();
+  }
   if (t == 0) {
     double tot[8];
-    for (int k = 0; k < 8; k++) {
-      double x = 0.0;
-      for (int i = 0; i < 64; i++) x += acc[k][i];
-      tot[k] = x;
-    }
+    for (int k = 0; k < 8; k++) tot[k] = acc[k][0];
     const double *P = ds->cur ? Psi1 : Psi0;
     double lA = 0.0, lE = 0.0;
     for (int m = 0; m < N; m++) {
@@ -564,11 +572,14 @@ __global__ void k_balance_final(int J, int Jp, int N, int G, int nblk, const dou
 }
 
 void launch_carry(Handle &h) {
+  // blocks of CB cells x G groups (at most 512 threads); balance partials per 32 cells
+  int CB = 128;
+  while (CB > 32 && CB * h.G > 512) CB /= 2;
   const int nblk = (h.J + 31) / 32;
-  dim3 block(32, h.G);
-  k_carry<<<nblk, block, 0, h.stream>>>(h.J, h.Jp, h.N, h.G, h.type, h.tt.dx, h.tt.sig, h.tt.Kap, h.v, h.dt, h.w,
+  dim3 block(CB, h.G);
+  k_carry<<<(h.J + CB - 1) / CB, block, (size_t)h.G * 4 * CB * sizeof(double), h.stream>>>(h.J, h.Jp, h.N, h.G, h.type, h.tt.dx, h.tt.sig, h.tt.Kap, h.v, h.dt, h.w,
                                         h.Q, h.Psi[0], h.Psi[1], h.ds, h.psi_prev, h.phi, h.bal_partials);
-  k_balance_final<<<h.G, 64, 0, h.stream>>>(h.J, h.Jp, h.N, h.G, nblk, h.bal_partials, h.mu, h.w, h.inc, h.Psi[0],
+  k_balance_final<<<h.G, kBalThreads, 0, h.stream>>>(h.J, h.Jp, h.N, h.G, nblk, h.bal_partials, h.mu, h.w, h.inc, h.Psi[0],
                                             h.Psi[1], h.ds, h.bal);
 }
 
