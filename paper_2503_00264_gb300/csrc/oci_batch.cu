@@ -446,12 +446,17 @@ __global__ void __launch_bounds__(256) k_b_mx_inner(BatchClassDev c, const DevSt
 }
 
 // One block per slab: fixed-order sum of its tile partials, then the mixed-form
-// stop rule and refinement decision; the last slab to finish ends the loop.
+// stop rule and refinement decision; the last slab to finish ends the loop.  In
+// the graph the class's refinement kernel sits under an IF node: the last
+// block of this launch (counter in flags[1]) sets it to whether any slab of the
+// class asked for a refinement (flags[0]) and resets both words.
 __global__ void __launch_bounds__(kBFinThreads) k_b_mx_finalize(BatchClassDev c, DevState *__restrict__ ds,
                                                                int *active, int use_cond,
-                                                               cudaGraphConditionalHandle cond) {
+                                                               cudaGraphConditionalHandle cond,
+                                                               unsigned *flags, cudaGraphConditionalHandle if_cond) {
   __shared__ double red[kBFinThreads / 32];
   const int s = blockIdx.x;
+  int refine = 0;
   if (ds[s].done) {
     // a slab that finished in the previous body: its last refinement has been
     // applied by that body's outer kernel; settle it so no later body repeats it
@@ -460,15 +465,26 @@ __global__ void __launch_bounds__(kBFinThreads) k_b_mx_finalize(BatchClassDev c,
       ds[s].refine = 0;
       ds[s].blk_i = 0;
     }
-    return;
+  } else {
+    const int t0 = c.slab_tile0[s];
+    const double v = block_sum_fixed(c.partials + t0, c.slab_tile1[s] - t0, red);
+    if (threadIdx.x == 0) {
+      finish_mixed(&ds[s], nullptr, sqrt(v), cond, 0);
+      refine = ds[s].refine;
+      if (ds[s].done) {
+        const int before = atomicSub(active, 1);
+        if (before == 1 && use_cond) cudaGraphSetConditional(cond, 0);
+      }
+    }
   }
-  const int t0 = c.slab_tile0[s];
-  const double v = block_sum_fixed(c.partials + t0, c.slab_tile1[s] - t0, red);
-  if (threadIdx.x != 0) return;
-  finish_mixed(&ds[s], nullptr, sqrt(v), cond, 0);
-  if (ds[s].done) {
-    const int before = atomicSub(active, 1);
-    if (before == 1 && use_cond) cudaGraphSetConditional(cond, 0);
+  if (threadIdx.x != 0 || !use_cond) return;
+  if (refine) atomicOr(&flags[0], 1u);
+  __threadfence();
+  if (atomicAdd(&flags[1], 1u) == gridDim.x - 1) {  // last block of the class
+    __threadfence();
+    const unsigned any = atomicExch(&flags[0], 0u);
+    flags[1] = 0;
+    cudaGraphSetConditional(if_cond, any ? 1u : 0u);
   }
 }
 
@@ -859,7 +875,8 @@ void launch_b_mx_inner(BatchClass &c, DevState *ds, cudaStream_t st) {
 
 void launch_b_mx_finalize(BatchClass &c, DevState *ds, int *active, int use_cond, cudaGraphConditionalHandle cond,
                           cudaStream_t st) {
-  k_b_mx_finalize<<<c.d.n_slabs, kBFinThreads, 0, st>>>(c.d, ds, active, use_cond, cond);
+  k_b_mx_finalize<<<c.d.n_slabs, kBFinThreads, 0, st>>>(c.d, ds, active, use_cond, cond, c.if_flags,
+                                                         (cudaGraphConditionalHandle)c.if_handle);
 }
 
 void launch_b_mx_outer(BatchClass &c, DevState *ds, int mode, cudaStream_t st) {

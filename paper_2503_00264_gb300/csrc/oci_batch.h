@@ -37,6 +37,8 @@ struct BatchClassDev {
 struct BatchClass {
   BatchClassDev d{};
   bool mixed = false;
+  unsigned *if_flags = nullptr;         // mixed form in the graph: {any slab refines, blocks done}
+  unsigned long long if_handle = 0;     // IF node of the class's refinement kernel
   int cb = 128;     // cells per tile (autotuned)
   int np = 0;       // angles per thread of the register sweep; 0 = shared-memory sweep (autotuned)
   int grid = 0;     // persistent grid size
@@ -59,6 +61,7 @@ struct Batch {
   double *h_bal = nullptr;    // pinned, per class concatenated
   int *h_active = nullptr;    // pinned copy of the unconverged count (host-driven loop)
   bool no_graph = false;      // drive the loop from the host (OCI_NO_GRAPH=1)
+  std::vector<cudaGraph_t> if_bodies;  // mixed form: per-class IF bodies while the graph is built
   cudaStream_t stream = nullptr;
   cudaGraphExec_t graph = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;

@@ -202,6 +202,9 @@ static int setup_class(Batch &B, BatchClass &c, const oci_problem *probs) {
     d.Linv32 = L32; d.Cin32 = C32; d.Mp32 = M32; d.w32 = W32; d.Lco = d_Lco;
     d.D0 = D0; d.D1 = D1; d.z32 = z32;
     d.cvec = tc;  // the mixed form keeps c itself where the FP64 form keeps Linv c
+    unsigned *fl;
+    if ((rc = balloc(c, &fl, 2, st))) return rc;
+    c.if_flags = fl;
   }
   // ---- autotune the sweep of this class (CUDA events over a few sweeps):
   // the shared-memory sweep over cb cells, or the register sweep with np
@@ -328,12 +331,56 @@ static int build_batch_graph(Batch &B) {
   if (e == cudaSuccess) {
     cudaEventRecord(fork, br[0]);
     for (int i = 1; i < nc; i++) cudaStreamWaitEvent(br[i], fork, 0);
-    launch_batch_body(B, br, cond, 1);
+    if (B.precision == OCI_FP64) {
+      launch_batch_body(B, br, cond, 1);
+    } else {
+      // per class: inner sweep, finalize (sets the class's IF), IF { refinement }
+      std::vector<cudaGraph_t> ifbodies(nc, nullptr);
+      for (int i = 0; i < nc && e == cudaSuccess; i++) {
+        BatchClass &c = B.cls[i];
+        cudaStreamCaptureStatus cst;
+        cudaGraph_t cg = nullptr;
+        const cudaGraphNode_t *deps = nullptr;
+        size_t nd = 0;
+        e = cudaStreamGetCaptureInfo(br[i], &cst, nullptr, &cg, nullptr, nullptr, nullptr);
+        cudaGraphConditionalHandle h_if{};
+        if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h_if, cg, 0, cudaGraphCondAssignDefault);
+        if (e != cudaSuccess) break;
+        c.if_handle = (unsigned long long)h_if;
+        launch_b_mx_inner(c, B.ds + c.slab0, br[i]);
+        launch_b_mx_finalize(c, B.ds + c.slab0, B.active, 1, cond, br[i]);
+        e = cudaStreamGetCaptureInfo(br[i], &cst, nullptr, &cg, &deps, nullptr, &nd);
+        cudaGraphNodeParams ip = {};
+        cudaGraphNode_t ifn;
+        if (e == cudaSuccess) {
+          ip.type = cudaGraphNodeTypeConditional;
+          ip.conditional.handle = h_if;
+          ip.conditional.type = cudaGraphCondTypeIf;
+          ip.conditional.size = 1;
+          e = cudaGraphAddNode(&ifn, cg, deps, nullptr, nd, &ip);
+        }
+        if (e == cudaSuccess)
+          e = cudaStreamUpdateCaptureDependencies(br[i], &ifn, nullptr, 1, cudaStreamSetCaptureDependencies);
+        if (e == cudaSuccess) ifbodies[i] = ip.conditional.phGraph_out[0];
+      }
+      // the refinement kernels go into the IF bodies after the main capture ends
+      B.if_bodies = ifbodies;
+    }
     for (int i = 1; i < nc; i++) {
       cudaEventRecord(join[i], br[i]);
       cudaStreamWaitEvent(br[0], join[i], 0);
     }
-    e = cudaStreamEndCapture(br[0], &body);
+    cudaError_t e2 = cudaStreamEndCapture(br[0], &body);
+    if (e == cudaSuccess) e = e2;
+    for (int i = 0; i < nc && e == cudaSuccess && B.precision != OCI_FP64; i++) {
+      cudaGraph_t ib = B.if_bodies[i];
+      e = cudaStreamBeginCaptureToGraph(br[i], ib, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        BatchClass &c = B.cls[i];
+        launch_b_mx_outer(c, B.ds + c.slab0, 1, br[i]);
+        e = cudaStreamEndCapture(br[i], &ib);
+      }
+    }
   }
   for (int i = 0; i < nc; i++) {
     if (br[i]) cudaStreamDestroy(br[i]);
