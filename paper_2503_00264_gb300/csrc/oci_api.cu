@@ -313,7 +313,7 @@ static int autotune(Handle &h) {
       for (int cb : {16, 32, 64, 128}) {
         const int thr = cb * h.G * P;
         if (thr <= 256 && thr % 32 == 0 && thr >= 64) cands.push_back({kMxReg, cb, P});
-        if (cb == 16) {  // 16-cell tiles: persistent forms with 8 angles per thread only
+        if (cb == 16 || cb == 128) {  // 16- and 128-cell tiles: persistent forms, 8 angles per thread
           if (np == 8 && thr <= 256 && thr % 32 == 0 && thr >= 64) cands.push_back({kMxTiledP, cb, P});
           continue;
         }
@@ -393,13 +393,23 @@ static int autotune(Handle &h) {
   const int reps = 3;
   for (auto &c : cands) {
     apply(c);
+    // the persistent tiled FP32 sweep runs as one multi-sweep cooperative launch in
+    // the graph: time it that way (reps sweeps in one launch)
+    const bool multi = mx && c.kind == kMxTiledP && h.mx_multi;
     auto sweep = [&]() {
       if (mx) launch_mx_inner(h, cudaGraphConditionalHandle{}, 0);
       else launch_oci_sweep(h, cudaGraphConditionalHandle{}, 0);
     };
+    h.mx_tune_sweeps = multi ? 1 : 0;
     sweep();
     CK(cudaEventRecord(h.ev0, h.stream));
-    for (int r = 0; r < reps; r++) sweep();
+    if (multi) {
+      h.mx_tune_sweeps = reps;
+      sweep();
+    } else {
+      for (int r = 0; r < reps; r++) sweep();
+    }
+    h.mx_tune_sweeps = 0;
     CK(cudaEventRecord(h.ev1, h.stream));
     CK(cudaEventSynchronize(h.ev1));
     CK(cudaGetLastError());
@@ -416,7 +426,7 @@ static int autotune(Handle &h) {
   CK(cudaMemsetAsync(h.Psi[0], 0, nPsi * 8, h.stream));
   CK(cudaMemsetAsync(h.Psi[1], 0, nPsi * 8, h.stream));
   if (mx) {
-    const size_t nPsi32 = (size_t)h.G * h.N * 4 * std::max<size_t>(h.Jp, (h.J + 63) / 64 * 64);
+    const size_t nPsi32 = (size_t)h.G * h.N * 4 * std::max<size_t>(h.Jp, (h.J + 127) / 128 * 128);
     CK(cudaMemsetAsync(h.delta[0], 0, nPsi32 * 4, h.stream));
     CK(cudaMemsetAsync(h.delta[1], 0, nPsi32 * 4, h.stream));
   }
@@ -650,8 +660,8 @@ static int setup_impl(const oci_problem *p, oci_handle *h) {
     if ((rc = dev_upload(&h->mu32, MU32.data(), MU32.size(), s))) return rc;
     CK(cudaStreamSynchronize(s));  // host vectors of the uploads go out of scope
     // FP32 correction arrays: room for both layouts ([R][Jp], and tile-major
-    // with tiles of up to 64 cells)
-    const size_t nPsi32 = (size_t)G * N * 4 * std::max<size_t>(Jp, (h->J + 63) / 64 * 64);
+    // with tiles of up to 128 cells)
+    const size_t nPsi32 = (size_t)G * N * 4 * std::max<size_t>(Jp, (h->J + 127) / 128 * 128);
     CK(cudaMalloc(&h->delta[0], nPsi32 * 4));
     CK(cudaMalloc(&h->delta[1], nPsi32 * 4));
     CK(cudaMalloc(&h->z32, nPsi32 * 4));

@@ -101,6 +101,7 @@ struct Handle {
   bool tma_ok = false;                 // tensor maps encoded (4NG <= 256)
   unsigned long long mx_cond_ref = 0;  // IF-node handle of the refinement in the mixed-form graph
   int mx_jac_kind = 0, mx_jac_cb = 0, mx_jac_P = 0;  // the Jacobi FP32 inner sweep (kept while red-black)
+  int mx_tune_sweeps = 0;              // > 0 while the autotuner times a multi-sweep launch of that many sweeps
   bool mx_multi = true;                // graph runs the persistent tiled FP32 sweep several sweeps per launch
   unsigned *gbar = nullptr;            // {count, generation} of the multi-sweep kernel's grid barrier
   int mx_kind = 0;                     // FP32 inner sweep picked by the autotuner: kMxPlain, kMxTma, kMxReg, kMxTiled

@@ -42,7 +42,7 @@ __device__ __forceinline__ size_t fidx(int tsh, int R, size_t Jp, int r, int j) 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 int mx_tile_shift(const Handle &h) {
-  const int sh = h.mx_cb == 16 ? 4 : h.mx_cb == 32 ? 5 : 6;
+  const int sh = h.mx_cb == 16 ? 4 : h.mx_cb == 32 ? 5 : h.mx_cb == 64 ? 6 : 7;
   if (h.mx_kind == kMxTiled || h.mx_kind == kMxTiledP || h.mx_kind == kMxTiledB) return sh;
   if (h.mx_kind == kMxRB) return sh | 0x100;
   return 0;
@@ -836,7 +836,7 @@ __global__ void __launch_bounds__(256) k_mx_inner_ms(int J, int N, int G, int n_
                                                      const float *Cin_g, const float *Mp_g, const float *w_g,
                                                      const float *__restrict__ z, float *D0, float *D1, DevState *ds,
                                                      double *__restrict__ partials, unsigned *gbar, double *e_hist,
-                                                     cudaGraphConditionalHandle cond) {
+                                                     cudaGraphConditionalHandle cond, int use_cond, int max_sweeps) {
   extern __shared__ __align__(16) float smr[];
   __shared__ double red[8];
   __shared__ DevState sd;
@@ -882,7 +882,7 @@ __global__ void __launch_bounds__(256) k_mx_inner_ms(int J, int N, int G, int n_
     const double tot = block_sum_fixed(part, gridDim.x, red);
     if (tid == 0) finish_mixed(&sd, blockIdx.x == 0 ? e_hist : nullptr, sqrt(tot), cond, 0);
     __syncthreads();
-    if (sd.done || sd.refine) break;  // uniform: every block holds the same state
+    if (sd.done || sd.refine || sw + 1 >= max_sweeps) break;  // uniform: every block holds the same state
   }
   if (blockIdx.x == 0 && tid == 0) {
     if (failed) {
@@ -891,8 +891,10 @@ __global__ void __launch_bounds__(256) k_mx_inner_ms(int J, int N, int G, int n_
       sd.refine = 0;
     }
     *ds = sd;
-    if (sd.done) cudaGraphSetConditional(cond, 0);
-    if (sd.cond_ref) cudaGraphSetConditional((cudaGraphConditionalHandle)sd.cond_ref, sd.refine);
+    if (use_cond) {
+      if (sd.done) cudaGraphSetConditional(cond, 0);
+      if (sd.cond_ref) cudaGraphSetConditional((cudaGraphConditionalHandle)sd.cond_ref, sd.refine);
+    }
   }
 }
 
@@ -908,7 +910,8 @@ static int ms_grid(const Handle &h, int P, size_t smem) {
 }
 
 template <int T, int NP>
-static void launch_ms(Handle &h, int P, size_t smem, bool stage, cudaGraphConditionalHandle cond) {
+static void launch_ms(Handle &h, int P, size_t smem, bool stage, cudaGraphConditionalHandle cond, int use_cond,
+                      int max_sweeps) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(ms_grid<T, NP>(h, P, smem));
   cfg.blockDim = dim3(T, h.G * P);
@@ -922,7 +925,7 @@ static void launch_ms(Handle &h, int P, size_t smem, bool stage, cudaGraphCondit
   cudaLaunchKernelEx(&cfg, k_mx_inner_ms<T, NP>, h.J, h.N, h.G, h.tt.n_types, (int)stage, (const int32_t *)h.type,
                      (const float *)h.tt.Linv32, (const float *)h.tt.Cin32, (const float *)h.tt.Mp32,
                      (const float *)h.w32, (const float *)h.z32, h.delta[0], h.delta[1], h.ds, h.partials, h.gbar,
-                     h.e_hist, cond);
+                     h.e_hist, cond, use_cond, max_sweeps);
 }
 
 template <int T, int NP>
@@ -1842,21 +1845,27 @@ void launch_mx_inner(Handle &h, cudaGraphConditionalHandle cond, int use_cond) {
 #undef OCI_MX_TB
     return;
   }
-  if (h.mx_kind == kMxTiledP && use_cond && h.mx_multi) {  // in the graph: several sweeps per launch
+  if (h.mx_kind == kMxTiledP && ((use_cond && h.mx_multi) || h.mx_tune_sweeps > 0)) {
+    // in the graph (or when the autotuner times it): several sweeps per cooperative launch
     const int T = h.mx_cb, P = h.mx_P, np = h.N / P;
     const bool stage = mx_tables_floats(h) * 4 <= 64 * 1024;
     const size_t smem = mx_tp_smem(h, T, P, stage);
+    const int ms = use_cond ? (1 << 30) : h.mx_tune_sweeps;
+#define OCI_MS(TT, NP) launch_ms<TT, NP>(h, P, smem, stage, cond, use_cond, ms)
     if (T == 16) {
-      launch_ms<16, 8>(h, P, smem, stage, cond);
+      OCI_MS(16, 8);
+    } else if (T == 128) {
+      OCI_MS(128, 8);
     } else if (T == 32) {
-      if (np == 2) launch_ms<32, 2>(h, P, smem, stage, cond);
-      else if (np == 4) launch_ms<32, 4>(h, P, smem, stage, cond);
-      else launch_ms<32, 8>(h, P, smem, stage, cond);
+      if (np == 2) OCI_MS(32, 2);
+      else if (np == 4) OCI_MS(32, 4);
+      else OCI_MS(32, 8);
     } else {
-      if (np == 2) launch_ms<64, 2>(h, P, smem, stage, cond);
-      else if (np == 4) launch_ms<64, 4>(h, P, smem, stage, cond);
-      else launch_ms<64, 8>(h, P, smem, stage, cond);
+      if (np == 2) OCI_MS(64, 2);
+      else if (np == 4) OCI_MS(64, 4);
+      else OCI_MS(64, 8);
     }
+#undef OCI_MS
     return;
   }
   if (h.mx_kind == kMxTiledP) {
@@ -1870,6 +1879,8 @@ void launch_mx_inner(Handle &h, cudaGraphConditionalHandle cond, int use_cond) {
       h.delta[1], h.ds, h.partials, h.counter, h.e_hist, cond, use_cond)
     if (T == 16) {
       OCI_MX_TP(16, 8);
+    } else if (T == 128) {
+      OCI_MX_TP(128, 8);
     } else if (T == 32) {
       if (np == 2) OCI_MX_TP(32, 2);
       else if (np == 4) OCI_MX_TP(32, 4);
@@ -1966,7 +1977,8 @@ const void *k_mx_inner_ptr() { return (const void *)k_mx_inner; }
 // Dynamic shared memory limits of the FP32 inner kernels above 48 KB (set once at setup).
 int mx_set_attributes() {
   const void *ks[] = {(const void *)k_mx_inner,          (const void *)k_mx_inner_tp<16, 8>,
-                      (const void *)k_mx_inner_ms<16, 8>, (const void *)k_mx_inner_tp<32, 2>,
+                      (const void *)k_mx_inner_ms<16, 8>, (const void *)k_mx_inner_tp<128, 8>,
+                      (const void *)k_mx_inner_ms<128, 8>, (const void *)k_mx_inner_tp<32, 2>,
                       (const void *)k_mx_inner_tp<32, 4>, (const void *)k_mx_inner_tp<32, 8>,
                       (const void *)k_mx_inner_tp<64, 2>, (const void *)k_mx_inner_tp<64, 4>,
                       (const void *)k_mx_inner_tp<64, 8>, (const void *)k_mx_inner_tb<32, 2>,

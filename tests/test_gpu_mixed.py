@@ -149,7 +149,8 @@ def test_fp32_inner_kernels_all_match_oracle(kernel, monkeypatch):
 @pytest.mark.parametrize("kernel,shape", [("reg", "32,8"), ("reg", "64,4"), ("reg", "128,2"), ("reg", "64,2"),
                                           ("tiled", "32,8"), ("tiled", "64,4"), ("tiled", "64,2"),
                                           ("tiled", "32,2"), ("tiledp", "32,8"), ("tiledp", "64,4"),
-                                          ("tiledp", "64,2"), ("tiledb", "32,8"), ("tiledb", "64,4"),
+                                          ("tiledp", "64,2"), ("tiledp", "128,2"), ("tiledb", "32,8"),
+                                          ("tiledb", "64,4"),
                                           ("tiledb", "64,2"), ("tiledb", "32,2")])
 def test_fp32_register_inner_shapes_match_oracle(kernel, shape, monkeypatch):
     """Register FP32 inner sweeps (row layout, and tile-major with T = 32 or 64
