@@ -256,9 +256,12 @@ def run_ours(args):
             info_mx = sv.info()
             sv.close()
             # HBM traffic of the form's step (algorithmic): per inner sweep the FP32
-            # operand z, delta_in and delta_out (12 B per unknown); per FP64 refinement
-            # (and the initial residual) Psi in/out, c, delta in, z out (32 B per unknown)
-            step_bytes = (mx_sweeps * 12 + (mx_ref + args.steps) * 32) * p.unknowns / args.steps
+            # operand z, delta_in and delta_out (12 B per unknown; 6 B when two sweeps
+            # share one pass over the correction -- the recompute pass at the end of
+            # an inner block is not counted); per FP64 refinement (and the initial
+            # residual) Psi in/out, c, delta in, z out (32 B per unknown)
+            b_sweep = 6 if info_mx["inner_kernel"] == 9 else 12
+            step_bytes = (mx_sweeps * b_sweep + (mx_ref + args.steps) * 32) * p.unknowns / args.steps
             step_gbs = step_bytes / (mx_ms / args.steps * 1e-3) / 1e9
             mixed.append({
                 "form": name, "block_apply": what,
@@ -273,6 +276,8 @@ def run_ours(args):
                                 "sweeps_diff_total": int(mx_sweeps - sweeps)},
                 "refinements_per_step": mx_ref / args.steps,
                 "inner_kernel": info_mx["inner_kernel"],
+                "inner_shape": {"cells_per_tile": info_mx["cells_per_block"],
+                                "angle_chunks": info_mx["angle_chunks"]},
                 "hbm": {"bytes_per_step": step_bytes, "achieved_gbs": step_gbs,
                         "peak_gbs": peaks_hbm, "frac": step_gbs / peaks_hbm,
                         "note": "whole step incl. refinements, FP64 norm/stop rule and carry"}

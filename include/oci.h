@@ -168,7 +168,9 @@ typedef struct {
                                 2 tcgen05 tensor-core block apply, 3 register FP32 sweep (angles
                                 split over threads), 4 the register sweep on tile-major FP32
                                 correction arrays, 5 the same as a persistent kernel, 6 that with
-                                the tiles moved by 1D bulk copies (TMA); -1 for the FP64 form     */
+                                the tiles moved by 1D bulk copies (TMA), 7 red-black ordering,
+                                9 two inner sweeps per pass over the correction (temporal
+                                blocking); -1 for the FP64 form                                   */
   double tuned_sweep_us;     /* measured time of one sweep with the chosen shape (0 if not tuned) */
 } oci_info;
 

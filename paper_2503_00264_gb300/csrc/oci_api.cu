@@ -320,12 +320,17 @@ static int autotune(Handle &h) {
         if (thr <= 256 && cb <= 64) {
           cands.push_back({kMxTiled, cb, P});
           cands.push_back({kMxTiledP, cb, P});
+          if (np <= 4 && cb >= 32 && thr % 32 == 0 &&
+              mx_ms2_smem(h, cb, P, mx_tables_floats(h) * 4 <= 64 * 1024) <= 160 * 1024) {
+            cands.push_back({kMxTiled2, cb, P});
+            if (h.N == 16 && h.G == 1) cands.push_back({kMxTiled2Occ, cb, P});
+          }
           if (mx_tb_smem(h, cb, P, mx_tables_floats(h) * 4 <= 64 * 1024) <= 200 * 1024)
             cands.push_back({kMxTiledB, cb, P});
         }
       }
     }
-  // OCI_MX_INNER=plain|tma|reg|tiled|tiledp|tiledb restricts the FP32 inner sweep to one kernel (for profiling)
+  // OCI_MX_INNER=plain|tma|reg|tiled|tiledp|tiledb|two|twoocc restricts the FP32 inner sweep to one kernel (for profiling)
   const char *only = getenv("OCI_MX_INNER");
   if (mx && only) {
     const std::string o(only);
@@ -334,6 +339,8 @@ static int autotune(Handle &h) {
                      : o == "tiled"  ? kMxTiled
                      : o == "tiledp" ? kMxTiledP
                      : o == "tiledb" ? kMxTiledB
+                     : o == "two"    ? kMxTiled2
+                     : o == "twoocc" ? kMxTiled2Occ
                                      : kMxPlain;
     std::vector<Cand> keep;
     for (auto &c : cands)
@@ -390,12 +397,12 @@ static int autotune(Handle &h) {
   CK(cudaMemcpyAsync(h.ds, h.h_ds, sizeof(DevState), cudaMemcpyHostToDevice, h.stream));
   float best = 1e30f;
   Cand bc = cands[0];
-  const int reps = 3;
+  const int reps = 4;  // even: the two-sweep form runs two full passes
   for (auto &c : cands) {
     apply(c);
     // the persistent tiled FP32 sweep runs as one multi-sweep cooperative launch in
     // the graph: time it that way (reps sweeps in one launch)
-    const bool multi = mx && c.kind == kMxTiledP && h.mx_multi;
+    const bool multi = mx && (c.kind == kMxTiledP || c.kind == kMxTiled2 || c.kind == kMxTiled2Occ) && h.mx_multi;
     auto sweep = [&]() {
       if (mx) launch_mx_inner(h, cudaGraphConditionalHandle{}, 0);
       else launch_oci_sweep(h, cudaGraphConditionalHandle{}, 0);

@@ -190,6 +190,9 @@ int mx_tma_setup(Handle &h);
 // ([J/T][4NG][T], T = mx_cb)
 constexpr int kMxPlain = 0, kMxTma = 1, kMxReg = 3, kMxTiled = 4, kMxTiledP = 5, kMxTiledB = 6, kMxRB = 7;
 constexpr int kSweepReg64 = 8;  // autotuner candidate kind of the FP64 register sweep
+constexpr int kMxTiled2 = 9;    // tile-major, two inner sweeps per pass (temporal blocking)
+constexpr int kMxTiled2Occ = 10;  // the same built for more resident blocks per SM (S16, one group)
+size_t mx_ms2_smem(const Handle &h, int T, int P, bool stage);
 size_t mx_tb_smem(const Handle &h, int T, int P, bool stage);
 size_t mx_tables_floats(const Handle &h);
 int mx_tile_shift(const Handle &h);

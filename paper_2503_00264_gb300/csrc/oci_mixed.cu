@@ -43,7 +43,9 @@ __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)
 
 int mx_tile_shift(const Handle &h) {
   const int sh = h.mx_cb == 16 ? 4 : h.mx_cb == 32 ? 5 : h.mx_cb == 64 ? 6 : 7;
-  if (h.mx_kind == kMxTiled || h.mx_kind == kMxTiledP || h.mx_kind == kMxTiledB) return sh;
+  if (h.mx_kind == kMxTiled || h.mx_kind == kMxTiledP || h.mx_kind == kMxTiledB || h.mx_kind == kMxTiled2 ||
+      h.mx_kind == kMxTiled2Occ)
+    return sh;
   if (h.mx_kind == kMxRB) return sh | 0x100;
   return 0;
 }
@@ -928,6 +930,462 @@ static void launch_ms(Handle &h, int P, size_t smem, bool stage, cudaGraphCondit
                      h.e_hist, cond, use_cond, max_sweeps);
 }
 
+// ---------------------------------------------------------------- inner sweeps, two per pass
+// Two consecutive inner sweeps in one pass over the correction (temporal
+// blocking).  Each block owns a contiguous run of tiles [t0, t1) and walks it
+// left to right: at step k it computes delta^{i+1} on tile k from delta^i in
+// global memory, then delta^{i+2} on tile k-1, whose lagged inflows are the
+// delta^{i+1} values of tiles k-2, k-1 and k held in a three-slot ring in
+// shared memory.  The delta^{i+1} values of the two cells just outside the run
+// (a0 - 1 and a1) are recomputed by the block before the walk, so blocks never
+// wait on one another inside a pass.  Per two sweeps a pass reads z and
+// delta^i once and writes delta^{i+2} once: 12 bytes per unknown instead of
+// 24.  Both sweeps' norms are reduced and the device state takes the two e
+// values in order; if the first already ends the inner block (a refinement or
+// the stop rule is due), delta^{i+1} is recomputed from delta^i -- still intact
+// in the input buffer -- by a one-sweep pass into the output buffer.  The cell
+// arithmetic is that of the tiled sweep.
+//
+// Template parameters: T cells per tile, NP angles per thread, and the angle
+// chunks per cell PS and groups GS when known at compile time (0: taken from
+// the arguments); with both fixed every index and loop bound folds.
+
+// Global loads of one cell column of a tile (z, the old correction when
+// want_old, the lagged inflows from delta_in); zeros for an inactive thread.
+template <int T, int NP, int PS, int GS>
+__device__ __forceinline__ void ms2_load(float (&zr)[NP][4], float (&old)[NP][4], float (&uk)[NP], float (&uh)[NP],
+                                         int tile, int cl, bool active, bool want_old, int J, int Nr, int Gr, int gy,
+                                         bool zero, const float *__restrict__ z, const float *__restrict__ Din) {
+  const int N = PS ? PS * NP : Nr, G = GS ? GS : Gr;
+  const int P = N / NP, R = 4 * N * G;
+  const int g = gy / P, ch = gy % P, m0 = ch * NP;
+  const int N2 = N / 2;
+  const int offL = cl > 0 ? -1 : (T - 1) - R * T;
+  const int offR = cl < T - 1 ? 1 : R * T - (T - 1);
+  const int j = tile * T + cl;
+  const size_t off = ((size_t)tile * R + (size_t)(g * N + m0) * 4) * T + cl;
+  const float *__restrict__ zb = z + off;
+  const float *__restrict__ db = Din + off;
+#pragma unroll
+  for (int i = 0; i < NP; i++) {
+    const int m = m0 + i;
+#pragma unroll
+    for (int p = 0; p < 4; p++) {
+      zr[i][p] = active ? zb[(i * 4 + p) * T] : 0.f;
+      old[i][p] = (active && want_old && !zero) ? db[(i * 4 + p) * T] : 0.f;
+    }
+    uk[i] = 0.f;
+    uh[i] = 0.f;
+    if (active && !zero) {
+      if (m >= N2) {
+        if (j > 0) {
+          uk[i] = db[offL + (i * 4 + 1) * T];
+          uh[i] = db[offL + (i * 4 + 3) * T];
+        }
+      } else if (j < J - 1) {
+        uk[i] = db[offR + (i * 4 + 0) * T];
+        uh[i] = db[offR + (i * 4 + 2) * T];
+      }
+    }
+  }
+}
+
+// Structured FP32 cell solve of the thread's (cell, group, NP angles):
+// t = z + Cin u, y = sum_m w t, s = Mp y, o = t + Linv s (the arithmetic of
+// tiled_compute).  Three block barriers; y_s / yr_s / s_s as there.
+template <int T, int NP, int PS, int GS>
+__device__ __forceinline__ void ms2_solve(float (&o)[NP][4], const float (&zr)[NP][4], const float (&uk)[NP],
+                                          const float (&uh)[NP], bool active, int tau, int Nr, int Gr, int cl, int gy,
+                                          const float *Linv, const float *Cin, const float *Mp, const float *w,
+                                          float *y_s, float *yr_s, float *s_s) {
+  const int N = PS ? PS * NP : Nr, G = GS ? GS : Gr;
+  const int P = N / NP, G4 = 4 * G;
+  const int g = gy / P, ch = gy % P, m0 = ch * NP;
+  const int tb = tau * G * N;
+  float y0 = 0.f, y1 = 0.f, y2 = 0.f, y3 = 0.f;
+#pragma unroll
+  for (int i = 0; i < NP; i++)
+#pragma unroll
+    for (int p = 0; p < 4; p++) o[i][p] = 0.f;
+  if (active) {
+#pragma unroll
+    for (int i = 0; i < NP; i++) {
+      const int m = m0 + i;
+      const float4 *C4 = reinterpret_cast<const float4 *>(Cin + (tb + g * N + m) * 8);
+      const float4 ca = C4[0], cb = C4[1];
+      o[i][0] = fmaf(ca.y, uh[i], fmaf(ca.x, uk[i], zr[i][0]));
+      o[i][1] = fmaf(ca.w, uh[i], fmaf(ca.z, uk[i], zr[i][1]));
+      o[i][2] = fmaf(cb.y, uh[i], fmaf(cb.x, uk[i], zr[i][2]));
+      o[i][3] = fmaf(cb.w, uh[i], fmaf(cb.z, uk[i], zr[i][3]));
+      const float wm = w[m];
+      y0 = fmaf(wm, o[i][0], y0);
+      y1 = fmaf(wm, o[i][1], y1);
+      y2 = fmaf(wm, o[i][2], y2);
+      y3 = fmaf(wm, o[i][3], y3);
+    }
+  }
+  {
+    float *ys = y_s + (gy * 4) * T + cl;
+    ys[0] = y0;
+    ys[T] = y1;
+    ys[2 * T] = y2;
+    ys[3 * T] = y3;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = ch; q < 4; q += P) {
+    float v = y_s[((g * P) * 4 + q) * T + cl];
+#pragma unroll
+    for (int k = 1; k < P; k++) v += y_s[((g * P + k) * 4 + q) * T + cl];
+    yr_s[(g * 4 + q) * T + cl] = v;
+  }
+  __syncthreads();
+  if (active)
+#pragma unroll
+    for (int q = ch; q < 4; q += P) {
+      const float *M = Mp + tau * G4 * G4 + (g * 4 + q) * G4;
+      float v = 0.f;
+#pragma unroll
+      for (int k = 0; k < G4; k++) v = fmaf(M[k], yr_s[k * T + cl], v);
+      s_s[(g * 4 + q) * T + cl] = v;
+    }
+  __syncthreads();
+  if (active) {
+    const float s0 = s_s[(g * 4 + 0) * T + cl], s1 = s_s[(g * 4 + 1) * T + cl];
+    const float s2 = s_s[(g * 4 + 2) * T + cl], s3 = s_s[(g * 4 + 3) * T + cl];
+#pragma unroll
+    for (int i = 0; i < NP; i++) {
+      const float4 *L4 = reinterpret_cast<const float4 *>(Linv + (tb + g * N + m0 + i) * 16);
+#pragma unroll
+      for (int p = 0; p < 4; p++) {
+        const float4 L = L4[p];
+        o[i][p] = fmaf(L.w, s3, fmaf(L.z, s2, fmaf(L.y, s1, fmaf(L.x, s0, o[i][p]))));
+      }
+    }
+  }
+}
+
+// The downstream edge values of a cell (mu > 0: corners 1, 3; mu < 0: corners
+// 0, 2) at edge[((g N + m) 2 + q)] (the run's outside neighbours).
+template <int NP>
+__device__ __forceinline__ void ms2_put_edges(float *edge, const float (&o)[NP][4], int N, int g, int m0) {
+#pragma unroll
+  for (int i = 0; i < NP; i++) {
+    const int m = m0 + i;
+    float *d = edge + (g * N + m) * 2;
+    if (m >= N / 2) {
+      d[0] = o[i][1];
+      d[1] = o[i][3];
+    } else {
+      d[0] = o[i][0];
+      d[1] = o[i][2];
+    }
+  }
+}
+
+// sum of squared changes
+template <int NP>
+__device__ __forceinline__ float ms2_dist2(const float (&a)[NP][4], const float (&b)[NP][4]) {
+  float e2 = 0.f;
+#pragma unroll
+  for (int i = 0; i < NP; i++)
+#pragma unroll
+    for (int p = 0; p < 4; p++) {
+      const float d = a[i][p] - b[i][p];
+      e2 = fmaf(d, d, e2);
+    }
+  return e2;
+}
+
+struct Ms2Args {
+  int J, N, G, t0, t1;
+  const int32_t *__restrict__ type;
+  const float *Linv, *Cin, *Mp, *w;
+  const float *__restrict__ z;
+  float *y_s, *yr_s, *s_s, *ring, *halo;
+};
+
+// One sweep over the block's run (delta_in -> delta_out); returns the thread's
+// sum of squared changes.
+template <int T, int NP, int PS, int GS>
+__device__ float ms2_pass1(const Ms2Args &a, int cl, int gy, bool zero, const float *__restrict__ Din,
+                           float *__restrict__ Dout) {
+  const int N = PS ? PS * NP : a.N, G = GS ? GS : a.G;
+  const int P = N / NP, R = 4 * N * G;
+  const int g = gy / P, m0 = (gy % P) * NP;
+  float e2 = 0.f;
+  for (int k = a.t0; k < a.t1; k++) {
+    float zr[NP][4], old[NP][4], uk[NP], uh[NP], o[NP][4];
+    const int j = k * T + cl;
+    const bool act = j < a.J;
+    const int tau = act ? a.type[j] : 0;
+    ms2_load<T, NP, PS, GS>(zr, old, uk, uh, k, cl, act, true, a.J, N, G, gy, zero, a.z, Din);
+    ms2_solve<T, NP, PS, GS>(o, zr, uk, uh, act, tau, N, G, cl, gy, a.Linv, a.Cin, a.Mp, a.w, a.y_s, a.yr_s,
+                             a.s_s);
+    if (act) {
+      e2 += ms2_dist2<NP>(o, old);
+      float *__restrict__ ob = Dout + ((size_t)k * R + (size_t)(g * N + m0) * 4) * T + cl;
+#pragma unroll
+      for (int i = 0; i < NP; i++)
+#pragma unroll
+        for (int p = 0; p < 4; p++) ob[(i * 4 + p) * T] = o[i][p];
+    }
+  }
+  return e2;
+}
+
+// Two sweeps over the block's run (delta_in -> delta_out = delta^{i+2}); the
+// threads' sums of squared changes of both sweeps in ea, eb.  delta^{i+1} of a
+// tile is kept whole in a ring slot [4NG][T] (for the second sweep's norm and
+// its inflows); z is read again for the second sweep (a cache hit: the tile
+// was read one step earlier).
+template <int T, int NP, int PS, int GS>
+__device__ void ms2_pass2(const Ms2Args &a, int cl, int gy, bool zero, const float *__restrict__ Din,
+                          float *__restrict__ Dout, float &ea, float &eb) {
+  const int N = PS ? PS * NP : a.N, G = GS ? GS : a.G;
+  const int J = a.J, P = N / NP, R = 4 * N * G, NG2 = 2 * N * G;
+  const int g = gy / P, m0 = (gy % P) * NP;
+  const int ntiles = (J + T - 1) / T;
+  float *halo_l = a.halo, *halo_r = a.halo + NG2;
+  // delta^{i+1} of the cells next to the run: thread column T-1 takes cell
+  // t0*T - 1 (last column of tile t0-1), column 0 takes cell t1*T (tile t1)
+  {
+    const bool hl = cl == T - 1 && a.t0 > 0, hr = cl == 0 && a.t1 < ntiles;
+    const bool act = hl || hr;
+    const int tile = hl ? a.t0 - 1 : (hr ? a.t1 : a.t0);
+    const int tau = act ? a.type[tile * T + cl] : 0;
+    float zr[NP][4], old[NP][4], uk[NP], uh[NP], o[NP][4];
+    ms2_load<T, NP, PS, GS>(zr, old, uk, uh, tile, cl, act, false, J, N, G, gy, zero, a.z, Din);
+    ms2_solve<T, NP, PS, GS>(o, zr, uk, uh, act, tau, N, G, cl, gy, a.Linv, a.Cin, a.Mp, a.w, a.y_s, a.yr_s,
+                             a.s_s);
+    if (hl) ms2_put_edges<NP>(halo_l, o, N, g, m0);
+    if (hr) ms2_put_edges<NP>(halo_r, o, N, g, m0);
+  }
+  // ring slots of tiles k (cur), k-1 (prv) and k-2 (pp)
+  float *cur = a.ring, *prv = a.ring + R * T, *pp = a.ring + 2 * R * T;
+  for (int k = a.t0; k <= a.t1; k++) {
+    if (k < a.t1) {  // sweep i+1 on tile k
+      float zr[NP][4], old[NP][4], uk[NP], uh[NP], o1[NP][4];
+      const int j = k * T + cl;
+      const bool act = j < J;
+      const int tau = act ? a.type[j] : 0;
+      ms2_load<T, NP, PS, GS>(zr, old, uk, uh, k, cl, act, true, J, N, G, gy, zero, a.z, Din);
+      ms2_solve<T, NP, PS, GS>(o1, zr, uk, uh, act, tau, N, G, cl, gy, a.Linv, a.Cin, a.Mp, a.w, a.y_s, a.yr_s,
+                               a.s_s);
+      if (act) {
+        ea += ms2_dist2<NP>(o1, old);
+        float *sl = cur + ((g * N + m0) * 4) * T + cl;
+#pragma unroll
+        for (int i = 0; i < NP; i++)
+#pragma unroll
+          for (int p = 0; p < 4; p++) sl[(i * 4 + p) * T] = o1[i][p];
+      }
+    }
+    __syncthreads();  // the ring slot of tile k is complete
+    if (k > a.t0) {   // sweep i+2 on tile k-1: inflows from delta^{i+1} of the neighbours
+      const int kk = k - 1, j = kk * T + cl;
+      const bool act = j < J;
+      const int tau = act ? a.type[j] : 0;
+      float zr[NP][4], o1[NP][4], uk[NP], uh[NP], o2[NP][4];
+      {
+        float dummy[NP][4], dk[NP], dh[NP];
+        ms2_load<T, NP, PS, GS>(zr, dummy, dk, dh, kk, cl, act, false, J, N, G, gy, true, a.z, Din);
+      }
+#pragma unroll
+      for (int i = 0; i < NP; i++) {
+        const int m = m0 + i, r0 = (g * N + m) * 4;
+#pragma unroll
+        for (int p = 0; p < 4; p++) o1[i][p] = act ? prv[(r0 + p) * T + cl] : 0.f;
+        const float *src = nullptr;
+        int st = 2 * T;
+        if (m >= N / 2) {  // corners 1, 3 of cell j - 1
+          if (j > 0) {
+            if (cl > 0) src = prv + (r0 + 1) * T + cl - 1;
+            else if (kk > a.t0) src = pp + (r0 + 1) * T + T - 1;
+            else src = halo_l + (g * N + m) * 2, st = 1;
+          }
+        } else if (j < J - 1) {  // corners 0, 2 of cell j + 1
+          if (cl < T - 1) src = prv + r0 * T + cl + 1;
+          else if (kk + 1 < a.t1) src = cur + r0 * T;
+          else src = halo_r + (g * N + m) * 2, st = 1;
+        }
+        uk[i] = (act && src) ? src[0] : 0.f;
+        uh[i] = (act && src) ? src[st] : 0.f;
+      }
+      ms2_solve<T, NP, PS, GS>(o2, zr, uk, uh, act, tau, N, G, cl, gy, a.Linv, a.Cin, a.Mp, a.w, a.y_s, a.yr_s,
+                               a.s_s);
+      if (act) {
+        eb += ms2_dist2<NP>(o2, o1);
+        float *__restrict__ ob = Dout + ((size_t)kk * R + (size_t)(g * N + m0) * 4) * T + cl;
+#pragma unroll
+        for (int i = 0; i < NP; i++)
+#pragma unroll
+          for (int p = 0; p < 4; p++) ob[(i * 4 + p) * T] = o2[i][p];
+      }
+    }
+    float *t = pp;  // rotate: the slot of tile k-2 takes tile k+1
+    pp = prv;
+    prv = cur;
+    cur = t;
+  }
+}
+
+// OCC: resident blocks per SM the register allocation is built for (the
+// block size is T * PS * GS threads when known at compile time, else <= 256).
+template <int T, int NP, int PS, int GS, int OCC>
+__global__ void __launch_bounds__((PS && GS) ? T * PS * GS : 256, OCC) k_mx_inner_ms2(int J, int N, int G, int n_types, int stage,
+                                                      const int32_t *__restrict__ type, const float *Linv_g,
+                                                      const float *Cin_g, const float *Mp_g, const float *w_g,
+                                                      const float *__restrict__ z, float *D0, float *D1,
+                                                      DevState *ds, double *__restrict__ partials, unsigned *gbar,
+                                                      double *e_hist, cudaGraphConditionalHandle cond, int use_cond,
+                                                      int max_sweeps) {
+  extern __shared__ __align__(16) float smr[];
+  __shared__ double red[8];
+  __shared__ DevState sd;
+  __shared__ int s_ok, s_roll;
+  const int P = N / NP, G4 = 4 * G, NG2 = 2 * N * G;
+  const int cl = threadIdx.x, gy = threadIdx.y;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int nthr = blockDim.x * blockDim.y;
+  if (tid == 0) sd = *ds;
+  __syncthreads();
+  if (sd.done) return;  // uniform across the grid
+  Ms2Args a;
+  a.J = J;
+  a.N = N;
+  a.G = G;
+  a.type = type;
+  a.z = z;
+  a.y_s = smr;
+  a.yr_s = a.y_s + (size_t)G * P * 4 * T;
+  a.s_s = a.yr_s + (size_t)G4 * T;
+  a.ring = a.s_s + (size_t)G4 * T;
+  a.halo = a.ring + (size_t)3 * 4 * N * G * T;
+  a.Linv = Linv_g;
+  a.Cin = Cin_g;
+  a.Mp = Mp_g;
+  a.w = w_g;
+  if (stage) {
+    stage_tables(a.halo + 2 * NG2, n_types, N, G, tid, nthr, a.Linv, a.Cin, a.Mp, a.w);
+    __syncthreads();
+  }
+  const int ntiles = (J + T - 1) / T;
+  a.t0 = (int)((long long)blockIdx.x * ntiles / gridDim.x);
+  a.t1 = (int)((long long)(blockIdx.x + 1) * ntiles / gridDim.x);
+  bool failed = false;
+  for (int sw = 0, pass = 0;; pass++) {
+    const int ns = max_sweeps - sw >= 2 ? 2 : 1;
+    const bool zero = sd.refine || sd.blk_i == 0;
+    const float *__restrict__ Din = sd.dcur ? D1 : D0;
+    float *__restrict__ Dout = sd.dcur ? D0 : D1;
+    float ea = 0.f, eb = 0.f;
+    if (ns == 2) ms2_pass2<T, NP, PS, GS>(a, cl, gy, zero, Din, Dout, ea, eb);
+    else ea = ms2_pass1<T, NP, PS, GS>(a, cl, gy, zero, Din, Dout);
+    const double ba = block_reduce_fixed(ea, red, tid, nthr);
+    const double bb = block_reduce_fixed(eb, red, tid, nthr);
+    double *part = partials + (size_t)(pass & 1) * 2 * gridDim.x;
+    if (tid == 0) {
+      part[blockIdx.x] = ba;
+      part[gridDim.x + blockIdx.x] = bb;
+      s_ok = grid_barrier(gbar, gridDim.x);
+    }
+    __syncthreads();
+    if (!s_ok) {
+      failed = true;
+      break;
+    }
+    const double ta = block_sum_fixed(part, gridDim.x, red);
+    const double tb = ns == 2 ? block_sum_fixed(part + gridDim.x, gridDim.x, red) : 0.0;
+    if (tid == 0) {
+      double *eh = blockIdx.x == 0 ? e_hist : nullptr;
+      finish_mixed(&sd, eh, sqrt(ta), cond, 0);
+      s_roll = 0;
+      if (ns == 2) {
+        if (sd.done || sd.refine) {
+          s_roll = 1;  // the inner block ends at sweep i+1
+        } else {
+          finish_mixed(&sd, eh, sqrt(tb), cond, 0);
+          if (!sd.inplace) sd.dcur ^= 1;  // one buffer flip per pass: delta^{i+2} is in Dout
+        }
+      }
+    }
+    __syncthreads();
+    if (s_roll) {  // delta^{i+1} into Dout (delta^i is untouched in Din)
+      ms2_pass1<T, NP, PS, GS>(a, cl, gy, zero, Din, Dout);
+      break;
+    }
+    sw += ns;
+    if (sd.done || sd.refine || sw >= max_sweeps) break;  // uniform: every block holds the same state
+  }
+  if (blockIdx.x == 0 && tid == 0) {
+    if (failed) {
+      sd.status = OCI_E_TIMEOUT;
+      sd.done = 1;
+      sd.refine = 0;
+    }
+    *ds = sd;
+    if (use_cond) {
+      if (sd.done) cudaGraphSetConditional(cond, 0);
+      if (sd.cond_ref) cudaGraphSetConditional((cudaGraphConditionalHandle)sd.cond_ref, sd.refine);
+    }
+  }
+}
+
+size_t mx_ms2_smem(const Handle &h, int T, int P, bool stage) {
+  const size_t G = h.G, N = h.N;
+  return ((size_t)T * (G * P * 4 + 8 * G) + 3 * 4 * N * G * T + 4 * N * G) * 4 +
+         (stage ? mx_tables_floats(h) * 4 + 16 : 0);
+}
+
+template <int T, int NP, int PS, int GS, int OCC>
+static void launch_ms2(Handle &h, int P, cudaGraphConditionalHandle cond, int use_cond, int max_sweeps) {
+  const bool stage = mx_tables_floats(h) * 4 <= 64 * 1024;
+  const size_t smem = mx_ms2_smem(h, T, P, stage);
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mx_inner_ms2<T, NP, PS, GS, OCC>, T * h.G * P, smem);
+  const int ntiles = (h.J + T - 1) / T;
+  const int grid = std::min(sms * (per > 0 ? per : 1), ntiles);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(T, h.G * P);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = h.stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;  // all blocks resident: they wait on one another
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k_mx_inner_ms2<T, NP, PS, GS, OCC>, h.J, h.N, h.G, h.tt.n_types, (int)stage,
+                     (const int32_t *)h.type, (const float *)h.tt.Linv32, (const float *)h.tt.Cin32,
+                     (const float *)h.tt.Mp32, (const float *)h.w32, (const float *)h.z32, h.delta[0], h.delta[1],
+                     h.ds, h.partials, h.gbar, h.e_hist, cond, use_cond, max_sweeps);
+}
+
+// S16, one group (the slab workloads): fully specialised, with registers for
+// 2 blocks of 256 / 4 of 128 threads per SM, or (kMxTiled2Occ) for 3 of 256 /
+// 5 of 128; everything else generic (2 blocks of up to 256 threads)
+static void launch_ms2_any(Handle &h, cudaGraphConditionalHandle cond, int use_cond, int max_sweeps) {
+  const int T = h.mx_cb, P = h.mx_P, np = h.N / P;
+  const bool s16 = h.N == 16 && h.G == 1, occ = h.mx_kind == kMxTiled2Occ;
+#define OCI_MS2(TT, NPP, OC, OCX)                                                              \
+  do {                                                                                         \
+    if (s16 && occ) launch_ms2<TT, NPP, 16 / NPP, 1, OCX>(h, P, cond, use_cond, max_sweeps);   \
+    else if (s16) launch_ms2<TT, NPP, 16 / NPP, 1, OC>(h, P, cond, use_cond, max_sweeps);      \
+    else launch_ms2<TT, NPP, 0, 0, 2>(h, P, cond, use_cond, max_sweeps);                       \
+  } while (0)
+  if (T == 32) {
+    if (np == 2) OCI_MS2(32, 2, 2, 3);
+    else OCI_MS2(32, 4, 4, 5);
+  } else {
+    if (np == 2) OCI_MS2(64, 2, 1, 1);  // 512 threads: not an S16 shape (no candidate)
+    else OCI_MS2(64, 4, 2, 3);
+  }
+#undef OCI_MS2
+}
+
 template <int T, int NP>
 static int tp_grid(const Handle &h, int P, size_t smem) {
   int dev = 0, sms = 0, per = 0;
@@ -1804,7 +2262,9 @@ int mx_partials(const Handle &h) {
   }
   int cb, P;
   mx_shape(h, cb, P);
-  return (h.J + cb - 1) / cb;
+  const int ntiles = (h.J + cb - 1) / cb;
+  // two sweeps x two parities per block
+  return (h.mx_kind == kMxTiled2 || h.mx_kind == kMxTiled2Occ) ? 4 * ntiles : ntiles;
 }
 
 // One inner sweep including its norm reduction, stop rule and refinement
@@ -1843,6 +2303,11 @@ void launch_mx_inner(Handle &h, cudaGraphConditionalHandle cond, int use_cond) {
       else OCI_MX_TB(64, 8);
     }
 #undef OCI_MX_TB
+    return;
+  }
+  if (h.mx_kind == kMxTiled2 || h.mx_kind == kMxTiled2Occ) {  // cooperative; in the graph passes of two sweeps
+    const int ms = h.mx_tune_sweeps > 0 ? h.mx_tune_sweeps : (use_cond && h.mx_multi) ? (1 << 30) : 1;
+    launch_ms2_any(h, cond, use_cond, ms);
     return;
   }
   if (h.mx_kind == kMxTiledP && ((use_cond && h.mx_multi) || h.mx_tune_sweeps > 0)) {
@@ -1990,7 +2455,12 @@ int mx_set_attributes() {
                       (const void *)k_mx_inner_ms<64, 8>, (const void *)k_mx_rb<32, 2>,
                       (const void *)k_mx_rb<32, 4>, (const void *)k_mx_rb<32, 8>,
                       (const void *)k_mx_rb<64, 2>, (const void *)k_mx_rb<64, 4>,
-                      (const void *)k_mx_rb<64, 8>};
+                      (const void *)k_mx_rb<64, 8>, (const void *)k_mx_inner_ms2<32, 2, 0, 0, 2>,
+                      (const void *)k_mx_inner_ms2<32, 4, 0, 0, 2>, (const void *)k_mx_inner_ms2<64, 2, 0, 0, 2>,
+                      (const void *)k_mx_inner_ms2<64, 4, 0, 0, 2>, (const void *)k_mx_inner_ms2<32, 2, 8, 1, 2>,
+                      (const void *)k_mx_inner_ms2<32, 4, 4, 1, 4>, (const void *)k_mx_inner_ms2<64, 2, 8, 1, 1>,
+                      (const void *)k_mx_inner_ms2<64, 4, 4, 1, 2>, (const void *)k_mx_inner_ms2<32, 2, 8, 1, 3>,
+                      (const void *)k_mx_inner_ms2<32, 4, 4, 1, 5>, (const void *)k_mx_inner_ms2<64, 4, 4, 1, 3>};
   for (const void *k : ks) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(FP32 inner sweep)");

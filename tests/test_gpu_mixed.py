@@ -125,7 +125,7 @@ def test_tensor_core_full_size_matches_fp64_path(prec):
         assert rel(b.psi(), a.psi()) < 1e-10
 
 
-@pytest.mark.parametrize("kernel", ["plain", "tma", "reg", "tiled", "tiledp", "tiledb"])
+@pytest.mark.parametrize("kernel", ["plain", "tma", "reg", "tiled", "tiledp", "tiledb", "two"])
 def test_fp32_inner_kernels_all_match_oracle(kernel, monkeypatch):
     """Every FP32 inner-sweep kernel (plain, tiles staged by 2D TMA bulk copies,
     angles split over threads with t in registers, and that on tile-major
@@ -138,7 +138,7 @@ def test_fp32_inner_kernels_all_match_oracle(kernel, monkeypatch):
     with oci.Solver(p, precision=oci.FP32_IR) as s:
         info = s.info()
         assert info["inner_kernel"] == {"plain": 0, "tma": 1, "reg": 3, "tiled": 4, "tiledp": 5,
-                                        "tiledb": 6}[kernel]
+                                        "tiledb": 6, "two": 9}[kernel]
         for k in range(2):
             r = o.step(OCI)
             st = s.step()
@@ -151,7 +151,9 @@ def test_fp32_inner_kernels_all_match_oracle(kernel, monkeypatch):
                                           ("tiled", "32,2"), ("tiledp", "32,8"), ("tiledp", "64,4"),
                                           ("tiledp", "64,2"), ("tiledp", "128,2"), ("tiledb", "32,8"),
                                           ("tiledb", "64,4"),
-                                          ("tiledb", "64,2"), ("tiledb", "32,2")])
+                                          ("tiledb", "64,2"), ("tiledb", "32,2"), ("two", "32,8"),
+                                          ("two", "32,4"), ("two", "64,4"), ("twoocc", "32,8"),
+                                          ("twoocc", "32,4"), ("twoocc", "64,4")])
 def test_fp32_register_inner_shapes_match_oracle(kernel, shape, monkeypatch):
     """Register FP32 inner sweeps (row layout, and tile-major with T = 32 or 64
     cells) at each angle split (P = 8, 4, 2 chunks of S16 angles, G = 1) on a
@@ -164,7 +166,7 @@ def test_fp32_register_inner_shapes_match_oracle(kernel, shape, monkeypatch):
         info = s.info()
         cb, P = (int(x) for x in shape.split(","))
         assert (info["inner_kernel"], info["cells_per_block"], info["angle_chunks"]) == (
-            {"reg": 3, "tiled": 4, "tiledp": 5, "tiledb": 6}[kernel], cb, P)
+            {"reg": 3, "tiled": 4, "tiledp": 5, "tiledb": 6, "two": 9, "twoocc": 10}[kernel], cb, P)
         for k in range(2):
             r = o.step(OCI)
             st = s.step()
@@ -194,6 +196,62 @@ def test_fp32_multi_sweep_launch_matches_single_sweep(monkeypatch):
         r = o.step(OCI)
         assert abs(res["1"][0][k] - r["iters"]) <= 2
     assert rel(res["1"][2], r["phi"]) < 1e-10
+
+
+@pytest.mark.parametrize("kernel,J,shape", [("two", 5000, "64,4"), ("two", 40000, "64,4"), ("two", 40000, "32,8"),
+                                            ("two", 333, "32,4"), ("two", 64, "32,8"), ("twoocc", 40000, "32,4"),
+                                            ("twoocc", 5000, "32,8")])
+def test_fp32_two_sweep_passes_equal_one_sweep_launches(kernel, J, shape, monkeypatch):
+    """Two inner sweeps per pass (each block walks a run of tiles, the second
+    sweep's inflows from the first sweep's values held in shared memory, the
+    run's two outside neighbours recomputed by the block) give bit for bit the
+    iterates, norms and sweep counts of one sweep per launch of the same
+    kernel (default and high-occupancy builds): the cell arithmetic and the
+    order of every sum are the same.  Runs
+    of one tile (J = 5000: 79 tiles, one per block), of several tiles, a
+    partial last tile, and a one-block slab; the first sweep of a pass ending
+    an inner block (refinement or stop) takes the recompute path."""
+    monkeypatch.setenv("OCI_MX_INNER", kernel)
+    monkeypatch.setenv("OCI_SWEEP_SHAPE", shape)
+    p = W.random_slab(33, J, 16, 1).replace(tol=1e-11)
+    res = {}
+    for multi in ("1", "0"):
+        monkeypatch.setenv("OCI_MX_MULTI", multi)
+        with oci.Solver(p, precision=oci.FP32_IR) as s:
+            assert s.info()["inner_kernel"] == {"two": 9, "twoocc": 10}[kernel]
+            sts = [s.step() for _ in range(3)]
+            res[multi] = ([(t["iters"], t["refinements"], t["e"]) for t in sts], s.psi(), s.phi())
+    assert res["1"][0] == res["0"][0]
+    assert np.array_equal(res["1"][1], res["0"][1])
+    o = Oracle(p)
+    for k in range(3):
+        r = o.step(OCI)
+        assert abs(res["1"][0][k][0] - r["iters"]) <= 2
+    assert rel(res["1"][2], r["phi"]) < 1e-10
+
+
+@pytest.mark.parametrize("seed,J,N,G", [(91, 1, 4, 1), (92, 33, 4, 2), (93, 257, 8, 1), (94, 129, 8, 4)])
+def test_fp32_two_sweep_passes_small_and_multigroup(seed, J, N, G, monkeypatch):
+    """Two sweeps per pass on one-cell and partial-tile slabs, few angles and
+    several groups: the sweep counts of the one-sweep persistent kernel and flux
+    within 1e-10 of the FP64 oracle.  Sweeps are within 2 of the oracle's, but
+    for one cell: there plain OCI is exact after one sweep, while each FP32
+    inner block resolves only about 7 digits, so the mixed form needs a
+    refinement sweep per 7 digits (3 extra at tol 1e-11)."""
+    p = W.random_slab(seed, J, N, G).replace(tol=1e-11)
+    res = {}
+    for kern in ("two", "tiledp"):
+        monkeypatch.setenv("OCI_MX_INNER", kern)
+        with oci.Solver(p, precision=oci.FP32_IR) as s:
+            assert s.info()["inner_kernel"] == {"two": 9, "tiledp": 5}[kern]
+            res[kern] = [(s.step(), s.phi()) for _ in range(2)]
+    o = Oracle(p)
+    for k in range(2):
+        r = o.step(OCI)
+        st, phi = res["two"][k]
+        assert st["status"] == 0 and st["iters"] == res["tiledp"][k][0]["iters"]
+        assert abs(st["iters"] - r["iters"]) <= (3 if J == 1 else 2)
+        assert rel(phi, r["phi"]) < 1e-10
 
 
 @pytest.mark.parametrize("seed,J,N,G,shape", [(71, 33, 8, 1, None), (72, 129, 8, 2, None), (73, 1, 4, 1, None),
