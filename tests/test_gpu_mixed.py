@@ -230,7 +230,8 @@ def test_fp32_two_sweep_passes_equal_one_sweep_launches(kernel, J, shape, monkey
     assert rel(res["1"][2], r["phi"]) < 1e-10
 
 
-@pytest.mark.parametrize("seed,J,N,G", [(91, 1, 4, 1), (92, 33, 4, 2), (93, 257, 8, 1), (94, 129, 8, 4)])
+@pytest.mark.parametrize("seed,J,N,G", [(91, 1, 4, 1), (92, 33, 4, 2), (93, 257, 8, 1), (94, 129, 8, 4),
+                                        (95, 100, 4, 1), (96, 1000, 32, 1)])
 def test_fp32_two_sweep_passes_small_and_multigroup(seed, J, N, G, monkeypatch):
     """Two sweeps per pass on one-cell and partial-tile slabs, few angles and
     several groups: the sweep counts of the one-sweep persistent kernel and flux
