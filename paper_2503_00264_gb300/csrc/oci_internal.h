@@ -95,8 +95,8 @@ struct Handle {
   float *z32 = nullptr;                  // [G][N][4][Jp] L~^{-1} r of the last refinement
   float *w32 = nullptr;
   float *mu32 = nullptr;           // mixed forms: FP32 copy of the ordinates
-  int mx_kmax = 64;
-  double mx_theta = 1e-3;
+  int mx_kmax = 128;
+  double mx_theta = 1e-4;
   CUtensorMap tm_z, tm_d[2];          // TMA descriptors of z32 and delta[0/1] ([R][Jp] FP32)
   bool tma_ok = false;                 // tensor maps encoded (4NG <= 256)
   unsigned long long mx_cond_ref = 0;  // IF-node handle of the refinement in the mixed-form graph
