@@ -444,19 +444,29 @@ static int autotune(Handle &h) {
   return OCI_OK;
 }
 
-// Red-black FP32 inner sweep of the mixed form: shapes (tile T cells, P angle
-// chunks) timed one sweep per launch; the Jacobi choice is kept for a switch back.
-// The handle's state is saved and restored around the timing.
+// Red-black FP32 inner sweep of the mixed form: kernels (one sweep per pass,
+// kMxRB; two sweeps per pass, kMxRB2) and shapes (tile T cells, P angle
+// chunks), each timed as one launch of four sweeps (as the graph runs them);
+// the Jacobi choice is kept for a switch back.  The handle's state is saved
+// and restored around the timing.  OCI_MX_RB=1|2 keeps one kernel.
 static int tune_rb(Handle &h) {
   h.mx_jac_kind = h.mx_kind;
   h.mx_jac_cb = h.mx_cb;
   h.mx_jac_P = h.mx_P;
-  std::vector<std::pair<int, int>> cands;
+  struct RbCand {
+    int kind, T, P;
+  };
+  std::vector<RbCand> cands;
+  const char *only = getenv("OCI_MX_RB");
+  const bool stage = mx_tables_floats(h) * 4 <= 64 * 1024;
   for (int T : {32, 64})
     for (int np : {2, 4, 8}) {
       if (h.N % np) continue;
       const int P = h.N / np, thr = (T / 2) * h.G * P;
-      if (thr <= 256 && thr % 32 == 0) cands.emplace_back(T, P);
+      if (thr > 256 || thr % 32) continue;
+      if (!(only && only[0] == '2')) cands.push_back({kMxRB, T, P});
+      if (!(only && only[0] == '1') && np <= 4 && mx_rb2_smem(h, T, P, stage) <= 160 * 1024)
+        cands.push_back({kMxRB2, T, P});
     }
   if (cands.empty()) return set_error("no red-black inner-sweep shape fits this N, G"), OCI_E_INVAL;
   const char *shape = getenv("OCI_SWEEP_SHAPE");
@@ -464,16 +474,19 @@ static int tune_rb(Handle &h) {
     int fT = 0, fP = 0;
     if (sscanf(shape, "%d,%d", &fT, &fP) == 2)
       for (auto &c : cands)
-        if (c.first == fT && c.second == fP) {
-          const auto keep = c;
+        if (c.T == fT && c.P == fP) {
+          const RbCand keep = c;
           cands.assign(1, keep);
           break;
         }
   }
-  h.mx_kind = kMxRB;
+  auto apply = [&](const RbCand &c) {
+    h.mx_kind = c.kind;
+    h.mx_cb = c.T;
+    h.mx_P = c.P;
+  };
   if (cands.size() == 1) {
-    h.mx_cb = cands[0].first;
-    h.mx_P = cands[0].second;
+    apply(cands[0]);
     return OCI_OK;
   }
   const DevState saved = *h.h_ds;
@@ -486,17 +499,20 @@ static int tune_rb(Handle &h) {
   d.max_iter = 0;
   d.k_max = 1 << 30;
   d.theta = 0.0;
-  d.inplace = 1;
-  *h.h_ds = d;
-  CK(cudaMemcpyAsync(h.ds, h.h_ds, sizeof(DevState), cudaMemcpyHostToDevice, h.stream));
   float best = 1e30f;
-  std::pair<int, int> bc = cands[0];
+  RbCand bc = cands[0];
+  const int reps = 4;
   for (auto &c : cands) {
-    h.mx_cb = c.first;
-    h.mx_P = c.second;
+    apply(c);
+    d.inplace = c.kind == kMxRB;
+    *h.h_ds = d;
+    CK(cudaMemcpyAsync(h.ds, h.h_ds, sizeof(DevState), cudaMemcpyHostToDevice, h.stream));
+    h.mx_tune_sweeps = 1;
     launch_mx_inner(h, cudaGraphConditionalHandle{}, 0);
     CK(cudaEventRecord(h.ev0, h.stream));
-    for (int r = 0; r < 3; r++) launch_mx_inner(h, cudaGraphConditionalHandle{}, 0);
+    h.mx_tune_sweeps = reps;
+    launch_mx_inner(h, cudaGraphConditionalHandle{}, 0);
+    h.mx_tune_sweeps = 0;
     CK(cudaEventRecord(h.ev1, h.stream));
     CK(cudaEventSynchronize(h.ev1));
     CK(cudaGetLastError());
@@ -507,9 +523,8 @@ static int tune_rb(Handle &h) {
       bc = c;
     }
   }
-  h.mx_cb = bc.first;
-  h.mx_P = bc.second;
-  h.tune_us = 1e3 * best / 3;
+  apply(bc);
+  h.tune_us = 1e3 * best / reps;
   *h.h_ds = saved;
   CK(cudaMemcpyAsync(h.ds, h.h_ds, sizeof(DevState), cudaMemcpyHostToDevice, h.stream));
   CK(cudaStreamSynchronize(h.stream));

@@ -192,6 +192,8 @@ constexpr int kMxPlain = 0, kMxTma = 1, kMxReg = 3, kMxTiled = 4, kMxTiledP = 5,
 constexpr int kSweepReg64 = 8;  // autotuner candidate kind of the FP64 register sweep
 constexpr int kMxTiled2 = 9;    // tile-major, two inner sweeps per pass (temporal blocking)
 constexpr int kMxTiled2Occ = 10;  // the same built for more resident blocks per SM (S16, one group)
+constexpr int kMxRB2 = 11;        // red-black ordering, two sweeps per pass (colour-ordered tiles)
+size_t mx_rb2_smem(const Handle &h, int T, int P, bool stage);
 size_t mx_ms2_smem(const Handle &h, int T, int P, bool stage);
 size_t mx_tb_smem(const Handle &h, int T, int P, bool stage);
 size_t mx_tables_floats(const Handle &h);

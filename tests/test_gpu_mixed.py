@@ -255,15 +255,25 @@ def test_fp32_two_sweep_passes_small_and_multigroup(seed, J, N, G, monkeypatch):
         assert rel(phi, r["phi"]) < 1e-10
 
 
-@pytest.mark.parametrize("seed,J,N,G,shape", [(71, 33, 8, 1, None), (72, 129, 8, 2, None), (73, 1, 4, 1, None),
-                                              (74, 300, 16, 1, None), (75, 257, 16, 1, "32,4"),
-                                              (76, 300, 16, 1, "64,2"), (77, 95, 4, 2, "32,2")])
-def test_fp32_red_black_matches_oracle(seed, J, N, G, shape, monkeypatch):
-    """Red-black ordering of the mixed form (FP32 correction updated in place,
-    even cells then odd cells per inner sweep, colour-ordered tile-major layout)
-    against the oracle's FP64 red-black sweep: sweep counts within 2 (3 for
-    J = 1), flux within 1e-10; forced shapes cover both tile widths."""
+RB_CASES = [(71, 33, 8, 1, None), (72, 129, 8, 2, None), (73, 1, 4, 1, None), (74, 300, 16, 1, None),
+            (75, 257, 16, 1, "32,4"), (76, 300, 16, 1, "64,2"), (77, 95, 4, 2, "32,2"), (78, 5000, 16, 1, "64,4"),
+            (79, 65, 16, 1, "32,8")]
+
+
+@pytest.mark.parametrize("kernel", ["1", "2"])
+@pytest.mark.parametrize("seed,J,N,G,shape", RB_CASES)
+def test_fp32_red_black_matches_oracle(seed, J, N, G, shape, kernel, monkeypatch):
+    """Red-black ordering of the mixed form (even cells then odd cells per
+    inner sweep, colour-ordered tile-major layout; kernel 1: one sweep per pass,
+    in place, grid barrier between the colours; kernel 2: two sweeps per pass
+    over the correction, each block walking a run of tiles) against the
+    oracle's FP64 red-black sweep: sweep counts within 2 (3 for J = 1), flux
+    within 1e-10; forced shapes cover both tile widths, one-tile runs
+    (J = 5000 at 64-cell tiles) and an odd partial last tile."""
     from oracle import RB
+    if kernel == "2" and shape == "64,2":
+        pytest.skip("two sweeps per pass keep at most 4 angles per thread")
+    monkeypatch.setenv("OCI_MX_RB", kernel)
     if shape:
         monkeypatch.setenv("OCI_SWEEP_SHAPE", shape)
     p = W.random_slab(seed, J, N, G).replace(tol=1e-11)
@@ -271,7 +281,7 @@ def test_fp32_red_black_matches_oracle(seed, J, N, G, shape, monkeypatch):
     with oci.Solver(p, precision=oci.FP32_IR) as s:
         s.set_ordering(oci.ORDER_RED_BLACK)
         info = s.info()
-        assert info["inner_kernel"] == 7
+        assert info["inner_kernel"] == {"1": 7, "2": 11}[kernel]
         if shape:
             assert (info["cells_per_block"], info["angle_chunks"]) == tuple(int(x) for x in shape.split(","))
         for k in range(2):
@@ -281,10 +291,30 @@ def test_fp32_red_black_matches_oracle(seed, J, N, G, shape, monkeypatch):
             assert rel(s.phi(), r["phi"]) < 1e-10
             assert rel(s.psi(), r["Psi"]) < 1e-10
         s.set_ordering(oci.ORDER_JACOBI)  # back to the tuned Jacobi inner sweep
-        assert s.info()["inner_kernel"] != 7
+        assert s.info()["inner_kernel"] not in (7, 11)
         r = o.step(OCI)
         st = s.step()
         assert abs(st["iters"] - r["iters"]) <= 2 and rel(s.phi(), r["phi"]) < 1e-10
+
+
+@pytest.mark.parametrize("J,shape", [(40000, "32,8"), (40000, "64,4"), (5000, "32,4"), (333, "64,8"), (65, "32,4")])
+def test_fp32_red_black_two_sweep_passes_equal_one_sweep_launches(J, shape, monkeypatch):
+    """Red-black sweeps two per pass (graph) and one per launch (host-driven)
+    of the same kernel give the same iterates bit for bit, the same norms and
+    sweep counts: the cell arithmetic and the order of every sum agree."""
+    monkeypatch.setenv("OCI_MX_RB", "2")
+    monkeypatch.setenv("OCI_SWEEP_SHAPE", shape)
+    p = W.random_slab(34, J, 16, 1).replace(tol=1e-11)
+    res = {}
+    for multi in ("1", "0"):
+        monkeypatch.setenv("OCI_MX_MULTI", multi)
+        with oci.Solver(p, precision=oci.FP32_IR) as s:
+            s.set_ordering(oci.ORDER_RED_BLACK)
+            assert s.info()["inner_kernel"] == 11
+            sts = [s.step() for _ in range(3)]
+            res[multi] = ([(t["iters"], t["refinements"], t["e"]) for t in sts], s.psi())
+    assert res["1"][0] == res["0"][0]
+    assert np.array_equal(res["1"][1], res["0"][1])
 
 
 def test_fp32_red_black_full_size_fewer_sweeps_same_answer():
