@@ -22,12 +22,13 @@ namespace oci {
     if (e_ != cudaSuccess) return cuda_fail(e_, #call);  \
   } while (0)
 
-constexpr int kPad = 128;
+constexpr int kPad = 128;     // slab padding (multiple of every tile size and of the 32-cell carry block)
 constexpr int kMinTile = 8;  // smallest tile (cells) of any sweep candidate
 // refinement schedule of the mixed form (as the single-slab FP32 form): refine
-// after kBatchMxKmax inner sweeps or once e fell below kBatchMxTheta of the block's first
+// after k_max inner sweeps or once e fell below theta of the block's first;
+// OCI_MX_KMAX / OCI_MX_THETA override
 constexpr int kBatchMxKmax = 64;
-constexpr double kBatchMxTheta = 1e-3;  // slab padding (multiple of every tile size and of the 32-cell carry block)
+constexpr double kBatchMxTheta = 1e-3;
 
 // [J][K] host/device rows -> class SoA column block: dst[k*stride + j], j < J only.
 __global__ void k_bt_in(int J, int stride, int K, const double *__restrict__ src, double *__restrict__ dst) {
@@ -487,6 +488,13 @@ static int batch_setup(const oci_problem *probs, int n, Batch &B) {
 static inline int slot(const Batch &B, int s) { return B.cls[B.slab_class[s]].slab0 + B.slab_local[s]; }
 
 static int batch_step(Batch &B, oci_stats *st) {
+  int kmax = kBatchMxKmax;
+  double theta = kBatchMxTheta;
+  {
+    const char *km = getenv("OCI_MX_KMAX"), *th = getenv("OCI_MX_THETA");
+    if (km) kmax = std::max(1, atoi(km));
+    if (th) theta = atof(th);
+  }
   cudaStream_t s = B.stream;
   for (int i = 0; i < B.n; i++) {
     DevState &d = B.h_ds[slot(B, i)];
@@ -501,9 +509,9 @@ static int batch_step(Batch &B, oci_stats *st) {
     d.blk_i = 0;
     d.refine = 0;
     d.applied = 0;
-    d.k_max = kBatchMxKmax;
+    d.k_max = kmax;
     d.n_refine = 0;
-    d.theta = kBatchMxTheta;
+    d.theta = theta;
     d.e_blk0 = 0.0;
     d.inplace = 0;
   }

@@ -47,11 +47,12 @@ def main():
     ap.add_argument("--slabs", type=int, default=64, help="batch: slabs drawn before the --ng filter")
     ap.add_argument("--ng", default=None, help="batch: keep only slabs of this N,G")
     ap.add_argument("--batch-max-iter", type=int, default=200)
+    ap.add_argument("--j-hi", type=int, default=8192, help="batch: largest slab (cells)")
     a = ap.parse_args()
     import torch
     prec = {"fp64": oci.FP64, "fp32": oci.FP32_IR, "tf32": oci.TF32_IR, "bf16x3": oci.BF16X3_IR}[a.precision]
     if a.case == "batch":
-        probs = [b.replace(max_iter=a.batch_max_iter) for b in W.batch_of_slabs(a.slabs, j_lo=1024, j_hi=8192)]
+        probs = [b.replace(max_iter=a.batch_max_iter) for b in W.batch_of_slabs(a.slabs, j_lo=1024, j_hi=a.j_hi)]
         if a.ng:
             n_, g_ = (int(x) for x in a.ng.split(","))
             probs = [b for b in probs if (b.N, b.G) == (n_, g_)]
