@@ -25,6 +25,7 @@
 #include <math.h>
 
 #include "oci_device.cuh"
+#include "oci_mixed_dev.cuh"
 
 namespace oci {
 
@@ -39,7 +40,6 @@ __device__ __forceinline__ size_t fidx(int tsh, int R, size_t Jp, int r, int j) 
   return ((((size_t)(j >> sh)) * R + r) << sh) + (size_t)c;
 }
 
-__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 int mx_tile_shift(const Handle &h) {
   const int sh = h.mx_cb == 16 ? 4 : h.mx_cb == 32 ? 5 : h.mx_cb == 64 ? 6 : 7;
@@ -470,24 +470,6 @@ size_t mx_tp_smem(const Handle &h, int T, int P, bool stage) {
   return mx_reg_smem(h.G, T, P) + (stage ? mx_tables_floats(h) * 4 + 16 : 0);
 }
 
-// Per-type tables into shared memory (16-byte aligned sections); the pointers
-// are redirected to the copies.  All threads; no barrier.
-__device__ __forceinline__ void stage_tables(float *tab, int n_types, int N, int G, int tid, int nthr,
-                                             const float *&Linv, const float *&Cin, const float *&Mp,
-                                             const float *&w) {
-  const int G4 = 4 * G;
-  const size_t nL = (size_t)n_types * G * N * 16, nC = (size_t)n_types * G * N * 8;
-  const size_t nM = (size_t)n_types * G4 * G4;
-  float *sL = tab, *sC = sL + nL, *sM = sC + nC, *sw = sM + nM;
-  for (size_t i = tid; i < nL; i += nthr) sL[i] = Linv[i];
-  for (size_t i = tid; i < nC; i += nthr) sC[i] = Cin[i];
-  for (size_t i = tid; i < nM; i += nthr) sM[i] = Mp[i];
-  for (int i = tid; i < N; i += nthr) sw[i] = w[i];
-  Linv = sL;
-  Cin = sC;
-  Mp = sM;
-  w = sw;
-}
 
 // One tile of the tiled register sweep by the whole block; returns this
 // thread's sum of squared changes.  Contains three block barriers; shared
@@ -739,19 +721,6 @@ __device__ __forceinline__ float tiled_sweep_pf(int J, int N, int G, int cl, int
   return e2;
 }
 
-// Fixed-order block sum of per-thread values (the result in thread 0).
-__device__ __forceinline__ double block_reduce_fixed(float e2, double *red, int tid, int nthr) {
-  double v = (double)e2;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  __syncthreads();  // red may still be read by a previous reduction
-  if ((tid & 31) == 0) red[tid >> 5] = v;
-  __syncthreads();
-  double bs = 0.0;
-  if (tid == 0)
-    for (int i = 0; i < (nthr + 31) / 32; i++) bs += red[i];
-  return bs;
-}
 
 template <int T, int NP>
 __global__ void __launch_bounds__(256) k_mx_inner_tp(int J, int N, int G, int n_types, int stage,
@@ -808,29 +777,6 @@ __global__ void __launch_bounds__(256) k_mx_inner_tp(int J, int N, int G, int n_
 // parity: a block that starts the next sweep cannot overwrite values another
 // block is still summing.  The barrier spin is bounded; a timeout records
 // OCI_E_TIMEOUT and ends the step.
-constexpr long long kGridSpin = 1 << 21;
-
-// Sense-reversing grid barrier on {count, generation}; thread 0 of every block.
-__device__ __forceinline__ bool grid_barrier(unsigned *gbar, unsigned nblocks) {
-  volatile unsigned *vgen = gbar + 1;
-  const unsigned g0 = *vgen;  // cannot advance before this block arrives
-  __threadfence();
-  const unsigned arrived = atomicAdd(gbar, 1u);
-  if (arrived == nblocks - 1) {
-    gbar[0] = 0;
-    __threadfence();
-    atomicAdd(gbar + 1, 1u);
-    return true;
-  }
-  for (long long k = 0; k < kGridSpin; k++) {
-    if (*vgen != g0) {
-      __threadfence();
-      return true;
-    }
-    __nanosleep(64);
-  }
-  return false;
-}
 
 template <int T, int NP>
 __global__ void __launch_bounds__(256) k_mx_inner_ms(int J, int N, int G, int n_types, int stage,
@@ -928,462 +874,6 @@ static void launch_ms(Handle &h, int P, size_t smem, bool stage, cudaGraphCondit
                      (const float *)h.tt.Linv32, (const float *)h.tt.Cin32, (const float *)h.tt.Mp32,
                      (const float *)h.w32, (const float *)h.z32, h.delta[0], h.delta[1], h.ds, h.partials, h.gbar,
                      h.e_hist, cond, use_cond, max_sweeps);
-}
-
-// ---------------------------------------------------------------- inner sweeps, two per pass
-// Two consecutive inner sweeps in one pass over the correction (temporal
-// blocking).  Each block owns a contiguous run of tiles [t0, t1) and walks it
-// left to right: at step k it computes delta^{i+1} on tile k from delta^i in
-// global memory, then delta^{i+2} on tile k-1, whose lagged inflows are the
-// delta^{i+1} values of tiles k-2, k-1 and k held in a three-slot ring in
-// shared memory.  The delta^{i+1} values of the two cells just outside the run
-// (a0 - 1 and a1) are recomputed by the block before the walk, so blocks never
-// wait on one another inside a pass.  Per two sweeps a pass reads z and
-// delta^i once and writes delta^{i+2} once: 12 bytes per unknown instead of
-// 24.  Both sweeps' norms are reduced and the device state takes the two e
-// values in order; if the first already ends the inner block (a refinement or
-// the stop rule is due), delta^{i+1} is recomputed from delta^i -- still intact
-// in the input buffer -- by a one-sweep pass into the output buffer.  The cell
-// arithmetic is that of the tiled sweep.
-//
-// Template parameters: T cells per tile, NP angles per thread, and the angle
-// chunks per cell PS and groups GS when known at compile time (0: taken from
-// the arguments); with both fixed every index and loop bound folds.
-
-// Global loads of one cell column of a tile (z, the old correction when
-// want_old, the lagged inflows from delta_in); zeros for an inactive thread.
-template <int T, int NP, int PS, int GS>
-__device__ __forceinline__ void ms2_load(float (&zr)[NP][4], float (&old)[NP][4], float (&uk)[NP], float (&uh)[NP],
-                                         int tile, int cl, bool active, bool want_old, int J, int Nr, int Gr, int gy,
-                                         bool zero, const float *__restrict__ z, const float *__restrict__ Din) {
-  const int N = PS ? PS * NP : Nr, G = GS ? GS : Gr;
-  const int P = N / NP, R = 4 * N * G;
-  const int g = gy / P, ch = gy % P, m0 = ch * NP;
-  const int N2 = N / 2;
-  const int offL = cl > 0 ? -1 : (T - 1) - R * T;
-  const int offR = cl < T - 1 ? 1 : R * T - (T - 1);
-  const int j = tile * T + cl;
-  const size_t off = ((size_t)tile * R + (size_t)(g * N + m0) * 4) * T + cl;
-  const float *__restrict__ zb = z + off;
-  const float *__restrict__ db = Din + off;
-#pragma unroll
-  for (int i = 0; i < NP; i++) {
-    const int m = m0 + i;
-#pragma unroll
-    for (int p = 0; p < 4; p++) {
-      zr[i][p] = active ? zb[(i * 4 + p) * T] : 0.f;
-      old[i][p] = (active && want_old && !zero) ? db[(i * 4 + p) * T] : 0.f;
-    }
-    uk[i] = 0.f;
-    uh[i] = 0.f;
-    if (active && !zero) {
-      if (m >= N2) {
-        if (j > 0) {
-          uk[i] = db[offL + (i * 4 + 1) * T];
-          uh[i] = db[offL + (i * 4 + 3) * T];
-        }
-      } else if (j < J - 1) {
-        uk[i] = db[offR + (i * 4 + 0) * T];
-        uh[i] = db[offR + (i * 4 + 2) * T];
-      }
-    }
-  }
-}
-
-// Structured FP32 cell solve of the thread's (cell, group, NP angles):
-// t = z + Cin u, y = sum_m w t, s = Mp y, o = t + Linv s (the arithmetic of
-// tiled_compute).  Three block barriers; y_s / yr_s / s_s as there.
-template <int T, int NP, int PS, int GS>
-__device__ __forceinline__ void ms2_solve(float (&o)[NP][4], const float (&zr)[NP][4], const float (&uk)[NP],
-                                          const float (&uh)[NP], bool active, int tau, int Nr, int Gr, int cl, int gy,
-                                          const float *Linv, const float *Cin, const float *Mp, const float *w,
-                                          float *y_s, float *yr_s, float *s_s) {
-  const int N = PS ? PS * NP : Nr, G = GS ? GS : Gr;
-  const int P = N / NP, G4 = 4 * G;
-  const int g = gy / P, ch = gy % P, m0 = ch * NP;
-  const int tb = tau * G * N;
-  float y0 = 0.f, y1 = 0.f, y2 = 0.f, y3 = 0.f;
-#pragma unroll
-  for (int i = 0; i < NP; i++)
-#pragma unroll
-    for (int p = 0; p < 4; p++) o[i][p] = 0.f;
-  if (active) {
-#pragma unroll
-    for (int i = 0; i < NP; i++) {
-      const int m = m0 + i;
-      const float4 *C4 = reinterpret_cast<const float4 *>(Cin + (tb + g * N + m) * 8);
-      const float4 ca = C4[0], cb = C4[1];
-      o[i][0] = fmaf(ca.y, uh[i], fmaf(ca.x, uk[i], zr[i][0]));
-      o[i][1] = fmaf(ca.w, uh[i], fmaf(ca.z, uk[i], zr[i][1]));
-      o[i][2] = fmaf(cb.y, uh[i], fmaf(cb.x, uk[i], zr[i][2]));
-      o[i][3] = fmaf(cb.w, uh[i], fmaf(cb.z, uk[i], zr[i][3]));
-      const float wm = w[m];
-      y0 = fmaf(wm, o[i][0], y0);
-      y1 = fmaf(wm, o[i][1], y1);
-      y2 = fmaf(wm, o[i][2], y2);
-      y3 = fmaf(wm, o[i][3], y3);
-    }
-  }
-  {
-    float *ys = y_s + (gy * 4) * T + cl;
-    ys[0] = y0;
-    ys[T] = y1;
-    ys[2 * T] = y2;
-    ys[3 * T] = y3;
-  }
-  __syncthreads();
-#pragma unroll
-  for (int q = ch; q < 4; q += P) {
-    float v = y_s[((g * P) * 4 + q) * T + cl];
-#pragma unroll
-    for (int k = 1; k < P; k++) v += y_s[((g * P + k) * 4 + q) * T + cl];
-    yr_s[(g * 4 + q) * T + cl] = v;
-  }
-  __syncthreads();
-  if (active)
-#pragma unroll
-    for (int q = ch; q < 4; q += P) {
-      const float *M = Mp + tau * G4 * G4 + (g * 4 + q) * G4;
-      float v = 0.f;
-#pragma unroll
-      for (int k = 0; k < G4; k++) v = fmaf(M[k], yr_s[k * T + cl], v);
-      s_s[(g * 4 + q) * T + cl] = v;
-    }
-  __syncthreads();
-  if (active) {
-    const float s0 = s_s[(g * 4 + 0) * T + cl], s1 = s_s[(g * 4 + 1) * T + cl];
-    const float s2 = s_s[(g * 4 + 2) * T + cl], s3 = s_s[(g * 4 + 3) * T + cl];
-#pragma unroll
-    for (int i = 0; i < NP; i++) {
-      const float4 *L4 = reinterpret_cast<const float4 *>(Linv + (tb + g * N + m0 + i) * 16);
-#pragma unroll
-      for (int p = 0; p < 4; p++) {
-        const float4 L = L4[p];
-        o[i][p] = fmaf(L.w, s3, fmaf(L.z, s2, fmaf(L.y, s1, fmaf(L.x, s0, o[i][p]))));
-      }
-    }
-  }
-}
-
-// The downstream edge values of a cell (mu > 0: corners 1, 3; mu < 0: corners
-// 0, 2) at edge[((g N + m) 2 + q)] (the run's outside neighbours).
-template <int NP>
-__device__ __forceinline__ void ms2_put_edges(float *edge, const float (&o)[NP][4], int N, int g, int m0) {
-#pragma unroll
-  for (int i = 0; i < NP; i++) {
-    const int m = m0 + i;
-    float *d = edge + (g * N + m) * 2;
-    if (m >= N / 2) {
-      d[0] = o[i][1];
-      d[1] = o[i][3];
-    } else {
-      d[0] = o[i][0];
-      d[1] = o[i][2];
-    }
-  }
-}
-
-// sum of squared changes
-template <int NP>
-__device__ __forceinline__ float ms2_dist2(const float (&a)[NP][4], const float (&b)[NP][4]) {
-  float e2 = 0.f;
-#pragma unroll
-  for (int i = 0; i < NP; i++)
-#pragma unroll
-    for (int p = 0; p < 4; p++) {
-      const float d = a[i][p] - b[i][p];
-      e2 = fmaf(d, d, e2);
-    }
-  return e2;
-}
-
-struct Ms2Args {
-  int J, N, G, t0, t1;
-  const int32_t *__restrict__ type;
-  const float *Linv, *Cin, *Mp, *w;
-  const float *__restrict__ z;
-  float *y_s, *yr_s, *s_s, *ring, *halo;
-};
-
-// One sweep over the block's run (delta_in -> delta_out); returns the thread's
-// sum of squared changes.
-template <int T, int NP, int PS, int GS>
-__device__ float ms2_pass1(const Ms2Args &a, int cl, int gy, bool zero, const float *__restrict__ Din,
-                           float *__restrict__ Dout) {
-  const int N = PS ? PS * NP : a.N, G = GS ? GS : a.G;
-  const int P = N / NP, R = 4 * N * G;
-  const int g = gy / P, m0 = (gy % P) * NP;
-  float e2 = 0.f;
-  for (int k = a.t0; k < a.t1; k++) {
-    float zr[NP][4], old[NP][4], uk[NP], uh[NP], o[NP][4];
-    const int j = k * T + cl;
-    const bool act = j < a.J;
-    const int tau = act ? a.type[j] : 0;
-    ms2_load<T, NP, PS, GS>(zr, old, uk, uh, k, cl, act, true, a.J, N, G, gy, zero, a.z, Din);
-    ms2_solve<T, NP, PS, GS>(o, zr, uk, uh, act, tau, N, G, cl, gy, a.Linv, a.Cin, a.Mp, a.w, a.y_s, a.yr_s,
-                             a.s_s);
-    if (act) {
-      e2 += ms2_dist2<NP>(o, old);
-      float *__restrict__ ob = Dout + ((size_t)k * R + (size_t)(g * N + m0) * 4) * T + cl;
-#pragma unroll
-      for (int i = 0; i < NP; i++)
-#pragma unroll
-        for (int p = 0; p < 4; p++) ob[(i * 4 + p) * T] = o[i][p];
-    }
-  }
-  return e2;
-}
-
-// Two sweeps over the block's run (delta_in -> delta_out = delta^{i+2}); the
-// threads' sums of squared changes of both sweeps in ea, eb.  delta^{i+1} of a
-// tile is kept whole in a ring slot [4NG][T] (for the second sweep's norm and
-// its inflows); z is read again for the second sweep (a cache hit: the tile
-// was read one step earlier).
-template <int T, int NP, int PS, int GS>
-__device__ void ms2_pass2(const Ms2Args &a, int cl, int gy, bool zero, const float *__restrict__ Din,
-                          float *__restrict__ Dout, float &ea, float &eb) {
-  const int N = PS ? PS * NP : a.N, G = GS ? GS : a.G;
-  const int J = a.J, P = N / NP, R = 4 * N * G, NG2 = 2 * N * G;
-  const int g = gy / P, m0 = (gy % P) * NP;
-  const int ntiles = (J + T - 1) / T;
-  float *halo_l = a.halo, *halo_r = a.halo + NG2;
-  // delta^{i+1} of the cells next to the run: thread column T-1 takes cell
-  // t0*T - 1 (last column of tile t0-1), column 0 takes cell t1*T (tile t1)
-  {
-    const bool hl = cl == T - 1 && a.t0 > 0, hr = cl == 0 && a.t1 < ntiles;
-    const bool act = hl || hr;
-    const int tile = hl ? a.t0 - 1 : (hr ? a.t1 : a.t0);
-    const int tau = act ? a.type[tile * T + cl] : 0;
-    float zr[NP][4], old[NP][4], uk[NP], uh[NP], o[NP][4];
-    ms2_load<T, NP, PS, GS>(zr, old, uk, uh, tile, cl, act, false, J, N, G, gy, zero, a.z, Din);
-    ms2_solve<T, NP, PS, GS>(o, zr, uk, uh, act, tau, N, G, cl, gy, a.Linv, a.Cin, a.Mp, a.w, a.y_s, a.yr_s,
-                             a.s_s);
-    if (hl) ms2_put_edges<NP>(halo_l, o, N, g, m0);
-    if (hr) ms2_put_edges<NP>(halo_r, o, N, g, m0);
-  }
-  // ring slots of tiles k (cur), k-1 (prv) and k-2 (pp)
-  float *cur = a.ring, *prv = a.ring + R * T, *pp = a.ring + 2 * R * T;
-  for (int k = a.t0; k <= a.t1; k++) {
-    if (k < a.t1) {  // sweep i+1 on tile k
-      float zr[NP][4], old[NP][4], uk[NP], uh[NP], o1[NP][4];
-      const int j = k * T + cl;
-      const bool act = j < J;
-      const int tau = act ? a.type[j] : 0;
-      ms2_load<T, NP, PS, GS>(zr, old, uk, uh, k, cl, act, true, J, N, G, gy, zero, a.z, Din);
-      ms2_solve<T, NP, PS, GS>(o1, zr, uk, uh, act, tau, N, G, cl, gy, a.Linv, a.Cin, a.Mp, a.w, a.y_s, a.yr_s,
-                               a.s_s);
-      if (act) {
-        ea += ms2_dist2<NP>(o1, old);
-        float *sl = cur + ((g * N + m0) * 4) * T + cl;
-#pragma unroll
-        for (int i = 0; i < NP; i++)
-#pragma unroll
-          for (int p = 0; p < 4; p++) sl[(i * 4 + p) * T] = o1[i][p];
-      }
-    }
-    __syncthreads();  // the ring slot of tile k is complete
-    if (k > a.t0) {   // sweep i+2 on tile k-1: inflows from delta^{i+1} of the neighbours
-      const int kk = k - 1, j = kk * T + cl;
-      const bool act = j < J;
-      const int tau = act ? a.type[j] : 0;
-      float zr[NP][4], o1[NP][4], uk[NP], uh[NP], o2[NP][4];
-      {
-        float dummy[NP][4], dk[NP], dh[NP];
-        ms2_load<T, NP, PS, GS>(zr, dummy, dk, dh, kk, cl, act, false, J, N, G, gy, true, a.z, Din);
-      }
-#pragma unroll
-      for (int i = 0; i < NP; i++) {
-        const int m = m0 + i, r0 = (g * N + m) * 4;
-#pragma unroll
-        for (int p = 0; p < 4; p++) o1[i][p] = act ? prv[(r0 + p) * T + cl] : 0.f;
-        const float *src = nullptr;
-        int st = 2 * T;
-        if (m >= N / 2) {  // corners 1, 3 of cell j - 1
-          if (j > 0) {
-            if (cl > 0) src = prv + (r0 + 1) * T + cl - 1;
-            else if (kk > a.t0) src = pp + (r0 + 1) * T + T - 1;
-            else src = halo_l + (g * N + m) * 2, st = 1;
-          }
-        } else if (j < J - 1) {  // corners 0, 2 of cell j + 1
-          if (cl < T - 1) src = prv + r0 * T + cl + 1;
-          else if (kk + 1 < a.t1) src = cur + r0 * T;
-          else src = halo_r + (g * N + m) * 2, st = 1;
-        }
-        uk[i] = (act && src) ? src[0] : 0.f;
-        uh[i] = (act && src) ? src[st] : 0.f;
-      }
-      ms2_solve<T, NP, PS, GS>(o2, zr, uk, uh, act, tau, N, G, cl, gy, a.Linv, a.Cin, a.Mp, a.w, a.y_s, a.yr_s,
-                               a.s_s);
-      if (act) {
-        eb += ms2_dist2<NP>(o2, o1);
-        float *__restrict__ ob = Dout + ((size_t)kk * R + (size_t)(g * N + m0) * 4) * T + cl;
-#pragma unroll
-        for (int i = 0; i < NP; i++)
-#pragma unroll
-          for (int p = 0; p < 4; p++) ob[(i * 4 + p) * T] = o2[i][p];
-      }
-    }
-    float *t = pp;  // rotate: the slot of tile k-2 takes tile k+1
-    pp = prv;
-    prv = cur;
-    cur = t;
-  }
-}
-
-// OCC: resident blocks per SM the register allocation is built for (the
-// block size is T * PS * GS threads when known at compile time, else <= 256).
-template <int T, int NP, int PS, int GS, int OCC>
-__global__ void __launch_bounds__((PS && GS) ? T * PS * GS : 256, OCC) k_mx_inner_ms2(int J, int N, int G, int n_types, int stage,
-                                                      const int32_t *__restrict__ type, const float *Linv_g,
-                                                      const float *Cin_g, const float *Mp_g, const float *w_g,
-                                                      const float *__restrict__ z, float *D0, float *D1,
-                                                      DevState *ds, double *__restrict__ partials, unsigned *gbar,
-                                                      double *e_hist, cudaGraphConditionalHandle cond, int use_cond,
-                                                      int max_sweeps) {
-  extern __shared__ __align__(16) float smr[];
-  __shared__ double red[8];
-  __shared__ DevState sd;
-  __shared__ int s_ok, s_roll;
-  const int P = N / NP, G4 = 4 * G, NG2 = 2 * N * G;
-  const int cl = threadIdx.x, gy = threadIdx.y;
-  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-  const int nthr = blockDim.x * blockDim.y;
-  if (tid == 0) sd = *ds;
-  __syncthreads();
-  if (sd.done) return;  // uniform across the grid
-  Ms2Args a;
-  a.J = J;
-  a.N = N;
-  a.G = G;
-  a.type = type;
-  a.z = z;
-  a.y_s = smr;
-  a.yr_s = a.y_s + (size_t)G * P * 4 * T;
-  a.s_s = a.yr_s + (size_t)G4 * T;
-  a.ring = a.s_s + (size_t)G4 * T;
-  a.halo = a.ring + (size_t)3 * 4 * N * G * T;
-  a.Linv = Linv_g;
-  a.Cin = Cin_g;
-  a.Mp = Mp_g;
-  a.w = w_g;
-  if (stage) {
-    stage_tables(a.halo + 2 * NG2, n_types, N, G, tid, nthr, a.Linv, a.Cin, a.Mp, a.w);
-    __syncthreads();
-  }
-  const int ntiles = (J + T - 1) / T;
-  a.t0 = (int)((long long)blockIdx.x * ntiles / gridDim.x);
-  a.t1 = (int)((long long)(blockIdx.x + 1) * ntiles / gridDim.x);
-  bool failed = false;
-  for (int sw = 0, pass = 0;; pass++) {
-    const int ns = max_sweeps - sw >= 2 ? 2 : 1;
-    const bool zero = sd.refine || sd.blk_i == 0;
-    const float *__restrict__ Din = sd.dcur ? D1 : D0;
-    float *__restrict__ Dout = sd.dcur ? D0 : D1;
-    float ea = 0.f, eb = 0.f;
-    if (ns == 2) ms2_pass2<T, NP, PS, GS>(a, cl, gy, zero, Din, Dout, ea, eb);
-    else ea = ms2_pass1<T, NP, PS, GS>(a, cl, gy, zero, Din, Dout);
-    const double ba = block_reduce_fixed(ea, red, tid, nthr);
-    const double bb = block_reduce_fixed(eb, red, tid, nthr);
-    double *part = partials + (size_t)(pass & 1) * 2 * gridDim.x;
-    if (tid == 0) {
-      part[blockIdx.x] = ba;
-      part[gridDim.x + blockIdx.x] = bb;
-      s_ok = grid_barrier(gbar, gridDim.x);
-    }
-    __syncthreads();
-    if (!s_ok) {
-      failed = true;
-      break;
-    }
-    const double ta = block_sum_fixed(part, gridDim.x, red);
-    const double tb = ns == 2 ? block_sum_fixed(part + gridDim.x, gridDim.x, red) : 0.0;
-    if (tid == 0) {
-      double *eh = blockIdx.x == 0 ? e_hist : nullptr;
-      finish_mixed(&sd, eh, sqrt(ta), cond, 0);
-      s_roll = 0;
-      if (ns == 2) {
-        if (sd.done || sd.refine) {
-          s_roll = 1;  // the inner block ends at sweep i+1
-        } else {
-          finish_mixed(&sd, eh, sqrt(tb), cond, 0);
-          if (!sd.inplace) sd.dcur ^= 1;  // one buffer flip per pass: delta^{i+2} is in Dout
-        }
-      }
-    }
-    __syncthreads();
-    if (s_roll) {  // delta^{i+1} into Dout (delta^i is untouched in Din)
-      ms2_pass1<T, NP, PS, GS>(a, cl, gy, zero, Din, Dout);
-      break;
-    }
-    sw += ns;
-    if (sd.done || sd.refine || sw >= max_sweeps) break;  // uniform: every block holds the same state
-  }
-  if (blockIdx.x == 0 && tid == 0) {
-    if (failed) {
-      sd.status = OCI_E_TIMEOUT;
-      sd.done = 1;
-      sd.refine = 0;
-    }
-    *ds = sd;
-    if (use_cond) {
-      if (sd.done) cudaGraphSetConditional(cond, 0);
-      if (sd.cond_ref) cudaGraphSetConditional((cudaGraphConditionalHandle)sd.cond_ref, sd.refine);
-    }
-  }
-}
-
-size_t mx_ms2_smem(const Handle &h, int T, int P, bool stage) {
-  const size_t G = h.G, N = h.N;
-  return ((size_t)T * (G * P * 4 + 8 * G) + 3 * 4 * N * G * T + 4 * N * G) * 4 +
-         (stage ? mx_tables_floats(h) * 4 + 16 : 0);
-}
-
-template <int T, int NP, int PS, int GS, int OCC>
-static void launch_ms2(Handle &h, int P, cudaGraphConditionalHandle cond, int use_cond, int max_sweeps) {
-  const bool stage = mx_tables_floats(h) * 4 <= 64 * 1024;
-  const size_t smem = mx_ms2_smem(h, T, P, stage);
-  int dev = 0, sms = 0, per = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mx_inner_ms2<T, NP, PS, GS, OCC>, T * h.G * P, smem);
-  const int ntiles = (h.J + T - 1) / T;
-  const int grid = std::min(sms * (per > 0 ? per : 1), ntiles);
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(T, h.G * P);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = h.stream;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeCooperative;  // all blocks resident: they wait on one another
-  attr[0].val.cooperative = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, k_mx_inner_ms2<T, NP, PS, GS, OCC>, h.J, h.N, h.G, h.tt.n_types, (int)stage,
-                     (const int32_t *)h.type, (const float *)h.tt.Linv32, (const float *)h.tt.Cin32,
-                     (const float *)h.tt.Mp32, (const float *)h.w32, (const float *)h.z32, h.delta[0], h.delta[1],
-                     h.ds, h.partials, h.gbar, h.e_hist, cond, use_cond, max_sweeps);
-}
-
-// S16, one group (the slab workloads): fully specialised, with registers for
-// 2 blocks of 256 / 4 of 128 threads per SM, or (kMxTiled2Occ) for 3 of 256 /
-// 5 of 128; everything else generic (2 blocks of up to 256 threads)
-static void launch_ms2_any(Handle &h, cudaGraphConditionalHandle cond, int use_cond, int max_sweeps) {
-  const int T = h.mx_cb, P = h.mx_P, np = h.N / P;
-  const bool s16 = h.N == 16 && h.G == 1, occ = h.mx_kind == kMxTiled2Occ;
-#define OCI_MS2(TT, NPP, OC, OCX)                                                              \
-  do {                                                                                         \
-    if (s16 && occ) launch_ms2<TT, NPP, 16 / NPP, 1, OCX>(h, P, cond, use_cond, max_sweeps);   \
-    else if (s16) launch_ms2<TT, NPP, 16 / NPP, 1, OC>(h, P, cond, use_cond, max_sweeps);      \
-    else launch_ms2<TT, NPP, 0, 0, 2>(h, P, cond, use_cond, max_sweeps);                       \
-  } while (0)
-  if (T == 32) {
-    if (np == 2) OCI_MS2(32, 2, 2, 3);
-    else OCI_MS2(32, 4, 4, 5);
-  } else {
-    if (np == 2) OCI_MS2(64, 2, 1, 1);  // 512 threads: not an S16 shape (no candidate)
-    else OCI_MS2(64, 4, 2, 3);
-  }
-#undef OCI_MS2
 }
 
 template <int T, int NP>
@@ -1860,466 +1350,6 @@ static void launch_rb(Handle &h, int P, cudaGraphConditionalHandle cond, int use
                      (const float *)h.tt.Linv32, (const float *)h.tt.Cin32, (const float *)h.tt.Mp32,
                      (const float *)h.w32, (const float *)h.z32, h.delta[0], h.ds, h.partials, h.gbar, h.e_hist,
                      cond, use_cond, max_sweeps);
-}
-
-// ---------------------------------------------------------------- inner sweeps, red-black, two per pass
-// Two red-black sweeps (i, i+1) in one pass over the correction, by the run
-// walk of the Jacobi form: at step k a block computes red^i on tile k+1 (from
-// delta^{i-1} in global memory), black^i on tile k, red^{i+1} on tile k and
-// black^{i+1} on tile k-1; every input is either global delta^{i-1} or a
-// half-tile of this pass kept in shared memory (red^i, black^i, red^{i+1}: two
-// slots each, by tile parity).  The cells next to the run whose values the walk
-// needs are recomputed by the block: red^i and black^i of the two cells before
-// it, red^i of the first two red cells after it, black^i between those and
-// red^{i+1} of the first cell after it.  Results go to the other buffer (not in
-// place: a neighbouring block still reads delta^{i-1} there), so one pass reads
-// z and delta^{i-1} once and writes delta^{i+1} once; the device state takes
-// the two norms in order, and when the first ends an inner block the sweep is
-// recomputed by a one-sweep pass from the untouched input.  Same cell
-// arithmetic and colour order as k_mx_rb; the correction arrays keep the
-// colour-ordered tile-major layout.
-
-// Lagged inflows of the thread's NP angles from the left neighbour (corners 1,
-// 3; mu > 0) and the right neighbour (corners 0, 2; mu < 0).  L / Rt point at
-// the neighbour's value in row (g N + m0) 4 of a column source with row stride
-// ls / rs; nullptr is zero inflow.
-template <int NP>
-__device__ __forceinline__ void rb2_inflow(float (&uk)[NP], float (&uh)[NP], const float *L, int ls, const float *Rt,
-                                           int rs, int m0, int N2) {
-#pragma unroll
-  for (int i = 0; i < NP; i++) {
-    const int m = m0 + i;
-    if (m >= N2) {
-      uk[i] = L ? L[(i * 4 + 1) * ls] : 0.f;
-      uh[i] = L ? L[(i * 4 + 3) * ls] : 0.f;
-    } else {
-      uk[i] = Rt ? Rt[(i * 4 + 0) * rs] : 0.f;
-      uh[i] = Rt ? Rt[(i * 4 + 2) * rs] : 0.f;
-    }
-  }
-}
-
-template <int NP>
-__device__ __forceinline__ void rb2_get(float (&v)[NP][4], const float *src, int st, bool act) {
-#pragma unroll
-  for (int i = 0; i < NP; i++)
-#pragma unroll
-    for (int p = 0; p < 4; p++) v[i][p] = (act && src) ? src[(i * 4 + p) * st] : 0.f;
-}
-
-template <int NP>
-__device__ __forceinline__ void rb2_put(float *dst, int st, const float (&v)[NP][4]) {
-#pragma unroll
-  for (int i = 0; i < NP; i++)
-#pragma unroll
-    for (int p = 0; p < 4; p++) dst[(i * 4 + p) * st] = v[i][p];
-}
-
-struct Rb2Args {
-  int J, N, G, t0, t1;
-  const int32_t *__restrict__ type;
-  const float *Linv, *Cin, *Mp, *w;
-  const float *__restrict__ z;
-  float *y_s, *yr_s, *s_s;
-  float *Ri, *Bi, *R2;                         // two half-tile slots each ([R][T/2])
-  float *hRL, *hBL, *hRR0, *hRR1, *hBR, *hR2;  // cells next to the run, [R] each
-};
-
-// One red-black pass over the block's run: ns = 2 sweeps i, i+1 (delta^{i+1}
-// into Dout), or ns = 1 sweep i (delta^i into Dout).  ea, eb: the thread's
-// squared changes of the two sweeps.
-template <int T, int NP, int PS, int GS>
-__device__ void rb2_pass(const Rb2Args &a, int cl, int gy, bool zero, int ns, const float *__restrict__ Din,
-                         float *__restrict__ Dout, float &ea, float &eb) {
-  constexpr int TH = T / 2;
-  const int N = PS ? PS * NP : a.N, G = GS ? GS : a.G;
-  const int J = a.J, P = N / NP, R = 4 * N * G, N2 = N / 2;
-  const int g = gy / P, m0 = (gy % P) * NP, row0 = (g * N + m0) * 4;
-  const int ntiles = (J + T - 1) / T, t0 = a.t0, t1 = a.t1;
-  const size_t RT = (size_t)R * T;
-  const int HS = R * TH;  // one half-tile slot
-  // column c of colour col of a global tile, at row row0 (row stride T)
-  auto gcol = [&](const float *base, int tile, int col, int c) -> const float * {
-    return base + (size_t)tile * RT + (size_t)row0 * T + col * TH + c;
-  };
-  auto gout = [&](int tile, int col, int c) -> float * {
-    return Dout + (size_t)tile * RT + (size_t)row0 * T + col * TH + c;
-  };
-  // column c of the slot of `tile` (by parity), at row row0 (row stride T/2)
-  auto scol = [&](float *slot, int tile, int c) -> float * { return slot + (tile & 1) * HS + row0 * TH + c; };
-  auto solve = [&](float (&o)[NP][4], const float (&zr)[NP][4], const float (&uk)[NP], const float (&uh)[NP],
-                   bool act, int j) {
-    const int tau = act ? a.type[j] : 0;
-    ms2_solve<TH, NP, PS, GS>(o, zr, uk, uh, act, tau, N, G, cl, gy, a.Linv, a.Cin, a.Mp, a.w, a.y_s, a.yr_s,
-                              a.s_s);
-  };
-  // inputs of red^i at (tile, c) from delta^{i-1}: inflows, z, old value
-  auto red_i_in = [&](int tile, int c, bool act, float (&zr)[NP][4], float (&old)[NP][4], float (&uk)[NP],
-                      float (&uh)[NP]) {
-    const int j = tile * T + 2 * c;
-    const float *L = nullptr, *Rt = nullptr;
-    if (act && !zero) {
-      if (c > 0) L = gcol(Din, tile, 1, c - 1);
-      else if (j > 0) L = gcol(Din, tile - 1, 1, TH - 1);
-      if (j + 1 < J) Rt = gcol(Din, tile, 1, c);
-    }
-    rb2_inflow<NP>(uk, uh, L, T, Rt, T, m0, N2);
-    rb2_get<NP>(zr, gcol(a.z, tile, 0, c), T, act);
-    rb2_get<NP>(old, zero ? nullptr : gcol(Din, tile, 0, c), T, act);
-  };
-  // --- reds of sweep i next to the run: column T/2-1 takes red (t0-1, T/2-1),
-  // columns 0 and 1 take reds (t1, 0) and (t1, 1)
-  {
-    int tile = t0;
-    bool act = false;
-    float *dst = nullptr;
-    if (cl == TH - 1 && t0 > 0 && ns == 2) {
-      tile = t0 - 1;
-      act = true;
-      dst = a.hRL;
-    } else if (cl == 0 && t1 < ntiles) {
-      tile = t1;
-      act = true;
-      dst = a.hRR0;
-    } else if (cl == 1 && ns == 2 && t1 < ntiles && t1 * T + 2 < J) {
-      tile = t1;
-      act = true;
-      dst = a.hRR1;
-    }
-    float zr[NP][4], old[NP][4], uk[NP], uh[NP], o[NP][4];
-    red_i_in(tile, cl, act, zr, old, uk, uh);
-    solve(o, zr, uk, uh, act, tile * T + 2 * cl);
-    if (act) rb2_put<NP>(dst + row0, 1, o);
-  }
-  // --- red^i of tile t0
-  {
-    const int j = t0 * T + 2 * cl;
-    const bool act = j < J;
-    float zr[NP][4], old[NP][4], uk[NP], uh[NP], o[NP][4];
-    red_i_in(t0, cl, act, zr, old, uk, uh);
-    solve(o, zr, uk, uh, act, j);
-    if (act) {
-      ea += ms2_dist2<NP>(o, old);
-      rb2_put<NP>(scol(a.Ri, t0, cl), TH, o);
-      if (ns == 1) rb2_put<NP>(gout(t0, 0, cl), T, o);
-    }
-  }
-  __syncthreads();
-  // --- blacks of sweep i next to the run: black (t0-1, T/2-1) and black (t1, 0)
-  if (ns == 2) {
-    const bool bl = cl == TH - 1 && t0 > 0;
-    const int jr = t1 * T + 1;
-    const bool br = cl == 0 && t1 < ntiles && jr < J;
-    const bool act = bl || br;
-    const float *L = nullptr, *Rt = nullptr;
-    int tile = t0, col = 0, j = 0, rs = 1;
-    if (bl) {
-      tile = t0 - 1;
-      col = TH - 1;
-      j = t0 * T - 1;
-      L = a.hRL + row0;
-      Rt = scol(a.Ri, t0, 0);
-      rs = TH;
-    } else if (br) {
-      tile = t1;
-      col = 0;
-      j = jr;
-      L = a.hRR0 + row0;
-      Rt = jr + 1 < J ? a.hRR1 + row0 : nullptr;
-    }
-    float zr[NP][4], uk[NP], uh[NP], o[NP][4];
-    rb2_inflow<NP>(uk, uh, L, 1, Rt, rs, m0, N2);
-    rb2_get<NP>(zr, gcol(a.z, tile, 1, col), T, act);
-    solve(o, zr, uk, uh, act, j);
-    if (bl) rb2_put<NP>(a.hBL + row0, 1, o);
-    if (br) rb2_put<NP>(a.hBR + row0, 1, o);
-  }
-  for (int k = t0; k < t1; k++) {
-    if (k + 1 < t1) {  // (a) red^i of tile k+1
-      const int j = (k + 1) * T + 2 * cl;
-      const bool act = j < J;
-      float zr[NP][4], old[NP][4], uk[NP], uh[NP], o[NP][4];
-      red_i_in(k + 1, cl, act, zr, old, uk, uh);
-      solve(o, zr, uk, uh, act, j);
-      if (act) {
-        ea += ms2_dist2<NP>(o, old);
-        rb2_put<NP>(scol(a.Ri, k + 1, cl), TH, o);
-        if (ns == 1) rb2_put<NP>(gout(k + 1, 0, cl), T, o);
-      }
-    }
-    __syncthreads();
-    {  // (b) black^i of tile k
-      const int j = k * T + 2 * cl + 1;
-      const bool act = j < J;
-      const float *L = nullptr, *Rt = nullptr;
-      int rs = TH;
-      if (act) {
-        L = scol(a.Ri, k, cl);
-        if (j + 1 < J) {
-          if (cl + 1 < TH) Rt = scol(a.Ri, k, cl + 1);
-          else if (k + 1 < t1) Rt = scol(a.Ri, k + 1, 0);
-          else Rt = a.hRR0 + row0, rs = 1;
-        }
-      }
-      float zr[NP][4], old[NP][4], uk[NP], uh[NP], o[NP][4];
-      rb2_inflow<NP>(uk, uh, L, TH, Rt, rs, m0, N2);
-      rb2_get<NP>(zr, gcol(a.z, k, 1, cl), T, act);
-      rb2_get<NP>(old, zero ? nullptr : gcol(Din, k, 1, cl), T, act);
-      solve(o, zr, uk, uh, act, j);
-      if (act) {
-        ea += ms2_dist2<NP>(o, old);
-        if (ns == 2) rb2_put<NP>(scol(a.Bi, k, cl), TH, o);
-        else rb2_put<NP>(gout(k, 1, cl), T, o);
-      }
-    }
-    if (ns == 1) continue;
-    __syncthreads();
-    {  // (c) red^{i+1} of tile k
-      const int j = k * T + 2 * cl;
-      const bool act = j < J;
-      const float *L = nullptr, *Rt = nullptr;
-      int ls = TH;
-      if (act) {
-        if (cl > 0) L = scol(a.Bi, k, cl - 1);
-        else if (j > 0) {
-          if (k > t0) L = scol(a.Bi, k - 1, TH - 1);
-          else L = a.hBL + row0, ls = 1;
-        }
-        if (j + 1 < J) Rt = scol(a.Bi, k, cl);
-      }
-      float zr[NP][4], old[NP][4], uk[NP], uh[NP], o[NP][4];
-      rb2_inflow<NP>(uk, uh, L, ls, Rt, TH, m0, N2);
-      rb2_get<NP>(zr, gcol(a.z, k, 0, cl), T, act);
-      rb2_get<NP>(old, scol(a.Ri, k, cl), TH, act);
-      solve(o, zr, uk, uh, act, j);
-      if (act) {
-        eb += ms2_dist2<NP>(o, old);
-        rb2_put<NP>(scol(a.R2, k, cl), TH, o);
-        rb2_put<NP>(gout(k, 0, cl), T, o);
-      }
-    }
-    if (k > t0) {  // (d) black^{i+1} of tile k-1
-      __syncthreads();
-      const int kk = k - 1, j = kk * T + 2 * cl + 1;
-      const bool act = j < J;
-      const float *L = nullptr, *Rt = nullptr;
-      if (act) {
-        L = scol(a.R2, kk, cl);
-        if (j + 1 < J) Rt = cl + 1 < TH ? scol(a.R2, kk, cl + 1) : scol(a.R2, k, 0);
-      }
-      float zr[NP][4], old[NP][4], uk[NP], uh[NP], o[NP][4];
-      rb2_inflow<NP>(uk, uh, L, TH, Rt, TH, m0, N2);
-      rb2_get<NP>(zr, gcol(a.z, kk, 1, cl), T, act);
-      rb2_get<NP>(old, scol(a.Bi, kk, cl), TH, act);
-      solve(o, zr, uk, uh, act, j);
-      if (act) {
-        eb += ms2_dist2<NP>(o, old);
-        rb2_put<NP>(gout(kk, 1, cl), T, o);
-      }
-    }
-  }
-  if (ns == 1) return;
-  __syncthreads();
-  {  // red^{i+1} of cell t1*T (column 0 of tile t1), for the run's last black cell
-    const int j = t1 * T;
-    const bool act = cl == 0 && t1 < ntiles;
-    const float *L = nullptr, *Rt = nullptr;
-    if (act) {
-      L = scol(a.Bi, t1 - 1, TH - 1);
-      if (j + 1 < J) Rt = a.hBR + row0;
-    }
-    float zr[NP][4], uk[NP], uh[NP], o[NP][4];
-    rb2_inflow<NP>(uk, uh, L, TH, Rt, 1, m0, N2);
-    rb2_get<NP>(zr, gcol(a.z, act ? t1 : t0, 0, 0), T, act);
-    solve(o, zr, uk, uh, act, j);
-    if (act) rb2_put<NP>(a.hR2 + row0, 1, o);
-  }
-  __syncthreads();
-  {  // black^{i+1} of tile t1-1
-    const int kk = t1 - 1, j = kk * T + 2 * cl + 1;
-    const bool act = j < J;
-    const float *L = nullptr, *Rt = nullptr;
-    int rs = TH;
-    if (act) {
-      L = scol(a.R2, kk, cl);
-      if (j + 1 < J) {
-        if (cl + 1 < TH) Rt = scol(a.R2, kk, cl + 1);
-        else Rt = a.hR2 + row0, rs = 1;
-      }
-    }
-    float zr[NP][4], old[NP][4], uk[NP], uh[NP], o[NP][4];
-    rb2_inflow<NP>(uk, uh, L, TH, Rt, rs, m0, N2);
-    rb2_get<NP>(zr, gcol(a.z, kk, 1, cl), T, act);
-    rb2_get<NP>(old, scol(a.Bi, kk, cl), TH, act);
-    solve(o, zr, uk, uh, act, j);
-    if (act) {
-      eb += ms2_dist2<NP>(o, old);
-      rb2_put<NP>(gout(kk, 1, cl), T, o);
-    }
-  }
-}
-
-// block size (when fixed at compile time) and resident blocks the registers are built for
-template <int T, int PS, int GS>
-struct Rb2Bounds {
-  static constexpr int thr = (PS && GS) ? T / 2 * PS * GS : 256;
-  static constexpr int minb = 512 / thr > 0 ? 512 / thr : 1;
-};
-
-template <int T, int NP, int PS, int GS>
-__global__ void __launch_bounds__(Rb2Bounds<T, PS, GS>::thr, Rb2Bounds<T, PS, GS>::minb)
-    k_mx_rb2(int J, int N, int G, int n_types, int stage, const int32_t *__restrict__ type, const float *Linv_g,
-             const float *Cin_g, const float *Mp_g, const float *w_g, const float *__restrict__ z, float *D0,
-             float *D1, DevState *ds, double *__restrict__ partials, unsigned *gbar, double *e_hist,
-             cudaGraphConditionalHandle cond, int use_cond, int max_sweeps) {
-  constexpr int TH = T / 2;
-  extern __shared__ __align__(16) float smr[];
-  __shared__ double red[8];
-  __shared__ DevState sd;
-  __shared__ int s_ok, s_roll;
-  const int P = N / NP, G4 = 4 * G, R = 4 * N * G;
-  const int cl = threadIdx.x, gy = threadIdx.y;
-  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-  const int nthr = blockDim.x * blockDim.y;
-  if (tid == 0) sd = *ds;
-  __syncthreads();
-  if (sd.done) return;  // uniform across the grid
-  Rb2Args a;
-  a.J = J;
-  a.N = N;
-  a.G = G;
-  a.type = type;
-  a.z = z;
-  a.y_s = smr;
-  a.yr_s = a.y_s + (size_t)G * P * 4 * TH;
-  a.s_s = a.yr_s + (size_t)G4 * TH;
-  a.Ri = a.s_s + (size_t)G4 * TH;
-  a.Bi = a.Ri + (size_t)2 * R * TH;
-  a.R2 = a.Bi + (size_t)2 * R * TH;
-  a.hRL = a.R2 + (size_t)2 * R * TH;
-  a.hBL = a.hRL + R;
-  a.hRR0 = a.hBL + R;
-  a.hRR1 = a.hRR0 + R;
-  a.hBR = a.hRR1 + R;
-  a.hR2 = a.hBR + R;
-  a.Linv = Linv_g;
-  a.Cin = Cin_g;
-  a.Mp = Mp_g;
-  a.w = w_g;
-  if (stage) {
-    stage_tables(a.hR2 + R, n_types, N, G, tid, nthr, a.Linv, a.Cin, a.Mp, a.w);
-    __syncthreads();
-  }
-  const int ntiles = (J + T - 1) / T;
-  a.t0 = (int)((long long)blockIdx.x * ntiles / gridDim.x);
-  a.t1 = (int)((long long)(blockIdx.x + 1) * ntiles / gridDim.x);
-  bool failed = false;
-  for (int sw = 0, pass = 0;; pass++) {
-    const int ns = max_sweeps - sw >= 2 ? 2 : 1;
-    const bool zero = sd.refine || sd.blk_i == 0;
-    const float *__restrict__ Din = sd.dcur ? D1 : D0;
-    float *__restrict__ Dout = sd.dcur ? D0 : D1;
-    float ea = 0.f, eb = 0.f;
-    rb2_pass<T, NP, PS, GS>(a, cl, gy, zero, ns, Din, Dout, ea, eb);
-    const double ba = block_reduce_fixed(ea, red, tid, nthr);
-    const double bb = block_reduce_fixed(eb, red, tid, nthr);
-    double *part = partials + (size_t)(pass & 1) * 2 * gridDim.x;
-    if (tid == 0) {
-      part[blockIdx.x] = ba;
-      part[gridDim.x + blockIdx.x] = bb;
-      s_ok = grid_barrier(gbar, gridDim.x);
-    }
-    __syncthreads();
-    if (!s_ok) {
-      failed = true;
-      break;
-    }
-    const double ta = block_sum_fixed(part, gridDim.x, red);
-    const double tb = ns == 2 ? block_sum_fixed(part + gridDim.x, gridDim.x, red) : 0.0;
-    if (tid == 0) {
-      double *eh = blockIdx.x == 0 ? e_hist : nullptr;
-      finish_mixed(&sd, eh, sqrt(ta), cond, 0);
-      s_roll = 0;
-      if (ns == 2) {
-        if (sd.done || sd.refine) {
-          s_roll = 1;  // the inner block ends at sweep i
-        } else {
-          finish_mixed(&sd, eh, sqrt(tb), cond, 0);
-          if (!sd.inplace) sd.dcur ^= 1;  // one buffer flip per pass
-        }
-      }
-    }
-    __syncthreads();
-    if (s_roll) {  // sweep i alone into Dout (delta^{i-1} is untouched in Din)
-      float x = 0.f, y = 0.f;
-      rb2_pass<T, NP, PS, GS>(a, cl, gy, zero, 1, Din, Dout, x, y);
-      break;
-    }
-    sw += ns;
-    if (sd.done || sd.refine || sw >= max_sweeps) break;  // uniform: every block holds the same state
-  }
-  if (blockIdx.x == 0 && tid == 0) {
-    if (failed) {
-      sd.status = OCI_E_TIMEOUT;
-      sd.done = 1;
-      sd.refine = 0;
-    }
-    *ds = sd;
-    if (use_cond) {
-      if (sd.done) cudaGraphSetConditional(cond, 0);
-      if (sd.cond_ref) cudaGraphSetConditional((cudaGraphConditionalHandle)sd.cond_ref, sd.refine);
-    }
-  }
-}
-
-size_t mx_rb2_smem(const Handle &h, int T, int P, bool stage) {
-  const size_t G = h.G, N = h.N, TH = T / 2, R = 4 * N * G;
-  return ((size_t)TH * (G * P * 4 + 8 * G) + 6 * R * TH + 6 * R) * 4 + (stage ? mx_tables_floats(h) * 4 + 16 : 0);
-}
-
-template <int T, int NP, int PS, int GS>
-static void launch_rb2(Handle &h, int P, cudaGraphConditionalHandle cond, int use_cond, int max_sweeps) {
-  const bool stage = mx_tables_floats(h) * 4 <= 64 * 1024;
-  const size_t smem = mx_rb2_smem(h, T, P, stage);
-  int dev = 0, sms = 0, per = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mx_rb2<T, NP, PS, GS>, (T / 2) * h.G * P, smem);
-  const int ntiles = (h.J + T - 1) / T;
-  const int grid = std::min(sms * (per > 0 ? per : 1), ntiles);
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(T / 2, h.G * P);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = h.stream;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeCooperative;  // all blocks resident: they wait on one another
-  attr[0].val.cooperative = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, k_mx_rb2<T, NP, PS, GS>, h.J, h.N, h.G, h.tt.n_types, (int)stage,
-                     (const int32_t *)h.type, (const float *)h.tt.Linv32, (const float *)h.tt.Cin32,
-                     (const float *)h.tt.Mp32, (const float *)h.w32, (const float *)h.z32, h.delta[0], h.delta[1],
-                     h.ds, h.partials, h.gbar, h.e_hist, cond, use_cond, max_sweeps);
-}
-
-// S16, one group: angle chunks and groups fixed at compile time; else generic
-static void launch_rb2_any(Handle &h, cudaGraphConditionalHandle cond, int use_cond, int max_sweeps) {
-  const int T = h.mx_cb, P = h.mx_P, np = h.N / P;
-  const bool s16 = h.N == 16 && h.G == 1;
-#define OCI_RB2(TT, NPP)                                                         \
-  do {                                                                           \
-    if (s16) launch_rb2<TT, NPP, 16 / NPP, 1>(h, P, cond, use_cond, max_sweeps); \
-    else launch_rb2<TT, NPP, 0, 0>(h, P, cond, use_cond, max_sweeps);            \
-  } while (0)
-  if (T == 32) {
-    if (np == 2) OCI_RB2(32, 2);
-    else OCI_RB2(32, 4);
-  } else {
-    if (np == 2) OCI_RB2(64, 2);
-    else OCI_RB2(64, 4);
-  }
-#undef OCI_RB2
 }
 
 // ---------------------------------------------------------------- inner sweep, TMA-staged
@@ -2920,21 +1950,12 @@ int mx_set_attributes() {
                       (const void *)k_mx_inner_ms<64, 8>, (const void *)k_mx_rb<32, 2>,
                       (const void *)k_mx_rb<32, 4>, (const void *)k_mx_rb<32, 8>,
                       (const void *)k_mx_rb<64, 2>, (const void *)k_mx_rb<64, 4>,
-                      (const void *)k_mx_rb<64, 8>, (const void *)k_mx_inner_ms2<32, 2, 0, 0, 2>,
-                      (const void *)k_mx_inner_ms2<32, 4, 0, 0, 2>, (const void *)k_mx_inner_ms2<64, 2, 0, 0, 2>,
-                      (const void *)k_mx_inner_ms2<64, 4, 0, 0, 2>, (const void *)k_mx_inner_ms2<32, 2, 8, 1, 2>,
-                      (const void *)k_mx_inner_ms2<32, 4, 4, 1, 4>, (const void *)k_mx_inner_ms2<64, 2, 8, 1, 1>,
-                      (const void *)k_mx_inner_ms2<64, 4, 4, 1, 2>, (const void *)k_mx_inner_ms2<32, 2, 8, 1, 3>,
-                      (const void *)k_mx_inner_ms2<32, 4, 4, 1, 5>, (const void *)k_mx_inner_ms2<64, 4, 4, 1, 3>,
-                      (const void *)k_mx_rb2<32, 2, 0, 0>, (const void *)k_mx_rb2<32, 4, 0, 0>,
-                      (const void *)k_mx_rb2<64, 2, 0, 0>, (const void *)k_mx_rb2<64, 4, 0, 0>,
-                      (const void *)k_mx_rb2<32, 2, 8, 1>, (const void *)k_mx_rb2<32, 4, 4, 1>,
-                      (const void *)k_mx_rb2<64, 2, 8, 1>, (const void *)k_mx_rb2<64, 4, 4, 1>};
+                      (const void *)k_mx_rb<64, 8>};
   for (const void *k : ks) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(FP32 inner sweep)");
   }
-  return OCI_OK;
+  return mx_two_set_attributes();
 }
 
 }  // namespace oci
