@@ -31,7 +31,7 @@ def test_fourier_si_flat_mode_closed_form():
 
 
 def test_fourier_oci_trend_with_mean_free_time():
-    """rho_OCI falls as the mean free time shrinks (spec trend)."""
+    """rho_OCI falls as the mean free time shrinks (the trend of Sec. 2.3 and Table 1)."""
     taus = np.array([10.0, 1.0, 0.1, 0.01])
     r = oci.fourier_rho(oci.FOURIER_OCI, 16, np.full(4, 0.1), taus, np.full(4, 0.99), n_theta=121)
     assert np.all(np.diff(r) < 0) and r[-1] < 0.1 * r[0]

@@ -335,7 +335,7 @@ def test_measured_rate_matches_fourier_verification_problem():
 
 
 def test_iteration_counts_fall_with_mean_free_time():
-    """North-star trend (Sec. 3.1): at fixed delta and c, OCI needs fewer
+    """Trend of Sec. 3.1: at fixed delta and c, OCI needs fewer
     iterations as tau shrinks, as the Fourier rho predicts."""
     J, N = 120, 8
     counts, rhos = [], []
