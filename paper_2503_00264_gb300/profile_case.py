@@ -4,6 +4,7 @@
     python -m paper_2503_00264_gb300.profile_case --case multigroup --sweeps 3
     python -m paper_2503_00264_gb300.profile_case --case slab3 --si --sweeps 2
     python -m paper_2503_00264_gb300.profile_case --case batch --slabs 64 --ng 32,4
+    python -m paper_2503_00264_gb300.profile_case --case slab3 --precision fp32 --ordering rb --steps 1
 
 Sets up the workload, loads a seeded random iterate and runs exactly --sweeps
 sweeps through the C ABI (oci_iterate / si_iterate), then exits.  Prints one
@@ -48,6 +49,7 @@ def main():
     ap.add_argument("--ng", default=None, help="batch: keep only slabs of this N,G")
     ap.add_argument("--batch-max-iter", type=int, default=200)
     ap.add_argument("--j-hi", type=int, default=8192, help="batch: largest slab (cells)")
+    ap.add_argument("--ordering", default="jacobi", choices=["jacobi", "rb"], help="cell ordering of the sweeps")
     a = ap.parse_args()
     import torch
     prec = {"fp64": oci.FP64, "fp32": oci.FP32_IR, "tf32": oci.TF32_IR, "bf16x3": oci.BF16X3_IR}[a.precision]
@@ -73,6 +75,8 @@ def main():
     solver = oci.SOLVER_DENSE_LU if a.solver == "dense" else oci.SOLVER_STRUCTURED
     stream = torch.cuda.Stream()
     with oci.Solver(p, solver=solver, precision=prec, stream=stream.cuda_stream) as s:
+        if a.ordering == "rb":
+            s.set_ordering(oci.ORDER_RED_BLACK)
         print("setup:", s.info())
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         if a.steps:
