@@ -13,9 +13,9 @@ namespace oci {
 // Two red-black sweeps (i, i+1) in one pass over the correction, by the run
 // walk of the Jacobi form: at step k a block computes red^i on tile k+1 (from
 // delta^{i-1} in global memory), black^i on tile k, red^{i+1} on tile k and
-// black^{i+1} on tile k-1; every input is either global delta^{i-1} or a
-// half-tile of this pass kept in shared memory (red^i, black^i, red^{i+1}: two
-// slots each, by tile parity).  The cells next to the run whose values the walk
+// black^{i+1} on tile k-1; every input is global delta^{i-1}, a half-tile of
+// this pass kept in shared memory (red^i, black^i: two slots each, by tile
+// parity), or red^{i+1} that the block itself has just written to the output.  The cells next to the run whose values the walk
 // needs are recomputed by the block: red^i and black^i of the two cells before
 // it, red^i of the first two red cells after it, black^i between those and
 // red^{i+1} of the first cell after it.  Results go to the other buffer (not in
@@ -68,7 +68,7 @@ struct Rb2Args {
   const float *Linv, *Cin, *Mp, *w;
   const float *__restrict__ z;
   float *y_s, *yr_s, *s_s;
-  float *Ri, *Bi, *R2;                         // two half-tile slots each ([R][T/2])
+  float *Ri, *Bi;                              // two half-tile slots each ([R][T/2])
   float *hRL, *hBL, *hRR0, *hRR1, *hBR, *hR2;  // cells next to the run, [R] each
 };
 
@@ -241,7 +241,6 @@ __device__ void rb2_pass(const Rb2Args &a, int cl, int gy, bool zero, int ns, co
       solve(o, zr, uk, uh, act, j);
       if (act) {
         eb += ms2_dist2<NP>(o, old);
-        rb2_put<NP>(scol(a.R2, k, cl), TH, o);
         rb2_put<NP>(gout(k, 0, cl), T, o);
       }
     }
@@ -250,12 +249,12 @@ __device__ void rb2_pass(const Rb2Args &a, int cl, int gy, bool zero, int ns, co
       const int kk = k - 1, j = kk * T + 2 * cl + 1;
       const bool act = j < J;
       const float *L = nullptr, *Rt = nullptr;
-      if (act) {
-        L = scol(a.R2, kk, cl);
-        if (j + 1 < J) Rt = cl + 1 < TH ? scol(a.R2, kk, cl + 1) : scol(a.R2, k, 0);
+      if (act) {  // red^{i+1} of tiles k-1 and k: written to Dout by this block at (c)
+        L = gcol(Dout, kk, 0, cl);
+        if (j + 1 < J) Rt = cl + 1 < TH ? gcol(Dout, kk, 0, cl + 1) : gcol(Dout, k, 0, 0);
       }
       float zr[NP][4], old[NP][4], uk[NP], uh[NP], o[NP][4];
-      rb2_inflow<NP>(uk, uh, L, TH, Rt, TH, m0, N2);
+      rb2_inflow<NP>(uk, uh, L, T, Rt, T, m0, N2);
       rb2_get<NP>(zr, gcol(a.z, kk, 1, cl), T, act);
       rb2_get<NP>(old, scol(a.Bi, kk, cl), TH, act);
       solve(o, zr, uk, uh, act, j);
@@ -286,16 +285,16 @@ __device__ void rb2_pass(const Rb2Args &a, int cl, int gy, bool zero, int ns, co
     const int kk = t1 - 1, j = kk * T + 2 * cl + 1;
     const bool act = j < J;
     const float *L = nullptr, *Rt = nullptr;
-    int rs = TH;
+    int rs = T;
     if (act) {
-      L = scol(a.R2, kk, cl);
+      L = gcol(Dout, kk, 0, cl);
       if (j + 1 < J) {
-        if (cl + 1 < TH) Rt = scol(a.R2, kk, cl + 1);
+        if (cl + 1 < TH) Rt = gcol(Dout, kk, 0, cl + 1);
         else Rt = a.hR2 + row0, rs = 1;
       }
     }
     float zr[NP][4], old[NP][4], uk[NP], uh[NP], o[NP][4];
-    rb2_inflow<NP>(uk, uh, L, TH, Rt, rs, m0, N2);
+    rb2_inflow<NP>(uk, uh, L, T, Rt, rs, m0, N2);
     rb2_get<NP>(zr, gcol(a.z, kk, 1, cl), T, act);
     rb2_get<NP>(old, scol(a.Bi, kk, cl), TH, act);
     solve(o, zr, uk, uh, act, j);
@@ -342,8 +341,7 @@ __global__ void __launch_bounds__(Rb2Bounds<T, PS, GS>::thr, Rb2Bounds<T, PS, GS
   a.s_s = a.yr_s + (size_t)G4 * TH;
   a.Ri = a.s_s + (size_t)G4 * TH;
   a.Bi = a.Ri + (size_t)2 * R * TH;
-  a.R2 = a.Bi + (size_t)2 * R * TH;
-  a.hRL = a.R2 + (size_t)2 * R * TH;
+  a.hRL = a.Bi + (size_t)2 * R * TH;
   a.hBL = a.hRL + R;
   a.hRR0 = a.hBL + R;
   a.hRR1 = a.hRR0 + R;
@@ -421,7 +419,7 @@ __global__ void __launch_bounds__(Rb2Bounds<T, PS, GS>::thr, Rb2Bounds<T, PS, GS
 
 size_t mx_rb2_smem(const Handle &h, int T, int P, bool stage) {
   const size_t G = h.G, N = h.N, TH = T / 2, R = 4 * N * G;
-  return ((size_t)TH * (G * P * 4 + 8 * G) + 6 * R * TH + 6 * R) * 4 + (stage ? mx_tables_floats(h) * 4 + 16 : 0);
+  return ((size_t)TH * (G * P * 4 + 8 * G) + 4 * R * TH + 6 * R) * 4 + (stage ? mx_tables_floats(h) * 4 + 16 : 0);
 }
 
 template <int T, int NP, int PS, int GS>
