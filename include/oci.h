@@ -170,7 +170,9 @@ typedef struct {
                                 correction arrays, 5 the same as a persistent kernel, 6 that with
                                 the tiles moved by 1D bulk copies (TMA), 7 red-black ordering,
                                 9 two inner sweeps per pass over the correction (temporal
-                                blocking); -1 for the FP64 form                                   */
+                                blocking), 10 the same built for more resident blocks per SM,
+                                11 red-black ordering with two sweeps per pass; -1 for the FP64
+                                form                                                              */
   double tuned_sweep_us;     /* measured time of one sweep with the chosen shape (0 if not tuned) */
 } oci_info;
 
