@@ -409,19 +409,23 @@ static int autotune(Handle &h) {
     };
     h.mx_tune_sweeps = multi ? 1 : 0;
     sweep();
-    CK(cudaEventRecord(h.ev0, h.stream));
-    if (multi) {
-      h.mx_tune_sweeps = reps;
-      sweep();
-    } else {
-      for (int r = 0; r < reps; r++) sweep();
+    float ms = 1e30f;
+    for (int t = 0; t < 2; t++) {  // the faster of two timings: one disturbed launch picks no shape
+      CK(cudaEventRecord(h.ev0, h.stream));
+      if (multi) {
+        h.mx_tune_sweeps = reps;
+        sweep();
+      } else {
+        for (int r = 0; r < reps; r++) sweep();
+      }
+      CK(cudaEventRecord(h.ev1, h.stream));
+      CK(cudaEventSynchronize(h.ev1));
+      CK(cudaGetLastError());
+      float m = 0.f;
+      cudaEventElapsedTime(&m, h.ev0, h.ev1);
+      ms = std::min(ms, m);
     }
     h.mx_tune_sweeps = 0;
-    CK(cudaEventRecord(h.ev1, h.stream));
-    CK(cudaEventSynchronize(h.ev1));
-    CK(cudaGetLastError());
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, h.ev0, h.ev1);
     if (ms < best) {
       best = ms;
       bc = c;
@@ -509,15 +513,19 @@ static int tune_rb(Handle &h) {
     CK(cudaMemcpyAsync(h.ds, h.h_ds, sizeof(DevState), cudaMemcpyHostToDevice, h.stream));
     h.mx_tune_sweeps = 1;
     launch_mx_inner(h, cudaGraphConditionalHandle{}, 0);
-    CK(cudaEventRecord(h.ev0, h.stream));
-    h.mx_tune_sweeps = reps;
-    launch_mx_inner(h, cudaGraphConditionalHandle{}, 0);
+    float ms = 1e30f;
+    for (int t = 0; t < 2; t++) {  // the faster of two timings: one disturbed launch picks no shape
+      CK(cudaEventRecord(h.ev0, h.stream));
+      h.mx_tune_sweeps = reps;
+      launch_mx_inner(h, cudaGraphConditionalHandle{}, 0);
+      CK(cudaEventRecord(h.ev1, h.stream));
+      CK(cudaEventSynchronize(h.ev1));
+      CK(cudaGetLastError());
+      float m = 0.f;
+      cudaEventElapsedTime(&m, h.ev0, h.ev1);
+      ms = std::min(ms, m);
+    }
     h.mx_tune_sweeps = 0;
-    CK(cudaEventRecord(h.ev1, h.stream));
-    CK(cudaEventSynchronize(h.ev1));
-    CK(cudaGetLastError());
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, h.ev0, h.ev1);
     if (ms < best) {
       best = ms;
       bc = c;
