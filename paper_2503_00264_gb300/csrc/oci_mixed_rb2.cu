@@ -15,10 +15,11 @@ namespace oci {
 // delta^{i-1} in global memory), black^i on tile k, red^{i+1} on tile k and
 // black^{i+1} on tile k-1; every input is global delta^{i-1}, a half-tile of
 // this pass kept in shared memory (red^i, black^i: two slots each, by tile
-// parity), or red^{i+1} that the block itself has just written to the output.  The cells next to the run whose values the walk
-// needs are recomputed by the block: red^i and black^i of the two cells before
-// it, red^i of the first two red cells after it, black^i between those and
-// red^{i+1} of the first cell after it.  Results go to the other buffer (not in
+// parity), or red^{i+1} that the block itself has just written to the output.
+// The cells next to the run whose values the walk needs are recomputed by the
+// block: red^i and black^i of the two cells before it, red^i of the first two
+// red cells after it, black^i between those and red^{i+1} of the first cell
+// after it.  Results go to the other buffer (not in
 // place: a neighbouring block still reads delta^{i-1} there), so one pass reads
 // z and delta^{i-1} once and writes delta^{i+1} once; the device state takes
 // the two norms in order, and when the first ends an inner block the sweep is

@@ -16,7 +16,7 @@ namespace oci {
 // global memory, then delta^{i+2} on tile k-1, whose lagged inflows are the
 // delta^{i+1} values of tiles k-2, k-1 and k held in a three-slot ring in
 // shared memory.  The delta^{i+1} values of the two cells just outside the run
-// (a0 - 1 and a1) are recomputed by the block before the walk, so blocks never
+// (t0 T - 1 and t1 T) are recomputed by the block before the walk, so blocks never
 // wait on one another inside a pass.  Per two sweeps a pass reads z and
 // delta^i once and writes delta^{i+2} once: 12 bytes per unknown instead of
 // 24.  Both sweeps' norms are reduced and the device state takes the two e
