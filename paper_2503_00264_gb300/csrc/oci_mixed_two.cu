@@ -165,13 +165,11 @@ __device__ void ms2_pass2(const Ms2Args &a, int cl, int gy, bool zero, const flo
 // OCC: resident blocks per SM the register allocation is built for (the
 // block size is T * PS * GS threads when known at compile time, else <= 256).
 template <int T, int NP, int PS, int GS, int OCC>
-__global__ void __launch_bounds__((PS && GS) ? T * PS * GS : 256, OCC) k_mx_inner_ms2(int J, int N, int G, int n_types, int stage,
-                                                      const int32_t *__restrict__ type, const float *Linv_g,
-                                                      const float *Cin_g, const float *Mp_g, const float *w_g,
-                                                      const float *__restrict__ z, float *D0, float *D1,
-                                                      DevState *ds, double *__restrict__ partials, unsigned *gbar,
-                                                      double *e_hist, cudaGraphConditionalHandle cond, int use_cond,
-                                                      int max_sweeps) {
+__global__ void __launch_bounds__((PS && GS) ? T * PS * GS : 256, OCC)
+    k_mx_inner_ms2(int J, int N, int G, int n_types, int stage, const int32_t *__restrict__ type, const float *Linv_g,
+                   const float *Cin_g, const float *Mp_g, const float *w_g, const float *__restrict__ z, float *D0,
+                   float *D1, DevState *ds, double *__restrict__ partials, unsigned *gbar, double *e_hist,
+                   cudaGraphConditionalHandle cond, int use_cond, int max_sweeps) {
   extern __shared__ __align__(16) float smr[];
   __shared__ double red[8];
   __shared__ DevState sd;
