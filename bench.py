@@ -34,7 +34,15 @@ SAMPLE_J = 3072
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_oci_sweep launch on this workload
 # (2^18 cells, S16, G = 1, tuned shape 64 cells x 2 angle chunks), from the ncu --set full
 # capture summarised in profiles/.
-SWEEP_DRAM_BYTES_NCU = 271.808768e6 + 100.235776e6
+# ncu dram__bytes_read.sum + dram__bytes_write.sum of one FP64 sweep launch on the 2^18-cell S16
+# slab, per (kernel: 0 staged / 1 register form, cells per block, angle chunks) the autotuner can pick
+SWEEP_DRAM_BYTES_NCU = {
+    (0, 64, 2): 271.829760e6 + 100.329984e6,
+    (1, 16, 4): 269.720832e6 + 103.894016e6, (1, 16, 8): 269.715712e6 + 105.035520e6,
+    (1, 32, 2): 269.782528e6 + 102.594304e6, (1, 32, 4): 269.660416e6 + 103.412224e6,
+    (1, 32, 8): 269.596160e6 + 104.473856e6, (1, 64, 2): 269.743616e6 + 102.103040e6,
+    (1, 64, 4): 269.611264e6 + 103.353856e6,
+}
 # FP64 issue rate of one SM: 2 DFMA per clock (GB300: 1.25 TFLOP/s FP64 = 152 SMs x 2 x 2 flops
 # x 2.07 GHz); the ALU roofline's peak = SMs x this x 2 flops x the maximum SM clock.
 FP64_FMA_PER_SM_CLK = 2
@@ -185,6 +193,7 @@ def run_ours(args):
     solver = oci.SOLVER_DENSE_LU if args.solver == "dense" else oci.SOLVER_STRUCTURED
     peak_fp64 = oci.fp64_peak()
     s = oci.Solver(p, solver=solver, stream=stream.cuda_stream)
+    info64 = s.info()
     smx = None if args.no_mixed else oci.Solver(p, precision=oci.FP32_IR, stream=stream.cuda_stream)
 
     def barrier():
@@ -432,6 +441,11 @@ def run_ours(args):
     bytes_cell = 96 * NG + 4
     flops = flops_cell * p.J
     achieved_tf = flops / (sweep_ms * 1e-3) / 1e12
+    # the FP64 sweep kernel and launch shape the autotuner picked for this handle
+    sweep_key = (info64["sweep_kernel"], info64["cells_per_block"], info64["angle_chunks"])
+    sweep_name = (f"k_oci_sweep_reg<{p.N // info64['angle_chunks']}>" if info64["sweep_kernel"] == 1
+                  else "k_oci_sweep_t<0>") + \
+        f" (FP64 structured cell solve; {info64['cells_per_block']} cells x {info64['angle_chunks']} angle chunks)"
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
     clk_mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
     peak_alu = n_sm * FP64_FMA_PER_SM_CLK * 2 * clk_mhz * 1e6
@@ -468,10 +482,11 @@ def run_ours(args):
             "sweeps_per_step": sweeps / args.steps,
             "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": peak_alu / 1e12, "unit": "TFLOP/s",
                          "frac": achieved_tf * 1e12 / peak_alu,
-                         "traffic": SWEEP_DRAM_BYTES_NCU if (p.J == 2 ** 18 and p.N == 16 and p.G == 1) else None,
+                         "traffic": SWEEP_DRAM_BYTES_NCU.get(sweep_key) if (p.J == 2 ** 18 and p.N == 16 and
+                                                                             p.G == 1) else None,
                          "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
                          "algorithmic_bytes": bytes_cell * p.J,
-                         "kernel": "k_oci_sweep (FP64 structured cell solve)",
+                         "kernel": sweep_name,
                          "peak_source": f"derived: {n_sm} SMs x {FP64_FMA_PER_SM_CLK} FP64 FMA/clk x 2 flops x "
                                         f"{clk_mhz:.0f} MHz max SM clock",
                          "peak_measured_dfma_loop": peak_fp64 / 1e12,

@@ -174,6 +174,9 @@ typedef struct {
                                 11 red-black ordering with two sweeps per pass; -1 for the FP64
                                 form                                                              */
   double tuned_sweep_us;     /* measured time of one sweep with the chosen shape (0 if not tuned) */
+  int32_t sweep_kernel;      /* FP64 form: 0 angles staged in shared memory (k_oci_sweep_t),
+                                1 angles in registers (k_oci_sweep_reg); -1 for the other forms  */
+  int32_t reserved;          /* 0                                                                 */
 } oci_info;
 
 typedef struct oci_handle oci_handle;

@@ -1326,6 +1326,8 @@ int oci_get_info(const oci_handle *h, oci_info *info) {
     info->inner_kernel = 2;
   }
   info->tuned_sweep_us = h->tune_us;
+  info->sweep_kernel = h->precision == OCI_FP64 && h->solver != OCI_SOLVER_DENSE_LU ? (h->tune_reg ? 1 : 0) : -1;
+  info->reserved = 0;
   return OCI_OK;
 }
 
