@@ -34,6 +34,38 @@ def test_exports_every_declared_symbol(lib):
     assert set(names) == set(oci.EXPORTS)
 
 
+def test_struct_layouts_match_the_compiled_header(tmp_path):
+    """sizeof and every field offset of oci_problem, oci_stats and oci_info as a C
+    compiler lays them out from include/oci.h equal those of the ctypes binding."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"oci_problem": oci.Problem, "oci_stats": oci.Stats, "oci_info": oci.Info}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "oci.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'  printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run([cc, "-std=c11", "-I", inc, str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for ln in out:
+        parts = ln.split()
+        if len(parts) == 3:
+            got[(parts[0], parts[1])] = int(parts[2])
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
+
+
 def test_struct_layout_matches_header():
     # oci_problem: 4 int32, 6 pointers, double, 3 pointers, double, 4 int32, pointer
     assert ctypes.sizeof(oci.Problem) == 16 + 6 * 8 + 8 + 3 * 8 + 8 + 16 + 8
