@@ -654,6 +654,8 @@ static int setup_impl(const oci_problem *p, oci_handle *h) {
   {
     const char *mm = getenv("OCI_MX_MULTI");  // 0: one inner sweep per launch in the graph as well
     h->mx_multi = !(mm && mm[0] == '0');
+    const char *cv = getenv("OCI_MX_OUTER_CVT");  // "hw": compiler conversions in the FP64 refinement
+    h->mx_hwcvt = (cv && cv[0] == 'h') ? 1 : 0;
   }
   const int nblk_carry = (h->J + 31) / 32;
   CK(cudaMalloc(&h->bal_partials, (size_t)nblk_carry * G * 8 * 8));

@@ -21,6 +21,7 @@
 #include <algorithm>
 
 #include "oci_batch.h"
+#include "oci_cvt.cuh"
 #include "oci_device.cuh"
 
 namespace oci {
@@ -491,7 +492,10 @@ __global__ void __launch_bounds__(kBFinThreads) k_b_mx_finalize(BatchClassDev c,
 // FP64 refinement per slab (k_mx_outer with slab ends): mode 0 residual of
 // Psi[cur] for every slab; mode 1 for slabs that asked for it: Psi[cur^1] =
 // Psi[cur] + delta[dcur] and, unless the slab is done, its residual.
-__global__ void __launch_bounds__(256) k_b_mx_outer(BatchClassDev c, const DevState *__restrict__ ds, int mode) {
+// hwcvt = 0: integer-pipe conversions and in-tile upstream neighbours read back
+// from Psi[cur^1], as in k_mx_outer; hwcvt = 1: compiler conversions (same bits).
+__global__ void __launch_bounds__(256) k_b_mx_outer(BatchClassDev c, const DevState *__restrict__ ds, int mode,
+                                                    int hwcvt) {
   extern __shared__ double smd[];
   const int CB = blockDim.x, N = c.N, G = c.G, Jc = c.Jc;
   const int cl = threadIdx.x, g = threadIdx.y;
@@ -501,6 +505,7 @@ __global__ void __launch_bounds__(256) k_b_mx_outer(BatchClassDev c, const DevSt
     if (mode == 0 && ds[s].done) continue;
     const bool apply = mode != 0;
     const bool resid = mode == 0 || !ds[s].done;
+    const bool reuse = apply && !hwcvt;
     const int cur = ds[s].cur;
     const double *__restrict__ Pin = cur ? c.Psi1 : c.Psi0;
     double *__restrict__ Pout = cur ? c.Psi0 : c.Psi1;
@@ -525,7 +530,7 @@ __global__ void __launch_bounds__(256) k_b_mx_outer(BatchClassDev c, const DevSt
           for (int p = 0; p < 4; p++) {
             double v = Pin[base + (size_t)p * Jc];
             if (apply) {
-              v += (double)Dl[base + (size_t)p * Jc];
+              v += cvt_f2d(hwcvt, Dl[base + (size_t)p * Jc]);
               Pout[base + (size_t)p * Jc] = v;
             }
             ph[p] = fma(wm, v, ph[p]);
@@ -545,7 +550,7 @@ __global__ void __launch_bounds__(256) k_b_mx_outer(BatchClassDev c, const DevSt
 #pragma unroll
         for (int p = 0; p < 4; p++) sv[p] = fma(k, ph_s[(size_t)(gp * 4 + p) * CB + cl], sv[p]);
       }
-      const double *__restrict__ P = apply ? Pout : Pin;
+      const double *P = apply ? Pout : Pin;  // Pout: written by this block before the barrier
       for (int m = 0; m < N; m++) {
         const int gm = g * N + m;
         const size_t base = (size_t)gm * 4 * Jc + j;
@@ -561,11 +566,16 @@ __global__ void __launch_bounds__(256) k_b_mx_outer(BatchClassDev c, const DevSt
           double uk, uh;
           if (jl > 0) {
             const size_t nb = base - 1;
-            uk = Pin[nb + (size_t)Jc];
-            uh = Pin[nb + 3 * (size_t)Jc];
-            if (apply) {
-              uk += (double)Dl[nb + (size_t)Jc];
-              uh += (double)Dl[nb + 3 * (size_t)Jc];
+            if (reuse && cl > 0) {
+              uk = Pout[nb + (size_t)Jc];
+              uh = Pout[nb + 3 * (size_t)Jc];
+            } else {
+              uk = Pin[nb + (size_t)Jc];
+              uh = Pin[nb + 3 * (size_t)Jc];
+              if (apply) {
+                uk += cvt_f2d(hwcvt, Dl[nb + (size_t)Jc]);
+                uh += cvt_f2d(hwcvt, Dl[nb + 3 * (size_t)Jc]);
+              }
             }
           } else {
             uk = inc[gm * 2 + 0];
@@ -577,11 +587,16 @@ __global__ void __launch_bounds__(256) k_b_mx_outer(BatchClassDev c, const DevSt
           double uk, uh;
           if (jl < Js - 1) {
             const size_t nb = base + 1;
-            uk = Pin[nb];
-            uh = Pin[nb + 2 * (size_t)Jc];
-            if (apply) {
-              uk += (double)Dl[nb];
-              uh += (double)Dl[nb + 2 * (size_t)Jc];
+            if (reuse && cl < CB - 1) {
+              uk = Pout[nb];
+              uh = Pout[nb + 2 * (size_t)Jc];
+            } else {
+              uk = Pin[nb];
+              uh = Pin[nb + 2 * (size_t)Jc];
+              if (apply) {
+                uk += cvt_f2d(hwcvt, Dl[nb]);
+                uh += cvt_f2d(hwcvt, Dl[nb + 2 * (size_t)Jc]);
+              }
             }
           } else {
             uk = inc[(G * N + gm) * 2 + 0];
@@ -594,7 +609,7 @@ __global__ void __launch_bounds__(256) k_b_mx_outer(BatchClassDev c, const DevSt
         r1 = fma(hm, v0, fma(-a, v1, fma(-ha, v3, r1)));
         r2 = fma(al, v0, fma(-aa, v2, fma(-hm, v3, r2)));
         r3 = fma(al, v1, fma(hm, v2, fma(-aa, v3, r3)));
-        const float f0 = (float)r0, f1 = (float)r1, f2 = (float)r2, f3 = (float)r3;
+        const float f0 = cvt_d2f(hwcvt, r0), f1 = cvt_d2f(hwcvt, r1), f2 = cvt_d2f(hwcvt, r2), f3 = cvt_d2f(hwcvt, r3);
         const float *Li = c.Linv32 + ((size_t)tau * G * N + gm) * 16;
 #pragma unroll
         for (int p = 0; p < 4; p++)
@@ -884,8 +899,10 @@ void launch_b_mx_outer(BatchClass &c, DevState *ds, int mode, cudaStream_t st) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int grid = std::min(c.d.n_tiles, 4 * sms);
+  const char *cv = getenv("OCI_MX_OUTER_CVT");  // "hw": compiler conversions
+  const int hwcvt = (cv && cv[0] == 'h') ? 1 : 0;
   k_b_mx_outer<<<grid > 0 ? grid : 1, dim3(c.cb, c.d.G), (size_t)c.cb * c.d.G * 4 * sizeof(double), st>>>(c.d, ds,
-                                                                                                         mode);
+                                                                                                         mode, hwcvt);
 }
 
 void launch_b_mx_settle(BatchClass &c, DevState *ds, cudaStream_t st) {

@@ -103,6 +103,7 @@ struct Handle {
   int mx_jac_kind = 0, mx_jac_cb = 0, mx_jac_P = 0;  // the Jacobi FP32 inner sweep (kept while red-black)
   int mx_tune_sweeps = 0;              // > 0 while the autotuner times a multi-sweep launch of that many sweeps
   bool mx_multi = true;                // graph runs the persistent tiled FP32 sweep several sweeps per launch
+  int mx_hwcvt = 0;                    // 1: FP64 refinement converts with the compiler's F2F (same bits, slower)
   unsigned *gbar = nullptr;            // {count, generation} of the multi-sweep kernel's grid barrier
   int mx_kind = 0;                     // FP32 inner sweep picked by the autotuner: kMxPlain, kMxTma, kMxReg, kMxTiled
   unsigned char *tc_img = nullptr;     // [T] x (A^{-1} image(s) in the tcgen05 K-major layout)

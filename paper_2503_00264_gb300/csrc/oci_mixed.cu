@@ -24,6 +24,7 @@
 #include <cuda.h>
 #include <math.h>
 
+#include "oci_cvt.cuh"
 #include "oci_device.cuh"
 #include "oci_mixed_dev.cuh"
 
@@ -1579,13 +1580,20 @@ int mx_tma_setup(Handle &h) {
 // mode 2: if ds->blk_i > 0: Psi[cur^1] = Psi[cur] + delta[dcur] (apply only)
 // The residual r = c + s + inflow - L_c Psi (Eqs. oci, Aj, rhs_sg, scatter) is
 // formed in FP64 and z = Linv r (FP32) is stored for the inner sweeps.
+// The kernel is bound by the FP64 pipe, so with hwcvt = 0 the conversions
+// between the FP32 correction / residual and FP64 run on the integer pipe
+// (oci_cvt.cuh, exact) and, in mode 1, an upstream neighbour inside the tile
+// is read back from Psi[cur^1] (written before the block barrier) instead of
+// adding its correction again; hwcvt = 1 keeps the compiler's conversions and
+// the recomputation.  Both give the same bits.
 __global__ void __launch_bounds__(256) k_mx_outer(int J, int Jp, int N, int G, const int32_t *__restrict__ type,
                                                   const double *__restrict__ Lco, const double *__restrict__ Kap,
                                                   const float *__restrict__ Linv32, const double *__restrict__ w,
                                                   const double *__restrict__ mu, const double *__restrict__ inc,
                                                   const double *__restrict__ cvec, double *Psi0, double *Psi1,
                                                   const float *D0, const float *D1, const DevState *__restrict__ ds,
-                                                  int mode, int store_r, float *__restrict__ z32, int tsh) {
+                                                  int mode, int store_r, float *__restrict__ z32, int tsh,
+                                                  int hwcvt) {
   extern __shared__ double smd[];
   const int CB = blockDim.x;
   const int R = 4 * N * G;
@@ -1600,6 +1608,7 @@ __global__ void __launch_bounds__(256) k_mx_outer(int J, int Jp, int N, int G, c
   const float *__restrict__ Dl = ds->dcur ? D1 : D0;
   const int N2 = N / 2;
   const int ntiles = (J + CB - 1) / CB;
+  const bool reuse = apply && !hwcvt;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int j = tile * CB + cl;
     const bool active = j < J;
@@ -1614,7 +1623,7 @@ __global__ void __launch_bounds__(256) k_mx_outer(int J, int Jp, int N, int G, c
         for (int p = 0; p < 4; p++) {
           double v = Pin[base + (size_t)p * Jp];
           if (apply) {
-            v += (double)Dl[fidx(tsh, R, Jp, gm * 4 + p, j)];
+            v += cvt_f2d(hwcvt, Dl[fidx(tsh, R, Jp, gm * 4 + p, j)]);
             Pout[base + (size_t)p * Jp] = v;
           }
           ph[p] = fma(wm, v, ph[p]);
@@ -1634,7 +1643,7 @@ __global__ void __launch_bounds__(256) k_mx_outer(int J, int Jp, int N, int G, c
 #pragma unroll
       for (int p = 0; p < 4; p++) s[p] = fma(k, ph_s[(size_t)(gp * 4 + p) * CB + cl], s[p]);
     }
-    const double *__restrict__ P = apply ? Pout : Pin;
+    const double *P = apply ? Pout : Pin;  // Pout: written by this block before the barrier
     for (int m = 0; m < N; m++) {
       const int gm = g * N + m;
       const size_t base = (size_t)gm * 4 * Jp + j;
@@ -1650,11 +1659,16 @@ __global__ void __launch_bounds__(256) k_mx_outer(int J, int Jp, int N, int G, c
         double uk, uh;
         if (j > 0) {
           const size_t nb = base - 1;
-          uk = Pin[nb + (size_t)Jp];
-          uh = Pin[nb + 3 * (size_t)Jp];
-          if (apply) {
-            uk += (double)Dl[fidx(tsh, R, Jp, gm * 4 + 1, j - 1)];
-            uh += (double)Dl[fidx(tsh, R, Jp, gm * 4 + 3, j - 1)];
+          if (reuse && cl > 0) {
+            uk = Pout[nb + (size_t)Jp];
+            uh = Pout[nb + 3 * (size_t)Jp];
+          } else {
+            uk = Pin[nb + (size_t)Jp];
+            uh = Pin[nb + 3 * (size_t)Jp];
+            if (apply) {
+              uk += cvt_f2d(hwcvt, Dl[fidx(tsh, R, Jp, gm * 4 + 1, j - 1)]);
+              uh += cvt_f2d(hwcvt, Dl[fidx(tsh, R, Jp, gm * 4 + 3, j - 1)]);
+            }
           }
         } else {
           uk = inc[gm * 2 + 0];
@@ -1666,11 +1680,16 @@ __global__ void __launch_bounds__(256) k_mx_outer(int J, int Jp, int N, int G, c
         double uk, uh;
         if (j < J - 1) {
           const size_t nb = base + 1;
-          uk = Pin[nb];
-          uh = Pin[nb + 2 * (size_t)Jp];
-          if (apply) {
-            uk += (double)Dl[fidx(tsh, R, Jp, gm * 4 + 0, j + 1)];
-            uh += (double)Dl[fidx(tsh, R, Jp, gm * 4 + 2, j + 1)];
+          if (reuse && cl < CB - 1) {
+            uk = Pout[nb];
+            uh = Pout[nb + 2 * (size_t)Jp];
+          } else {
+            uk = Pin[nb];
+            uh = Pin[nb + 2 * (size_t)Jp];
+            if (apply) {
+              uk += cvt_f2d(hwcvt, Dl[fidx(tsh, R, Jp, gm * 4 + 0, j + 1)]);
+              uh += cvt_f2d(hwcvt, Dl[fidx(tsh, R, Jp, gm * 4 + 2, j + 1)]);
+            }
           }
         } else {
           uk = inc[(G * N + gm) * 2 + 0];
@@ -1684,7 +1703,7 @@ __global__ void __launch_bounds__(256) k_mx_outer(int J, int Jp, int N, int G, c
       r1 = fma(hm, v0, fma(-a, v1, fma(-ha, v3, r1)));
       r2 = fma(al, v0, fma(-aa, v2, fma(-hm, v3, r2)));
       r3 = fma(al, v1, fma(hm, v2, fma(-aa, v3, r3)));
-      const float f0 = (float)r0, f1 = (float)r1, f2 = (float)r2, f3 = (float)r3;
+      const float f0 = cvt_d2f(hwcvt, r0), f1 = cvt_d2f(hwcvt, r1), f2 = cvt_d2f(hwcvt, r2), f3 = cvt_d2f(hwcvt, r3);
       if (store_r) {  // the tensor-core inner sweep applies the dense inverse to r itself
         z32[fidx(tsh, R, Jp, gm * 4 + 0, j)] = f0;
         z32[fidx(tsh, R, Jp, gm * 4 + 1, j)] = f1;
@@ -1923,7 +1942,8 @@ void launch_mx_outer(Handle &h, int mode) {
   k_mx_outer<<<grid, block, smem, h.stream>>>(h.J, h.Jp, h.N, h.G, h.type, h.tt.Lco, h.tt.Kap,
                                                              h.tt.Linv32, h.w, h.mu, h.inc, h.tc, h.Psi[0], h.Psi[1],
                                                              h.delta[0], h.delta[1], h.ds, mode,
-                                                             h.precision != OCI_FP32_IR, h.z32, mx_tile_shift(h));
+                                                             h.precision != OCI_FP32_IR, h.z32, mx_tile_shift(h),
+                                                             h.mx_hwcvt);
 }
 
 void launch_mx_finalize(Handle &h, cudaGraphConditionalHandle cond, int use_cond) {
