@@ -654,6 +654,8 @@ static int setup_impl(const oci_problem *p, oci_handle *h) {
   {
     const char *mm = getenv("OCI_MX_MULTI");  // 0: one inner sweep per launch in the graph as well
     h->mx_multi = !(mm && mm[0] == '0');
+    const char *rf = getenv("OCI_RB_FP64");  // "inplace": FP64 red-black half sweeps update Psi[cur] in place
+    h->rb_pingpong = !(rf && rf[0] == 'i');
     const char *cv = getenv("OCI_MX_OUTER_CVT");  // "hw": compiler conversions in the FP64 refinement
     h->mx_hwcvt = (cv && cv[0] == 'h') ? 1 : 0;
   }
@@ -676,6 +678,7 @@ static int setup_impl(const oci_problem *p, oci_handle *h) {
   }
   CK(cudaFuncSetAttribute(k_oci_sweep_ptr(), cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   CK(cudaFuncSetAttribute(k_oci_sweep_rb_ptr(), cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  CK(cudaFuncSetAttribute(k_oci_sweep_rbpp_ptr(), cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   if (h->precision != OCI_FP64) {
     auto to32 = [](const std::vector<double> &a) {
       std::vector<float> f(a.size());
@@ -871,7 +874,8 @@ static int begin_iteration(Handle &h, int fixed, int cap) {
   d.n_refine = 0;
   d.theta = h.mx_theta;
   d.e_blk0 = 0.0;
-  d.inplace = (h.ordering == OCI_ORDER_RED_BLACK && h.precision == OCI_FP64 && h.solver != OCI_SOLVER_DENSE_LU) ||
+  d.inplace = (h.ordering == OCI_ORDER_RED_BLACK && h.precision == OCI_FP64 && h.solver != OCI_SOLVER_DENSE_LU &&
+               !h.rb_pingpong) ||
               h.mx_kind == kMxRB;
   d.cond_ref = h.mx_cond_ref;  // read only by kernels launched from the graph (use_cond)
   CK(cudaMemcpyAsync(h.ds, h.h_ds, sizeof(DevState), cudaMemcpyHostToDevice, h.stream));

@@ -103,6 +103,7 @@ struct Handle {
   int mx_jac_kind = 0, mx_jac_cb = 0, mx_jac_P = 0;  // the Jacobi FP32 inner sweep (kept while red-black)
   int mx_tune_sweeps = 0;              // > 0 while the autotuner times a multi-sweep launch of that many sweeps
   bool mx_multi = true;                // graph runs the persistent tiled FP32 sweep several sweeps per launch
+  bool rb_pingpong = true;             // FP64 red-black: ping-pong buffers (false: in place)
   int mx_hwcvt = 0;                    // 1: FP64 refinement converts with the compiler's F2F (same bits, slower)
   unsigned *gbar = nullptr;            // {count, generation} of the multi-sweep kernel's grid barrier
   int mx_kind = 0;                     // FP32 inner sweep picked by the autotuner: kMxPlain, kMxTma, kMxReg, kMxTiled
@@ -166,6 +167,7 @@ void gmres_free(Handle &h);
 void launch_oci_sweep(Handle &h, cudaGraphConditionalHandle cond, int use_cond);
 const void *k_oci_sweep_ptr();
 const void *k_oci_sweep_rb_ptr();
+const void *k_oci_sweep_rbpp_ptr();
 int sweep_partials(const Handle &h);
 void launch_finalize(Handle &h, const double *partials, int n, cudaGraphConditionalHandle cond,
                      int use_cond);

@@ -65,12 +65,17 @@ __device__ __forceinline__ double block_sum(double v, double *red) {
 // (cell, g, c) handles the angles m in [c N/P, (c+1) N/P) of group g.
 // Block Jacobi (RB = false): reads Psi[cur], writes Psi[cur^1].
 // Red-black (RB = true, half sweep of one colour): thread i handles cell
-// 2i + colour and updates Psi[cur] in place -- its neighbours have the other
-// colour and are not written by this launch; red-black uses one plain pointer so
-// that the compiler keeps each cell's read of its old value before its write.
+// 2i + colour.  PP = false: Psi[cur] is updated in place -- the neighbours have
+// the other colour and are not written by this launch; one plain pointer keeps
+// each cell's read of its old value before its write, which also keeps the
+// loads of one angle behind the stores of the previous one.  PP = true
+// (ping-pong): both colours read their own old values from Psi[cur] and write
+// Psi[cur^1]; the first colour reads its neighbours from Psi[cur], the second
+// from Psi[cur^1] (the first colour's new values), so no launch reads what it
+// writes and the loads carry no ordering against the stores.  Same values.
 // Writes this block's sum of (Psi_new - Psi_old)^2 (per colour for red-black).
 // Shared memory: t [G*N*4][CB], partial y [G*P*4][CB], reduction scratch.
-template <bool RB>
+template <bool RB, bool PP = false>
 __global__ void __launch_bounds__(256) k_oci_sweep_t(
     int J, int Jp, int N, int G, int P, int color, const int32_t *__restrict__ type,
     const double *__restrict__ Linv, const double *__restrict__ Cin, const double *__restrict__ Mp,
@@ -86,12 +91,16 @@ __global__ void __launch_bounds__(256) k_oci_sweep_t(
   const int j = RB ? 2 * (blockIdx.x * CB + cl) + color : blockIdx.x * CB + cl;
   if (ds->done) return;  // uniform across the grid
   const int cur = ds->cur;
+  constexpr bool IP = RB && !PP;  // in place
   double *Pself = cur ? Psi1 : Psi0;
   const double *__restrict__ PinJ = cur ? Psi1 : Psi0;
   double *__restrict__ PoutJ = cur ? Psi0 : Psi1;
-  auto Pin = [&](size_t i) -> double { return RB ? Pself[i] : PinJ[i]; };
+  // upstream neighbours: the second colour of a ping-pong sweep reads the first colour's new values
+  const double *__restrict__ PnbJ = (PP && color == 1) ? (cur ? Psi0 : Psi1) : PinJ;
+  auto Pin = [&](size_t i) -> double { return IP ? Pself[i] : PinJ[i]; };
+  auto Pnb = [&](size_t i) -> double { return IP ? Pself[i] : PnbJ[i]; };
   auto Pput = [&](size_t i, double v) {
-    if (RB) Pself[i] = v;
+    if (IP) Pself[i] = v;
     else PoutJ[i] = v;
   };
   double *t_s = sm;
@@ -111,16 +120,16 @@ __global__ void __launch_bounds__(256) k_oci_sweep_t(
       double uk, uh;
       if (m >= N2) {  // mu > 0: upstream edge is the R corner of cell j-1
         if (j > 0) {
-          uk = Pin(base + 1 * (size_t)Jp - 1);
-          uh = Pin(base + 3 * (size_t)Jp - 1);
+          uk = Pnb(base + 1 * (size_t)Jp - 1);
+          uh = Pnb(base + 3 * (size_t)Jp - 1);
         } else {
           uk = inc[gm * 2 + 0];
           uh = inc[gm * 2 + 1];
         }
       } else {  // mu < 0: upstream edge is the L corner of cell j+1
         if (j < J - 1) {
-          uk = Pin(base + 0 * (size_t)Jp + 1);
-          uh = Pin(base + 2 * (size_t)Jp + 1);
+          uk = Pnb(base + 0 * (size_t)Jp + 1);
+          uh = Pnb(base + 2 * (size_t)Jp + 1);
         } else {
           uk = inc[(G * N + gm) * 2 + 0];
           uh = inc[(G * N + gm) * 2 + 1];
@@ -203,6 +212,7 @@ __global__ void __launch_bounds__(256) k_oci_sweep_t(
 
 const void *k_oci_sweep_ptr() { return (const void *)k_oci_sweep_t<false>; }
 const void *k_oci_sweep_rb_ptr() { return (const void *)k_oci_sweep_t<true>; }
+const void *k_oci_sweep_rbpp_ptr() { return (const void *)k_oci_sweep_t<true, true>; }
 
 size_t sweep_smem(int N, int G, int cb, int P, size_t es) {
   return (size_t)cb * ((size_t)G * N * 4 + (size_t)G * P * 4) * es + 64 * sizeof(double);
@@ -395,10 +405,16 @@ void launch_oci_sweep(Handle &h, cudaGraphConditionalHandle cond, int use_cond) 
     // the odd half reduces the partials of both
     const int half = (h.J + 1) / 2;
     const int grid = (half + c.cells_per_block - 1) / c.cells_per_block;
-    for (int color = 0; color < 2; color++)
-      k_oci_sweep_t<true><<<grid, block, c.smem, h.stream>>>(
-          h.J, h.Jp, h.N, h.G, c.chunks, color, h.type, h.tt.Linv, h.tt.Cin, h.tt.Mp, h.w, h.inc, h.tc, h.Psi[0],
-          h.Psi[1], h.ds, h.partials, h.counter, h.e_hist, cond, use_cond, color == 1, 2 * grid);
+    for (int color = 0; color < 2; color++) {
+      if (h.rb_pingpong)
+        k_oci_sweep_t<true, true><<<grid, block, c.smem, h.stream>>>(
+            h.J, h.Jp, h.N, h.G, c.chunks, color, h.type, h.tt.Linv, h.tt.Cin, h.tt.Mp, h.w, h.inc, h.tc, h.Psi[0],
+            h.Psi[1], h.ds, h.partials, h.counter, h.e_hist, cond, use_cond, color == 1, 2 * grid);
+      else
+        k_oci_sweep_t<true><<<grid, block, c.smem, h.stream>>>(
+            h.J, h.Jp, h.N, h.G, c.chunks, color, h.type, h.tt.Linv, h.tt.Cin, h.tt.Mp, h.w, h.inc, h.tc, h.Psi[0],
+            h.Psi[1], h.ds, h.partials, h.counter, h.e_hist, cond, use_cond, color == 1, 2 * grid);
+    }
     return;
   }
   k_oci_sweep_t<false><<<c.grid, block, c.smem, h.stream>>>(h.J, h.Jp, h.N, h.G, c.chunks, -1, h.type, h.tt.Linv,

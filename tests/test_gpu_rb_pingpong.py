@@ -1,0 +1,67 @@
+"""FP64 red-black sweeps with ping-pong buffers (both colours read Psi[cur] and
+write Psi[cur^1], the second colour taking its neighbours' new values from
+Psi[cur^1]; the default) against the same half sweeps in place on Psi[cur]
+(OCI_RB_FP64=inplace).  Every cell reads the same values and every block sums
+the same partials, so steps, exact-count iterations, norm history, iterates and
+flux agree bit for bit; the sweep counts equal the oracle's red-black sweep; a
+step that does not converge leaves the last iterate readable and commits
+nothing."""
+import numpy as np
+import pytest
+
+from oracle import RB, Oracle
+from paper_2503_00264_gb300 import oci
+from paper_2503_00264_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _layout(monkeypatch, inplace):
+    monkeypatch.setenv("OCI_AUTOTUNE", "0")  # the same launch shape in both runs
+    if inplace:
+        monkeypatch.setenv("OCI_RB_FP64", "inplace")
+    else:
+        monkeypatch.delenv("OCI_RB_FP64", raising=False)
+
+
+def _solve(p, monkeypatch, inplace):
+    _layout(monkeypatch, inplace)
+    with oci.Solver(p) as s:
+        s.set_ordering(oci.ORDER_RED_BLACK)
+        sts = [s.step() for _ in range(2)]
+        eh = s.e_hist().copy()
+        it = s.iterate(5)
+        return ([(t["status"], t["iters"], t["e"], t["rho"]) for t in sts], eh, it, s.psi(), s.phi())
+
+
+@pytest.mark.parametrize("seed,J,N,G", [(141, 1, 4, 1), (142, 2, 4, 1), (143, 33, 8, 1), (144, 257, 8, 2),
+                                        (145, 1000, 16, 1), (146, 4097, 8, 3)])
+def test_ping_pong_equals_in_place_bitwise(seed, J, N, G, monkeypatch):
+    p = W.random_slab(seed, J, N, G).replace(tol=1e-11)
+    a = _solve(p, monkeypatch, inplace=False)
+    b = _solve(p, monkeypatch, inplace=True)
+    assert a[0] == b[0]
+    for x, y in zip(a[1:], b[1:]):
+        assert np.array_equal(x, y)
+    o = Oracle(p)
+    for k in range(2):
+        r = o.step(RB)
+        assert a[0][k][0] == 0 and a[0][k][1] == r["iters"], (k, a[0][k], r["iters"])
+
+
+def test_ping_pong_noconv_keeps_state_and_last_iterate(monkeypatch):
+    p = W.random_slab(147, 301, 8, 1, c_max=0.99).replace(tol=1e-15, max_iter=4)
+    out = {}
+    for inplace in (False, True):
+        _layout(monkeypatch, inplace)
+        with oci.Solver(p) as s:
+            s.set_ordering(oci.ORDER_RED_BLACK)
+            pp0, t0 = s.state()
+            with pytest.raises(oci.OCIError) as ei:
+                s.step()
+            assert ei.value.code == oci.E_NOCONV
+            pp1, t1 = s.state()
+            assert t1 == t0 and np.array_equal(pp0, pp1)
+            out[inplace] = s.psi()
+    assert np.any(out[False])
+    assert np.array_equal(out[False], out[True])
