@@ -175,7 +175,9 @@ typedef struct {
                                 form                                                              */
   double tuned_sweep_us;     /* measured time of one sweep with the chosen shape (0 if not tuned) */
   int32_t sweep_kernel;      /* FP64 form: 0 angles staged in shared memory (k_oci_sweep_t),
-                                1 angles in registers (k_oci_sweep_reg); -1 for the other forms  */
+                                1 angles in registers (k_oci_sweep_reg); red-black order: 2 staged
+                                and 3 register form on ping-pong buffers, 4 staged in place;
+                                -1 for the other forms                                            */
   int32_t reserved;          /* 0                                                                 */
 } oci_info;
 

@@ -448,6 +448,93 @@ static int autotune(Handle &h) {
   return OCI_OK;
 }
 
+// FP64 red-black sweep on ping-pong buffers: the staged and the register form
+// over the legal shapes, each timed (CUDA events) as a few sweeps of two half
+// sweeps, at setup (the state is zeroed afterwards, as after autotune) so that a
+// later switch of the ordering keeps the handle's state.  OCI_RB_SHAPE="s,cb,P"
+// or "r,cb,P" keeps one staged / register shape without timing; OCI_AUTOTUNE=0
+// or OCI_SWEEP_SHAPE leave the Jacobi staged shape in use.
+static int tune_rb64(Handle &h) {
+  if (h.precision != OCI_FP64 || h.solver == OCI_SOLVER_DENSE_LU || !h.rb_pingpong) return OCI_OK;
+  struct RbC {
+    bool reg;
+    int cb, P;
+  };
+  std::vector<RbC> rcs;
+  for (int cb : {32, 64, 128, 256})
+    for (int P : {1, 2, 4, 8}) {
+      const int thr = cb * h.G * P;
+      if (h.N % P || thr < 32 || thr > 256 || sweep_smem(h.N, h.G, cb, P, 8) > 100 * 1024) continue;
+      rcs.push_back({false, cb, P});
+    }
+  for (int np : {2, 4, 8}) {
+    if (h.N % np) continue;
+    const int P = h.N / np;
+    for (int cb : {16, 32, 64}) {
+      const int thr = cb * h.G * P;
+      if (thr <= 256 && thr % 32 == 0 && thr >= 64) rcs.push_back({true, cb, P});
+    }
+  }
+  auto apply = [&](const RbC &c) {
+    h.rb_reg = c.reg;
+    h.rb_cb = c.cb;
+    h.rb_P = c.P;
+  };
+  const char *force = getenv("OCI_RB_SHAPE");
+  if (force) {
+    char k = 0;
+    int fcb = 0, fP = 0;
+    if (sscanf(force, "%c,%d,%d", &k, &fcb, &fP) == 3)
+      for (auto &c : rcs)
+        if (c.reg == (k == 'r') && c.cb == fcb && c.P == fP) {
+          apply(c);
+          return OCI_OK;
+        }
+    return set_error("OCI_RB_SHAPE names no legal red-black shape for this N, G"), OCI_E_INVAL;
+  }
+  const char *at = getenv("OCI_AUTOTUNE");
+  if ((at && at[0] == '0') || getenv("OCI_SWEEP_SHAPE") || rcs.size() < 2) return OCI_OK;
+  DevState &d = *h.h_ds;
+  std::memset(h.h_ds, 0, sizeof(DevState));
+  d.fixed = 1;
+  d.max_iter = 0;  // no e history while timing
+  CK(cudaMemcpyAsync(h.ds, h.h_ds, sizeof(DevState), cudaMemcpyHostToDevice, h.stream));
+  const int ordering = h.ordering, reps = 4;
+  h.ordering = OCI_ORDER_RED_BLACK;
+  float best = 1e30f;
+  RbC bc = rcs[0];
+  for (auto &c : rcs) {
+    apply(c);
+    launch_oci_sweep(h, cudaGraphConditionalHandle{}, 0);
+    float ms = 1e30f;
+    for (int t = 0; t < 2; t++) {  // the faster of two timings
+      CK(cudaEventRecord(h.ev0, h.stream));
+      for (int r = 0; r < reps; r++) launch_oci_sweep(h, cudaGraphConditionalHandle{}, 0);
+      CK(cudaEventRecord(h.ev1, h.stream));
+      CK(cudaEventSynchronize(h.ev1));
+      CK(cudaGetLastError());
+      float m = 0.f;
+      cudaEventElapsedTime(&m, h.ev0, h.ev1);
+      ms = std::min(ms, m);
+    }
+    if (ms < best) {
+      best = ms;
+      bc = c;
+    }
+  }
+  h.ordering = ordering;
+  apply(bc);
+  h.rb_tune_us = 1e3 * best / reps;
+  const size_t nPsi = (size_t)h.G * h.N * 4 * h.Jp;
+  CK(cudaMemsetAsync(h.Psi[0], 0, nPsi * 8, h.stream));
+  CK(cudaMemsetAsync(h.Psi[1], 0, nPsi * 8, h.stream));
+  std::memset(h.h_ds, 0, sizeof(DevState));
+  h.h_ds->done = 1;
+  CK(cudaMemcpyAsync(h.ds, h.h_ds, sizeof(DevState), cudaMemcpyHostToDevice, h.stream));
+  CK(cudaStreamSynchronize(h.stream));
+  return OCI_OK;
+}
+
 // Red-black FP32 inner sweep of the mixed form: kernels (one sweep per pass,
 // kMxRB; two sweeps per pass, kMxRB2) and shapes (tile T cells, P angle
 // chunks), each timed as one launch of four sweeps (as the graph runs them);
@@ -754,6 +841,7 @@ static int setup_impl(const oci_problem *p, oci_handle *h) {
     if (th) h->mx_theta = atof(th);
   }
   if ((rc = autotune(*h))) return rc;
+  if ((rc = tune_rb64(*h))) return rc;
   if ((rc = build_graph(*h, false, &h->g_oci))) return rc;
   CK(cudaStreamSynchronize(s));
   CK(cudaGetLastError());
@@ -1333,6 +1421,18 @@ int oci_get_info(const oci_handle *h, oci_info *info) {
   }
   info->tuned_sweep_us = h->tune_us;
   info->sweep_kernel = h->precision == OCI_FP64 && h->solver != OCI_SOLVER_DENSE_LU ? (h->tune_reg ? 1 : 0) : -1;
+  if (info->sweep_kernel >= 0 && h->ordering == OCI_ORDER_RED_BLACK) {
+    if (!h->rb_pingpong) {
+      info->sweep_kernel = 4;
+    } else if (h->rb_cb > 0) {
+      info->sweep_kernel = h->rb_reg ? 3 : 2;
+      info->cells_per_block = h->rb_cb;
+      info->angle_chunks = h->rb_P;
+      info->tuned_sweep_us = h->rb_tune_us;
+    } else {
+      info->sweep_kernel = 2;
+    }
+  }
   info->reserved = 0;
   return OCI_OK;
 }

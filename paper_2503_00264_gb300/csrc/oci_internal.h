@@ -104,6 +104,9 @@ struct Handle {
   int mx_tune_sweeps = 0;              // > 0 while the autotuner times a multi-sweep launch of that many sweeps
   bool mx_multi = true;                // graph runs the persistent tiled FP32 sweep several sweeps per launch
   bool rb_pingpong = true;             // FP64 red-black: ping-pong buffers (false: in place)
+  int rb_cb = 0, rb_P = 0;             // FP64 red-black shape timed at setup (0: the Jacobi staged shape)
+  bool rb_reg = false;                 // that shape is the register form
+  double rb_tune_us = 0.0;             // its timed sweep (both colours), microseconds
   int mx_hwcvt = 0;                    // 1: FP64 refinement converts with the compiler's F2F (same bits, slower)
   unsigned *gbar = nullptr;            // {count, generation} of the multi-sweep kernel's grid barrier
   int mx_kind = 0;                     // FP32 inner sweep picked by the autotuner: kMxPlain, kMxTma, kMxReg, kMxTiled

@@ -263,27 +263,33 @@ void launch_step_const(Handle &h) {
 // each keeping its NP angles' t = tc + Cin u in registers: no per-angle staging
 // in shared memory, so problems with many unknowns per cell (large N*G) keep
 // more warps resident.  The angle sum y is reduced over the chunks in a fixed
-// order and s = Mp y is split over the chunk threads of each group.  Jacobi
-// ordering; the norm and stop rule are fused into the last block.
-template <int NP>
+// order and s = Mp y is split over the chunk threads of each group.  The norm
+// and stop rule are fused into the last block.  RB = false: Jacobi ordering.
+// RB = true: half sweep of one colour (cell j = 2i + colour) on ping-pong
+// buffers as in k_oci_sweep_t<true, true>; the first colour only writes its
+// block partials, the second reduces both colours' (nparts in all).
+template <int NP, bool RB = false>
 __global__ void __launch_bounds__(256) k_oci_sweep_reg(
     int J, int Jp, int N, int G, const int32_t *__restrict__ type, const double *__restrict__ Linv,
     const double *__restrict__ Cin, const double *__restrict__ Mp, const double *__restrict__ w,
     const double *__restrict__ inc, const double *__restrict__ tc, double *Psi0, double *Psi1, DevState *ds,
-    double *__restrict__ partials, unsigned *counter, double *e_hist, cudaGraphConditionalHandle cond, int use_cond) {
+    double *__restrict__ partials, unsigned *counter, double *e_hist, cudaGraphConditionalHandle cond, int use_cond,
+    int color, int nparts) {
   extern __shared__ double smrd[];
   __shared__ double red[8];
   __shared__ bool s_last;
   const int CB = blockDim.x, P = N / NP, G4 = 4 * G;
   const int cl = threadIdx.x, gy = threadIdx.y;
   const int g = gy / P, ch = gy % P, m0 = ch * NP;
-  const int j = blockIdx.x * CB + cl;
+  const int j = RB ? 2 * (blockIdx.x * CB + cl) + color : blockIdx.x * CB + cl;
   const int tid = threadIdx.y * CB + threadIdx.x;
   const int nthr = CB * blockDim.y;
   if (ds->done) return;  // uniform across the grid
   const int cur = ds->cur;
   const double *__restrict__ Pin = cur ? Psi1 : Psi0;
   double *__restrict__ Pout = cur ? Psi0 : Psi1;
+  // upstream neighbours: the second colour of a red-black sweep reads the first colour's new values
+  const double *__restrict__ Pnb = (RB && color == 1) ? (cur ? Psi0 : Psi1) : Pin;
   double *y_s = smrd;                           // [G*P*4][CB]
   double *yr_s = y_s + (size_t)G * P * 4 * CB;  // [4G][CB]
   double *s_s = yr_s + (size_t)G4 * CB;         // [4G][CB]
@@ -302,15 +308,15 @@ __global__ void __launch_bounds__(256) k_oci_sweep_reg(
       double uk, uh;
       if (m >= N2) {
         if (j > 0) {
-          uk = Pin[base + (size_t)Jp - 1];
-          uh = Pin[base + 3 * (size_t)Jp - 1];
+          uk = Pnb[base + (size_t)Jp - 1];
+          uh = Pnb[base + 3 * (size_t)Jp - 1];
         } else {
           uk = inc[gm * 2 + 0];
           uh = inc[gm * 2 + 1];
         }
       } else if (j < J - 1) {
-        uk = Pin[base + 1];
-        uh = Pin[base + 2 * (size_t)Jp + 1];
+        uk = Pnb[base + 1];
+        uh = Pnb[base + 2 * (size_t)Jp + 1];
       } else {
         uk = inc[(G * N + gm) * 2 + 0];
         uh = inc[(G * N + gm) * 2 + 1];
@@ -366,8 +372,13 @@ __global__ void __launch_bounds__(256) k_oci_sweep_reg(
     }
   }
   const double bs = block_sum(e2, red);
-  if (publish_partial(partials, blockIdx.x, bs, counter, gridDim.x, &s_last)) {
-    const double tot = block_sum_fixed(partials, gridDim.x, red);
+  const int slot = blockIdx.x + (RB ? color * gridDim.x : 0);
+  if (RB && color == 0) {
+    if (tid == 0) partials[slot] = bs;
+    return;
+  }
+  if (publish_partial(partials, slot, bs, counter, gridDim.x, &s_last)) {
+    const double tot = block_sum_fixed(partials, nparts, red);
     if (tid == 0) {
       *counter = 0;
       finish_fp64(ds, e_hist, sqrt(tot), cond, use_cond);
@@ -391,7 +402,7 @@ void launch_oci_sweep(Handle &h, cudaGraphConditionalHandle cond, int use_cond) 
 #define OCI_SWEEP_REG(NP)                                                                                        \
   k_oci_sweep_reg<NP><<<grid, block, smem, h.stream>>>(h.J, h.Jp, h.N, h.G, h.type, h.tt.Linv, h.tt.Cin, h.tt.Mp, \
                                                        h.w, h.inc, h.tc, h.Psi[0], h.Psi[1], h.ds, h.partials,   \
-                                                       h.counter, h.e_hist, cond, use_cond)
+                                                       h.counter, h.e_hist, cond, use_cond, 0, (int)grid.x)
     if (np == 2) OCI_SWEEP_REG(2);
     else if (np == 4) OCI_SWEEP_REG(4);
     else OCI_SWEEP_REG(8);
@@ -400,6 +411,33 @@ void launch_oci_sweep(Handle &h, cudaGraphConditionalHandle cond, int use_cond) 
   }
   SweepCfg c = sweep_config(h);
   dim3 block(c.cells_per_block, h.G * c.chunks);
+  if (h.ordering == OCI_ORDER_RED_BLACK && h.rb_pingpong && h.rb_cb > 0) {
+    // the red-black shape timed at setup (staged or register form, ping-pong)
+    const int cb = h.rb_cb, P = h.rb_P, half = (h.J + 1) / 2, grid = (half + cb - 1) / cb;
+    const dim3 rblock(cb, h.G * P);
+    if (!h.rb_reg) {
+      const size_t smem = sweep_smem(h.N, h.G, cb, P, 8);
+      for (int color = 0; color < 2; color++)
+        k_oci_sweep_t<true, true><<<grid, rblock, smem, h.stream>>>(
+            h.J, h.Jp, h.N, h.G, P, color, h.type, h.tt.Linv, h.tt.Cin, h.tt.Mp, h.w, h.inc, h.tc, h.Psi[0],
+            h.Psi[1], h.ds, h.partials, h.counter, h.e_hist, cond, use_cond, color == 1, 2 * grid);
+      return;
+    }
+    const int np = h.N / P;
+    const size_t smem = sweep_reg_smem(h.G, cb, P);
+    for (int color = 0; color < 2; color++) {
+#define OCI_SWEEP_REG_RB(NP)                                                                                     \
+  k_oci_sweep_reg<NP, true><<<grid, rblock, smem, h.stream>>>(h.J, h.Jp, h.N, h.G, h.type, h.tt.Linv, h.tt.Cin,   \
+                                                              h.tt.Mp, h.w, h.inc, h.tc, h.Psi[0], h.Psi[1], h.ds, \
+                                                              h.partials, h.counter, h.e_hist, cond, use_cond,     \
+                                                              color, 2 * grid)
+      if (np == 2) OCI_SWEEP_REG_RB(2);
+      else if (np == 4) OCI_SWEEP_REG_RB(4);
+      else OCI_SWEEP_REG_RB(8);
+#undef OCI_SWEEP_REG_RB
+    }
+    return;
+  }
   if (h.ordering == OCI_ORDER_RED_BLACK) {
     // two half sweeps, even cells then odd cells, each over ceil(J/2) threads;
     // the odd half reduces the partials of both

@@ -65,3 +65,42 @@ def test_ping_pong_noconv_keeps_state_and_last_iterate(monkeypatch):
             out[inplace] = s.psi()
     assert np.any(out[False])
     assert np.array_equal(out[False], out[True])
+
+
+def _legal(shape, N, G):
+    kind, cb, P = shape.split(",")
+    cb, P = int(cb), int(P)
+    thr = cb * G * P
+    if kind == "s":
+        return N % P == 0 and 32 <= thr <= 256 and cb * (G * N * 4 + G * P * 4) * 8 + 512 <= 100 * 1024
+    return N % P == 0 and N // P in (2, 4, 8) and cb in (16, 32, 64) and thr <= 256 and thr % 32 == 0 and thr >= 64
+
+
+@pytest.mark.parametrize("shape", ["s,32,1", "s,64,2", "s,128,1", "r,16,4", "r,32,2", "r,64,1", "r,16,2"])
+@pytest.mark.parametrize("seed,J,N,G", [(151, 1, 4, 1), (152, 77, 8, 1), (153, 300, 8, 2), (154, 1025, 16, 1)])
+def test_forced_red_black_shapes_match_oracle(shape, seed, J, N, G, monkeypatch):
+    """Every red-black form the setup tuner can pick (staged or register, ping-pong),
+    forced with OCI_RB_SHAPE: the oracle's red-black sweep counts, flux within 1e-12."""
+    if not _legal(shape, N, G):
+        pytest.skip("shape not legal for this N, G")
+    monkeypatch.setenv("OCI_RB_SHAPE", shape)
+    p = W.random_slab(seed, J, N, G).replace(tol=1e-11)
+    o = Oracle(p)
+    with oci.Solver(p) as s:
+        s.set_ordering(oci.ORDER_RED_BLACK)
+        info = s.info()
+        assert info["sweep_kernel"] == (3 if shape[0] == "r" else 2)
+        assert (info["cells_per_block"], info["angle_chunks"]) == tuple(int(x) for x in shape.split(",")[1:])
+        for k in range(2):
+            r = o.step(RB)
+            st = s.step()
+            assert st["status"] == 0 and st["iters"] == r["iters"], (k, st["iters"], r["iters"])
+            assert float(np.abs(s.phi() - r["phi"]).max() / np.abs(r["phi"]).max()) < 1e-12
+            assert float(np.abs(s.psi() - r["Psi"]).max() / np.abs(r["Psi"]).max()) < 1e-11
+
+
+def test_illegal_red_black_shape_rejected(monkeypatch):
+    monkeypatch.setenv("OCI_RB_SHAPE", "r,16,3")
+    with pytest.raises(oci.OCIError) as ei:
+        oci.Solver(W.random_slab(155, 40, 8, 1))
+    assert ei.value.code == oci.E_INVAL
