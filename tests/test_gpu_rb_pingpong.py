@@ -104,3 +104,19 @@ def test_illegal_red_black_shape_rejected(monkeypatch):
     with pytest.raises(oci.OCIError) as ei:
         oci.Solver(W.random_slab(155, 40, 8, 1))
     assert ei.value.code == oci.E_INVAL
+
+
+def test_switching_ordering_between_steps_keeps_the_state():
+    """Jacobi, red-black, red-black, Jacobi steps on one handle: each step starts
+    from the previous step's state (the red-black shape was timed at setup, not at
+    the switch) and matches the oracle's sequence of the same orderings."""
+    from oracle import OCI
+    p = W.random_slab(156, 500, 8, 2).replace(tol=1e-11)
+    o = Oracle(p)
+    with oci.Solver(p) as s:
+        for order in (OCI, RB, RB, OCI):
+            s.set_ordering(oci.ORDER_RED_BLACK if order == RB else oci.ORDER_JACOBI)
+            r = o.step(order)
+            st = s.step()
+            assert st["status"] == 0 and st["iters"] == r["iters"], (order, st["iters"], r["iters"])
+            assert float(np.abs(s.phi() - r["phi"]).max() / np.abs(r["phi"]).max()) < 1e-12
