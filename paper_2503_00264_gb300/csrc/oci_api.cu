@@ -450,10 +450,11 @@ static int autotune(Handle &h) {
 
 // FP64 red-black sweep on ping-pong buffers: the staged and the register form
 // over the legal shapes, each timed (CUDA events) as a few sweeps of two half
-// sweeps, at setup (the state is zeroed afterwards, as after autotune) so that a
-// later switch of the ordering keeps the handle's state.  OCI_RB_SHAPE="s,cb,P"
-// or "r,cb,P" keeps one staged / register shape without timing; OCI_AUTOTUNE=0
-// or OCI_SWEEP_SHAPE leave the Jacobi staged shape in use.
+// sweeps, on the first switch to red-black order.  The timing keeps the state:
+// with the device state marked in place, every timed sweep reads Psi[cur] and
+// writes only Psi[cur^1], and the state record is restored afterwards.
+// OCI_RB_SHAPE="s,cb,P" or "r,cb,P" keeps one staged / register shape without
+// timing; OCI_AUTOTUNE=0 or OCI_SWEEP_SHAPE leave the Jacobi staged shape in use.
 static int tune_rb64(Handle &h) {
   if (h.precision != OCI_FP64 || h.solver == OCI_SOLVER_DENSE_LU || !h.rb_pingpong) return OCI_OK;
   struct RbC {
@@ -494,10 +495,12 @@ static int tune_rb64(Handle &h) {
   }
   const char *at = getenv("OCI_AUTOTUNE");
   if ((at && at[0] == '0') || getenv("OCI_SWEEP_SHAPE") || rcs.size() < 2) return OCI_OK;
+  const DevState saved = *h.h_ds;
   DevState &d = *h.h_ds;
-  std::memset(h.h_ds, 0, sizeof(DevState));
+  d.done = 0;
   d.fixed = 1;
   d.max_iter = 0;  // no e history while timing
+  d.inplace = 1;   // no flip of cur: Psi[cur] is only read
   CK(cudaMemcpyAsync(h.ds, h.h_ds, sizeof(DevState), cudaMemcpyHostToDevice, h.stream));
   const int ordering = h.ordering, reps = 4;
   h.ordering = OCI_ORDER_RED_BLACK;
@@ -525,11 +528,7 @@ static int tune_rb64(Handle &h) {
   h.ordering = ordering;
   apply(bc);
   h.rb_tune_us = 1e3 * best / reps;
-  const size_t nPsi = (size_t)h.G * h.N * 4 * h.Jp;
-  CK(cudaMemsetAsync(h.Psi[0], 0, nPsi * 8, h.stream));
-  CK(cudaMemsetAsync(h.Psi[1], 0, nPsi * 8, h.stream));
-  std::memset(h.h_ds, 0, sizeof(DevState));
-  h.h_ds->done = 1;
+  *h.h_ds = saved;
   CK(cudaMemcpyAsync(h.ds, h.h_ds, sizeof(DevState), cudaMemcpyHostToDevice, h.stream));
   CK(cudaStreamSynchronize(h.stream));
   return OCI_OK;
@@ -841,7 +840,6 @@ static int setup_impl(const oci_problem *p, oci_handle *h) {
     if (th) h->mx_theta = atof(th);
   }
   if ((rc = autotune(*h))) return rc;
-  if ((rc = tune_rb64(*h))) return rc;
   if ((rc = build_graph(*h, false, &h->g_oci))) return rc;
   CK(cudaStreamSynchronize(s));
   CK(cudaGetLastError());
@@ -1314,6 +1312,11 @@ int oci_set_ordering(oci_handle *h, int32_t ordering) {
   if (ordering == h->ordering) return OCI_OK;
   if (ordering == OCI_ORDER_RED_BLACK && h->accel != OCI_ACCEL_NONE)
     return set_error("red-black ordering and GMRES acceleration do not combine"), OCI_E_INVAL;
+  if (ordering == OCI_ORDER_RED_BLACK && !h->rb_tuned) {  // FP64: time the red-black shapes once
+    int rc = tune_rb64(*h);
+    if (rc) return rc;
+    h->rb_tuned = true;
+  }
   h->ordering = ordering;
   if (h->precision == OCI_FP32_IR) {
     int rc = ordering == OCI_ORDER_RED_BLACK ? tune_rb(*h) : OCI_OK;

@@ -107,6 +107,7 @@ struct Handle {
   int rb_cb = 0, rb_P = 0;             // FP64 red-black shape timed at setup (0: the Jacobi staged shape)
   bool rb_reg = false;                 // that shape is the register form
   double rb_tune_us = 0.0;             // its timed sweep (both colours), microseconds
+  bool rb_tuned = false;               // red-black shapes timed (on the first switch to red-black)
   int mx_hwcvt = 0;                    // 1: FP64 refinement converts with the compiler's F2F (same bits, slower)
   unsigned *gbar = nullptr;            // {count, generation} of the multi-sweep kernel's grid barrier
   int mx_kind = 0;                     // FP32 inner sweep picked by the autotuner: kMxPlain, kMxTma, kMxReg, kMxTiled

@@ -101,15 +101,19 @@ def test_forced_red_black_shapes_match_oracle(shape, seed, J, N, G, monkeypatch)
 
 def test_illegal_red_black_shape_rejected(monkeypatch):
     monkeypatch.setenv("OCI_RB_SHAPE", "r,16,3")
-    with pytest.raises(oci.OCIError) as ei:
-        oci.Solver(W.random_slab(155, 40, 8, 1))
-    assert ei.value.code == oci.E_INVAL
+    with oci.Solver(W.random_slab(155, 40, 8, 1)) as s:
+        with pytest.raises(oci.OCIError) as ei:
+            s.set_ordering(oci.ORDER_RED_BLACK)
+        assert ei.value.code == oci.E_INVAL
+        assert s.info()["sweep_kernel"] in (0, 1)  # still Jacobi
+        assert s.step()["status"] == 0
 
 
 def test_switching_ordering_between_steps_keeps_the_state():
     """Jacobi, red-black, red-black, Jacobi steps on one handle: each step starts
-    from the previous step's state (the red-black shape was timed at setup, not at
-    the switch) and matches the oracle's sequence of the same orderings."""
+    from the previous step's state (the red-black shapes are timed at the first
+    switch without touching it) and matches the oracle's sequence of the same
+    orderings."""
     from oracle import OCI
     p = W.random_slab(156, 500, 8, 2).replace(tol=1e-11)
     o = Oracle(p)
@@ -120,3 +124,21 @@ def test_switching_ordering_between_steps_keeps_the_state():
             st = s.step()
             assert st["status"] == 0 and st["iters"] == r["iters"], (order, st["iters"], r["iters"])
             assert float(np.abs(s.phi() - r["phi"]).max() / np.abs(r["phi"]).max()) < 1e-12
+
+
+def test_first_switch_to_red_black_keeps_the_last_iterate():
+    """The red-black shapes are timed on the first switch: an unconverged step's
+    last iterate, the carried state and the time are untouched by it, and the
+    next (red-black) step starts from that iterate as the oracle's does."""
+    p = W.random_slab(157, 3000, 8, 1, c_max=0.99).replace(tol=1e-14, max_iter=6)
+    with oci.Solver(p) as s:
+        with pytest.raises(oci.OCIError) as ei:
+            s.step()
+        assert ei.value.code == oci.E_NOCONV
+        psi0 = s.psi()
+        pp0, t0 = s.state()
+        s.set_ordering(oci.ORDER_RED_BLACK)
+        assert s.info()["tuned_sweep_us"] > 0
+        assert np.array_equal(s.psi(), psi0)
+        pp1, t1 = s.state()
+        assert t1 == t0 and np.array_equal(pp0, pp1)
