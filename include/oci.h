@@ -237,8 +237,12 @@ int oci_set_boundary(oci_handle *h, const double *inc_left, const double *inc_ri
 int oci_get_e_hist(const oci_handle *h, double *e_hist, int32_t *n);
 
 /* Cell ordering of the following OCI sweeps (OCI_ORDER_*; default Jacobi).
- * Red-black needs the FP64 structured solver (else OCI_E_INVAL).  The norm and
- * the stop rule are those of Sec. 2.1 over one full (red + black) sweep. */
+ * Red-black needs the FP64 structured solver or the OCI_FP32_IR form and no
+ * GMRES acceleration (else OCI_E_INVAL).  The norm and the stop rule are those
+ * of Sec. 2.1 over one full (red + black) sweep.  The first switch to red-black
+ * times the red-black launch shapes on the handle's stream (the state -- last
+ * iterate, psi_{k-1/2}, t -- is left as it was); the switch rebuilds the step's
+ * CUDA graph.  Errors leave the ordering unchanged. */
 int oci_set_ordering(oci_handle *h, int32_t ordering);
 
 /* March of the following SI sweeps (OCI_SI_*; default sequential). */

@@ -1317,10 +1317,14 @@ int oci_set_ordering(oci_handle *h, int32_t ordering) {
     if (rc) return rc;
     h->rb_tuned = true;
   }
+  const int previous = h->ordering;
   h->ordering = ordering;
   if (h->precision == OCI_FP32_IR) {
     int rc = ordering == OCI_ORDER_RED_BLACK ? tune_rb(*h) : OCI_OK;
-    if (rc) return rc;
+    if (rc) {
+      h->ordering = previous;
+      return rc;
+    }
     if (ordering == OCI_ORDER_JACOBI) {  // back to the Jacobi inner sweep tuned at setup
       h->mx_kind = h->mx_jac_kind;
       h->mx_cb = h->mx_jac_cb;
