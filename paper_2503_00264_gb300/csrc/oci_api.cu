@@ -640,7 +640,8 @@ static void free_handle(Handle *h) {
                   h->tt.Cin, h->tt.Mp,  h->tt.Kap,    h->tt.dx,     h->tt.sig,       h->si_z,      h->si_uin,
                   h->LU,     h->piv,    h->partials,  h->bal_partials, h->bal,       h->e_hist,    h->ds,
                   h->stage,  h->delta[0], h->delta[1], h->z32, h->w32, h->tt.Lco, h->tt.Linv32, h->tt.Cin32,
-                  h->tt.Mp32, h->tc_img, h->si_maps, h->si_segin, h->counter, h->psi_user, h->gbar, h->mu32};
+                  h->tt.Mp32, h->tc_img, h->si_maps, h->si_segin, h->counter, h->psi_user, h->gbar, h->mu32,
+                  h->yc,     h->tt.Win};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (h->h_ds) cudaFreeHost(h->h_ds);
@@ -686,6 +687,7 @@ static int setup_impl(const oci_problem *p, oci_handle *h) {
   CK(cudaMalloc(&h->Psi[0], nPsi * 8));
   CK(cudaMalloc(&h->Psi[1], nPsi * 8));
   CK(cudaMalloc(&h->tc, nPsi * 8));
+  CK(cudaMalloc(&h->yc, G * 4 * Jp * 8));
   CK(cudaMalloc(&h->psi_prev, G * N * 2 * Jp * 8));
   CK(cudaMalloc(&h->phi, G * 4 * Jp * 8));
   CK(cudaMalloc(&h->stage, nPsi * 8));
@@ -696,6 +698,7 @@ static int setup_impl(const oci_problem *p, oci_handle *h) {
   CK(cudaMemsetAsync(h->Psi[0], 0, nPsi * 8, s));
   CK(cudaMemsetAsync(h->Psi[1], 0, nPsi * 8, s));
   CK(cudaMemsetAsync(h->tc, 0, nPsi * 8, s));
+  CK(cudaMemsetAsync(h->yc, 0, G * 4 * Jp * 8, s));
   CK(cudaMemsetAsync(h->psi_prev, 0, G * N * 2 * Jp * 8, s));
   CK(cudaMemsetAsync(h->phi, 0, G * 4 * Jp * 8, s));
   std::vector<int32_t> typ(Jp, 0);
@@ -706,6 +709,13 @@ static int setup_impl(const oci_problem *p, oci_handle *h) {
   if ((rc = dev_upload(&h->v, h->h_v.data(), G, s))) return rc;
   if ((rc = dev_upload(&h->tt.Linv, Linv.data(), Linv.size(), s))) return rc;
   if ((rc = dev_upload(&h->tt.Cin, Cin.data(), Cin.size(), s))) return rc;
+  {
+    std::vector<double> Win(Cin.size());
+    for (size_t o = 0; o < Cin.size() / 8; o++)
+      for (int k = 0; k < 8; k++) Win[o * 8 + k] = h->h_w[o % N] * Cin[o * 8 + k];
+    if ((rc = dev_upload(&h->tt.Win, Win.data(), Win.size(), s))) return rc;
+    CK(cudaStreamSynchronize(s));  // Win is a local vector
+  }
   if ((rc = dev_upload(&h->tt.Mp, Mp.data(), Mp.size(), s))) return rc;
   if ((rc = dev_upload(&h->tt.Kap, Kap.data(), Kap.size(), s))) return rc;
   if ((rc = dev_upload(&h->tt.dx, tdx.data(), tdx.size(), s))) return rc;

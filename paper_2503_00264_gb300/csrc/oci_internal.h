@@ -52,6 +52,7 @@ struct TypeTables {
   int n_types = 0;
   double *Linv = nullptr;   // [T][G][N][16]  inverse of the 4x4 L_{c,g,m} (Eq. Aj), row-major
   double *Cin = nullptr;    // [T][G][N][8]   |mu| * the two columns of Linv that the inflow feeds
+  double *Win = nullptr;    // [T][G][N][8]   w_m * Cin (the inflow's part of y)
   double *Mp = nullptr;     // [T][4G][4G]    s = Mp y: within-cell scattering source from y
   double *Kap = nullptr;    // [T][G][G]      dx/4 * Sigma_s,gp->g  (index [gp][g])
   double *dx = nullptr;     // [T]
@@ -82,6 +83,7 @@ struct Handle {
   // device state
   double *Psi[2] = {nullptr, nullptr};
   double *tc = nullptr;          // per-step constant Linv * c (structured) or c (dense)
+  double *yc = nullptr;  // [G][4][Jp] yc = sum_m w_m tc (per step; register sweep)
   double *psi_prev = nullptr;
   double *phi = nullptr;
   double *phi_si[2] = {nullptr, nullptr};

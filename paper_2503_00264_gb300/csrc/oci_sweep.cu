@@ -13,6 +13,10 @@
 // which is A_j^{-1} b_j up to rounding.  b = c + (lagged inflow) with the
 // per-step constant c of Eq. rhs_sg, so t = tc + Cin u with tc = L^{-1} c
 // computed once per step (k_step_const) and u the two upstream edge values.
+// The register form regroups the same algebra: y = yc + sum_m (w_m Cin) u_m
+// with yc = sum_m w_m tc per step (k_step_yc), and Psi_{g,m} = tc_{g,m} +
+// L_{g,m}^{-1} (s_g + |mu| u placed in the inflow rows), which saves two FP64
+// operations per cell, group and angle.
 #include <math.h>
 
 #include "oci_device.cuh"
@@ -44,6 +48,20 @@ __global__ void k_step_const(int J, int Jp, int N, int G, const int32_t *__restr
 #pragma unroll
   for (int p = 0; p < 4; p++)
     tc[(size_t)(gm * 4 + p) * Jp + j] = L[p * 4 + 0] * c0 + L[p * 4 + 1] * c1 + L[p * 4 + 2] * q[2] + L[p * 4 + 3] * q[3];
+}
+
+// yc_{g,p} = sum_m w_m tc_{g,m,p} (ascending m), for the register sweep.
+__global__ void k_step_yc(int J, int Jp, int N, const double *__restrict__ w, const double *__restrict__ tc,
+                          double *__restrict__ yc) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int g = blockIdx.y;
+  if (j >= J) return;
+#pragma unroll
+  for (int p = 0; p < 4; p++) {
+    double a = 0.0;
+    for (int m = 0; m < N; m++) a = fma(w[m], tc[(size_t)((g * N + m) * 4 + p) * Jp + j], a);
+    yc[(size_t)(g * 4 + p) * Jp + j] = a;
+  }
 }
 
 // Deterministic block sum of one double; result valid in thread 0.
@@ -254,16 +272,18 @@ void launch_step_const(Handle &h) {
   dim3 grid((h.J + 255) / 256, h.G * h.N);
   k_step_const<<<grid, 256, 0, h.stream>>>(h.J, h.Jp, h.N, h.G, h.type, h.tt.dx, h.v, h.dt, h.Q, h.psi_prev,
                                            h.tt.Linv, h.tc);
+  k_step_yc<<<dim3((h.J + 255) / 256, h.G), 256, 0, h.stream>>>(h.J, h.Jp, h.N, h.w, h.tc, h.yc);
 }
 
 // One sweep including its norm reduction and stop rule (fused into the last block).
 
 // ---------------------------------------------------------------- register form (FP64)
 // The same FP64 sweep with the N angles of a cell split over P = N/NP threads,
-// each keeping its NP angles' t = tc + Cin u in registers: no per-angle staging
-// in shared memory, so problems with many unknowns per cell (large N*G) keep
-// more warps resident.  The angle sum y is reduced over the chunks in a fixed
-// order and s = Mp y is split over the chunk threads of each group.  The norm
+// each keeping its NP angles' inflow u in registers: no per-angle staging in
+// shared memory, so problems with many unknowns per cell (large N*G) keep more
+// warps resident.  y = yc + sum_m Win_m u_m is reduced over the chunks in a
+// fixed order, s = Mp y is split over the chunk threads of each group, and
+// Psi = tc + Linv (s + |mu| u in the inflow rows).  The norm
 // and stop rule are fused into the last block.  RB = false: Jacobi ordering.
 // RB = true: half sweep of one colour (cell j = 2i + colour) on ping-pong
 // buffers as in k_oci_sweep_t<true, true>; the first colour only writes its
@@ -274,7 +294,8 @@ __global__ void __launch_bounds__(256) k_oci_sweep_reg(
     const double *__restrict__ Cin, const double *__restrict__ Mp, const double *__restrict__ w,
     const double *__restrict__ inc, const double *__restrict__ tc, double *Psi0, double *Psi1, DevState *ds,
     double *__restrict__ partials, unsigned *counter, double *e_hist, cudaGraphConditionalHandle cond, int use_cond,
-    int color, int nparts) {
+    int color, int nparts, const double *__restrict__ Win, const double *__restrict__ yc,
+    const double *__restrict__ mu) {
   extern __shared__ double smrd[];
   __shared__ double red[8];
   __shared__ bool s_last;
@@ -297,7 +318,7 @@ __global__ void __launch_bounds__(256) k_oci_sweep_reg(
   const int tau = active ? type[j] : 0;
   const int N2 = N / 2;
   const size_t tb = (size_t)tau * G * N;
-  double t[NP][4];
+  double u[NP][2];
   double y0 = 0.0, y1 = 0.0, y2 = 0.0, y3 = 0.0;
   if (active) {
 #pragma unroll
@@ -321,14 +342,13 @@ __global__ void __launch_bounds__(256) k_oci_sweep_reg(
         uk = inc[(G * N + gm) * 2 + 0];
         uh = inc[(G * N + gm) * 2 + 1];
       }
-      const double *C = Cin + (tb + gm) * 8;
-#pragma unroll
-      for (int p = 0; p < 4; p++) t[i][p] = fma(C[2 * p + 1], uh, fma(C[2 * p], uk, tc[base + (size_t)p * Jp]));
-      const double wm = w[m];
-      y0 = fma(wm, t[i][0], y0);
-      y1 = fma(wm, t[i][1], y1);
-      y2 = fma(wm, t[i][2], y2);
-      y3 = fma(wm, t[i][3], y3);
+      u[i][0] = uk;
+      u[i][1] = uh;
+      const double *W = Win + (tb + gm) * 8;
+      y0 = fma(W[1], uh, fma(W[0], uk, y0));
+      y1 = fma(W[3], uh, fma(W[2], uk, y1));
+      y2 = fma(W[5], uh, fma(W[4], uk, y2));
+      y3 = fma(W[7], uh, fma(W[6], uk, y3));
     }
   }
   {
@@ -339,9 +359,9 @@ __global__ void __launch_bounds__(256) k_oci_sweep_reg(
     ys[3 * CB] = y3;
   }
   __syncthreads();
-  for (int q = ch; q < 4; q += P) {  // y_{g,q}: fixed-order sum over the group's chunks
-    double v = y_s[(size_t)((g * P) * 4 + q) * CB + cl];
-    for (int k = 1; k < P; k++) v += y_s[(size_t)((g * P + k) * 4 + q) * CB + cl];
+  for (int q = ch; q < 4; q += P) {  // y_{g,q} = yc + fixed-order sum over the group's chunks
+    double v = active ? yc[(size_t)(g * 4 + q) * Jp + j] : 0.0;
+    for (int k = 0; k < P; k++) v += y_s[(size_t)((g * P + k) * 4 + q) * CB + cl];
     yr_s[(size_t)(g * 4 + q) * CB + cl] = v;
   }
   __syncthreads();
@@ -359,12 +379,18 @@ __global__ void __launch_bounds__(256) k_oci_sweep_reg(
     const double s2 = s_s[(size_t)(g * 4 + 2) * CB + cl], s3 = s_s[(size_t)(g * 4 + 3) * CB + cl];
 #pragma unroll
     for (int i = 0; i < NP; i++) {
-      const int gm = g * N + m0 + i;
+      const int m = m0 + i;
+      const int gm = g * N + m;
       const size_t base = (size_t)gm * 4 * Jp + j;
       const double *L = Linv + (tb + gm) * 16;
+      // v = s + |mu| u in the rows the inflow feeds (0, 2 for mu > 0; 1, 3 for mu < 0)
+      const double am = fabs(mu[m]);
+      const bool pos = m >= N2;
+      const double v0 = pos ? fma(am, u[i][0], s0) : s0, v1 = pos ? s1 : fma(am, u[i][0], s1);
+      const double v2 = pos ? fma(am, u[i][1], s2) : s2, v3 = pos ? s3 : fma(am, u[i][1], s3);
 #pragma unroll
       for (int p = 0; p < 4; p++) {
-        const double o = fma(L[p * 4 + 3], s3, fma(L[p * 4 + 2], s2, fma(L[p * 4 + 1], s1, fma(L[p * 4 + 0], s0, t[i][p]))));
+        const double o = fma(L[p * 4 + 3], v3, fma(L[p * 4 + 2], v2, fma(L[p * 4 + 1], v1, fma(L[p * 4 + 0], v0, tc[base + (size_t)p * Jp]))));
         const double d = o - Pin[base + (size_t)p * Jp];
         e2 = fma(d, d, e2);
         Pout[base + (size_t)p * Jp] = o;
@@ -402,7 +428,8 @@ void launch_oci_sweep(Handle &h, cudaGraphConditionalHandle cond, int use_cond) 
 #define OCI_SWEEP_REG(NP)                                                                                        \
   k_oci_sweep_reg<NP><<<grid, block, smem, h.stream>>>(h.J, h.Jp, h.N, h.G, h.type, h.tt.Linv, h.tt.Cin, h.tt.Mp, \
                                                        h.w, h.inc, h.tc, h.Psi[0], h.Psi[1], h.ds, h.partials,   \
-                                                       h.counter, h.e_hist, cond, use_cond, 0, (int)grid.x)
+                                                       h.counter, h.e_hist, cond, use_cond, 0, (int)grid.x,      \
+                                                       h.tt.Win, h.yc, h.mu)
     if (np == 2) OCI_SWEEP_REG(2);
     else if (np == 4) OCI_SWEEP_REG(4);
     else OCI_SWEEP_REG(8);
@@ -430,7 +457,7 @@ void launch_oci_sweep(Handle &h, cudaGraphConditionalHandle cond, int use_cond) 
   k_oci_sweep_reg<NP, true><<<grid, rblock, smem, h.stream>>>(h.J, h.Jp, h.N, h.G, h.type, h.tt.Linv, h.tt.Cin,   \
                                                               h.tt.Mp, h.w, h.inc, h.tc, h.Psi[0], h.Psi[1], h.ds, \
                                                               h.partials, h.counter, h.e_hist, cond, use_cond,     \
-                                                              color, 2 * grid)
+                                                              color, 2 * grid, h.tt.Win, h.yc, h.mu)
       if (np == 2) OCI_SWEEP_REG_RB(2);
       else if (np == 4) OCI_SWEEP_REG_RB(4);
       else OCI_SWEEP_REG_RB(8);

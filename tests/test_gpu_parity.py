@@ -270,9 +270,10 @@ def test_scan_si_full_size_matches_sequential():
                                               (94, 300, 16, 4, "16,2"), (95, 129, 16, 1, "64,2"),
                                               (96, 95, 32, 2, "32,4")])
 def test_fp64_register_sweep_matches_oracle(seed, J, N, G, shape, monkeypatch):
-    """FP64 sweep with the angles of a cell split over threads and t kept in
-    registers (the autotuner's candidate for large N*G): same sweep counts as
-    the oracle, flux within 1e-12."""
+    """FP64 sweep with the angles of a cell split over threads and their inflow
+    kept in registers (y = yc + sum_m w_m Cin_m u_m, Psi = tc + Linv (s + |mu| u);
+    the autotuner's candidate for large N*G): same sweep counts as the oracle,
+    flux within 1e-12."""
     monkeypatch.setenv("OCI_SWEEP_REG", "1")
     if shape:
         monkeypatch.setenv("OCI_SWEEP_SHAPE", shape)
