@@ -31,17 +31,14 @@ from paper_2503_00264_gb300 import workloads as W  # noqa: E402
 METRIC = "OCI cell-unknown updates/s"
 UNIT = "updates/s"
 SAMPLE_J = 3072
-# dram__bytes_read.sum + dram__bytes_write.sum of one k_oci_sweep launch on this workload
-# (2^18 cells, S16, G = 1, tuned shape 64 cells x 2 angle chunks), from the ncu --set full
-# capture summarised in profiles/.
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of one FP64 sweep launch on the 2^18-cell S16
 # slab, per (kernel: 0 staged / 1 register form, cells per block, angle chunks) the autotuner can pick
 SWEEP_DRAM_BYTES_NCU = {
     (0, 64, 2): 271.829760e6 + 100.329984e6,
-    (1, 16, 4): 269.720832e6 + 103.894016e6, (1, 16, 8): 269.715712e6 + 105.035520e6,
-    (1, 32, 2): 269.782528e6 + 102.594304e6, (1, 32, 4): 269.660416e6 + 103.412224e6,
-    (1, 32, 8): 269.596160e6 + 104.473856e6, (1, 64, 2): 269.743616e6 + 102.103040e6,
-    (1, 64, 4): 269.611264e6 + 103.353856e6,
+    (1, 16, 4): 278.830592e6 + 106.181632e6, (1, 16, 8): 278.059520e6 + 106.986240e6,
+    (1, 32, 2): 286.433024e6 + 105.320704e6, (1, 32, 4): 278.543104e6 + 105.922560e6,
+    (1, 32, 8): 277.979392e6 + 106.466304e6, (1, 64, 2): 286.132736e6 + 105.421056e6,
+    (1, 64, 4): 278.674944e6 + 105.612800e6,
 }
 # FP64 issue rate of one SM: 2 DFMA per clock (GB300: 1.25 TFLOP/s FP64 = 152 SMs x 2 x 2 flops
 # x 2.07 GHz); the ALU roofline's peak = SMs x this x 2 flops x the maximum SM clock.
