@@ -223,7 +223,7 @@ def run_ours(args):
         st = s.step()
         stats.append(st)
         sweeps += st["iters"]
-        launches += 1 + st["iters"] + 2  # step constant, fused sweeps, carry + balance
+        launches += 2 + st["iters"] + 2  # step constant + y_c, fused sweeps, carry + balance
     e1.record(stream)
     barrier()
     clocks = clk.stop()
