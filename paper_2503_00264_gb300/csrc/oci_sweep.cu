@@ -283,7 +283,9 @@ void launch_step_const(Handle &h) {
 // shared memory, so problems with many unknowns per cell (large N*G) keep more
 // warps resident.  y = yc + sum_m Win_m u_m is reduced over the chunks in a
 // fixed order, s = Mp y is split over the chunk threads of each group, and
-// Psi = tc + Linv (s + |mu| u in the inflow rows).  The norm
+// Psi = tc + Linv (s + |mu| u in the inflow rows).  Cin and w are not read here
+// (Win = w Cin and yc carry them); they stay in the argument list the staged
+// form shares.  The norm
 // and stop rule are fused into the last block.  RB = false: Jacobi ordering.
 // RB = true: half sweep of one colour (cell j = 2i + colour) on ping-pong
 // buffers as in k_oci_sweep_t<true, true>; the first colour only writes its
