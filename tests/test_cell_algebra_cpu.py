@@ -1,0 +1,93 @@
+"""CPU check of the algebra the FP64 sweep kernels use for the exact cell solve,
+restated here in numpy from the balance equations, against the oracle's own
+dense cell matrix A_j and right-hand side b_j (Eqs. Aj, scatter, fullOCIlhs,
+rhs_sg): for random cells and lagged iterates both forms give A_j^{-1} b_j to
+rounding.
+
+  staged form:     t_m = tc_m + C_in,m u_m,  y = sum_m w_m t_m,  s = M' y,
+                   Psi_m = t_m + L_m^{-1} s
+  register form:   y = y_c + sum_m (w_m C_in,m) u_m,  y_c = sum_m w_m tc_m,
+                   s = M' y,  Psi_m = tc_m + L_m^{-1} (s + |mu_m| u_m in the
+                   inflow rows)
+
+with tc_m = L_m^{-1} c_m (c: the per-step constant), C_in,m = |mu_m| times the
+two columns of L_m^{-1} that the inflow feeds (rows 0, 2 for mu > 0; 1, 3 for
+mu < 0), H = blockdiag_g sum_m w_m L_{g,m}^{-1}, K[g][g'] = dx/4 Sigma_s,g'->g,
+M' = (I - K H)^{-1} K."""
+import numpy as np
+import pytest
+
+from oracle import Oracle
+from paper_2503_00264_gb300 import workloads as W
+
+
+def _blocks(p, o, j):
+    N, G = p.N, p.G
+    mat, dx = int(p.mat[j]), float(p.dx[j])
+    Linv = np.zeros((G, N, 4, 4))
+    for g in range(G):
+        al = dx / (p.v[g] * p.dt)
+        for m in range(N):
+            mu = o.mu[m]
+            a = (abs(mu) + dx * p.sigma_t[mat, g]) / 2.0
+            L = np.array([[a, mu / 2, al / 2, 0.0], [-mu / 2, a, 0.0, al / 2],
+                          [-al, 0.0, al + a, mu / 2], [0.0, -al, -mu / 2, al + a]])
+            Linv[g, m] = np.linalg.inv(L)
+    rows = [(0, 2) if o.mu[m] > 0 else (1, 3) for m in range(N)]
+    Cin = np.zeros((G, N, 4, 2))
+    for g in range(G):
+        for m in range(N):
+            Cin[g, m] = abs(o.mu[m]) * Linv[g, m][:, list(rows[m])]
+    H = np.zeros((4 * G, 4 * G))
+    K = np.zeros((4 * G, 4 * G))
+    for g in range(G):
+        H[4 * g:4 * g + 4, 4 * g:4 * g + 4] = np.einsum("m,mpq->pq", o.w, Linv[g])
+        for gp in range(G):
+            K[4 * g:4 * g + 4, 4 * gp:4 * gp + 4] = dx / 4 * p.sigma_s[mat, gp, g] * np.eye(4)
+    Mp = np.linalg.solve(np.eye(4 * G) - K @ H, K)
+    return Linv, Cin, Mp, rows
+
+
+def _inflow(p, o, j, Psi_l):
+    u = np.zeros((p.G, p.N, 2))
+    for g in range(p.G):
+        for m in range(p.N):
+            if o.mu[m] > 0:
+                u[g, m] = Psi_l[j - 1, g, m, [1, 3]]
+            else:
+                u[g, m] = Psi_l[j + 1, g, m, [0, 2]]
+    return u
+
+
+@pytest.mark.parametrize("seed,N,G", [(201, 4, 1), (202, 8, 2), (203, 16, 1), (204, 8, 3), (205, 2, 4)])
+def test_staged_and_register_forms_equal_the_dense_solve(seed, N, G):
+    p = W.random_slab(seed, 6, N, G)
+    o = Oracle(p, factor=False)
+    rng = np.random.default_rng(seed)
+    for j in (1, 2, 4):  # interior cells: the inflow comes from the lagged iterate
+        Psi_l = rng.uniform(0.0, 2.0, size=(p.J, G, N, 4))
+        A = o.cell_matrix(j)
+        b = o.rhs(j, Psi_l)
+        ref = np.linalg.solve(A, b).reshape(G, N, 4)
+        c = o.rhs(j, np.zeros_like(Psi_l)).reshape(G, N, 4)  # interior cell: no inflow term
+        Linv, Cin, Mp, rows = _blocks(p, o, j)
+        u = _inflow(p, o, j, Psi_l)
+        tc = np.einsum("gmpq,gmq->gmp", Linv, c)
+        # staged form
+        t = tc + np.einsum("gmpk,gmk->gmp", Cin, u)
+        y = np.einsum("m,gmp->gp", o.w, t).reshape(4 * G)
+        s = (Mp @ y).reshape(G, 4)
+        psi_staged = t + np.einsum("gmpq,gq->gmp", Linv, s)
+        # register form
+        yc = np.einsum("m,gmp->gp", o.w, tc)
+        y2 = (yc + np.einsum("m,gmpk,gmk->gp", o.w, Cin, u)).reshape(4 * G)
+        s2 = (Mp @ y2).reshape(G, 4)
+        v = np.repeat(s2[:, None, :], N, axis=1)
+        for m in range(N):
+            r0, r1 = rows[m]
+            v[:, m, r0] += abs(o.mu[m]) * u[:, m, 0]
+            v[:, m, r1] += abs(o.mu[m]) * u[:, m, 1]
+        psi_reg = tc + np.einsum("gmpq,gmq->gmp", Linv, v)
+        scale = np.abs(ref).max()
+        assert np.abs(psi_staged - ref).max() < 1e-12 * scale
+        assert np.abs(psi_reg - ref).max() < 1e-12 * scale
