@@ -91,3 +91,42 @@ def test_staged_and_register_forms_equal_the_dense_solve(seed, N, G):
         scale = np.abs(ref).max()
         assert np.abs(psi_staged - ref).max() < 1e-12 * scale
         assert np.abs(psi_reg - ref).max() < 1e-12 * scale
+
+
+@pytest.mark.parametrize("seed,N,G", [(211, 4, 1), (212, 8, 2), (213, 16, 3)])
+def test_refinement_residual_equals_b_minus_A_psi(seed, N, G):
+    """The FP64 residual of the mixed forms' refinement, restated from the
+    kernel's row formulas (r = c + s + inflow - L_c Psi with s_g = sum_g'
+    dx/4 Sigma_s,g'->g phi_g'), equals b_j - A_j Psi_j from the oracle's dense
+    cell matrix for random iterates."""
+    p = W.random_slab(seed, 6, N, G)
+    o = Oracle(p, factor=False)
+    rng = np.random.default_rng(seed)
+    for j in (1, 3, 4):
+        Psi = rng.uniform(-1.0, 2.0, size=(p.J, G, N, 4))
+        ref = o.rhs(j, Psi) - o.cell_matrix(j) @ Psi[j].reshape(-1)
+        c = o.rhs(j, np.zeros_like(Psi)).reshape(G, N, 4)
+        mat, dx = int(p.mat[j]), float(p.dx[j])
+        phi = np.einsum("m,gmp->gp", o.w, Psi[j])
+        r = np.zeros((G, N, 4))
+        for g in range(G):
+            s = sum(dx / 4 * p.sigma_s[mat, gp, g] * phi[gp] for gp in range(G))
+            al = dx / (p.v[g] * p.dt)
+            for m in range(N):
+                mu = o.mu[m]
+                a = (abs(mu) + dx * p.sigma_t[mat, g]) / 2
+                hm, ha, aa = mu / 2, al / 2, al + a
+                v0, v1, v2, v3 = Psi[j, g, m]
+                rr = c[g, m] + s
+                if mu > 0:
+                    rr[0] += mu * Psi[j - 1, g, m, 1]
+                    rr[2] += mu * Psi[j - 1, g, m, 3]
+                else:
+                    rr[1] += -mu * Psi[j + 1, g, m, 0]
+                    rr[3] += -mu * Psi[j + 1, g, m, 2]
+                rr[0] -= a * v0 + hm * v1 + ha * v2
+                rr[1] -= -hm * v0 + a * v1 + ha * v3
+                rr[2] -= -al * v0 + aa * v2 + hm * v3
+                rr[3] -= -al * v1 - hm * v2 + aa * v3
+                r[g, m] = rr
+        assert np.abs(r.reshape(-1) - ref).max() < 1e-12 * np.abs(o.rhs(j, Psi)).max()
