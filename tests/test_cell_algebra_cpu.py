@@ -130,3 +130,61 @@ def test_refinement_residual_equals_b_minus_A_psi(seed, N, G):
                 rr[3] -= -al * v1 - hm * v2 + aa * v3
                 r[g, m] = rr
         assert np.abs(r.reshape(-1) - ref).max() < 1e-12 * np.abs(o.rhs(j, Psi)).max()
+
+
+@pytest.mark.parametrize("seed,J,N,G", [(221, 1, 2, 1), (222, 37, 8, 1), (223, 64, 4, 2), (224, 100, 16, 1)])
+def test_si_scan_composition_equals_the_sequential_sweep(seed, J, N, G):
+    """The scan form of SI: per (g, m) the outgoing edge of cell j is an affine
+    map u_out = T_j u_in + e_j of its incoming edge (T_j = |mu| times the 2x2 block
+    of L_j^{-1} from the inflow rows to the outflow corners, e_j the outflow corners
+    of L_j^{-1} d_j), the maps compose associatively ((T2, e2) after (T1, e1) =
+    (T2 T1, T2 e1 + e2)), and a log-depth inclusive scan of them gives every
+    cell's incoming edge.  Restated here in numpy, one SI sweep this way equals
+    the oracle's sequential sweep (Algorithm 1)."""
+    p = W.random_slab(seed, J, N, G)
+    o = Oracle(p, factor=False)
+    rng = np.random.default_rng(seed)
+    Psi0 = rng.uniform(0.0, 1.0, size=(J, G, N, 4))
+    o.Psi[...] = Psi0
+    o.iterate(1, method=1)  # one SI sweep from Psi0
+    ref = o.Psi.copy()
+    phi = np.einsum("m,jgmp->jgp", o.w, Psi0)
+    got = np.zeros_like(ref)
+    for g in range(G):
+        for m in range(N):
+            mu = o.mu[m]
+            order = list(range(J)) if mu > 0 else list(range(J - 1, -1, -1))
+            rin, rout = ([0, 2], [1, 3]) if mu > 0 else ([1, 3], [0, 2])
+            inc = p.inc_left if mu > 0 else p.inc_right
+            u0 = np.zeros(2) if inc is None else np.array(inc[g, m])
+            Li, d, T, e = [], [], [], []
+            for j in order:
+                mat, dx = int(p.mat[j]), float(p.dx[j])
+                al = dx / (p.v[g] * p.dt)
+                a = (abs(mu) + dx * p.sigma_t[mat, g]) / 2
+                L = np.array([[a, mu / 2, al / 2, 0.0], [-mu / 2, a, 0.0, al / 2],
+                              [-al, 0.0, al + a, mu / 2], [0.0, -al, -mu / 2, al + a]])
+                src = (0.0 if p.Q is None else p.Q[j, g]) + sum(p.sigma_s[mat, gp, g] * phi[j, gp] for gp in range(G))
+                dj = dx / 4 * np.broadcast_to(src, (4,)).astype(float).copy()
+                dj[0] += al / 2 * o.psi_prev[j, g, m, 0]
+                dj[1] += al / 2 * o.psi_prev[j, g, m, 1]
+                inv = np.linalg.inv(L)
+                Li.append(inv)
+                d.append(dj)
+                T.append(abs(mu) * inv[np.ix_(rout, rin)])
+                e.append((inv @ dj)[rout])
+            # Hillis-Steele inclusive scan of the affine maps
+            ST, Se = [t.copy() for t in T], [x.copy() for x in e]
+            off = 1
+            while off < J:
+                nT, ne = [t.copy() for t in ST], [x.copy() for x in Se]
+                for i in range(off, J):
+                    nT[i] = ST[i] @ ST[i - off]
+                    ne[i] = ST[i] @ Se[i - off] + Se[i]
+                ST, Se, off = nT, ne, off * 2
+            for s, j in enumerate(order):
+                uin = u0 if s == 0 else ST[s - 1] @ u0 + Se[s - 1]
+                rhs = d[s].copy()
+                rhs[rin] += abs(mu) * uin
+                got[j, g, m] = Li[s] @ rhs
+    assert np.abs(got - ref).max() < 1e-12 * np.abs(ref).max()
