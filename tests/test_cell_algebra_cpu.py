@@ -188,3 +188,44 @@ def test_si_scan_composition_equals_the_sequential_sweep(seed, J, N, G):
                 rhs[rin] += abs(mu) * uin
                 got[j, g, m] = Li[s] @ rhs
     assert np.abs(got - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("seed,J,N,G", [(231, 9, 4, 1), (232, 12, 8, 2)])
+def test_correction_refinement_converges_to_the_global_solve(seed, J, N, G):
+    """The precision forms' outer/inner structure, restated in numpy FP64: from
+    an iterate Psi, the residual r = b(Psi) - A Psi (per cell, inflow from Psi's
+    neighbours), then OCI sweeps on the correction (delta_j <- A_j^{-1} (r_j +
+    inflow of delta from the neighbours, zero at the slab ends)), then Psi <-
+    Psi + delta and a fresh residual.  A few refinements of a few inner sweeps
+    reach the oracle's global direct solve of the step, as the plain OCI
+    iteration does."""
+    from oracle import brute
+    p = W.random_slab(seed, J, N, G)
+    o = Oracle(p, factor=False)
+    A = [o.cell_matrix(j) for j in range(J)]
+    ref = brute.solve_step(p, o.psi_prev)
+    rng = np.random.default_rng(seed)
+    Psi = rng.uniform(0.0, 1.0, size=(J, G, N, 4))
+    n = 4 * N * G
+
+    def inflow(D, j):
+        """The inflow part of b_j taken from the array D (the A_j-independent rows)."""
+        b = np.zeros((G, N, 4))
+        for g in range(G):
+            for m in range(N):
+                mu = o.mu[m]
+                if mu > 0 and j > 0:
+                    b[g, m, 0] += mu * D[j - 1, g, m, 1]
+                    b[g, m, 2] += mu * D[j - 1, g, m, 3]
+                if mu < 0 and j < J - 1:
+                    b[g, m, 1] += -mu * D[j + 1, g, m, 0]
+                    b[g, m, 3] += -mu * D[j + 1, g, m, 2]
+        return b.reshape(n)
+
+    for _ in range(12):  # refinements
+        r = np.stack([o.rhs(j, Psi) - A[j] @ Psi[j].reshape(n) for j in range(J)])
+        delta = np.zeros_like(Psi)
+        for _ in range(8):  # inner correction sweeps (block Jacobi)
+            delta = np.stack([np.linalg.solve(A[j], r[j] + inflow(delta, j)).reshape(G, N, 4) for j in range(J)])
+        Psi = Psi + delta
+    assert np.abs(Psi - ref).max() < 1e-12 * np.abs(ref).max()
