@@ -53,7 +53,9 @@ class _Prob(ctypes.Structure):
                 ("n_mat", ctypes.c_int32),
                 ("dx", ctypes.c_void_p), ("mat", ctypes.c_void_p), ("sigma_t", ctypes.c_void_p),
                 ("sigma_s", ctypes.c_void_p), ("v", ctypes.c_void_p), ("Q", ctypes.c_void_p),
-                ("dt", ctypes.c_double), ("inc_left", ctypes.c_void_p), ("inc_right", ctypes.c_void_p)]
+                ("dt", ctypes.c_double), ("inc_left", ctypes.c_void_p), ("inc_right", ctypes.c_void_p),
+                ("n_slots", ctypes.c_int32), ("slot_of_cell", ctypes.c_void_p),
+                ("slot_first_cell", ctypes.c_void_p)]
 
 
 def lib():
@@ -73,8 +75,19 @@ def lib():
             L.orc_iterate.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp]
             L.orc_balance.argtypes = [vp, vp, vp, vp, vp, vp]
             L.orc_scalar_flux.argtypes = [vp, vp, vp, vp]
+            L.orc_set_threads.argtypes = [i32]
+            L.orc_get_threads.restype = i32
             _lib = L
         return _lib
+
+
+def set_threads(n: int) -> None:
+    """Threads of the oracle's OpenMP loops (timing only)."""
+    lib().orc_set_threads(int(n))
+
+
+def get_threads() -> int:
+    return int(lib().orc_get_threads())
 
 
 def _p(a):
@@ -92,11 +105,21 @@ class Oracle:
     """One slab problem held by the oracle: quadrature, factored A_j for every
     cell, the carried psi_{k-1/2} and the current iterate Psi."""
 
-    def __init__(self, prob, factor: bool = True):
+    def __init__(self, prob, factor: bool = True, share_factors: bool = False):
+        """share_factors: factor A_j once per distinct (material, dx) pair and
+        let every cell of that pair use it (bit-identical A_j, so bit-identical
+        results; needed where one factor per cell would not fit in memory)."""
         self.prob = prob
         P = prob
         self._keep = dict(dx=P.dx, mat=P.mat, st=P.sigma_t, ss=P.sigma_s, v=P.v, Q=P.Q,
-                          il=P.inc_left, ir=P.inc_right)
+                          il=P.inc_left, ir=P.inc_right, slot=None, first=None)
+        self.n_slots = P.J
+        if share_factors:
+            key = np.stack([np.asarray(P.mat, np.int64), np.asarray(P.dx, np.float64).view(np.int64)], axis=1)
+            _, first, slot = np.unique(key, axis=0, return_index=True, return_inverse=True)
+            self._keep["slot"] = np.ascontiguousarray(slot.reshape(-1), np.int32)
+            self._keep["first"] = np.ascontiguousarray(first, np.int32)
+            self.n_slots = len(first)
         self._mk_struct()
         self.mu, self.w = gauss_legendre(P.N)
         self.n = 4 * P.N * P.G
@@ -113,7 +136,7 @@ class Oracle:
         k = self._keep
         self.cp = _Prob(self.prob.J, self.prob.N, self.prob.G, self.prob.n_mat, _p(k["dx"]), _p(k["mat"]),
                         _p(k["st"]), _p(k["ss"]), _p(k["v"]), _p(k["Q"]), float(self.prob.dt),
-                        _p(k["il"]), _p(k["ir"]))
+                        _p(k["il"]), _p(k["ir"]), int(self.n_slots), _p(k["slot"]), _p(k["first"]))
 
     def set_boundary(self, inc_left, inc_right):
         P = self.prob
@@ -123,8 +146,8 @@ class Oracle:
 
     def factor(self):
         P = self.prob
-        self.LU = np.zeros((P.J, self.n, self.n))
-        self.piv = np.zeros((P.J, self.n), np.int32)
+        self.LU = np.zeros((self.n_slots, self.n, self.n))
+        self.piv = np.zeros((self.n_slots, self.n), np.int32)
         rc = lib().orc_factor_all(ctypes.byref(self.cp), _p(self.mu), _p(self.w), _p(self.LU), _p(self.piv))
         if rc != OK:
             raise RuntimeError(f"oracle factorisation failed ({rc})")

@@ -46,6 +46,7 @@
  *   unknown index inside a cell: idx(g,m,p) = (g*N + m)*4 + p   (Eq. x_vec)
  */
 #include <math.h>
+#include <omp.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -67,7 +68,20 @@ typedef struct {
   double dt;
   const double *inc_left;  /* [G][N][2] or NULL */
   const double *inc_right; /* [G][N][2] or NULL */
+  /* Optional factor sharing.  Cells whose (material, dx) are equal have
+   * bit-identical A_j (A_j depends on nothing else), so their LU factors are
+   * identical too; with slot_of_cell != NULL the factors are stored once per
+   * slot: slot_of_cell[j] in [0, n_slots) names the factor of cell j and
+   * slot_first_cell[s] the cell that slot s is factored from.  NULL: one
+   * factor per cell (slot = j).  Results are the same bits either way.        */
+  int32_t n_slots;
+  const int32_t *slot_of_cell;    /* [J] or NULL       */
+  const int32_t *slot_first_cell; /* [n_slots] or NULL */
 } orc_problem;
+
+static size_t lu_slot(const orc_problem *p, int j) {
+  return p->slot_of_cell ? (size_t)p->slot_of_cell[j] : (size_t)j;
+}
 
 /* ------------------------------------------------------------------------ */
 /* Gauss-Legendre quadrature on [-1,1] (the S_N set used throughout the paper,
@@ -207,15 +221,18 @@ void orc_lu_solve(int32_t n, const double *LU, const int32_t *piv, double *b) {
   }
 }
 
-/* Factor every cell's A_j (the paper's gesv on the first iteration, done once). */
+/* Factor every cell's A_j (the paper's gesv on the first iteration, done once);
+ * with factor sharing, once per slot from its first cell.                       */
 int orc_factor_all(const orc_problem *p, const double *mu, const double *w, double *LU, int32_t *piv) {
   const size_t n = (size_t)4 * p->N * p->G;
+  const int nf = p->slot_of_cell ? p->n_slots : p->J;
   int bad = 0;
 #pragma omp parallel for schedule(dynamic, 16) reduction(| : bad)
-  for (int j = 0; j < p->J; j++) {
-    double *A = LU + (size_t)j * n * n;
+  for (int s = 0; s < nf; s++) {
+    const int j = p->slot_of_cell ? p->slot_first_cell[s] : s;
+    double *A = LU + (size_t)s * n * n;
     orc_cell_matrix(p, mu, w, j, A);
-    if (orc_lu_factor((int32_t)n, A, piv + (size_t)j * n) != ORC_OK) bad = 1;
+    if (orc_lu_factor((int32_t)n, A, piv + (size_t)s * n) != ORC_OK) bad = 1;
   }
   return bad ? ORC_SINGULAR : ORC_OK;
 }
@@ -273,7 +290,7 @@ double orc_oci_sweep(const orc_problem *p, const double *mu, const double *LU, c
   for (int j = 0; j < p->J; j++) {
     double *b = Psi_new + (size_t)j * n;
     orc_rhs(p, mu, j, psi_prev, Psi_l, b);
-    orc_lu_solve((int32_t)n, LU + (size_t)j * n * n, piv + (size_t)j * n, b);
+    orc_lu_solve((int32_t)n, LU + lu_slot(p, j) * n * n, piv + lu_slot(p, j) * n, b);
   }
   double s = 0.0;
   for (size_t i = 0; i < (size_t)p->J * n; i++) {
@@ -296,7 +313,7 @@ double orc_rb_sweep(const orc_problem *p, const double *mu, const double *LU, co
   for (int color = 0; color < 2; color++)
     for (int j = color; j < p->J; j += 2) {
       orc_rhs(p, mu, j, psi_prev, Psi_new, b);
-      orc_lu_solve((int32_t)n, LU + (size_t)j * n * n, piv + (size_t)j * n, b);
+      orc_lu_solve((int32_t)n, LU + lu_slot(p, j) * n * n, piv + lu_slot(p, j) * n, b);
       memcpy(Psi_new + (size_t)j * n, b, n * sizeof(double));
     }
   free(b);
@@ -587,3 +604,8 @@ int orc_iterate(const orc_problem *p, int32_t method, int32_t n, const double *L
   free(Psi_a); free(phi_a); free(phi_b);
   return ORC_OK;
 }
+
+/* Thread count of the OpenMP loops above (used only to time the oracle on one
+ * core and on all cores; results do not depend on it).                        */
+void orc_set_threads(int32_t n) { omp_set_num_threads(n > 0 ? n : 1); }
+int32_t orc_get_threads(void) { return omp_get_max_threads(); }

@@ -452,3 +452,20 @@ def test_si_multigroup_rate_is_jacobi_over_groups(st, ss, v, dt):
     rg = np.abs(np.linalg.eigvals(_si_flat_iteration_matrix(st, ss, v, dt, "gauss_seidel"))).max()
     assert abs(rate - rj) < 0.02 * rj, (rate, rj)
     assert abs(rate - rg) > 0.10 * rg, (rate, rg)
+
+
+def test_shared_factors_give_the_same_bits():
+    """Factoring A_j once per distinct (material, dx) pair (the memory-saving
+    mode used at full size) changes nothing: A_j depends on no other cell
+    datum, so the iterates, norms and committed steps are bitwise equal to one
+    factor per cell, for OCI and red-black OCI."""
+    p = W.slab_3region(c=0.9, tau=0.3, J=3 * 40 + 7, N=8, region=40)
+    for method in (OCI, RB):
+        a, b = Oracle(p), Oracle(p, share_factors=True)
+        assert b.n_slots == 3 and b.LU.shape[0] == 3
+        for _ in range(2):
+            ra, rb = a.step(method), b.step(method)
+            assert ra["iters"] == rb["iters"]
+            assert np.array_equal(ra["Psi"], rb["Psi"]) and np.array_equal(ra["e_hist"], rb["e_hist"])
+    q = W.random_slab(8, 30, 4, 2)
+    assert Oracle(q, share_factors=True).n_slots == 30
