@@ -31,6 +31,25 @@
  *   - Unknowns of one cell are ordered idx(g,m,p) = (g*N + m)*4 + p with
  *     p = 0 kL, 1 kR, 2 hL, 3 hR (k: time average over the step, h: time edge
  *     t_{k+1/2}; L/R: left/right corner) -- Eq. x_vec extended to groups.
+ *   - The environment does not change what runs.  For tests and profiling the
+ *     library honours these variables, read at setup (the spin limit at every
+ *     step), only when OCI_TEST_HOOKS=1 is also set:
+ *       OCI_AUTOTUNE=0            keep the default launch shapes (no timing)
+ *       OCI_SWEEP_SHAPE=cb,P      pin the sweep shape (cells per block, angle chunks)
+ *       OCI_SWEEP_REG=0|1         FP64 sweep: staged or register form only
+ *       OCI_MX_INNER=plain|tma|reg|tiled|tiledp|tiledb|two|twoocc
+ *                                 FP32 inner sweep kernel of the mixed form
+ *       OCI_MX_RB=1|2             red-black FP32 inner sweep, one or two sweeps per pass
+ *       OCI_MX_MULTI=0            one inner sweep per launch in the graph
+ *       OCI_MX_KMAX, OCI_MX_THETA refinement schedule of the mixed forms
+ *       OCI_MX_OUTER_CVT=hw       compiler conversions in the FP64 refinement
+ *       OCI_RB_FP64=inplace       FP64 red-black half sweeps in place
+ *       OCI_RB_SHAPE=s|r,cb,P     pin the FP64 red-black shape
+ *       OCI_TC_PIPE=0             one-tile-per-CTA tensor-core kernel
+ *       OCI_BATCH_SWEEP           pin the batched sweep form
+ *       OCI_NO_GRAPH=1            host-driven loop instead of the CUDA graph
+ *       OCI_TEST_SPIN_LIMIT=k     grid-barrier spin limit of the cooperative
+ *                                 kernels (0: the step ends with OCI_E_TIMEOUT)
  */
 #ifndef OCI_H
 #define OCI_H
@@ -265,8 +284,10 @@ int oci_commit(oci_handle *h, oci_stats *st);
  * order, groups, materials, dt, tolerances) advanced together.  Slabs that
  * share (N, G) are packed into one cell range; every time step is one CUDA
  * graph launch whose persistent sweep kernels skip slabs that have converged,
- * each slab with its own stop rule (Sec. 2.1).  FP64, structured solver and
- * OCI_GUESS_PREV only; all problems must name the same stream.  The returned
+ * each slab with its own stop rule (Sec. 2.1).  Precision OCI_FP64, or
+ * OCI_FP32_IR (FP32 inner sweeps with per-slab FP64 refinement), one precision
+ * for the whole batch; structured solver and OCI_GUESS_PREV only; all problems
+ * must name the same stream.  The returned
  * handle accepts only the oci_batch_* calls and oci_destroy (others return
  * OCI_E_STATE). */
 int oci_batch_setup(const oci_problem *probs, int32_t n, oci_handle **out);
@@ -289,8 +310,8 @@ int oci_batch_get_balance(const oci_handle *h, int32_t s, double *bal);
 /* Convergence norm e = ||a - b||_2 over n FP64 values, for callers that cannot
  * allocate device memory when they need it (allocator callbacks, loops whose
  * memory is budgeted once at start-up, applications whose device memory is
- * owned by another framework).  The paper has no counterpart: this is a
- * standalone form of the norm of Sec. 2.1 that oci_step takes internally.
+ * owned by another framework).  The paper has no counterpart: it is an extra
+ * entry point of this library (oci_step computes the same norm internally).
  *   a, b   device pointers to n values each (any layout, same for both)
  *   n      0 <= n <= 33,554,432 (the fixed scratch holds 16,384 partial sums of
  *          2,048 values each); larger n returns OCI_E_INVAL
@@ -300,8 +321,10 @@ int oci_batch_get_balance(const oci_handle *h, int32_t s, double *bal);
  * Nothing is allocated: the partial sums live in one fixed 128 KiB device array
  * per GPU, held until the process exits.  The first call on a device looks up
  * that array's device address (cudaGetSymbolAddress); make that first call
- * before capturing a stream.  Calls that overlap on the GPU share the array
- * and race; the result is deterministic for a given n. */
+ * before capturing a stream.  The address is kept for the life of the process:
+ * it does not survive cudaDeviceReset (or any new primary context) on that
+ * device, after which this call must not be used.  Calls that overlap on the
+ * GPU share the array and race; the result is deterministic for a given n. */
 int oci_diff_norm_noalloc(const double *a, const double *b, int64_t n, double *e_out, void *stream);
 
 /* Facts of the setup of a single-slab handle (see oci_info). */
@@ -335,17 +358,26 @@ int oci_set_acceleration(oci_handle *h, int32_t accel, int32_t restart, double r
  * rho[i] = max over theta_k = 2 pi k / (n_theta - 1), k = 0 .. n_theta-1 (theta
  * = 0 alone if n_theta = 1), of the spectral radius of the iteration operator of
  * a mode e^{i theta j}:
- *   OCI_FOURIER_OCI: T = (L_c - S)^{-1} B(theta)   (one-cell inversion)
- *   OCI_FOURIER_SI:  T = (L_c - B(theta))^{-1} S   (source iteration)
+ *   OCI_FOURIER_OCI:   T = (L_c - S)^{-1} B(theta)   (one-cell inversion)
+ *   OCI_FOURIER_SI:    T = (L_c - B(theta))^{-1} S   (source iteration)
+ *   OCI_FOURIER_MARCH: the time-march amplification of Sec. 2.2 (Eqs. eig1-4,
+ *                      K+ and K-), psi_{k+1/2} = K psi_{k-1/2}: the largest
+ *                      |eigenvalue| of the per-ordinate 2 x 2 matrix
+ *                      K = gamma (K+- K+- + (dx/(v dt)) K+- + gamma I)^{-1},
+ *                      gamma = (dx/(v dt)) (dx/(2 v dt)), over theta and the N
+ *                      ordinates; the model problem has no scattering, so c is
+ *                      not read (it may be NULL); tau = +inf gives 0.
+ *                      Unconditional stability is rho <= 1 everywhere.
  * with L_c the cell operator (Eq. Aj), S the within-cell scattering (Eq.
- * scatter, column-angle weight) and B(theta) the lagged inflow.  Computed on
- * reduced matrices with the same nonzero spectrum (2N x 2N for OCI, 4 x 4 for
- * SI) as lim ||M^n||^{1/n} with n = 2^30 (normalised repeated squaring, FP64).
+ * scatter, column-angle weight) and B(theta) the lagged inflow.  OCI and SI are
+ * computed on reduced matrices with the same nonzero spectrum (2N x 2N for OCI,
+ * 4 x 4 for SI) as lim ||M^n||^{1/n} with n = 2^30 (normalised repeated
+ * squaring, FP64); MARCH from the closed-form eigenvalues of each 2 x 2 K.
  * N even, 2 <= N <= 32; 1 <= n_cases <= 65535.  delta, tau, c: [n_cases], all host or all device;
  * rho: [n_cases], host or device.  stream: cudaStream_t or NULL.  Blocks until
  * the result is written.  Returns OCI_E_INVAL for bad arguments before any
  * device work. */
-enum { OCI_FOURIER_OCI = 0, OCI_FOURIER_SI = 1 };
+enum { OCI_FOURIER_OCI = 0, OCI_FOURIER_SI = 1, OCI_FOURIER_MARCH = 2 };
 int oci_fourier_rho(int32_t kind, int32_t N, int32_t n_cases, const double *delta, const double *tau,
                     const double *c, int32_t n_theta, double *rho, void *stream);
 

@@ -276,8 +276,16 @@ static int build_graph(Handle &h, bool si, cudaGraphExec_t *out);
 // memory <= 100 KB -- is timed over a few sweeps of this problem (CUDA events),
 // and the fastest is kept for the graphs.  State is zeroed afterwards.
 // OCI_AUTOTUNE=0 keeps the default shape.
+// A candidate shape whose launch the runtime refuses (more blocks than can be
+// co-resident for a cooperative launch, or an empty grid where not one block
+// fits on an SM) is skipped by the autotuners rather than timed.
+static bool launch_refused(cudaError_t e) {
+  return e == cudaErrorCooperativeLaunchTooLarge || e == cudaErrorInvalidConfiguration ||
+         e == cudaErrorLaunchOutOfResources;
+}
+
 static int autotune(Handle &h) {
-  const char *at = getenv("OCI_AUTOTUNE");
+  const char *at = hook_env("OCI_AUTOTUNE");
   if (at && at[0] == '0') return OCI_OK;
   const bool mx = h.precision == OCI_FP32_IR;
   if (h.solver == OCI_SOLVER_DENSE_LU || (h.precision != OCI_FP64 && !mx)) return OCI_OK;
@@ -331,7 +339,7 @@ static int autotune(Handle &h) {
       }
     }
   // OCI_MX_INNER=plain|tma|reg|tiled|tiledp|tiledb|two|twoocc restricts the FP32 inner sweep to one kernel (for profiling)
-  const char *only = getenv("OCI_MX_INNER");
+  const char *only = hook_env("OCI_MX_INNER");
   if (mx && only) {
     const std::string o(only);
     const int want = o == "tma"      ? kMxTma
@@ -348,7 +356,7 @@ static int autotune(Handle &h) {
     if (!keep.empty()) cands.swap(keep);
   }
   // OCI_SWEEP_REG=0|1 restricts the FP64 Jacobi sweep to the staged / register form
-  const char *sreg = getenv("OCI_SWEEP_REG");
+  const char *sreg = hook_env("OCI_SWEEP_REG");
   if (!mx && sreg) {
     const int want = sreg[0] == '1' ? kSweepReg64 : kMxPlain;
     std::vector<Cand> keep;
@@ -358,7 +366,7 @@ static int autotune(Handle &h) {
   }
   // OCI_SWEEP_SHAPE="cb,P" keeps one legal shape (the first of the remaining
   // candidates with that shape) without timing, so a profiler sees no tuning launches
-  const char *shape = getenv("OCI_SWEEP_SHAPE");
+  const char *shape = hook_env("OCI_SWEEP_SHAPE");
   if (shape) {
     int fcb = 0, fP = 0;
     if (sscanf(shape, "%d,%d", &fcb, &fP) == 2)
@@ -420,7 +428,12 @@ static int autotune(Handle &h) {
       }
       CK(cudaEventRecord(h.ev1, h.stream));
       CK(cudaEventSynchronize(h.ev1));
-      CK(cudaGetLastError());
+      const cudaError_t le = cudaGetLastError();
+      if (launch_refused(le)) {
+        ms = 1e30f;
+        break;
+      }
+      if (le != cudaSuccess) return cuda_fail(le, "timing a sweep shape");
       float m = 0.f;
       cudaEventElapsedTime(&m, h.ev0, h.ev1);
       ms = std::min(ms, m);
@@ -431,6 +444,7 @@ static int autotune(Handle &h) {
       bc = c;
     }
   }
+  if (best >= 1e30f) return set_error("no sweep shape could be launched on this device"), OCI_E_CUDA;
   apply(bc);
   h.tune_us = 1e3 * best / reps;
   const size_t nPsi = (size_t)h.G * h.N * 4 * h.Jp;
@@ -443,6 +457,7 @@ static int autotune(Handle &h) {
   }
   std::memset(h.h_ds, 0, sizeof(DevState));
   h.h_ds->done = 1;
+  h.h_ds->spin = kGridSpin;
   CK(cudaMemcpyAsync(h.ds, h.h_ds, sizeof(DevState), cudaMemcpyHostToDevice, h.stream));
   CK(cudaStreamSynchronize(h.stream));
   return OCI_OK;
@@ -481,7 +496,7 @@ static int tune_rb64(Handle &h) {
     h.rb_cb = c.cb;
     h.rb_P = c.P;
   };
-  const char *force = getenv("OCI_RB_SHAPE");
+  const char *force = hook_env("OCI_RB_SHAPE");
   if (force) {
     char k = 0;
     int fcb = 0, fP = 0;
@@ -493,44 +508,54 @@ static int tune_rb64(Handle &h) {
         }
     return set_error("OCI_RB_SHAPE names no legal red-black shape for this N, G"), OCI_E_INVAL;
   }
-  const char *at = getenv("OCI_AUTOTUNE");
-  if ((at && at[0] == '0') || getenv("OCI_SWEEP_SHAPE") || rcs.size() < 2) return OCI_OK;
+  const char *at = hook_env("OCI_AUTOTUNE");
+  if ((at && at[0] == '0') || hook_env("OCI_SWEEP_SHAPE") || rcs.size() < 2) return OCI_OK;
+  // the handle's ordering, red-black shape and state record are put back on
+  // every path, so a failed timing leaves the handle as it was
   const DevState saved = *h.h_ds;
-  DevState &d = *h.h_ds;
-  d.done = 0;
-  d.fixed = 1;
-  d.max_iter = 0;  // no e history while timing
-  d.inplace = 1;   // no flip of cur: Psi[cur] is only read
-  CK(cudaMemcpyAsync(h.ds, h.h_ds, sizeof(DevState), cudaMemcpyHostToDevice, h.stream));
-  const int ordering = h.ordering, reps = 4;
-  h.ordering = OCI_ORDER_RED_BLACK;
+  const int ordering = h.ordering;
+  const RbC before{h.rb_reg, h.rb_cb, h.rb_P};
+  const int reps = 4;
   float best = 1e30f;
   RbC bc = rcs[0];
-  for (auto &c : rcs) {
-    apply(c);
-    launch_oci_sweep(h, cudaGraphConditionalHandle{}, 0);
-    float ms = 1e30f;
-    for (int t = 0; t < 2; t++) {  // the faster of two timings
-      CK(cudaEventRecord(h.ev0, h.stream));
-      for (int r = 0; r < reps; r++) launch_oci_sweep(h, cudaGraphConditionalHandle{}, 0);
-      CK(cudaEventRecord(h.ev1, h.stream));
-      CK(cudaEventSynchronize(h.ev1));
-      CK(cudaGetLastError());
-      float m = 0.f;
-      cudaEventElapsedTime(&m, h.ev0, h.ev1);
-      ms = std::min(ms, m);
+  auto time_all = [&]() -> int {
+    DevState &d = *h.h_ds;
+    d.done = 0;
+    d.fixed = 1;
+    d.max_iter = 0;  // no e history while timing
+    d.inplace = 1;   // no flip of cur: Psi[cur] is only read
+    CK(cudaMemcpyAsync(h.ds, h.h_ds, sizeof(DevState), cudaMemcpyHostToDevice, h.stream));
+    h.ordering = OCI_ORDER_RED_BLACK;
+    for (auto &c : rcs) {
+      apply(c);
+      launch_oci_sweep(h, cudaGraphConditionalHandle{}, 0);
+      float ms = 1e30f;
+      for (int t = 0; t < 2; t++) {  // the faster of two timings
+        CK(cudaEventRecord(h.ev0, h.stream));
+        for (int r = 0; r < reps; r++) launch_oci_sweep(h, cudaGraphConditionalHandle{}, 0);
+        CK(cudaEventRecord(h.ev1, h.stream));
+        CK(cudaEventSynchronize(h.ev1));
+        CK(cudaGetLastError());
+        float m = 0.f;
+        cudaEventElapsedTime(&m, h.ev0, h.ev1);
+        ms = std::min(ms, m);
+      }
+      if (ms < best) {
+        best = ms;
+        bc = c;
+      }
     }
-    if (ms < best) {
-      best = ms;
-      bc = c;
-    }
-  }
+    return OCI_OK;
+  };
+  const int rc = time_all();
   h.ordering = ordering;
-  apply(bc);
-  h.rb_tune_us = 1e3 * best / reps;
+  apply(rc ? before : bc);
+  if (!rc) h.rb_tune_us = 1e3 * best / reps;
   *h.h_ds = saved;
-  CK(cudaMemcpyAsync(h.ds, h.h_ds, sizeof(DevState), cudaMemcpyHostToDevice, h.stream));
-  CK(cudaStreamSynchronize(h.stream));
+  cudaMemcpyAsync(h.ds, h.h_ds, sizeof(DevState), cudaMemcpyHostToDevice, h.stream);
+  const cudaError_t e = cudaStreamSynchronize(h.stream);
+  if (rc) return rc;
+  if (e != cudaSuccess) return cuda_fail(e, "restoring the state after red-black timing");
   return OCI_OK;
 }
 
@@ -547,7 +572,7 @@ static int tune_rb(Handle &h) {
     int kind, T, P;
   };
   std::vector<RbCand> cands;
-  const char *only = getenv("OCI_MX_RB");
+  const char *only = hook_env("OCI_MX_RB");
   const bool stage = mx_tables_floats(h) * 4 <= 64 * 1024;
   for (int T : {32, 64})
     for (int np : {2, 4, 8}) {
@@ -559,7 +584,7 @@ static int tune_rb(Handle &h) {
         cands.push_back({kMxRB2, T, P});
     }
   if (cands.empty()) return set_error("no red-black inner-sweep shape fits this N, G"), OCI_E_INVAL;
-  const char *shape = getenv("OCI_SWEEP_SHAPE");
+  const char *shape = hook_env("OCI_SWEEP_SHAPE");
   if (shape) {
     int fT = 0, fP = 0;
     if (sscanf(shape, "%d,%d", &fT, &fP) == 2)
@@ -579,49 +604,65 @@ static int tune_rb(Handle &h) {
     apply(cands[0]);
     return OCI_OK;
   }
+  // the inner-sweep choice and the state record are put back on a failure
   const DevState saved = *h.h_ds;
-  DevState d = saved;
-  d.done = 0;
-  d.fixed = 1;
-  d.refine = 0;
-  d.blk_i = 1;
-  d.dcur = 0;
-  d.max_iter = 0;
-  d.k_max = 1 << 30;
-  d.theta = 0.0;
+  const RbCand before{h.mx_kind, h.mx_cb, h.mx_P};
   float best = 1e30f;
   RbCand bc = cands[0];
   const int reps = 4;
-  for (auto &c : cands) {
-    apply(c);
-    d.inplace = c.kind == kMxRB;
-    *h.h_ds = d;
-    CK(cudaMemcpyAsync(h.ds, h.h_ds, sizeof(DevState), cudaMemcpyHostToDevice, h.stream));
-    h.mx_tune_sweeps = 1;
-    launch_mx_inner(h, cudaGraphConditionalHandle{}, 0);
-    float ms = 1e30f;
-    for (int t = 0; t < 2; t++) {  // the faster of two timings: one disturbed launch picks no shape
-      CK(cudaEventRecord(h.ev0, h.stream));
-      h.mx_tune_sweeps = reps;
+  auto time_all = [&]() -> int {
+    DevState d = saved;
+    d.done = 0;
+    d.fixed = 1;
+    d.refine = 0;
+    d.blk_i = 1;
+    d.dcur = 0;
+    d.max_iter = 0;
+    d.k_max = 1 << 30;
+    d.theta = 0.0;
+    d.spin = kGridSpin;
+    for (auto &c : cands) {
+      apply(c);
+      d.inplace = c.kind == kMxRB;
+      *h.h_ds = d;
+      CK(cudaMemcpyAsync(h.ds, h.h_ds, sizeof(DevState), cudaMemcpyHostToDevice, h.stream));
+      h.mx_tune_sweeps = 1;
       launch_mx_inner(h, cudaGraphConditionalHandle{}, 0);
-      CK(cudaEventRecord(h.ev1, h.stream));
-      CK(cudaEventSynchronize(h.ev1));
-      CK(cudaGetLastError());
-      float m = 0.f;
-      cudaEventElapsedTime(&m, h.ev0, h.ev1);
-      ms = std::min(ms, m);
+      float ms = 1e30f;
+      for (int t = 0; t < 2; t++) {  // the faster of two timings: one disturbed launch picks no shape
+        CK(cudaEventRecord(h.ev0, h.stream));
+        h.mx_tune_sweeps = reps;
+        launch_mx_inner(h, cudaGraphConditionalHandle{}, 0);
+        CK(cudaEventRecord(h.ev1, h.stream));
+        CK(cudaEventSynchronize(h.ev1));
+        const cudaError_t le = cudaGetLastError();
+        if (launch_refused(le)) {
+          ms = 1e30f;
+          break;
+        }
+        if (le != cudaSuccess) return cuda_fail(le, "timing a red-black inner sweep");
+        float m = 0.f;
+        cudaEventElapsedTime(&m, h.ev0, h.ev1);
+        ms = std::min(ms, m);
+      }
+      h.mx_tune_sweeps = 0;
+      if (ms < best) {
+        best = ms;
+        bc = c;
+      }
     }
-    h.mx_tune_sweeps = 0;
-    if (ms < best) {
-      best = ms;
-      bc = c;
-    }
-  }
-  apply(bc);
-  h.tune_us = 1e3 * best / reps;
+    if (best >= 1e30f) return set_error("no red-black inner sweep could be launched on this device"), OCI_E_CUDA;
+    return OCI_OK;
+  };
+  const int rc = time_all();
+  h.mx_tune_sweeps = 0;
+  apply(rc ? before : bc);
+  if (!rc) h.tune_us = 1e3 * best / reps;
   *h.h_ds = saved;
-  CK(cudaMemcpyAsync(h.ds, h.h_ds, sizeof(DevState), cudaMemcpyHostToDevice, h.stream));
-  CK(cudaStreamSynchronize(h.stream));
+  cudaMemcpyAsync(h.ds, h.h_ds, sizeof(DevState), cudaMemcpyHostToDevice, h.stream);
+  const cudaError_t e = cudaStreamSynchronize(h.stream);
+  if (rc) return rc;
+  if (e != cudaSuccess) return cuda_fail(e, "restoring the state after red-black timing");
   return OCI_OK;
 }
 
@@ -667,7 +708,7 @@ static int setup_impl(const oci_problem *p, oci_handle *h) {
   h->solver = p->solver == OCI_SOLVER_AUTO ? OCI_SOLVER_STRUCTURED : p->solver;
   h->stream = (cudaStream_t)p->stream;
   {
-    const char *ng = getenv("OCI_NO_GRAPH");
+    const char *ng = hook_env("OCI_NO_GRAPH");
     h->no_graph = ng && ng[0] == '1';
   }
   CK(cudaGetDevice(&h->device));
@@ -748,11 +789,11 @@ static int setup_impl(const oci_problem *p, oci_handle *h) {
   CK(cudaMalloc(&h->gbar, 2 * sizeof(unsigned)));
   CK(cudaMemsetAsync(h->gbar, 0, 2 * sizeof(unsigned), s));
   {
-    const char *mm = getenv("OCI_MX_MULTI");  // 0: one inner sweep per launch in the graph as well
+    const char *mm = hook_env("OCI_MX_MULTI");  // 0: one inner sweep per launch in the graph as well
     h->mx_multi = !(mm && mm[0] == '0');
-    const char *rf = getenv("OCI_RB_FP64");  // "inplace": FP64 red-black half sweeps update Psi[cur] in place
+    const char *rf = hook_env("OCI_RB_FP64");  // "inplace": FP64 red-black half sweeps update Psi[cur] in place
     h->rb_pingpong = !(rf && rf[0] == 'i');
-    const char *cv = getenv("OCI_MX_OUTER_CVT");  // "hw": compiler conversions in the FP64 refinement
+    const char *cv = hook_env("OCI_MX_OUTER_CVT");  // "hw": compiler conversions in the FP64 refinement
     h->mx_hwcvt = (cv && cv[0] == 'h') ? 1 : 0;
   }
   const int nblk_carry = (h->J + 31) / 32;
@@ -766,6 +807,7 @@ static int setup_impl(const oci_problem *p, oci_handle *h) {
   CK(cudaMallocHost(&h->h_bal, G * 10 * 8));
   std::memset(h->h_ds, 0, sizeof(DevState));
   h->h_ds->done = 1;
+  h->h_ds->spin = kGridSpin;
   CK(cudaMemcpyAsync(h->ds, h->h_ds, sizeof(DevState), cudaMemcpyHostToDevice, s));
   CK(cudaEventCreate(&h->ev0));
   CK(cudaEventCreate(&h->ev1));
@@ -844,9 +886,9 @@ static int setup_impl(const oci_problem *p, oci_handle *h) {
       if ((rc = tc_build_images(*h, Ainv_all))) return rc;
       if ((rc = tc_prepare(*h))) return rc;
     }
-    const char *km = getenv("OCI_MX_KMAX");
+    const char *km = hook_env("OCI_MX_KMAX");
     if (km) h->mx_kmax = std::max(1, atoi(km));
-    const char *th = getenv("OCI_MX_THETA");
+    const char *th = hook_env("OCI_MX_THETA");
     if (th) h->mx_theta = atof(th);
   }
   if ((rc = autotune(*h))) return rc;
@@ -953,8 +995,21 @@ static int build_graph(Handle &h, bool si, cudaGraphExec_t *out) {
 }
 
 // ---------------------------------------------------------------- stepping
+// Spin limit of the cooperative kernels' grid barrier for the coming step:
+// kGridSpin, or the test hook OCI_TEST_SPIN_LIMIT (an integer >= 0; 0 makes
+// every block that is not the last to arrive give up at once, so the step ends
+// with OCI_E_TIMEOUT without any wait).
+static long long step_spin_limit() {
+  const char *v = hook_env("OCI_TEST_SPIN_LIMIT");
+  if (!v) return kGridSpin;
+  char *end = nullptr;
+  const long long x = strtoll(v, &end, 10);
+  return (end != v && x >= 0 && x <= kGridSpin) ? x : kGridSpin;
+}
+
 static int begin_iteration(Handle &h, int fixed, int cap) {
   DevState &d = *h.h_ds;
+  d.spin = step_spin_limit();
   d.l = 0;
   d.status = OCI_OK;
   d.done = 0;
@@ -1067,6 +1122,8 @@ static int run_step(Handle &h, bool si, oci_stats *st) {
     set_error(buf);
   } else if (d.status == OCI_E_NONFINITE) {
     set_error("the convergence norm is not finite");
+  } else if (d.status == OCI_E_TIMEOUT) {
+    set_error("a bounded device-side wait gave up (step not committed)");
   }
   return d.status;
 }

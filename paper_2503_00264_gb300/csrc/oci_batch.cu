@@ -899,7 +899,7 @@ void launch_b_mx_outer(BatchClass &c, DevState *ds, int mode, cudaStream_t st) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int grid = std::min(c.d.n_tiles, 4 * sms);
-  const char *cv = getenv("OCI_MX_OUTER_CVT");  // "hw": compiler conversions
+  const char *cv = hook_env("OCI_MX_OUTER_CVT");  // "hw": compiler conversions
   const int hwcvt = (cv && cv[0] == 'h') ? 1 : 0;
   k_b_mx_outer<<<grid > 0 ? grid : 1, dim3(c.cb, c.d.G), (size_t)c.cb * c.d.G * 4 * sizeof(double), st>>>(c.d, ds,
                                                                                                          mode, hwcvt);

@@ -222,7 +222,7 @@ static int setup_class(Batch &B, BatchClass &c, const oci_problem *probs) {
   }
   if (cands.empty()) cands.emplace_back(0, 32);
   std::pair<int, int> best = cands.back();
-  const char *at = getenv("OCI_AUTOTUNE");
+  const char *at = hook_env("OCI_AUTOTUNE");
   if (cands.size() > 1 && !(at && at[0] == '0')) {
     for (int i = 0; i < c.d.n_slabs; i++) {
       DevState &x = B.h_ds[c.slab0 + i];
@@ -266,7 +266,7 @@ static int setup_class(Batch &B, BatchClass &c, const oci_problem *probs) {
   // it is valid for the class: np = 0 or np | N; cb a power of two in
   // [kMinTile, 128]; whole warps (the reductions shuffle over full warps), at
   // most 256 threads; shared memory within the set limit
-  const char *force = getenv("OCI_BATCH_SWEEP");
+  const char *force = hook_env("OCI_BATCH_SWEEP");
   if (force) {
     int fnp = -1, fcb = -1;
     if (sscanf(force, "%d,%d", &fnp, &fcb) == 2 && fcb >= kMinTile && fcb <= 128 && (fcb & (fcb - 1)) == 0) {
@@ -473,7 +473,7 @@ static int batch_setup(const oci_problem *probs, int n, Batch &B) {
   BCK(cudaMallocHost(&B.h_active, sizeof(int)));
   // OCI_NO_GRAPH=1: drive the loop from the host (profilers that do not
   // descend into conditional graph bodies see every kernel)
-  const char *ng = getenv("OCI_NO_GRAPH");
+  const char *ng = hook_env("OCI_NO_GRAPH");
   B.no_graph = ng && ng[0] == '1';
   if (!B.no_graph) {
     int rc = build_batch_graph(B);
@@ -491,7 +491,7 @@ static int batch_step(Batch &B, oci_stats *st) {
   int kmax = kBatchMxKmax;
   double theta = kBatchMxTheta;
   {
-    const char *km = getenv("OCI_MX_KMAX"), *th = getenv("OCI_MX_THETA");
+    const char *km = hook_env("OCI_MX_KMAX"), *th = hook_env("OCI_MX_THETA");
     if (km) kmax = std::max(1, atoi(km));
     if (th) theta = atof(th);
   }

@@ -21,6 +21,8 @@
 // The spectral radius of each small matrix M is lim ||M^n||^{1/n}, evaluated with
 // 2^30 as n by normalised repeated squaring (Frobenius norm, FP64 complex);
 // rho of a case is the maximum over theta_k = 2 pi k / (n_theta - 1).
+// The time-march amplification of Sec. 2.2 (kind OCI_FOURIER_MARCH) is a 2x2
+// matrix per ordinate in closed form; its eigenvalues come from the quadratic.
 #include <math.h>
 
 #include <vector>
@@ -295,6 +297,75 @@ __global__ void k_fourier_rho_si(int N, int n_theta, const double *__restrict__ 
   if (lane == 0) atomic_max_pos(rho + cse, r);
 }
 
+__device__ __forceinline__ cplx cdiv(cplx a, cplx b) {
+  const double d = cabs2(b);
+  return {(a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d};
+}
+
+// Principal square root of a complex number (half-angle form).
+__device__ __forceinline__ cplx csqrt_(cplx z) {
+  const double r = hypot(z.x, z.y);
+  const double re = sqrt(fmax(0.0, 0.5 * (r + z.x)));
+  const double im = sqrt(fmax(0.0, 0.5 * (r - z.x)));
+  return {re, z.y < 0.0 ? -im : im};
+}
+
+// Time-march amplification of Sec. 2.2 (infinite homogeneous medium, no
+// scattering, Sigma = v = 1 so dx = delta and dt = tau): per ordinate and wave
+// number the 2x2 matrix K = gamma (K+- K+- + (dx/(v dt)) K+- + gamma I)^{-1},
+// gamma = (dx/(v dt)) (dx/(2 v dt)), with
+//   K+ = [[mu/2 + delta/2, mu (1/2 - e^{-i theta})], [-mu/2, mu/2 + delta/2]]     (mu > 0)
+//   K- = [[-mu/2 + delta/2, mu/2], [mu (e^{i theta} - 1/2), -mu/2 + delta/2]]     (mu < 0)
+// and its eigenvalues from the characteristic quadratic.  One thread per
+// (theta, ordinate, case); rho of a case = the largest |lambda| over all of them.
+__global__ void k_fourier_rho_march(int N, int n_theta, int n_cases, const double *__restrict__ mu,
+                                    const double *__restrict__ delta, const double *__restrict__ tau,
+                                    double *__restrict__ rho) {
+  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long total = (long long)n_theta * N * n_cases;
+  if (gid >= total) return;
+  const int cse = (int)(gid / ((long long)n_theta * N));
+  const int rem = (int)(gid % ((long long)n_theta * N));
+  const int it = rem / N, m = rem % N;
+  const double d = delta[cse], t = tau[cse];
+  if (isinf(t)) {  // steady state: no time march (K = 0)
+    atomic_max_pos(rho + cse, 0.0);
+    return;
+  }
+  const double th = n_theta > 1 ? 2.0 * M_PI * it / (n_theta - 1) : 0.0;
+  const double mm = mu[m], al = d / t, g = al * al / 2.0;
+  const double cs = cos(th), sn = sin(th);
+  cplx k00, k01, k10, k11;
+  if (mm > 0) {
+    k00 = {mm / 2 + d / 2, 0.0};
+    k01 = {mm * (0.5 - cs), mm * sn};  // mu (1/2 - e^{-i theta})
+    k10 = {-mm / 2, 0.0};
+    k11 = k00;
+  } else {
+    k00 = {-mm / 2 + d / 2, 0.0};
+    k01 = {mm / 2, 0.0};
+    k10 = {mm * (cs - 0.5), mm * sn};  // mu (e^{i theta} - 1/2)
+    k11 = k00;
+  }
+  // Q = K K + al K + g I
+  const cplx q00 = {cmul(k00, k00).x + cmul(k01, k10).x + al * k00.x + g, cmul(k00, k00).y + cmul(k01, k10).y + al * k00.y};
+  const cplx q01 = {cmul(k00, k01).x + cmul(k01, k11).x + al * k01.x, cmul(k00, k01).y + cmul(k01, k11).y + al * k01.y};
+  const cplx q10 = {cmul(k10, k00).x + cmul(k11, k10).x + al * k10.x, cmul(k10, k00).y + cmul(k11, k10).y + al * k10.y};
+  const cplx q11 = {cmul(k10, k01).x + cmul(k11, k11).x + al * k11.x + g, cmul(k10, k01).y + cmul(k11, k11).y + al * k11.y};
+  // K = g Q^{-1} = g / det(Q) [[q11, -q01], [-q10, q00]]
+  const cplx det = {cmul(q00, q11).x - cmul(q01, q10).x, cmul(q00, q11).y - cmul(q01, q10).y};
+  const cplx sc = cdiv({g, 0.0}, det);
+  const cplx a = cmul(sc, q11), b = cmul(sc, {-q01.x, -q01.y}), c = cmul(sc, {-q10.x, -q10.y}), e = cmul(sc, q00);
+  // eigenvalues of [[a, b], [c, e]]: (tr +- sqrt(tr^2 - 4 det)) / 2
+  const cplx tr = {a.x + e.x, a.y + e.y};
+  const cplx dk = {cmul(a, e).x - cmul(b, c).x, cmul(a, e).y - cmul(b, c).y};
+  const cplx disc = csqrt_({cmul(tr, tr).x - 4.0 * dk.x, cmul(tr, tr).y - 4.0 * dk.y});
+  const cplx l1 = {0.5 * (tr.x + disc.x), 0.5 * (tr.y + disc.y)};
+  const cplx l2 = {0.5 * (tr.x - disc.x), 0.5 * (tr.y - disc.y)};
+  const double r = fmax(sqrt(cabs2(l1)), sqrt(cabs2(l2)));
+  atomic_max_pos(rho + cse, isfinite(r) ? r : INFINITY);
+}
+
 bool is_dev(const void *p) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -311,24 +382,30 @@ using namespace oci;
 
 extern "C" int oci_fourier_rho(int32_t kind, int32_t N, int32_t n_cases, const double *delta, const double *tau,
                                const double *c, int32_t n_theta, double *rho, void *stream) {
-  if (kind != OCI_FOURIER_OCI && kind != OCI_FOURIER_SI) return set_error("kind must be OCI or SI"), OCI_E_INVAL;
+  if (kind != OCI_FOURIER_OCI && kind != OCI_FOURIER_SI && kind != OCI_FOURIER_MARCH)
+    return set_error("kind must be OCI_FOURIER_OCI, _SI or _MARCH"), OCI_E_INVAL;
+  const bool march = kind == OCI_FOURIER_MARCH;
   if (N < 2 || N > kMaxFourierN || (N & 1)) return set_error("N must be even, 2 <= N <= 32"), OCI_E_INVAL;
   if (n_cases < 1 || n_theta < 1 || n_cases > 65535)
     return set_error("need 1 <= n_cases <= 65535 and n_theta >= 1"), OCI_E_INVAL;
-  if (!delta || !tau || !c || !rho) return set_error("delta, tau, c and rho must be given"), OCI_E_INVAL;
+  if (march && ((long long)n_theta * N * n_cases + 255) / 256 > 2147483647LL)
+    return set_error("n_theta * N * n_cases too large for one launch"), OCI_E_INVAL;
+  if (!delta || !tau || (!c && !march) || !rho) return set_error("delta, tau, c and rho must be given"), OCI_E_INVAL;
   const bool dev_in = is_dev(delta);
-  if (dev_in != is_dev(tau) || dev_in != is_dev(c)) return set_error("delta, tau, c: all host or all device"), OCI_E_INVAL;
+  if (dev_in != is_dev(tau) || (c && dev_in != is_dev(c)))
+    return set_error("delta, tau, c: all host or all device"), OCI_E_INVAL;
   std::vector<double> hd(n_cases), ht(n_cases), hc(n_cases);
   cudaStream_t st = (cudaStream_t)stream;
   if (dev_in) {
     cudaMemcpy(hd.data(), delta, n_cases * 8, cudaMemcpyDeviceToHost);
     cudaMemcpy(ht.data(), tau, n_cases * 8, cudaMemcpyDeviceToHost);
-    cudaMemcpy(hc.data(), c, n_cases * 8, cudaMemcpyDeviceToHost);
+    if (c) cudaMemcpy(hc.data(), c, n_cases * 8, cudaMemcpyDeviceToHost);
   } else {
     hd.assign(delta, delta + n_cases);
     ht.assign(tau, tau + n_cases);
-    hc.assign(c, c + n_cases);
+    if (c) hc.assign(c, c + n_cases);
   }
+  if (march) hc.assign(n_cases, 0.0);  // the time-march model problem has no scattering
   for (int i = 0; i < n_cases; i++)
     if (!(hd[i] > 0.0) || !isfinite(hd[i]) || !(ht[i] > 0.0) || !(hc[i] >= 0.0) || !isfinite(hc[i]))
       return set_error("each case needs delta > 0 finite, tau > 0 (inf: steady state), c >= 0"), OCI_E_INVAL;
@@ -360,8 +437,12 @@ extern "C" int oci_fourier_rho(int32_t kind, int32_t N, int32_t n_cases, const d
           cudaSuccess)
         break;
       k_fourier_rho_oci<<<dim3(n_theta, n_cases), 256, sm2, st>>>(N, n_theta, d_mu, d_C0, d_rho);
-    } else {
+    } else if (kind == OCI_FOURIER_SI) {
       k_fourier_rho_si<<<dim3(n_theta, n_cases), 32, 0, st>>>(N, n_theta, d_mu, d_w, d_del, d_tau, d_c, d_rho);
+    } else {
+      const long long total = (long long)n_theta * N * n_cases;
+      k_fourier_rho_march<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(N, n_theta, n_cases, d_mu, d_del, d_tau,
+                                                                           d_rho);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) break;
     if ((e = cudaMemcpyAsync(rho, d_rho, n_cases * 8, cudaMemcpyDefault, st)) != cudaSuccess) break;

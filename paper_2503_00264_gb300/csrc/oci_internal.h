@@ -11,6 +11,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdlib.h>
 
 #include <string>
 #include <vector>
@@ -23,6 +24,21 @@ constexpr int kMaxN = 128;
 constexpr int kMaxG = 16;
 constexpr int kMaxUnknowns = 2048;      // 4*N*G per cell
 constexpr int kFinalizeThreads = 512;
+
+// Test and profiling overrides.  liboci reads its OCI_* environment variables
+// (a pinned kernel or launch shape, no graph, the autotuner off, a short
+// device spin limit, ...) only when OCI_TEST_HOOKS=1 is set as well; otherwise
+// every override is ignored, so a caller's environment cannot change which
+// code runs.  The variables are listed in include/oci.h.
+inline const char *hook_env(const char *name) {
+  const char *on = getenv("OCI_TEST_HOOKS");
+  if (!on || on[0] != '1' || on[1] != 0) return nullptr;
+  return getenv(name);
+}
+
+// Iterations of the bounded grid-barrier spin of the cooperative multi-sweep
+// kernels (each iteration sleeps ~64 ns); OCI_TEST_SPIN_LIMIT lowers it.
+constexpr long long kGridSpin = 1 << 21;
 
 // Device-resident iteration state of one handle.
 struct DevState {
@@ -45,6 +61,7 @@ struct DevState {
   double e_blk0;
   int inplace;    // 1: the sweep updates Psi[cur] in place (red-black ordering)
   unsigned long long cond_ref;  // mixed forms in a graph: handle of the IF node of the refinement
+  long long spin;               // grid-barrier spin limit of the cooperative kernels (kGridSpin)
 };
 
 // Per-cell-type tables of the structured solve (all FP64, device).

@@ -821,7 +821,7 @@ __global__ void __launch_bounds__(256) k_mx_inner_ms(int J, int N, int G, int n_
     double *part = partials + (size_t)(sw & 1) * gridDim.x;
     if (tid == 0) {
       part[blockIdx.x] = bs;
-      s_ok = grid_barrier(gbar, gridDim.x);
+      s_ok = grid_barrier(gbar, gridDim.x, sd.spin);
     }
     __syncthreads();
     if (!s_ok) {
@@ -854,7 +854,7 @@ static int ms_grid(const Handle &h, int P, size_t smem) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mx_inner_ms<T, NP>, T * h.G * P, smem);
   const int ntiles = (h.J + T - 1) / T;
-  const int grid = sms * (per > 0 ? per : 1);
+  const int grid = sms * per;
   return grid < ntiles ? grid : ntiles;
 }
 
@@ -884,7 +884,7 @@ static int tp_grid(const Handle &h, int P, size_t smem) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mx_inner_tp<T, NP>, T * h.G * P, smem);
   const int ntiles = (h.J + T - 1) / T;
-  const int grid = sms * (per > 0 ? per : 1);
+  const int grid = sms * per;
   return grid < ntiles ? grid : ntiles;
 }
 
@@ -1123,7 +1123,7 @@ static int tb_grid(const Handle &h, int P, size_t smem) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mx_inner_tb<T, NP>, T * h.G * P, smem);
   const int ntiles = (h.J + T - 1) / T;
-  const int grid = sms * (per > 0 ? per : 1);
+  const int grid = sms * per;
   return grid < ntiles ? grid : ntiles;
 }
 
@@ -1290,7 +1290,7 @@ __global__ void __launch_bounds__(256) k_mx_rb(int J, int N, int G, int n_types,
         e2 += rb_tile<T, NP>(tile, color, J, N, G, cl, gy, zero, type, Linv, Cin, Mp, w, z, D, y_s, yr_s, s_s);
       if (color == 0) {  // every red cell is written before any black cell reads it
         __syncthreads();
-        if (tid == 0) s_ok = grid_barrier(gbar, gridDim.x);
+        if (tid == 0) s_ok = grid_barrier(gbar, gridDim.x, sd.spin);
         __syncthreads();
         if (!s_ok) failed = true;
       }
@@ -1300,7 +1300,7 @@ __global__ void __launch_bounds__(256) k_mx_rb(int J, int N, int G, int n_types,
     double *part = partials + (size_t)(sw & 1) * gridDim.x;
     if (tid == 0) {
       part[blockIdx.x] = bs;
-      s_ok = grid_barrier(gbar, gridDim.x);
+      s_ok = grid_barrier(gbar, gridDim.x, sd.spin);
     }
     __syncthreads();
     if (!s_ok) {
@@ -1335,7 +1335,7 @@ static void launch_rb(Handle &h, int P, cudaGraphConditionalHandle cond, int use
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mx_rb<T, NP>, (T / 2) * h.G * P, smem);
   const int ntiles = (h.J + T - 1) / T;
-  int grid = sms * (per > 0 ? per : 1);
+  int grid = sms * per;
   if (grid > ntiles) grid = ntiles;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
@@ -1766,7 +1766,7 @@ int mx_partials(const Handle &h) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mx_inner_tma, kTmaCells * h.G * h.mx_P,
                                                   mx_tma_smem(h, h.mx_P));
     const int ntiles = (h.J + kTmaCells - 1) / kTmaCells;
-    const int grid = sms * (per > 0 ? per : 1);
+    const int grid = sms * per;
     return grid < ntiles ? grid : ntiles;
   }
   int cb, P;
@@ -1914,7 +1914,7 @@ void launch_mx_inner(Handle &h, cudaGraphConditionalHandle cond, int use_cond) {
     const size_t smem = mx_tma_smem(h, P);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mx_inner_tma, kTmaCells * h.G * P, smem);
     const int ntiles = (h.J + kTmaCells - 1) / kTmaCells;
-    int grid = sms * (per > 0 ? per : 1);
+    int grid = sms * per;
     if (grid > ntiles) grid = ntiles;
     k_mx_inner_tma<<<grid, dim3(kTmaCells, h.G * P), smem, h.stream>>>(
         h.tm_z, h.tm_d[0], h.tm_d[1], h.J, h.Jp, h.N, h.G, P, h.type, h.tt.Linv32, h.tt.Cin32, h.tt.Mp32, h.w32,

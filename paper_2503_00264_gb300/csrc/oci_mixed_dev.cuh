@@ -42,11 +42,10 @@ __device__ __forceinline__ double block_reduce_fixed(float e2, double *red, int 
   return bs;
 }
 
-// Grid barrier of the multi-sweep cooperative kernels; the spin is bounded.
-constexpr long long kGridSpin = 1 << 21;
-
 // Sense-reversing grid barrier on {count, generation}; thread 0 of every block.
-__device__ __forceinline__ bool grid_barrier(unsigned *gbar, unsigned nblocks) {
+// The spin is bounded by `limit` iterations (the device state's spin field,
+// kGridSpin unless a test lowers it); false when it gave up.
+__device__ __forceinline__ bool grid_barrier(unsigned *gbar, unsigned nblocks, long long limit) {
   volatile unsigned *vgen = gbar + 1;
   const unsigned g0 = *vgen;  // cannot advance before this block arrives
   __threadfence();
@@ -57,7 +56,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned *gbar, unsigned nblocks) {
     atomicAdd(gbar + 1, 1u);
     return true;
   }
-  for (long long k = 0; k < kGridSpin; k++) {
+  for (long long k = 0; k < limit; k++) {
     if (*vgen != g0) {
       __threadfence();
       return true;

@@ -373,7 +373,7 @@ __global__ void __launch_bounds__(Rb2Bounds<T, PS, GS>::thr, Rb2Bounds<T, PS, GS
     if (tid == 0) {
       part[blockIdx.x] = ba;
       part[gridDim.x + blockIdx.x] = bb;
-      s_ok = grid_barrier(gbar, gridDim.x);
+      s_ok = grid_barrier(gbar, gridDim.x, sd.spin);
     }
     __syncthreads();
     if (!s_ok) {
@@ -432,7 +432,7 @@ static void launch_rb2(Handle &h, int P, cudaGraphConditionalHandle cond, int us
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mx_rb2<T, NP, PS, GS>, (T / 2) * h.G * P, smem);
   const int ntiles = (h.J + T - 1) / T;
-  const int grid = std::min(sms * (per > 0 ? per : 1), ntiles);
+  const int grid = std::min(sms * per, ntiles);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(T / 2, h.G * P);

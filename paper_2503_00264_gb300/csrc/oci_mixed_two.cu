@@ -218,7 +218,7 @@ __global__ void __launch_bounds__((PS && GS) ? T * PS * GS : 256, OCC)
     if (tid == 0) {
       part[blockIdx.x] = ba;
       part[gridDim.x + blockIdx.x] = bb;
-      s_ok = grid_barrier(gbar, gridDim.x);
+      s_ok = grid_barrier(gbar, gridDim.x, sd.spin);
     }
     __syncthreads();
     if (!s_ok) {
@@ -277,7 +277,7 @@ static void launch_ms2(Handle &h, int P, cudaGraphConditionalHandle cond, int us
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mx_inner_ms2<T, NP, PS, GS, OCC>, T * h.G * P, smem);
   const int ntiles = (h.J + T - 1) / T;
-  const int grid = std::min(sms * (per > 0 ? per : 1), ntiles);
+  const int grid = std::min(sms * per, ntiles);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(T, h.G * P);

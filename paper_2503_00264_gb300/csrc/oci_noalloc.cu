@@ -15,7 +15,9 @@
 //
 // In host code the array's name does not denote a device address; its device
 // address is obtained once per device with cudaGetSymbolAddress (on the first
-// call made with that device current) and passed to the kernels.
+// call made with that device current) and passed to the kernels.  The cached
+// address belongs to the device's primary context: after cudaDeviceReset the
+// entry point must not be called again in that process.
 #include <math.h>
 
 #include <mutex>

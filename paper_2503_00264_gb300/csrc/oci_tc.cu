@@ -32,6 +32,19 @@ constexpr int kTcN = 128;   // MMA N (cells per tile)
 constexpr int kTcCols = 128;  // TMEM columns allocated (FP32 accumulator, N columns)
 constexpr long long kTcSpin = 1 << 22;
 
+// Bounded wait for phase `parity` of an mbarrier in shared memory.
+__device__ __forceinline__ bool tc_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok = 0;
+  for (long long it = 0; it < kTcSpin && !ok; it++) {
+    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(ok)
+                 : "r"(bar), "r"(parity)
+                 : "memory");
+    if (!ok) __nanosleep(32);
+  }
+  return ok != 0;
+}
+
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ uint64_t tc_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
@@ -187,6 +200,9 @@ __global__ void __launch_bounds__(128) k_tc_inner(int J, int Jp, int N, int G, c
         for (int i = 0; i < 32; i++) Dt[row * (kTcN + 1) + c0 + i] = __uint_as_float(r[i]);
     }
   } else if (t == 0) {
+    // one more bounded wait: the MMA issued above may still read the operand
+    // images and write the accumulator that is freed below
+    tc_wait(smem_u32(&mbar), 0);
     atomicExch(&ds->status, OCI_E_TIMEOUT);
     ds->done = 1;
   }
@@ -255,17 +271,6 @@ void launch_tc_inner(Handle &h) {
 // OCI_E_TIMEOUT.
 constexpr int kTcPipeThreads = 256;
 
-__device__ __forceinline__ bool tc_wait(uint32_t bar, uint32_t parity) {
-  uint32_t ok = 0;
-  for (long long it = 0; it < kTcSpin && !ok; it++) {
-    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
-                 : "=r"(ok)
-                 : "r"(bar), "r"(parity)
-                 : "memory");
-    if (!ok) __nanosleep(32);
-  }
-  return ok != 0;
-}
 
 // KB rows k0..k0+KB-1 of one cell's RHS r + B delta (FP32), written into the
 // K-major operand image (TF32, or BF16 hi/lo); all loads first.
@@ -523,7 +528,7 @@ size_t tc_pipe_smem(const Handle &h) {
 }
 
 bool tc_pipe_ok(const Handle &h) {
-  const char *e = getenv("OCI_TC_PIPE");  // 0: the one-tile-per-CTA kernel
+  const char *e = hook_env("OCI_TC_PIPE");  // 0: the one-tile-per-CTA kernel
   if (e && e[0] == '0') return false;
   return tc_pipe_smem(h) <= 220 * 1024;
 }

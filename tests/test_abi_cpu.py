@@ -127,7 +127,8 @@ def test_fourier_tool_validates_before_device_work(lib):
     d = np.array([0.1]); t = np.array([0.1]); c = np.array([0.9]); out = np.zeros(1)
     args = lambda **k: (k.get("kind", 0), k.get("N", 8), k.get("n", 1), oci._ptr(d), oci._ptr(t), oci._ptr(c),
                         k.get("nt", 10), oci._ptr(out, writable=True), None)
-    assert lib.oci_fourier_rho(*args(kind=2)) == oci.E_INVAL
+    assert lib.oci_fourier_rho(*args(kind=3)) == oci.E_INVAL
+    assert lib.oci_fourier_rho(*args(kind=-1)) == oci.E_INVAL
     assert lib.oci_fourier_rho(*args(N=3)) == oci.E_INVAL
     assert lib.oci_fourier_rho(*args(N=34)) == oci.E_INVAL
     assert lib.oci_fourier_rho(*args(n=0)) == oci.E_INVAL

@@ -3,8 +3,9 @@
 It is meant for callers that cannot allocate device memory at the moment they
 need the convergence norm; its partial sums live in a fixed device array.  This
 test calls it through the C ABI on two sweeps in a row and checks each result
-against the norm the regular path (oci_iterate) reports for the same sweep, so
-stale contents of the shared scratch array would show up on the second call."""
+against the norm the regular path (oci_iterate) reports for the same sweep and
+against numpy's norm of the host copies, so stale contents of the shared
+scratch array would show up on the second call."""
 import ctypes
 
 import numpy as np
@@ -46,6 +47,9 @@ def test_noalloc_norm_matches_regular_path_twice():
     got = out.cpu().numpy()
     for k in range(2):
         assert abs(got[k] - refs[k]) <= 1e-12 * refs[k], (k, got[k], refs[k])
+        # and against numpy's norm of the host copies of the same arrays
+        host = float(np.linalg.norm((psis[k + 1] - psis[k]).ravel()))
+        assert abs(got[k] - host) <= 1e-12 * host, (k, got[k], host)
     assert got[0] != got[1]
 
 
