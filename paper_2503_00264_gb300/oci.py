@@ -135,17 +135,18 @@ def _ptr(x, dtype=np.float64, writable=False):
     return x.ctypes.data
 
 
-FOURIER_OCI, FOURIER_SI = 0, 1
+FOURIER_OCI, FOURIER_SI, FOURIER_MARCH = 0, 1, 2
 ACCEL_NONE, ACCEL_GMRES = 0, 1
 
 
 def fourier_rho(kind: int, N: int, delta, tau, c, n_theta: int = 250, stream=None) -> np.ndarray:
-    """Fourier spectral radius of the OCI or SI iteration (oci_fourier_rho) for the
-    model problems (delta[i], tau[i], c[i]): max over n_theta wave numbers."""
+    """Fourier spectral radius of the OCI or SI iteration, or the largest
+    time-march amplification (oci_fourier_rho), for the model problems
+    (delta[i], tau[i], c[i]): max over n_theta wave numbers."""
     L = load()
     d = np.ascontiguousarray(np.atleast_1d(delta), np.float64)
     t = np.ascontiguousarray(np.broadcast_to(np.atleast_1d(tau), d.shape), np.float64)
-    cc = np.ascontiguousarray(np.broadcast_to(np.atleast_1d(c), d.shape), np.float64)
+    cc = None if c is None else np.ascontiguousarray(np.broadcast_to(np.atleast_1d(c), d.shape), np.float64)
     out = np.zeros(d.shape)
     _check(L.oci_fourier_rho(int(kind), int(N), int(d.size), _ptr(d), _ptr(t), _ptr(cc), int(n_theta),
                              _ptr(out, writable=True), stream))
