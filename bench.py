@@ -9,6 +9,20 @@ device, carry / scalar flux / balance.  Metric: cell-unknown updates per second
 
 --impl reference times the CPU FP64 oracle on a bounded sample of the same
 workload (the host cores of this machine).
+
+Subcommands (measurement tools around the same library; no JSON contract line):
+  python bench.py profile --case slab3 --sweeps 3 [--precision fp32] [--ordering rb]
+                          [--steps N] [--si] [--solver dense] [--J J]
+  python bench.py profile --case batch --slabs 64 --ng 32,4
+      one small case for a profiler: set up, run exactly --sweeps sweeps from a
+      seeded random iterate (or --steps time steps, or one batched step) and exit
+  python bench.py grid [--steps 2] [--json out.json]
+      the 2^18-cell slab over c in {0.5, 0.9, 0.99} x tau in {0.01, 0.1, 1, 10}:
+      OCI (FP64 Jacobi and red-black, red-black FP32_IR) against SI (scan form)
+  python bench.py table2 [--json out.json]
+      the paper's GPU experiment (Sec. 3.2, Table 2): OCI and SI seconds per
+      converged step over delta_2 x S_N x dt (also in the default run's
+      "table2" key)
 """
 from __future__ import annotations
 
@@ -62,6 +76,7 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-design-cmp", action="store_true")
     ap.add_argument("--no-fourier", action="store_true")
+    ap.add_argument("--no-table2", action="store_true")
     ap.add_argument("--batch-max-iter", type=int, default=600)
     return ap.parse_args()
 
@@ -128,25 +143,42 @@ class Clocks:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(args, budget_s=12.0, steps=None):
-    """The oracle as it stands on the host cores, on the first SAMPLE_J cells of
-    the workload (3 regions of 1024 cells)."""
+def _oracle_step_times(p, n, threads):
+    """Times (s) and sweeps of n consecutive oracle time steps at `threads` OpenMP threads."""
     import oracle
-    p = workload(args, SAMPLE_J)
+    oracle.set_threads(threads)
     o = oracle.Oracle(p)
-    done_steps, upd, t_tot = 0, 0, 0.0
-    while True:
+    out = []
+    for _ in range(n):
         t0 = time.perf_counter()
         r = o.step()
-        t_tot += time.perf_counter() - t0
-        upd += p.unknowns * r["iters"]
-        done_steps += 1
-        if (steps is not None and done_steps >= steps) or (steps is None and t_tot >= budget_s):
-            break
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": upd / t_tot, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{SAMPLE_J} cells (3 regions of 1024) of the same slab, {done_steps} time steps, "
-                      f"{t_tot:.1f} s of convergence loops"}
+        out.append((time.perf_counter() - t0, r["iters"]))
+    return out
+
+
+def cpu_baseline(args):
+    """The oracle as it stands on the host cores, on the first SAMPLE_J cells of
+    the workload (3 regions of 1024 cells): the median of 5 time steps on all
+    cores (the reported value) and the median of 3 on one core.  Each step is
+    timed from the same state sequence the GPU run starts from (zero initial
+    flux); the median step's rate is reported."""
+    import oracle
+    p = workload(args, SAMPLE_J)
+    cores = os.cpu_count() or 1
+    allc = _oracle_step_times(p, 5, cores)
+    used = oracle.get_threads()
+    one = _oracle_step_times(p, 3, 1)
+    oracle.set_threads(cores)
+
+    def med(rows):
+        rates = sorted(p.unknowns * it / t for t, it in rows)
+        return rates[len(rates) // 2]
+
+    return {"value": med(allc), "unit": UNIT, "cores": used, "kind": "oracle",
+            "one_thread": {"value": med(one), "unit": UNIT, "cores": 1, "steps": len(one)},
+            "sample": f"{SAMPLE_J} cells (3 regions of 1024) of the same slab; median over 5 time steps "
+                      f"(all {used} threads; {sum(t for t, _ in allc):.1f} s) and over 3 (one thread; "
+                      f"{sum(t for t, _ in one):.1f} s) of the convergence loop"}
 
 
 def run_reference(args):
@@ -165,11 +197,12 @@ def run_reference(args):
         t_tot += time.perf_counter() - t0
         upd += p.unknowns * r["iters"]
     v = upd / t_tot
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    cores = oracle.get_threads()
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_tot / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config(args, workload(args)),
+            "config": dict(config(args, workload(args)), sample_cells=SAMPLE_J,
+                           sample=f"each timed step runs the first {SAMPLE_J} cells (3 regions of 1024)"),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"{SAMPLE_J} cells of the same slab per step"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -230,6 +263,17 @@ def run_ours(args):
     ms = max_over_ranks(e0.elapsed_time(e1))
     total_sweeps = sweeps * world  # replicas: every rank does the same work
     value = p.unknowns * total_sweeps / (ms * 1e-3)
+
+    n_sw = 50
+    psi_keep = s.psi()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    f0.record(stream)
+    s.iterate(n_sw)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    sweep_ms_iter = f0.elapsed_time(f1) / n_sw
+    s.set_psi(psi_keep)
 
     mixed = None
     if smx is not None:
@@ -361,6 +405,17 @@ def run_ours(args):
         fourier["table1_grid_c1_s8"] = {"tau": [0.01, 0.1, 1.0, 10.0, "inf"], "delta": [0.01, 0.1, 1.0, 10.0],
                                         "rho_oci": rho_grid.reshape(tg.shape).tolist(), "n_theta": 1001,
                                         "seconds": time.perf_counter() - w0}
+        # time-march stability map of Sec. 2.2 (Fig. 3's axes: mean free time x cell
+        # optical thickness, S16, 75 wave numbers): max |lambda_K| must not exceed 1
+        taus_k, dels_k = np.logspace(-3, 3, 25), np.logspace(-3, 2, 21)
+        tk, dk = np.meshgrid(taus_k, dels_k, indexing="ij")
+        w0 = time.perf_counter()
+        lam = oci.fourier_rho(oci.FOURIER_MARCH, 16, dk.ravel(), tk.ravel(), None, 75, stream.cuda_stream)
+        fourier["time_march_s16"] = {"tau": taus_k.tolist(), "delta": dels_k.tolist(), "n_theta": 75,
+                                     "max_abs_lambda_K": lam.reshape(tk.shape).tolist(),
+                                     "sup_abs_lambda_K": float(lam.max()),
+                                     "unconditionally_stable": bool(lam.max() <= 1.0 + 1e-12),
+                                     "seconds": time.perf_counter() - w0}
 
     # multigroup slab (G = 8, S16, 2^16 cells): FP64 and the FP32-inner mixed form
     multigroup = None
@@ -418,21 +473,16 @@ def run_ours(args):
                         (np.abs(bs.phi(i) - phi_b[i]).max() / np.abs(phi_b[i]).max() for i in both), default=0.0))
                 batched[name] = ent
 
+    # the paper's GPU experiment (Sec. 3.2, Table 2): one converged step of the
+    # two-group problem over delta_2 x S_N x dt, OCI (FP64, FP32_IR) against SI
+    table2 = None if args.no_table2 else table2_rows(stream)
+
     # dominant kernel: the fused sweep.  Its average launch duration over the timed
     # region = device time of the K steps / sweeps (an upper bound: includes the
-    # per-step constant, carry and balance kernels, < 1 %); cross-checked by a run
-    # of n sweeps through oci_iterate
-    n_sw = 50
-    psi_keep = s.psi()
-    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    barrier()
-    f0.record(stream)
-    s.iterate(n_sw)
-    f1.record(stream)
-    torch.cuda.synchronize()
-    sweep_ms_iter = f0.elapsed_time(f1) / n_sw
+    # per-step constant, carry and balance kernels, < 1 %); cross-checked right
+    # after the timed region by n sweeps through oci_iterate (host-launched, so
+    # each sweep also waits for the finalize of its predecessor's launch slot)
     sweep_ms = ms / sweeps
-    s.set_psi(psi_keep)
     NG = p.N * p.G
     flops_cell = 68 * NG + 32 * p.G * p.G
     bytes_cell = 96 * NG + 4
@@ -502,7 +552,8 @@ def run_ours(args):
             "multigroup": multigroup,
             "batched_form": batched,
             "paper_scheme_comparison": design_cmp,
-            "fourier": fourier}
+            "fourier": fourier,
+            "table2": table2}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args)
     if rank == 0:
@@ -512,9 +563,204 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-if __name__ == "__main__":
-    a = parse()
-    if a.impl == "reference":
-        run_reference(a)
+# ---------------------------------------------------------------- table 2 (Sec. 3.2)
+TABLE2_DELTAS = (0.05, 0.1, 0.25, 0.5, 1.0, 2.0, 4.0, 8.0)
+
+
+def _one_step_ms(p, stream, si=False, precision=None):
+    """Device time (CUDA events) of one converged step from the problem's initial
+    state, after a warm step from the same state (graphs built, memory touched)."""
+    import torch
+
+    from paper_2503_00264_gb300 import oci
+    kw = {} if precision is None else {"precision": precision}
+    with oci.Solver(p, stream=stream.cuda_stream, **kw) as s:
+        pp0, t0 = s.state()
+        zero = np.zeros((p.J, p.G, p.N, 4))
+        step = s.si_step if si else s.step
+        step(allow_noconv=True)
+        s.set_state(pp0, t0)
+        s.set_psi(zero)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = step(allow_noconv=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return {"ms": e0.elapsed_time(e1), "sweeps": st["iters"], "status": st["status"]}
+
+
+def table2_rows(stream, tol=1e-10, max_iter=200000, verbose=False):
+    from paper_2503_00264_gb300 import oci
+    rows = []
+    for dt in (10.0, 0.1):
+        for N in (16, 32):
+            if verbose:
+                print(f"\n### dt = {dt} (tau_2 = {0.45468 * 0.5 * dt:.4g}), S{N}\n")
+                print("| delta_2 | J | OCI sweeps | OCI ms | OCI-FP32IR ms | SI sweeps | SI ms | SI/OCI | SI/OCI-FP32IR |")
+                print("|---|---|---|---|---|---|---|---|---|")
+            for d in TABLE2_DELTAS:
+                p = W.rosa_two_group(d, N, dt).replace(tol=tol, max_iter=max_iter)
+                o = _one_step_ms(p, stream)
+                m = _one_step_ms(p, stream, precision=oci.FP32_IR)
+                si = _one_step_ms(p, stream, si=True)
+                row = {"dt": dt, "N": N, "delta2": d, "J": p.J, "oci_fp64": o, "oci_fp32ir": m, "si_fp64": si,
+                       "si_over_oci": si["ms"] / o["ms"], "si_over_oci_fp32ir": si["ms"] / m["ms"]}
+                rows.append(row)
+                if verbose:
+                    print(f"| {d} | {p.J} | {o['sweeps']} | {o['ms']:.2f} | {m['ms']:.2f} | {si['sweeps']} | "
+                          f"{si['ms']:.2f} | {row['si_over_oci']:.2f} | {row['si_over_oci_fp32ir']:.2f} |", flush=True)
+    return rows
+
+
+def cmd_table2(argv):
+    import torch
+    ap = argparse.ArgumentParser(prog="bench.py table2")
+    ap.add_argument("--tol", type=float, default=1e-10)
+    ap.add_argument("--max-iter", type=int, default=200000)
+    ap.add_argument("--json", default=None)
+    a = ap.parse_args(argv)
+    rows = table2_rows(torch.cuda.Stream(), a.tol, a.max_iter, verbose=True)
+    if a.json:
+        with open(a.json, "w") as f:
+            json.dump(rows, f, indent=1)
+
+
+# ---------------------------------------------------------------- c x tau grid of the 2^18-cell slab
+def cmd_grid(argv):
+    import torch
+
+    from paper_2503_00264_gb300 import oci
+    ap = argparse.ArgumentParser(prog="bench.py grid")
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--J", type=int, default=2 ** 18)
+    ap.add_argument("--json", default=None)
+    a = ap.parse_args(argv)
+    stream = torch.cuda.Stream()
+
+    def timed(p, si=False, precision=oci.FP64, red_black=False, scan=False):
+        with oci.Solver(p, precision=precision, stream=stream.cuda_stream) as s:
+            if red_black:
+                s.set_ordering(oci.ORDER_RED_BLACK)
+            if scan:
+                s.set_si_mode(oci.SI_SCAN)
+            step = s.si_step if si else s.step
+            step(allow_noconv=True)  # warm step
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            sweeps, rho, ok = 0, 0.0, True
+            e0.record(stream)
+            for _ in range(a.steps):
+                st = step(allow_noconv=True)
+                sweeps += st["iters"]
+                rho = st["rho"]
+                ok &= st["status"] == 0
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return {"ms_per_step": e0.elapsed_time(e1) / a.steps, "sweeps_per_step": sweeps / a.steps,
+                    "rho_e": rho, "converged": ok}
+
+    rows = []
+    print("| c | tau | rho OCI / SI (Fourier, max over regions) | OCI FP64 sweeps / ms | final rho_e | "
+          "red-black FP64 sweeps / ms | red-black FP32_IR sweeps / ms | SI sweeps / scan ms | "
+          "SI scan / best FP64 OCI | SI scan / best OCI |")
+    print("|---|---|---|---|---|---|---|---|---|---|")
+    deltas = np.array(W.SLAB3_DELTAS)
+    for c in W.SLAB3_C:
+        for tau in W.SLAB3_TAU:
+            p = W.slab_3region(c=c, tau=tau, J=a.J)
+            r_oci = float(oci.fourier_rho(oci.FOURIER_OCI, p.N, deltas, tau, c, 250).max())
+            r_si = float(oci.fourier_rho(oci.FOURIER_SI, p.N, deltas, tau, c, 250).max())
+            jac = timed(p)
+            rb = timed(p, red_black=True)
+            rbm = timed(p, precision=oci.FP32_IR, red_black=True)
+            si = timed(p, si=True, scan=True)
+            best64 = min(jac["ms_per_step"], rb["ms_per_step"])
+            best = min(best64, rbm["ms_per_step"])
+            row = {"c": c, "tau": tau, "rho_oci": r_oci, "rho_si": r_si, "oci_fp64": jac, "oci_rb_fp64": rb,
+                   "oci_rb_fp32ir": rbm, "si_scan": si, "si_over_best_fp64_oci": si["ms_per_step"] / best64,
+                   "si_over_best_oci": si["ms_per_step"] / best}
+            rows.append(row)
+            print(f"| {c} | {tau} | {r_oci:.3f} / {r_si:.3f} | {jac['sweeps_per_step']:.0f} / "
+                  f"{jac['ms_per_step']:.1f} | {jac['rho_e']:.3f} | {rb['sweeps_per_step']:.0f} / "
+                  f"{rb['ms_per_step']:.1f} | {rbm['sweeps_per_step']:.0f} / {rbm['ms_per_step']:.2f} | "
+                  f"{si['sweeps_per_step']:.0f} / {si['ms_per_step']:.2f} | {row['si_over_best_fp64_oci']:.2f} | "
+                  f"{row['si_over_best_oci']:.2f} |", flush=True)
+    if a.json:
+        with open(a.json, "w") as f:
+            json.dump(rows, f, indent=1)
+
+
+# ---------------------------------------------------------------- one small case for a profiler
+def cmd_profile(argv):
+    import torch
+
+    from paper_2503_00264_gb300 import oci
+    ap = argparse.ArgumentParser(prog="bench.py profile")
+    ap.add_argument("--case", default="slab3", choices=["slab3", "slab3_ragged", "multigroup", "batch"])
+    ap.add_argument("--J", type=int, default=None)
+    ap.add_argument("--sweeps", type=int, default=3)
+    ap.add_argument("--solver", default="structured", choices=["structured", "dense"])
+    ap.add_argument("--si", action="store_true")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "tf32", "bf16x3"])
+    ap.add_argument("--steps", type=int, default=0, help="run full time steps instead of --sweeps sweeps")
+    ap.add_argument("--slabs", type=int, default=64, help="batch: slabs drawn before the --ng filter")
+    ap.add_argument("--ng", default=None, help="batch: keep only slabs of this N,G")
+    ap.add_argument("--batch-max-iter", type=int, default=200)
+    ap.add_argument("--j-hi", type=int, default=8192, help="batch: largest slab (cells)")
+    ap.add_argument("--ordering", default="jacobi", choices=["jacobi", "rb"], help="cell ordering of the sweeps")
+    a = ap.parse_args(argv)
+    prec = {"fp64": oci.FP64, "fp32": oci.FP32_IR, "tf32": oci.TF32_IR, "bf16x3": oci.BF16X3_IR}[a.precision]
+    stream = torch.cuda.Stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if a.case == "batch":
+        probs = [b.replace(max_iter=a.batch_max_iter) for b in W.batch_of_slabs(a.slabs, j_lo=1024, j_hi=a.j_hi)]
+        if a.ng:
+            n_, g_ = (int(x) for x in a.ng.split(","))
+            probs = [b for b in probs if (b.N, b.G) == (n_, g_)]
+        with oci.BatchSolver(probs, stream=stream.cuda_stream, precision=prec) as bs:
+            e0.record(stream)
+            sts = bs.step(allow_noconv=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            its = [st["iters"] for st in sts]
+            upd = sum(b.unknowns * k for b, k in zip(probs, its))
+            ms_b = e0.elapsed_time(e1)
+            print(f"batch of {len(probs)} slabs ({sum(b.J for b in probs)} cells): sweeps {min(its)}..{max(its)}, "
+                  f"{ms_b:.2f} ms, {upd / ms_b / 1e6:.1f} G updates/s")
+        return
+    if a.case == "slab3":
+        p = W.slab_3region(c=0.9, tau=0.1, J=a.J or 2 ** 18)
+    elif a.case == "slab3_ragged":
+        p = W.slab_3region(c=0.9, tau=0.1, J=a.J or 2 ** 16, ragged=True)
     else:
-        run_ours(a)
+        p = W.slab_multigroup(J=a.J or 2 ** 16)
+    solver = oci.SOLVER_DENSE_LU if a.solver == "dense" else oci.SOLVER_STRUCTURED
+    with oci.Solver(p, solver=solver, precision=prec, stream=stream.cuda_stream) as s:
+        if a.ordering == "rb":
+            s.set_ordering(oci.ORDER_RED_BLACK)
+        print("setup:", s.info())
+        if a.steps:
+            e0.record(stream)
+            its = sum((s.si_step if a.si else s.step)()["iters"] for _ in range(a.steps))
+            e1.record(stream)
+            torch.cuda.synchronize()
+            print(f"{p.name}: {a.steps} steps, {its} sweeps, {e0.elapsed_time(e1) / a.steps:.2f} ms/step")
+            return
+        s.set_psi(W.random_guess(p, 1))
+        e0.record(stream)
+        (s.si_iterate if a.si else s.iterate)(a.sweeps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        print(f"{p.name}: {a.sweeps} {'SI' if a.si else 'OCI'} sweeps, "
+              f"{e0.elapsed_time(e1) / a.sweeps * 1e3:.1f} us/sweep")
+
+
+if __name__ == "__main__":
+    sub = {"profile": cmd_profile, "grid": cmd_grid, "table2": cmd_table2}
+    if len(sys.argv) > 1 and sys.argv[1] in sub:
+        sub[sys.argv[1]](sys.argv[2:])
+    else:
+        a = parse()
+        if a.impl == "reference":
+            run_reference(a)
+        else:
+            run_ours(a)
