@@ -139,8 +139,9 @@ struct Handle {
   double *si_segin = nullptr;    // [G*N][K][2]     scan form: incoming edge of each segment
   int si_mode = 0;               // 0 sequential chain (the paper's SI), 1 scan form
   // dense path
-  double *LU = nullptr;          // [J][n][n] column-major per cell
-  int32_t *piv = nullptr;        // [J][n]
+  double *LU = nullptr;          // [J][n][n] column-major per cell: A_j^{-1} (dense_inv) or its LU factors
+  int32_t *piv = nullptr;        // [J][n] (LU factors only)
+  int dense_inv = 1;             // 1: apply the explicit inverse; 0: triangular solves with the LU factors
   // reductions
   double *partials = nullptr;    // [max blocks]
   unsigned *counter = nullptr;   // blocks finished in the current sweep launch (last block resets it)

@@ -52,6 +52,15 @@ def test_oci_dense_lu_matches_oracle(seed, J, N, G):
 
 
 @pytest.mark.parametrize("seed,J,N,G", SMALL[:6])
+def test_oci_dense_triangular_solves_match_oracle(seed, J, N, G, monkeypatch):
+    """The per-cell path with the LU factors and two triangular solves per
+    sweep (getrs, as the paper applies them; the default applies the inverse
+    formed once from the same elimination)."""
+    monkeypatch.setenv("OCI_DENSE_APPLY", "lu")
+    compare_steps(W.random_slab(seed, J, N, G).replace(tol=1e-11), 2, solver=oci.SOLVER_DENSE_LU)
+
+
+@pytest.mark.parametrize("seed,J,N,G", SMALL[:6])
 def test_si_matches_oracle(seed, J, N, G):
     compare_steps(W.random_slab(seed, J, N, G).replace(tol=1e-11), 2, method="si")
 
