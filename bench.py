@@ -46,13 +46,16 @@ METRIC = "OCI cell-unknown updates/s"
 UNIT = "updates/s"
 SAMPLE_J = 3072
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of one FP64 sweep launch on the 2^18-cell S16
-# slab, per (kernel: 0 staged / 1 register form, cells per block, angle chunks) the autotuner can pick
+# slab (mean of two launches after one warm sweep; the ncu capture of this build summarised in
+# profiles/k_oci_sweep_slab3_J262144_S16.md), per (kernel: 0 staged / 1 register form, cells per
+# block, angle chunks) the autotuner can pick.  A table of measured constants: it is valid for the
+# kernels as built here and is re-taken whenever the sweep kernels change.
 SWEEP_DRAM_BYTES_NCU = {
-    (0, 64, 2): 271.829760e6 + 100.329984e6,
-    (1, 16, 4): 278.830592e6 + 106.181632e6, (1, 16, 8): 278.059520e6 + 106.986240e6,
-    (1, 32, 2): 286.433024e6 + 105.320704e6, (1, 32, 4): 278.543104e6 + 105.922560e6,
-    (1, 32, 8): 277.979392e6 + 106.466304e6, (1, 64, 2): 286.132736e6 + 105.421056e6,
-    (1, 64, 4): 278.674944e6 + 105.612800e6,
+    (0, 64, 2): 272.343552e6 + 98.906880e6,
+    (1, 16, 4): 278.945024e6 + 104.983808e6, (1, 16, 8): 278.031616e6 + 105.982080e6,
+    (1, 32, 2): 279.294592e6 + 104.551168e6, (1, 32, 4): 278.674176e6 + 105.039488e6,
+    (1, 32, 8): 278.053632e6 + 105.760896e6, (1, 64, 2): 279.072256e6 + 104.132864e6,
+    (1, 64, 4): 278.801792e6 + 104.745856e6,
 }
 # FP64 issue rate of one SM: 2 DFMA per clock (GB300: 1.25 TFLOP/s FP64 = 152 SMs x 2 x 2 flops
 # x 2.07 GHz); the ALU roofline's peak = SMs x this x 2 flops x the maximum SM clock.
@@ -422,7 +425,8 @@ def run_ours(args):
     if not args.no_multigroup:
         q = W.slab_multigroup()
         multigroup = {"workload": q.name, "J": q.J, "N": q.N, "G": q.G, "unknowns_per_cell": 4 * q.N * q.G}
-        for name, kw in (("fp64", {}), ("fp32ir", {"precision": oci.FP32_IR})):
+        for name, kw in (("fp64", {}), ("fp32ir", {"precision": oci.FP32_IR}),
+                         ("tf32ir", {"precision": oci.TF32_IR}), ("bf16x3ir", {"precision": oci.BF16X3_IR})):
             with oci.Solver(q, stream=stream.cuda_stream, **kw) as sv:
                 sv.step()  # warm step
                 t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -532,6 +536,9 @@ def run_ours(args):
                          "traffic": SWEEP_DRAM_BYTES_NCU.get(sweep_key) if (p.J == 2 ** 18 and p.N == 16 and
                                                                              p.G == 1) else None,
                          "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
+                         "traffic_source": "ncu capture of this kernel and launch shape on the same workload "
+                                           "(profiles/k_oci_sweep_slab3_J262144_S16.md); a table of measured "
+                                           "constants, not taken in this run",
                          "algorithmic_bytes": bytes_cell * p.J,
                          "kernel": sweep_name,
                          "peak_source": f"derived: {n_sm} SMs x {FP64_FMA_PER_SM_CLK} FP64 FMA/clk x 2 flops x "

@@ -9,8 +9,13 @@ interface (the paper's Sec. 4 outlook: subdomains exchanging every iteration):
   - the squared norms of the ranks' sweeps are summed (one allreduce) and the
     stop rule of Sec. 2.1 is applied to e = sqrt(sum) on every rank.
 The iterates are those of single-domain OCI; only the summation order of e
-changes.  The local solver is any object with edges(), set_boundary(l, r),
-iterate(1) and commit() -- the GPU `oci.Solver`, or a CPU stand-in in tests.
+changes.  The local solver is any object with edges(left, right) (fills the
+two [G][N][2] buffers), set_boundary(l, r), iterate(1, e_hist) and commit() --
+the GPU `oci.Solver`, or a CPU stand-in in tests.  With a CUDA device (NCCL)
+the edge buffers, the received incident fluxes and the norm stay on the GPU:
+oci_get_edges writes the send buffers, NCCL moves them, oci_set_boundary reads
+the receive buffers, and only the summed e (one scalar per sweep, for the stop
+rule) comes to the host.  With gloo they are host tensors.
 """
 from __future__ import annotations
 
@@ -44,7 +49,8 @@ class RankFailure(RuntimeError):
 
 
 class HaloExchange:
-    """Edge exchange and norm allreduce over torch.distributed (gloo or NCCL)."""
+    """Edge exchange and norm allreduce over torch.distributed (gloo or NCCL),
+    with send / receive buffers and the norm kept on `device`."""
 
     def __init__(self, rank: int, world: int, G: int, N: int, device: str = "cpu"):
         import torch
@@ -52,29 +58,38 @@ class HaloExchange:
         self.rank, self.world, self.G, self.N = rank, world, G, N
         self.device = device
 
-    def exchange(self, left_edge: np.ndarray, right_edge: np.ndarray):
-        """Send my first cell's L values left and my last cell's R values right;
-        return (inflow from the left neighbour, inflow from the right neighbour),
-        None at the slab ends."""
+        def buf(shape):
+            return torch.zeros(shape, dtype=torch.float64, device=device)
+
+        self.send_l, self.send_r = buf((G, N, 2)), buf((G, N, 2))
+        self.recv_l, self.recv_r = buf((G, N, 2)), buf((G, N, 2))
+        self.e = buf((1,))
+
+    def view(self, t):
+        """The buffer as the local solver takes it: the tensor itself on a GPU,
+        a numpy view of the same memory on the host."""
+        return t.numpy() if t.device.type == "cpu" else t
+
+    def exchange(self):
+        """Send send_l to the left neighbour and send_r to the right one; return
+        (inflow from the left neighbour, inflow from the right neighbour) as
+        buffers, None at the slab ends."""
         import torch.distributed as dist
-        t = self.torch
-        ops, recv_l, recv_r = [], None, None
+        ops = []
         if self.rank > 0:
-            recv_l = t.empty((self.G, self.N, 2), dtype=t.float64, device=self.device)
-            ops.append(dist.P2POp(dist.irecv, recv_l, self.rank - 1))
-            ops.append(dist.P2POp(dist.isend, t.as_tensor(left_edge, device=self.device), self.rank - 1))
+            ops.append(dist.P2POp(dist.irecv, self.recv_l, self.rank - 1))
+            ops.append(dist.P2POp(dist.isend, self.send_l, self.rank - 1))
         if self.rank < self.world - 1:
-            recv_r = t.empty((self.G, self.N, 2), dtype=t.float64, device=self.device)
-            ops.append(dist.P2POp(dist.irecv, recv_r, self.rank + 1))
-            ops.append(dist.P2POp(dist.isend, t.as_tensor(right_edge, device=self.device), self.rank + 1))
+            ops.append(dist.P2POp(dist.irecv, self.recv_r, self.rank + 1))
+            ops.append(dist.P2POp(dist.isend, self.send_r, self.rank + 1))
         try:
             if ops:
                 for r in dist.batch_isend_irecv(ops):
                     r.wait()
         except RuntimeError as e:  # gloo/NCCL timeout or a peer that left
             raise RankFailure(f"rank {self.rank}: edge exchange failed: {e}") from e
-        return (None if recv_l is None else recv_l.cpu().numpy(),
-                None if recv_r is None else recv_r.cpu().numpy())
+        return (self.view(self.recv_l) if self.rank > 0 else None,
+                self.view(self.recv_r) if self.rank < self.world - 1 else None)
 
     def allreduce_sum(self, x: float) -> float:
         import torch.distributed as dist
@@ -85,18 +100,29 @@ class HaloExchange:
             raise RankFailure(f"rank {self.rank}: norm allreduce failed: {e}") from e
         return float(v.item())
 
+    def norm_of_local(self) -> float:
+        """e = sqrt(sum over ranks of e_local^2), e_local in the buffer `e`."""
+        import torch.distributed as dist
+        v = self.e * self.e
+        try:
+            dist.all_reduce(v, op=dist.ReduceOp.SUM)
+        except RuntimeError as e:
+            raise RankFailure(f"rank {self.rank}: norm allreduce failed: {e}") from e
+        return math.sqrt(float(v.item()))
+
 
 def step(local, halo: HaloExchange, inc_left: Optional[np.ndarray], inc_right: Optional[np.ndarray],
          tol: float, max_iter: int) -> dict:
     """One time step of OCI over all ranks; returns dict(status, iters, e, rho)."""
     e_prev, rho = 0.0, 0.0
+    send_l, send_r, e_buf = halo.view(halo.send_l), halo.view(halo.send_r), halo.view(halo.e)
     for l in range(max_iter):
-        left, right = local.edges()
-        from_left, from_right = halo.exchange(left, right)
+        local.edges(send_l, send_r)
+        from_left, from_right = halo.exchange()
         local.set_boundary(inc_left if from_left is None else from_left,
                            inc_right if from_right is None else from_right)
-        e_loc = float(local.iterate(1)[0])
-        e = math.sqrt(halo.allreduce_sum(e_loc * e_loc))
+        local.iterate(1, e_buf)
+        e = halo.norm_of_local()
         if not math.isfinite(e):
             return dict(status=-6, iters=l + 1, e=e, rho=rho)
         rho = e / e_prev if (l >= 1 and e_prev > 0) else 0.0

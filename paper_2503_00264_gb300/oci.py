@@ -323,9 +323,12 @@ class Solver:
         return out
 
     def set_boundary(self, inc_left, inc_right):
-        a = None if inc_left is None else np.ascontiguousarray(inc_left, np.float64)
-        b = None if inc_right is None else np.ascontiguousarray(inc_right, np.float64)
-        _check(self.L.oci_set_boundary(self.h, _ptr(a), _ptr(b)))
+        """Incident fluxes [G][N][2] (numpy, or torch tensors on the host or the device)."""
+        def arr(x):
+            if x is None or hasattr(x, "data_ptr"):
+                return x
+            return np.ascontiguousarray(x, np.float64)
+        _check(self.L.oci_set_boundary(self.h, _ptr(arr(inc_left)), _ptr(arr(inc_right))))
 
     def e_hist(self) -> np.ndarray:
         n = ctypes.c_int32()
@@ -348,9 +351,11 @@ class Solver:
     def set_ordering(self, ordering: int):
         _check(self.L.oci_set_ordering(self.h, int(ordering)))
 
-    def edges(self):
-        left = np.zeros((self.G, self.N, 2))
-        right = np.zeros((self.G, self.N, 2))
+    def edges(self, left=None, right=None):
+        """Edge values [G][N][2] of cell 0 (kL, hL) and cell J-1 (kR, hR), into the
+        given buffers (numpy, or torch tensors on the host or the device) or new arrays."""
+        left = np.zeros((self.G, self.N, 2)) if left is None else left
+        right = np.zeros((self.G, self.N, 2)) if right is None else right
         _check(self.L.oci_get_edges(self.h, _ptr(left, writable=True), _ptr(right, writable=True)))
         return left, right
 

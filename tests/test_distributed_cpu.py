@@ -27,15 +27,17 @@ class OracleLocal:
         import oracle
         self.o = oracle.Oracle(prob)
 
-    def edges(self):
+    def edges(self, left, right):
         P = self.o.Psi
-        return np.ascontiguousarray(P[0][..., [0, 2]]), np.ascontiguousarray(P[-1][..., [1, 3]])
+        left[...] = P[0][..., [0, 2]]
+        right[...] = P[-1][..., [1, 3]]
 
     def set_boundary(self, il, ir):
         self.o.set_boundary(il, ir)
 
-    def iterate(self, n):
-        return self.o.iterate(n)
+    def iterate(self, n, e_hist):
+        e_hist[:n] = self.o.iterate(n)
+        return e_hist
 
     def commit(self):
         self.o.psi_prev = np.ascontiguousarray(self.o.Psi[..., 2:4])
