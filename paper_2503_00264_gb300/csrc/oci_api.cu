@@ -159,8 +159,8 @@ int validate(const oci_problem *p) {
   if (p->solver == OCI_SOLVER_DENSE_LU && 4 * p->N * p->G > 1024)
     return set_error("the dense per-cell solver needs 4*N*G <= 1024"), OCI_E_INVAL;
   if ((p->precision == OCI_TF32_IR || p->precision == OCI_BF16X3_IR) &&
-      (4 * p->N * p->G > 128 || (4 * p->N * p->G) % 32 != 0))
-    return set_error("the tensor-core forms need 4*N*G <= 128 and a multiple of 32"), OCI_E_INVAL;
+      (4 * p->N * p->G > 512 || (4 * p->N * p->G) % 32 != 0))
+    return set_error("the tensor-core forms need 4*N*G <= 512 and a multiple of 32"), OCI_E_INVAL;
   return OCI_OK;
 }
 
@@ -903,6 +903,8 @@ static int setup_impl(const oci_problem *p, oci_handle *h) {
 static void launch_mx_sweep(Handle &h, cudaGraphConditionalHandle cond, int use_cond) {
   if (h.precision == OCI_FP32_IR) {
     launch_mx_inner(h, cond, use_cond);  // norm and stop rule fused in
+  } else if (tc_big_used(h)) {
+    launch_tc_big(h, cond, use_cond);  // 4NG > 128: M-tiled, A^{-1} streamed per K-chunk
   } else if (tc_pipe_ok(h)) {
     launch_tc_pipe(h, cond, use_cond);  // persistent pipelined tensor-core sweep, norm fused in
   } else {

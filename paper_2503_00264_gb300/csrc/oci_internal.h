@@ -242,6 +242,12 @@ void launch_tc_pipe(Handle &h, cudaGraphConditionalHandle cond, int use_cond);
 int tc_partials(const Handle &h);
 void launch_tc_inner(Handle &h);
 int tc_build_images(Handle &h, const std::vector<double> &Ainv);
+// tensor-core form for 128 < 4NG <= 512 (oci_tc_big.cu)
+bool tc_big_used(const Handle &h);
+int tc_big_prepare(const Handle &h);
+void launch_tc_big(Handle &h, cudaGraphConditionalHandle cond, int use_cond);
+int tc_big_build_images(Handle &h, const std::vector<double> &Ainv, float (*round_tf32)(float),
+                        uint16_t (*bf16_bits)(float), float (*bf16_value)(uint16_t));
 // dense path
 int dense_setup(Handle &h);
 void launch_dense_step_const(Handle &h);

@@ -555,6 +555,7 @@ void launch_tc_pipe(Handle &h, cudaGraphConditionalHandle cond, int use_cond) {
 }
 
 int tc_prepare(Handle &h) {
+  if (tc_big_used(h)) return tc_big_prepare(h);
   const size_t smem = tc_smem(h);
   cudaError_t e = cudaFuncSetAttribute(k_tc_inner<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess)
@@ -594,6 +595,7 @@ static float bf16_bits_to_float(uint16_t h) {
 
 // Ainv: [T][n][n] row-major FP64 inverses of the per-type cell matrices.
 int tc_build_images(Handle &h, const std::vector<double> &Ainv) {
+  if (tc_big_used(h)) return tc_big_build_images(h, Ainv, host_tf32, host_bf16_bits, bf16_bits_to_float);
   const int n = 4 * h.N * h.G, T = h.tt.n_types;
   const bool tf = h.precision == OCI_TF32_IR;
   const int es = tf ? 4 : 2, parts = tf ? 1 : 2;

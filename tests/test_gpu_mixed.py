@@ -364,3 +364,44 @@ def test_fp32_multigroup_16_cell_tiles_match_oracle(kernel, kind, monkeypatch):
             st = s.step()
             assert st["status"] == 0 and abs(st["iters"] - r["iters"]) <= 2
             assert rel(s.phi(), r["phi"]) < 1e-10
+
+
+# more than 128 unknowns per cell: A^{-1} in M-tiles of 128 rows, streamed in K-chunks of 32
+TC_BIG_CASES = [(41, 300, 16, 3), (42, 257, 16, 4), (43, 200, 10, 4), (44, 140, 32, 4), (45, 129, 16, 8)]
+
+
+@pytest.mark.parametrize("prec", [oci.TF32_IR, oci.BF16X3_IR])
+@pytest.mark.parametrize("seed,J,N,G", TC_BIG_CASES)
+def test_tensor_core_forms_more_than_128_unknowns_match_oracle(prec, seed, J, N, G):
+    """4NG = 192 (two M-tiles, zero rows), 256, 160 (five K-chunks), 512 (four
+    M-tiles): flux within 1e-10 of the FP64 oracle over three steps, ragged last tile."""
+    p = _uniform_tiles(seed, J, N, G)
+    o = Oracle(p)
+    with oci.Solver(p, precision=prec) as s:
+        for k in range(3):
+            r = o.step(OCI)
+            st = s.step()
+            assert st["status"] == 0
+            assert st["iters"] <= r["iters"] + 12, (st["iters"], r["iters"])
+            assert rel(s.phi(), r["phi"]) < 1e-10
+            assert rel(s.psi(), r["Psi"]) < 1e-10
+            assert np.abs(s.balance() - r["bal"]).max() <= 1e-10 * np.abs(r["bal"]).max()
+
+
+@pytest.mark.parametrize("prec", [oci.TF32_IR, oci.BF16X3_IR])
+def test_tensor_core_multigroup_recipe_matches_oracle_per_group(prec):
+    """The 8-group, S16, 4-material recipe (512 unknowns per cell, blocks of
+    256 cells) on 1024 cells: two converged steps against the oracle, per group
+    within 1e-8 of each group's scale and 1e-10 of the largest."""
+    p = W.slab_multigroup(J=1024, region=256)
+    o = Oracle(p, share_factors=True)
+    with oci.Solver(p, precision=prec) as s:
+        for k in range(2):
+            r = o.step(OCI)
+            st = s.step()
+            assert st["status"] == 0
+            assert st["iters"] <= r["iters"] + 12, (st["iters"], r["iters"])
+            phi = s.phi()
+            assert rel(phi, r["phi"]) < 1e-10
+            d = np.abs(phi - r["phi"]).max(axis=(0, 2)) / np.abs(r["phi"]).max(axis=(0, 2))
+            assert d.max() < 1e-8, d
