@@ -118,6 +118,7 @@ struct Handle {
   double mx_theta = 1e-4;
   CUtensorMap tm_z, tm_d[2];          // TMA descriptors of z32 and delta[0/1] ([R][Jp] FP32)
   bool tma_ok = false;                 // tensor maps encoded (4NG <= 256)
+  CUtensorMap tm_bg_r, tm_bg_d[2];     // tensor-core form, 4NG > 128: r and correction boxes of 32 rows
   unsigned long long mx_cond_ref = 0;  // IF-node handle of the refinement in the mixed-form graph
   int mx_jac_kind = 0, mx_jac_cb = 0, mx_jac_P = 0;  // the Jacobi FP32 inner sweep (kept while red-black)
   int mx_tune_sweeps = 0;              // > 0 while the autotuner times a multi-sweep launch of that many sweeps
@@ -244,7 +245,7 @@ void launch_tc_inner(Handle &h);
 int tc_build_images(Handle &h, const std::vector<double> &Ainv);
 // tensor-core form for 128 < 4NG <= 512 (oci_tc_big.cu)
 bool tc_big_used(const Handle &h);
-int tc_big_prepare(const Handle &h);
+int tc_big_prepare(Handle &h);
 void launch_tc_big(Handle &h, cudaGraphConditionalHandle cond, int use_cond);
 int tc_big_build_images(Handle &h, const std::vector<double> &Ainv, float (*round_tf32)(float),
                         uint16_t (*bf16_bits)(float), float (*bf16_value)(uint16_t));
