@@ -39,16 +39,18 @@
 
 namespace oci {
 
-constexpr int kBigM = 128;        // MMA M: cells per tile
-constexpr int kBigN = 128;        // cells per tile (the M of the MMA)
-constexpr int kBigNT = 256;       // MMA N: unknowns per N-tile
-constexpr int kBigKC = 32;        // K elements per chunk
-constexpr int kBigABlk = 32768;   // one chunk of A^{-1} for one N-tile: 256 rows x 32 K (TF32, or BF16 hi + lo)
-constexpr int kBigRBlk = 16384;   // one chunk of the RHS: 128 cells x 32 K (TF32, or BF16 hi + lo)
-constexpr int kBigThreads = 256;
+constexpr int kBigM = 128;         // MMA M: cells per tile
+constexpr int kBigN = 128;         // cells per tile (the M of the MMA)
+constexpr int kBigNT = 256;        // MMA N: unknowns per N-tile
+constexpr int kBigKC = 16;         // K elements per chunk
+constexpr int kBigABlk = 16384;    // one chunk of A^{-1} for one N-tile: 256 rows x 16 K (TF32, or BF16 hi + lo)
+constexpr int kBigRBlk = 8192;     // one chunk of the RHS: 128 cells x 16 K (TF32, or BF16 hi + lo)
+constexpr int kBigStages = 3;      // A^{-1} + RHS stages
+constexpr int kBigBuilders = 256;  // eight warps: RHS builders and drain
+constexpr int kBigThreads = kBigBuilders + 32;  // and one control warp: copies and MMAs
 constexpr long long kBigSpin = 1 << 22;
-constexpr int kBigHalo = 4;                       // columns each side of the delta box (16 B)
-constexpr int kBigDW = kBigN + 2 * kBigHalo;      // delta box width
+constexpr int kBigHalo = 4;                                 // columns each side of the delta box (16 B)
+constexpr int kBigDW = kBigN + 2 * kBigHalo;                // delta box width
 constexpr int kBigInBytes = kBigKC * (kBigN + kBigDW) * 4;  // r box + delta box of one chunk
 
 namespace {
@@ -91,22 +93,31 @@ __host__ __device__ inline uint32_t big_off(int row, int k, int es) {
 template <int KIND>  // 1 = TF32, 2 = BF16 x3
 __global__ void __launch_bounds__(kBigThreads, 1) k_tc_big(
     const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CUtensorMap tmD0,
-    const __grid_constant__ CUtensorMap tmD1, int J, int Jp, int N, int G, int NT, int NK, const int32_t *__restrict__ type,
-    const unsigned char *__restrict__ Aimg, const float *__restrict__ mu, const float *__restrict__ r32, float *D0,
-    float *D1, DevState *ds, double *__restrict__ partials, unsigned *counter, double *e_hist,
-    cudaGraphConditionalHandle cond, int use_cond) {
+    const __grid_constant__ CUtensorMap tmD1, int J, int Jp, int N, int G, int NT, int NK,
+    const int32_t *__restrict__ type, const unsigned char *__restrict__ Aimg, const float *__restrict__ mu,
+    const float *__restrict__ r32, float *D0, float *D1, DevState *ds, double *__restrict__ partials,
+    unsigned *counter, double *e_hist, cudaGraphConditionalHandle cond, int use_cond) {
   extern __shared__ __align__(1024) unsigned char smb_[];
-  __shared__ __align__(8) uint64_t tma_bar[2], mma_bar[2], in_bar;
+  // a_full: a stage's A^{-1} chunk has landed; rhs_full: the eight builder warps
+  // have written a stage's RHS chunk; mma_done: a stage's MMAs have completed;
+  // in_full: an input buffer's r / delta boxes have landed; tmem_empty: the
+  // accumulators of the last tile have been drained
+  __shared__ __align__(8) uint64_t a_full[kBigStages], rhs_full[kBigStages], mma_done[kBigStages], in_full[2],
+      tmem_empty;
   __shared__ uint32_t tslot;
+  __shared__ float mu_s[kMaxN];
   __shared__ double red[kBigThreads / 32];
   __shared__ bool s_last;
   __shared__ int s_fail;
   constexpr int es = KIND == 1 ? 4 : 2;
   constexpr int apart = kBigABlk / 2;  // BF16: the lo image follows the hi image
   constexpr int rpart = kBigRBlk / 2;
+  constexpr int ksteps = kBigKC * es / 32;  // MMAs per chunk, N-tile and pass (K = 8 TF32 / 16 BF16)
+  constexpr int npass = KIND == 1 ? 1 : 3;  // BF16 x3: hi.hi + lo.hi + hi.lo
   const int n = 4 * N * G;
   unsigned char *sm = (unsigned char *)(((uintptr_t)smb_ + 1023) & ~(uintptr_t)1023);
   const size_t stage_bytes = (size_t)NT * kBigABlk + kBigRBlk;  // NT A^{-1} blocks, then the RHS block
+  unsigned char *in_base = sm + kBigStages * stage_bytes;        // two input buffers
   const int t = threadIdx.x, w = t >> 5, lane = t & 31;
   if (ds->done) return;  // uniform
   const bool zero = ds->refine || ds->blk_i == 0;
@@ -119,273 +130,276 @@ __global__ void __launch_bounds__(kBigThreads, 1) k_tc_big(
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (t == 0) {
-    for (int s = 0; s < 2; s++) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&tma_bar[s])), "r"(1));
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&mma_bar[s])), "r"(1));
+    for (int q = 0; q < kBigStages; q++) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&a_full[q])), "r"(1));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&rhs_full[q])), "r"(kBigBuilders / 32));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&mma_done[q])), "r"(1));
     }
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&in_bar)), "r"(1));
+    for (int q = 0; q < 2; q++) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&in_full[q])), "r"(1));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&tmem_empty)), "r"(kBigBuilders / 32));
     asm volatile("fence.mbarrier_init.release.cluster;");
     s_fail = 0;
   }
+  for (int i = t; i < N; i += kBigThreads) mu_s[i] = mu[i];
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tslot;
   const int ntiles = (J + kBigN - 1) / kBigN;
+  const int my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  const int n_chunks = my_tiles * NK;  // chunk g: tile blockIdx.x + (g / NK) gridDim.x, K-chunk g % NK
   const int N2 = N / 2;
-  const uint32_t fmt = KIND == 1 ? 2u : 1u;  // kind::tf32 operands TF32 / kind::f16 operands BF16
-  // instruction descriptor without N: F32 accumulator, both operands K-major, M = 128
-  const uint32_t idesc0 = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(kBigM >> 4) << 24);
-  const uint32_t lbo = 128, sbo = (uint32_t)(kBigKC * es / 16) * 128;
-  constexpr int ksteps = kBigKC * es / 32;  // MMAs per chunk and pass (K = 8 TF32 / 16 BF16)
-  constexpr int npass = KIND == 1 ? 1 : 3;  // BF16 x3: hi.hi + hi.lo + lo.hi
-  // per-stage counts kept by thread 0 (copies issued, MMA groups committed)
-  int n_tma[2] = {0, 0}, n_mma[2] = {0, 0}, n_in = 0;
   float e2 = 0.f;
   bool failed = false;
-  // RHS inputs of a chunk, staged by the tensor memory accelerator into one
-  // buffer after the two stages: rows kb .. kb+31 of r (128 cells) and of the old
-  // correction (cells j0-4 .. j0+131, the halo for the neighbours' inflow; a box
-  // reaching past the array reads zeros).  Thread t owns cell c = t % 128 and
-  // the 16 rows hh*16 .. hh*16+15 of the chunk.
-  const int c = t & (kBigN - 1), hh = t >> 7;
-  float *in_r = (float *)(sm + 2 * stage_bytes);  // [32][128]
-  float *in_d = in_r + kBigKC * kBigN;            // [32][136]
-  const CUtensorMap *tmD = dcur ? &tmD1 : &tmD0;
-  auto issue_in = [&](int tile_, int kc_) {  // thread 0
-    const uint32_t bar = su32(&in_bar);
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kBigInBytes) : "memory");
-    const int x0 = tile_ * kBigN, y0 = kc_ * kBigKC;
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-            su32(in_r)),
-        "l"(reinterpret_cast<uint64_t>(&tmR)), "r"(x0), "r"(y0), "r"(bar)
-        : "memory");
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-            su32(in_d)),
-        "l"(reinterpret_cast<uint64_t>(tmD)), "r"(x0 - kBigHalo), "r"(y0), "r"(bar)
-        : "memory");
-    n_in++;
-  };
-  // the A copies of chunk gk_ (type tau_, chunk kc_) into stage gk_ & 1; thread 0
-  auto issue_tma = [&](int gk_, int tau_, int kc_) {
-    const int s_ = gk_ & 1;
-    const uint32_t bar = su32(&tma_bar[s_]);
-    unsigned char *stA_ = sm + (size_t)s_ * stage_bytes;
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(NT * kBigABlk) : "memory");
-    for (int nt = 0; nt < NT; nt++) {
-      const unsigned char *src = Aimg + (((size_t)tau_ * NT + nt) * NK + kc_) * kBigABlk;
-      asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                       su32(stA_ + (size_t)nt * kBigABlk)),
-                   "l"(reinterpret_cast<uint64_t>(src)), "r"(kBigABlk), "r"(bar)
-                   : "memory");
-    }
-    n_tma[s_]++;
-  };
-  auto advance = [&](int &tl, int &k) {
-    if (++k == NK) {
-      k = 0;
-      tl += gridDim.x;
-    }
-  };
-  const uint64_t dhi = big_desc(0, lbo, sbo);  // descriptor without its start address
-  int tile = blockIdx.x, kc = 0, gk = 0;
-  int tau_cur = 0, tau_nt = 0;  // types of the current and the next tile (thread 0)
-  // one chunk: returns 0 to go on, 1 when this CTA's work is done, -1 on a failure
-  auto chunk = [&]() -> int {
-    const int s = gk & 1;
-    unsigned char *stA = sm + (size_t)s * stage_bytes;
-    unsigned char *stB = stA + (size_t)NT * kBigABlk;  // the RHS chunk: the MMA's A operand
-    int ntile = tile, nkc = kc;
-    advance(ntile, nkc);
-    const bool has_next = ntile < ntiles;
-    // (1) stage s is free once the MMAs of chunk gk - 2 have completed, and this
-    // chunk's inputs have landed: thread 0 waits on the mbarriers (acquire), the
-    // others in the block barrier behind it
-    bool ok = true;
-    if (t == 0) {
-      if (gk >= 2) ok = big_wait(su32(&mma_bar[s]), (uint32_t)(((gk >> 1) - 1) & 1));
-      ok = ok && big_wait(su32(&in_bar), (uint32_t)(gk & 1));
-    }
-    if (!__syncthreads_and(ok && s_fail == 0)) return -1;
-    // (2) this chunk's RHS r + B delta into the stage: TF32 or BF16 hi/lo
-    {
-      const int j = tile * kBigN + c;
-      const bool act = j < J;
-      const int kb = kc * kBigKC + hh * 16;
-      float vc[16];
+
+  if (w < kBigBuilders / 32) {
+    // ------------------------------------------------ builders (and drain)
+    const int c = t & (kBigN - 1), hh = t >> 7;  // cell c, rows hh*8 .. hh*8+7 of a chunk
+    for (int g = 0, kc = 0, tile = blockIdx.x, s = 0, u3 = 0; g < n_chunks; g++) {
+      const int ib = g & 1;
+      float *in_r = (float *)(in_base + (size_t)ib * kBigInBytes);  // [16][128]
+      float *in_d = in_r + kBigKC * kBigN;                            // [16][136]
+      unsigned char *stB = sm + (size_t)s * stage_bytes + (size_t)NT * kBigABlk;
+      // this chunk's inputs have landed and the stage's MMAs of chunk g - 3 are done
+      bool ok = big_wait(su32(&in_full[ib]), (uint32_t)((g >> 1) & 1));
+      if (ok && g >= kBigStages) ok = big_wait(su32(&mma_done[s]), (uint32_t)((u3 - 1) & 1));
+      if (!__all_sync(0xffffffffu, ok)) {  // warp-uniform: the warp leaves together
+        s_fail = 1;
+        failed = true;
+        break;
+      }
+      {  // RHS r + B delta of cell c, rows hh*8 .. hh*8+7: TF32, or BF16 hi / lo
+        const int j = tile * kBigN + c;
+        const bool act = j < J;
+        float v[8];
 #pragma unroll
-      for (int i = 0; i < 16; i++) vc[i] = act ? in_r[(hh * 16 + i) * kBigN + c] : 0.f;
-      if (act && !zero) {
+        for (int i = 0; i < 8; i++) v[i] = act ? in_r[(hh * 8 + i) * kBigN + c] : 0.f;
+        if (act && !zero) {
+          // rows kc*16 + hh*8 .. +7 are two (group, angle) blocks of four corners
+          const int m0 = (kc * (kBigKC / 4) + hh * 2) % N;
+          const int m1 = m0 + 1 == N ? 0 : m0 + 1;
 #pragma unroll
-        for (int q = 0; q < 8; q++) {
-          const int k = kb + 2 * q, kl2 = hh * 16 + 2 * q;
-          const int m = (k >> 2) % N;
-          const float mf = mu[m];
-          if (m >= N2) {  // p even: mu * (R corner of cell j-1)
-            if (j > 0) vc[2 * q] = fmaf(mf, in_d[(kl2 + 1) * kBigDW + c + kBigHalo - 1], vc[2 * q]);
-          } else if (j < J - 1) {  // p odd: |mu| * (L corner of cell j+1)
-            vc[2 * q + 1] = fmaf(-mf, in_d[kl2 * kBigDW + c + kBigHalo + 1], vc[2 * q + 1]);
+          for (int q = 0; q < 4; q++) {
+            const int kl2 = hh * 8 + 2 * q;
+            const int m = q < 2 ? m0 : m1;
+            const float mf = mu_s[m];
+            if (m >= N2) {  // p even: mu * (R corner of cell j-1)
+              if (j > 0) v[2 * q] = fmaf(mf, in_d[(kl2 + 1) * kBigDW + c + kBigHalo - 1], v[2 * q]);
+            } else if (j < J - 1) {  // p odd: |mu| * (L corner of cell j+1)
+              v[2 * q + 1] = fmaf(-mf, in_d[kl2 * kBigDW + c + kBigHalo + 1], v[2 * q + 1]);
+            }
           }
         }
-      }
-      const int kl = hh * 16;  // row inside the chunk
-      if (KIND == 1) {
-#pragma unroll
-        for (int g4 = 0; g4 < 16; g4 += 4)
-          *(float4 *)(stB + big_off(c, kl + g4, 4)) = make_float4(vc[g4], vc[g4 + 1], vc[g4 + 2], vc[g4 + 3]);
-      } else {
-#pragma unroll
-        for (int g8 = 0; g8 < 16; g8 += 8) {
+        if (KIND == 1) {
+          *(float4 *)(stB + big_off(c, hh * 8, 4)) = make_float4(v[0], v[1], v[2], v[3]);
+          *(float4 *)(stB + big_off(c, hh * 8 + 4, 4)) = make_float4(v[4], v[5], v[6], v[7]);
+        } else {
           uint32_t hi[4], lo[4];
 #pragma unroll
           for (int i = 0; i < 4; i++) {
-            const float a0 = vc[g8 + 2 * i], a1 = vc[g8 + 2 * i + 1];
+            const float a0 = v[2 * i], a1 = v[2 * i + 1];
             const __nv_bfloat16 h0 = __float2bfloat16_rn(a0), h1 = __float2bfloat16_rn(a1);
             const __nv_bfloat16 l0 = __float2bfloat16_rn(a0 - __bfloat162float(h0));
             const __nv_bfloat16 l1 = __float2bfloat16_rn(a1 - __bfloat162float(h1));
             hi[i] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
             lo[i] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
           }
-          const uint32_t off = big_off(c, kl + g8, 2);
+          const uint32_t off = big_off(c, hh * 8, 2);
           *(uint4 *)(stB + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
           *(uint4 *)(stB + rpart + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
         }
       }
-    }
-    // (4) the RHS is visible to the tensor cores; the previous tile's drain is done
-    asm volatile("fence.proxy.async.shared::cta;");
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    // (5) one thread: wait for this chunk's copies, issue the MMAs of every M-tile and
-    // commit; then, once chunk gk - 1's MMAs have freed the other stage, start the
-    // copies of chunk gk + 1 into it
-    if (t == 0) {
-      if (has_next) issue_in(ntile, nkc);  // every thread has read this chunk's inputs
-      if (!big_wait(su32(&tma_bar[s]), (uint32_t)((gk >> 1) & 1))) {
-        s_fail = 1;
-      } else {
-        const uint32_t bA = su32(stA), bR = su32(stB);
-        for (int nt = 0; nt < NT; nt++) {
-          const int nn = min(kBigNT, n - nt * kBigNT);  // unknowns of this N-tile (a multiple of 16)
-          const uint32_t idesc = idesc0 | ((uint32_t)(nn >> 3) << 17);
-          const uint32_t d_tmem = tmem + (uint32_t)(nt * kBigNT);
-          for (int pass = 0; pass < npass; pass++) {
-            const uint32_t a0 = bR + (pass == 1 ? rpart : 0);                                 // RHS (cells x K)
-            const uint32_t b0 = bA + (uint32_t)(nt * kBigABlk) + (pass == 2 ? apart : 0);  // A^{-1} rows (unknowns x K)
-            for (int kk = 0; kk < ksteps; kk++) {
-              const uint64_t ad = dhi | (uint64_t)(((a0 + kk * 256) & 0x3FFFF) >> 4);
-              const uint64_t bd = dhi | (uint64_t)(((b0 + kk * 256) & 0x3FFFF) >> 4);
-              const uint32_t acc = (kc > 0 || pass > 0 || kk > 0) ? 1u : 0u;
-              if (KIND == 1)
-                asm volatile(
-                    "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(
-                        d_tmem),
-                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
-              else
-                asm volatile(
-                    "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
-                        d_tmem),
-                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+      // the RHS is visible to the tensor cores and the inputs are consumed
+      asm volatile("fence.proxy.async.shared::cta;");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(&rhs_full[s])) : "memory");
+      if (kc == NK - 1) {
+        // last chunk of the tile: drain the accumulators once its MMAs are done.  Warp
+        // w reads the lanes (cells) 32 (w % 4) .. +31; the n columns (unknowns) go in
+        // blocks of 32 to the two warps of a lane quarter alternately; each register
+        // of a block is one unknown of the lane's cell, so every load and store is a
+        // 128-byte row of 32 cells.  The old correction of the next block is loaded
+        // before this one's accumulators are read.
+        if (!__all_sync(0xffffffffu, big_wait(su32(&mma_done[s]), (uint32_t)(u3 & 1)))) {
+          s_fail = 1;
+          failed = true;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const int q4 = w & 3, g2 = w >> 2;
+        const int j = tile * kBigN + 32 * q4 + lane;
+        const bool act = j < J;
+        const int nb = n / 32;  // column blocks
+        float dold[32], dnxt[32];
+        auto load_old = [&](int b_, float *dst) {
+#pragma unroll
+          for (int i = 0; i < 32; i++) dst[i] = (act && !zero) ? Din[(size_t)(b_ * 32 + i) * Jp + j] : 0.f;
+        };
+        if (g2 < nb) load_old(g2, dold);
+#pragma unroll 1
+        for (int b_ = g2; b_ < nb; b_ += 2) {
+          uint32_t r[32];
+          const uint32_t addr = tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)(b_ * 32);
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+              : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+              : "r"(addr));
+          if (b_ + 2 < nb) load_old(b_ + 2, dnxt);
+          asm volatile("tcgen05.wait::ld.sync.aligned;");
+          if (act) {
+#pragma unroll
+            for (int i = 0; i < 32; i++) {
+              const float o = __uint_as_float(r[i]);
+              const float d = o - dold[i];
+              e2 = fmaf(d, d, e2);
+              Dout[(size_t)(b_ * 32 + i) * Jp + j] = o;
             }
           }
+#pragma unroll
+          for (int i = 0; i < 32; i++) dold[i] = dnxt[i];
         }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-            su32(&mma_bar[s])));
-        n_mma[s]++;
-        if (has_next) {
-          if (gk >= 1 && !big_wait(su32(&mma_bar[s ^ 1]), (uint32_t)(((gk - 1) >> 1) & 1))) s_fail = 1;
-          else issue_tma(gk + 1, nkc == 0 ? tau_nt : tau_cur, nkc);
-        }
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncwarp();
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(&tmem_empty)) : "memory");
+      }
+      if (++kc == NK) {
+        kc = 0;
+        tile += gridDim.x;
+      }
+      if (++s == kBigStages) {
+        s = 0;
+        u3++;
       }
     }
-    // (6) last chunk of the tile: drain the accumulators.  Warp w reads the lanes
-    // (cells) 32 (w % 4) .. +31; the n columns (unknowns) go in blocks of 32 to
-    // the two warps of a lane quarter alternately; each register of a block is one
-    // unknown of the lane's cell, so every load and store is a 128-byte row of 32
-    // cells.  The old correction of the next block is loaded before this one's
-    // accumulators are read.
-    if (kc == NK - 1) {
-      bool okd = true;
-      if (t == 0) okd = s_fail == 0 && big_wait(su32(&mma_bar[s]), (uint32_t)((gk >> 1) & 1));
-      if (!__syncthreads_and(okd)) return -1;
-      asm volatile("tcgen05.fence::after_thread_sync;");
-      const int q4 = w & 3, g2 = w >> 2;
-      const int j = tile * kBigN + 32 * q4 + lane;
-      const bool act = j < J;
-      const int nb = n / 32;  // column blocks
-      float dold[32], dnxt[32];
-      auto load_old = [&](int b_, float *dst) {
-#pragma unroll
-        for (int i = 0; i < 32; i++) dst[i] = (act && !zero) ? Din[(size_t)(b_ * 32 + i) * Jp + j] : 0.f;
-      };
-      if (g2 < nb) load_old(g2, dold);
-#pragma unroll 1
-      for (int b_ = g2; b_ < nb; b_ += 2) {
-        uint32_t r[32];
-        const uint32_t addr = tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)(b_ * 32);
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-              "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-              "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-            : "r"(addr));
-        if (b_ + 2 < nb) load_old(b_ + 2, dnxt);
-        asm volatile("tcgen05.wait::ld.sync.aligned;");
-        if (act) {
-#pragma unroll
-          for (int i = 0; i < 32; i++) {
-            const float o = __uint_as_float(r[i]);
-            const float d = o - dold[i];
-            e2 = fmaf(d, d, e2);
-            Dout[(size_t)(b_ * 32 + i) * Jp + j] = o;
-          }
-        }
-#pragma unroll
-        for (int i = 0; i < 32; i++) dold[i] = dnxt[i];
+  } else if (lane == 0) {
+    // ------------------------------------------------ control: copies and MMAs (one thread)
+    const uint32_t fmt = KIND == 1 ? 2u : 1u;  // kind::tf32 operands TF32 / kind::f16 operands BF16
+    // instruction descriptor without N: F32 accumulator, both operands K-major, M = 128
+    const uint32_t idesc0 = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(kBigM >> 4) << 24);
+    const uint64_t dhi = big_desc(0, 128, (uint32_t)(kBigKC * es / 16) * 128);  // descriptor without its address
+    int n_a[kBigStages] = {0, 0, 0}, n_m[kBigStages] = {0, 0, 0}, n_in[2] = {0, 0};
+    auto chunk_tile = [&](int g_) { return (int)blockIdx.x + (g_ / NK) * (int)gridDim.x; };
+    auto issue_in = [&](int g_) {
+      const int b_ = g_ & 1;
+      float *dst = (float *)(in_base + (size_t)b_ * kBigInBytes);
+      const uint32_t bar = su32(&in_full[b_]);
+      const int x0 = chunk_tile(g_) * kBigN, y0 = (g_ % NK) * kBigKC;
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kBigInBytes) : "memory");
+      asm volatile(
+          "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+              su32(dst)),
+          "l"(reinterpret_cast<uint64_t>(&tmR)), "r"(x0), "r"(y0), "r"(bar)
+          : "memory");
+      asm volatile(
+          "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+              su32(dst + kBigKC * kBigN)),
+          "l"(reinterpret_cast<uint64_t>(dcur ? &tmD1 : &tmD0)), "r"(x0 - kBigHalo), "r"(y0), "r"(bar)
+          : "memory");
+      n_in[b_]++;
+    };
+    // types of this CTA's tiles, read ahead: tau_of[i & 3] is the type of its i-th tile
+    int tau_of[4] = {0, 0, 0, 0};
+    for (int i = 0; i < 4 && i < my_tiles; i++) tau_of[i] = type[chunk_tile(i * NK) * kBigN];
+    auto issue_a = [&](int g_) {
+      const int s_ = g_ % kBigStages;
+      const int ti = g_ / NK, tau_ = tau_of[ti & 3], kc_ = g_ % NK;
+      unsigned char *dst = sm + (size_t)s_ * stage_bytes;
+      const uint32_t bar = su32(&a_full[s_]);
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(NT * kBigABlk) : "memory");
+      for (int nt = 0; nt < NT; nt++) {
+        const unsigned char *src = Aimg + (((size_t)tau_ * NT + nt) * NK + kc_) * kBigABlk;
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                         su32(dst + (size_t)nt * kBigABlk)),
+                     "l"(reinterpret_cast<uint64_t>(src)), "r"(kBigABlk), "r"(bar)
+                     : "memory");
       }
-      asm volatile("tcgen05.fence::before_thread_sync;");
+      n_a[s_]++;
+    };
+    for (int g = 0; g < 2 && g < n_chunks; g++) {
+      issue_in(g);
+      issue_a(g);
     }
-    if (t == 0 && nkc == 0 && has_next) {  // entering the next tile: its type, and the one after
-      tau_cur = tau_nt;
-      if (ntile + (int)gridDim.x < ntiles) tau_nt = type[(ntile + gridDim.x) * kBigN];
-    }
-    tile = ntile;
-    kc = nkc;
-    gk++;
-    return has_next ? 0 : 1;
-  };
-  if (tile < ntiles) {
-    if (t == 0) {
-      tau_cur = type[tile * kBigN];
-      if (tile + (int)gridDim.x < ntiles) tau_nt = type[(tile + gridDim.x) * kBigN];
-      issue_in(tile, 0);
-      issue_tma(0, tau_cur, 0);
-    }
-    for (;;) {
-      const int rc = chunk();
-      if (rc != 0) {
-        failed = rc < 0;
+    for (int g = 0; g < n_chunks; g++) {
+      const int s = g % kBigStages, u3 = g / kBigStages, kc = g % NK;
+      // the builders have written this chunk's RHS (and read its inputs)
+      if (!big_wait(su32(&rhs_full[s]), (uint32_t)(u3 & 1))) {
+        failed = true;
         break;
       }
+      if (g + 2 < n_chunks) issue_in(g + 2);
+      if (!big_wait(su32(&a_full[s]), (uint32_t)(u3 & 1))) {
+        failed = true;
+        break;
+      }
+      if (kc == 0 && g > 0 && !big_wait(su32(&tmem_empty), (uint32_t)(((g / NK) - 1) & 1))) {
+        failed = true;
+        break;
+      }
+      if (kc == 0) {  // entering tile i = g / NK: tiles up to i + 3 have their types read
+        const int ti = g / NK + 3;
+        if (ti < my_tiles) tau_of[ti & 3] = type[chunk_tile(ti * NK) * kBigN];
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint32_t bA = su32(sm + (size_t)s * stage_bytes);
+      const uint32_t bR = bA + (uint32_t)(NT * kBigABlk);
+      for (int nt = 0; nt < NT; nt++) {
+        const int nn = min(kBigNT, n - nt * kBigNT);  // unknowns of this N-tile (a multiple of 16)
+        const uint32_t idesc = idesc0 | ((uint32_t)(nn >> 3) << 17);
+        const uint32_t d_tmem = tmem + (uint32_t)(nt * kBigNT);
+        for (int pass = 0; pass < npass; pass++) {
+          const uint32_t a0 = bR + (pass == 1 ? rpart : 0);                                 // RHS (cells x K)
+          const uint32_t b0 = bA + (uint32_t)(nt * kBigABlk) + (pass == 2 ? apart : 0);  // A^{-1} rows (unknowns x K)
+          for (int kk = 0; kk < ksteps; kk++) {
+            const uint64_t ad = dhi | (uint64_t)(((a0 + kk * 256) & 0x3FFFF) >> 4);
+            const uint64_t bd = dhi | (uint64_t)(((b0 + kk * 256) & 0x3FFFF) >> 4);
+            const uint32_t acc = (kc > 0 || pass > 0 || kk > 0) ? 1u : 0u;
+            if (KIND == 1)
+              asm volatile(
+                  "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(
+                      d_tmem),
+                  "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+            else
+              asm volatile(
+                  "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
+                      d_tmem),
+                  "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+          }
+        }
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          su32(&mma_done[s])));
+      n_m[s]++;
+      // chunk g + 2 goes into the stage of chunk g - 1 once its MMAs are done
+      if (g + 2 < n_chunks) {
+        if (g >= 1 && !big_wait(su32(&mma_done[(g - 1) % kBigStages]), (uint32_t)(((g - 1) / kBigStages) & 1))) {
+          failed = true;
+          break;
+        }
+        issue_a(g + 2);
+      }
     }
-  }
-  if (failed && t == 0) {
-    // let the copies and MMAs still in flight finish (bounded) before tensor memory is freed
-    for (int s = 0; s < 2; s++) {
-      if (n_tma[s] > 0) big_wait(su32(&tma_bar[s]), (uint32_t)((n_tma[s] - 1) & 1));
-      if (n_mma[s] > 0) big_wait(su32(&mma_bar[s]), (uint32_t)((n_mma[s] - 1) & 1));
+    if (failed) {
+      s_fail = 1;
+      // let the copies and MMAs still in flight finish (bounded) before tensor memory is freed
+      for (int q = 0; q < kBigStages; q++) {
+        if (n_a[q] > 0) big_wait(su32(&a_full[q]), (uint32_t)((n_a[q] - 1) & 1));
+        if (n_m[q] > 0) big_wait(su32(&mma_done[q]), (uint32_t)((n_m[q] - 1) & 1));
+      }
+      for (int q = 0; q < 2; q++)
+        if (n_in[q] > 0) big_wait(su32(&in_full[q]), (uint32_t)((n_in[q] - 1) & 1));
     }
-    if (n_in > 0) big_wait(su32(&in_bar), (uint32_t)((n_in - 1) & 1));
-    atomicExch(&ds->status, OCI_E_TIMEOUT);
-    ds->done = 1;
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   if (w == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(cols));
+  if (t == 0 && s_fail) {
+    atomicExch(&ds->status, OCI_E_TIMEOUT);
+    ds->done = 1;
+  }
   double ve = (double)e2;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) ve += __shfl_down_sync(0xffffffffu, ve, o);
@@ -407,7 +421,7 @@ static int tc_big_nt(const Handle &h) { return (4 * h.N * h.G + kBigNT - 1) / kB
 static int tc_big_nk(const Handle &h) { return (4 * h.N * h.G + kBigKC - 1) / kBigKC; }
 
 size_t tc_big_smem(const Handle &h) {
-  const size_t need = 2 * ((size_t)tc_big_nt(h) * kBigABlk + kBigRBlk) + kBigInBytes + 1024;
+  const size_t need = kBigStages * ((size_t)tc_big_nt(h) * kBigABlk + kBigRBlk) + 2 * (size_t)kBigInBytes + 1024;
   const size_t floor_bytes = 116 * 1024;  // one CTA per SM: its tensor memory never waits for another CTA's
   return need > floor_bytes ? need : floor_bytes;
 }
