@@ -47,7 +47,7 @@ constexpr int kBigABlk = 16384;    // one chunk of A^{-1} for one N-tile: 256 ro
 constexpr int kBigRBlk = 8192;     // one chunk of the RHS: 128 cells x 16 K (TF32, or BF16 hi + lo)
 constexpr int kBigStages = 3;      // A^{-1} + RHS stages
 constexpr int kBigBuilders = 256;  // eight warps: RHS builders and drain
-constexpr int kBigThreads = kBigBuilders + 32;  // and one control warp: copies and MMAs
+constexpr int kBigThreads = kBigBuilders + 64;  // and two control warps: MMAs, copies
 constexpr long long kBigSpin = 1 << 22;
 constexpr int kBigHalo = 4;                                 // columns each side of the delta box (16 B)
 constexpr int kBigDW = kBigN + 2 * kBigHalo;                // delta box width
@@ -276,121 +276,136 @@ __global__ void __launch_bounds__(kBigThreads, 1) k_tc_big(
       }
     }
   } else if (lane == 0) {
-    // ------------------------------------------------ control: copies and MMAs (one thread)
-    const uint32_t fmt = KIND == 1 ? 2u : 1u;  // kind::tf32 operands TF32 / kind::f16 operands BF16
-    // instruction descriptor without N: F32 accumulator, both operands K-major, M = 128
-    const uint32_t idesc0 = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(kBigM >> 4) << 24);
-    const uint64_t dhi = big_desc(0, 128, (uint32_t)(kBigKC * es / 16) * 128);  // descriptor without its address
-    int n_a[kBigStages] = {0, 0, 0}, n_m[kBigStages] = {0, 0, 0}, n_in[2] = {0, 0};
+    // ------------------------------------------------ control: warp 8 issues the MMAs, warp 9 the copies
+    const bool mma_role = w == kBigBuilders / 32;
     auto chunk_tile = [&](int g_) { return (int)blockIdx.x + (g_ / NK) * (int)gridDim.x; };
-    auto issue_in = [&](int g_) {
-      const int b_ = g_ & 1;
-      float *dst = (float *)(in_base + (size_t)b_ * kBigInBytes);
-      const uint32_t bar = su32(&in_full[b_]);
-      const int x0 = chunk_tile(g_) * kBigN, y0 = (g_ % NK) * kBigKC;
-      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kBigInBytes) : "memory");
-      asm volatile(
-          "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-              su32(dst)),
-          "l"(reinterpret_cast<uint64_t>(&tmR)), "r"(x0), "r"(y0), "r"(bar)
-          : "memory");
-      asm volatile(
-          "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-              su32(dst + kBigKC * kBigN)),
-          "l"(reinterpret_cast<uint64_t>(dcur ? &tmD1 : &tmD0)), "r"(x0 - kBigHalo), "r"(y0), "r"(bar)
-          : "memory");
-      n_in[b_]++;
-    };
-    // types of this CTA's tiles, read ahead: tau_of[i & 3] is the type of its i-th tile
-    int tau_of[4] = {0, 0, 0, 0};
-    for (int i = 0; i < 4 && i < my_tiles; i++) tau_of[i] = type[chunk_tile(i * NK) * kBigN];
-    auto issue_a = [&](int g_) {
-      const int s_ = g_ % kBigStages;
-      const int ti = g_ / NK, tau_ = tau_of[ti & 3], kc_ = g_ % NK;
-      unsigned char *dst = sm + (size_t)s_ * stage_bytes;
-      const uint32_t bar = su32(&a_full[s_]);
-      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(NT * kBigABlk) : "memory");
-      for (int nt = 0; nt < NT; nt++) {
-        const unsigned char *src = Aimg + (((size_t)tau_ * NT + nt) * NK + kc_) * kBigABlk;
-        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                         su32(dst + (size_t)nt * kBigABlk)),
-                     "l"(reinterpret_cast<uint64_t>(src)), "r"(kBigABlk), "r"(bar)
-                     : "memory");
-      }
-      n_a[s_]++;
-    };
-    for (int g = 0; g < 2 && g < n_chunks; g++) {
-      issue_in(g);
-      issue_a(g);
-    }
-    for (int g = 0; g < n_chunks; g++) {
-      const int s = g % kBigStages, u3 = g / kBigStages, kc = g % NK;
-      // the builders have written this chunk's RHS (and read its inputs)
-      if (!big_wait(su32(&rhs_full[s]), (uint32_t)(u3 & 1))) {
-        failed = true;
-        break;
-      }
-      if (g + 2 < n_chunks) issue_in(g + 2);
-      if (!big_wait(su32(&a_full[s]), (uint32_t)(u3 & 1))) {
-        failed = true;
-        break;
-      }
-      if (kc == 0 && g > 0 && !big_wait(su32(&tmem_empty), (uint32_t)(((g / NK) - 1) & 1))) {
-        failed = true;
-        break;
-      }
-      if (kc == 0) {  // entering tile i = g / NK: tiles up to i + 3 have their types read
-        const int ti = g / NK + 3;
-        if (ti < my_tiles) tau_of[ti & 3] = type[chunk_tile(ti * NK) * kBigN];
-      }
-      asm volatile("tcgen05.fence::after_thread_sync;");
-      const uint32_t bA = su32(sm + (size_t)s * stage_bytes);
-      const uint32_t bR = bA + (uint32_t)(NT * kBigABlk);
-      for (int nt = 0; nt < NT; nt++) {
-        const int nn = min(kBigNT, n - nt * kBigNT);  // unknowns of this N-tile (a multiple of 16)
-        const uint32_t idesc = idesc0 | ((uint32_t)(nn >> 3) << 17);
-        const uint32_t d_tmem = tmem + (uint32_t)(nt * kBigNT);
-        for (int pass = 0; pass < npass; pass++) {
-          const uint32_t a0 = bR + (pass == 1 ? rpart : 0);                                 // RHS (cells x K)
-          const uint32_t b0 = bA + (uint32_t)(nt * kBigABlk) + (pass == 2 ? apart : 0);  // A^{-1} rows (unknowns x K)
-          for (int kk = 0; kk < ksteps; kk++) {
-            const uint64_t ad = dhi | (uint64_t)(((a0 + kk * 256) & 0x3FFFF) >> 4);
-            const uint64_t bd = dhi | (uint64_t)(((b0 + kk * 256) & 0x3FFFF) >> 4);
-            const uint32_t acc = (kc > 0 || pass > 0 || kk > 0) ? 1u : 0u;
-            if (KIND == 1)
-              asm volatile(
-                  "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(
-                      d_tmem),
-                  "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
-            else
-              asm volatile(
-                  "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
-                      d_tmem),
-                  "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
-          }
-        }
-      }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          su32(&mma_done[s])));
-      n_m[s]++;
-      // chunk g + 2 goes into the stage of chunk g - 1 once its MMAs are done
-      if (g + 2 < n_chunks) {
-        if (g >= 1 && !big_wait(su32(&mma_done[(g - 1) % kBigStages]), (uint32_t)(((g - 1) / kBigStages) & 1))) {
+    if (mma_role) {
+      const uint32_t fmt = KIND == 1 ? 2u : 1u;  // kind::tf32 operands TF32 / kind::f16 operands BF16
+      // instruction descriptor without N: F32 accumulator, both operands K-major, M = 128
+      const uint32_t idesc0 = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(kBigM >> 4) << 24);
+      const uint64_t dhi = big_desc(0, 128, (uint32_t)(kBigKC * es / 16) * 128);  // descriptor without its address
+      int n_m[kBigStages] = {0, 0, 0};
+      for (int g = 0, s = 0, u3 = 0, kc = 0; g < n_chunks; g++) {
+        // this chunk's RHS is built and its A^{-1} chunk has landed; a new tile waits for the drain
+        bool ok = big_wait(su32(&rhs_full[s]), (uint32_t)(u3 & 1)) && big_wait(su32(&a_full[s]), (uint32_t)(u3 & 1));
+        if (ok && kc == 0 && g > 0) ok = big_wait(su32(&tmem_empty), (uint32_t)(((g / NK) - 1) & 1));
+        if (!ok) {
           failed = true;
           break;
         }
-        issue_a(g + 2);
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t bA = su32(sm + (size_t)s * stage_bytes);
+        const uint32_t bR = bA + (uint32_t)(NT * kBigABlk);
+        for (int nt = 0; nt < NT; nt++) {
+          const int nn = min(kBigNT, n - nt * kBigNT);  // unknowns of this N-tile (a multiple of 16)
+          const uint32_t idesc = idesc0 | ((uint32_t)(nn >> 3) << 17);
+          const uint32_t d_tmem = tmem + (uint32_t)(nt * kBigNT);
+          for (int pass = 0; pass < npass; pass++) {
+            const uint32_t a0 = bR + (pass == 1 ? rpart : 0);                                 // RHS (cells x K)
+            const uint32_t b0 = bA + (uint32_t)(nt * kBigABlk) + (pass == 2 ? apart : 0);  // A^{-1} rows (unknowns x K)
+            for (int kk = 0; kk < ksteps; kk++) {
+              const uint64_t ad = dhi | (uint64_t)(((a0 + kk * 256) & 0x3FFFF) >> 4);
+              const uint64_t bd = dhi | (uint64_t)(((b0 + kk * 256) & 0x3FFFF) >> 4);
+              const uint32_t acc = (kc > 0 || pass > 0 || kk > 0) ? 1u : 0u;
+              if (KIND == 1)
+                asm volatile(
+                    "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(
+                        d_tmem),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+              else
+                asm volatile(
+                    "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
+                        d_tmem),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+            }
+          }
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            su32(&mma_done[s])));
+        n_m[s]++;
+        if (++kc == NK) kc = 0;
+        if (++s == kBigStages) {
+          s = 0;
+          u3++;
+        }
       }
-    }
-    if (failed) {
-      s_fail = 1;
-      // let the copies and MMAs still in flight finish (bounded) before tensor memory is freed
-      for (int q = 0; q < kBigStages; q++) {
-        if (n_a[q] > 0) big_wait(su32(&a_full[q]), (uint32_t)((n_a[q] - 1) & 1));
-        if (n_m[q] > 0) big_wait(su32(&mma_done[q]), (uint32_t)((n_m[q] - 1) & 1));
+      if (failed) {
+        s_fail = 1;
+        for (int q = 0; q < kBigStages; q++)  // MMAs still in flight finish before tensor memory is freed
+          if (n_m[q] > 0) big_wait(su32(&mma_done[q]), (uint32_t)((n_m[q] - 1) & 1));
       }
-      for (int q = 0; q < 2; q++)
-        if (n_in[q] > 0) big_wait(su32(&in_full[q]), (uint32_t)((n_in[q] - 1) & 1));
+    } else {
+      int n_a[kBigStages] = {0, 0, 0}, n_in[2] = {0, 0};
+      // types of this CTA's tiles, read ahead: tau_of[i & 3] is the type of its i-th tile
+      int tau_of[4] = {0, 0, 0, 0};
+      for (int i = 0; i < 4 && i < my_tiles; i++) tau_of[i] = type[chunk_tile(i * NK) * kBigN];
+      auto issue_in = [&](int g_) {
+        const int b_ = g_ & 1;
+        float *dst = (float *)(in_base + (size_t)b_ * kBigInBytes);
+        const uint32_t bar = su32(&in_full[b_]);
+        const int x0 = chunk_tile(g_) * kBigN, y0 = (g_ % NK) * kBigKC;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kBigInBytes) : "memory");
+        asm volatile(
+            "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+                su32(dst)),
+            "l"(reinterpret_cast<uint64_t>(&tmR)), "r"(x0), "r"(y0), "r"(bar)
+            : "memory");
+        asm volatile(
+            "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+                su32(dst + kBigKC * kBigN)),
+            "l"(reinterpret_cast<uint64_t>(dcur ? &tmD1 : &tmD0)), "r"(x0 - kBigHalo), "r"(y0), "r"(bar)
+            : "memory");
+        n_in[b_]++;
+      };
+      auto issue_a = [&](int g_) {
+        const int s_ = g_ % kBigStages;
+        const int ti = g_ / NK, tau_ = tau_of[ti & 3], kc_ = g_ % NK;
+        unsigned char *dst = sm + (size_t)s_ * stage_bytes;
+        const uint32_t bar = su32(&a_full[s_]);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(NT * kBigABlk) : "memory");
+        for (int nt = 0; nt < NT; nt++) {
+          const unsigned char *src = Aimg + (((size_t)tau_ * NT + nt) * NK + kc_) * kBigABlk;
+          asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                           su32(dst + (size_t)nt * kBigABlk)),
+                       "l"(reinterpret_cast<uint64_t>(src)), "r"(kBigABlk), "r"(bar)
+                       : "memory");
+        }
+        n_a[s_]++;
+      };
+      for (int g = 0; g < 2 && g < n_chunks; g++) issue_in(g);
+      for (int g = 0; g < kBigStages && g < n_chunks; g++) issue_a(g);
+      for (int g = 0, s = 0, u3 = 0; g < n_chunks; g++) {
+        // the builders have read chunk g's inputs: chunk g + 2's go into its buffer
+        if (!big_wait(su32(&rhs_full[s]), (uint32_t)(u3 & 1))) {
+          failed = true;
+          break;
+        }
+        if (g + 2 < n_chunks) issue_in(g + 2);
+        if ((g + kBigStages) % NK == 0) {  // tile i + 3 gets its type read when tile i's last A copy is issued
+          const int ti = (g + kBigStages) / NK + 3;
+          if (ti < my_tiles) tau_of[ti & 3] = type[chunk_tile(ti * NK) * kBigN];
+        }
+        // chunk g's MMAs are done: chunk g + 3's A^{-1} goes into its stage
+        if (g + kBigStages < n_chunks) {
+          if (!big_wait(su32(&mma_done[s]), (uint32_t)(u3 & 1))) {
+            failed = true;
+            break;
+          }
+          issue_a(g + kBigStages);
+        }
+        if (++s == kBigStages) {
+          s = 0;
+          u3++;
+        }
+      }
+      if (failed) {
+        s_fail = 1;
+        // let the copies still in flight finish (bounded) before the CTA leaves
+        for (int q = 0; q < kBigStages; q++)
+          if (n_a[q] > 0) big_wait(su32(&a_full[q]), (uint32_t)((n_a[q] - 1) & 1));
+        for (int q = 0; q < 2; q++)
+          if (n_in[q] > 0) big_wait(su32(&in_full[q]), (uint32_t)((n_in[q] - 1) & 1));
+      }
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
