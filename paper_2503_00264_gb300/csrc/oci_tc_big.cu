@@ -171,24 +171,35 @@ __global__ void __launch_bounds__(kBigThreads, 1) k_tc_big(
       {  // RHS r + B delta of cell c, rows hh*8 .. hh*8+7: TF32, or BF16 hi / lo
         const int j = tile * kBigN + c;
         const bool act = j < J;
-        float v[8];
+        // all shared-memory loads first (no branch between them), then the inflow terms:
+        // rows kc*16 + hh*8 .. +7 are two (group, angle) blocks of four corners; for
+        // mu > 0 the even rows take mu * (R corner of cell j-1), for mu < 0 the odd
+        // rows |mu| * (L corner of cell j+1)
+        float v[8], up[4], dn[4];
 #pragma unroll
-        for (int i = 0; i < 8; i++) v[i] = act ? in_r[(hh * 8 + i) * kBigN + c] : 0.f;
-        if (act && !zero) {
-          // rows kc*16 + hh*8 .. +7 are two (group, angle) blocks of four corners
-          const int m0 = (kc * (kBigKC / 4) + hh * 2) % N;
-          const int m1 = m0 + 1 == N ? 0 : m0 + 1;
+        for (int i = 0; i < 8; i++) v[i] = in_r[(hh * 8 + i) * kBigN + c];
 #pragma unroll
-          for (int q = 0; q < 4; q++) {
-            const int kl2 = hh * 8 + 2 * q;
-            const int m = q < 2 ? m0 : m1;
-            const float mf = mu_s[m];
-            if (m >= N2) {  // p even: mu * (R corner of cell j-1)
-              if (j > 0) v[2 * q] = fmaf(mf, in_d[(kl2 + 1) * kBigDW + c + kBigHalo - 1], v[2 * q]);
-            } else if (j < J - 1) {  // p odd: |mu| * (L corner of cell j+1)
-              v[2 * q + 1] = fmaf(-mf, in_d[kl2 * kBigDW + c + kBigHalo + 1], v[2 * q + 1]);
-            }
-          }
+        for (int q = 0; q < 4; q++) {
+          const int kl2 = hh * 8 + 2 * q;
+          up[q] = in_d[(kl2 + 1) * kBigDW + c + kBigHalo - 1];
+          dn[q] = in_d[kl2 * kBigDW + c + kBigHalo + 1];
+        }
+        const int m0 = (kc * (kBigKC / 4) + hh * 2) % N;
+        const int m1 = m0 + 1 == N ? 0 : m0 + 1;
+        const float mf0 = mu_s[m0], mf1 = mu_s[m1];
+        const bool lag = act && !zero;
+        const bool has_l = lag && j > 0, has_r = lag && j < J - 1;
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+          const int m = q < 2 ? m0 : m1;
+          const float mf = q < 2 ? mf0 : mf1;
+          const bool pos = m >= N2;
+          v[2 * q] = fmaf(mf, (pos && has_l) ? up[q] : 0.f, v[2 * q]);
+          v[2 * q + 1] = fmaf(-mf, (!pos && has_r) ? dn[q] : 0.f, v[2 * q + 1]);
+        }
+        if (!act) {
+#pragma unroll
+          for (int i = 0; i < 8; i++) v[i] = 0.f;
         }
         if (KIND == 1) {
           *(float4 *)(stB + big_off(c, hh * 8, 4)) = make_float4(v[0], v[1], v[2], v[3]);
