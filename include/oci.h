@@ -45,7 +45,11 @@
  *       OCI_MX_OUTER_CVT=hw       compiler conversions in the FP64 refinement
  *       OCI_RB_FP64=inplace       FP64 red-black half sweeps in place
  *       OCI_RB_SHAPE=s|r,cb,P     pin the FP64 red-black shape
- *       OCI_TC_PIPE=0             one-tile-per-CTA tensor-core kernel
+ *       OCI_TC_BIG=0              tensor-core forms at 4NG <= 128: the persistent kernel with
+ *                                 the inverse resident in shared memory (not the streamed one)
+ *       OCI_TC_PIPE=0             with OCI_TC_BIG=0: the one-tile-per-CTA tensor-core kernel
+ *       OCI_DENSE_APPLY=lu        dense per-cell path: triangular solves with the LU
+ *                                 factors instead of the explicit inverse
  *       OCI_BATCH_SWEEP           pin the batched sweep form
  *       OCI_NO_GRAPH=1            host-driven loop instead of the CUDA graph
  *       OCI_TEST_SPIN_LIMIT=k     grid-barrier spin limit of the cooperative

@@ -1,29 +1,30 @@
-// oci_tc_big.cu -- tcgen05 block apply of the TF32 / BF16x3 mixed forms for cells
-// with more than 128 unknowns (128 < 4NG <= 512, e.g. S16 with 8 groups).
+// oci_tc_big.cu -- tcgen05 block apply of the TF32 / BF16x3 mixed forms, for any
+// number of unknowns per cell up to 4NG = 512 (e.g. S16 with 8 groups).
 //
 // The inner sweep of the mixed forms is delta^{i+1} = A~^{-1} (r + B delta^i) per
-// cell (spec: where cells share material, width and dt, the inverse of
-// the cell matrix of Eqs. Aj, scatter, fullOCIlhs is applied to all of their
-// right-hand sides as one dense GEMM).  For a tile of 128 cells of one type this
-// is, transposed so that the cells are the MMA's M and the unknowns its N,
+// cell (where cells share material, width and dt, the inverse of the cell
+// matrix of Eqs. Aj, scatter, fullOCIlhs is applied to all of their right-hand
+// sides as one dense GEMM).  For a tile of 128 cells of one type this is,
+// transposed so that the cells are the MMA's M and the unknowns its N,
 //   D[128 cells x n] = RHS[128 cells x n] . (A^{-1})^T,      n = 4NG <= 512,
 // with the accumulator in tensor memory (lane = cell, column = unknown; n
-// columns).  The inverse (1 MB per type in TF32) does not fit in shared memory:
-//   - the K dimension is walked in chunks of 32: per chunk one 1D bulk copy per
-//     N-tile of 256 unknowns brings that chunk of A^{-1} (32 KB, stored chunk
-//     by chunk in the K-major no-swizzle canonical layout) into shared memory,
-//     and two 2D tensor copies bring rows k .. k+31 of r and of the old
-//     correction (with a halo of 4 cells each side for the neighbours' inflow);
-//     all threads then build that chunk of the RHS (r + B delta, FP32 -> TF32 or
-//     BF16 hi/lo) next to it;
-//   - the MMAs of a chunk (M = 128 cells, N = 256 unknowns, one thread issues
-//     them, completion on an mbarrier) read the RHS chunk once per N-tile and
-//     each A^{-1} row once;
-//   - two stages: the MMAs of chunk k run while the copies and the RHS of chunk
-//     k+1 are prepared; the copies of chunk k+1 start as soon as chunk k-1's
-//     MMAs free their stage;
-//   - after the last chunk of a tile the CTA drains the accumulators
-//     (tcgen05.ld: one register per unknown, one lane per cell), forms delta
+// columns).  The inverse (1 MB per type in TF32 at n = 512) does not fit in
+// shared memory, so the K dimension is walked in chunks of 16:
+//   - per chunk one 1D bulk copy per N-tile of 256 unknowns brings that chunk of
+//     A^{-1} (stored chunk by chunk in the K-major no-swizzle canonical layout)
+//     into a stage of shared memory, and two 2D tensor copies bring rows
+//     k .. k+15 of r and of the old correction (with a halo of 4 cells each side
+//     for the neighbours' inflow) into one of two input buffers;
+//   - eight builder warps form that chunk of the RHS (r + B delta, FP32 -> TF32
+//     or BF16 hi/lo) in the stage next to the A^{-1} chunk;
+//   - one thread of a control warp issues the chunk's MMAs (M = 128 cells,
+//     N <= 256 unknowns per N-tile) and commits them to the stage's mbarrier;
+//     one thread of a second control warp issues the copies: a chunk's inputs
+//     as soon as the builders have consumed the buffer two chunks back, its
+//     A^{-1} chunk as soon as the MMAs three chunks back have freed the stage
+//     (three stages);
+//   - after the last chunk of a tile the builder warps drain the accumulators
+//     (tcgen05.ld: one register per unknown, one lane per cell), form delta
 //     and the FP32 norm partial; loads and stores are 128-byte rows of 32 cells.
 // One CTA per SM walks the tiles persistently; the norm, the stop rule and the
 // refinement decision are fused into the last CTA to finish.  Every wait is
@@ -452,7 +453,13 @@ size_t tc_big_smem(const Handle &h) {
   return need > floor_bytes ? need : floor_bytes;
 }
 
-bool tc_big_used(const Handle &h) { return 4 * h.N * h.G > 128; }
+// This kernel serves every size; OCI_TC_BIG=0 (a test hook) keeps the earlier
+// persistent form with the inverse resident in shared memory (k_tc_pipe) for 4NG <= 128.
+bool tc_big_used(const Handle &h) {
+  if (4 * h.N * h.G > 128) return true;
+  const char *e = hook_env("OCI_TC_BIG");
+  return !(e && e[0] == '0');
+}
 
 int tc_big_prepare(Handle &h) {
   // tensor maps of r (z32) and of the two correction buffers, [R][Jp] FP32, boxes of

@@ -104,6 +104,27 @@ def test_tensor_core_forms_match_fp64_oracle(prec, seed, J, N, G):
             assert np.abs(s.balance() - r["bal"]).max() <= 1e-10 * np.abs(r["bal"]).max()
 
 
+@pytest.mark.parametrize("pipe", ["1", "0"])
+@pytest.mark.parametrize("prec", [oci.TF32_IR, oci.BF16X3_IR])
+@pytest.mark.parametrize("seed,J,N,G", [(37, 300, 16, 1), (38, 257, 8, 2)])
+def test_tensor_core_resident_inverse_kernels_match_oracle(pipe, prec, seed, J, N, G, monkeypatch):
+    """The two tensor-core kernels that keep the inverse resident in shared
+    memory (4NG <= 128; persistent, and one tile per CTA) against the FP64
+    oracle, as the streamed kernel is above."""
+    monkeypatch.setenv("OCI_TC_BIG", "0")
+    monkeypatch.setenv("OCI_TC_PIPE", pipe)
+    p = _uniform_tiles(seed, J, N, G)
+    o = Oracle(p)
+    with oci.Solver(p, precision=prec) as s:
+        for k in range(2):
+            r = o.step(OCI)
+            st = s.step()
+            assert st["status"] == 0
+            assert st["iters"] <= r["iters"] + 12, (st["iters"], r["iters"])
+            assert rel(s.phi(), r["phi"]) < 1e-10
+            assert rel(s.psi(), r["Psi"]) < 1e-10
+
+
 def test_tensor_core_forms_reject_mixed_tiles():
     p = W.random_slab(36, 200, 8, 1)  # a different cell type in almost every cell
     with pytest.raises(oci.OCIError) as ei:
@@ -373,8 +394,9 @@ TC_BIG_CASES = [(41, 300, 16, 3), (42, 257, 16, 4), (43, 200, 10, 4), (44, 140, 
 @pytest.mark.parametrize("prec", [oci.TF32_IR, oci.BF16X3_IR])
 @pytest.mark.parametrize("seed,J,N,G", TC_BIG_CASES)
 def test_tensor_core_forms_more_than_128_unknowns_match_oracle(prec, seed, J, N, G):
-    """4NG = 192 (two M-tiles, zero rows), 256, 160 (five K-chunks), 512 (four
-    M-tiles): flux within 1e-10 of the FP64 oracle over three steps, ragged last tile."""
+    """4NG = 192 (one N-tile narrower than 256), 256, 160 (ten K-chunks of 16),
+    512 (two N-tiles of 256): flux within 1e-10 of the FP64 oracle over three
+    steps, ragged last tile."""
     p = _uniform_tiles(seed, J, N, G)
     o = Oracle(p)
     with oci.Solver(p, precision=prec) as s:
