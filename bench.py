@@ -313,7 +313,7 @@ def run_ours(args):
             # share one pass over the correction -- the recompute pass at the end of
             # an inner block is not counted); per FP64 refinement (and the initial
             # residual) Psi in/out, c, delta in, z out (32 B per unknown)
-            b_sweep = 6 if info_mx["inner_kernel"] == 9 else 12
+            b_sweep = 6 if info_mx["inner_kernel"] in (9, 10, 12) else 12
             step_bytes = (mx_sweeps * b_sweep + (mx_ref + args.steps) * 32) * p.unknowns / args.steps
             step_gbs = step_bytes / (mx_ms / args.steps * 1e-3) / 1e9
             mixed.append({

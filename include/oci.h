@@ -37,7 +37,7 @@
  *       OCI_AUTOTUNE=0            keep the default launch shapes (no timing)
  *       OCI_SWEEP_SHAPE=cb,P      pin the sweep shape (cells per block, angle chunks)
  *       OCI_SWEEP_REG=0|1         FP64 sweep: staged or register form only
- *       OCI_MX_INNER=plain|tma|reg|tiled|tiledp|tiledb|two|twoocc
+ *       OCI_MX_INNER=plain|tma|reg|tiled|tiledp|tiledb|two|twoocc|warp (or a comma list)
  *                                 FP32 inner sweep kernel of the mixed form
  *       OCI_MX_RB=1|2             red-black FP32 inner sweep, one or two sweeps per pass
  *       OCI_MX_MULTI=0            one inner sweep per launch in the graph
@@ -194,7 +194,8 @@ typedef struct {
                                 the tiles moved by 1D bulk copies (TMA), 7 red-black ordering,
                                 9 two inner sweeps per pass over the correction (temporal
                                 blocking), 10 the same built for more resident blocks per SM,
-                                11 red-black ordering with two sweeps per pass; -1 for the FP64
+                                11 red-black ordering with two sweeps per pass, 12 two sweeps per
+                                pass with one run of cells per warp (one group); -1 for the FP64
                                 form                                                              */
   double tuned_sweep_us;     /* measured time of one sweep with the chosen shape (0 if not tuned) */
   int32_t sweep_kernel;      /* FP64 form: 0 angles staged in shared memory (k_oci_sweep_t),

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liboci.so")
-SOURCES = ["oci_api.cu", "oci_sweep.cu", "oci_si.cu", "oci_dense.cu", "oci_mixed.cu", "oci_mixed_two.cu", "oci_mixed_rb2.cu", "oci_tc.cu", "oci_tc_big.cu", "oci_batch.cu", "oci_batch_host.cu", "oci_noalloc.cu", "oci_fourier.cu", "oci_gmres.cu"]
+SOURCES = ["oci_api.cu", "oci_sweep.cu", "oci_si.cu", "oci_dense.cu", "oci_mixed.cu", "oci_mixed_two.cu", "oci_mixed_warp.cu", "oci_mixed_rb2.cu", "oci_tc.cu", "oci_tc_big.cu", "oci_batch.cu", "oci_batch_host.cu", "oci_noalloc.cu", "oci_fourier.cu", "oci_gmres.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
          "--expt-relaxed-constexpr"]

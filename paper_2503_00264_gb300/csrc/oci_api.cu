@@ -333,26 +333,34 @@ static int autotune(Handle &h) {
             cands.push_back({kMxTiled2, cb, P});
             if (h.N == 16 && h.G == 1) cands.push_back({kMxTiled2Occ, cb, P});
           }
+          if (np == 4 && cb == 32 && mx_w2_supported(h)) cands.push_back({kMxWarp2, 32, P});
           if (mx_tb_smem(h, cb, P, mx_tables_floats(h) * 4 <= 64 * 1024) <= 200 * 1024)
             cands.push_back({kMxTiledB, cb, P});
         }
       }
     }
-  // OCI_MX_INNER=plain|tma|reg|tiled|tiledp|tiledb|two|twoocc restricts the FP32 inner sweep to one kernel (for profiling)
+  // OCI_MX_INNER=plain|tma|reg|tiled|tiledp|tiledb|two|twoocc|warp restricts the FP32 inner sweep to one kernel (for profiling)
   const char *only = hook_env("OCI_MX_INNER");
-  if (mx && only) {
-    const std::string o(only);
-    const int want = o == "tma"      ? kMxTma
+  if (mx && only) {  // a comma-separated list keeps several kernels (timed against one another)
+    std::vector<int> want;
+    std::string rest(only);
+    while (!rest.empty()) {
+      const size_t cut = rest.find(',');
+      const std::string o = rest.substr(0, cut);
+      rest = cut == std::string::npos ? "" : rest.substr(cut + 1);
+      want.push_back(o == "tma"      ? kMxTma
                      : o == "reg"    ? kMxReg
                      : o == "tiled"  ? kMxTiled
                      : o == "tiledp" ? kMxTiledP
                      : o == "tiledb" ? kMxTiledB
                      : o == "two"    ? kMxTiled2
                      : o == "twoocc" ? kMxTiled2Occ
-                                     : kMxPlain;
+                     : o == "warp"   ? kMxWarp2
+                                     : kMxPlain);
+    }
     std::vector<Cand> keep;
     for (auto &c : cands)
-      if (c.kind == want) keep.push_back(c);
+      if (std::find(want.begin(), want.end(), c.kind) != want.end()) keep.push_back(c);
     if (!keep.empty()) cands.swap(keep);
   }
   // OCI_SWEEP_REG=0|1 restricts the FP64 Jacobi sweep to the staged / register form
@@ -410,7 +418,9 @@ static int autotune(Handle &h) {
     apply(c);
     // the persistent tiled FP32 sweep runs as one multi-sweep cooperative launch in
     // the graph: time it that way (reps sweeps in one launch)
-    const bool multi = mx && (c.kind == kMxTiledP || c.kind == kMxTiled2 || c.kind == kMxTiled2Occ) && h.mx_multi;
+    const bool multi = mx &&
+                       (c.kind == kMxTiledP || c.kind == kMxTiled2 || c.kind == kMxTiled2Occ || c.kind == kMxWarp2) &&
+                       h.mx_multi;
     auto sweep = [&]() {
       if (mx) launch_mx_inner(h, cudaGraphConditionalHandle{}, 0);
       else launch_oci_sweep(h, cudaGraphConditionalHandle{}, 0);

@@ -221,12 +221,17 @@ constexpr int kSweepReg64 = 8;  // autotuner candidate kind of the FP64 register
 constexpr int kMxTiled2 = 9;    // tile-major, two inner sweeps per pass (temporal blocking)
 constexpr int kMxTiled2Occ = 10;  // the same built for more resident blocks per SM (S16, one group)
 constexpr int kMxRB2 = 11;        // red-black ordering, two sweeps per pass (colour-ordered tiles)
+constexpr int kMxWarp2 = 12;      // tile-major, two sweeps per pass, one run of cells per warp (one group)
 size_t mx_rb2_smem(const Handle &h, int T, int P, bool stage);
 // two-sweep-per-pass inner kernels (oci_mixed_two.cu, oci_mixed_rb2.cu)
 void launch_ms2_any(Handle &h, cudaGraphConditionalHandle cond, int use_cond, int max_sweeps);
 void launch_rb2_any(Handle &h, cudaGraphConditionalHandle cond, int use_cond, int max_sweeps);
 int mx_two_set_attributes();
 int mx_rb2_set_attributes();
+// warp-run two-sweep inner kernel (oci_mixed_warp.cu): one group, N = 8, 16, 32
+bool mx_w2_supported(const Handle &h);
+void launch_w2_any(Handle &h, cudaGraphConditionalHandle cond, int use_cond, int max_sweeps);
+int mx_w2_set_attributes();
 size_t mx_ms2_smem(const Handle &h, int T, int P, bool stage);
 size_t mx_tb_smem(const Handle &h, int T, int P, bool stage);
 size_t mx_tables_floats(const Handle &h);

@@ -45,7 +45,7 @@ __device__ __forceinline__ size_t fidx(int tsh, int R, size_t Jp, int r, int j) 
 int mx_tile_shift(const Handle &h) {
   const int sh = h.mx_cb == 16 ? 4 : h.mx_cb == 32 ? 5 : h.mx_cb == 64 ? 6 : 7;
   if (h.mx_kind == kMxTiled || h.mx_kind == kMxTiledP || h.mx_kind == kMxTiledB || h.mx_kind == kMxTiled2 ||
-      h.mx_kind == kMxTiled2Occ)
+      h.mx_kind == kMxTiled2Occ || h.mx_kind == kMxWarp2)
     return sh;
   if (h.mx_kind == kMxRB || h.mx_kind == kMxRB2) return sh | 0x100;
   return 0;
@@ -1773,7 +1773,9 @@ int mx_partials(const Handle &h) {
   mx_shape(h, cb, P);
   const int ntiles = (h.J + cb - 1) / cb;
   // two sweeps x two parities per block
-  return (h.mx_kind == kMxTiled2 || h.mx_kind == kMxTiled2Occ || h.mx_kind == kMxRB2) ? 4 * ntiles : ntiles;
+  return (h.mx_kind == kMxTiled2 || h.mx_kind == kMxTiled2Occ || h.mx_kind == kMxRB2 || h.mx_kind == kMxWarp2)
+             ? 4 * ntiles
+             : ntiles;
 }
 
 // One inner sweep including its norm reduction, stop rule and refinement
@@ -1817,6 +1819,11 @@ void launch_mx_inner(Handle &h, cudaGraphConditionalHandle cond, int use_cond) {
       else OCI_MX_TB(64, 8);
     }
 #undef OCI_MX_TB
+    return;
+  }
+  if (h.mx_kind == kMxWarp2) {  // cooperative; in the graph passes of two sweeps
+    const int ms = h.mx_tune_sweeps > 0 ? h.mx_tune_sweeps : (use_cond && h.mx_multi) ? (1 << 30) : 1;
+    launch_w2_any(h, cond, use_cond, ms);
     return;
   }
   if (h.mx_kind == kMxTiled2 || h.mx_kind == kMxTiled2Occ) {  // cooperative; in the graph passes of two sweeps

@@ -221,7 +221,9 @@ def test_fp32_multi_sweep_launch_matches_single_sweep(monkeypatch):
 
 @pytest.mark.parametrize("kernel,J,shape", [("two", 5000, "64,4"), ("two", 40000, "64,4"), ("two", 40000, "32,8"),
                                             ("two", 333, "32,4"), ("two", 64, "32,8"), ("twoocc", 40000, "32,4"),
-                                            ("twoocc", 5000, "32,8")])
+                                            ("twoocc", 5000, "32,8"), ("warp", 40000, "32,4"),
+                                            ("warp", 5000, "32,4"), ("warp", 333, "32,4"), ("warp", 64, "32,4"),
+                                            ("warp", 40, "32,4")])
 def test_fp32_two_sweep_passes_equal_one_sweep_launches(kernel, J, shape, monkeypatch):
     """Two inner sweeps per pass (each block walks a run of tiles, the second
     sweep's inflows from the first sweep's values held in shared memory, the
@@ -231,7 +233,10 @@ def test_fp32_two_sweep_passes_equal_one_sweep_launches(kernel, J, shape, monkey
     order of every sum are the same.  Runs
     of one tile (J = 5000: 79 tiles, one per block), of several tiles, a
     partial last tile, and a one-block slab; the first sweep of a pass ending
-    an inner block (refinement or stop) takes the recompute path."""
+    an inner block (refinement or stop) takes the recompute path.  The
+    warp-run kernel (each warp walks its own run of 8-cell groups, inflows
+    of the second sweep from a per-warp ring) the same way: runs of 1 to 14
+    groups, warps with empty runs (a 40-cell slab)."""
     monkeypatch.setenv("OCI_MX_INNER", kernel)
     monkeypatch.setenv("OCI_SWEEP_SHAPE", shape)
     p = W.random_slab(33, J, 16, 1).replace(tol=1e-11)
@@ -239,7 +244,7 @@ def test_fp32_two_sweep_passes_equal_one_sweep_launches(kernel, J, shape, monkey
     for multi in ("1", "0"):
         monkeypatch.setenv("OCI_MX_MULTI", multi)
         with oci.Solver(p, precision=oci.FP32_IR) as s:
-            assert s.info()["inner_kernel"] == {"two": 9, "twoocc": 10}[kernel]
+            assert s.info()["inner_kernel"] == {"two": 9, "twoocc": 10, "warp": 12}[kernel]
             sts = [s.step() for _ in range(3)]
             res[multi] = ([(t["iters"], t["refinements"], t["e"]) for t in sts], s.psi(), s.phi())
     assert res["1"][0] == res["0"][0]
@@ -249,6 +254,26 @@ def test_fp32_two_sweep_passes_equal_one_sweep_launches(kernel, J, shape, monkey
         r = o.step(OCI)
         assert abs(res["1"][0][k][0] - r["iters"]) <= 2
     assert rel(res["1"][2], r["phi"]) < 1e-10
+
+
+@pytest.mark.parametrize("seed,J,N", [(97, 1000, 8), (98, 257, 8), (99, 1000, 32), (100, 70, 32), (101, 17, 16),
+                                      (102, 20000, 8), (103, 9000, 32)])
+def test_fp32_warp_run_kernel_angle_counts(seed, J, N, monkeypatch):
+    """The warp-run two-sweep kernel at S8 (16 cells per warp step, two lanes
+    per cell) and S32 (4 cells, eight lanes): sweep counts within 2 of the
+    FP64 oracle's and flux within 1e-10 of it, on ragged slabs."""
+    monkeypatch.setenv("OCI_MX_INNER", "warp")
+    p = W.random_slab(seed, J, N, 1).replace(tol=1e-11)
+    o = Oracle(p)
+    with oci.Solver(p, precision=oci.FP32_IR) as s:
+        info = s.info()
+        assert (info["inner_kernel"], info["cells_per_block"], info["angle_chunks"]) == (12, 32, N // 4)
+        for k in range(3):
+            r = o.step(OCI)
+            st = s.step()
+            assert st["status"] == 0 and abs(st["iters"] - r["iters"]) <= 2, (st["iters"], r["iters"])
+            assert rel(s.phi(), r["phi"]) < 1e-10
+            assert rel(s.psi(), r["Psi"]) < 1e-10
 
 
 @pytest.mark.parametrize("seed,J,N,G", [(91, 1, 4, 1), (92, 33, 4, 2), (93, 257, 8, 1), (94, 129, 8, 4),
