@@ -14,13 +14,13 @@
 //     A^{-1} (stored chunk by chunk in the K-major no-swizzle canonical layout)
 //     into a stage of shared memory, and two 2D tensor copies bring rows
 //     k .. k+15 of r and of the old correction (with a halo of 4 cells each side
-//     for the neighbours' inflow) into one of two input buffers;
+//     for the neighbours' inflow) into one of three input buffers;
 //   - eight builder warps form that chunk of the RHS (r + B delta, FP32 -> TF32
 //     or BF16 hi/lo) in the stage next to the A^{-1} chunk;
 //   - one thread of a control warp issues the chunk's MMAs (M = 128 cells,
 //     N <= 256 unknowns per N-tile) and commits them to the stage's mbarrier;
 //     one thread of a second control warp issues the copies: a chunk's inputs
-//     as soon as the builders have consumed the buffer two chunks back, its
+//     as soon as the builders have consumed the buffer three chunks back, its
 //     A^{-1} chunk as soon as the MMAs three chunks back have freed the stage
 //     (three stages);
 //   - after the last chunk of a tile the builder warps drain the accumulators
@@ -53,6 +53,13 @@ constexpr long long kBigSpin = 1 << 22;
 constexpr int kBigHalo = 4;                                 // columns each side of the delta box (16 B)
 constexpr int kBigDW = kBigN + 2 * kBigHalo;                // delta box width
 constexpr int kBigInBytes = kBigKC * (kBigN + kBigDW) * 4;  // r box + delta box of one chunk
+// Input buffers: a chunk's copies are issued once the builders have consumed the
+// buffer kBigInBuf chunks back, so the builders can be at most kBigInBuf chunks
+// ahead of the copy thread's wait on rhs_full; with more buffers than stages they
+// could complete the same stage's next phase before that wait and it would miss
+// a phase.  Hence kBigInBuf <= kBigStages.
+constexpr int kBigInBuf = 3;
+static_assert(kBigInBuf <= kBigStages, "input buffers must not outnumber the stages");
 
 namespace {
 
@@ -103,7 +110,7 @@ __global__ void __launch_bounds__(kBigThreads, 1) k_tc_big(
   // have written a stage's RHS chunk; mma_done: a stage's MMAs have completed;
   // in_full: an input buffer's r / delta boxes have landed; tmem_empty: the
   // accumulators of the last tile have been drained
-  __shared__ __align__(8) uint64_t a_full[kBigStages], rhs_full[kBigStages], mma_done[kBigStages], in_full[2],
+  __shared__ __align__(8) uint64_t a_full[kBigStages], rhs_full[kBigStages], mma_done[kBigStages], in_full[kBigInBuf],
       tmem_empty;
   __shared__ uint32_t tslot;
   __shared__ float mu_s[kMaxN];
@@ -118,7 +125,7 @@ __global__ void __launch_bounds__(kBigThreads, 1) k_tc_big(
   const int n = 4 * N * G;
   unsigned char *sm = (unsigned char *)(((uintptr_t)smb_ + 1023) & ~(uintptr_t)1023);
   const size_t stage_bytes = (size_t)NT * kBigABlk + kBigRBlk;  // NT A^{-1} blocks, then the RHS block
-  unsigned char *in_base = sm + kBigStages * stage_bytes;        // two input buffers
+  unsigned char *in_base = sm + kBigStages * stage_bytes;        // kBigInBuf input buffers
   const int t = threadIdx.x, w = t >> 5, lane = t & 31;
   if (ds->done) return;  // uniform
   const bool zero = ds->refine || ds->blk_i == 0;
@@ -136,7 +143,8 @@ __global__ void __launch_bounds__(kBigThreads, 1) k_tc_big(
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&rhs_full[q])), "r"(kBigBuilders / 32));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&mma_done[q])), "r"(1));
     }
-    for (int q = 0; q < 2; q++) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&in_full[q])), "r"(1));
+    for (int q = 0; q < kBigInBuf; q++)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&in_full[q])), "r"(1));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&tmem_empty)), "r"(kBigBuilders / 32));
     asm volatile("fence.mbarrier_init.release.cluster;");
     s_fail = 0;
@@ -157,12 +165,12 @@ __global__ void __launch_bounds__(kBigThreads, 1) k_tc_big(
     // ------------------------------------------------ builders (and drain)
     const int c = t & (kBigN - 1), hh = t >> 7;  // cell c, rows hh*8 .. hh*8+7 of a chunk
     for (int g = 0, kc = 0, tile = blockIdx.x, s = 0, u3 = 0; g < n_chunks; g++) {
-      const int ib = g & 1;
+      const int ib = g % kBigInBuf;
       float *in_r = (float *)(in_base + (size_t)ib * kBigInBytes);  // [16][128]
       float *in_d = in_r + kBigKC * kBigN;                            // [16][136]
       unsigned char *stB = sm + (size_t)s * stage_bytes + (size_t)NT * kBigABlk;
       // this chunk's inputs have landed and the stage's MMAs of chunk g - 3 are done
-      bool ok = big_wait(su32(&in_full[ib]), (uint32_t)((g >> 1) & 1));
+      bool ok = big_wait(su32(&in_full[ib]), (uint32_t)((g / kBigInBuf) & 1));
       if (ok && g >= kBigStages) ok = big_wait(su32(&mma_done[s]), (uint32_t)((u3 - 1) & 1));
       if (!__all_sync(0xffffffffu, ok)) {  // warp-uniform: the warp leaves together
         s_fail = 1;
@@ -347,12 +355,12 @@ __global__ void __launch_bounds__(kBigThreads, 1) k_tc_big(
           if (n_m[q] > 0) big_wait(su32(&mma_done[q]), (uint32_t)((n_m[q] - 1) & 1));
       }
     } else {
-      int n_a[kBigStages] = {0, 0, 0}, n_in[2] = {0, 0};
+      int n_a[kBigStages] = {0, 0, 0}, n_in[kBigInBuf] = {0, 0, 0};
       // types of this CTA's tiles, read ahead: tau_of[i & 3] is the type of its i-th tile
       int tau_of[4] = {0, 0, 0, 0};
       for (int i = 0; i < 4 && i < my_tiles; i++) tau_of[i] = type[chunk_tile(i * NK) * kBigN];
       auto issue_in = [&](int g_) {
-        const int b_ = g_ & 1;
+        const int b_ = g_ % kBigInBuf;
         float *dst = (float *)(in_base + (size_t)b_ * kBigInBytes);
         const uint32_t bar = su32(&in_full[b_]);
         const int x0 = chunk_tile(g_) * kBigN, y0 = (g_ % NK) * kBigKC;
@@ -384,15 +392,15 @@ __global__ void __launch_bounds__(kBigThreads, 1) k_tc_big(
         }
         n_a[s_]++;
       };
-      for (int g = 0; g < 2 && g < n_chunks; g++) issue_in(g);
+      for (int g = 0; g < kBigInBuf && g < n_chunks; g++) issue_in(g);
       for (int g = 0; g < kBigStages && g < n_chunks; g++) issue_a(g);
       for (int g = 0, s = 0, u3 = 0; g < n_chunks; g++) {
-        // the builders have read chunk g's inputs: chunk g + 2's go into its buffer
+        // the builders have read chunk g's inputs: chunk g + 3's go into its buffer
         if (!big_wait(su32(&rhs_full[s]), (uint32_t)(u3 & 1))) {
           failed = true;
           break;
         }
-        if (g + 2 < n_chunks) issue_in(g + 2);
+        if (g + kBigInBuf < n_chunks) issue_in(g + kBigInBuf);
         if ((g + kBigStages) % NK == 0) {  // tile i + 3 gets its type read when tile i's last A copy is issued
           const int ti = (g + kBigStages) / NK + 3;
           if (ti < my_tiles) tau_of[ti & 3] = type[chunk_tile(ti * NK) * kBigN];
@@ -415,7 +423,7 @@ __global__ void __launch_bounds__(kBigThreads, 1) k_tc_big(
         // let the copies still in flight finish (bounded) before the CTA leaves
         for (int q = 0; q < kBigStages; q++)
           if (n_a[q] > 0) big_wait(su32(&a_full[q]), (uint32_t)((n_a[q] - 1) & 1));
-        for (int q = 0; q < 2; q++)
+        for (int q = 0; q < kBigInBuf; q++)
           if (n_in[q] > 0) big_wait(su32(&in_full[q]), (uint32_t)((n_in[q] - 1) & 1));
       }
     }
@@ -448,7 +456,7 @@ static int tc_big_nt(const Handle &h) { return (4 * h.N * h.G + kBigNT - 1) / kB
 static int tc_big_nk(const Handle &h) { return (4 * h.N * h.G + kBigKC - 1) / kBigKC; }
 
 size_t tc_big_smem(const Handle &h) {
-  const size_t need = kBigStages * ((size_t)tc_big_nt(h) * kBigABlk + kBigRBlk) + 2 * (size_t)kBigInBytes + 1024;
+  const size_t need = kBigStages * ((size_t)tc_big_nt(h) * kBigABlk + kBigRBlk) + kBigInBuf * (size_t)kBigInBytes + 1024;
   const size_t floor_bytes = 116 * 1024;  // one CTA per SM: its tensor memory never waits for another CTA's
   return need > floor_bytes ? need : floor_bytes;
 }
