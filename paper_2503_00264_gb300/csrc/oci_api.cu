@@ -997,7 +997,10 @@ static int build_graph(Handle &h, bool si, cudaGraphExec_t *out) {
   h.stream = saved;
   cudaStreamDestroy(cs);
   if (e != cudaSuccess) {
-    cudaGraphDestroy(graph);
+    // A capture that failed inside a conditional node's body leaves the parent
+    // graph in a state that the driver does not survive destroying (a failed
+    // kernel launch there crashed the process in cudaGraphDestroy): the graph
+    // is left to the process's exit and the error is returned.
     return cuda_fail(e, "capturing the convergence loop");
   }
   e = cudaGraphInstantiate(out, graph, 0);

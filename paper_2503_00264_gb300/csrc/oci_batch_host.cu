@@ -389,7 +389,10 @@ static int build_batch_graph(Batch &B) {
   }
   if (fork) cudaEventDestroy(fork);
   if (e != cudaSuccess) {
-    cudaGraphDestroy(graph);
+    // A capture that failed inside a conditional node's body leaves the parent
+    // graph in a state that the driver does not survive destroying (a failed
+    // kernel launch there crashed the process in cudaGraphDestroy): the graph
+    // is left to the process's exit and the error is returned.
     return cuda_fail(e, "capturing the batched convergence loop");
   }
   e = cudaGraphInstantiate(&B.graph, graph, 0);

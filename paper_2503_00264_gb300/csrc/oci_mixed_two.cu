@@ -329,7 +329,8 @@ int mx_two_set_attributes() {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(two-sweep FP32 inner sweep)");
   }
-  return mx_rb2_set_attributes();
+  const int e = mx_rb2_set_attributes();
+  return e != OCI_OK ? e : mx_w2_set_attributes();
 }
 
 }  // namespace oci
