@@ -237,6 +237,20 @@ int si_sweep(oci_handle *h, oci_stats *st);
  * commit; e_hist: [n] (host or device) receives e of each sweep, or NULL.
  * For timing and for parity at a fixed sweep count. */
 int oci_iterate(oci_handle *h, int32_t n, double *e_hist);
+
+/* One OCI sweep (Eq. oci, Algorithm 2) in two calls, so that a subdomain can
+ * sweep its interior while the lagged edge values of its neighbours are in
+ * flight (a spatial decomposition exchanges them before every sweep, Sec. 4):
+ * part 0 sweeps the cells of every block but the first and the last -- cells
+ * that read no incident flux -- and returns without waiting for the GPU;
+ * the caller may then change the incident fluxes (oci_set_boundary); part 1
+ * sweeps the first and the last block, forms e = ||Psi^{l+1} - Psi^l||_2 of
+ * the whole sweep in the same fixed order as oci_iterate, writes it to e_out
+ * (one double, host or device, or NULL) and waits for the GPU.  Together the
+ * two parts are oci_iterate(h, 1, e_out) bit for bit.  FP64, structured
+ * solver, Jacobi ordering, no acceleration; otherwise OCI_E_STATE, as is part 1
+ * without a preceding part 0 and part 0 twice.  e_out is ignored in part 0. */
+int oci_iterate_part(oci_handle *h, int32_t part, double *e_out);
 int si_iterate(oci_handle *h, int32_t n, double *e_hist);
 
 /* State access.  psi: [J][G][N][4]; phi: [J][G][4]; psi_prev: [J][G][N][2];

@@ -1050,6 +1050,7 @@ static int begin_iteration(Handle &h, int fixed, int cap) {
 }
 
 static int run_step(Handle &h, bool si, oci_stats *st) {
+  if (h.part_pending) return set_error("a sweep split by oci_iterate_part is not finished"), OCI_E_STATE;
   const size_t nPsi = (size_t)h.G * h.N * 4 * h.Jp;
   cudaStream_t s = h.stream;
   if (h.guess == OCI_GUESS_ZERO) CK(cudaMemsetAsync(h.Psi[h.h_ds->cur], 0, nPsi * 8, s));
@@ -1145,6 +1146,7 @@ static int run_step(Handle &h, bool si, oci_stats *st) {
 
 static int run_fixed(Handle &h, bool si, int n, double *e_hist) {
   if (n < 0) return set_error("n must be >= 0"), OCI_E_INVAL;
+  if (h.part_pending) return set_error("a sweep split by oci_iterate_part is not finished"), OCI_E_STATE;
   if (n > h.e_hist_cap) {
     cudaFree(h.e_hist);
     h.e_hist_cap = n;
@@ -1302,6 +1304,37 @@ int si_sweep(oci_handle *h, oci_stats *st) {
 int oci_iterate(oci_handle *h, int32_t n, double *e_hist) {
   GUARD(h);
   return run_fixed(*h, false, n, e_hist);
+}
+
+int oci_iterate_part(oci_handle *h, int32_t part, double *e_out) {
+  GUARD(h);
+  if (part != 0 && part != 1) return set_error("part must be 0 or 1"), OCI_E_INVAL;
+  if (h->precision != OCI_FP64 || h->solver != OCI_SOLVER_STRUCTURED || h->ordering != OCI_ORDER_JACOBI ||
+      h->accel != 0)
+    return set_error("oci_iterate_part: FP64 structured solver, Jacobi ordering, no acceleration"), OCI_E_STATE;
+  Handle &H = *h;
+  if (part == 0) {
+    if (H.part_pending) return set_error("oci_iterate_part: part 0 issued twice"), OCI_E_STATE;
+    int rc = begin_iteration(H, 1, H.e_hist_cap);
+    if (rc) return rc;
+    launch_step_const(H);
+    launch_oci_sweep_part(H, 0);
+    CK(cudaGetLastError());
+    H.part_pending = 1;
+    return OCI_OK;
+  }
+  if (!H.part_pending) return set_error("oci_iterate_part: part 1 without part 0"), OCI_E_STATE;
+  H.part_pending = 0;
+  launch_oci_sweep_part(H, 1);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(H.h_ds, H.ds, sizeof(DevState), cudaMemcpyDeviceToHost, H.stream));
+  if (e_out) CK(cudaMemcpyAsync(e_out, H.e_hist, 8, cudaMemcpyDefault, H.stream));
+  CK(cudaStreamSynchronize(H.stream));
+  H.last_iters = 1;
+  H.h_ds->done = 1;
+  CK(cudaMemcpyAsync(H.ds, H.h_ds, sizeof(DevState), cudaMemcpyHostToDevice, H.stream));
+  CK(cudaStreamSynchronize(H.stream));
+  return OCI_OK;
 }
 
 int si_iterate(oci_handle *h, int32_t n, double *e_hist) {

@@ -161,6 +161,7 @@ struct Handle {
   cudaGraphExec_t g_oci = nullptr, g_si = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   int last_iters = 0;
+  int part_pending = 0;  // oci_iterate_part: part 0 issued, part 1 not yet
   bool no_graph = false;           // OCI_NO_GRAPH=1: host-driven loop instead of the WHILE graph
   int tune_cb = 0, tune_P = 0;     // sweep launch shape picked by the autotuner (0: default)
   bool tune_reg = false;           // FP64 Jacobi sweep in the register form (k_oci_sweep_reg)
@@ -190,6 +191,7 @@ void launch_oci_apply(Handle &h, const double *in, double *out, const double *tc
 int gmres_solve(Handle &h, double tol_g, int max_sweeps, int &sweeps, double &e_last, int &status);
 void gmres_free(Handle &h);
 void launch_oci_sweep(Handle &h, cudaGraphConditionalHandle cond, int use_cond);
+void launch_oci_sweep_part(Handle &h, int part);  // FP64 Jacobi sweep as interior (0) and end blocks (1)
 const void *k_oci_sweep_ptr();
 const void *k_oci_sweep_rb_ptr();
 const void *k_oci_sweep_rbpp_ptr();

@@ -99,14 +99,17 @@ __global__ void __launch_bounds__(256) k_oci_sweep_t(
     const double *__restrict__ Linv, const double *__restrict__ Cin, const double *__restrict__ Mp,
     const double *__restrict__ w, const double *__restrict__ inc, const double *__restrict__ tc, double *Psi0,
     double *Psi1, DevState *ds, double *__restrict__ partials, unsigned *counter, double *e_hist,
-    cudaGraphConditionalHandle cond, int use_cond, int fuse, int nparts) {
+    cudaGraphConditionalHandle cond, int use_cond, int fuse, int nparts, int boff = 0, int bstride = 1) {
   extern __shared__ double sm[];
   __shared__ bool s_last;
   const int CB = blockDim.x;
   const int cl = threadIdx.x, gy = threadIdx.y;
   const int g = gy / P, ch = gy % P;
   const int NP = N / P, m0 = ch * NP;
-  const int j = RB ? 2 * (blockIdx.x * CB + cl) + color : blockIdx.x * CB + cl;
+  // Jacobi: logical block boff + blockIdx.x * bstride (one sweep may be split into
+  // the interior blocks and the two end blocks, see launch_oci_sweep_part)
+  const int lb = RB ? (int)blockIdx.x : boff + (int)blockIdx.x * bstride;
+  const int j = RB ? 2 * (blockIdx.x * CB + cl) + color : lb * CB + cl;
   if (ds->done) return;  // uniform across the grid
   const int cur = ds->cur;
   constexpr bool IP = RB && !PP;  // in place
@@ -213,7 +216,7 @@ __global__ void __launch_bounds__(256) k_oci_sweep_t(
     }
   }
   const double bs = block_sum(e2, red);
-  const int slot = blockIdx.x + (RB ? color * gridDim.x : 0);
+  const int slot = lb + (RB ? color * gridDim.x : 0);
   if (!fuse) {
     if (threadIdx.x == 0 && threadIdx.y == 0) partials[slot] = bs;
     return;
@@ -297,14 +300,16 @@ __global__ void __launch_bounds__(256) k_oci_sweep_reg(
     const double *__restrict__ inc, const double *__restrict__ tc, double *Psi0, double *Psi1, DevState *ds,
     double *__restrict__ partials, unsigned *counter, double *e_hist, cudaGraphConditionalHandle cond, int use_cond,
     int color, int nparts, const double *__restrict__ Win, const double *__restrict__ yc,
-    const double *__restrict__ mu) {
+    const double *__restrict__ mu, int fuse = 1, int boff = 0, int bstride = 1) {
   extern __shared__ double smrd[];
   __shared__ double red[8];
   __shared__ bool s_last;
   const int CB = blockDim.x, P = N / NP, G4 = 4 * G;
   const int cl = threadIdx.x, gy = threadIdx.y;
   const int g = gy / P, ch = gy % P, m0 = ch * NP;
-  const int j = RB ? 2 * (blockIdx.x * CB + cl) + color : blockIdx.x * CB + cl;
+  // Jacobi: logical block boff + blockIdx.x * bstride (as in k_oci_sweep_t)
+  const int lb = RB ? (int)blockIdx.x : boff + (int)blockIdx.x * bstride;
+  const int j = RB ? 2 * (blockIdx.x * CB + cl) + color : lb * CB + cl;
   const int tid = threadIdx.y * CB + threadIdx.x;
   const int nthr = CB * blockDim.y;
   if (ds->done) return;  // uniform across the grid
@@ -400,8 +405,8 @@ __global__ void __launch_bounds__(256) k_oci_sweep_reg(
     }
   }
   const double bs = block_sum(e2, red);
-  const int slot = blockIdx.x + (RB ? color * gridDim.x : 0);
-  if (RB && color == 0) {
+  const int slot = lb + (RB ? color * gridDim.x : 0);
+  if ((RB && color == 0) || !fuse) {
     if (tid == 0) partials[slot] = bs;
     return;
   }
@@ -488,6 +493,43 @@ void launch_oci_sweep(Handle &h, cudaGraphConditionalHandle cond, int use_cond) 
                                                             h.tt.Cin, h.tt.Mp, h.w, h.inc, h.tc, h.Psi[0], h.Psi[1],
                                                             h.ds, h.partials, h.counter, h.e_hist, cond, use_cond, 1,
                                                             c.grid);
+}
+
+// One FP64 Jacobi sweep in two launches: part 0 the blocks that hold neither cell
+// 0 nor cell J-1 (they read no incident flux), block partials only; part 1 the
+// first and the last block, then the fixed-order sum of all block partials, the
+// stop rule and the ping-pong flip.  Same cells, same partial slots and the same
+// sum as one launch, so the same bits; between the parts the incident fluxes may
+// change (a subdomain's halo arriving while its interior is swept).
+void launch_oci_sweep_part(Handle &h, int part) {
+  cudaGraphConditionalHandle none{};
+  const bool reg = h.tune_reg != 0;
+  const int cb = reg ? h.tune_cb : sweep_config(h).cells_per_block;
+  const int nb = (h.J + cb - 1) / cb;
+  int grid, boff, bstride, fuse;
+  if (part == 0) {
+    if (nb <= 2) return;  // no interior block
+    grid = nb - 2, boff = 1, bstride = 1, fuse = 0;
+  } else {
+    grid = nb == 1 ? 1 : 2, boff = 0, bstride = nb == 1 ? 1 : nb - 1, fuse = 1;
+  }
+  if (reg) {
+    const int P = h.tune_P, np = h.N / P;
+    const dim3 block(cb, h.G * P);
+    const size_t smem = sweep_reg_smem(h.G, cb, P);
+#define OCI_SWEEP_REG_PART(NP)                                                                                     k_oci_sweep_reg<NP><<<grid, block, smem, h.stream>>>(h.J, h.Jp, h.N, h.G, h.type, h.tt.Linv, h.tt.Cin, h.tt.Mp,                                                        h.w, h.inc, h.tc, h.Psi[0], h.Psi[1], h.ds, h.partials,                                                          h.counter, h.e_hist, none, 0, 0, nb, h.tt.Win, h.yc, h.mu,                                                         fuse, boff, bstride)
+    if (np == 2) OCI_SWEEP_REG_PART(2);
+    else if (np == 4) OCI_SWEEP_REG_PART(4);
+    else OCI_SWEEP_REG_PART(8);
+#undef OCI_SWEEP_REG_PART
+    return;
+  }
+  SweepCfg c = sweep_config(h);
+  dim3 block(c.cells_per_block, h.G * c.chunks);
+  k_oci_sweep_t<false><<<grid, block, c.smem, h.stream>>>(h.J, h.Jp, h.N, h.G, c.chunks, -1, h.type, h.tt.Linv,
+                                                          h.tt.Cin, h.tt.Mp, h.w, h.inc, h.tc, h.Psi[0], h.Psi[1],
+                                                          h.ds, h.partials, h.counter, h.e_hist, none, 0, fuse, nb,
+                                                          boff, bstride);
 }
 
 int sweep_partials(const Handle &h) {

@@ -11,7 +11,10 @@ interface (the paper's Sec. 4 outlook: subdomains exchanging every iteration):
 The iterates are those of single-domain OCI; only the summation order of e
 changes.  The local solver is any object with edges(left, right) (fills the
 two [G][N][2] buffers), set_boundary(l, r), iterate(1, e_hist) and commit() --
-the GPU `oci.Solver`, or a CPU stand-in in tests.  With a CUDA device (NCCL)
+the GPU `oci.Solver`, or a CPU stand-in in tests.  A solver that also has
+iterate_part(part, e_out) (the GPU solver: oci_iterate_part) sweeps its
+interior cells while the exchange is in flight -- they read no incident flux --
+and its two end cells once the halo has arrived.  With a CUDA device (NCCL)
 the edge buffers, the received incident fluxes and the norm stay on the GPU:
 oci_get_edges writes the send buffers, NCCL moves them, oci_set_boundary reads
 the receive buffers, and only the summed e (one scalar per sweep, for the stop
@@ -70,10 +73,9 @@ class HaloExchange:
         a numpy view of the same memory on the host."""
         return t.numpy() if t.device.type == "cpu" else t
 
-    def exchange(self):
-        """Send send_l to the left neighbour and send_r to the right one; return
-        (inflow from the left neighbour, inflow from the right neighbour) as
-        buffers, None at the slab ends."""
+    def start(self):
+        """Post the sends of send_l (to the left neighbour) and send_r (to the
+        right one) and the matching receives; return the pending requests."""
         import torch.distributed as dist
         ops = []
         if self.rank > 0:
@@ -83,13 +85,25 @@ class HaloExchange:
             ops.append(dist.P2POp(dist.irecv, self.recv_r, self.rank + 1))
             ops.append(dist.P2POp(dist.isend, self.send_r, self.rank + 1))
         try:
-            if ops:
-                for r in dist.batch_isend_irecv(ops):
-                    r.wait()
+            return dist.batch_isend_irecv(ops) if ops else []
         except RuntimeError as e:  # gloo/NCCL timeout or a peer that left
+            raise RankFailure(f"rank {self.rank}: edge exchange failed: {e}") from e
+
+    def finish(self, reqs):
+        """Wait for the requests of start(); return (inflow from the left
+        neighbour, inflow from the right neighbour) as buffers, None at the slab
+        ends."""
+        try:
+            for r in reqs:
+                r.wait()
+        except RuntimeError as e:
             raise RankFailure(f"rank {self.rank}: edge exchange failed: {e}") from e
         return (self.view(self.recv_l) if self.rank > 0 else None,
                 self.view(self.recv_r) if self.rank < self.world - 1 else None)
+
+    def exchange(self):
+        """start() and finish() back to back."""
+        return self.finish(self.start())
 
     def allreduce_sum(self, x: float) -> float:
         import torch.distributed as dist
@@ -112,16 +126,25 @@ class HaloExchange:
 
 
 def step(local, halo: HaloExchange, inc_left: Optional[np.ndarray], inc_right: Optional[np.ndarray],
-         tol: float, max_iter: int) -> dict:
-    """One time step of OCI over all ranks; returns dict(status, iters, e, rho)."""
+         tol: float, max_iter: int, overlap: bool = True) -> dict:
+    """One time step of OCI over all ranks; returns dict(status, iters, e, rho).
+    overlap: sweep the interior while the edge values are exchanged, where the
+    local solver can split a sweep (iterate_part); the iterates are the same."""
     e_prev, rho = 0.0, 0.0
     send_l, send_r, e_buf = halo.view(halo.send_l), halo.view(halo.send_r), halo.view(halo.e)
+    split = overlap and hasattr(local, "iterate_part")
     for l in range(max_iter):
         local.edges(send_l, send_r)
-        from_left, from_right = halo.exchange()
+        reqs = halo.start()
+        if split:
+            local.iterate_part(0)  # interior cells: no incident flux read
+        from_left, from_right = halo.finish(reqs)
         local.set_boundary(inc_left if from_left is None else from_left,
                            inc_right if from_right is None else from_right)
-        local.iterate(1, e_buf)
+        if split:
+            local.iterate_part(1, e_buf)  # the two end blocks, then e of the whole sweep
+        else:
+            local.iterate(1, e_buf)
         e = halo.norm_of_local()
         if not math.isfinite(e):
             return dict(status=-6, iters=l + 1, e=e, rho=rho)

@@ -25,7 +25,7 @@ SOLVER_AUTO, SOLVER_STRUCTURED, SOLVER_DENSE_LU = 0, 1, 2
 ORDER_JACOBI, ORDER_RED_BLACK = 0, 1
 SI_SEQUENTIAL, SI_SCAN = 0, 1
 
-EXPORTS = ["oci_setup", "oci_step", "oci_solve_transient", "si_sweep", "oci_iterate", "si_iterate",
+EXPORTS = ["oci_setup", "oci_step", "oci_solve_transient", "si_sweep", "oci_iterate", "oci_iterate_part", "si_iterate",
            "oci_get_psi", "oci_set_psi", "oci_get_phi", "oci_get_state", "oci_set_state", "oci_get_balance",
            "oci_set_boundary", "oci_set_ordering", "oci_set_si_mode", "oci_get_e_hist", "oci_get_edges", "oci_commit", "oci_get_info", "oci_destroy", "oci_last_error",
            "oci_probe_fp64_peak", "oci_batch_setup", "oci_batch_step", "oci_batch_size", "oci_batch_get_psi",
@@ -84,6 +84,7 @@ def load(path: Optional[str] = None):
     L.oci_solve_transient.argtypes = [vp, i32, vp, ctypes.POINTER(Stats)]
     L.si_sweep.argtypes = [vp, ctypes.POINTER(Stats)]
     L.oci_iterate.argtypes = [vp, i32, vp]
+    L.oci_iterate_part.argtypes = [vp, i32, vp]
     L.si_iterate.argtypes = [vp, i32, vp]
     for f in ("oci_get_psi", "oci_set_psi", "oci_get_phi", "oci_get_balance"):
         getattr(L, f).argtypes = [vp, vp]
@@ -280,6 +281,13 @@ class Solver:
         out = np.zeros(max(n, 1)) if e_hist is None else e_hist
         _check(self.L.oci_iterate(self.h, int(n), _ptr(out, writable=True)))
         return out[:n] if e_hist is None else out
+
+    def iterate_part(self, part: int, e_out=None):
+        """One sweep in two calls (oci_iterate_part): part 0 sweeps the interior
+        blocks and returns at once; part 1 sweeps the two end blocks and writes e
+        of the whole sweep into e_out (numpy or a torch tensor of one double, host
+        or device), if given."""
+        _check(self.L.oci_iterate_part(self.h, int(part), _ptr(e_out, writable=True) if e_out is not None else None))
 
     def si_iterate(self, n: int) -> np.ndarray:
         out = np.zeros(max(n, 1))

@@ -44,7 +44,32 @@ class OracleLocal:
         self.o.t += self.o.prob.dt
 
 
-def _worker(rank, world, port, seed, steps, fail_rank, q):
+class OracleSplitLocal(OracleLocal):
+    """The stand-in with the two-call sweep of the GPU solver (iterate_part):
+    the oracle cannot sweep part of a slab, so part 0 only checks the order of
+    the calls (it must come between the posting of the exchange and the new
+    incident fluxes) and part 1 does the whole sweep."""
+
+    def __init__(self, prob):
+        super().__init__(prob)
+        self.pending = False
+        self.parts = 0
+
+    def set_boundary(self, il, ir):
+        assert self.pending, "the incident fluxes must be set between part 0 and part 1"
+        super().set_boundary(il, ir)
+
+    def iterate_part(self, part, e_out=None):
+        assert self.pending == (part == 1)
+        self.pending = part == 0
+        self.parts += 1
+        if part == 1:
+            e = self.o.iterate(1)
+            if e_out is not None:
+                e_out[:1] = e
+
+
+def _worker(rank, world, port, seed, steps, fail_rank, q, split=False):
     import sys
     sys.path.insert(0, ROOT)
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
@@ -56,7 +81,7 @@ def _worker(rank, world, port, seed, steps, fail_rank, q):
         p = W.random_slab(seed, 37, 8, 2).replace(tol=1e-11)
         starts = D.split_cells(p.J, world)
         sub = D.subproblem(p, starts[rank], starts[rank + 1])
-        loc = OracleLocal(sub)
+        loc = OracleSplitLocal(sub) if split else OracleLocal(sub)
         halo = D.HaloExchange(rank, world, p.G, p.N)
         res = []
         for k in range(steps):
@@ -64,6 +89,7 @@ def _worker(rank, world, port, seed, steps, fail_rank, q):
                 raise SystemExit(3)  # this rank leaves between steps
             r = D.step(loc, halo, p.inc_left, p.inc_right, p.tol, 5000)
             res.append((r["status"], r["iters"]))
+        assert not split or loc.parts == 2 * sum(it for _, it in res)
         q.put((rank, "ok", res, loc.o.Psi.copy()))
     except D.RankFailure as e:
         q.put((rank, "rankfailure", str(e)[:200], None))
@@ -76,12 +102,13 @@ def _worker(rank, world, port, seed, steps, fail_rank, q):
             pass
 
 
-def _run(world, seed=5, steps=2, fail_rank=-1):
+def _run(world, seed=5, steps=2, fail_rank=-1, split=False):
     import multiprocessing as mp
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    ps = [ctx.Process(target=_worker, args=(r, world, port, seed, steps, fail_rank, q)) for r in range(world)]
+    ps = [ctx.Process(target=_worker, args=(r, world, port, seed, steps, fail_rank, q, split))
+          for r in range(world)]
     for p in ps:
         p.start()
     out = {}
@@ -93,14 +120,17 @@ def _run(world, seed=5, steps=2, fail_rank=-1):
     return out
 
 
+@pytest.mark.parametrize("split", [False, True])
 @pytest.mark.parametrize("world", [2, 3])
-def test_domain_decomposed_equals_single_domain(world):
+def test_domain_decomposed_equals_single_domain(world, split):
+    """Single-domain OCI over 2 and 3 ranks, with the plain sweep and with the
+    split sweep (interior during the exchange, ends after it)."""
     import oracle
     from paper_2503_00264_gb300 import workloads as W
     p = W.random_slab(5, 37, 8, 2).replace(tol=1e-11)
     o = oracle.Oracle(p)
     ref = [o.step() for _ in range(2)]
-    out = _run(world)
+    out = _run(world, split=split)
     psi = np.concatenate([out[r][2] for r in range(world)])
     for r in range(world):
         assert out[r][0] == "ok"

@@ -24,7 +24,7 @@ def _free_port():
     return p
 
 
-def _worker(rank, world, port, seed, J, N, G, steps, q):
+def _worker(rank, world, port, seed, J, N, G, steps, q, overlap=True):
     import sys
     sys.path.insert(0, ROOT)
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
@@ -43,7 +43,7 @@ def _worker(rank, world, port, seed, J, N, G, steps, q):
         res = []
         with oci.Solver(sub, stream=torch.cuda.current_stream().cuda_stream) as loc:
             for _ in range(steps):
-                r = D.step(loc, halo, p.inc_left, p.inc_right, p.tol, 5000)
+                r = D.step(loc, halo, p.inc_left, p.inc_right, p.tol, 5000, overlap=overlap)
                 res.append((r["status"], r["iters"]))
             q.put((rank, "ok", res, loc.psi(), loc.phi()))
     except Exception as e:  # reported to the parent, which fails the test
@@ -55,8 +55,11 @@ def _worker(rank, world, port, seed, J, N, G, steps, q):
             pass
 
 
+@pytest.mark.parametrize("overlap", [True, False])
 @pytest.mark.parametrize("seed,J,N,G", [(7, 301, 8, 2), (8, 1000, 16, 1)])
-def test_decomposed_gpu_solver_equals_single_domain_oracle(seed, J, N, G):
+def test_decomposed_gpu_solver_equals_single_domain_oracle(seed, J, N, G, overlap):
+    """With overlap every rank sweeps its interior (oci_iterate_part 0) while
+    the edge values are in flight and its two end blocks after they arrive."""
     import multiprocessing as mp
 
     import oracle
@@ -68,7 +71,8 @@ def test_decomposed_gpu_solver_equals_single_domain_oracle(seed, J, N, G):
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    ps = [ctx.Process(target=_worker, args=(r, world, port, seed, J, N, G, steps, q)) for r in range(world)]
+    ps = [ctx.Process(target=_worker, args=(r, world, port, seed, J, N, G, steps, q, overlap))
+          for r in range(world)]
     for pr in ps:
         pr.start()
     out = {}
