@@ -51,11 +51,11 @@ SAMPLE_J = 3072
 # block, angle chunks) the autotuner can pick.  A table of measured constants: it is valid for the
 # kernels as built here and is re-taken whenever the sweep kernels change.
 SWEEP_DRAM_BYTES_NCU = {
-    (0, 64, 2): 272.343552e6 + 98.906880e6,
-    (1, 16, 4): 278.945024e6 + 104.983808e6, (1, 16, 8): 278.031616e6 + 105.982080e6,
-    (1, 32, 2): 279.294592e6 + 104.551168e6, (1, 32, 4): 278.674176e6 + 105.039488e6,
-    (1, 32, 8): 278.053632e6 + 105.760896e6, (1, 64, 2): 279.072256e6 + 104.132864e6,
-    (1, 64, 4): 278.801792e6 + 104.745856e6,
+    (0, 64, 2): 272.535552e6 + 99.228544e6,
+    (1, 16, 4): 278.423552e6 + 105.256064e6, (1, 16, 8): 278.029312e6 + 106.006912e6,
+    (1, 32, 2): 286.496128e6 + 104.577792e6, (1, 32, 4): 278.290304e6 + 104.930688e6,
+    (1, 32, 8): 277.979264e6 + 105.660672e6, (1, 64, 2): 286.199680e6 + 104.362752e6,
+    (1, 64, 4): 278.013440e6 + 104.868352e6,
 }
 # FP64 issue rate of one SM: 2 DFMA per clock (GB300: 1.25 TFLOP/s FP64 = 152 SMs x 2 x 2 flops
 # x 2.07 GHz); the ALU roofline's peak = SMs x this x 2 flops x the maximum SM clock.
