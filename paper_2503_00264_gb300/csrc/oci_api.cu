@@ -691,7 +691,7 @@ static void free_handle(Handle *h) {
                   h->tt.Cin, h->tt.Mp,  h->tt.Kap,    h->tt.dx,     h->tt.sig,       h->si_z,      h->si_uin,
                   h->LU,     h->piv,    h->partials,  h->bal_partials, h->bal,       h->e_hist,    h->ds,
                   h->stage,  h->delta[0], h->delta[1], h->z32, h->w32, h->tt.Lco, h->tt.Linv32, h->tt.Cin32,
-                  h->tt.Mp32, h->tc_img, h->si_maps, h->si_segin, h->counter, h->psi_user, h->gbar, h->mu32,
+                  h->tt.Mp32, h->tc_img, h->tc_items, h->si_maps, h->si_segin, h->counter, h->psi_user, h->gbar, h->mu32,
                   h->yc,     h->tt.Win};
   for (void *p : ptrs)
     if (p) cudaFree(p);
@@ -861,15 +861,34 @@ static int setup_impl(const oci_problem *p, oci_handle *h) {
       h->mx_kmax = 48;
     }
     if (h->precision == OCI_TF32_IR || h->precision == OCI_BF16X3_IR) {
-      // one cell type per aligned tile of 128 cells
-      for (int j0 = 0; j0 < h->J; j0 += 128)
+      // The streamed kernel takes a tile of 128 cells once per cell type in it; the
+      // resident-inverse kernels (behind a test hook) need one type per tile.  Passes
+      // are bounded at twice the tiles, so that many small regions do not multiply the
+      // work, and the per-type inverses at 2^28 entries.
+      const bool streamed = tc_big_used(*h);
+      size_t passes = 0;
+      const size_t ntiles = (size_t)(h->J + 127) / 128;
+      for (int j0 = 0; j0 < h->J; j0 += 128) {
+        std::vector<int32_t> seen;
         for (int j = j0; j < std::min(h->J, j0 + 128); j++)
-          if (h->h_type[j] != h->h_type[j0]) {
-            set_error("the tensor-core forms need one cell type per aligned tile of 128 cells");
-            return OCI_E_INVAL;
-          }
+          if (std::find(seen.begin(), seen.end(), h->h_type[j]) == seen.end()) seen.push_back(h->h_type[j]);
+        passes += seen.size();
+        if (!streamed && seen.size() > 1) {
+          set_error("the resident-inverse tensor-core kernels need one cell type per aligned tile of 128 cells");
+          return OCI_E_INVAL;
+        }
+      }
+      if (passes > 2 * ntiles) {
+        set_error("the tensor-core forms take a 128-cell tile once per cell type in it; these cell types "
+                  "would need more than twice the tiles");
+        return OCI_E_INVAL;
+      }
       // dense A = L_c - S per type (Eqs. Aj, scatter, fullOCIlhs) and its inverse
       const int n = 4 * h->N * h->G, T = h->tt.n_types;
+      if ((size_t)T * n * n > ((size_t)1 << 28)) {
+        set_error("the tensor-core forms keep one dense inverse per cell type: too many types for this cell size");
+        return OCI_E_INVAL;
+      }
       std::vector<double> Ainv_all((size_t)T * n * n), A((size_t)n * n), Ai;
       for (int t = 0; t < T; t++) {
         std::fill(A.begin(), A.end(), 0.0);

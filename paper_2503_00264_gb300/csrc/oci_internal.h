@@ -133,6 +133,9 @@ struct Handle {
   int mx_kind = 0;                     // FP32 inner sweep picked by the autotuner: kMxPlain, kMxTma, kMxReg, kMxTiled
   unsigned char *tc_img = nullptr;     // [T] x (A^{-1} image(s) in the tcgen05 K-major layout)
   size_t tc_img_bytes = 0;             // bytes per type
+  int2 *tc_items = nullptr;            // streamed tcgen05 apply: (tile, cell type) work items
+  int tc_n_items = 0;
+  bool tc_mixed = false;               // some 128-cell tile holds more than one cell type
   // SI scratch
   double *si_z = nullptr;        // [G][N][4][Jp]   Linv * d0
   double *si_uin = nullptr;      // [G][N][2][Jp]   incoming edge of every cell

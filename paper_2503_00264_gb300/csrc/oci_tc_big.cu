@@ -33,6 +33,7 @@
 #include <cuda_bf16.h>
 #include <math.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "oci_device.cuh"
@@ -98,13 +99,17 @@ __host__ __device__ inline uint32_t big_off(int row, int k, int es) {
   return (uint32_t)((row >> 3) * (kBigKC * es / 16) * 128 + (k / kc4) * 128 + (row & 7) * 16 + (k % kc4) * es);
 }
 
-template <int KIND>  // 1 = TF32, 2 = BF16 x3
+// KIND: 1 = TF32, 2 = BF16 x3.  MIXED: some tile holds cells of more than one type
+// (work items from `items`); otherwise item i of a CTA is its i-th tile and
+// `items` is not read.
+template <int KIND, bool MIXED>
 __global__ void __launch_bounds__(kBigThreads, 1) k_tc_big(
     const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CUtensorMap tmD0,
     const __grid_constant__ CUtensorMap tmD1, int J, int Jp, int N, int G, int NT, int NK,
     const int32_t *__restrict__ type, const unsigned char *__restrict__ Aimg, const float *__restrict__ mu,
     const float *__restrict__ r32, float *D0, float *D1, DevState *ds, double *__restrict__ partials,
-    unsigned *counter, double *e_hist, cudaGraphConditionalHandle cond, int use_cond) {
+    unsigned *counter, double *e_hist, cudaGraphConditionalHandle cond, int use_cond,
+    const int2 *__restrict__ items, int n_items) {
   extern __shared__ __align__(1024) unsigned char smb_[];
   // a_full: a stage's A^{-1} chunk has landed; rhs_full: the eight builder warps
   // have written a stage's RHS chunk; mma_done: a stage's MMAs have completed;
@@ -154,9 +159,11 @@ __global__ void __launch_bounds__(kBigThreads, 1) k_tc_big(
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tslot;
-  const int ntiles = (J + kBigN - 1) / kBigN;
-  const int my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-  const int n_chunks = my_tiles * NK;  // chunk g: tile blockIdx.x + (g / NK) gridDim.x, K-chunk g % NK
+  // work items (tile, cell type): one per tile, or one per type present in a tile
+  // whose cells are not all of one type (then bit 30 of the type word is set); the
+  // CTA's i-th item is items[blockIdx.x + i gridDim.x]
+  const int my_items = (int)blockIdx.x < n_items ? (n_items - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  const int n_chunks = my_items * NK;  // chunk g: the CTA's item g / NK, K-chunk g % NK
   const int N2 = N / 2;
   float e2 = 0.f;
   bool failed = false;
@@ -164,7 +171,16 @@ __global__ void __launch_bounds__(kBigThreads, 1) k_tc_big(
   if (w < kBigBuilders / 32) {
     // ------------------------------------------------ builders (and drain)
     const int c = t & (kBigN - 1), hh = t >> 7;  // cell c, rows hh*8 .. hh*8+7 of a chunk
-    for (int g = 0, kc = 0, tile = blockIdx.x, s = 0, u3 = 0; g < n_chunks; g++) {
+    int it = blockIdx.x;
+    int2 wi = make_int2((int)blockIdx.x, 0), wn = wi;
+    if (MIXED && my_items > 0) wi = wn = items[it];
+    bool keep = true;  // the drained cell of this thread is of the item's type
+    for (int g = 0, kc = 0, tile = wi.x, s = 0, u3 = 0; g < n_chunks; g++) {
+      if (MIXED && kc == 0) {  // loads for this item's drain and the next item, well ahead of their use
+        if (it + (int)gridDim.x < n_items) wn = items[it + gridDim.x];
+        const int jd = tile * kBigN + 32 * (w & 3) + lane;
+        keep = !(wi.y >> 30) || (jd < J && type[jd] == (wi.y & 0x3FFFFFFF));
+      }
       const int ib = g % kBigInBuf;
       float *in_r = (float *)(in_base + (size_t)ib * kBigInBytes);  // [16][128]
       float *in_d = in_r + kBigKC * kBigN;                            // [16][136]
@@ -248,7 +264,7 @@ __global__ void __launch_bounds__(kBigThreads, 1) k_tc_big(
         asm volatile("tcgen05.fence::after_thread_sync;");
         const int q4 = w & 3, g2 = w >> 2;
         const int j = tile * kBigN + 32 * q4 + lane;
-        const bool act = j < J;
+        const bool act = j < J && keep;  // only this item's cells
         const int nb = n / 32;  // column blocks
         float dold[32], dnxt[32];
         auto load_old = [&](int b_, float *dst) {
@@ -288,7 +304,13 @@ __global__ void __launch_bounds__(kBigThreads, 1) k_tc_big(
       }
       if (++kc == NK) {
         kc = 0;
-        tile += gridDim.x;
+        it += gridDim.x;
+        if (MIXED) {
+          wi = wn;
+          tile = wi.x;
+        } else {
+          tile += gridDim.x;
+        }
       }
       if (++s == kBigStages) {
         s = 0;
@@ -298,7 +320,7 @@ __global__ void __launch_bounds__(kBigThreads, 1) k_tc_big(
   } else if (lane == 0) {
     // ------------------------------------------------ control: warp 8 issues the MMAs, warp 9 the copies
     const bool mma_role = w == kBigBuilders / 32;
-    auto chunk_tile = [&](int g_) { return (int)blockIdx.x + (g_ / NK) * (int)gridDim.x; };
+    auto item_at = [&](int i_) { return items[(int)blockIdx.x + i_ * (int)gridDim.x]; };
     if (mma_role) {
       const uint32_t fmt = KIND == 1 ? 2u : 1u;  // kind::tf32 operands TF32 / kind::f16 operands BF16
       // instruction descriptor without N: F32 accumulator, both operands K-major, M = 128
@@ -356,14 +378,20 @@ __global__ void __launch_bounds__(kBigThreads, 1) k_tc_big(
       }
     } else {
       int n_a[kBigStages] = {0, 0, 0}, n_in[kBigInBuf] = {0, 0, 0};
-      // types of this CTA's tiles, read ahead: tau_of[i & 3] is the type of its i-th tile
+      // this CTA's work items, read ahead: icache[i & 3] is its i-th (tile, type) --
+      // with one type per tile only the type, tau_of[i & 3], of its i-th tile
+      int2 icache[4] = {make_int2(0, 0), make_int2(0, 0), make_int2(0, 0), make_int2(0, 0)};
       int tau_of[4] = {0, 0, 0, 0};
-      for (int i = 0; i < 4 && i < my_tiles; i++) tau_of[i] = type[chunk_tile(i * NK) * kBigN];
+      auto tile_at = [&](int i_) { return (int)blockIdx.x + i_ * (int)gridDim.x; };
+      for (int i = 0; i < 4 && i < my_items; i++) {
+        if (MIXED) icache[i] = item_at(i);
+        else tau_of[i] = type[tile_at(i) * kBigN];
+      }
       auto issue_in = [&](int g_) {
         const int b_ = g_ % kBigInBuf;
         float *dst = (float *)(in_base + (size_t)b_ * kBigInBytes);
         const uint32_t bar = su32(&in_full[b_]);
-        const int x0 = chunk_tile(g_) * kBigN, y0 = (g_ % NK) * kBigKC;
+        const int x0 = (MIXED ? icache[(g_ / NK) & 3].x : tile_at(g_ / NK)) * kBigN, y0 = (g_ % NK) * kBigKC;
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kBigInBytes) : "memory");
         asm volatile(
             "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
@@ -379,7 +407,7 @@ __global__ void __launch_bounds__(kBigThreads, 1) k_tc_big(
       };
       auto issue_a = [&](int g_) {
         const int s_ = g_ % kBigStages;
-        const int ti = g_ / NK, tau_ = tau_of[ti & 3], kc_ = g_ % NK;
+        const int ti = g_ / NK, tau_ = MIXED ? icache[ti & 3].y & 0x3FFFFFFF : tau_of[ti & 3], kc_ = g_ % NK;
         unsigned char *dst = sm + (size_t)s_ * stage_bytes;
         const uint32_t bar = su32(&a_full[s_]);
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(NT * kBigABlk) : "memory");
@@ -401,9 +429,12 @@ __global__ void __launch_bounds__(kBigThreads, 1) k_tc_big(
           break;
         }
         if (g + kBigInBuf < n_chunks) issue_in(g + kBigInBuf);
-        if ((g + kBigStages) % NK == 0) {  // tile i + 3 gets its type read when tile i's last A copy is issued
+        if ((g + kBigStages) % NK == 0) {  // item i + 3 gets its type read when item i's last A copy is issued
           const int ti = (g + kBigStages) / NK + 3;
-          if (ti < my_tiles) tau_of[ti & 3] = type[chunk_tile(ti * NK) * kBigN];
+          if (ti < my_items) {
+            if (MIXED) icache[ti & 3] = item_at(ti);
+            else tau_of[ti & 3] = type[tile_at(ti) * kBigN];
+          }
         }
         // chunk g's MMAs are done: chunk g + 3's A^{-1} goes into its stage
         if (g + kBigStages < n_chunks) {
@@ -497,9 +528,30 @@ int tc_big_prepare(Handle &h) {
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r1 != CUDA_SUCCESS || r2 != CUDA_SUCCESS || r3 != CUDA_SUCCESS)
     return set_error("tensor maps of the tensor-core form could not be encoded"), OCI_E_CUDA;
+  // work items: a tile of 128 cells per cell type present in it (in the order of first
+  // appearance), so a region boundary inside a tile costs a second pass over that tile
+  std::vector<int2> items;
+  for (int t0 = 0; t0 < h.J; t0 += kBigN) {
+    const int t1 = std::min(h.J, t0 + kBigN);
+    std::vector<int> seen;
+    for (int j = t0; j < t1; j++)
+      if (std::find(seen.begin(), seen.end(), h.h_type[j]) == seen.end()) seen.push_back(h.h_type[j]);
+    for (int tau : seen) items.push_back(make_int2(t0 / kBigN, tau | (seen.size() > 1 ? 0x40000000 : 0)));
+  }
+  if (h.tc_items) cudaFree(h.tc_items);
+  h.tc_items = nullptr;
+  cudaError_t ei = cudaMalloc(&h.tc_items, items.size() * sizeof(int2));
+  if (ei == cudaSuccess)
+    ei = cudaMemcpyAsync(h.tc_items, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice, h.stream);
+  if (ei == cudaSuccess) ei = cudaStreamSynchronize(h.stream);
+  if (ei != cudaSuccess) return cuda_fail(ei, "tensor-core work items");
+  h.tc_n_items = (int)items.size();
+  h.tc_mixed = items.size() > (size_t)((h.J + kBigN - 1) / kBigN);
   const int sm = (int)tc_big_smem(h);
-  cudaError_t e = cudaFuncSetAttribute(k_tc_big<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tc_big<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  cudaError_t e = cudaSuccess;
+  for (const void *k : {(const void *)k_tc_big<1, false>, (const void *)k_tc_big<2, false>,
+                        (const void *)k_tc_big<1, true>, (const void *)k_tc_big<2, true>})
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_tc_big)");
   return OCI_OK;
 }
@@ -508,26 +560,31 @@ int tc_big_grid(const Handle &h) {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int ntiles = (h.J + kBigN - 1) / kBigN;
-  return ntiles < sms ? ntiles : sms;
+  return h.tc_n_items < sms ? h.tc_n_items : sms;
 }
 
 void launch_tc_big(Handle &h, cudaGraphConditionalHandle cond, int use_cond) {
   const size_t smem = tc_big_smem(h);
   const int grid = tc_big_grid(h), NT = tc_big_nt(h), NK = tc_big_nk(h);
-  if (h.precision == OCI_TF32_IR)
-    k_tc_big<1><<<grid, kBigThreads, smem, h.stream>>>(h.tm_bg_r, h.tm_bg_d[0], h.tm_bg_d[1], h.J, h.Jp, h.N, h.G, NT, NK, h.type, h.tc_img, h.mu32, h.z32,
-                                                        h.delta[0], h.delta[1], h.ds, h.partials, h.counter,
-                                                        h.e_hist, cond, use_cond);
-  else
-    k_tc_big<2><<<grid, kBigThreads, smem, h.stream>>>(h.tm_bg_r, h.tm_bg_d[0], h.tm_bg_d[1], h.J, h.Jp, h.N, h.G, NT, NK, h.type, h.tc_img, h.mu32, h.z32,
-                                                        h.delta[0], h.delta[1], h.ds, h.partials, h.counter,
-                                                        h.e_hist, cond, use_cond);
+#define OCI_TC_BIG_LAUNCH(K, M)                                                                                     \
+  k_tc_big<K, M><<<grid, kBigThreads, smem, h.stream>>>(h.tm_bg_r, h.tm_bg_d[0], h.tm_bg_d[1], h.J, h.Jp, h.N, h.G, \
+                                                        NT, NK, h.type, h.tc_img, h.mu32, h.z32, h.delta[0],          \
+                                                        h.delta[1], h.ds, h.partials, h.counter, h.e_hist, cond,      \
+                                                        use_cond, h.tc_items, h.tc_n_items)
+  const bool tf = h.precision == OCI_TF32_IR;
+  if (h.tc_mixed) {
+    if (tf) OCI_TC_BIG_LAUNCH(1, true);
+    else OCI_TC_BIG_LAUNCH(2, true);
+  } else {
+    if (tf) OCI_TC_BIG_LAUNCH(1, false);
+    else OCI_TC_BIG_LAUNCH(2, false);
+  }
+#undef OCI_TC_BIG_LAUNCH
 }
 
 // Host: the per-type inverses in the chunk-major layout the kernel streams:
 // block ((type * NT + nt) * NK + kc) holds rows 256 nt .. 256 nt + 255 (unknowns)
-// and columns 32 kc .. 32 kc + 31 of A^{-1} (zero beyond n), TF32 -- or BF16 hi,
+// and columns 16 kc .. 16 kc + 15 of A^{-1} (zero beyond n), TF32 -- or BF16 hi,
 // then BF16 lo -- in the canonical K-major layout of big_off.  `round_tf32`,
 // `bf16_bits` and `bf16_value` are the host roundings of the small form.
 int tc_big_build_images(Handle &h, const std::vector<double> &Ainv, float (*round_tf32)(float),

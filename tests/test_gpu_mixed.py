@@ -77,7 +77,8 @@ def test_fp32_ir_noconv_keeps_last_iterate():
 
 def _uniform_tiles(seed, J, N, G, region=128):
     """Random slab whose material and width are constant over aligned blocks of
-    `region` cells (one cell type per 128-cell tile, as the tensor-core forms need)."""
+    `region` cells (with region 128: one cell type per 128-cell tile, as the
+    resident-inverse tensor-core kernels need)."""
     p = W.random_slab(seed, J, N, G)
     blk = np.arange(J) // region
     return p.replace(mat=(blk % p.n_mat).astype(np.int32), dx=p.dx[(blk * region) % J].copy(), tol=1e-11)
@@ -125,11 +126,38 @@ def test_tensor_core_resident_inverse_kernels_match_oracle(pipe, prec, seed, J, 
             assert rel(s.psi(), r["Psi"]) < 1e-10
 
 
-def test_tensor_core_forms_reject_mixed_tiles():
-    p = W.random_slab(36, 200, 8, 1)  # a different cell type in almost every cell
+def test_tensor_core_forms_reject_mixed_tiles(monkeypatch):
+    """A different cell type in almost every cell would need a pass per cell over
+    each tile: rejected.  Region boundaries inside tiles are taken by the streamed
+    kernel but not by the resident-inverse kernels (test hook)."""
+    p = W.random_slab(36, 200, 8, 1)
     with pytest.raises(oci.OCIError) as ei:
         oci.Solver(p, precision=oci.TF32_IR)
     assert ei.value.code == oci.E_INVAL
+    monkeypatch.setenv("OCI_TC_BIG", "0")
+    with pytest.raises(oci.OCIError) as ei:
+        oci.Solver(_uniform_tiles(39, 300, 8, 1, region=100), precision=oci.TF32_IR)
+    assert ei.value.code == oci.E_INVAL
+
+
+@pytest.mark.parametrize("prec", [oci.TF32_IR, oci.BF16X3_IR])
+@pytest.mark.parametrize("seed,J,N,G,region", [(46, 500, 16, 1, 100), (47, 700, 16, 3, 180), (48, 333, 16, 8, 100),
+                                               (49, 129, 8, 2, 100)])
+def test_tensor_core_forms_with_regions_inside_tiles_match_oracle(prec, seed, J, N, G, region):
+    """Region boundaries that fall inside 128-cell tiles (regions of 100 and 180
+    cells): the streamed kernel takes such a tile once per cell type in it and
+    keeps each pass's cells; flux within 1e-10 of the FP64 oracle over three steps
+    at 64, 192, 512 and 32 unknowns per cell."""
+    p = _uniform_tiles(seed, J, N, G, region=region)
+    o = Oracle(p)
+    with oci.Solver(p, precision=prec) as s:
+        for k in range(3):
+            r = o.step(OCI)
+            st = s.step()
+            assert st["status"] == 0
+            assert st["iters"] <= r["iters"] + 12, (st["iters"], r["iters"])
+            assert rel(s.phi(), r["phi"]) < 1e-10
+            assert rel(s.psi(), r["Psi"]) < 1e-10
 
 
 @pytest.mark.parametrize("prec", [oci.TF32_IR, oci.BF16X3_IR])
