@@ -93,7 +93,12 @@ enum {
  * iterate Psi (delta^{i+1} = A~^{-1}(r + B delta^i), r = c + B Psi - A Psi in
  * FP64) and fold delta into Psi with a fresh FP64 residual every few sweeps
  * (defect correction).  In exact arithmetic the iterates, and so the norm and
- * the stop rule, are those of the FP64 form; the fixed point is the FP64 one. */
+ * the stop rule, are those of the FP64 form; the fixed point is the FP64 one.
+ * The tensor-core forms (TF32_IR, BF16X3_IR) keep one dense inverse per cell
+ * type (4NG <= 512) and apply it to tiles of 128 consecutive cells; a tile with
+ * several cell types is taken once per type.  oci_setup returns OCI_E_INVAL
+ * when that would more than double the tiles' work or the inverses would
+ * exceed 2^28 entries (cell types that change from cell to cell). */
 
 /* initial iterate of every time step (oci_problem.guess) */
 enum {
