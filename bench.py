@@ -770,8 +770,82 @@ def cmd_profile(argv):
               f"{e0.elapsed_time(e1) / a.sweeps * 1e3:.1f} us/sweep")
 
 
+def cmd_decompose(argv):
+    """The benchmark slab split into contiguous cell ranges over the ranks (the
+    spatial decomposition of the paper's Sec. 4 outlook,
+    paper_2503_00264_gb300.distributed): every rank sweeps its range with the GPU
+    solver -- its interior while the edge values are exchanged, its two end
+    blocks after -- and the squared norms are summed every sweep.  Strong
+    scaling: the total work is fixed.  Launch one rank per GPU (torchrun, NCCL);
+    --backend gloo runs the ranks on one GPU with the exchange through the host.
+    Rank 0 prints one JSON line."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_2503_00264_gb300 import distributed as D
+    from paper_2503_00264_gb300 import oci
+    ap = argparse.ArgumentParser(prog="bench.py decompose")
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=1)
+    ap.add_argument("--backend", default="nccl", choices=["nccl", "gloo"])
+    ap.add_argument("--J", type=int, default=2 ** 18)
+    ap.add_argument("--c", type=float, default=0.9)
+    ap.add_argument("--tau", type=float, default=0.1)
+    ap.add_argument("--no-overlap", action="store_true")
+    a = ap.parse_args(argv)
+    rank, world, local = dist_env()
+    if "MASTER_ADDR" not in os.environ:  # one rank started without a launcher
+        import socket
+        so = socket.socket()
+        so.bind(("127.0.0.1", 0))
+        os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(so.getsockname()[1]), RANK="0", WORLD_SIZE="1")
+        so.close()
+    torch.cuda.set_device(local if a.backend == "nccl" else 0)
+    D.init_process_group(a.backend, timeout_s=600.0)
+    p = W.slab_3region(c=a.c, tau=a.tau, J=a.J)
+    starts = D.split_cells(p.J, world)
+    sub = D.subproblem(p, starts[rank], starts[rank + 1])
+    halo = D.HaloExchange(rank, world, p.G, p.N, device="cuda" if a.backend == "nccl" else "cpu")
+    stream = torch.cuda.current_stream()
+    overlap = not a.no_overlap
+
+    def steps(n):
+        its = 0
+        for _ in range(n):
+            r = D.step(loc, halo, p.inc_left, p.inc_right, p.tol, p.max_iter, overlap=overlap)
+            if r["status"] != 0:
+                raise RuntimeError(f"rank {rank}: decomposed step ended with status {r['status']}")
+            its += r["iters"]
+        return its
+
+    with oci.Solver(sub, stream=stream.cuda_stream) as loc:
+        steps(a.warmup)
+        dist.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sweeps = steps(a.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        dist.barrier()
+        t = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64,
+                         device="cuda" if a.backend == "nccl" else "cpu")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    if rank == 0:
+        line = {"metric": METRIC, "value": p.unknowns * sweeps / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
+                "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True,
+                "scaling": "strong", "dtype": "f64", "data": "synthetic", "mode": "decompose",
+                "sweeps_per_step": sweeps / a.steps,
+                "config": {"workload": p.name, "J": p.J, "N": p.N, "G": p.G, "c": a.c, "tau": a.tau, "tol": p.tol,
+                           "parallelism": f"spatial decomposition over {world} ranks ({a.backend})",
+                           "overlap": overlap, "cells_per_rank": [starts[r + 1] - starts[r] for r in range(world)]}}
+        print(json.dumps(line), flush=True)
+    dist.destroy_process_group()
+
+
 if __name__ == "__main__":
-    sub = {"profile": cmd_profile, "grid": cmd_grid, "table2": cmd_table2}
+    sub = {"profile": cmd_profile, "grid": cmd_grid, "table2": cmd_table2, "decompose": cmd_decompose}
     if len(sys.argv) > 1 and sys.argv[1] in sub:
         sub[sys.argv[1]](sys.argv[2:])
     else:

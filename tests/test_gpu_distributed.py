@@ -90,3 +90,30 @@ def test_decomposed_gpu_solver_equals_single_domain_oracle(seed, J, N, G, overla
     phi = np.concatenate([out[r][3] for r in range(world)])
     assert np.abs(psi - o.Psi).max() <= 1e-11 * np.abs(o.Psi).max()
     assert np.abs(phi - ref[-1]["phi"]).max() <= 1e-12 * np.abs(ref[-1]["phi"]).max()
+
+
+def test_bench_decompose_mode_two_ranks_on_one_gpu():
+    """bench.py decompose launched by torchrun as two gloo ranks on the one GPU:
+    one JSON line from rank 0 whose sweeps per step are those of the
+    single-domain solver within one (only the norm's summation order differs)."""
+    import json
+    import subprocess
+    import sys
+
+    from paper_2503_00264_gb300 import oci
+    from paper_2503_00264_gb300 import workloads as W
+    J, steps = 4096, 2
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes", "1", "--nproc-per-node", "2",
+           "--master-addr", "127.0.0.1", "--master-port", str(_free_port()), os.path.join(ROOT, "bench.py"),
+           "decompose", "--backend", "gloo", "--J", str(J), "--steps", str(steps), "--warmup", "1"]
+    r = subprocess.run(cmd, capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1, r.stdout[-2000:]
+    d = json.loads(lines[0])
+    assert d["n_gpus"] == 2 and d["scaling"] == "strong" and d["mode"] == "decompose" and d["value"] > 0
+    assert d["config"]["overlap"] is True and d["config"]["cells_per_rank"] == [J // 2, J // 2]
+    p = W.slab_3region(c=0.9, tau=0.1, J=J)
+    with oci.Solver(p) as s:
+        its = [s.step()["iters"] for _ in range(1 + steps)][1:]
+    assert abs(d["sweeps_per_step"] - sum(its) / steps) <= 1.0, (d["sweeps_per_step"], its)
