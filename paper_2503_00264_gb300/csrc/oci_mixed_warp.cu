@@ -10,22 +10,23 @@
 // Lanes: P = N/4 lanes per cell (four angles each), CW = 32/P cells per warp
 // step; lane = ch * CW + c holds cell c of the step, angles 4 ch .. 4 ch + 3.
 // The angular sum y is a butterfly over the P lanes of a cell (warp shuffles),
-// so a cell solve needs no block barrier and no shared memory beyond the
-// per-type tables.  Each warp owns a contiguous run of steps (groups of CW
-// cells) [k0, k1) and walks it left to right: at step k it computes
-// delta^{i+1} of group k from delta^i in global memory, then delta^{i+2} of
-// group k-1, whose lagged inflows are delta^{i+1} of its neighbours:
+// so a cell solve needs no block barrier.  Each warp owns a contiguous run of
+// steps (groups of CW cells) [k0, k1) and walks it left to right: at step k it
+// computes delta^{i+1} of group k from delta^i in global memory, then
+// delta^{i+2} of group k-1, whose lagged inflows are delta^{i+1} of its
+// neighbours, read from a per-warp ring in shared memory that holds
+// delta^{i+1} of groups k, k-1 and k-2:
 //   - mu > 0 (corners 1, 3 of cell j-1): the lane one to the left, or for the
-//     group's first cell the last cell of group k-2 (kept in registers);
+//     group's first cell the last cell of group k-2;
 //   - mu < 0 (corners 0, 2 of cell j+1): the lane one to the right, or for the
-//     group's last cell the first cell of group k (just computed).
+//     group's last cell the first cell of group k.
 // delta^{i+1} of the two cells just outside the run is recomputed by the warp
-// before the walk, so warps never wait on one another inside a pass.  A pass
-// reads z and delta^i once and writes delta^{i+2} once (12 bytes per unknown
-// per two sweeps); z and delta^{i+1} of group k-1 stay in registers.  The
-// norms, the stop rule and the refinement decision follow the two-sweep tiled
-// kernel (a grid barrier per pass; every block applies the stop rule to the
-// fixed-order sum of the partials).
+// before the walk (a fourth ring slot), so warps never wait on one another
+// inside a pass.  A pass reads z and delta^i once and writes delta^{i+2} once
+// (12 bytes per unknown per two sweeps); z of group k-1 stays in registers.
+// The norms, the stop rule and the refinement decision follow the two-sweep
+// tiled kernel (a grid barrier per pass; every block applies the stop rule to
+// the fixed-order sum of the partials).
 #include <math.h>
 
 #include <algorithm>
@@ -377,7 +378,8 @@ void launch_w2(Handle &h, cudaGraphConditionalHandle cond, int use_cond, int max
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mx_inner_w2<N, OCC>, kW2Threads, smem);
   constexpr int CW = 32 / (N / kW2NP);
   const int ngr = (h.J + CW - 1) / CW;
-  const int grid = std::max(1, std::min(sms * per, (ngr + kW2Warps - 1) / kW2Warps));
+  // no block resident (per = 0) gives an empty grid: the launch is refused, the tuner skips the kernel
+  const int grid = std::min(sms * per, (ngr + kW2Warps - 1) / kW2Warps);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(kW2Threads);
