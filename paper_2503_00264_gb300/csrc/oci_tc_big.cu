@@ -26,8 +26,11 @@
 //   - after the last chunk of a tile the builder warps drain the accumulators
 //     (tcgen05.ld: one register per unknown, one lane per cell), form delta
 //     and the FP32 norm partial; loads and stores are 128-byte rows of 32 cells.
-// One CTA per SM walks the tiles persistently; the norm, the stop rule and the
-// refinement decision are fused into the last CTA to finish.  Every wait is
+// One CTA per SM walks the tiles persistently; a tile whose cells are of more
+// than one type (a region boundary inside it) is taken once per type, each pass
+// keeping only its own cells (work items (tile, type), a separate instantiation).
+// The norm, the stop rule and the refinement decision are fused into the last
+// CTA to finish.  Every wait is
 // bounded: on a timeout the CTA waits (bounded) for its copies and MMAs in
 // flight, frees its tensor memory and records OCI_E_TIMEOUT.
 #include <cuda_bf16.h>
