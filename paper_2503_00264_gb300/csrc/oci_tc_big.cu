@@ -63,6 +63,7 @@ constexpr int kBigInBytes = kBigKC * (kBigN + kBigDW) * 4;  // r box + delta box
 // could complete the same stage's next phase before that wait and it would miss
 // a phase.  Hence kBigInBuf <= kBigStages.
 constexpr int kBigInBuf = 3;
+constexpr int kBigStash = 256;  // first tensor-memory column of the old correction (n <= 256)
 static_assert(kBigInBuf <= kBigStages, "input buffers must not outnumber the stages");
 
 namespace {
@@ -140,7 +141,11 @@ __global__ void __launch_bounds__(kBigThreads, 1) k_tc_big(
   const int dcur = ds->dcur;
   const float *__restrict__ Din = dcur ? D1 : D0;
   float *__restrict__ Dout = dcur ? D0 : D1;
-  const uint32_t cols = n <= 256 ? 256u : 512u;  // one column per unknown
+  // one column per unknown; with n <= 256 the old correction of the tile's cells is
+  // also kept in tensor memory (columns kBigStash ..), stored by the builders as the
+  // chunks arrive, so the drain reads it there instead of from HBM
+  const uint32_t cols = 512u;
+  const bool stash = n <= kBigNT;
   if (w == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tslot)), "r"(cols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -188,9 +193,15 @@ __global__ void __launch_bounds__(kBigThreads, 1) k_tc_big(
       float *in_r = (float *)(in_base + (size_t)ib * kBigInBytes);  // [16][128]
       float *in_d = in_r + kBigKC * kBigN;                            // [16][136]
       unsigned char *stB = sm + (size_t)s * stage_bytes + (size_t)NT * kBigABlk;
-      // this chunk's inputs have landed and the stage's MMAs of chunk g - 3 are done
+      // this chunk's inputs have landed and the stage's MMAs of chunk g - 3 are done; a new
+      // tile's old-correction copy in tensor memory waits until every builder warp has
+      // drained the previous tile (a warp drains columns its partner warp stored)
       bool ok = big_wait(su32(&in_full[ib]), (uint32_t)((g / kBigInBuf) & 1));
       if (ok && g >= kBigStages) ok = big_wait(su32(&mma_done[s]), (uint32_t)((u3 - 1) & 1));
+      if (ok && stash && kc == 0 && g > 0) {
+        ok = big_wait(su32(&tmem_empty), (uint32_t)(((g / NK) - 1) & 1));
+        asm volatile("tcgen05.fence::after_thread_sync;");
+      }
       if (!__all_sync(0xffffffffu, ok)) {  // warp-uniform: the warp leaves together
         s_fail = 1;
         failed = true;
@@ -248,6 +259,17 @@ __global__ void __launch_bounds__(kBigThreads, 1) k_tc_big(
           *(uint4 *)(stB + rpart + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
         }
       }
+      if (stash) {  // old correction of cell c, rows hh*8 .. hh*8+7 of this chunk -> tensor memory
+        uint32_t ov[8];
+#pragma unroll
+        for (int i = 0; i < 8; i++) ov[i] = __float_as_uint(in_d[(hh * 8 + i) * kBigDW + c + kBigHalo]);
+        const uint32_t sa = tmem + ((uint32_t)(32 * (w & 3)) << 16) + (uint32_t)(kBigStash + kc * kBigKC + hh * 8);
+        asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(sa), "r"(ov[0]),
+                     "r"(ov[1]), "r"(ov[2]), "r"(ov[3]), "r"(ov[4]), "r"(ov[5]), "r"(ov[6]), "r"(ov[7])
+                     : "memory");
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;");
+      }
       // the RHS is visible to the tensor cores and the inputs are consumed
       asm volatile("fence.proxy.async.shared::cta;");
       __syncwarp();
@@ -271,8 +293,24 @@ __global__ void __launch_bounds__(kBigThreads, 1) k_tc_big(
         const int nb = n / 32;  // column blocks
         float dold[32], dnxt[32];
         auto load_old = [&](int b_, float *dst) {
+          if (stash) {  // from the builders' copy in tensor memory
+            uint32_t o[32];
+            const uint32_t oa = tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)(kBigStash + b_ * 32);
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                : "=r"(o[0]), "=r"(o[1]), "=r"(o[2]), "=r"(o[3]), "=r"(o[4]), "=r"(o[5]), "=r"(o[6]), "=r"(o[7]),
+                  "=r"(o[8]), "=r"(o[9]), "=r"(o[10]), "=r"(o[11]), "=r"(o[12]), "=r"(o[13]), "=r"(o[14]),
+                  "=r"(o[15]), "=r"(o[16]), "=r"(o[17]), "=r"(o[18]), "=r"(o[19]), "=r"(o[20]), "=r"(o[21]),
+                  "=r"(o[22]), "=r"(o[23]), "=r"(o[24]), "=r"(o[25]), "=r"(o[26]), "=r"(o[27]), "=r"(o[28]),
+                  "=r"(o[29]), "=r"(o[30]), "=r"(o[31])
+                : "r"(oa));
+            asm volatile("tcgen05.wait::ld.sync.aligned;");
 #pragma unroll
-          for (int i = 0; i < 32; i++) dst[i] = (act && !zero) ? Din[(size_t)(b_ * 32 + i) * Jp + j] : 0.f;
+            for (int i = 0; i < 32; i++) dst[i] = (act && !zero) ? __uint_as_float(o[i]) : 0.f;
+          } else {
+#pragma unroll
+            for (int i = 0; i < 32; i++) dst[i] = (act && !zero) ? Din[(size_t)(b_ * 32 + i) * Jp + j] : 0.f;
+          }
         };
         if (g2 < nb) load_old(g2, dold);
 #pragma unroll 1
