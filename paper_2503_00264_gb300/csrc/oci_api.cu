@@ -1070,6 +1070,7 @@ static int begin_iteration(Handle &h, int fixed, int cap) {
 
 static int run_step(Handle &h, bool si, oci_stats *st) {
   if (h.part_pending) return set_error("a sweep split by oci_iterate_part is not finished"), OCI_E_STATE;
+  h.tc_fresh = 0;
   const size_t nPsi = (size_t)h.G * h.N * 4 * h.Jp;
   cudaStream_t s = h.stream;
   if (h.guess == OCI_GUESS_ZERO) CK(cudaMemsetAsync(h.Psi[h.h_ds->cur], 0, nPsi * 8, s));
@@ -1166,6 +1167,7 @@ static int run_step(Handle &h, bool si, oci_stats *st) {
 static int run_fixed(Handle &h, bool si, int n, double *e_hist) {
   if (n < 0) return set_error("n must be >= 0"), OCI_E_INVAL;
   if (h.part_pending) return set_error("a sweep split by oci_iterate_part is not finished"), OCI_E_STATE;
+  h.tc_fresh = 0;
   if (n > h.e_hist_cap) {
     cudaFree(h.e_hist);
     h.e_hist_cap = n;
@@ -1336,7 +1338,10 @@ int oci_iterate_part(oci_handle *h, int32_t part, double *e_out) {
     if (H.part_pending) return set_error("oci_iterate_part: part 0 issued twice"), OCI_E_STATE;
     int rc = begin_iteration(H, 1, H.e_hist_cap);
     if (rc) return rc;
-    launch_step_const(H);
+    if (!H.tc_fresh) {  // the step constant depends only on psi_{k-1/2}, Q and dt
+      launch_step_const(H);
+      H.tc_fresh = 1;
+    }
     launch_oci_sweep_part(H, 0);
     CK(cudaGetLastError());
     H.part_pending = 1;
@@ -1397,6 +1402,7 @@ int oci_get_state(const oci_handle *h, double *psi_prev, double *t) {
 int oci_set_state(oci_handle *h, const double *psi_prev, double t) {
   GUARD(h);
   if (!std::isfinite(t)) return set_error("t must be finite"), OCI_E_INVAL;
+  h->tc_fresh = 0;
   if (psi_prev) {
     int rc = put_soa(*h, psi_prev, h->psi_prev, h->G * h->N * 2);
     if (rc) return rc;
@@ -1517,6 +1523,7 @@ int oci_get_edges(const oci_handle *hc, double *left, double *right) {
 
 int oci_commit(oci_handle *h, oci_stats *st) {
   GUARD(h);
+  h->tc_fresh = 0;  // the carry writes psi_{k-1/2}
   h->h_ds->status = OCI_OK;
   h->h_ds->done = 1;
   CK(cudaMemcpyAsync(h->ds, h->h_ds, sizeof(DevState), cudaMemcpyHostToDevice, h->stream));

@@ -165,6 +165,8 @@ struct Handle {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   int last_iters = 0;
   int part_pending = 0;  // oci_iterate_part: part 0 issued, part 1 not yet
+  int tc_fresh = 0;      // oci_iterate_part: tc holds this step's constant (cleared by any other
+                         // path that runs sweeps, commits or sets the state)
   bool no_graph = false;           // OCI_NO_GRAPH=1: host-driven loop instead of the WHILE graph
   int tune_cb = 0, tune_P = 0;     // sweep launch shape picked by the autotuner (0: default)
   bool tune_reg = false;           // FP64 Jacobi sweep in the register form (k_oci_sweep_reg)

@@ -5,7 +5,7 @@ while its neighbours' edge values are in flight.  The two calls must be one
 oci_iterate sweep bit for bit -- same cells, same block partials, same
 fixed-order sum -- also when the incident fluxes change between them, for the
 staged and the register form of the FP64 sweep and for one, two, three and
-many blocks."""
+many blocks, and after the state (psi_{k-1/2}) changes between sweeps."""
 import numpy as np
 import pytest
 
@@ -33,10 +33,14 @@ def test_split_sweep_equals_one_sweep(seed, J, N, G, reg, shape, monkeypatch):
         assert ia["sweep_kernel"] == int(reg)
         a.set_psi(psi0)
         b.set_psi(psi0)
-        for k in range(4):
+        for k in range(6):
             if k >= 2:  # new incident fluxes: before the sweep, or between its two parts
                 il, ir = rng.uniform(0.0, 2.0, (G, N, 2)), rng.uniform(0.0, 2.0, (G, N, 2))
                 a.set_boundary(il, ir)
+            if k == 4:  # a new psi_{k-1/2}: the split sweep recomputes its step constant
+                pp = rng.uniform(0.0, 1.0, (J, G, N, 2))
+                a.set_state(pp, 0.5)
+                b.set_state(pp, 0.5)
             ea = a.iterate(1)
             eb = np.zeros(1)
             b.iterate_part(0)
