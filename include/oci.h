@@ -37,6 +37,8 @@
  *       OCI_AUTOTUNE=0            keep the default launch shapes (no timing)
  *       OCI_SWEEP_SHAPE=cb,P      pin the sweep shape (cells per block, angle chunks)
  *       OCI_SWEEP_REG=0|1         FP64 sweep: staged or register form only
+ *       OCI_SWEEP_MS=0            FP64 register form: one launch per sweep in the graph even
+ *                                 where all cell blocks fit at once
  *       OCI_MX_INNER=plain|tma|reg|tiled|tiledp|tiledb|two|twoocc|warp (or a comma list)
  *                                 FP32 inner sweep kernel of the mixed form
  *       OCI_MX_RB=1|2             red-black FP32 inner sweep, one or two sweeps per pass
@@ -207,7 +209,10 @@ typedef struct {
                                 1 angles in registers (k_oci_sweep_reg); red-black order: 2 staged
                                 and 3 register form on ping-pong buffers, 4 staged in place;
                                 -1 for the other forms                                            */
-  int32_t reserved;          /* 0                                                                 */
+  int32_t multi_sweep;       /* FP64 Jacobi register form: 1 when the convergence loop runs all
+                                sweeps of a step in one cooperative launch (every cell block of
+                                the sweep resident at once; same iterates, norms and sweep counts
+                                as one launch per sweep), else 0                                 */
 } oci_info;
 
 typedef struct oci_handle oci_handle;
@@ -222,8 +227,11 @@ int oci_setup(const oci_problem *p, oci_handle **out);
  * iterate per p->guess, sweep until the stop rule holds, then commit: scalar
  * flux, balance tallies, psi_{k+1/2} -> psi_{k-1/2}, t += dt.  The whole
  * convergence loop runs on the device (CUDA graph with a conditional WHILE
- * node); the host reads a small stats record once per step.  st may be NULL.
- * Returns OCI_E_NOCONV without committing when max_iter is reached. */
+ * node; where every cell block of the FP64 register sweep fits on the GPU at
+ * once, one cooperative launch runs all sweeps with a bounded grid barrier
+ * between them); the host reads a small stats record once per step.  st may
+ * be NULL.  Returns OCI_E_NOCONV without committing when max_iter is reached,
+ * OCI_E_TIMEOUT without committing when a bounded device-side wait gave up. */
 int oci_step(oci_handle *h, oci_stats *st);
 
 /* n_steps calls of oci_step.  phi_out: [n_steps][J][G][4] (host or device) or

@@ -418,9 +418,11 @@ static int autotune(Handle &h) {
     apply(c);
     // the persistent tiled FP32 sweep runs as one multi-sweep cooperative launch in
     // the graph: time it that way (reps sweeps in one launch)
-    const bool multi = mx &&
-                       (c.kind == kMxTiledP || c.kind == kMxTiled2 || c.kind == kMxTiled2Occ || c.kind == kMxWarp2) &&
-                       h.mx_multi;
+    // (and so does the FP64 register form where all its blocks fit at once)
+    const bool multi = (mx &&
+                        (c.kind == kMxTiledP || c.kind == kMxTiled2 || c.kind == kMxTiled2Occ || c.kind == kMxWarp2) &&
+                        h.mx_multi) ||
+                       (!mx && c.kind == kSweepReg64 && sweep_ms_grid(h) > 0);
     auto sweep = [&]() {
       if (mx) launch_mx_inner(h, cudaGraphConditionalHandle{}, 0);
       else launch_oci_sweep(h, cudaGraphConditionalHandle{}, 0);
@@ -1581,7 +1583,7 @@ int oci_get_info(const oci_handle *h, oci_info *info) {
       info->sweep_kernel = 2;
     }
   }
-  info->reserved = 0;
+  info->multi_sweep = info->sweep_kernel == 1 && sweep_ms_grid(*h) > 0;
   return OCI_OK;
 }
 

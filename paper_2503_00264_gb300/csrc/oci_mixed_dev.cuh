@@ -42,30 +42,6 @@ __device__ __forceinline__ double block_reduce_fixed(float e2, double *red, int 
   return bs;
 }
 
-// Sense-reversing grid barrier on {count, generation}; thread 0 of every block.
-// The spin is bounded by `limit` iterations (the device state's spin field,
-// kGridSpin unless a test lowers it); false when it gave up.
-__device__ __forceinline__ bool grid_barrier(unsigned *gbar, unsigned nblocks, long long limit) {
-  volatile unsigned *vgen = gbar + 1;
-  const unsigned g0 = *vgen;  // cannot advance before this block arrives
-  __threadfence();
-  const unsigned arrived = atomicAdd(gbar, 1u);
-  if (arrived == nblocks - 1) {
-    gbar[0] = 0;
-    __threadfence();
-    atomicAdd(gbar + 1, 1u);
-    return true;
-  }
-  for (long long k = 0; k < limit; k++) {
-    if (*vgen != g0) {
-      __threadfence();
-      return true;
-    }
-    __nanosleep(64);
-  }
-  return false;
-}
-
 // ---- cell-column loads and the structured FP32 cell solve of the two-sweep kernels
 // Global loads of one cell column of a tile (z, the old correction when
 // want_old, the lagged inflows from delta_in); zeros for an inactive thread.

@@ -17,6 +17,7 @@
 // with yc = sum_m w_m tc per step (k_step_yc), and Psi_{g,m} = tc_{g,m} +
 // L_{g,m}^{-1} (s_g + |mu| u placed in the inflow rows), which saves two FP64
 // operations per cell, group and angle.
+#include <limits.h>
 #include <math.h>
 
 #include "oci_device.cuh"
@@ -278,56 +279,45 @@ void launch_step_const(Handle &h) {
   k_step_yc<<<dim3((h.J + 255) / 256, h.G), 256, 0, h.stream>>>(h.J, h.Jp, h.N, h.w, h.tc, h.yc);
 }
 
-// One sweep including its norm reduction and stop rule (fused into the last block).
+// Loads of the iterate: plain, or through L2 only (ld.global.cg) where another
+// block of the same launch may have rewritten the line since this SM cached it.
+template <bool CG>
+__device__ __forceinline__ double ld_psi(const double *p) {
+  if constexpr (CG) return __ldcg(p);
+  else return *p;
+}
 
-// ---------------------------------------------------------------- register form (FP64)
-// The same FP64 sweep with the N angles of a cell split over P = N/NP threads,
-// each keeping its NP angles' inflow u in registers: no per-angle staging in
-// shared memory, so problems with many unknowns per cell (large N*G) keep more
-// warps resident.  y = yc + sum_m Win_m u_m is reduced over the chunks in a
-// fixed order, s = Mp y is split over the chunk threads of each group, and
-// Psi = tc + Linv (s + |mu| u in the inflow rows).  Cin and w are not read here
-// (Win = w Cin and yc carry them); they stay in the argument list the staged
-// form shares.  The norm
-// and stop rule are fused into the last block.  RB = false: Jacobi ordering.
-// RB = true: half sweep of one colour (cell j = 2i + colour) on ping-pong
-// buffers as in k_oci_sweep_t<true, true>; the first colour only writes its
-// block partials, the second reduces both colours' (nparts in all).
-template <int NP, bool RB = false>
-__global__ void __launch_bounds__(256) k_oci_sweep_reg(
-    int J, int Jp, int N, int G, const int32_t *__restrict__ type, const double *__restrict__ Linv,
-    const double *__restrict__ Cin, const double *__restrict__ Mp, const double *__restrict__ w,
-    const double *__restrict__ inc, const double *__restrict__ tc, double *Psi0, double *Psi1, DevState *ds,
-    double *__restrict__ partials, unsigned *counter, double *e_hist, cudaGraphConditionalHandle cond, int use_cond,
-    int color, int nparts, const double *__restrict__ Win, const double *__restrict__ yc,
-    const double *__restrict__ mu, int fuse = 1, int boff = 0, int bstride = 1) {
-  extern __shared__ double smrd[];
-  __shared__ double red[8];
-  __shared__ bool s_last;
-  const int CB = blockDim.x, P = N / NP, G4 = 4 * G;
-  const int cl = threadIdx.x, gy = threadIdx.y;
+// The cells of one block of the register form: thread (cl, gy) of cell j; the
+// block's shared memory holds y [G*P*4][CB], y reduced [4G][CB] and s [4G][CB].
+// Writes Pout for the active cells and returns the thread's sum of
+// (Psi_new - Psi_old)^2.  Contains block-wide barriers: every thread calls it.
+template <int NP, bool CG>
+__device__ __forceinline__ double reg_cells(int j, int J, int Jp, int N, int G, int CB, int cl, int gy,
+                                            const int32_t *__restrict__ type, const double *__restrict__ Linv,
+                                            const double *__restrict__ Mp, const double *__restrict__ inc,
+                                            const double *__restrict__ tc, const double *__restrict__ Pin,
+                                            double *__restrict__ Pout, const double *__restrict__ Pnb,
+                                            const double *__restrict__ Win, const double *__restrict__ yc,
+                                            const double *__restrict__ mu, double *y_s, double *yr_s, double *s_s) {
+  const int P = N / NP, G4 = 4 * G;
   const int g = gy / P, ch = gy % P, m0 = ch * NP;
-  // Jacobi: logical block boff + blockIdx.x * bstride (as in k_oci_sweep_t)
-  const int lb = RB ? (int)blockIdx.x : boff + (int)blockIdx.x * bstride;
-  const int j = RB ? 2 * (blockIdx.x * CB + cl) + color : lb * CB + cl;
-  const int tid = threadIdx.y * CB + threadIdx.x;
-  const int nthr = CB * blockDim.y;
-  if (ds->done) return;  // uniform across the grid
-  const int cur = ds->cur;
-  const double *__restrict__ Pin = cur ? Psi1 : Psi0;
-  double *__restrict__ Pout = cur ? Psi0 : Psi1;
-  // upstream neighbours: the second colour of a red-black sweep reads the first colour's new values
-  const double *__restrict__ Pnb = (RB && color == 1) ? (cur ? Psi0 : Psi1) : Pin;
-  double *y_s = smrd;                           // [G*P*4][CB]
-  double *yr_s = y_s + (size_t)G * P * 4 * CB;  // [4G][CB]
-  double *s_s = yr_s + (size_t)G4 * CB;         // [4G][CB]
   const bool active = j < J;
   const int tau = active ? type[j] : 0;
   const int N2 = N / 2;
   const size_t tb = (size_t)tau * G * N;
   double u[NP][2];
+  // CG (all sweeps in one launch): the old values are loaded with the inflows,
+  // so one round trip to L2 per sweep serves both; the one-sweep kernel loads
+  // them where they are used
+  double old[CG ? NP : 1][4];
   double y0 = 0.0, y1 = 0.0, y2 = 0.0, y3 = 0.0;
   if (active) {
+    if constexpr (CG) {
+#pragma unroll
+      for (int i = 0; i < NP; i++)
+#pragma unroll
+        for (int p = 0; p < 4; p++) old[i][p] = __ldcg(Pin + (size_t)(g * N + m0 + i) * 4 * Jp + j + (size_t)p * Jp);
+    }
 #pragma unroll
     for (int i = 0; i < NP; i++) {
       const int m = m0 + i;
@@ -336,15 +326,15 @@ __global__ void __launch_bounds__(256) k_oci_sweep_reg(
       double uk, uh;
       if (m >= N2) {
         if (j > 0) {
-          uk = Pnb[base + (size_t)Jp - 1];
-          uh = Pnb[base + 3 * (size_t)Jp - 1];
+          uk = ld_psi<CG>(Pnb + base + (size_t)Jp - 1);
+          uh = ld_psi<CG>(Pnb + base + 3 * (size_t)Jp - 1);
         } else {
           uk = inc[gm * 2 + 0];
           uh = inc[gm * 2 + 1];
         }
       } else if (j < J - 1) {
-        uk = Pnb[base + 1];
-        uh = Pnb[base + 2 * (size_t)Jp + 1];
+        uk = ld_psi<CG>(Pnb + base + 1);
+        uh = ld_psi<CG>(Pnb + base + 2 * (size_t)Jp + 1);
       } else {
         uk = inc[(G * N + gm) * 2 + 0];
         uh = inc[(G * N + gm) * 2 + 1];
@@ -398,12 +388,56 @@ __global__ void __launch_bounds__(256) k_oci_sweep_reg(
 #pragma unroll
       for (int p = 0; p < 4; p++) {
         const double o = fma(L[p * 4 + 3], v3, fma(L[p * 4 + 2], v2, fma(L[p * 4 + 1], v1, fma(L[p * 4 + 0], v0, tc[base + (size_t)p * Jp]))));
-        const double d = o - Pin[base + (size_t)p * Jp];
+        const double d = o - (CG ? old[CG ? i : 0][p] : Pin[base + (size_t)p * Jp]);
         e2 = fma(d, d, e2);
         Pout[base + (size_t)p * Jp] = o;
       }
     }
   }
+  return e2;
+}
+
+// ---------------------------------------------------------------- register form (FP64)
+// The same FP64 sweep with the N angles of a cell split over P = N/NP threads,
+// each keeping its NP angles' inflow u in registers: no per-angle staging in
+// shared memory, so problems with many unknowns per cell (large N*G) keep more
+// warps resident.  y = yc + sum_m Win_m u_m is reduced over the chunks in a
+// fixed order, s = Mp y is split over the chunk threads of each group, and
+// Psi = tc + Linv (s + |mu| u in the inflow rows).  Cin and w are not read here
+// (Win = w Cin and yc carry them); they stay in the argument list the staged
+// form shares.  The norm
+// and stop rule are fused into the last block.  RB = false: Jacobi ordering.
+// RB = true: half sweep of one colour (cell j = 2i + colour) on ping-pong
+// buffers as in k_oci_sweep_t<true, true>; the first colour only writes its
+// block partials, the second reduces both colours' (nparts in all).
+template <int NP, bool RB = false>
+__global__ void __launch_bounds__(256) k_oci_sweep_reg(
+    int J, int Jp, int N, int G, const int32_t *__restrict__ type, const double *__restrict__ Linv,
+    const double *__restrict__ Cin, const double *__restrict__ Mp, const double *__restrict__ w,
+    const double *__restrict__ inc, const double *__restrict__ tc, double *Psi0, double *Psi1, DevState *ds,
+    double *__restrict__ partials, unsigned *counter, double *e_hist, cudaGraphConditionalHandle cond, int use_cond,
+    int color, int nparts, const double *__restrict__ Win, const double *__restrict__ yc,
+    const double *__restrict__ mu, int fuse = 1, int boff = 0, int bstride = 1) {
+  extern __shared__ double smrd[];
+  __shared__ double red[8];
+  __shared__ bool s_last;
+  const int CB = blockDim.x, P = N / NP;
+  const int cl = threadIdx.x, gy = threadIdx.y;
+  // Jacobi: logical block boff + blockIdx.x * bstride (as in k_oci_sweep_t)
+  const int lb = RB ? (int)blockIdx.x : boff + (int)blockIdx.x * bstride;
+  const int j = RB ? 2 * (blockIdx.x * CB + cl) + color : lb * CB + cl;
+  const int tid = threadIdx.y * CB + threadIdx.x;
+  if (ds->done) return;  // uniform across the grid
+  const int cur = ds->cur;
+  const double *__restrict__ Pin = cur ? Psi1 : Psi0;
+  double *__restrict__ Pout = cur ? Psi0 : Psi1;
+  // upstream neighbours: the second colour of a red-black sweep reads the first colour's new values
+  const double *__restrict__ Pnb = (RB && color == 1) ? (cur ? Psi0 : Psi1) : Pin;
+  double *y_s = smrd;                           // [G*P*4][CB]
+  double *yr_s = y_s + (size_t)G * P * 4 * CB;  // [4G][CB]
+  double *s_s = yr_s + (size_t)4 * G * CB;      // [4G][CB]
+  const double e2 = reg_cells<NP, false>(j, J, Jp, N, G, CB, cl, gy, type, Linv, Mp, inc, tc, Pin, Pout, Pnb, Win,
+                                         yc, mu, y_s, yr_s, s_s);
   const double bs = block_sum(e2, red);
   const int slot = lb + (RB ? color * gridDim.x : 0);
   if ((RB && color == 0) || !fuse) {
@@ -417,7 +451,77 @@ __global__ void __launch_bounds__(256) k_oci_sweep_reg(
       finish_fp64(ds, e_hist, sqrt(tot), cond, use_cond);
     }
   }
-  (void)nthr;
+  (void)Cin;
+  (void)w;
+}
+
+// ---------------------------------------------------------------- register form, all sweeps in one launch
+// A problem whose cell blocks are all resident at once spends most of a sweep
+// on the launch.  This kernel runs the consecutive Jacobi sweeps of a step in
+// one cooperative launch, one block per cell block: each block sweeps its
+// cells, writes its partial, meets the others at a grid barrier (bounded spin)
+// and sums all nb partials in the fixed order of the one-sweep kernel's last
+// block, so every block takes the same stop-rule decision on its own copy of
+// the device state and the iterates, norms and sweep counts are those of one
+// launch per sweep, bit for bit.  Partials are double-buffered by sweep parity
+// (a block that starts the next sweep cannot overwrite values another block is
+// still summing); the iterate is read through L2, since this SM's L1 may hold
+// lines that other blocks rewrote in the previous sweep.  The launch ends when
+// the step is done or after max_sweeps sweeps; a barrier that gives up records
+// OCI_E_TIMEOUT and ends the step.  gcount is zero at the launch.
+template <int NP>
+__global__ void __launch_bounds__(256, 2) k_oci_sweep_reg_ms(
+    int J, int Jp, int N, int G, const int32_t *__restrict__ type, const double *__restrict__ Linv,
+    const double *__restrict__ Mp, const double *__restrict__ inc, const double *__restrict__ tc, double *Psi0,
+    double *Psi1, DevState *ds, double *__restrict__ partials, unsigned long long *gcount, double *e_hist,
+    cudaGraphConditionalHandle cond, int use_cond, const double *__restrict__ Win, const double *__restrict__ yc,
+    const double *__restrict__ mu, int max_sweeps) {
+  extern __shared__ double smrd[];
+  __shared__ double red[8];
+  __shared__ DevState sd;
+  __shared__ int s_ok;
+  const int CB = blockDim.x, P = N / NP;
+  const int cl = threadIdx.x, gy = threadIdx.y;
+  const int tid = threadIdx.y * CB + threadIdx.x;
+  const int nb = gridDim.x;
+  const int j = blockIdx.x * CB + cl;
+  if (tid == 0) sd = *ds;
+  __syncthreads();
+  if (sd.done) return;  // uniform across the grid
+  double *y_s = smrd;
+  double *yr_s = y_s + (size_t)G * P * 4 * CB;
+  double *s_s = yr_s + (size_t)4 * G * CB;
+  bool failed = false;
+  for (int sw = 0;; sw++) {
+    const int cur = sd.cur;
+    const double *Pin = cur ? Psi1 : Psi0;
+    double *Pout = cur ? Psi0 : Psi1;
+    const double e2 = reg_cells<NP, true>(j, J, Jp, N, G, CB, cl, gy, type, Linv, Mp, inc, tc, Pin, Pout, Pin, Win,
+                                          yc, mu, y_s, yr_s, s_s);
+    const double bs = block_sum(e2, red);
+    double *part = partials + (size_t)(sw & 1) * nb;
+    if (tid == 0) {
+      part[blockIdx.x] = bs;
+      s_ok = grid_barrier_count(gcount, (unsigned long long)(sw + 1) * nb, sd.spin);
+    }
+    __syncthreads();
+    if (!s_ok) {
+      failed = true;
+      break;
+    }
+    const double tot = block_sum_fixed(part, nb, red);
+    if (tid == 0) finish_fp64(&sd, blockIdx.x == 0 ? e_hist : nullptr, sqrt(tot), cond, 0);
+    __syncthreads();
+    if (sd.done || sw + 1 >= max_sweeps) break;  // uniform: every block holds the same state
+  }
+  if (blockIdx.x == 0 && tid == 0) {
+    if (failed) {
+      sd.status = OCI_E_TIMEOUT;
+      sd.done = 1;
+    }
+    *ds = sd;
+    if (use_cond && sd.done) cudaGraphSetConditional(cond, 0);
+  }
 }
 
 size_t sweep_reg_smem(int G, int cb, int P) { return (size_t)cb * ((size_t)G * P * 4 + 8 * (size_t)G) * 8; }
@@ -427,7 +531,73 @@ const void *k_oci_sweep_reg_ptr(int np) {
                                                                : (const void *)k_oci_sweep_reg<8>;
 }
 
+// Grid of k_oci_sweep_reg_ms for the current register shape: the number of
+// cell blocks when all of them can be resident at once (and two sets of their
+// partials fit the reduction scratch), else 0 -- one launch per sweep.
+// OCI_SWEEP_MS=0 keeps one launch per sweep.
+int sweep_ms_grid(const Handle &h) {
+  if (!h.tune_reg || h.ordering == OCI_ORDER_RED_BLACK || h.precision != OCI_FP64 ||
+      h.solver == OCI_SOLVER_DENSE_LU)
+    return 0;
+  const char *v = hook_env("OCI_SWEEP_MS");
+  if (v && v[0] == '0') return 0;
+  const int cb = h.tune_cb, P = h.tune_P, np = h.N / P;
+  const int nb = (h.J + cb - 1) / cb;
+  if (2 * nb > h.n_partials) return 0;
+  const void *k = np == 2 ? (const void *)k_oci_sweep_reg_ms<2>
+                  : np == 4 ? (const void *)k_oci_sweep_reg_ms<4>
+                            : (const void *)k_oci_sweep_reg_ms<8>;
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, cb * h.G * P, sweep_reg_smem(h.G, cb, P)) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return nb <= sms * per ? nb : 0;
+}
+
+// Up to max_sweeps sweeps of the step in one cooperative launch (grid from
+// sweep_ms_grid); ends earlier when the step is done.  Outside a graph the
+// barrier count is zeroed first.
+void launch_oci_sweep_ms(Handle &h, int grid, cudaGraphConditionalHandle cond, int use_cond, int max_sweeps) {
+  const int cb = h.tune_cb, P = h.tune_P, np = h.N / P;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(cb, h.G * P);
+  cfg.dynamicSmemBytes = sweep_reg_smem(h.G, cb, P);
+  cfg.stream = h.stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;  // all blocks resident: they wait on one another
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  // the two words of the barrier record as one count; in the graph it was zeroed
+  // at the start of the step and the one launch runs to the step's end
+  unsigned long long *gcount = reinterpret_cast<unsigned long long *>(h.gbar);
+  if (!use_cond) cudaMemsetAsync(gcount, 0, sizeof(unsigned long long), h.stream);
+#define OCI_SWEEP_MS(NP)                                                                                          \
+  cudaLaunchKernelEx(&cfg, k_oci_sweep_reg_ms<NP>, h.J, h.Jp, h.N, h.G, (const int32_t *)h.type,                 \
+                     (const double *)h.tt.Linv, (const double *)h.tt.Mp, (const double *)h.inc,                 \
+                     (const double *)h.tc, h.Psi[0], h.Psi[1], h.ds, h.partials, gcount, h.e_hist, cond, use_cond, \
+                     (const double *)h.tt.Win, (const double *)h.yc, (const double *)h.mu, max_sweeps)
+  if (np == 2) OCI_SWEEP_MS(2);
+  else if (np == 4) OCI_SWEEP_MS(4);
+  else OCI_SWEEP_MS(8);
+#undef OCI_SWEEP_MS
+}
+
 void launch_oci_sweep(Handle &h, cudaGraphConditionalHandle cond, int use_cond) {
+  // in the graph (or when the autotuner times it): all sweeps of the step in one launch where the blocks fit
+  if (use_cond || h.mx_tune_sweeps > 0) {
+    const int msg = sweep_ms_grid(h);
+    if (msg > 0) {
+      // in the graph: no sweep limit (the stop rule ends the step by max_iter at the latest)
+      launch_oci_sweep_ms(h, msg, cond, use_cond, h.mx_tune_sweeps > 0 ? h.mx_tune_sweeps : INT_MAX);
+      return;
+    }
+  }
   if (h.tune_reg && h.ordering != OCI_ORDER_RED_BLACK) {  // register form (Jacobi)
     const int cb = h.tune_cb, P = h.tune_P, np = h.N / P;
     const dim3 block(cb, h.G * P), grid((h.J + cb - 1) / cb);

@@ -52,7 +52,7 @@ class Problem(ctypes.Structure):
 class Info(ctypes.Structure):
     _fields_ = [("n_types", ctypes.c_int32), ("cells_per_block", ctypes.c_int32), ("angle_chunks", ctypes.c_int32),
                 ("inner_kernel", ctypes.c_int32), ("tuned_sweep_us", ctypes.c_double),
-                ("sweep_kernel", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("sweep_kernel", ctypes.c_int32), ("multi_sweep", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):

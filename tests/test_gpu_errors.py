@@ -1,7 +1,8 @@
 """Failure paths of the C ABI, made on the host or by a bounded device wait
 that is told to give up at once -- no GPU fault is involved.
 
-  - OCI_E_TIMEOUT: the cooperative multi-sweep FP32 kernels wait on a bounded
+  - OCI_E_TIMEOUT: the cooperative multi-sweep kernels (the FP32 inner sweeps
+    and the FP64 register sweep where all its blocks fit) wait on a bounded
     grid barrier; with the test hook OCI_TEST_SPIN_LIMIT=0 every block that is
     not the last to arrive gives up without waiting, the kernel returns and the
     step ends with OCI_E_TIMEOUT, not committed.  The next step on the same
@@ -30,15 +31,18 @@ def rel(a, b):
 @pytest.mark.parametrize("kernel,env", [("two", {"OCI_MX_INNER": "two", "OCI_SWEEP_SHAPE": "32,4"}),
                                         ("tiledp", {"OCI_MX_INNER": "tiledp", "OCI_SWEEP_SHAPE": "64,4"}),
                                         ("rb2", {"OCI_MX_RB": "2", "OCI_SWEEP_SHAPE": "64,4"}),
-                                        ("rb", {"OCI_MX_RB": "1", "OCI_SWEEP_SHAPE": "64,4"})])
+                                        ("rb", {"OCI_MX_RB": "1", "OCI_SWEEP_SHAPE": "64,4"}),
+                                        ("fp64", {"OCI_SWEEP_REG": "1", "OCI_SWEEP_SHAPE": "64,4"})])
 def test_grid_barrier_timeout_returns_status_and_handle_recovers(kernel, env, monkeypatch):
     for k, v in env.items():
         monkeypatch.setenv(k, v)
     p = W.random_slab(81, 4000, 16, 1).replace(tol=1e-11)
     psi0 = W.random_guess(p, 3)
-    with oci.Solver(p, precision=oci.FP32_IR) as s:
+    with oci.Solver(p, precision=oci.FP64 if kernel == "fp64" else oci.FP32_IR) as s:
         if kernel.startswith("rb"):
             s.set_ordering(oci.ORDER_RED_BLACK)
+        if kernel == "fp64":  # all FP64 sweeps of the step in one cooperative launch
+            assert s.info()["multi_sweep"] == 1
         pp0, t0 = s.state()
         s.set_psi(psi0)
         monkeypatch.setenv("OCI_TEST_SPIN_LIMIT", "0")
