@@ -37,8 +37,8 @@
  *       OCI_AUTOTUNE=0            keep the default launch shapes (no timing)
  *       OCI_SWEEP_SHAPE=cb,P      pin the sweep shape (cells per block, angle chunks)
  *       OCI_SWEEP_REG=0|1         FP64 sweep: staged or register form only
- *       OCI_SWEEP_MS=0            FP64 register form: one launch per sweep in the graph even
- *                                 where all cell blocks fit at once
+ *       OCI_SWEEP_MS=0|grid       FP64 register form in the graph: one launch per sweep, or
+ *                                 the cooperative all-sweeps launch but not the cluster one
  *       OCI_MX_INNER=plain|tma|reg|tiled|tiledp|tiledb|two|twoocc|warp (or a comma list)
  *                                 FP32 inner sweep kernel of the mixed form
  *       OCI_MX_RB=1|2             red-black FP32 inner sweep, one or two sweeps per pass
@@ -209,10 +209,12 @@ typedef struct {
                                 1 angles in registers (k_oci_sweep_reg); red-black order: 2 staged
                                 and 3 register form on ping-pong buffers, 4 staged in place;
                                 -1 for the other forms                                            */
-  int32_t multi_sweep;       /* FP64 Jacobi register form: 1 when the convergence loop runs all
-                                sweeps of a step in one cooperative launch (every cell block of
-                                the sweep resident at once; same iterates, norms and sweep counts
-                                as one launch per sweep), else 0                                 */
+  int32_t multi_sweep;       /* FP64 Jacobi register form: how the convergence loop runs the
+                                sweeps of a step -- 0 one launch per sweep; 1 all in one
+                                cooperative launch (every cell block resident at once, a grid
+                                barrier between sweeps); 2 all in one thread-block cluster (at
+                                most 16 cell blocks, the iterate kept on chip).  Same iterates,
+                                norms and sweep counts in all three                              */
 } oci_info;
 
 typedef struct oci_handle oci_handle;
@@ -228,8 +230,9 @@ int oci_setup(const oci_problem *p, oci_handle **out);
  * flux, balance tallies, psi_{k+1/2} -> psi_{k-1/2}, t += dt.  The whole
  * convergence loop runs on the device (CUDA graph with a conditional WHILE
  * node; where every cell block of the FP64 register sweep fits on the GPU at
- * once, one cooperative launch runs all sweeps with a bounded grid barrier
- * between them); the host reads a small stats record once per step.  st may
+ * once, one launch runs all sweeps: a thread-block cluster with the iterate on
+ * chip for up to 16 blocks, else a cooperative grid with a bounded barrier
+ * between sweeps); the host reads a small stats record once per step.  st may
  * be NULL.  Returns OCI_E_NOCONV without committing when max_iter is reached,
  * OCI_E_TIMEOUT without committing when a bounded device-side wait gave up. */
 int oci_step(oci_handle *h, oci_stats *st);

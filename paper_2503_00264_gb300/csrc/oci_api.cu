@@ -309,9 +309,12 @@ static int autotune(Handle &h) {
     for (int np : {2, 4, 8}) {
       if (h.N % np) continue;
       const int P = h.N / np;
-      for (int cb : {16, 32, 64}) {
+      // blocks of 4 and 8 cells spread a small problem over more SMs (the FP64
+      // pipe of one SM bounds a block's sweep); timed only where one launch
+      // runs all sweeps of a step (below)
+      for (int cb : {4, 8, 16, 32, 64}) {
         const int thr = cb * h.G * P;
-        if (thr <= 256 && thr % 32 == 0 && thr >= 64) cands.push_back({kSweepReg64, cb, P});
+        if (thr <= 256 && thr % 32 == 0 && thr >= (cb < 16 ? 32 : 64)) cands.push_back({kSweepReg64, cb, P});
       }
     }
   if (mx)
@@ -422,11 +425,12 @@ static int autotune(Handle &h) {
     const bool multi = (mx &&
                         (c.kind == kMxTiledP || c.kind == kMxTiled2 || c.kind == kMxTiled2Occ || c.kind == kMxWarp2) &&
                         h.mx_multi) ||
-                       (!mx && c.kind == kSweepReg64 && sweep_ms_grid(h) > 0);
+                       (!mx && c.kind == kSweepReg64 && (sweep_cl_grid(h) > 0 || sweep_ms_grid(h) > 0));
     auto sweep = [&]() {
       if (mx) launch_mx_inner(h, cudaGraphConditionalHandle{}, 0);
       else launch_oci_sweep(h, cudaGraphConditionalHandle{}, 0);
     };
+    if (!mx && c.kind == kSweepReg64 && c.cb < 16 && !multi) continue;
     h.mx_tune_sweeps = multi ? 1 : 0;
     sweep();
     float ms = 1e30f;
@@ -1583,7 +1587,7 @@ int oci_get_info(const oci_handle *h, oci_info *info) {
       info->sweep_kernel = 2;
     }
   }
-  info->multi_sweep = info->sweep_kernel == 1 && sweep_ms_grid(*h) > 0;
+  info->multi_sweep = info->sweep_kernel != 1 ? 0 : sweep_cl_grid(*h) > 0 ? 2 : sweep_ms_grid(*h) > 0 ? 1 : 0;
   return OCI_OK;
 }
 

@@ -197,6 +197,8 @@ int gmres_solve(Handle &h, double tol_g, int max_sweeps, int &sweeps, double &e_
 void gmres_free(Handle &h);
 void launch_oci_sweep(Handle &h, cudaGraphConditionalHandle cond, int use_cond);
 int sweep_ms_grid(const Handle &h);
+int sweep_cl_grid(const Handle &h);
+void launch_oci_sweep_cl(Handle &h, int grid, cudaGraphConditionalHandle cond, int use_cond, int max_sweeps);
 void launch_oci_sweep_ms(Handle &h, int grid, cudaGraphConditionalHandle cond, int use_cond, int max_sweeps);
 void launch_oci_sweep_part(Handle &h, int part);  // FP64 Jacobi sweep as interior (0) and end blocks (1)
 const void *k_oci_sweep_ptr();

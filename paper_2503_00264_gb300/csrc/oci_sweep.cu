@@ -524,6 +524,204 @@ __global__ void __launch_bounds__(256, 2) k_oci_sweep_reg_ms(
   }
 }
 
+// ---------------------------------------------------------------- register form, one cluster, iterate on chip
+// A problem of at most 16 cell blocks runs all sweeps of a step in one thread-
+// block cluster, one block per cell block, with the iterate held on chip: each
+// thread keeps its NP angles' four corner values of its cell in registers from
+// sweep to sweep, and only the values a neighbouring cell reads (the two
+// downstream corners of each angle) are published in shared memory, double-
+// buffered by sweep parity.  A cell reads its upstream neighbour there (its
+// own block's buffer, or through distributed shared memory the adjacent
+// block's at the block's first and last cell), block partials of the norm are
+// read from every block's shared memory the same way, and one hardware cluster
+// barrier per sweep orders it all: no global-memory round trip per sweep and
+// no spin.  The arithmetic and the partial sums are those of k_oci_sweep_reg
+// with the same shape (same operations in the same order), so the iterates,
+// norms and sweep counts are those of one launch per sweep, bit for bit.  The
+// last iterate goes to Psi[cur] when the launch ends (the step is done, or
+// max_sweeps sweeps); Psi[cur^1], which the next sweep only writes, is not
+// touched.
+__device__ __forceinline__ double ld_cluster(const double *local, unsigned rank) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(local);
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  double v;
+  asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(r) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void cluster_barrier() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+template <int NP>
+__global__ void __launch_bounds__(256, 1) k_oci_sweep_cl(
+    int J, int Jp, int N, int G, const int32_t *__restrict__ type, const double *__restrict__ Linv,
+    const double *__restrict__ Mp, const double *__restrict__ inc, const double *__restrict__ tc, double *Psi0,
+    double *Psi1, DevState *ds, double *e_hist, cudaGraphConditionalHandle cond, int use_cond,
+    const double *__restrict__ Win, const double *__restrict__ yc, const double *__restrict__ mu, int max_sweeps) {
+  extern __shared__ double smrd[];
+  __shared__ double red[8];
+  __shared__ double part[2];
+  __shared__ DevState sd;
+  const int CB = blockDim.x, P = N / NP, G4 = 4 * G, GP = G * P;
+  const int cl = threadIdx.x, gy = threadIdx.y;
+  const int g = gy / P, ch = gy % P, m0 = ch * NP;
+  const int tid = threadIdx.y * CB + threadIdx.x;
+  const int nthr = CB * blockDim.y;
+  const unsigned lb = blockIdx.x, nb = gridDim.x;  // the grid is one cluster
+  const int j = (int)lb * CB + cl;
+  const int N2 = N / 2;
+  const bool active = j < J;
+  const int tau = active ? type[j] : 0;
+  const size_t tb = (size_t)tau * G * N;
+  if (tid == 0) sd = *ds;
+  __syncthreads();
+  if (sd.done) return;  // uniform across the cluster
+  double *y_s = smrd;                           // [G*P*4][CB]
+  double *yr_s = y_s + (size_t)G * P * 4 * CB;  // [4G][CB]
+  double *s_s = yr_s + (size_t)G4 * CB;         // [4G][CB]
+  double *E = s_s + (size_t)G4 * CB;            // [2][G*P][NP][2][CB] published downstream corners
+  auto eix = [&](int par, int i, int k, int c) -> size_t {
+    return ((((size_t)par * GP + gy) * NP + i) * 2 + k) * CB + c;
+  };
+  double ps[NP][4];
+  {
+    const double *Pin = sd.cur ? Psi1 : Psi0;
+#pragma unroll
+    for (int i = 0; i < NP; i++)
+#pragma unroll
+      for (int p = 0; p < 4; p++) ps[i][p] = active ? Pin[(size_t)((g * N + m0 + i) * 4 + p) * Jp + j] : 0.0;
+  }
+  auto publish = [&](int par) {
+#pragma unroll
+    for (int i = 0; i < NP; i++) {
+      const bool pos = m0 + i >= N2;  // mu > 0: the right corners feed cell j+1, else the left ones cell j-1
+      E[eix(par, i, 0, cl)] = pos ? ps[i][1] : ps[i][0];
+      E[eix(par, i, 1, cl)] = pos ? ps[i][3] : ps[i][2];
+    }
+  };
+  publish(0);
+  cluster_barrier();
+  for (int sw = 0;; sw++) {
+    const int par = sw & 1;
+    double u[NP][2];
+    double y0 = 0.0, y1 = 0.0, y2 = 0.0, y3 = 0.0;
+    if (active) {
+#pragma unroll
+      for (int i = 0; i < NP; i++) {
+        const int m = m0 + i;
+        const int gm = g * N + m;
+        double uk, uh;
+        if (m >= N2) {
+          if (j == 0) {
+            uk = inc[gm * 2 + 0];
+            uh = inc[gm * 2 + 1];
+          } else if (cl > 0) {
+            uk = E[eix(par, i, 0, cl - 1)];
+            uh = E[eix(par, i, 1, cl - 1)];
+          } else {
+            uk = ld_cluster(E + eix(par, i, 0, CB - 1), lb - 1);
+            uh = ld_cluster(E + eix(par, i, 1, CB - 1), lb - 1);
+          }
+        } else if (j == J - 1) {
+          uk = inc[(G * N + gm) * 2 + 0];
+          uh = inc[(G * N + gm) * 2 + 1];
+        } else if (cl < CB - 1) {
+          uk = E[eix(par, i, 0, cl + 1)];
+          uh = E[eix(par, i, 1, cl + 1)];
+        } else {
+          uk = ld_cluster(E + eix(par, i, 0, 0), lb + 1);
+          uh = ld_cluster(E + eix(par, i, 1, 0), lb + 1);
+        }
+        u[i][0] = uk;
+        u[i][1] = uh;
+        const double *W = Win + (tb + gm) * 8;
+        y0 = fma(W[1], uh, fma(W[0], uk, y0));
+        y1 = fma(W[3], uh, fma(W[2], uk, y1));
+        y2 = fma(W[5], uh, fma(W[4], uk, y2));
+        y3 = fma(W[7], uh, fma(W[6], uk, y3));
+      }
+    }
+    {
+      double *ys = y_s + (size_t)(gy * 4) * CB + cl;
+      ys[0] = y0;
+      ys[CB] = y1;
+      ys[2 * CB] = y2;
+      ys[3 * CB] = y3;
+    }
+    __syncthreads();
+    for (int q = ch; q < 4; q += P) {
+      double v = active ? yc[(size_t)(g * 4 + q) * Jp + j] : 0.0;
+      for (int k = 0; k < P; k++) v += y_s[(size_t)((g * P + k) * 4 + q) * CB + cl];
+      yr_s[(size_t)(g * 4 + q) * CB + cl] = v;
+    }
+    __syncthreads();
+    if (active)
+      for (int q = ch; q < 4; q += P) {
+        const double *M = Mp + (size_t)tau * G4 * G4 + (size_t)(g * 4 + q) * G4;
+        double v = 0.0;
+        for (int k = 0; k < G4; k++) v = fma(M[k], yr_s[(size_t)k * CB + cl], v);
+        s_s[(size_t)(g * 4 + q) * CB + cl] = v;
+      }
+    __syncthreads();
+    double e2 = 0.0;
+    if (active) {
+      const double s0 = s_s[(size_t)(g * 4 + 0) * CB + cl], s1 = s_s[(size_t)(g * 4 + 1) * CB + cl];
+      const double s2 = s_s[(size_t)(g * 4 + 2) * CB + cl], s3 = s_s[(size_t)(g * 4 + 3) * CB + cl];
+#pragma unroll
+      for (int i = 0; i < NP; i++) {
+        const int m = m0 + i;
+        const int gm = g * N + m;
+        const size_t base = (size_t)gm * 4 * Jp + j;
+        const double *L = Linv + (tb + gm) * 16;
+        const double am = fabs(mu[m]);
+        const bool pos = m >= N2;
+        const double v0 = pos ? fma(am, u[i][0], s0) : s0, v1 = pos ? s1 : fma(am, u[i][0], s1);
+        const double v2 = pos ? fma(am, u[i][1], s2) : s2, v3 = pos ? s3 : fma(am, u[i][1], s3);
+#pragma unroll
+        for (int p = 0; p < 4; p++) {
+          const double o = fma(L[p * 4 + 3], v3, fma(L[p * 4 + 2], v2, fma(L[p * 4 + 1], v1, fma(L[p * 4 + 0], v0, tc[base + (size_t)p * Jp]))));
+          const double d = o - ps[i][p];
+          e2 = fma(d, d, e2);
+          ps[i][p] = o;
+        }
+      }
+    }
+    publish(par ^ 1);
+    const double bs = block_sum(e2, red);
+    if (tid == 0) part[par] = bs;
+    cluster_barrier();  // the new corners and every block's partial are visible cluster-wide
+    // fixed-order sum of the nb block partials, as the one-sweep kernel's last block does
+    double s = 0.0;
+    for (int i = tid; i < (int)nb; i += nthr) s += ld_cluster(&part[par], (unsigned)i);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((tid & 31) == 0) red[tid >> 5] = s;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int w = 0; w < (nthr + 31) / 32; w++) t += red[w];
+      finish_fp64(&sd, lb == 0 ? e_hist : nullptr, sqrt(t), cond, 0);
+    }
+    __syncthreads();
+    if (sd.done || sw + 1 >= max_sweeps) break;  // uniform: every block holds the same state
+  }
+  // the last iterate to Psi[cur] (the stop rule flipped cur with every sweep)
+  if (active) {
+    double *Pnew = sd.cur ? Psi1 : Psi0;
+#pragma unroll
+    for (int i = 0; i < NP; i++)
+#pragma unroll
+      for (int p = 0; p < 4; p++) Pnew[(size_t)((g * N + m0 + i) * 4 + p) * Jp + j] = ps[i][p];
+  }
+  if (lb == 0 && tid == 0) {
+    *ds = sd;
+    if (use_cond && sd.done) cudaGraphSetConditional(cond, 0);
+  }
+  cluster_barrier();  // no block leaves while another may still read its shared memory
+}
+
 size_t sweep_reg_smem(int G, int cb, int P) { return (size_t)cb * ((size_t)G * P * 4 + 8 * (size_t)G) * 8; }
 
 const void *k_oci_sweep_reg_ptr(int np) {
@@ -588,9 +786,86 @@ void launch_oci_sweep_ms(Handle &h, int grid, cudaGraphConditionalHandle cond, i
 #undef OCI_SWEEP_MS
 }
 
+// Shared memory of k_oci_sweep_cl: the register form's plus the published
+// corners, [2][G*P][NP][2][CB] doubles.
+static size_t sweep_cl_smem(int N, int G, int cb, int P) {
+  return sweep_reg_smem(G, cb, P) + (size_t)2 * G * N * 2 * cb * 8;
+}
+
+static const void *k_oci_sweep_cl_ptr(int np) {
+  return np == 2 ? (const void *)k_oci_sweep_cl<2> : np == 4 ? (const void *)k_oci_sweep_cl<4>
+                                                              : (const void *)k_oci_sweep_cl<8>;
+}
+
+// Cluster launch of k_oci_sweep_cl over nb blocks (the whole grid one cluster).
+static void sweep_cl_config(const Handle &h, int nb, cudaLaunchConfig_t &cfg, cudaLaunchAttribute *attr) {
+  const int cb = h.tune_cb, P = h.tune_P;
+  cfg = {};
+  cfg.gridDim = dim3(nb);
+  cfg.blockDim = dim3(cb, h.G * P);
+  cfg.dynamicSmemBytes = sweep_cl_smem(h.N, h.G, cb, P);
+  cfg.stream = h.stream;
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = nb;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+}
+
+// Blocks of k_oci_sweep_cl for the current register shape: the number of cell
+// blocks when there are at most 16 and one cluster of them can be scheduled on
+// this GPU, else 0.  OCI_SWEEP_MS=0 or =grid turns the cluster form off.
+int sweep_cl_grid(const Handle &h) {
+  if (!h.tune_reg || h.ordering == OCI_ORDER_RED_BLACK || h.precision != OCI_FP64 ||
+      h.solver == OCI_SOLVER_DENSE_LU)
+    return 0;
+  const char *v = hook_env("OCI_SWEEP_MS");
+  if (v && (v[0] == '0' || v[0] == 'g')) return 0;
+  const int cb = h.tune_cb, P = h.tune_P, np = h.N / P;
+  const int nb = (h.J + cb - 1) / cb;
+  if (nb > 16) return 0;
+  const void *k = k_oci_sweep_cl_ptr(np);
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute attr[1];
+  sweep_cl_config(h, nb, cfg, attr);
+  int nc = 0;
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess ||
+      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.dynamicSmemBytes) !=
+          cudaSuccess ||
+      cudaOccupancyMaxActiveClusters(&nc, k, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return nc >= 1 ? nb : 0;
+}
+
+// Up to max_sweeps sweeps of the step in one cluster launch (grid from
+// sweep_cl_grid); ends earlier when the step is done.
+void launch_oci_sweep_cl(Handle &h, int grid, cudaGraphConditionalHandle cond, int use_cond, int max_sweeps) {
+  const int np = h.N / h.tune_P;
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute attr[1];
+  sweep_cl_config(h, grid, cfg, attr);
+#define OCI_SWEEP_CL(NP)                                                                                          \
+  cudaLaunchKernelEx(&cfg, k_oci_sweep_cl<NP>, h.J, h.Jp, h.N, h.G, (const int32_t *)h.type,                     \
+                     (const double *)h.tt.Linv, (const double *)h.tt.Mp, (const double *)h.inc,                 \
+                     (const double *)h.tc, h.Psi[0], h.Psi[1], h.ds, h.e_hist, cond, use_cond,                  \
+                     (const double *)h.tt.Win, (const double *)h.yc, (const double *)h.mu, max_sweeps)
+  if (np == 2) OCI_SWEEP_CL(2);
+  else if (np == 4) OCI_SWEEP_CL(4);
+  else OCI_SWEEP_CL(8);
+#undef OCI_SWEEP_CL
+}
+
 void launch_oci_sweep(Handle &h, cudaGraphConditionalHandle cond, int use_cond) {
   // in the graph (or when the autotuner times it): all sweeps of the step in one launch where the blocks fit
   if (use_cond || h.mx_tune_sweeps > 0) {
+    const int ncl = sweep_cl_grid(h);
+    if (ncl > 0) {
+      launch_oci_sweep_cl(h, ncl, cond, use_cond, h.mx_tune_sweeps > 0 ? h.mx_tune_sweeps : INT_MAX);
+      return;
+    }
     const int msg = sweep_ms_grid(h);
     if (msg > 0) {
       // in the graph: no sweep limit (the stop rule ends the step by max_iter at the latest)
