@@ -14,6 +14,7 @@ Subcommands (measurement tools around the same library; no JSON contract line):
   python bench.py profile --case slab3 --sweeps 3 [--precision fp32] [--ordering rb]
                           [--steps N] [--si] [--solver dense] [--J J]
   python bench.py profile --case batch --slabs 64 --ng 32,4
+  python bench.py profile --case table2 --delta2 1.0 --N 16 --dt 10 --steps 1
       one small case for a profiler: set up, run exactly --sweeps sweeps from a
       seeded random iterate (or --steps time steps, or one batched step) and exit
   python bench.py grid [--steps 2] [--json out.json]
@@ -711,7 +712,10 @@ def cmd_profile(argv):
 
     from paper_2503_00264_gb300 import oci
     ap = argparse.ArgumentParser(prog="bench.py profile")
-    ap.add_argument("--case", default="slab3", choices=["slab3", "slab3_ragged", "multigroup", "batch"])
+    ap.add_argument("--case", default="slab3", choices=["slab3", "slab3_ragged", "multigroup", "batch", "table2"])
+    ap.add_argument("--delta2", type=float, default=1.0, help="table2: cell width in mean free paths of group 2")
+    ap.add_argument("--N", type=int, default=16, help="table2: angles")
+    ap.add_argument("--dt", type=float, default=10.0, help="table2: time step")
     ap.add_argument("--J", type=int, default=None)
     ap.add_argument("--sweeps", type=int, default=3)
     ap.add_argument("--solver", default="structured", choices=["structured", "dense"])
@@ -747,6 +751,8 @@ def cmd_profile(argv):
         p = W.slab_3region(c=0.9, tau=0.1, J=a.J or 2 ** 18)
     elif a.case == "slab3_ragged":
         p = W.slab_3region(c=0.9, tau=0.1, J=a.J or 2 ** 16, ragged=True)
+    elif a.case == "table2":  # the two-group problem of Sec. 3.2 (J = 100 / delta2 cells)
+        p = W.rosa_two_group(a.delta2, a.N, a.dt).replace(tol=1e-10)
     else:
         p = W.slab_multigroup(J=a.J or 2 ** 16)
     solver = oci.SOLVER_DENSE_LU if a.solver == "dense" else oci.SOLVER_STRUCTURED
