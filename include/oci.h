@@ -50,6 +50,8 @@
  *       OCI_TC_BIG=0              tensor-core forms at 4NG <= 128: the persistent kernel with
  *                                 the inverse resident in shared memory (not the streamed one)
  *       OCI_TC_PIPE=0             with OCI_TC_BIG=0: the one-tile-per-CTA tensor-core kernel
+ *       OCI_TC_HALF=0             streamed tensor-core kernel: the full form r + B delta for
+ *                                 every inner sweep (not z + (A~^{-1} B) u after the first)
  *       OCI_DENSE_APPLY=lu        dense per-cell path: triangular solves with the LU
  *                                 factors instead of the explicit inverse
  *       OCI_BATCH_SWEEP           pin the batched sweep form

@@ -698,7 +698,7 @@ static void free_handle(Handle *h) {
                   h->LU,     h->piv,    h->partials,  h->bal_partials, h->bal,       h->e_hist,    h->ds,
                   h->stage,  h->delta[0], h->delta[1], h->z32, h->w32, h->tt.Lco, h->tt.Linv32, h->tt.Cin32,
                   h->tt.Mp32, h->tc_img, h->tc_items, h->si_maps, h->si_segin, h->counter, h->psi_user, h->gbar, h->mu32,
-                  h->yc,     h->tt.Win};
+                  h->yc,     h->tt.Win, h->tc_img_h, h->tc_z};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (h->h_ds) cudaFreeHost(h->h_ds);

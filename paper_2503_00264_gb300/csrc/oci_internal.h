@@ -133,6 +133,8 @@ struct Handle {
   int mx_kind = 0;                     // FP32 inner sweep picked by the autotuner: kMxPlain, kMxTma, kMxReg, kMxTiled
   unsigned char *tc_img = nullptr;     // [T] x (A^{-1} image(s) in the tcgen05 K-major layout)
   size_t tc_img_bytes = 0;             // bytes per type
+  unsigned char *tc_img_h = nullptr;   // [T] x image of A~^{-1} B: the inflow columns, |mu| folded in (k_tc_big)
+  float *tc_z = nullptr;               // [R][Jp] z = A~^{-1} r of the current refinement block (k_tc_big)
   int2 *tc_items = nullptr;            // streamed tcgen05 apply: (tile, cell type) work items
   int tc_n_items = 0;
   bool tc_mixed = false;               // some 128-cell tile holds more than one cell type

@@ -26,6 +26,13 @@
 //   - after the last chunk of a tile the builder warps drain the accumulators
 //     (tcgen05.ld: one register per unknown, one lane per cell), form delta
 //     and the FP32 norm partial; loads and stores are 128-byte rows of 32 cells.
+// Coupling form (n a multiple of 32, n <= 256): r is the same for every inner sweep
+// of a refinement block, so the block's first sweep (zero old correction, the
+// full form above) also stores z = A~^{-1} r, and every later sweep computes
+//   delta = z + U . (A~^{-1} B)^T
+// over the n/2 inflow columns only (B delta puts |mu| times an upstream corner of
+// the neighbour into two rows of each (group, angle) block): half the K-chunks,
+// a builder step that only gathers the upstream corners, and z added in the drain.
 // One CTA per SM walks the tiles persistently; a tile whose cells are of more
 // than one type (a region boundary inside it) is taken once per type, each pass
 // keeping only its own cells (work items (tile, type), a separate instantiation).
@@ -56,7 +63,9 @@ constexpr int kBigThreads = kBigBuilders + 64;  // and two control warps: MMAs, 
 constexpr long long kBigSpin = 1 << 22;
 constexpr int kBigHalo = 4;                                 // columns each side of the delta box (16 B)
 constexpr int kBigDW = kBigN + 2 * kBigHalo;                // delta box width
-constexpr int kBigInBytes = kBigKC * (kBigN + kBigDW) * 4;  // r box + delta box of one chunk
+constexpr int kBigInFull = kBigKC * (kBigN + kBigDW) * 4;   // full form: r box + delta box of one chunk
+constexpr int kBigInHalf = 2 * kBigKC * kBigDW * 4;         // coupling form: delta box of 32 rows
+constexpr int kBigInBytes = kBigInFull > kBigInHalf ? kBigInFull : kBigInHalf;
 // Input buffers: a chunk's copies are issued once the builders have consumed the
 // buffer kBigInBuf chunks back, so the builders can be at most kBigInBuf chunks
 // ahead of the copy thread's wait on rhs_full; with more buffers than stages they
@@ -113,7 +122,7 @@ __global__ void __launch_bounds__(kBigThreads, 1) k_tc_big(
     const int32_t *__restrict__ type, const unsigned char *__restrict__ Aimg, const float *__restrict__ mu,
     const float *__restrict__ r32, float *D0, float *D1, DevState *ds, double *__restrict__ partials,
     unsigned *counter, double *e_hist, cudaGraphConditionalHandle cond, int use_cond,
-    const int2 *__restrict__ items, int n_items) {
+    const int2 *__restrict__ items, int n_items, const unsigned char *__restrict__ AimgH, int NKH, float *Zt) {
   extern __shared__ __align__(1024) unsigned char smb_[];
   // a_full: a stage's A^{-1} chunk has landed; rhs_full: the eight builder warps
   // have written a stage's RHS chunk; mma_done: a stage's MMAs have completed;
@@ -138,6 +147,11 @@ __global__ void __launch_bounds__(kBigThreads, 1) k_tc_big(
   const int t = threadIdx.x, w = t >> 5, lane = t & 31;
   if (ds->done) return;  // uniform
   const bool zero = ds->refine || ds->blk_i == 0;
+  // coupling form (an image of the inflow columns is present, and this is not the
+  // first sweep of a refinement block): D = U . (A~^{-1} B)^T over the n/2 inflow
+  // columns, delta = z + D with z = A~^{-1} r kept from the block's first sweep
+  const bool half = !zero && AimgH != nullptr;
+  const int NKe = half ? NKH : NK;
   const int dcur = ds->dcur;
   const float *__restrict__ Din = dcur ? D1 : D0;
   float *__restrict__ Dout = dcur ? D0 : D1;
@@ -171,7 +185,7 @@ __global__ void __launch_bounds__(kBigThreads, 1) k_tc_big(
   // whose cells are not all of one type (then bit 30 of the type word is set); the
   // CTA's i-th item is items[blockIdx.x + i gridDim.x]
   const int my_items = (int)blockIdx.x < n_items ? (n_items - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-  const int n_chunks = my_items * NK;  // chunk g: the CTA's item g / NK, K-chunk g % NK
+  const int n_chunks = my_items * NKe;  // chunk g: the CTA's item g / NKe, K-chunk g % NKe
   const int N2 = N / 2;
   float e2 = 0.f;
   bool failed = false;
@@ -190,8 +204,8 @@ __global__ void __launch_bounds__(kBigThreads, 1) k_tc_big(
         keep = !(wi.y >> 30) || (jd < J && type[jd] == (wi.y & 0x3FFFFFFF));
       }
       const int ib = g % kBigInBuf;
-      float *in_r = (float *)(in_base + (size_t)ib * kBigInBytes);  // [16][128]
-      float *in_d = in_r + kBigKC * kBigN;                            // [16][136]
+      float *in_r = (float *)(in_base + (size_t)ib * kBigInBytes);  // full form: r [16][128]
+      float *in_d = half ? in_r : in_r + kBigKC * kBigN;             // delta [16][136], coupling form [32][136]
       unsigned char *stB = sm + (size_t)s * stage_bytes + (size_t)NT * kBigABlk;
       // this chunk's inputs have landed and the stage's MMAs of chunk g - 3 are done; a new
       // tile's old-correction copy in tensor memory waits until every builder warp has
@@ -199,7 +213,7 @@ __global__ void __launch_bounds__(kBigThreads, 1) k_tc_big(
       bool ok = big_wait(su32(&in_full[ib]), (uint32_t)((g / kBigInBuf) & 1));
       if (ok && g >= kBigStages) ok = big_wait(su32(&mma_done[s]), (uint32_t)((u3 - 1) & 1));
       if (ok && stash && kc == 0 && g > 0) {
-        ok = big_wait(su32(&tmem_empty), (uint32_t)(((g / NK) - 1) & 1));
+        ok = big_wait(su32(&tmem_empty), (uint32_t)(((g / NKe) - 1) & 1));
         asm volatile("tcgen05.fence::after_thread_sync;");
       }
       if (!__all_sync(0xffffffffu, ok)) {  // warp-uniform: the warp leaves together
@@ -207,38 +221,60 @@ __global__ void __launch_bounds__(kBigThreads, 1) k_tc_big(
         failed = true;
         break;
       }
-      {  // RHS r + B delta of cell c, rows hh*8 .. hh*8+7: TF32, or BF16 hi / lo
+      {  // RHS of cell c, K rows hh*8 .. hh*8+7 of this chunk: TF32, or BF16 hi / lo
         const int j = tile * kBigN + c;
         const bool act = j < J;
-        // all shared-memory loads first (no branch between them), then the inflow terms:
-        // rows kc*16 + hh*8 .. +7 are two (group, angle) blocks of four corners; for
-        // mu > 0 the even rows take mu * (R corner of cell j-1), for mu < 0 the odd
-        // rows |mu| * (L corner of cell j+1)
-        float v[8], up[4], dn[4];
+        float v[8];
+        if (half) {
+          // coupling form: K column 2 (gN + m) + s is the inflow of (group, angle) gN + m
+          // (s = 0 time average, 1 time edge): for mu > 0 corner 2s + 1 (R) of cell j-1,
+          // for mu < 0 corner 2s (L) of cell j+1 (|mu| is in the image).  The chunk's box
+          // holds the 32 unknowns of the (g, m) blocks 8 kc .. 8 kc + 7.
+          const bool has_l = act && j > 0, has_r = act && j < J - 1;
+          int m = (kc * 8 + hh * 4) % N;
 #pragma unroll
-        for (int i = 0; i < 8; i++) v[i] = in_r[(hh * 8 + i) * kBigN + c];
+          for (int q = 0; q < 4; q++) {
+            const int ql = hh * 4 + q;
+            const bool pos = m >= N2;
 #pragma unroll
-        for (int q = 0; q < 4; q++) {
-          const int kl2 = hh * 8 + 2 * q;
-          up[q] = in_d[(kl2 + 1) * kBigDW + c + kBigHalo - 1];
-          dn[q] = in_d[kl2 * kBigDW + c + kBigHalo + 1];
-        }
-        const int m0 = (kc * (kBigKC / 4) + hh * 2) % N;
-        const int m1 = m0 + 1 == N ? 0 : m0 + 1;
-        const float mf0 = mu_s[m0], mf1 = mu_s[m1];
-        const bool lag = act && !zero;
-        const bool has_l = lag && j > 0, has_r = lag && j < J - 1;
+            for (int sc = 0; sc < 2; sc++) {
+              const float up = in_d[(4 * ql + 2 * sc + 1) * kBigDW + c + kBigHalo - 1];
+              const float dn = in_d[(4 * ql + 2 * sc) * kBigDW + c + kBigHalo + 1];
+              v[2 * q + sc] = pos ? (has_l ? up : 0.f) : (has_r ? dn : 0.f);
+            }
+            m = m + 1 == N ? 0 : m + 1;
+          }
+        } else {
+          // full form, r + B delta: all shared-memory loads first (no branch between
+          // them), then the inflow terms: rows kc*16 + hh*8 .. +7 are two (group, angle)
+          // blocks of four corners; for mu > 0 the even rows take mu * (R corner of cell
+          // j-1), for mu < 0 the odd rows |mu| * (L corner of cell j+1)
+          float up[4], dn[4];
 #pragma unroll
-        for (int q = 0; q < 4; q++) {
-          const int m = q < 2 ? m0 : m1;
-          const float mf = q < 2 ? mf0 : mf1;
-          const bool pos = m >= N2;
-          v[2 * q] = fmaf(mf, (pos && has_l) ? up[q] : 0.f, v[2 * q]);
-          v[2 * q + 1] = fmaf(-mf, (!pos && has_r) ? dn[q] : 0.f, v[2 * q + 1]);
-        }
-        if (!act) {
+          for (int i = 0; i < 8; i++) v[i] = in_r[(hh * 8 + i) * kBigN + c];
 #pragma unroll
-          for (int i = 0; i < 8; i++) v[i] = 0.f;
+          for (int q = 0; q < 4; q++) {
+            const int kl2 = hh * 8 + 2 * q;
+            up[q] = in_d[(kl2 + 1) * kBigDW + c + kBigHalo - 1];
+            dn[q] = in_d[kl2 * kBigDW + c + kBigHalo + 1];
+          }
+          const int m0 = (kc * (kBigKC / 4) + hh * 2) % N;
+          const int m1 = m0 + 1 == N ? 0 : m0 + 1;
+          const float mf0 = mu_s[m0], mf1 = mu_s[m1];
+          const bool lag = act && !zero;
+          const bool has_l = lag && j > 0, has_r = lag && j < J - 1;
+#pragma unroll
+          for (int q = 0; q < 4; q++) {
+            const int m = q < 2 ? m0 : m1;
+            const float mf = q < 2 ? mf0 : mf1;
+            const bool pos = m >= N2;
+            v[2 * q] = fmaf(mf, (pos && has_l) ? up[q] : 0.f, v[2 * q]);
+            v[2 * q + 1] = fmaf(-mf, (!pos && has_r) ? dn[q] : 0.f, v[2 * q + 1]);
+          }
+          if (!act) {
+#pragma unroll
+            for (int i = 0; i < 8; i++) v[i] = 0.f;
+          }
         }
         if (KIND == 1) {
           *(float4 *)(stB + big_off(c, hh * 8, 4)) = make_float4(v[0], v[1], v[2], v[3]);
@@ -259,7 +295,19 @@ __global__ void __launch_bounds__(kBigThreads, 1) k_tc_big(
           *(uint4 *)(stB + rpart + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
         }
       }
-      if (stash) {  // old correction of cell c, rows hh*8 .. hh*8+7 of this chunk -> tensor memory
+      if (stash && half) {  // old correction of cell c, box rows hh*16 .. +15 (unknowns 32 kc + ..) -> tensor memory
+        uint32_t ov[16];
+#pragma unroll
+        for (int i = 0; i < 16; i++) ov[i] = __float_as_uint(in_d[(hh * 16 + i) * kBigDW + c + kBigHalo]);
+        const uint32_t sa = tmem + ((uint32_t)(32 * (w & 3)) << 16) + (uint32_t)(kBigStash + kc * 32 + hh * 16);
+        asm volatile(
+            "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(sa),
+            "r"(ov[0]), "r"(ov[1]), "r"(ov[2]), "r"(ov[3]), "r"(ov[4]), "r"(ov[5]), "r"(ov[6]), "r"(ov[7]), "r"(ov[8]),
+            "r"(ov[9]), "r"(ov[10]), "r"(ov[11]), "r"(ov[12]), "r"(ov[13]), "r"(ov[14]), "r"(ov[15])
+            : "memory");
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;");
+      } else if (stash) {  // old correction of cell c, rows hh*8 .. hh*8+7 of this chunk -> tensor memory
         uint32_t ov[8];
 #pragma unroll
         for (int i = 0; i < 8; i++) ov[i] = __float_as_uint(in_d[(hh * 8 + i) * kBigDW + c + kBigHalo]);
@@ -274,76 +322,129 @@ __global__ void __launch_bounds__(kBigThreads, 1) k_tc_big(
       asm volatile("fence.proxy.async.shared::cta;");
       __syncwarp();
       if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(&rhs_full[s])) : "memory");
-      if (kc == NK - 1) {
+      if (kc == NKe - 1) {
         // last chunk of the tile: drain the accumulators once its MMAs are done.  Warp
         // w reads the lanes (cells) 32 (w % 4) .. +31; the n columns (unknowns) go in
         // blocks of 32 to the two warps of a lane quarter alternately; each register
         // of a block is one unknown of the lane's cell, so every load and store is a
         // 128-byte row of 32 cells.  The old correction of the next block is loaded
-        // before this one's accumulators are read.
+        // before this one's accumulators are read; in the coupling form z of the
+        // warp's first block is loaded while the last chunk's MMAs run.
+        const int q4 = w & 3, g2 = w >> 2;
+        const int j = tile * kBigN + 32 * q4 + lane;
+        const bool act = j < J && keep;  // only this item's cells
+        const int nb = n / 32;  // column blocks
+        if (half && act && g2 < nb) {  // z of the warp's first block into L1 while the last chunk's MMAs run
+#pragma unroll
+          for (int i = 0; i < 32; i++) asm volatile("prefetch.global.L1 [%0];" ::"l"(Zt + (size_t)(g2 * 32 + i) * Jp + j));
+        }
         if (!__all_sync(0xffffffffu, big_wait(su32(&mma_done[s]), (uint32_t)(u3 & 1)))) {
           s_fail = 1;
           failed = true;
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;");
-        const int q4 = w & 3, g2 = w >> 2;
-        const int j = tile * kBigN + 32 * q4 + lane;
-        const bool act = j < J && keep;  // only this item's cells
-        const int nb = n / 32;  // column blocks
-        float dold[32], dnxt[32];
-        auto load_old = [&](int b_, float *dst) {
-          if (stash) {  // from the builders' copy in tensor memory
-            uint32_t o[32];
-            const uint32_t oa = tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)(kBigStash + b_ * 32);
+        if (half) {  // delta = z + D; the old correction from the builders' copy in tensor memory
+          // (in half blocks of 16 columns: two tensor-memory reads and z per half; z of the
+          // warp's next block is prefetched into L1 when a block starts)
+#pragma unroll 1
+          for (int hb = 2 * g2; hb < 2 * nb; hb += (hb & 1) ? 3 : 1) {  // halves 2 b_, 2 b_ + 1 of the warp's blocks
+            if (!(hb & 1) && act && hb / 2 + 2 < nb) {
+#pragma unroll
+              for (int i = 0; i < 32; i++)
+                asm volatile("prefetch.global.L1 [%0];" ::"l"(Zt + (size_t)((hb / 2 + 2) * 32 + i) * Jp + j));
+            }
+            float zc[16];
+#pragma unroll
+            for (int i = 0; i < 16; i++) zc[i] = act ? Zt[(size_t)(hb * 16 + i) * Jp + j] : 0.f;
+            uint32_t r[16], o[16];
+            const uint32_t addr = tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)(hb * 16);
             asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                  "=r"(r[15])
+                : "r"(addr));
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
                 : "=r"(o[0]), "=r"(o[1]), "=r"(o[2]), "=r"(o[3]), "=r"(o[4]), "=r"(o[5]), "=r"(o[6]), "=r"(o[7]),
                   "=r"(o[8]), "=r"(o[9]), "=r"(o[10]), "=r"(o[11]), "=r"(o[12]), "=r"(o[13]), "=r"(o[14]),
-                  "=r"(o[15]), "=r"(o[16]), "=r"(o[17]), "=r"(o[18]), "=r"(o[19]), "=r"(o[20]), "=r"(o[21]),
-                  "=r"(o[22]), "=r"(o[23]), "=r"(o[24]), "=r"(o[25]), "=r"(o[26]), "=r"(o[27]), "=r"(o[28]),
-                  "=r"(o[29]), "=r"(o[30]), "=r"(o[31])
-                : "r"(oa));
+                  "=r"(o[15])
+                : "r"(addr + (uint32_t)kBigStash));
             asm volatile("tcgen05.wait::ld.sync.aligned;");
+            if (act) {
 #pragma unroll
-            for (int i = 0; i < 32; i++) dst[i] = (act && !zero) ? __uint_as_float(o[i]) : 0.f;
-          } else {
-#pragma unroll
-            for (int i = 0; i < 32; i++) dst[i] = (act && !zero) ? Din[(size_t)(b_ * 32 + i) * Jp + j] : 0.f;
-          }
-        };
-        if (g2 < nb) load_old(g2, dold);
-#pragma unroll 1
-        for (int b_ = g2; b_ < nb; b_ += 2) {
-          uint32_t r[32];
-          const uint32_t addr = tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)(b_ * 32);
-          asm volatile(
-              "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-              : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
-                "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
-                "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-              : "r"(addr));
-          if (b_ + 2 < nb) load_old(b_ + 2, dnxt);
-          asm volatile("tcgen05.wait::ld.sync.aligned;");
-          if (act) {
-#pragma unroll
-            for (int i = 0; i < 32; i++) {
-              const float o = __uint_as_float(r[i]);
-              const float d = o - dold[i];
-              e2 = fmaf(d, d, e2);
-              Dout[(size_t)(b_ * 32 + i) * Jp + j] = o;
+              for (int i = 0; i < 16; i++) {
+                const float x = __uint_as_float(r[i]) + zc[i];
+                const float d = x - __uint_as_float(o[i]);
+                e2 = fmaf(d, d, e2);
+                Dout[(size_t)(hb * 16 + i) * Jp + j] = x;
+              }
             }
           }
+          asm volatile("tcgen05.fence::before_thread_sync;");
+          __syncwarp();
+          if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(&tmem_empty)) : "memory");
+        } else {
+          float dold[32], dnxt[32];
+          const bool zt_w = zero && Zt && act;
+          auto load_old = [&](int b_, float *dst) {
+            if (stash) {  // from the builders' copy in tensor memory
+              uint32_t o[32];
+              const uint32_t oa = tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)(kBigStash + b_ * 32);
+              asm volatile(
+                  "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                  : "=r"(o[0]), "=r"(o[1]), "=r"(o[2]), "=r"(o[3]), "=r"(o[4]), "=r"(o[5]), "=r"(o[6]), "=r"(o[7]),
+                    "=r"(o[8]), "=r"(o[9]), "=r"(o[10]), "=r"(o[11]), "=r"(o[12]), "=r"(o[13]), "=r"(o[14]),
+                    "=r"(o[15]), "=r"(o[16]), "=r"(o[17]), "=r"(o[18]), "=r"(o[19]), "=r"(o[20]), "=r"(o[21]),
+                    "=r"(o[22]), "=r"(o[23]), "=r"(o[24]), "=r"(o[25]), "=r"(o[26]), "=r"(o[27]), "=r"(o[28]),
+                    "=r"(o[29]), "=r"(o[30]), "=r"(o[31])
+                  : "r"(oa));
+              asm volatile("tcgen05.wait::ld.sync.aligned;");
 #pragma unroll
-          for (int i = 0; i < 32; i++) dold[i] = dnxt[i];
+              for (int i = 0; i < 32; i++) dst[i] = (act && !zero) ? __uint_as_float(o[i]) : 0.f;
+            } else {
+#pragma unroll
+              for (int i = 0; i < 32; i++) dst[i] = (act && !zero) ? Din[(size_t)(b_ * 32 + i) * Jp + j] : 0.f;
+            }
+          };
+          if (g2 < nb) load_old(g2, dold);
+#pragma unroll 1
+          for (int b_ = g2; b_ < nb; b_ += 2) {
+            uint32_t r[32];
+            const uint32_t addr = tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)(b_ * 32);
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                  "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                  "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                  "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                : "r"(addr));
+            if (b_ + 2 < nb) load_old(b_ + 2, dnxt);
+            asm volatile("tcgen05.wait::ld.sync.aligned;");
+            if (act) {
+#pragma unroll
+              for (int i = 0; i < 32; i++) {
+                const float o = __uint_as_float(r[i]);
+                const float d = o - dold[i];
+                e2 = fmaf(d, d, e2);
+                Dout[(size_t)(b_ * 32 + i) * Jp + j] = o;
+              }
+            }
+            if (zt_w) {  // the first sweep of a refinement block is z = A~^{-1} r, kept for the coupling sweeps
+#pragma unroll
+              for (int i = 0; i < 32; i++) Zt[(size_t)(b_ * 32 + i) * Jp + j] = __uint_as_float(r[i]);
+            }
+#pragma unroll
+            for (int i = 0; i < 32; i++) dold[i] = dnxt[i];
+          }
+          asm volatile("tcgen05.fence::before_thread_sync;");
+          __syncwarp();
+          if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(&tmem_empty)) : "memory");
         }
-        asm volatile("tcgen05.fence::before_thread_sync;");
-        __syncwarp();
-        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(&tmem_empty)) : "memory");
       }
-      if (++kc == NK) {
+      if (++kc == NKe) {
         kc = 0;
         it += gridDim.x;
         if (MIXED) {
@@ -371,7 +472,7 @@ __global__ void __launch_bounds__(kBigThreads, 1) k_tc_big(
       for (int g = 0, s = 0, u3 = 0, kc = 0; g < n_chunks; g++) {
         // this chunk's RHS is built and its A^{-1} chunk has landed; a new tile waits for the drain
         bool ok = big_wait(su32(&rhs_full[s]), (uint32_t)(u3 & 1)) && big_wait(su32(&a_full[s]), (uint32_t)(u3 & 1));
-        if (ok && kc == 0 && g > 0) ok = big_wait(su32(&tmem_empty), (uint32_t)(((g / NK) - 1) & 1));
+        if (ok && kc == 0 && g > 0) ok = big_wait(su32(&tmem_empty), (uint32_t)(((g / NKe) - 1) & 1));
         if (!ok) {
           failed = true;
           break;
@@ -406,7 +507,7 @@ __global__ void __launch_bounds__(kBigThreads, 1) k_tc_big(
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
             su32(&mma_done[s])));
         n_m[s]++;
-        if (++kc == NK) kc = 0;
+        if (++kc == NKe) kc = 0;
         if (++s == kBigStages) {
           s = 0;
           u3++;
@@ -428,32 +529,46 @@ __global__ void __launch_bounds__(kBigThreads, 1) k_tc_big(
         if (MIXED) icache[i] = item_at(i);
         else tau_of[i] = type[tile_at(i) * kBigN];
       }
+      int next_item = 4;  // the next item to read ahead
       auto issue_in = [&](int g_) {
         const int b_ = g_ % kBigInBuf;
         float *dst = (float *)(in_base + (size_t)b_ * kBigInBytes);
         const uint32_t bar = su32(&in_full[b_]);
-        const int x0 = (MIXED ? icache[(g_ / NK) & 3].x : tile_at(g_ / NK)) * kBigN, y0 = (g_ % NK) * kBigKC;
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kBigInBytes) : "memory");
-        asm volatile(
-            "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-                su32(dst)),
-            "l"(reinterpret_cast<uint64_t>(&tmR)), "r"(x0), "r"(y0), "r"(bar)
-            : "memory");
-        asm volatile(
-            "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-                su32(dst + kBigKC * kBigN)),
-            "l"(reinterpret_cast<uint64_t>(dcur ? &tmD1 : &tmD0)), "r"(x0 - kBigHalo), "r"(y0), "r"(bar)
-            : "memory");
+        const int x0 = (MIXED ? icache[(g_ / NKe) & 3].x : tile_at(g_ / NKe)) * kBigN;
+        const uint64_t tmd = reinterpret_cast<uint64_t>(dcur ? &tmD1 : &tmD0);
+        if (half) {  // rows 32 kc .. 32 kc + 31 of the correction, as two boxes of 16
+          const int y0 = (g_ % NKe) * 2 * kBigKC;
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kBigInHalf) : "memory");
+          for (int h2 = 0; h2 < 2; h2++)
+            asm volatile(
+                "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+                    su32(dst + h2 * kBigKC * kBigDW)),
+                "l"(tmd), "r"(x0 - kBigHalo), "r"(y0 + h2 * kBigKC), "r"(bar)
+                : "memory");
+        } else {
+          const int y0 = (g_ % NKe) * kBigKC;
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kBigInFull) : "memory");
+          asm volatile(
+              "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+                  su32(dst)),
+              "l"(reinterpret_cast<uint64_t>(&tmR)), "r"(x0), "r"(y0), "r"(bar)
+              : "memory");
+          asm volatile(
+              "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+                  su32(dst + kBigKC * kBigN)),
+              "l"(tmd), "r"(x0 - kBigHalo), "r"(y0), "r"(bar)
+              : "memory");
+        }
         n_in[b_]++;
       };
       auto issue_a = [&](int g_) {
         const int s_ = g_ % kBigStages;
-        const int ti = g_ / NK, tau_ = MIXED ? icache[ti & 3].y & 0x3FFFFFFF : tau_of[ti & 3], kc_ = g_ % NK;
+        const int ti = g_ / NKe, tau_ = MIXED ? icache[ti & 3].y & 0x3FFFFFFF : tau_of[ti & 3], kc_ = g_ % NKe;
         unsigned char *dst = sm + (size_t)s_ * stage_bytes;
         const uint32_t bar = su32(&a_full[s_]);
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(NT * kBigABlk) : "memory");
         for (int nt = 0; nt < NT; nt++) {
-          const unsigned char *src = Aimg + (((size_t)tau_ * NT + nt) * NK + kc_) * kBigABlk;
+          const unsigned char *src = (half ? AimgH : Aimg) + (((size_t)tau_ * NT + nt) * NKe + kc_) * kBigABlk;
           asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                            su32(dst + (size_t)nt * kBigABlk)),
                        "l"(reinterpret_cast<uint64_t>(src)), "r"(kBigABlk), "r"(bar)
@@ -470,12 +585,12 @@ __global__ void __launch_bounds__(kBigThreads, 1) k_tc_big(
           break;
         }
         if (g + kBigInBuf < n_chunks) issue_in(g + kBigInBuf);
-        if ((g + kBigStages) % NK == 0) {  // item i + 3 gets its type read when item i's last A copy is issued
-          const int ti = (g + kBigStages) / NK + 3;
-          if (ti < my_items) {
-            if (MIXED) icache[ti & 3] = item_at(ti);
-            else tau_of[ti & 3] = type[tile_at(ti) * kBigN];
-          }
+        // items up to three past the one whose chunk is issued now are read ahead: item i
+        // takes the slot of item i - 4, all of whose copies have been issued (with one or
+        // two chunks per item several items may become due in one step)
+        for (const int due = (g + kBigStages) / NKe + 3; next_item < my_items && next_item <= due; next_item++) {
+          if (MIXED) icache[next_item & 3] = item_at(next_item);
+          else tau_of[next_item & 3] = type[tile_at(next_item) * kBigN];
         }
         // chunk g's MMAs are done: chunk g + 3's A^{-1} goes into its stage
         if (g + kBigStages < n_chunks) {
@@ -606,12 +721,12 @@ int tc_big_grid(const Handle &h) {
 
 void launch_tc_big(Handle &h, cudaGraphConditionalHandle cond, int use_cond) {
   const size_t smem = tc_big_smem(h);
-  const int grid = tc_big_grid(h), NT = tc_big_nt(h), NK = tc_big_nk(h);
+  const int grid = tc_big_grid(h), NT = tc_big_nt(h), NK = tc_big_nk(h), NKH = 4 * h.N * h.G / 32;
 #define OCI_TC_BIG_LAUNCH(K, M)                                                                                     \
   k_tc_big<K, M><<<grid, kBigThreads, smem, h.stream>>>(h.tm_bg_r, h.tm_bg_d[0], h.tm_bg_d[1], h.J, h.Jp, h.N, h.G, \
                                                         NT, NK, h.type, h.tc_img, h.mu32, h.z32, h.delta[0],          \
                                                         h.delta[1], h.ds, h.partials, h.counter, h.e_hist, cond,      \
-                                                        use_cond, h.tc_items, h.tc_n_items)
+                                                        use_cond, h.tc_items, h.tc_n_items, h.tc_img_h, NKH, h.tc_z)
   const bool tf = h.precision == OCI_TF32_IR;
   if (h.tc_mixed) {
     if (tf) OCI_TC_BIG_LAUNCH(1, true);
@@ -662,6 +777,48 @@ int tc_big_build_images(Handle &h, const std::vector<double> &Ainv, float (*roun
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(tensor images)");
   e = cudaStreamSynchronize(h.stream);
   if (e != cudaSuccess) return cuda_fail(e, "tensor images");
+  // Coupling image, for n a multiple of 32 up to one N-tile (the old correction then
+  // stays in tensor memory): the inner sweeps after a refinement block's first are
+  // delta = z + (A~^{-1} B) U, where B delta^i puts |mu_m| times an upstream corner
+  // of the neighbour into two rows of each (group, angle) block -- kL, hL for mu > 0,
+  // kR, hR for mu < 0 (Eq. rhs_sg applied to the correction).  Column 2 (gN + m) + s
+  // (s = 0 time average, 1 time edge) of the image is |mu_m| times column
+  // 4 (gN + m) + (mu_m > 0 ? 2s : 2s + 1) of A~^{-1}, laid out like the full image
+  // with K = n / 2.  OCI_TC_HALF=0 (a test hook) keeps the full form for every sweep.
+  const char *hv = hook_env("OCI_TC_HALF");
+  if (n % 32 != 0 || n > kBigNT || (hv && hv[0] == '0')) return OCI_OK;
+  const int NKH = n / 32, nh = n / 2;
+  std::vector<unsigned char> imh((size_t)T * NT * NKH * kBigABlk, 0);
+  for (int t = 0; t < T; t++)
+    for (int nt = 0; nt < NT; nt++)
+      for (int kc = 0; kc < NKH; kc++) {
+        unsigned char *blk = imh.data() + (((size_t)t * NT + nt) * NKH + kc) * kBigABlk;
+        for (int rl = 0; rl < kBigNT; rl++)
+          for (int kl = 0; kl < kBigKC; kl++) {
+            const int r = nt * kBigNT + rl, k = kc * kBigKC + kl;
+            if (r >= n || k >= nh) continue;
+            const int gm = k / 2, sc = k % 2, m = gm % h.N;
+            const bool pos = m >= h.N / 2;
+            const int col = 4 * gm + (pos ? 2 * sc : 2 * sc + 1);
+            const float v = (float)(fabs(h.h_mu[m]) * Ainv[((size_t)t * n + r) * n + col]);
+            const uint32_t off = big_off(rl, kl, es);
+            if (tf) {
+              const float q = round_tf32(v);
+              memcpy(blk + off, &q, 4);
+            } else {
+              const uint16_t hi = bf16_bits(v);
+              const uint16_t lo = bf16_bits(v - bf16_value(hi));
+              memcpy(blk + off, &hi, 2);
+              memcpy(blk + kBigABlk / 2 + off, &lo, 2);
+            }
+          }
+      }
+  e = cudaMalloc(&h.tc_img_h, imh.size());
+  if (e == cudaSuccess) e = cudaMalloc(&h.tc_z, (size_t)n * h.Jp * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemsetAsync(h.tc_z, 0, (size_t)n * h.Jp * sizeof(float), h.stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h.tc_img_h, imh.data(), imh.size(), cudaMemcpyHostToDevice, h.stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h.stream);
+  if (e != cudaSuccess) return cuda_fail(e, "tensor coupling image");
   return OCI_OK;
 }
 

@@ -161,9 +161,13 @@ def test_tensor_core_forms_with_regions_inside_tiles_match_oracle(prec, seed, J,
 
 
 @pytest.mark.parametrize("prec", [oci.TF32_IR, oci.BF16X3_IR])
-def test_tensor_core_full_size_matches_fp64_path(prec):
-    """Precision form of the 2^18-cell S16 slab: two steps against the FP64 path."""
-    p = W.slab_3region(c=0.9, tau=0.1)
+@pytest.mark.parametrize("N,J", [(16, 2 ** 18), (8, 2 ** 17)])
+def test_tensor_core_full_size_matches_fp64_path(prec, N, J):
+    """Precision form of the three-region slab at full size (2^18 cells at S16;
+    2^17 at S8, 32 unknowns per cell: two K-chunks per tile in the full form, one
+    in the coupling form, and more than four tiles per CTA): two steps against
+    the FP64 path."""
+    p = W.slab_3region(c=0.9, tau=0.1, J=J, N=N)
     with oci.Solver(p) as a, oci.Solver(p, precision=prec) as b:
         for _ in range(2):
             sa, sb = a.step(), b.step()
@@ -480,3 +484,31 @@ def test_tensor_core_multigroup_recipe_matches_oracle_per_group(prec):
             assert rel(phi, r["phi"]) < 1e-10
             d = np.abs(phi - r["phi"]).max(axis=(0, 2)) / np.abs(r["phi"]).max(axis=(0, 2))
             assert d.max() < 1e-8, d
+
+
+@pytest.mark.parametrize("prec", [oci.TF32_IR, oci.BF16X3_IR])
+@pytest.mark.parametrize("seed,J,N,G,region", [(50, 700, 16, 1, 128), (51, 333, 8, 2, 100), (52, 257, 16, 4, 128),
+                                               (53, 200, 10, 4, 128), (54, 40, 8, 1, 128)])
+def test_tensor_core_coupling_sweeps_equal_full_sweeps(prec, seed, J, N, G, region, monkeypatch):
+    """Inner sweeps after the first of a refinement block as delta = z + (A~^{-1} B) u
+    over the n/2 inflow columns (z = A~^{-1} r from the block's first sweep) against
+    every sweep as the full A~^{-1} (r + B delta) (test hook OCI_TC_HALF=0): the same
+    converged step within 1e-10 of each other and of the oracle, sweeps within 12;
+    64, 128, 256 and 160 unknowns per cell, region boundaries inside tiles, one tile."""
+    p = _uniform_tiles(seed, J, N, G, region=region)
+    o = Oracle(p)
+    ref = [o.step(OCI) for _ in range(2)]
+    out = {}
+    for half in ("1", "0"):
+        monkeypatch.setenv("OCI_TC_HALF", half)
+        with oci.Solver(p, precision=prec) as s:
+            sts = [s.step() for _ in range(2)]
+            out[half] = (sts, s.phi(), s.psi())
+    for half in ("1", "0"):
+        sts, phi, psi = out[half]
+        for k in range(2):
+            assert sts[k]["status"] == 0
+            assert sts[k]["iters"] <= ref[k]["iters"] + 12, (half, k, sts[k]["iters"], ref[k]["iters"])
+        assert rel(phi, ref[-1]["phi"]) < 1e-10
+        assert rel(psi, o.Psi) < 1e-10
+    assert rel(out["1"][1], out["0"][1]) < 1e-10
