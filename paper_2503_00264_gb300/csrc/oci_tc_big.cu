@@ -26,7 +26,7 @@
 //   - after the last chunk of a tile the builder warps drain the accumulators
 //     (tcgen05.ld: one register per unknown, one lane per cell), form delta
 //     and the FP32 norm partial; loads and stores are 128-byte rows of 32 cells.
-// Coupling form (n a multiple of 32, n <= 256): r is the same for every inner sweep
+// Coupling form (n a multiple of 32): r is the same for every inner sweep
 // of a refinement block, so the block's first sweep (zero old correction, the
 // full form above) also stores z = A~^{-1} r, and every later sweep computes
 //   delta = z + U . (A~^{-1} B)^T
@@ -334,26 +334,30 @@ __global__ void __launch_bounds__(kBigThreads, 1) k_tc_big(
         const int j = tile * kBigN + 32 * q4 + lane;
         const bool act = j < J && keep;  // only this item's cells
         const int nb = n / 32;  // column blocks
-        if (half && act && g2 < nb) {  // z of the warp's first block into L1 while the last chunk's MMAs run
-#pragma unroll
-          for (int i = 0; i < 32; i++) asm volatile("prefetch.global.L1 [%0];" ::"l"(Zt + (size_t)(g2 * 32 + i) * Jp + j));
-        }
+        // coupling form: z (and, above 256 unknowns, the old correction) of the warp's first
+        // block into L1 while the last chunk's MMAs run
+        auto prefetch_block = [&](int b_) {
+          const size_t ix = (size_t)(b_ * 32) * Jp + j;
+          const float *pz = Zt + ix, *pd = Din + ix;
+#pragma unroll 4
+          for (int i = 0; i < 32; i++, pz += Jp, pd += Jp) {
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(pz));
+            if (!stash) asm volatile("prefetch.global.L1 [%0];" ::"l"(pd));
+          }
+        };
+        if (half && act && g2 < nb) prefetch_block(g2);
         if (!__all_sync(0xffffffffu, big_wait(su32(&mma_done[s]), (uint32_t)(u3 & 1)))) {
           s_fail = 1;
           failed = true;
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;");
-        if (half) {  // delta = z + D; the old correction from the builders' copy in tensor memory
+        if (half) {  // delta = z + D
           // (in half blocks of 16 columns: two tensor-memory reads and z per half; z of the
           // warp's next block is prefetched into L1 when a block starts)
 #pragma unroll 1
           for (int hb = 2 * g2; hb < 2 * nb; hb += (hb & 1) ? 3 : 1) {  // halves 2 b_, 2 b_ + 1 of the warp's blocks
-            if (!(hb & 1) && act && hb / 2 + 2 < nb) {
-#pragma unroll
-              for (int i = 0; i < 32; i++)
-                asm volatile("prefetch.global.L1 [%0];" ::"l"(Zt + (size_t)((hb / 2 + 2) * 32 + i) * Jp + j));
-            }
+            if (!(hb & 1) && act && hb / 2 + 2 < nb) prefetch_block(hb / 2 + 2);
             float zc[16];
 #pragma unroll
             for (int i = 0; i < 16; i++) zc[i] = act ? Zt[(size_t)(hb * 16 + i) * Jp + j] : 0.f;
@@ -365,12 +369,17 @@ __global__ void __launch_bounds__(kBigThreads, 1) k_tc_big(
                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
                   "=r"(r[15])
                 : "r"(addr));
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                : "=r"(o[0]), "=r"(o[1]), "=r"(o[2]), "=r"(o[3]), "=r"(o[4]), "=r"(o[5]), "=r"(o[6]), "=r"(o[7]),
-                  "=r"(o[8]), "=r"(o[9]), "=r"(o[10]), "=r"(o[11]), "=r"(o[12]), "=r"(o[13]), "=r"(o[14]),
-                  "=r"(o[15])
-                : "r"(addr + (uint32_t)kBigStash));
+            if (stash) {  // the old correction from the builders' copy in tensor memory
+              asm volatile(
+                  "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                  : "=r"(o[0]), "=r"(o[1]), "=r"(o[2]), "=r"(o[3]), "=r"(o[4]), "=r"(o[5]), "=r"(o[6]), "=r"(o[7]),
+                    "=r"(o[8]), "=r"(o[9]), "=r"(o[10]), "=r"(o[11]), "=r"(o[12]), "=r"(o[13]), "=r"(o[14]),
+                    "=r"(o[15])
+                  : "r"(addr + (uint32_t)kBigStash));
+            } else {  // from HBM (prefetched into L1 a block ahead)
+#pragma unroll
+              for (int i = 0; i < 16; i++) o[i] = act ? __float_as_uint(Din[(size_t)(hb * 16 + i) * Jp + j]) : 0u;
+            }
             asm volatile("tcgen05.wait::ld.sync.aligned;");
             if (act) {
 #pragma unroll
@@ -777,8 +786,7 @@ int tc_big_build_images(Handle &h, const std::vector<double> &Ainv, float (*roun
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(tensor images)");
   e = cudaStreamSynchronize(h.stream);
   if (e != cudaSuccess) return cuda_fail(e, "tensor images");
-  // Coupling image, for n a multiple of 32 up to one N-tile (the old correction then
-  // stays in tensor memory): the inner sweeps after a refinement block's first are
+  // Coupling image, for n a multiple of 32: the inner sweeps after a refinement block's first are
   // delta = z + (A~^{-1} B) U, where B delta^i puts |mu_m| times an upstream corner
   // of the neighbour into two rows of each (group, angle) block -- kL, hL for mu > 0,
   // kR, hR for mu < 0 (Eq. rhs_sg applied to the correction).  Column 2 (gN + m) + s
@@ -786,7 +794,7 @@ int tc_big_build_images(Handle &h, const std::vector<double> &Ainv, float (*roun
   // 4 (gN + m) + (mu_m > 0 ? 2s : 2s + 1) of A~^{-1}, laid out like the full image
   // with K = n / 2.  OCI_TC_HALF=0 (a test hook) keeps the full form for every sweep.
   const char *hv = hook_env("OCI_TC_HALF");
-  if (n % 32 != 0 || n > kBigNT || (hv && hv[0] == '0')) return OCI_OK;
+  if (n % 32 != 0 || (hv && hv[0] == '0')) return OCI_OK;
   const int NKH = n / 32, nh = n / 2;
   std::vector<unsigned char> imh((size_t)T * NT * NKH * kBigABlk, 0);
   for (int t = 0; t < T; t++)

@@ -488,13 +488,15 @@ def test_tensor_core_multigroup_recipe_matches_oracle_per_group(prec):
 
 @pytest.mark.parametrize("prec", [oci.TF32_IR, oci.BF16X3_IR])
 @pytest.mark.parametrize("seed,J,N,G,region", [(50, 700, 16, 1, 128), (51, 333, 8, 2, 100), (52, 257, 16, 4, 128),
-                                               (53, 200, 10, 4, 128), (54, 40, 8, 1, 128)])
+                                               (53, 200, 10, 4, 128), (54, 40, 8, 1, 128), (55, 300, 16, 8, 100),
+                                               (56, 140, 32, 4, 128)])
 def test_tensor_core_coupling_sweeps_equal_full_sweeps(prec, seed, J, N, G, region, monkeypatch):
     """Inner sweeps after the first of a refinement block as delta = z + (A~^{-1} B) u
     over the n/2 inflow columns (z = A~^{-1} r from the block's first sweep) against
     every sweep as the full A~^{-1} (r + B delta) (test hook OCI_TC_HALF=0): the same
     converged step within 1e-10 of each other and of the oracle, sweeps within 12;
-    64, 128, 256 and 160 unknowns per cell, region boundaries inside tiles, one tile."""
+    64, 128, 256, 160 and 512 unknowns per cell (above 256 the old correction comes
+    from HBM), region boundaries inside tiles, one tile."""
     p = _uniform_tiles(seed, J, N, G, region=region)
     o = Oracle(p)
     ref = [o.step(OCI) for _ in range(2)]
