@@ -37,6 +37,20 @@ struct Ms2Args {
   float *y_s, *yr_s, *s_s, *ring, *halo;
 };
 
+// The next tile's z and correction (two contiguous chunks of 4NG*T floats in the
+// tile-major layout) into L1 while this tile is solved: one prefetch per thread
+// and 128-byte line, no registers held.
+template <int T>
+__device__ __forceinline__ void ms2_prefetch_tile(const float *z, const float *Din, int tile, int R, int tid,
+                                                  int nthr) {
+  const int lines = R * T / 32;
+  const size_t base = (size_t)tile * R * T;
+  for (int l = tid; l < 2 * lines; l += nthr) {
+    const float *p = (l < lines ? z : Din) + base + (size_t)(l < lines ? l : l - lines) * 32;
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+  }
+}
+
 // One sweep over the block's run (delta_in -> delta_out); returns the thread's
 // sum of squared changes.
 template <int T, int NP, int PS, int GS>
@@ -47,6 +61,7 @@ __device__ float ms2_pass1(const Ms2Args &a, int cl, int gy, bool zero, const fl
   const int g = gy / P, m0 = (gy % P) * NP;
   float e2 = 0.f;
   for (int k = a.t0; k < a.t1; k++) {
+    if (k + 1 < a.t1) ms2_prefetch_tile<T>(a.z, Din, k + 1, R, gy * T + cl, T * P * G);
     float zr[NP][4], old[NP][4], uk[NP], uh[NP], o[NP][4];
     const int j = k * T + cl;
     const bool act = j < a.J;
@@ -96,6 +111,7 @@ __device__ void ms2_pass2(const Ms2Args &a, int cl, int gy, bool zero, const flo
   // ring slots of tiles k (cur), k-1 (prv) and k-2 (pp)
   float *cur = a.ring, *prv = a.ring + R * T, *pp = a.ring + 2 * R * T;
   for (int k = a.t0; k <= a.t1; k++) {
+    if (k + 1 < a.t1) ms2_prefetch_tile<T>(a.z, Din, k + 1, R, gy * T + cl, T * P * G);
     if (k < a.t1) {  // sweep i+1 on tile k
       float zr[NP][4], old[NP][4], uk[NP], uh[NP], o1[NP][4];
       const int j = k * T + cl;
