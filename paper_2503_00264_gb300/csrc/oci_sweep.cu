@@ -291,14 +291,19 @@ __device__ __forceinline__ double ld_psi(const double *p) {
 // block's shared memory holds y [G*P*4][CB], y reduced [4G][CB] and s [4G][CB].
 // Writes Pout for the active cells and returns the thread's sum of
 // (Psi_new - Psi_old)^2.  Contains block-wide barriers: every thread calls it.
-template <int NP, bool CG>
+// HOIST: the cell's inflow weights, L^{-1}, step constant and |mu| of the
+// thread's angles come from the caller's registers (Wh, Lh, tch, amh) instead
+// of memory.
+template <int NP, bool CG, bool HOIST = false>
 __device__ __forceinline__ double reg_cells(int j, int J, int Jp, int N, int G, int CB, int cl, int gy,
                                             const int32_t *__restrict__ type, const double *__restrict__ Linv,
                                             const double *__restrict__ Mp, const double *__restrict__ inc,
                                             const double *__restrict__ tc, const double *__restrict__ Pin,
                                             double *__restrict__ Pout, const double *__restrict__ Pnb,
                                             const double *__restrict__ Win, const double *__restrict__ yc,
-                                            const double *__restrict__ mu, double *y_s, double *yr_s, double *s_s) {
+                                            const double *__restrict__ mu, double *y_s, double *yr_s, double *s_s,
+                                            const double (*Wh)[8] = nullptr, const double (*Lh)[16] = nullptr,
+                                            const double (*tch)[4] = nullptr, const double *amh = nullptr) {
   const int P = N / NP, G4 = 4 * G;
   const int g = gy / P, ch = gy % P, m0 = ch * NP;
   const bool active = j < J;
@@ -341,7 +346,9 @@ __device__ __forceinline__ double reg_cells(int j, int J, int Jp, int N, int G, 
       }
       u[i][0] = uk;
       u[i][1] = uh;
-      const double *W = Win + (tb + gm) * 8;
+      const double *W;
+      if constexpr (HOIST) W = Wh[i];
+      else W = Win + (tb + gm) * 8;
       y0 = fma(W[1], uh, fma(W[0], uk, y0));
       y1 = fma(W[3], uh, fma(W[2], uk, y1));
       y2 = fma(W[5], uh, fma(W[4], uk, y2));
@@ -379,15 +386,21 @@ __device__ __forceinline__ double reg_cells(int j, int J, int Jp, int N, int G, 
       const int m = m0 + i;
       const int gm = g * N + m;
       const size_t base = (size_t)gm * 4 * Jp + j;
-      const double *L = Linv + (tb + gm) * 16;
-      // v = s + |mu| u in the rows the inflow feeds (0, 2 for mu > 0; 1, 3 for mu < 0)
-      const double am = fabs(mu[m]);
+      const double *L;
+      double am;  // v = s + |mu| u in the rows the inflow feeds (0, 2 for mu > 0; 1, 3 for mu < 0)
+      if constexpr (HOIST) {
+        L = Lh[i];
+        am = amh[i];
+      } else {
+        L = Linv + (tb + gm) * 16;
+        am = fabs(mu[m]);
+      }
       const bool pos = m >= N2;
       const double v0 = pos ? fma(am, u[i][0], s0) : s0, v1 = pos ? s1 : fma(am, u[i][0], s1);
       const double v2 = pos ? fma(am, u[i][1], s2) : s2, v3 = pos ? s3 : fma(am, u[i][1], s3);
 #pragma unroll
       for (int p = 0; p < 4; p++) {
-        const double o = fma(L[p * 4 + 3], v3, fma(L[p * 4 + 2], v2, fma(L[p * 4 + 1], v1, fma(L[p * 4 + 0], v0, tc[base + (size_t)p * Jp]))));
+        const double o = fma(L[p * 4 + 3], v3, fma(L[p * 4 + 2], v2, fma(L[p * 4 + 1], v1, fma(L[p * 4 + 0], v0, HOIST ? tch[HOIST ? i : 0][p] : tc[base + (size_t)p * Jp]))));
         const double d = o - (CG ? old[CG ? i : 0][p] : Pin[base + (size_t)p * Jp]);
         e2 = fma(d, d, e2);
         Pout[base + (size_t)p * Jp] = o;
@@ -470,7 +483,7 @@ __global__ void __launch_bounds__(256) k_oci_sweep_reg(
 // the step is done or after max_sweeps sweeps; a barrier that gives up records
 // OCI_E_TIMEOUT and ends the step.  gcount is zero at the launch.
 template <int NP>
-__global__ void __launch_bounds__(256, 2) k_oci_sweep_reg_ms(
+__global__ void __launch_bounds__(256, NP == 4 ? 2 : 1) k_oci_sweep_reg_ms(
     int J, int Jp, int N, int G, const int32_t *__restrict__ type, const double *__restrict__ Linv,
     const double *__restrict__ Mp, const double *__restrict__ inc, const double *__restrict__ tc, double *Psi0,
     double *Psi1, DevState *ds, double *__restrict__ partials, unsigned long long *gcount, double *e_hist,
@@ -491,13 +504,35 @@ __global__ void __launch_bounds__(256, 2) k_oci_sweep_reg_ms(
   double *y_s = smrd;
   double *yr_s = y_s + (size_t)G * P * 4 * CB;
   double *s_s = yr_s + (size_t)4 * G * CB;
+  // with two angles per thread the cell's constants stay in registers across the sweeps
+  // (the grid barrier's fences would otherwise have them reloaded in every sweep)
+  constexpr bool HOIST = NP == 2;
+  constexpr int NH = HOIST ? NP : 1;
+  double Wr[NH][8], Lr[NH][16], tcr[NH][4], amr[NH];
+  if constexpr (HOIST) {
+    const bool active = j < J;
+    const size_t tb = (size_t)(active ? type[j] : 0) * G * N;
+    const int g = gy / P, m0 = (gy % P) * NP;
+#pragma unroll
+    for (int i = 0; i < NP; i++) {
+      const int gm = g * N + m0 + i;
+      const size_t base = (size_t)gm * 4 * Jp + j;
+#pragma unroll
+      for (int k = 0; k < 8; k++) Wr[i][k] = active ? Win[(tb + gm) * 8 + k] : 0.0;
+#pragma unroll
+      for (int k = 0; k < 16; k++) Lr[i][k] = active ? Linv[(tb + gm) * 16 + k] : 0.0;
+#pragma unroll
+      for (int p = 0; p < 4; p++) tcr[i][p] = active ? tc[base + (size_t)p * Jp] : 0.0;
+      amr[i] = fabs(mu[m0 + i]);
+    }
+  }
   bool failed = false;
   for (int sw = 0;; sw++) {
     const int cur = sd.cur;
     const double *Pin = cur ? Psi1 : Psi0;
     double *Pout = cur ? Psi0 : Psi1;
-    const double e2 = reg_cells<NP, true>(j, J, Jp, N, G, CB, cl, gy, type, Linv, Mp, inc, tc, Pin, Pout, Pin, Win,
-                                          yc, mu, y_s, yr_s, s_s);
+    const double e2 = reg_cells<NP, true, HOIST>(j, J, Jp, N, G, CB, cl, gy, type, Linv, Mp, inc, tc, Pin, Pout, Pin,
+                                                 Win, yc, mu, y_s, yr_s, s_s, Wr, Lr, tcr, amr);
     const double bs = block_sum(e2, red);
     double *part = partials + (size_t)(sw & 1) * nb;
     if (tid == 0) {
@@ -593,6 +628,27 @@ __global__ void __launch_bounds__(256, 1) k_oci_sweep_cl(
 #pragma unroll
       for (int p = 0; p < 4; p++) ps[i][p] = active ? Pin[(size_t)((g * N + m0 + i) * 4 + p) * Jp + j] : 0.0;
   }
+  // The cell's constants of the solve -- the inflow weights, L^{-1}, the step constant
+  // and |mu| of the thread's angles -- are the same in every sweep; with two angles
+  // per thread they stay in registers (the cluster barrier's memory clobber would
+  // otherwise have them reloaded in every sweep).
+  constexpr bool HOIST = NP == 2;
+  constexpr int NH = HOIST ? NP : 1;
+  double Wr[NH][8], Lr[NH][16], tcr[NH][4], amr[NH];
+  if constexpr (HOIST) {
+#pragma unroll
+    for (int i = 0; i < NP; i++) {
+      const int gm = g * N + m0 + i;
+      const size_t base = (size_t)gm * 4 * Jp + j;
+#pragma unroll
+      for (int k = 0; k < 8; k++) Wr[i][k] = active ? Win[(tb + gm) * 8 + k] : 0.0;
+#pragma unroll
+      for (int k = 0; k < 16; k++) Lr[i][k] = active ? Linv[(tb + gm) * 16 + k] : 0.0;
+#pragma unroll
+      for (int p = 0; p < 4; p++) tcr[i][p] = active ? tc[base + (size_t)p * Jp] : 0.0;
+      amr[i] = fabs(mu[m0 + i]);
+    }
+  }
   auto publish = [&](int par) {
 #pragma unroll
     for (int i = 0; i < NP; i++) {
@@ -636,7 +692,9 @@ __global__ void __launch_bounds__(256, 1) k_oci_sweep_cl(
         }
         u[i][0] = uk;
         u[i][1] = uh;
-        const double *W = Win + (tb + gm) * 8;
+        double W[8];
+#pragma unroll
+        for (int k = 0; k < 8; k++) W[k] = HOIST ? Wr[HOIST ? i : 0][k] : Win[(tb + gm) * 8 + k];
         y0 = fma(W[1], uh, fma(W[0], uk, y0));
         y1 = fma(W[3], uh, fma(W[2], uk, y1));
         y2 = fma(W[5], uh, fma(W[4], uk, y2));
@@ -674,14 +732,18 @@ __global__ void __launch_bounds__(256, 1) k_oci_sweep_cl(
         const int m = m0 + i;
         const int gm = g * N + m;
         const size_t base = (size_t)gm * 4 * Jp + j;
-        const double *L = Linv + (tb + gm) * 16;
-        const double am = fabs(mu[m]);
+        double L[16], tcv[4];
+#pragma unroll
+        for (int k = 0; k < 16; k++) L[k] = HOIST ? Lr[HOIST ? i : 0][k] : Linv[(tb + gm) * 16 + k];
+#pragma unroll
+        for (int p = 0; p < 4; p++) tcv[p] = HOIST ? tcr[HOIST ? i : 0][p] : tc[base + (size_t)p * Jp];
+        const double am = HOIST ? amr[HOIST ? i : 0] : fabs(mu[m]);
         const bool pos = m >= N2;
         const double v0 = pos ? fma(am, u[i][0], s0) : s0, v1 = pos ? s1 : fma(am, u[i][0], s1);
         const double v2 = pos ? fma(am, u[i][1], s2) : s2, v3 = pos ? s3 : fma(am, u[i][1], s3);
 #pragma unroll
         for (int p = 0; p < 4; p++) {
-          const double o = fma(L[p * 4 + 3], v3, fma(L[p * 4 + 2], v2, fma(L[p * 4 + 1], v1, fma(L[p * 4 + 0], v0, tc[base + (size_t)p * Jp]))));
+          const double o = fma(L[p * 4 + 3], v3, fma(L[p * 4 + 2], v2, fma(L[p * 4 + 1], v1, fma(L[p * 4 + 0], v0, tcv[p]))));
           const double d = o - ps[i][p];
           e2 = fma(d, d, e2);
           ps[i][p] = o;
