@@ -287,14 +287,49 @@ __device__ __forceinline__ double ld_psi(const double *p) {
   else return *p;
 }
 
+// The inflows u of thread (cl, gy) of cell j, as reg_cells<NP, true> reads them
+// (through L2): the upstream corners of the neighbour in Pin, or the incident
+// flux at the slab ends; zeros for an inactive cell.
+template <int NP>
+__device__ __forceinline__ void reg_inflows(int j, int J, int Jp, int N, int G, int gy, const double *__restrict__ inc,
+                                            const double *Pin, double (&u)[NP][2]) {
+  const int P = N / NP, g = gy / P, m0 = (gy % P) * NP, N2 = N / 2;
+  const bool active = j < J;
+#pragma unroll
+  for (int i = 0; i < NP; i++) {
+    const int m = m0 + i, gm = g * N + m;
+    const size_t base = (size_t)gm * 4 * Jp + j;
+    double uk = 0.0, uh = 0.0;
+    if (active) {
+      if (m >= N2) {
+        if (j > 0) {
+          uk = __ldcg(Pin + base + (size_t)Jp - 1);
+          uh = __ldcg(Pin + base + 3 * (size_t)Jp - 1);
+        } else {
+          uk = inc[gm * 2 + 0];
+          uh = inc[gm * 2 + 1];
+        }
+      } else if (j < J - 1) {
+        uk = __ldcg(Pin + base + 1);
+        uh = __ldcg(Pin + base + 2 * (size_t)Jp + 1);
+      } else {
+        uk = inc[(G * N + gm) * 2 + 0];
+        uh = inc[(G * N + gm) * 2 + 1];
+      }
+    }
+    u[i][0] = uk;
+    u[i][1] = uh;
+  }
+}
+
 // The cells of one block of the register form: thread (cl, gy) of cell j; the
 // block's shared memory holds y [G*P*4][CB], y reduced [4G][CB] and s [4G][CB].
 // Writes Pout for the active cells and returns the thread's sum of
 // (Psi_new - Psi_old)^2.  Contains block-wide barriers: every thread calls it.
 // HOIST: the cell's inflow weights, L^{-1}, step constant and |mu| of the
 // thread's angles come from the caller's registers (Wh, Lh, tch, amh) instead
-// of memory.
-template <int NP, bool CG, bool HOIST = false>
+// of memory.  PRE: the inflows u were loaded by the caller (upre, reg_inflows).
+template <int NP, bool CG, bool HOIST = false, bool PRE = false>
 __device__ __forceinline__ double reg_cells(int j, int J, int Jp, int N, int G, int CB, int cl, int gy,
                                             const int32_t *__restrict__ type, const double *__restrict__ Linv,
                                             const double *__restrict__ Mp, const double *__restrict__ inc,
@@ -303,7 +338,8 @@ __device__ __forceinline__ double reg_cells(int j, int J, int Jp, int N, int G, 
                                             const double *__restrict__ Win, const double *__restrict__ yc,
                                             const double *__restrict__ mu, double *y_s, double *yr_s, double *s_s,
                                             const double (*Wh)[8] = nullptr, const double (*Lh)[16] = nullptr,
-                                            const double (*tch)[4] = nullptr, const double *amh = nullptr) {
+                                            const double (*tch)[4] = nullptr, const double *amh = nullptr,
+                                            const double (*upre)[2] = nullptr) {
   const int P = N / NP, G4 = 4 * G;
   const int g = gy / P, ch = gy % P, m0 = ch * NP;
   const bool active = j < J;
@@ -329,7 +365,10 @@ __device__ __forceinline__ double reg_cells(int j, int J, int Jp, int N, int G, 
       const int gm = g * N + m;
       const size_t base = (size_t)gm * 4 * Jp + j;
       double uk, uh;
-      if (m >= N2) {
+      if constexpr (PRE) {
+        uk = upre[i][0];
+        uh = upre[i][1];
+      } else if (m >= N2) {
         if (j > 0) {
           uk = ld_psi<CG>(Pnb + base + (size_t)Jp - 1);
           uh = ld_psi<CG>(Pnb + base + 3 * (size_t)Jp - 1);
@@ -483,7 +522,7 @@ __global__ void __launch_bounds__(256) k_oci_sweep_reg(
 // the step is done or after max_sweeps sweeps; a barrier that gives up records
 // OCI_E_TIMEOUT and ends the step.  gcount is zero at the launch.
 template <int NP>
-__global__ void __launch_bounds__(256, NP == 4 ? 2 : 1) k_oci_sweep_reg_ms(
+__global__ void __launch_bounds__(256, 1) k_oci_sweep_reg_ms(
     int J, int Jp, int N, int G, const int32_t *__restrict__ type, const double *__restrict__ Linv,
     const double *__restrict__ Mp, const double *__restrict__ inc, const double *__restrict__ tc, double *Psi0,
     double *Psi1, DevState *ds, double *__restrict__ partials, unsigned long long *gcount, double *e_hist,
@@ -527,12 +566,16 @@ __global__ void __launch_bounds__(256, NP == 4 ? 2 : 1) k_oci_sweep_reg_ms(
     }
   }
   bool failed = false;
+  // the inflows of a sweep are loaded right after the previous sweep's grid barrier,
+  // before its norm and stop rule (they do not depend on the decision)
+  double u[NP][2];
+  reg_inflows<NP>(j, J, Jp, N, G, gy, inc, sd.cur ? Psi1 : Psi0, u);
   for (int sw = 0;; sw++) {
     const int cur = sd.cur;
     const double *Pin = cur ? Psi1 : Psi0;
     double *Pout = cur ? Psi0 : Psi1;
-    const double e2 = reg_cells<NP, true, HOIST>(j, J, Jp, N, G, CB, cl, gy, type, Linv, Mp, inc, tc, Pin, Pout, Pin,
-                                                 Win, yc, mu, y_s, yr_s, s_s, Wr, Lr, tcr, amr);
+    const double e2 = reg_cells<NP, true, HOIST, true>(j, J, Jp, N, G, CB, cl, gy, type, Linv, Mp, inc, tc, Pin,
+                                                       Pout, Pin, Win, yc, mu, y_s, yr_s, s_s, Wr, Lr, tcr, amr, u);
     const double bs = block_sum(e2, red);
     double *part = partials + (size_t)(sw & 1) * nb;
     if (tid == 0) {
@@ -544,6 +587,7 @@ __global__ void __launch_bounds__(256, NP == 4 ? 2 : 1) k_oci_sweep_reg_ms(
       failed = true;
       break;
     }
+    reg_inflows<NP>(j, J, Jp, N, G, gy, inc, Pout, u);  // the next sweep's (harmless if the step ends here)
     const double tot = block_sum_fixed(part, nb, red);
     if (tid == 0) finish_fp64(&sd, blockIdx.x == 0 ? e_hist : nullptr, sqrt(tot), cond, 0);
     __syncthreads();
