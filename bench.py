@@ -55,7 +55,7 @@ SWEEP_DRAM_BYTES_NCU = {
     (0, 64, 2): 272.535552e6 + 99.228544e6,
     (1, 16, 4): 278.423552e6 + 105.256064e6, (1, 16, 8): 278.029312e6 + 106.006912e6,
     (1, 32, 2): 286.496128e6 + 104.577792e6, (1, 32, 4): 278.290304e6 + 104.930688e6,
-    (1, 32, 8): 277.979264e6 + 105.660672e6, (1, 64, 2): 286.199680e6 + 104.362752e6,
+    (1, 32, 8): 277.979264e6 + 105.660672e6, (1, 64, 2): 285.929216e6 + 105.565184e6,
     (1, 64, 4): 278.013440e6 + 104.868352e6,
 }
 # FP64 issue rate of one SM: 2 DFMA per clock (GB300: 1.25 TFLOP/s FP64 = 152 SMs x 2 x 2 flops
