@@ -44,41 +44,18 @@ __device__ __forceinline__ bool publish_partial(double *partials, int slot, doub
   return last;
 }
 
-// Sense-reversing grid barrier on {count, generation}; thread 0 of every block.
-// The spin is bounded by `limit` iterations (the device state's spin field,
-// kGridSpin unless a test lowers it); false when it gave up.
-__device__ __forceinline__ bool grid_barrier(unsigned *gbar, unsigned nblocks, long long limit) {
-  volatile unsigned *vgen = gbar + 1;
-  const unsigned g0 = *vgen;  // cannot advance before this block arrives
-  __threadfence();
-  const unsigned arrived = atomicAdd(gbar, 1u);
-  if (arrived == nblocks - 1) {
-    gbar[0] = 0;
-    __threadfence();
-    atomicAdd(gbar + 1, 1u);
-    return true;
-  }
-  for (long long k = 0; k < limit; k++) {
-    if (*vgen != g0) {
-      __threadfence();
-      return true;
-    }
-    __nanosleep(64);
-  }
-  return false;
-}
-
 // Grid barrier on a 64-bit arrival count that only grows within a launch (the
 // host zeroes it before the launch); thread 0 of every block.  Episode k of
 // the launch (k = 1, 2, ...) is passed once the count reaches k * nblocks: one
-// atomic add with release semantics per block (it publishes the block's
-// writes, ordered before it by the caller's __syncthreads) and acquire loads
-// while waiting -- no separate fences, no reset by the last block.  The spin is
+// atomic add with acquire-release semantics per block (release publishes the
+// block's writes, ordered before it by the caller's __syncthreads; acquire
+// makes the last block to arrive see everyone else's) and acquire loads while
+// waiting -- no separate fences, no reset by the last block.  The spin is
 // bounded by `limit`; false when it gave up.
 __device__ __forceinline__ bool grid_barrier_count(unsigned long long *count, unsigned long long target,
                                                    long long limit) {
   unsigned long long v;
-  asm volatile("atom.add.release.gpu.global.u64 %0, [%1], 1;" : "=l"(v) : "l"(count) : "memory");
+  asm volatile("atom.add.acq_rel.gpu.global.u64 %0, [%1], 1;" : "=l"(v) : "l"(count) : "memory");
   if (v + 1 >= target) return true;
   for (long long k = 0; k < limit; k++) {
     asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(count) : "memory");

@@ -129,7 +129,7 @@ struct Handle {
   double rb_tune_us = 0.0;             // its timed sweep (both colours), microseconds
   bool rb_tuned = false;               // red-black shapes timed (on the first switch to red-black)
   int mx_hwcvt = 0;                    // 1: FP64 refinement converts with the compiler's F2F (same bits, slower)
-  unsigned *gbar = nullptr;            // {count, generation} of the multi-sweep kernel's grid barrier
+  unsigned *gbar = nullptr;            // two words: the 64-bit arrival count of the cooperative kernels' grid barrier
   int mx_kind = 0;                     // FP32 inner sweep picked by the autotuner: kMxPlain, kMxTma, kMxReg, kMxTiled
   unsigned char *tc_img = nullptr;     // [T] x (A^{-1} image(s) in the tcgen05 K-major layout)
   size_t tc_img_bytes = 0;             // bytes per type

@@ -784,12 +784,13 @@ __global__ void __launch_bounds__(256) k_mx_inner_ms(int J, int N, int G, int n_
                                                      const int32_t *__restrict__ type, const float *Linv_g,
                                                      const float *Cin_g, const float *Mp_g, const float *w_g,
                                                      const float *__restrict__ z, float *D0, float *D1, DevState *ds,
-                                                     double *__restrict__ partials, unsigned *gbar, double *e_hist,
+                                                     double *__restrict__ partials, unsigned long long *gbar, double *e_hist,
                                                      cudaGraphConditionalHandle cond, int use_cond, int max_sweeps) {
   extern __shared__ __align__(16) float smr[];
   __shared__ double red[8];
   __shared__ DevState sd;
   __shared__ int s_ok;
+  unsigned long long gep = 0;  // thread 0: the arrival count the next grid barrier waits for
   const int P = N / NP, G4 = 4 * G;
   const int cl = threadIdx.x, gy = threadIdx.y;
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
@@ -821,7 +822,7 @@ __global__ void __launch_bounds__(256) k_mx_inner_ms(int J, int N, int G, int n_
     double *part = partials + (size_t)(sw & 1) * gridDim.x;
     if (tid == 0) {
       part[blockIdx.x] = bs;
-      s_ok = grid_barrier(gbar, gridDim.x, sd.spin);
+      s_ok = grid_barrier_count(gbar, gep += gridDim.x, sd.spin);
     }
     __syncthreads();
     if (!s_ok) {
@@ -871,9 +872,10 @@ static void launch_ms(Handle &h, int P, size_t smem, bool stage, cudaGraphCondit
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+  k_zero_gcount<<<1, 1, 0, h.stream>>>(reinterpret_cast<unsigned long long *>(h.gbar));
   cudaLaunchKernelEx(&cfg, k_mx_inner_ms<T, NP>, h.J, h.N, h.G, h.tt.n_types, (int)stage, (const int32_t *)h.type,
                      (const float *)h.tt.Linv32, (const float *)h.tt.Cin32, (const float *)h.tt.Mp32,
-                     (const float *)h.w32, (const float *)h.z32, h.delta[0], h.delta[1], h.ds, h.partials, h.gbar,
+                     (const float *)h.w32, (const float *)h.z32, h.delta[0], h.delta[1], h.ds, h.partials, reinterpret_cast<unsigned long long *>(h.gbar),
                      h.e_hist, cond, use_cond, max_sweeps);
 }
 
@@ -1258,12 +1260,13 @@ __global__ void __launch_bounds__(256) k_mx_rb(int J, int N, int G, int n_types,
                                                const int32_t *__restrict__ type, const float *Linv_g,
                                                const float *Cin_g, const float *Mp_g, const float *w_g,
                                                const float *__restrict__ z, float *D, DevState *ds,
-                                               double *__restrict__ partials, unsigned *gbar, double *e_hist,
+                                               double *__restrict__ partials, unsigned long long *gbar, double *e_hist,
                                                cudaGraphConditionalHandle cond, int use_cond, int max_sweeps) {
   extern __shared__ __align__(16) float smr[];
   __shared__ double red[8];
   __shared__ DevState sd;
   __shared__ int s_ok;
+  unsigned long long gep = 0;  // thread 0: the arrival count the next grid barrier waits for
   constexpr int TH = T / 2;
   const int P = N / NP, G4 = 4 * G;
   const int cl = threadIdx.x, gy = threadIdx.y;
@@ -1290,7 +1293,7 @@ __global__ void __launch_bounds__(256) k_mx_rb(int J, int N, int G, int n_types,
         e2 += rb_tile<T, NP>(tile, color, J, N, G, cl, gy, zero, type, Linv, Cin, Mp, w, z, D, y_s, yr_s, s_s);
       if (color == 0) {  // every red cell is written before any black cell reads it
         __syncthreads();
-        if (tid == 0) s_ok = grid_barrier(gbar, gridDim.x, sd.spin);
+        if (tid == 0) s_ok = grid_barrier_count(gbar, gep += gridDim.x, sd.spin);
         __syncthreads();
         if (!s_ok) failed = true;
       }
@@ -1300,7 +1303,7 @@ __global__ void __launch_bounds__(256) k_mx_rb(int J, int N, int G, int n_types,
     double *part = partials + (size_t)(sw & 1) * gridDim.x;
     if (tid == 0) {
       part[blockIdx.x] = bs;
-      s_ok = grid_barrier(gbar, gridDim.x, sd.spin);
+      s_ok = grid_barrier_count(gbar, gep += gridDim.x, sd.spin);
     }
     __syncthreads();
     if (!s_ok) {
@@ -1347,9 +1350,10 @@ static void launch_rb(Handle &h, int P, cudaGraphConditionalHandle cond, int use
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+  k_zero_gcount<<<1, 1, 0, h.stream>>>(reinterpret_cast<unsigned long long *>(h.gbar));
   cudaLaunchKernelEx(&cfg, k_mx_rb<T, NP>, h.J, h.N, h.G, h.tt.n_types, (int)stage, (const int32_t *)h.type,
                      (const float *)h.tt.Linv32, (const float *)h.tt.Cin32, (const float *)h.tt.Mp32,
-                     (const float *)h.w32, (const float *)h.z32, h.delta[0], h.ds, h.partials, h.gbar, h.e_hist,
+                     (const float *)h.w32, (const float *)h.z32, h.delta[0], h.ds, h.partials, reinterpret_cast<unsigned long long *>(h.gbar), h.e_hist,
                      cond, use_cond, max_sweeps);
 }
 

@@ -28,6 +28,10 @@ __device__ __forceinline__ void stage_tables(float *tab, int n_types, int N, int
   w = sw;
 }
 
+// Zero the grid barrier's arrival count (grid_barrier_count) before a cooperative
+// multi-sweep launch; one thread.
+static __global__ void k_zero_gcount(unsigned long long *c) { *c = 0ull; }
+
 // Fixed-order block sum of per-thread values (the result in thread 0).
 __device__ __forceinline__ double block_reduce_fixed(float e2, double *red, int tid, int nthr) {
   double v = (double)e2;

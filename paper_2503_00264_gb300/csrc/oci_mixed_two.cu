@@ -184,12 +184,13 @@ template <int T, int NP, int PS, int GS, int OCC>
 __global__ void __launch_bounds__((PS && GS) ? T * PS * GS : 256, OCC)
     k_mx_inner_ms2(int J, int N, int G, int n_types, int stage, const int32_t *__restrict__ type, const float *Linv_g,
                    const float *Cin_g, const float *Mp_g, const float *w_g, const float *__restrict__ z, float *D0,
-                   float *D1, DevState *ds, double *__restrict__ partials, unsigned *gbar, double *e_hist,
+                   float *D1, DevState *ds, double *__restrict__ partials, unsigned long long *gbar, double *e_hist,
                    cudaGraphConditionalHandle cond, int use_cond, int max_sweeps) {
   extern __shared__ __align__(16) float smr[];
   __shared__ double red[8];
   __shared__ DevState sd;
   __shared__ int s_ok, s_roll;
+  unsigned long long gep = 0;  // thread 0: the arrival count the next grid barrier waits for
   const int P = N / NP, G4 = 4 * G, NG2 = 2 * N * G;
   const int cl = threadIdx.x, gy = threadIdx.y;
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
@@ -234,7 +235,7 @@ __global__ void __launch_bounds__((PS && GS) ? T * PS * GS : 256, OCC)
     if (tid == 0) {
       part[blockIdx.x] = ba;
       part[gridDim.x + blockIdx.x] = bb;
-      s_ok = grid_barrier(gbar, gridDim.x, sd.spin);
+      s_ok = grid_barrier_count(gbar, gep += gridDim.x, sd.spin);
     }
     __syncthreads();
     if (!s_ok) {
@@ -304,10 +305,11 @@ static void launch_ms2(Handle &h, int P, cudaGraphConditionalHandle cond, int us
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+  k_zero_gcount<<<1, 1, 0, h.stream>>>(reinterpret_cast<unsigned long long *>(h.gbar));
   cudaLaunchKernelEx(&cfg, k_mx_inner_ms2<T, NP, PS, GS, OCC>, h.J, h.N, h.G, h.tt.n_types, (int)stage,
                      (const int32_t *)h.type, (const float *)h.tt.Linv32, (const float *)h.tt.Cin32,
                      (const float *)h.tt.Mp32, (const float *)h.w32, (const float *)h.z32, h.delta[0], h.delta[1],
-                     h.ds, h.partials, h.gbar, h.e_hist, cond, use_cond, max_sweeps);
+                     h.ds, h.partials, reinterpret_cast<unsigned long long *>(h.gbar), h.e_hist, cond, use_cond, max_sweeps);
 }
 
 // S16, one group (the slab workloads): fully specialised, with registers for

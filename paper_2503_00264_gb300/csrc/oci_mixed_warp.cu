@@ -277,13 +277,14 @@ template <int N, int OCC>
 __global__ void __launch_bounds__(kW2Threads, OCC)
     k_mx_inner_w2(int J, int n_types, int stage, const int32_t *__restrict__ type, const float *Linv_g,
                   const float *Cin_g, const float *Mp_g, const float *w_g, const float *__restrict__ z, float *D0,
-                  float *D1, DevState *ds, double *__restrict__ partials, unsigned *gbar, double *e_hist,
+                  float *D1, DevState *ds, double *__restrict__ partials, unsigned long long *gbar, double *e_hist,
                   cudaGraphConditionalHandle cond, int use_cond, int max_sweeps) {
   constexpr int P = N / kW2NP, CW = 32 / P;
   extern __shared__ __align__(16) float smw[];
   __shared__ double red[kW2Warps];
   __shared__ DevState sd;
   __shared__ int s_ok, s_roll;
+  unsigned long long gep = 0;  // thread 0: the arrival count the next grid barrier waits for
   const int tid = threadIdx.x, nthr = kW2Threads;
   if (tid == 0) sd = *ds;
   __syncthreads();
@@ -320,7 +321,7 @@ __global__ void __launch_bounds__(kW2Threads, OCC)
     if (tid == 0) {
       part[blockIdx.x] = ba;
       part[gridDim.x + blockIdx.x] = bb;
-      s_ok = grid_barrier(gbar, gridDim.x, sd.spin);
+      s_ok = grid_barrier_count(gbar, gep += gridDim.x, sd.spin);
     }
     __syncthreads();
     if (!s_ok) {
@@ -390,9 +391,10 @@ void launch_w2(Handle &h, cudaGraphConditionalHandle cond, int use_cond, int max
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+  k_zero_gcount<<<1, 1, 0, h.stream>>>(reinterpret_cast<unsigned long long *>(h.gbar));
   cudaLaunchKernelEx(&cfg, k_mx_inner_w2<N, OCC>, h.J, h.tt.n_types, (int)stage, (const int32_t *)h.type,
                      (const float *)h.tt.Linv32, (const float *)h.tt.Cin32, (const float *)h.tt.Mp32,
-                     (const float *)h.w32, (const float *)h.z32, h.delta[0], h.delta[1], h.ds, h.partials, h.gbar,
+                     (const float *)h.w32, (const float *)h.z32, h.delta[0], h.delta[1], h.ds, h.partials, reinterpret_cast<unsigned long long *>(h.gbar),
                      h.e_hist, cond, use_cond, max_sweeps);
 }
 
