@@ -22,7 +22,8 @@ pytestmark = pytest.mark.gpu
 # (seed, J, N, G, OCI_SWEEP_SHAPE "cells per block, angle chunks")
 CASES = [(91, 40, 8, 1, "64,2"), (92, 1000, 16, 1, "64,4"), (93, 333, 8, 2, "32,2"),
          (94, 2049, 32, 1, "32,4"), (95, 500, 16, 1, "32,8"), (96, 6000, 16, 1, "16,4"),
-         (98, 17, 16, 2, "16,4"), (99, 1024, 16, 2, "64,2")]
+         (98, 17, 16, 2, "16,4"), (99, 1024, 16, 2, "64,2"), (101, 300, 2, 3, "32,1"),
+         (102, 200, 4, 2, "16,2"), (103, 700, 8, 2, "4,4")]
 # OCI_SWEEP_MS: "grid" keeps the cooperative form, unset lets the cluster form take <= 16 blocks
 FORMS = {"grid": "grid", "cluster": None}
 
